@@ -1,0 +1,277 @@
+"""CPU oracle for TPC sector tracking — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import this
+package. The product path (``paper_2009_07515_gb300``) never imports it and shares no code with it.
+
+``tpc_oracle.c`` is compiled twice with gcc (``-ffp-contract=off``, no fast-math): REAL = double
+(``precision="f64"``) and REAL = float (``precision="f32"``). The step-by-step definition of what it
+computes is in the header of ``tpc_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpc_oracle.c")
+_lock = threading.Lock()
+_libs: dict = {}
+
+BRUTE_FORCE = 1
+
+
+def _lib_path(precision: str) -> str:
+    return os.path.join(_HERE, f"libtpcoracle_{precision}.so")
+
+
+def build(force: bool = False) -> None:
+    """Compile both precisions beside the source (a checker build; nothing on the product path)."""
+    with _lock:
+        for prec in ("f32", "f64"):
+            out = _lib_path(prec)
+            if (not force and os.path.exists(out)
+                    and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+                continue
+            tmp = out + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                   "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+            if prec == "f32":
+                cmd.insert(1, "-DORACLE_F32")
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, out)
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("bz", ctypes.c_double),
+        ("ky", ctypes.c_double), ("kw", ctypes.c_double), ("eps", ctypes.c_double),
+        ("chi_n_max", ctypes.c_double),
+        ("lmin", ctypes.c_int32),
+        ("sigma_y", ctypes.c_double), ("sigma_w", ctypes.c_double),
+        ("chi2_hit_max", ctypes.c_double),
+        ("n_miss_max", ctypes.c_int32),
+        ("win_nsig", ctypes.c_double), ("win_add", ctypes.c_double),
+        ("x0_per_row", ctypes.c_double),
+        ("max_sin", ctypes.c_double),
+        ("y_margin", ctypes.c_double),
+        ("nmin", ctypes.c_int32),
+        ("cov0", ctypes.c_double * 5),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cov0"}
+        d["cov0"] = list(self.cov0)
+        return d
+
+
+_P = ctypes.POINTER
+_i32p, _i64p, _f64p = _P(ctypes.c_int32), _P(ctypes.c_int64), _P(ctypes.c_double)
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("n_clusters", ctypes.c_int64),
+        ("up", _i32p), ("down", _i32p), ("up_c", _i32p), ("down_c", _i32p),
+        ("nb_margin", _f64p),
+        ("n_start", ctypes.c_int64), ("start", _i32p),
+        ("n_tracklets", ctypes.c_int64),
+        ("tl_sector", _i32p), ("tl_start", _i32p), ("tl_nhits", _i32p), ("tl_ndf", _i32p),
+        ("tl_row_ref", _i32p), ("tl_row_top", _i32p), ("tl_ok", _i32p),
+        ("tl_xref", _f64p), ("tl_param", _f64p), ("tl_cov", _f64p), ("tl_chi2", _f64p),
+        ("tl_margin", _f64p),
+        ("tl_hit_off", _i64p), ("tl_hits", _i32p),
+        ("n_tracks", ctypes.c_int64),
+        ("tr_sector", _i32p), ("tr_ndf", _i32p), ("tr_nhits", _i32p), ("tr_tracklet", _i32p),
+        ("tr_xref", _f64p), ("tr_param", _f64p), ("tr_cov", _f64p), ("tr_chi2", _f64p),
+        ("tr_hit_off", _i64p), ("tr_hits", _i32p),
+    ]
+
+
+def _load(precision: str):
+    if precision not in ("f32", "f64"):
+        raise ValueError("precision must be 'f32' or 'f64'")
+    if precision in _libs:
+        return _libs[precision]
+    build()
+    lib = ctypes.CDLL(_lib_path(precision))
+    pre = f"oracle_{precision}_"
+    f = getattr(lib, pre + "default_params"); f.argtypes = [_P(Params)]; f.restype = None
+    f = getattr(lib, pre + "track")
+    f.argtypes = [_P(Params), ctypes.c_int64, _P(ctypes.c_uint8), _P(ctypes.c_uint8), _f64p, _f64p,
+                  ctypes.c_int, ctypes.c_int, _P(_P(_Result))]
+    f.restype = ctypes.c_int
+    f = getattr(lib, pre + "free_result"); f.argtypes = [_P(_Result)]; f.restype = None
+    f = getattr(lib, pre + "propagate")
+    f.argtypes = [_P(Params), _f64p, _f64p, ctypes.c_double, ctypes.c_double, _f64p]
+    f.restype = ctypes.c_int
+    f = getattr(lib, pre + "update"); f.argtypes = [_P(Params), _f64p, _f64p, ctypes.c_double, ctypes.c_double]
+    f.restype = ctypes.c_double
+    f = getattr(lib, pre + "seed"); f.argtypes = [_P(Params), _f64p, _f64p]; f.restype = ctypes.c_int
+    f = getattr(lib, pre + "asin"); f.argtypes = [ctypes.c_double]; f.restype = ctypes.c_double
+    f = getattr(lib, pre + "row_x"); f.argtypes = [ctypes.c_int]; f.restype = ctypes.c_double
+    _libs[precision] = lib
+    return lib
+
+
+def default_params(precision: str = "f64", **overrides) -> Params:
+    p = Params()
+    getattr(_load(precision), f"oracle_{precision}_default_params")(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "cov0":
+            for i in range(5):
+                p.cov0[i] = float(v[i])
+        else:
+            setattr(p, k, v)
+    return p
+
+
+@dataclass
+class Result:
+    """Oracle output. Link arrays are in caller index space; tracks are in canonical order
+    (sector, smallest original cluster index); hit lists are in ascending row order."""
+    up: np.ndarray
+    down: np.ndarray
+    up_c: np.ndarray
+    down_c: np.ndarray
+    nb_margin: np.ndarray
+    start: np.ndarray
+    tl_sector: np.ndarray
+    tl_start: np.ndarray
+    tl_nhits: np.ndarray
+    tl_ndf: np.ndarray
+    tl_row_ref: np.ndarray
+    tl_row_top: np.ndarray
+    tl_ok: np.ndarray
+    tl_xref: np.ndarray
+    tl_param: np.ndarray
+    tl_cov: np.ndarray
+    tl_chi2: np.ndarray
+    tl_margin: np.ndarray
+    tl_hit_off: np.ndarray
+    tl_hits: np.ndarray
+    tr_sector: np.ndarray
+    tr_ndf: np.ndarray
+    tr_nhits: np.ndarray
+    tr_tracklet: np.ndarray
+    tr_xref: np.ndarray
+    tr_param: np.ndarray
+    tr_cov: np.ndarray
+    tr_chi2: np.ndarray
+    tr_hit_off: np.ndarray
+    tr_hits: np.ndarray
+
+    @property
+    def n_tracks(self) -> int:
+        return int(self.tr_sector.shape[0])
+
+    def track_hits(self, i: int) -> np.ndarray:
+        return self.tr_hits[self.tr_hit_off[i]:self.tr_hit_off[i + 1]]
+
+    def tracklet_hits(self, i: int) -> np.ndarray:
+        return self.tl_hits[self.tl_hit_off[i]:self.tl_hit_off[i + 1]]
+
+
+def _copy(ptr, n, dtype, shape=None):
+    if n == 0:
+        return np.zeros(shape if shape else (0,), dtype=dtype)
+    a = np.ctypeslib.as_array(ptr, shape=(n,)).copy().astype(dtype, copy=False)
+    return a.reshape(shape) if shape else a
+
+
+def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = None,
+          brute_force: bool = False, n_threads: int = 0) -> Result:
+    """Run the oracle tracker on one frame (clusters in caller order)."""
+    lib = _load(precision)
+    pre = f"oracle_{precision}_"
+    if params is None:
+        params = default_params(precision)
+    sector = np.ascontiguousarray(sector, dtype=np.uint8)
+    row = np.ascontiguousarray(row, dtype=np.uint8)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = int(y.shape[0])
+    if n_threads <= 0:
+        n_threads = 1
+    rp = _P(_Result)()
+    rc = getattr(lib, pre + "track")(
+        ctypes.byref(params), n, sector.ctypes.data_as(_P(ctypes.c_uint8)),
+        row.ctypes.data_as(_P(ctypes.c_uint8)), y.ctypes.data_as(_f64p), w.ctypes.data_as(_f64p),
+        BRUTE_FORCE if brute_force else 0, int(n_threads), ctypes.byref(rp))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the input (code {rc})")
+    try:
+        R = rp.contents
+        nt, ntr = int(R.n_tracklets), int(R.n_tracks)
+        tl_off = _copy(R.tl_hit_off, nt + 1, np.int64)
+        tr_off = _copy(R.tr_hit_off, ntr + 1, np.int64)
+        res = Result(
+            up=_copy(R.up, n, np.int32), down=_copy(R.down, n, np.int32),
+            up_c=_copy(R.up_c, n, np.int32), down_c=_copy(R.down_c, n, np.int32),
+            nb_margin=_copy(R.nb_margin, n, np.float64),
+            start=_copy(R.start, int(R.n_start), np.int32),
+            tl_sector=_copy(R.tl_sector, nt, np.int32), tl_start=_copy(R.tl_start, nt, np.int32),
+            tl_nhits=_copy(R.tl_nhits, nt, np.int32), tl_ndf=_copy(R.tl_ndf, nt, np.int32),
+            tl_row_ref=_copy(R.tl_row_ref, nt, np.int32), tl_row_top=_copy(R.tl_row_top, nt, np.int32),
+            tl_ok=_copy(R.tl_ok, nt, np.int32), tl_xref=_copy(R.tl_xref, nt, np.float64),
+            tl_param=_copy(R.tl_param, 5 * nt, np.float64, (nt, 5)),
+            tl_cov=_copy(R.tl_cov, 15 * nt, np.float64, (nt, 15)),
+            tl_chi2=_copy(R.tl_chi2, nt, np.float64), tl_margin=_copy(R.tl_margin, nt, np.float64),
+            tl_hit_off=tl_off, tl_hits=_copy(R.tl_hits, int(tl_off[-1]), np.int32),
+            tr_sector=_copy(R.tr_sector, ntr, np.int32), tr_ndf=_copy(R.tr_ndf, ntr, np.int32),
+            tr_nhits=_copy(R.tr_nhits, ntr, np.int32), tr_tracklet=_copy(R.tr_tracklet, ntr, np.int32),
+            tr_xref=_copy(R.tr_xref, ntr, np.float64),
+            tr_param=_copy(R.tr_param, 5 * ntr, np.float64, (ntr, 5)),
+            tr_cov=_copy(R.tr_cov, 15 * ntr, np.float64, (ntr, 15)),
+            tr_chi2=_copy(R.tr_chi2, ntr, np.float64),
+            tr_hit_off=tr_off, tr_hits=_copy(R.tr_hits, int(tr_off[-1]), np.int32))
+    finally:
+        getattr(lib, pre + "free_result")(rp)
+    return res
+
+
+# ---------------------------------------------------------------- unit entry points (pins)
+
+def propagate(P, C, x0, x1, *, precision="f64", params: Params | None = None):
+    lib = _load(precision)
+    params = params or default_params(precision)
+    P = np.array(P, dtype=np.float64).copy()
+    C = np.array(C, dtype=np.float64).reshape(5, 5).copy()
+    J = np.zeros((5, 5))
+    rc = getattr(lib, f"oracle_{precision}_propagate")(ctypes.byref(params), P.ctypes.data_as(_f64p),
+                                                       C.ctypes.data_as(_f64p), float(x0), float(x1),
+                                                       J.ctypes.data_as(_f64p))
+    return rc, P, C, J
+
+
+def update(P, C, ym, wm, *, precision="f64", params: Params | None = None):
+    lib = _load(precision)
+    params = params or default_params(precision)
+    P = np.array(P, dtype=np.float64).copy()
+    C = np.array(C, dtype=np.float64).reshape(5, 5).copy()
+    chi2 = getattr(lib, f"oracle_{precision}_update")(ctypes.byref(params), P.ctypes.data_as(_f64p),
+                                                      C.ctypes.data_as(_f64p), float(ym), float(wm))
+    return chi2, P, C
+
+
+def seed(h, *, precision="f64", params: Params | None = None):
+    """h: 3x3 array of (x, y, w) for the first, middle and last chain hits."""
+    lib = _load(precision)
+    params = params or default_params(precision)
+    h = np.ascontiguousarray(np.asarray(h, dtype=np.float64).reshape(9))
+    P = np.zeros(5)
+    rc = getattr(lib, f"oracle_{precision}_seed")(ctypes.byref(params), h.ctypes.data_as(_f64p),
+                                                  P.ctypes.data_as(_f64p))
+    return rc, P
+
+
+def asin(t: float, *, precision="f64") -> float:
+    return getattr(_load(precision), f"oracle_{precision}_asin")(float(t))
+
+
+def row_x(r: int, *, precision="f64") -> float:
+    return getattr(_load(precision), f"oracle_{precision}_row_x")(int(r))

@@ -1,0 +1,954 @@
+/*
+ * tpc_oracle.c — plain, slow CPU reference tracker for TPC sector tracking.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the package smoke check and the CPU-baseline leg of the
+ * benchmark may load this. The product path never calls it and shares no code with it.
+ *
+ * What it computes: the standalone TPC sector tracking of the paper's synchronous reconstruction
+ * (Sec. 6: the TPC tracking runs first standalone, without space-charge, field or hit-error
+ * corrections, on clusters whose z is unknown in continuous readout, Sec. 2; the algorithm is
+ * derived from the Run-2 HLT tracker). The paper names the method but defers its steps to the HLT
+ * papers it cites, so each step below states the reading this project takes:
+ *
+ *   1. per-(sector, row) search index (here: the row's hits sorted by drift coordinate w);
+ *   2. cellular-automaton neighbour finding: for each hit, the best (down, up) pair in rows r-1/r+1
+ *      by the mid-point deviation chi_n inside slope windows;
+ *   3. neighbour cleaning: keep only reciprocal links;
+ *   4. start hits: heads of cleaned chains (up link, no down link) of at least lmin hits;
+ *   5. tracklet construction: 3-point circle seed, Kalman filter (exact helix propagation in the
+ *      solenoid field, multiple-scattering noise, Joseph-form update) along the chain, outward
+ *      extension by row-by-row search, then an inward refit (covariance reset) through the found
+ *      hits and inward extension;
+ *   6. tracklet selection: each hit goes to the tracklet with the largest (nhits, -start index) key;
+ *      a tracklet becomes a track if it keeps >= nmin hits and at least half of its hits.
+ *
+ * Precision: compiled twice, REAL = double (FP64 oracle) and REAL = float (FP32 oracle), with
+ * -ffp-contract=off and no fast-math. Only +, -, *, /, sqrt are used on REAL values; asin is
+ * evaluated by half-angle argument reduction and its Maclaurin series (oracle_asin), so every REAL
+ * result is a fixed sequence of correctly rounded operations.
+ *
+ * Coordinates: sector s in [0,36) (s/18 = drift side, s%18 = phi sector), row r in [0,152) at
+ * x_r = 85 + r * 160/151 cm (sector-local, radial), y along the pad row, w = v_d * t_arrival.
+ * Track state at x: (y, w, sin(phi), t = dw/ds_xy, q/pT); curvature k = kq * (q/pT),
+ * kq = -0.0029979246 * Bz; d(sin phi)/dx = k.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifdef ORACLE_F32
+typedef float real;
+#define SQRT sqrtf
+#define ORACLE_SYM(name) oracle_f32_##name
+#else
+typedef double real;
+#define SQRT sqrt
+#define ORACLE_SYM(name) oracle_f64_##name
+#endif
+
+#define NSEC 36
+#define NROW 152
+
+/* ------------------------------------------------------------------------------------------------
+ * Parameters (interface in double; converted to REAL once)
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct {
+  double bz;          /* T */
+  double ky, kw, eps; /* neighbour windows: |dy| <= ky*dx + eps, |dw| <= kw*dx + eps */
+  double chi_n_max;   /* cut on the mid-point deviation dy^2 + dw^2 (cm^2) */
+  int32_t lmin;       /* minimum chain length for a start hit */
+  double sigma_y, sigma_w;
+  double chi2_hit_max;
+  int32_t n_miss_max; /* consecutive rows without a hit that end an extension */
+  double win_nsig, win_add; /* extension search window: nsig*sqrt(C) + add */
+  double x0_per_row;  /* X/X0 per row for the scattering noise; 0 = off */
+  double max_sin;
+  double y_margin;    /* stop when |y| > x*tan(10 deg) + y_margin */
+  int32_t nmin;       /* minimum hits of a voting tracklet and of a track */
+  double cov0[5];     /* initial diagonal covariance of the seed */
+} oracle_params;
+
+void ORACLE_SYM(default_params)(oracle_params* p) {
+  p->bz = 0.5;
+  p->ky = 2.0; p->kw = 2.4; p->eps = 0.5;
+  p->chi_n_max = 0.2;
+  p->lmin = 3;
+  p->sigma_y = 0.1; p->sigma_w = 0.1;
+  p->chi2_hit_max = 16.0;
+  p->n_miss_max = 5;
+  p->win_nsig = 3.0; p->win_add = 0.3;
+  p->x0_per_row = 0.03 / 152.0;
+  p->max_sin = 0.999;
+  p->y_margin = 1.0;
+  p->nmin = 10;
+  p->cov0[0] = 1.0; p->cov0[1] = 1.0; p->cov0[2] = 1.0; p->cov0[3] = 1.0; p->cov0[4] = 100.0;
+}
+
+typedef struct {
+  real kq;                 /* dk/d(q/pT) = -0.0029979246 * Bz */
+  real ky, kw, eps, chi_n_max;
+  int lmin;
+  real r00, r11;           /* measurement variances */
+  real chi2_hit_max;
+  int n_miss_max;
+  real win_nsig, win_add;
+  int ms_on;
+  real x0_row, ms_c, mass2;
+  real max_sin, y_margin, tan10;
+  int nmin;
+  real cov0[5];
+  real x[NROW];
+  int want_margins;
+} ctx_t;
+
+static void make_ctx(const oracle_params* p, ctx_t* c) {
+  c->kq = (real)(-0.0029979246 * p->bz);
+  c->ky = (real)p->ky; c->kw = (real)p->kw; c->eps = (real)p->eps;
+  c->chi_n_max = (real)p->chi_n_max;
+  c->lmin = p->lmin;
+  c->r00 = (real)(p->sigma_y * p->sigma_y);
+  c->r11 = (real)(p->sigma_w * p->sigma_w);
+  c->chi2_hit_max = (real)p->chi2_hit_max;
+  c->n_miss_max = p->n_miss_max;
+  c->win_nsig = (real)p->win_nsig; c->win_add = (real)p->win_add;
+  c->ms_on = p->x0_per_row > 0;
+  c->x0_row = (real)p->x0_per_row;
+  /* Highland: theta0 = 0.0136/(beta p) sqrt(x/X0) (1 + 0.038 ln(x/X0)); the log term is taken at
+   * the nominal per-row thickness, so theta0^2 = ms_c * (x/X0) / (beta^2 p^2). */
+  {
+    double hl = p->x0_per_row > 0 ? 0.0136 * (1.0 + 0.038 * log(p->x0_per_row)) : 0.0;
+    c->ms_c = (real)(hl * hl);
+  }
+  c->mass2 = (real)(0.13957039 * 0.13957039);
+  c->max_sin = (real)p->max_sin;
+  c->y_margin = (real)p->y_margin;
+  c->tan10 = (real)0.17632698070846498;
+  c->nmin = p->nmin;
+  for (int i = 0; i < 5; ++i) c->cov0[i] = (real)p->cov0[i];
+  for (int r = 0; r < NROW; ++r) c->x[r] = (real)85 + (real)r * ((real)160 / (real)151);
+  c->want_margins = 1;
+}
+
+static inline real absr(real v) { return v < 0 ? -v : v; }
+
+/* Relative distance of a decision variable from its cut, for tracing disagreements. */
+static inline void note_margin(double* m, real value, real cut) {
+  if (!m) return;
+  double d = fabs((double)value - (double)cut);
+  double s = fabs((double)cut);
+  double rel = s > 1e-30 ? d / s : d;
+  if (rel < *m) *m = rel;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * asin by half-angle reduction + Maclaurin series (no library transcendental):
+ *   asin(t)/t = 1 + t^2/6 + 3t^4/40 + 5t^6/112 + 35t^8/1152 + 63t^10/2816 + ...   for |t| < 0.1,
+ *   sin(a/2) = sin(a) / sqrt(2 (1 + cos a))  ->  asin(t) = 2 asin(t / sqrt(2 (1 + sqrt(1 - t^2)))).
+ * ---------------------------------------------------------------------------------------------- */
+static real asin_series_ratio(real t) {
+  real t2 = t * t;
+  return (real)1 +
+         t2 * ((real)0.16666666666666666 +
+               t2 * ((real)0.075 +
+                     t2 * ((real)0.044642857142857144 +
+                           t2 * ((real)0.030381944444444444 + t2 * (real)0.022372159090909092))));
+}
+static real asin_hr(real t) {
+  real scale = (real)1;
+  while (absr(t) >= (real)0.1) {
+    t = t / SQRT((real)2 * ((real)1 + SQRT((real)1 - t * t)));
+    scale = scale * (real)2;
+  }
+  return scale * t * asin_series_ratio(t);
+}
+/* asin(t)/t: arc length over chord for a circle, t = chord * k / 2 */
+static real arc_ratio(real t) {
+  if (absr(t) < (real)0.1) return asin_series_ratio(t);
+  return asin_hr(t) / t;
+}
+/* d/dt (asin(t)/t) */
+static real arc_ratio_deriv(real t) {
+  if (absr(t) < (real)0.1) {
+    real t2 = t * t;
+    return t * ((real)0.3333333333333333 +
+                t2 * ((real)0.3 +
+                      t2 * ((real)0.26785714285714285 +
+                            t2 * ((real)0.24305555555555555 + t2 * (real)0.22372159090909091))));
+  }
+  return ((real)1 / SQRT((real)1 - t * t) - arc_ratio(t)) / t;
+}
+
+double ORACLE_SYM(asin)(double t) { return (double)asin_hr((real)t); }
+
+/* ------------------------------------------------------------------------------------------------
+ * Small dense linear algebra (5x5), written out plainly.
+ * ---------------------------------------------------------------------------------------------- */
+static void mat_mul5(real A[5][5], real B[5][5], real O[5][5]) {
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 5; ++k) {
+      real acc = 0;
+      for (int j = 0; j < 5; ++j) acc += A[i][j] * B[j][k];
+      O[i][k] = acc;
+    }
+}
+static void mat_mul5_bt(real A[5][5], real B[5][5], real O[5][5]) { /* O = A * B^T */
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 5; ++k) {
+      real acc = 0;
+      for (int j = 0; j < 5; ++j) acc += A[i][j] * B[k][j];
+      O[i][k] = acc;
+    }
+}
+/* keep symmetric: the lower triangle (row >= column) is the value, mirrored to the upper */
+static void mirror_lower(real C[5][5]) {
+  for (int i = 0; i < 5; ++i)
+    for (int k = i + 1; k < 5; ++k) C[i][k] = C[k][i];
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Kalman filter pieces
+ * ---------------------------------------------------------------------------------------------- */
+
+/* Exact helix transport of (P, C) from x0 to x1 in the sector frame, with multiple-scattering
+ * process noise. Returns 0 on success, 1 if |sin phi| would reach max_sin. */
+static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real x1, double* m,
+                        real (*Jout)[5]) {
+  const real dx = x1 - x0;
+  const real k = cx->kq * P[4];
+  const real s0 = P[2];
+  const real s1 = s0 + k * dx;
+  note_margin(m, absr(s1), cx->max_sin);
+  if (!(absr(s1) < cx->max_sin)) return 1;
+  const real c0 = SQRT((real)1 - s0 * s0);
+  const real c1 = SQRT((real)1 - s1 * s1);
+  const real N = s0 + s1, D = c0 + c1;
+  const real dy = dx * (N / D);                 /* chord relation of a circle */
+  const real l = SQRT(dx * dx + dy * dy);       /* chord length in the xy plane */
+  const real t = l * k * (real)0.5;             /* sin of half the turning angle */
+  real a = l * arc_ratio(t);                    /* arc length */
+  if (dx < 0) a = -a;
+  const real tw = P[3];
+  /* Jacobian d(y1, w1, s1, t, q/pT) / d(y0, w0, s0, t, q/pT) */
+  const real DD = D * D;
+  const real dy_ds0 = dx * ((real)2 / D + N * (s0 / c0 + s1 / c1) / DD);
+  const real dy_dk = dx * dx * ((real)1 / D + N * s1 / (c1 * DD));
+  real da_dl = (real)1 / SQRT((real)1 - t * t);
+  real da_dk = l * l * (real)0.5 * arc_ratio_deriv(t); /* at fixed chord */
+  if (dx < 0) { da_dl = -da_dl; da_dk = -da_dk; }
+  const real dl_ds0 = dy * dy_ds0 / l;
+  const real dl_dk = dy * dy_dk / l;
+  real J[5][5];
+  memset(J, 0, sizeof(J));
+  for (int i = 0; i < 5; ++i) J[i][i] = 1;
+  J[0][2] = dy_ds0;
+  J[0][4] = dy_dk * cx->kq;
+  J[1][2] = tw * (da_dl * dl_ds0);
+  J[1][3] = a;
+  J[1][4] = tw * (da_dl * dl_dk + da_dk) * cx->kq;
+  J[2][4] = dx * cx->kq;
+  if (Jout) memcpy(Jout, J, sizeof(J));
+  /* state */
+  P[0] = P[0] + dy;
+  P[1] = P[1] + tw * a;
+  P[2] = s1;
+  /* covariance: J C J^T */
+  real T[5][5], O[5][5];
+  mat_mul5(J, C, T);
+  mat_mul5_bt(T, J, O);
+  mirror_lower(O);
+  /* multiple scattering: theta0^2 on the direction; var(sin phi) = c^2 (1+t^2) th^2,
+   * var(t) = (1+t^2)^2 th^2 */
+  if (cx->ms_on && P[4] != 0) {
+    const real one_tw2 = (real)1 + tw * tw;
+    const real pathf = SQRT(one_tw2) / c1;
+    const real xx0 = cx->x0_row * pathf;
+    const real p2 = one_tw2 / (P[4] * P[4]);
+    const real beta2 = p2 / (p2 + cx->mass2);
+    const real th2 = cx->ms_c * xx0 / (beta2 * p2);
+    O[2][2] = O[2][2] + th2 * (c1 * c1) * one_tw2;
+    O[3][3] = O[3][3] + th2 * one_tw2 * one_tw2;
+  }
+  memcpy(C, O, sizeof(O));
+  return 0;
+}
+
+/* chi2 of a measurement (ym, wm) against the state; returns +inf if S is not positive definite */
+static real kf_chi2(const ctx_t* cx, const real P[5], real C[5][5], real ym, real wm) {
+  const real S00 = C[0][0] + cx->r00, S01 = C[0][1], S10 = C[1][0], S11 = C[1][1] + cx->r11;
+  const real det = S00 * S11 - S01 * S10;
+  if (!(det > 0)) return (real)INFINITY;
+  const real i00 = S11 / det, i01 = -S01 / det, i10 = -S10 / det, i11 = S00 / det;
+  const real r0 = ym - P[0], r1 = wm - P[1];
+  return r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
+}
+
+/* Kalman update with measurement (ym, wm): gain K = C H^T S^-1, Joseph form
+ * C' = (I - K H) C (I - K H)^T + K R K^T, then symmetrised from the lower triangle. */
+static void kf_update(const ctx_t* cx, real P[5], real C[5][5], real ym, real wm) {
+  real S[2][2], Si[2][2];
+  S[0][0] = C[0][0] + cx->r00; S[0][1] = C[0][1] + 0;
+  S[1][0] = C[1][0] + 0;       S[1][1] = C[1][1] + cx->r11;
+  const real det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
+  Si[0][0] = S[1][1] / det; Si[0][1] = -S[0][1] / det;
+  Si[1][0] = -S[1][0] / det; Si[1][1] = S[0][0] / det;
+  real K[5][2];
+  for (int i = 0; i < 5; ++i)
+    for (int l = 0; l < 2; ++l) {
+      real acc = 0;
+      for (int m = 0; m < 2; ++m) acc += C[i][m] * Si[m][l]; /* (C H^T)[i][m] = C[i][m] */
+      K[i][l] = acc;
+    }
+  const real r[2] = {ym - P[0], wm - P[1]};
+  for (int i = 0; i < 5; ++i) {
+    real acc = 0;
+    for (int l = 0; l < 2; ++l) acc += K[i][l] * r[l];
+    P[i] = P[i] + acc;
+  }
+  real A[5][5], T[5][5], O[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) {
+      real kh = 0;
+      for (int l = 0; l < 2; ++l) kh += K[i][l] * (real)(l == j ? 1 : 0); /* (K H)[i][j] */
+      A[i][j] = (real)(i == j ? 1 : 0) - kh;
+    }
+  mat_mul5(A, C, T);
+  mat_mul5_bt(T, A, O);
+  real KR[5][2];
+  for (int i = 0; i < 5; ++i) {
+    real acc0 = 0, acc1 = 0;
+    acc0 += K[i][0] * cx->r00; acc0 += K[i][1] * (real)0;
+    acc1 += K[i][0] * (real)0; acc1 += K[i][1] * cx->r11;
+    KR[i][0] = acc0; KR[i][1] = acc1;
+  }
+  for (int i = 0; i < 5; ++i)
+    for (int k = 0; k < 5; ++k) {
+      real acc = 0;
+      for (int b = 0; b < 2; ++b) acc += KR[i][b] * K[k][b];
+      O[i][k] = O[i][k] + acc;
+    }
+  mirror_lower(O);
+  memcpy(C, O, sizeof(O));
+}
+
+/* Seed from three hits (x, y, w) of a chain: circle through them in (x, y), the state at the first
+ * hit, w-slope from the end points over the arc. Returns 0 on success. */
+static int kf_seed(const ctx_t* cx, const real h[3][3], real P[5], double* m) {
+  const real ax = h[1][0] - h[0][0], ay = h[1][1] - h[0][1];
+  const real bx = h[2][0] - h[0][0], by = h[2][1] - h[0][1];
+  const real cx_ = h[2][0] - h[1][0], cy = h[2][1] - h[1][1];
+  const real cross = ax * by - ay * bx;
+  const real d01 = SQRT(ax * ax + ay * ay);
+  const real d02 = SQRT(bx * bx + by * by);
+  const real d12 = SQRT(cx_ * cx_ + cy * cy);
+  const real k = (real)2 * cross / (d01 * d02 * d12);
+  const real sg = k * d02 * (real)0.5;      /* sin of the angle between chord and tangent */
+  note_margin(m, absr(sg), (real)1);
+  if (!(absr(sg) < (real)1)) return 1;
+  const real cg = SQRT((real)1 - sg * sg);
+  const real sphi = (by * cg - bx * sg) / d02;
+  note_margin(m, absr(sphi), cx->max_sin);
+  if (!(absr(sphi) < cx->max_sin)) return 1;
+  const real arc = d02 * arc_ratio(sg);
+  P[0] = h[0][1];
+  P[1] = h[0][2];
+  P[2] = sphi;
+  P[3] = (h[2][2] - h[0][2]) / arc;
+  P[4] = cx->kq != 0 ? k / cx->kq : (real)0;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Exported unit entry points (for the pins): one propagation, one update, one seed.
+ * State/covariance exchange in double: P[5], C[25] (row-major full matrix).
+ * ---------------------------------------------------------------------------------------------- */
+int ORACLE_SYM(propagate)(const oracle_params* p, double* P, double* C, double x0, double x1,
+                          double* J) {
+  ctx_t cx;
+  make_ctx(p, &cx);
+  real Pr[5], Cr[5][5], Jr[5][5];
+  for (int i = 0; i < 5; ++i) Pr[i] = (real)P[i];
+  for (int i = 0; i < 25; ++i) Cr[i / 5][i % 5] = (real)C[i];
+  memset(Jr, 0, sizeof(Jr));
+  int rc = kf_propagate(&cx, Pr, Cr, (real)x0, (real)x1, NULL, Jr);
+  for (int i = 0; i < 5; ++i) P[i] = Pr[i];
+  for (int i = 0; i < 25; ++i) C[i] = Cr[i / 5][i % 5];
+  if (J)
+    for (int i = 0; i < 25; ++i) J[i] = Jr[i / 5][i % 5];
+  return rc;
+}
+double ORACLE_SYM(update)(const oracle_params* p, double* P, double* C, double ym, double wm) {
+  ctx_t cx;
+  make_ctx(p, &cx);
+  real Pr[5], Cr[5][5];
+  for (int i = 0; i < 5; ++i) Pr[i] = (real)P[i];
+  for (int i = 0; i < 25; ++i) Cr[i / 5][i % 5] = (real)C[i];
+  real chi2 = kf_chi2(&cx, Pr, Cr, (real)ym, (real)wm);
+  kf_update(&cx, Pr, Cr, (real)ym, (real)wm);
+  for (int i = 0; i < 5; ++i) P[i] = Pr[i];
+  for (int i = 0; i < 25; ++i) C[i] = Cr[i / 5][i % 5];
+  return (double)chi2;
+}
+int ORACLE_SYM(seed)(const oracle_params* p, const double* h9, double* P) {
+  ctx_t cx;
+  make_ctx(p, &cx);
+  real h[3][3], Pr[5];
+  for (int i = 0; i < 9; ++i) h[i / 3][i % 3] = (real)h9[i];
+  int rc = kf_seed(&cx, h, Pr, NULL);
+  for (int i = 0; i < 5; ++i) P[i] = rc ? NAN : (double)Pr[i];
+  return rc;
+}
+double ORACLE_SYM(row_x)(int r) {
+  ctx_t cx;
+  oracle_params p;
+  ORACLE_SYM(default_params)(&p);
+  make_ctx(&p, &cx);
+  return (r >= 0 && r < NROW) ? (double)cx.x[r] : NAN;
+}
+
+/* ------------------------------------------------------------------------------------------------
+ * Whole-frame tracker
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct {
+  int64_t n_clusters;
+  /* links in caller (original) index space, -1 = none */
+  int32_t *up, *down, *up_c, *down_c;
+  double* nb_margin;               /* per cluster: min relative margin of its neighbour decisions */
+  /* start hits in canonical order (sector, original index) */
+  int64_t n_start;
+  int32_t* start;
+  /* tracklets (one per start hit, same order) */
+  int64_t n_tracklets;
+  int32_t *tl_sector, *tl_start, *tl_nhits, *tl_ndf, *tl_row_ref, *tl_row_top, *tl_ok;
+  double *tl_xref, *tl_param, *tl_cov, *tl_chi2, *tl_margin;
+  int64_t* tl_hit_off;             /* [n_tracklets + 1] */
+  int32_t* tl_hits;                /* original indices, ascending row */
+  /* tracks in canonical order (sector, smallest original index of its hits) */
+  int64_t n_tracks;
+  int32_t *tr_sector, *tr_ndf, *tr_nhits, *tr_tracklet;
+  double *tr_xref, *tr_param, *tr_cov, *tr_chi2;
+  int64_t* tr_hit_off;
+  int32_t* tr_hits;                /* original indices, ascending row */
+} oracle_result;
+
+#define ORACLE_BRUTE_FORCE 1
+
+typedef struct {
+  int64_t n;                 /* clusters of this sector */
+  int64_t row_start[NROW + 1];
+  int32_t* orig;             /* sorted by (row, w, orig) */
+  real *y, *w;
+  int32_t *up, *dn, *upc, *dnc; /* local indices */
+  double* nbm;
+  /* tracklets */
+  int64_t nt, cap_t;
+  int32_t *t_start, *t_rank, *t_nhits, *t_ndf, *t_rref, *t_rtop, *t_ok;
+  real *t_x, *t_p, *t_c, *t_chi2;
+  double* t_m;
+  int32_t* t_slots;          /* [nt][NROW] local hit per row, -1 */
+  /* tracks */
+  int64_t ntr;
+  int32_t* tr_t;             /* tracklet index */
+  int32_t* tr_nk;            /* kept hits */
+  int32_t* tr_min;           /* smallest original index among kept hits */
+  uint64_t* weight;          /* per local hit */
+} sector_t;
+
+/* Each row is ordered by (w, y, original index). A hit's position in this order (its "rank") is
+ * the tie-break of every arg-min below and of the selection key, so results do not depend on the
+ * caller's cluster order unless two clusters of a row have identical coordinates. */
+typedef struct { real w; int32_t orig; real y; } rowhit;
+static int cmp_rowhit(const void* a, const void* b) {
+  const rowhit* x = (const rowhit*)a;
+  const rowhit* y = (const rowhit*)b;
+  if (x->w < y->w) return -1;
+  if (x->w > y->w) return 1;
+  if (x->y < y->y) return -1;
+  if (x->y > y->y) return 1;
+  return x->orig < y->orig ? -1 : (x->orig > y->orig);
+}
+
+/* first local index in row r with w >= v (rows are sorted by w) */
+static int64_t row_lower_bound(const sector_t* S, int r, real v) {
+  int64_t lo = S->row_start[r], hi = S->row_start[r + 1];
+  while (lo < hi) {
+    int64_t mid = lo + (hi - lo) / 2;
+    if (S->w[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/* candidates in row rr of hit (yi, wi) within |dy| <= wy, |dw| <= ww: index range to scan */
+static void scan_range(const sector_t* S, int rr, real wi, real ww, int brute, int64_t* b, int64_t* e) {
+  if (brute) { *b = S->row_start[rr]; *e = S->row_start[rr + 1]; return; }
+  /* widen by a hair so that hits just outside the window are visited for the margin trace; the
+   * exact window test below decides */
+  real pad = ww * (real)1e-3 + (real)1e-3;
+  *b = row_lower_bound(S, rr, wi - ww - pad);
+  int64_t hi = row_lower_bound(S, rr, wi + ww + pad);
+  while (hi < S->row_start[rr + 1] && !(S->w[hi] > wi + ww + pad)) ++hi;
+  *e = hi;
+}
+
+static void find_neighbours(const ctx_t* cx, sector_t* S, int brute) {
+  for (int64_t i = 0; i < S->n; ++i) { S->up[i] = -1; S->dn[i] = -1; S->nbm[i] = INFINITY; }
+  for (int r = 1; r + 1 < NROW; ++r) {
+    const real dxm = cx->x[r] - cx->x[r - 1];
+    const real dxp = cx->x[r + 1] - cx->x[r];
+    const real wy_dn = cx->ky * dxm + cx->eps, ww_dn = cx->kw * dxm + cx->eps;
+    const real wy_up = cx->ky * dxp + cx->eps, ww_up = cx->kw * dxp + cx->eps;
+    const real f = dxm / (dxm + dxp);
+    for (int64_t i = S->row_start[r]; i < S->row_start[r + 1]; ++i) {
+      const real yi = S->y[i], wi = S->w[i];
+      double* m = &S->nbm[i];
+      int64_t db, de, ub, ue;
+      scan_range(S, r - 1, wi, ww_dn, brute, &db, &de);
+      scan_range(S, r + 1, wi, ww_up, brute, &ub, &ue);
+      real best = (real)INFINITY, second = (real)INFINITY;
+      int64_t bd = -1, bu = -1;
+      for (int64_t d = db; d < de; ++d) {
+        const real ady = absr(S->y[d] - yi), adw = absr(S->w[d] - wi);
+        note_margin(m, ady, wy_dn);
+        note_margin(m, adw, ww_dn);
+        if (!(ady <= wy_dn && adw <= ww_dn)) continue;
+        for (int64_t u = ub; u < ue; ++u) {
+          const real uy = absr(S->y[u] - yi), uw = absr(S->w[u] - wi);
+          note_margin(m, uy, wy_up);
+          note_margin(m, uw, ww_up);
+          if (!(uy <= wy_up && uw <= ww_up)) continue;
+          const real py = S->y[d] + (S->y[u] - S->y[d]) * f;
+          const real pw = S->w[d] + (S->w[u] - S->w[d]) * f;
+          const real ey = yi - py, ew = wi - pw;
+          const real chi = ey * ey + ew * ew;
+          /* lexicographic minimum of (chi_n, rank of d, rank of u) */
+          int better;
+          if (bd < 0 || chi < best) better = 1;
+          else if (chi > best) better = 0;
+          else if (d != bd) better = d < bd;
+          else better = u < bu;
+          if (better) { second = best; best = chi; bd = d; bu = u; }
+          else if (chi < second) second = chi;
+        }
+      }
+      if (bd >= 0) {
+        note_margin(m, best, cx->chi_n_max);
+        if (second < (real)INFINITY) note_margin(m, second, best);
+        if (best <= cx->chi_n_max) { S->dn[i] = (int32_t)bd; S->up[i] = (int32_t)bu; }
+      }
+    }
+  }
+}
+
+static void clean_links(sector_t* S) {
+  for (int64_t i = 0; i < S->n; ++i) {
+    int32_t u = S->up[i], d = S->dn[i];
+    S->upc[i] = (u >= 0 && S->dn[u] == i) ? u : -1;
+    S->dnc[i] = (d >= 0 && S->up[d] == i) ? d : -1;
+  }
+}
+
+/* Search row r of the sector for the hit with the smallest chi2 inside the window around the
+ * predicted (y, w). Returns the local index or -1, and its chi2. */
+static int64_t search_row(const ctx_t* cx, const sector_t* S, int r, const real P[5], real C[5][5],
+                          real* chi2_out, double* m) {
+  const real wy = cx->win_nsig * SQRT(C[0][0]) + cx->win_add;
+  const real ww = cx->win_nsig * SQRT(C[1][1]) + cx->win_add;
+  int64_t b, e;
+  scan_range(S, r, P[1], ww, 0, &b, &e);
+  int64_t best = -1;
+  real bchi = (real)INFINITY, second = (real)INFINITY;
+  for (int64_t h = b; h < e; ++h) {
+    const real ady = absr(S->y[h] - P[0]), adw = absr(S->w[h] - P[1]);
+    note_margin(m, ady, wy);
+    note_margin(m, adw, ww);
+    if (!(ady <= wy && adw <= ww)) continue;
+    const real chi = kf_chi2(cx, P, C, S->y[h], S->w[h]);
+    /* lexicographic minimum of (chi2, rank) */
+    int better;
+    if (best < 0 || chi < bchi) better = 1;
+    else if (chi > bchi) better = 0;
+    else better = h < best;
+    if (better) { second = bchi; bchi = chi; best = h; }
+    else if (chi < second) second = chi;
+  }
+  if (best >= 0 && second < (real)INFINITY) note_margin(m, second, bchi);
+  *chi2_out = bchi;
+  return best;
+}
+
+static void add_tracklet_storage(sector_t* S) {
+  if (S->nt < S->cap_t) return;
+  int64_t nc = S->cap_t ? 2 * S->cap_t : 64;
+  S->t_start = realloc(S->t_start, nc * sizeof(int32_t));
+  S->t_rank = realloc(S->t_rank, nc * sizeof(int32_t));
+  S->t_nhits = realloc(S->t_nhits, nc * sizeof(int32_t));
+  S->t_ndf = realloc(S->t_ndf, nc * sizeof(int32_t));
+  S->t_rref = realloc(S->t_rref, nc * sizeof(int32_t));
+  S->t_rtop = realloc(S->t_rtop, nc * sizeof(int32_t));
+  S->t_ok = realloc(S->t_ok, nc * sizeof(int32_t));
+  S->t_x = realloc(S->t_x, nc * sizeof(real));
+  S->t_p = realloc(S->t_p, nc * 5 * sizeof(real));
+  S->t_c = realloc(S->t_c, nc * 15 * sizeof(real));
+  S->t_chi2 = realloc(S->t_chi2, nc * sizeof(real));
+  S->t_m = realloc(S->t_m, nc * sizeof(double));
+  S->t_slots = realloc(S->t_slots, nc * NROW * sizeof(int32_t));
+  S->cap_t = nc;
+}
+
+/* Build the tracklet of start hit h0 (local index) in row r0. */
+static void build_tracklet(const ctx_t* cx, sector_t* S, int64_t h0, int r0) {
+  add_tracklet_storage(S);
+  const int64_t t = S->nt++;
+  double mg = INFINITY;
+  double* m = cx->want_margins ? &mg : NULL;
+  int32_t* slotC = &S->t_slots[t * NROW];
+  int32_t slotAB[NROW];
+  for (int r = 0; r < NROW; ++r) { slotC[r] = -1; slotAB[r] = -1; }
+  S->t_start[t] = S->orig[h0];
+  S->t_rank[t] = (int32_t)h0;
+  S->t_ok[t] = 0; S->t_nhits[t] = 0; S->t_ndf[t] = -5; S->t_rref[t] = -1; S->t_rtop[t] = -1;
+  S->t_x[t] = 0; S->t_chi2[t] = 0;
+  for (int i = 0; i < 5; ++i) S->t_p[t * 5 + i] = 0;
+  for (int i = 0; i < 15; ++i) S->t_c[t * 15 + i] = 0;
+  /* the chain */
+  int64_t chain[NROW];
+  int mlen = 0;
+  for (int64_t h = h0; h >= 0 && mlen < NROW; h = S->upc[h]) chain[mlen++] = h;
+  /* seed */
+  real hh[3][3];
+  const int64_t hs[3] = {chain[0], chain[mlen / 2], chain[mlen - 1]};
+  const int rs[3] = {r0, r0 + mlen / 2, r0 + mlen - 1};
+  for (int j = 0; j < 3; ++j) { hh[j][0] = cx->x[rs[j]]; hh[j][1] = S->y[hs[j]]; hh[j][2] = S->w[hs[j]]; }
+  real P[5], C[5][5];
+  if (kf_seed(cx, hh, P, m)) { S->t_m[t] = mg; return; }
+  memset(C, 0, sizeof(C));
+  for (int i = 0; i < 5; ++i) C[i][i] = cx->cov0[i];
+  /* Phase A (chain) and B (outward extension) */
+  real Ptop[5], Ctop[5][5];
+  int top = -1, nmiss = 0;
+  for (int r = r0; r < NROW; ++r) {
+    if (r > r0) {
+      if (kf_propagate(cx, P, C, cx->x[r - 1], cx->x[r], m, NULL)) break;
+      const real lim = cx->x[r] * cx->tan10 + cx->y_margin;
+      note_margin(m, absr(P[0]), lim);
+      if (absr(P[0]) > lim) break;
+    }
+    int64_t hit;
+    real chi;
+    if (r < r0 + mlen) {
+      hit = chain[r - r0];
+      chi = kf_chi2(cx, P, C, S->y[hit], S->w[hit]);
+    } else {
+      hit = search_row(cx, S, r, P, C, &chi, m);
+    }
+    if (hit >= 0) note_margin(m, chi, cx->chi2_hit_max);
+    if (hit >= 0 && chi <= cx->chi2_hit_max) {
+      kf_update(cx, P, C, S->y[hit], S->w[hit]);
+      slotAB[r] = (int32_t)hit;
+      nmiss = 0;
+      top = r;
+      memcpy(Ptop, P, sizeof(Ptop));
+      memcpy(Ctop, C, sizeof(Ctop));
+    } else {
+      ++nmiss;
+      if (r >= r0 + mlen && nmiss >= cx->n_miss_max) break;
+    }
+  }
+  if (top < 0) { S->t_m[t] = mg; return; }
+  /* Phase C: inward refit from the outermost hit with the covariance reset, then inward extension */
+  memcpy(P, Ptop, sizeof(P));
+  memset(C, 0, sizeof(C));
+  for (int i = 0; i < 5; ++i) C[i][i] = cx->cov0[i];
+  real Pout[5], Cout[5][5];
+  int ref = -1, nh = 0;
+  real chi2sum = 0;
+  nmiss = 0;
+  for (int r = top; r >= 0; --r) {
+    if (r < top) {
+      if (kf_propagate(cx, P, C, cx->x[r + 1], cx->x[r], m, NULL)) break;
+      const real lim = cx->x[r] * cx->tan10 + cx->y_margin;
+      note_margin(m, absr(P[0]), lim);
+      if (absr(P[0]) > lim) break;
+    }
+    int64_t hit;
+    real chi = (real)INFINITY;
+    if (r >= r0) {
+      hit = slotAB[r];
+      if (hit >= 0) chi = kf_chi2(cx, P, C, S->y[hit], S->w[hit]);
+    } else {
+      hit = search_row(cx, S, r, P, C, &chi, m);
+    }
+    if (hit >= 0) note_margin(m, chi, cx->chi2_hit_max);
+    if (hit >= 0 && chi <= cx->chi2_hit_max) {
+      kf_update(cx, P, C, S->y[hit], S->w[hit]);
+      slotC[r] = (int32_t)hit;
+      ++nh;
+      chi2sum = chi2sum + chi;
+      nmiss = 0;
+      ref = r;
+      memcpy(Pout, P, sizeof(Pout));
+      memcpy(Cout, C, sizeof(Cout));
+    } else {
+      ++nmiss;
+      if (r < r0 && nmiss >= cx->n_miss_max) break;
+    }
+  }
+  S->t_m[t] = mg;
+  if (ref < 0) return;
+  S->t_ok[t] = 1;
+  S->t_nhits[t] = nh;
+  S->t_ndf[t] = 2 * nh - 5;
+  S->t_rref[t] = ref;
+  S->t_rtop[t] = top;
+  S->t_x[t] = cx->x[ref];
+  S->t_chi2[t] = chi2sum;
+  for (int i = 0; i < 5; ++i) S->t_p[t * 5 + i] = Pout[i];
+  for (int i = 0, o = 0; i < 5; ++i)
+    for (int k = 0; k <= i; ++k, ++o) S->t_c[t * 15 + o] = Cout[i][k];
+}
+
+/* selection key: more hits first, then the smaller rank (position in the sector's row-ordered
+ * hits) of the start hit; unique within a sector */
+static uint64_t tracklet_key(const sector_t* S, int64_t t) {
+  return ((uint64_t)(uint32_t)S->t_nhits[t] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)S->t_rank[t]);
+}
+
+static void select_tracks(const ctx_t* cx, sector_t* S) {
+  S->weight = (uint64_t*)calloc(S->n > 0 ? S->n : 1, sizeof(uint64_t));
+  for (int64_t t = 0; t < S->nt; ++t) {
+    if (!S->t_ok[t] || S->t_nhits[t] < cx->nmin) continue;
+    const uint64_t key = tracklet_key(S, t);
+    for (int r = 0; r < NROW; ++r) {
+      int32_t h = S->t_slots[t * NROW + r];
+      if (h >= 0 && S->weight[h] < key) S->weight[h] = key;
+    }
+  }
+  S->tr_t = (int32_t*)malloc(sizeof(int32_t) * (S->nt > 0 ? S->nt : 1));
+  S->tr_nk = (int32_t*)malloc(sizeof(int32_t) * (S->nt > 0 ? S->nt : 1));
+  S->tr_min = (int32_t*)malloc(sizeof(int32_t) * (S->nt > 0 ? S->nt : 1));
+  S->ntr = 0;
+  for (int64_t t = 0; t < S->nt; ++t) {
+    if (!S->t_ok[t] || S->t_nhits[t] < cx->nmin) continue;
+    const uint64_t key = tracklet_key(S, t);
+    int kept = 0;
+    int32_t mn = INT32_MAX;
+    for (int r = 0; r < NROW; ++r) {
+      int32_t h = S->t_slots[t * NROW + r];
+      if (h >= 0 && S->weight[h] == key) {
+        ++kept;
+        if (S->orig[h] < mn) mn = S->orig[h];
+      }
+    }
+    if (kept >= cx->nmin && 2 * kept >= S->t_nhits[t]) {
+      S->tr_t[S->ntr] = (int32_t)t;
+      S->tr_nk[S->ntr] = kept;
+      S->tr_min[S->ntr] = mn;
+      S->ntr++;
+    }
+  }
+}
+
+static void track_sector(const ctx_t* cx, sector_t* S, int brute) {
+  find_neighbours(cx, S, brute);
+  clean_links(S);
+  /* start hits in (row, w, orig) order; tracklets are built independently of each other */
+  for (int r = 1; r + 1 < NROW; ++r)
+    for (int64_t i = S->row_start[r]; i < S->row_start[r + 1]; ++i) {
+      if (!(S->upc[i] >= 0 && S->dnc[i] < 0)) continue;
+      int len = 1;
+      for (int64_t h = S->upc[i]; h >= 0 && len < cx->lmin; h = S->upc[h]) ++len;
+      if (len < cx->lmin) continue;
+      build_tracklet(cx, S, i, r);
+    }
+  select_tracks(cx, S);
+}
+
+/* bottom-up merge sort of idx[] by key[] (stable) for the canonical output order */
+static void sort_idx_by_key(int32_t* idx, int64_t n, const int32_t* key) {
+  if (n < 2) return;
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * n);
+  for (int64_t width = 1; width < n; width *= 2) {
+    for (int64_t lo = 0; lo < n; lo += 2 * width) {
+      int64_t mid = lo + width < n ? lo + width : n, hi = lo + 2 * width < n ? lo + 2 * width : n;
+      int64_t a = lo, b = mid, o = lo;
+      while (a < mid && b < hi) tmp[o++] = (key[idx[b]] < key[idx[a]]) ? idx[b++] : idx[a++];
+      while (a < mid) tmp[o++] = idx[a++];
+      while (b < hi) tmp[o++] = idx[b++];
+    }
+    memcpy(idx, tmp, sizeof(int32_t) * n);
+  }
+  free(tmp);
+}
+
+void ORACLE_SYM(free_result)(oracle_result* R) {
+  if (!R) return;
+  free(R->up); free(R->down); free(R->up_c); free(R->down_c); free(R->nb_margin); free(R->start);
+  free(R->tl_sector); free(R->tl_start); free(R->tl_nhits); free(R->tl_ndf); free(R->tl_row_ref);
+  free(R->tl_row_top); free(R->tl_ok); free(R->tl_xref); free(R->tl_param); free(R->tl_cov);
+  free(R->tl_chi2); free(R->tl_margin); free(R->tl_hit_off); free(R->tl_hits);
+  free(R->tr_sector); free(R->tr_ndf); free(R->tr_nhits); free(R->tr_tracklet); free(R->tr_xref);
+  free(R->tr_param); free(R->tr_cov); free(R->tr_chi2); free(R->tr_hit_off); free(R->tr_hits);
+  free(R);
+}
+
+static void free_sector(sector_t* S) {
+  free(S->orig); free(S->y); free(S->w); free(S->up); free(S->dn); free(S->upc); free(S->dnc);
+  free(S->nbm); free(S->t_start); free(S->t_rank); free(S->t_nhits); free(S->t_ndf); free(S->t_rref); free(S->t_rtop);
+  free(S->t_ok); free(S->t_x); free(S->t_p); free(S->t_c); free(S->t_chi2); free(S->t_m);
+  free(S->t_slots); free(S->tr_t); free(S->tr_nk); free(S->tr_min); free(S->weight);
+}
+
+/* Track one frame. Inputs: n clusters in caller order (sector, row, y, w); y and w are given in
+ * double and rounded to REAL on entry. flags: ORACLE_BRUTE_FORCE scans whole rows in the neighbour
+ * search instead of the sorted-w index. n_threads > 0 runs sectors in parallel (sectors are
+ * independent). Returns 0, or -1 for malformed input, -2 for allocation failure. */
+int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, const uint8_t* row,
+                      const double* y, const double* w, int flags, int n_threads,
+                      oracle_result** out) {
+  *out = NULL;
+  if (n < 0 || n >= INT32_MAX) return -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (sector[i] >= NSEC || row[i] >= NROW || !isfinite(y[i]) || !isfinite(w[i])) return -1;
+  ctx_t cx;
+  make_ctx(p, &cx);
+  sector_t* secs = (sector_t*)calloc(NSEC, sizeof(sector_t));
+  /* group by sector and row; rows sorted by (w, orig) */
+  int64_t cnt[NSEC][NROW];
+  memset(cnt, 0, sizeof(cnt));
+  for (int64_t i = 0; i < n; ++i) cnt[sector[i]][row[i]]++;
+  for (int s = 0; s < NSEC; ++s) {
+    sector_t* S = &secs[s];
+    S->row_start[0] = 0;
+    for (int r = 0; r < NROW; ++r) S->row_start[r + 1] = S->row_start[r] + cnt[s][r];
+    S->n = S->row_start[NROW];
+    int64_t na = S->n > 0 ? S->n : 1;
+    S->orig = malloc(na * sizeof(int32_t));
+    S->y = malloc(na * sizeof(real)); S->w = malloc(na * sizeof(real));
+    S->up = malloc(na * sizeof(int32_t)); S->dn = malloc(na * sizeof(int32_t));
+    S->upc = malloc(na * sizeof(int32_t)); S->dnc = malloc(na * sizeof(int32_t));
+    S->nbm = malloc(na * sizeof(double));
+  }
+  {
+    int64_t fill[NSEC][NROW];
+    for (int s = 0; s < NSEC; ++s)
+      for (int r = 0; r < NROW; ++r) fill[s][r] = secs[s].row_start[r];
+    for (int64_t i = 0; i < n; ++i) {
+      sector_t* S = &secs[sector[i]];
+      int64_t o = fill[sector[i]][row[i]]++;
+      S->orig[o] = (int32_t)i; S->y[o] = (real)y[i]; S->w[o] = (real)w[i];
+    }
+  }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
+  for (int s = 0; s < NSEC; ++s) {
+    sector_t* S = &secs[s];
+    for (int r = 0; r < NROW; ++r) {
+      int64_t b = S->row_start[r], m = S->row_start[r + 1] - b;
+      if (m < 2) continue;
+      rowhit* tmp = (rowhit*)malloc(m * sizeof(rowhit));
+      for (int64_t j = 0; j < m; ++j) { tmp[j].w = S->w[b + j]; tmp[j].orig = S->orig[b + j]; tmp[j].y = S->y[b + j]; }
+      qsort(tmp, m, sizeof(rowhit), cmp_rowhit);
+      for (int64_t j = 0; j < m; ++j) { S->w[b + j] = tmp[j].w; S->orig[b + j] = tmp[j].orig; S->y[b + j] = tmp[j].y; }
+      free(tmp);
+    }
+    track_sector(&cx, S, flags & ORACLE_BRUTE_FORCE);
+  }
+  /* gather results */
+  oracle_result* R = (oracle_result*)calloc(1, sizeof(oracle_result));
+  int64_t na = n > 0 ? n : 1;
+  R->n_clusters = n;
+  R->up = malloc(na * sizeof(int32_t)); R->down = malloc(na * sizeof(int32_t));
+  R->up_c = malloc(na * sizeof(int32_t)); R->down_c = malloc(na * sizeof(int32_t));
+  R->nb_margin = malloc(na * sizeof(double));
+  int64_t nt = 0, ntr = 0, nhl = 0, nhr = 0;
+  for (int s = 0; s < NSEC; ++s) {
+    sector_t* S = &secs[s];
+    for (int64_t i = 0; i < S->n; ++i) {
+      int32_t o = S->orig[i];
+      R->up[o] = S->up[i] >= 0 ? S->orig[S->up[i]] : -1;
+      R->down[o] = S->dn[i] >= 0 ? S->orig[S->dn[i]] : -1;
+      R->up_c[o] = S->upc[i] >= 0 ? S->orig[S->upc[i]] : -1;
+      R->down_c[o] = S->dnc[i] >= 0 ? S->orig[S->dnc[i]] : -1;
+      R->nb_margin[o] = S->nbm[i];
+    }
+    nt += S->nt;
+    ntr += S->ntr;
+    for (int64_t t = 0; t < S->nt; ++t) nhl += S->t_ok[t] ? S->t_nhits[t] : 0;
+    for (int64_t k = 0; k < S->ntr; ++k) nhr += S->tr_nk[k];
+  }
+  R->n_start = nt;
+  R->n_tracklets = nt;
+  int64_t ta = nt > 0 ? nt : 1, ra = ntr > 0 ? ntr : 1;
+  R->start = malloc(ta * sizeof(int32_t));
+  R->tl_sector = malloc(ta * sizeof(int32_t)); R->tl_start = malloc(ta * sizeof(int32_t));
+  R->tl_nhits = malloc(ta * sizeof(int32_t)); R->tl_ndf = malloc(ta * sizeof(int32_t));
+  R->tl_row_ref = malloc(ta * sizeof(int32_t)); R->tl_row_top = malloc(ta * sizeof(int32_t));
+  R->tl_ok = malloc(ta * sizeof(int32_t));
+  R->tl_xref = malloc(ta * sizeof(double)); R->tl_param = malloc(ta * 5 * sizeof(double));
+  R->tl_cov = malloc(ta * 15 * sizeof(double)); R->tl_chi2 = malloc(ta * sizeof(double));
+  R->tl_margin = malloc(ta * sizeof(double));
+  R->tl_hit_off = malloc((nt + 1) * sizeof(int64_t));
+  R->tl_hits = malloc((nhl > 0 ? nhl : 1) * sizeof(int32_t));
+  R->n_tracks = ntr;
+  R->tr_sector = malloc(ra * sizeof(int32_t)); R->tr_ndf = malloc(ra * sizeof(int32_t));
+  R->tr_nhits = malloc(ra * sizeof(int32_t)); R->tr_tracklet = malloc(ra * sizeof(int32_t));
+  R->tr_xref = malloc(ra * sizeof(double)); R->tr_param = malloc(ra * 5 * sizeof(double));
+  R->tr_cov = malloc(ra * 15 * sizeof(double)); R->tr_chi2 = malloc(ra * sizeof(double));
+  R->tr_hit_off = malloc((ntr + 1) * sizeof(int64_t));
+  R->tr_hits = malloc((nhr > 0 ? nhr : 1) * sizeof(int32_t));
+  int64_t ot = 0, otr = 0, ohl = 0, ohr = 0;
+  R->tl_hit_off[0] = 0;
+  R->tr_hit_off[0] = 0;
+  for (int s = 0; s < NSEC; ++s) {
+    sector_t* S = &secs[s];
+    /* tracklets in (original start index) order */
+    int32_t* ti = malloc((S->nt > 0 ? S->nt : 1) * sizeof(int32_t));
+    for (int64_t t = 0; t < S->nt; ++t) ti[t] = (int32_t)t;
+    sort_idx_by_key(ti, S->nt, S->t_start);
+    int32_t* tpos = malloc((S->nt > 0 ? S->nt : 1) * sizeof(int32_t));
+    for (int64_t j = 0; j < S->nt; ++j) {
+      int64_t t = ti[j];
+      tpos[t] = (int32_t)(ot);
+      R->start[ot] = S->t_start[t];
+      R->tl_sector[ot] = s; R->tl_start[ot] = S->t_start[t]; R->tl_nhits[ot] = S->t_nhits[t];
+      R->tl_ndf[ot] = S->t_ndf[t]; R->tl_row_ref[ot] = S->t_rref[t]; R->tl_row_top[ot] = S->t_rtop[t];
+      R->tl_ok[ot] = S->t_ok[t]; R->tl_xref[ot] = S->t_x[t]; R->tl_chi2[ot] = S->t_chi2[t];
+      R->tl_margin[ot] = S->t_m[t];
+      for (int i = 0; i < 5; ++i) R->tl_param[ot * 5 + i] = S->t_p[t * 5 + i];
+      for (int i = 0; i < 15; ++i) R->tl_cov[ot * 15 + i] = S->t_c[t * 15 + i];
+      if (S->t_ok[t])
+        for (int r = 0; r < NROW; ++r) {
+          int32_t h = S->t_slots[t * NROW + r];
+          if (h >= 0) R->tl_hits[ohl++] = S->orig[h];
+        }
+      R->tl_hit_off[ot + 1] = ohl;
+      ++ot;
+    }
+    /* tracks in (smallest original hit index) order */
+    int32_t* ki = malloc((S->ntr > 0 ? S->ntr : 1) * sizeof(int32_t));
+    for (int64_t k = 0; k < S->ntr; ++k) ki[k] = (int32_t)k;
+    sort_idx_by_key(ki, S->ntr, S->tr_min);
+    for (int64_t j = 0; j < S->ntr; ++j) {
+      int64_t k = ki[j], t = S->tr_t[k];
+      const uint64_t key = tracklet_key(S, t);
+      R->tr_sector[otr] = s; R->tr_ndf[otr] = S->t_ndf[t]; R->tr_nhits[otr] = S->tr_nk[k];
+      R->tr_tracklet[otr] = tpos[t];
+      R->tr_xref[otr] = S->t_x[t]; R->tr_chi2[otr] = S->t_chi2[t];
+      for (int i = 0; i < 5; ++i) R->tr_param[otr * 5 + i] = S->t_p[t * 5 + i];
+      for (int i = 0; i < 15; ++i) R->tr_cov[otr * 15 + i] = S->t_c[t * 15 + i];
+      for (int r = 0; r < NROW; ++r) {
+        int32_t h = S->t_slots[t * NROW + r];
+        if (h >= 0 && S->weight[h] == key) R->tr_hits[ohr++] = S->orig[h];
+      }
+      R->tr_hit_off[otr + 1] = ohr;
+      ++otr;
+    }
+    free(ti); free(tpos); free(ki);
+    free_sector(S);
+  }
+  free(secs);
+  *out = R;
+  return 0;
+}

@@ -1,0 +1,414 @@
+/*
+ * tpcsynth.c — seeded synthetic TPC time frames (input generator).
+ *
+ * This module produces inputs only. It holds none of the tracker's arithmetic and is shared by the
+ * CPU oracle tests and the CUDA path alike. It models the workloads of the paper's synchronous
+ * reconstruction (Sec. 2: continuous readout, clusters in native row/time coordinates; Sec. 7.1:
+ * time frames of many overlapping collisions) with the detector layout of the Pb-Pb/pp configurations
+ * used throughout this project: 36 sectors of 20 degrees (18 in phi x 2 drift sides), 152 pad rows
+ * at radii 85-245 cm, 250 cm drift length, solenoid field Bz along +z.
+ *
+ * Physics model (all in double precision):
+ *   - primaries from the origin; pT log-uniform, |eta| uniform below eta_max, phi uniform, q = +-1;
+ *   - exact helix in the solenoid field: d(phi)/ds = k = -0.0029979246 * Bz * q / pT  [1/cm];
+ *   - one cluster per crossed pad row on the first outgoing leg (loopers are not followed);
+ *   - continuous readout: the cluster's drift coordinate is w = v_d * t_coll + (250 - |z|) with
+ *     v_d = 250 cm / 90 us; clusters arriving after the frame end are lost (Sec. 2);
+ *   - multiple scattering: Highland kick at every row with x/X0 = x0_total/152 per row (scaled by
+ *     the path length through the row), log term at the nominal per-row thickness;
+ *   - Gaussian smearing (sigma_y, sigma_w), row-crossing inefficiency, and uniform noise clusters.
+ *
+ * Random numbers: counter-based SplitMix64 streams keyed by (seed, frame, kind, id), so results do
+ * not depend on thread count or scheduling.
+ */
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define SY_NSEC_PHI 18
+#define SY_NSEC 36
+#define SY_NROW 152
+#define SY_PI 3.14159265358979323846
+#define SY_VDRIFT (250.0 / 90.0) /* cm per microsecond */
+#define SY_ZMAX 250.0
+#define SY_PION_MASS 0.13957039
+#define SY_CHUNK 512
+
+typedef struct {
+  uint64_t seed;
+  uint64_t frame_id;
+  int32_t n_collisions;  /* >= 0: fixed count; < 0: Poisson(poisson_mean) */
+  double poisson_mean;
+  int32_t mult_fixed;    /* > 0: fixed multiplicity per collision */
+  double mult_mean;      /* otherwise exponential with this mean ... */
+  int32_t mult_cap;      /* ... capped here */
+  double pt_min, pt_max, eta_max;
+  double bz;             /* tesla */
+  double sigma_y, sigma_w;
+  double dropout;        /* probability to lose a row crossing */
+  double noise_frac;     /* noise clusters per signal cluster in each (sector,row) */
+  double x0_total;       /* total X/X0 over the 152 rows; 0 disables scattering */
+  double frame_us;       /* collision window: collision times uniform in [0, frame_us) */
+  double tail_us;        /* readout continues this long after the window; later clusters are lost */
+  int32_t t_zero;        /* 1: every collision at t = 0 */
+  int32_t shuffle;       /* 1: emit clusters in a seeded random order */
+  int32_t want_truth;    /* 1: fill per-cluster truth */
+  int32_t n_threads;     /* 0: OpenMP default */
+} synth_params;
+
+typedef struct {
+  int64_t n_clusters, n_tracks, n_collisions;
+  uint8_t* sector;
+  uint8_t* row;
+  float* y;
+  float* w;
+  int32_t* truth_track;   /* -1 for noise; may be NULL */
+  double* truth_state;    /* [n][5]: y, w, sin(phi_local), dw/ds, q/pT at the crossing; may be NULL */
+  /* per track */
+  int32_t* trk_coll;
+  int8_t* trk_q;
+  double* trk_pt;
+  double* trk_eta;
+  double* trk_phi0;
+  double* trk_tc;          /* collision time, us */
+  int32_t* trk_ncl;
+  double* coll_tc;
+} synth_frame;
+
+/* ---------------------------------------------------------------- RNG (SplitMix64) */
+static inline uint64_t sy_mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+typedef struct { uint64_t s; } sy_rng;
+enum { SY_K_EVENT = 1, SY_K_TRACK = 2, SY_K_NOISE = 3, SY_K_SHUFFLE = 4 };
+static sy_rng sy_stream(const synth_params* p, uint64_t kind, uint64_t id) {
+  sy_rng r;
+  r.s = sy_mix(p->seed * 0x9E3779B97F4A7C15ULL + 0x632BE59BD9B4E019ULL) ^
+        sy_mix(p->frame_id + 0xD1B54A32D192ED03ULL) ^ sy_mix((kind << 58) ^ (id + 1));
+  return r;
+}
+static inline uint64_t sy_next(sy_rng* r) {
+  r->s += 0x9E3779B97F4A7C15ULL;
+  return sy_mix(r->s);
+}
+static inline double sy_u01(sy_rng* r) { return (double)(sy_next(r) >> 11) * 0x1.0p-53; }
+static inline double sy_gauss(sy_rng* r) {
+  double u1 = 1.0 - sy_u01(r); /* (0,1] */
+  double u2 = sy_u01(r);
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * SY_PI * u2);
+}
+static int sy_poisson(sy_rng* r, double lam) {
+  double L = exp(-lam), prod = sy_u01(r);
+  int n = 0;
+  while (prod > L) { ++n; prod *= sy_u01(r); }
+  return n;
+}
+
+/* ---------------------------------------------------------------- geometry */
+static inline double sy_row_x(int r) { return 85.0 + (double)r * (160.0 / 151.0); }
+static inline double sy_alpha(int k) { return ((double)k + 0.5) * (SY_PI / 9.0); }
+static inline double sy_wrap(double a) { /* into (-pi, pi] */
+  a = fmod(a, 2.0 * SY_PI);
+  if (a > SY_PI) a -= 2.0 * SY_PI;
+  if (a <= -SY_PI) a += 2.0 * SY_PI;
+  return a;
+}
+
+typedef struct {
+  uint8_t sector, row;
+  float y, w;
+  int32_t track;
+  double truth[5];
+} sy_rec;
+
+typedef struct {
+  double phi0, eta, pt, tc;
+  int q, coll;
+} sy_track;
+
+/* Propagate one primary and emit its clusters into out[] (<= SY_NROW records). */
+static int sy_track_clusters(const synth_params* p, const sy_track* t, int64_t tid, sy_rec* out) {
+  sy_rng rng = sy_stream(p, SY_K_TRACK, (uint64_t)tid);
+  const double kappa = 0.0029979246 * p->bz;
+  const double tan10 = tan(10.0 * SY_PI / 180.0);
+  const double w_end = SY_VDRIFT * (p->frame_us + p->tail_us);
+  const double xx0_row = p->x0_total / (double)SY_NROW;
+  const double hl_log = xx0_row > 0 ? (1.0 + 0.038 * log(xx0_row)) : 1.0;
+  double px = 0, py = 0, pz = 0, phi = t->phi0, tgl = sinh(t->eta), pt = t->pt;
+  const double ptot = pt * sqrt(1.0 + tgl * tgl);
+  const int q = t->q;
+  const int side = t->eta >= 0 ? 0 : 1;
+  double s_total = 0;
+  int sec = -1, n = 0;
+  for (int r = 0; r < SY_NROW; ++r) {
+    const double X = sy_row_x(r);
+    const double k = -kappa * (double)q / pt;
+    double best_s = INFINITY;
+    int best_k = -1;
+    double bx = 0, by = 0, bphi = 0;
+    int ncand = sec < 0 ? SY_NSEC_PHI : 3;
+    for (int c = 0; c < ncand; ++c) {
+      int kk = sec < 0 ? c : (sec + c - 1 + SY_NSEC_PHI) % SY_NSEC_PHI;
+      double al = sy_alpha(kk), ux = cos(al), uy = sin(al);
+      double d = X - (px * ux + py * uy);
+      double psi = sy_wrap(phi - al);
+      double s;
+      if (fabs(k) < 1e-12) {
+        double cp = cos(psi);
+        if (cp <= 1e-12) continue;
+        s = d / cp;
+      } else {
+        double sig = sin(psi) + k * d;
+        if (fabs(sig) >= 1.0) continue;
+        double ang = asin(sig) - psi; /* k*s must equal ang modulo 2 pi */
+        if (k > 0) {
+          while (ang <= 1e-13) ang += 2.0 * SY_PI;
+          while (ang > 2.0 * SY_PI + 1e-13) ang -= 2.0 * SY_PI;
+        } else {
+          while (ang >= -1e-13) ang -= 2.0 * SY_PI;
+          while (ang < -2.0 * SY_PI - 1e-13) ang += 2.0 * SY_PI;
+        }
+        s = ang / k;
+        if ((s_total + s) * fabs(k) >= SY_PI) continue; /* beyond the first outgoing leg */
+      }
+      if (!(s > 1e-9) || s >= best_s) continue;
+      double nx, ny, nphi;
+      if (fabs(k) < 1e-12) {
+        nx = px + s * cos(phi);
+        ny = py + s * sin(phi);
+        nphi = phi;
+      } else {
+        nphi = phi + k * s;
+        nx = px + (sin(nphi) - sin(phi)) / k;
+        ny = py - (cos(nphi) - cos(phi)) / k;
+      }
+      double yl = -nx * uy + ny * ux;
+      if (fabs(yl) > X * tan10) continue;
+      best_s = s; best_k = kk; bx = nx; by = ny; bphi = nphi;
+    }
+    if (best_k < 0) break;
+    px = bx; py = by; phi = bphi;
+    pz += tgl * best_s;
+    s_total += best_s;
+    sec = best_k;
+    if (fabs(pz) > SY_ZMAX) break;
+    if ((side == 0 && pz < 0) || (side == 1 && pz > 0)) break; /* crossed the central membrane */
+    const double al = sy_alpha(sec), ux = cos(al), uy = sin(al);
+    const double yl = -px * uy + py * ux;
+    const double w_true = SY_VDRIFT * t->tc + (SY_ZMAX - fabs(pz));
+    const double psi_loc = phi - al;
+    const double tw = -fabs(tgl);
+    const int lost = sy_u01(&rng) < p->dropout;
+    const double gy = sy_gauss(&rng), gw = sy_gauss(&rng);
+    if (!lost && w_true <= w_end) {
+      sy_rec* o = &out[n++];
+      o->sector = (uint8_t)(sec + SY_NSEC_PHI * side);
+      o->row = (uint8_t)r;
+      o->y = (float)(yl + p->sigma_y * gy);
+      o->w = (float)(w_true + p->sigma_w * gw);
+      o->track = (int32_t)tid;
+      o->truth[0] = yl;
+      o->truth[1] = w_true;
+      o->truth[2] = sin(psi_loc);
+      o->truth[3] = tw;
+      o->truth[4] = (double)q / pt;
+    }
+    if (xx0_row > 0) {
+      double lam = atan(tgl);
+      double cosloc = cos(psi_loc) * cos(lam);
+      if (cosloc < 0.05) cosloc = 0.05;
+      double xx0 = xx0_row / cosloc;
+      double beta = ptot / sqrt(ptot * ptot + SY_PION_MASS * SY_PION_MASS);
+      double th0 = 0.0136 / (beta * ptot) * sqrt(xx0) * hl_log;
+      double t1 = th0 * sy_gauss(&rng), t2 = th0 * sy_gauss(&rng);
+      phi += t1 / cos(lam);
+      lam += t2;
+      if (fabs(lam) > 1.4) break;
+      tgl = tan(lam);
+      pt = ptot * cos(lam);
+    }
+  }
+  return n;
+}
+
+static void sy_free_frame(synth_frame* f) {
+  if (!f) return;
+  free(f->sector); free(f->row); free(f->y); free(f->w); free(f->truth_track); free(f->truth_state);
+  free(f->trk_coll); free(f->trk_q); free(f->trk_pt); free(f->trk_eta); free(f->trk_phi0);
+  free(f->trk_tc); free(f->trk_ncl); free(f->coll_tc);
+  free(f);
+}
+
+void synth_free(synth_frame* f) { sy_free_frame(f); }
+
+/* Returns 0 and a frame in *out, or a negative value on allocation failure / bad parameters. */
+int synth_generate(const synth_params* p, synth_frame** out) {
+  *out = NULL;
+  if (!p || p->pt_min <= 0 || p->pt_max < p->pt_min || p->frame_us < 0) return -1;
+  synth_frame* f = (synth_frame*)calloc(1, sizeof(synth_frame));
+  if (!f) return -2;
+  /* collisions */
+  sy_rng ev = sy_stream(p, SY_K_EVENT, 0);
+  int ncoll = p->n_collisions >= 0 ? p->n_collisions : sy_poisson(&ev, p->poisson_mean);
+  f->n_collisions = ncoll;
+  f->coll_tc = (double*)malloc(sizeof(double) * (ncoll > 0 ? ncoll : 1));
+  int* mult = (int*)malloc(sizeof(int) * (ncoll > 0 ? ncoll : 1));
+  int64_t ntrk = 0;
+  for (int c = 0; c < ncoll; ++c) {
+    f->coll_tc[c] = p->t_zero ? 0.0 : sy_u01(&ev) * p->frame_us;
+    int m;
+    if (p->mult_fixed > 0) m = p->mult_fixed;
+    else {
+      double x = -p->mult_mean * log(1.0 - sy_u01(&ev));
+      m = (int)ceil(x);
+      if (m < 1) m = 1;
+      if (m > p->mult_cap) m = p->mult_cap;
+    }
+    mult[c] = m;
+    ntrk += m;
+  }
+  f->n_tracks = ntrk;
+  sy_track* trk = (sy_track*)malloc(sizeof(sy_track) * (ntrk > 0 ? ntrk : 1));
+  f->trk_coll = (int32_t*)malloc(sizeof(int32_t) * (ntrk > 0 ? ntrk : 1));
+  f->trk_q = (int8_t*)malloc(ntrk > 0 ? ntrk : 1);
+  f->trk_pt = (double*)malloc(sizeof(double) * (ntrk > 0 ? ntrk : 1));
+  f->trk_eta = (double*)malloc(sizeof(double) * (ntrk > 0 ? ntrk : 1));
+  f->trk_phi0 = (double*)malloc(sizeof(double) * (ntrk > 0 ? ntrk : 1));
+  f->trk_tc = (double*)malloc(sizeof(double) * (ntrk > 0 ? ntrk : 1));
+  f->trk_ncl = (int32_t*)calloc(ntrk > 0 ? ntrk : 1, sizeof(int32_t));
+  {
+    int64_t t = 0;
+    const double lr = log(p->pt_max / p->pt_min);
+    for (int c = 0; c < ncoll; ++c)
+      for (int i = 0; i < mult[c]; ++i, ++t) {
+        sy_rng tr = sy_stream(p, SY_K_TRACK + 16, (uint64_t)t);
+        trk[t].phi0 = 2.0 * SY_PI * sy_u01(&tr);
+        trk[t].eta = p->eta_max * (2.0 * sy_u01(&tr) - 1.0);
+        trk[t].pt = p->pt_min * exp(lr * sy_u01(&tr));
+        trk[t].q = sy_u01(&tr) < 0.5 ? -1 : 1;
+        trk[t].tc = f->coll_tc[c];
+        trk[t].coll = c;
+        f->trk_coll[t] = c; f->trk_q[t] = (int8_t)trk[t].q; f->trk_pt[t] = trk[t].pt;
+        f->trk_eta[t] = trk[t].eta; f->trk_phi0[t] = trk[t].phi0; f->trk_tc[t] = trk[t].tc;
+      }
+  }
+  free(mult);
+  /* signal clusters, in chunks of tracks (deterministic order) */
+  int64_t nchunk = (ntrk + SY_CHUNK - 1) / SY_CHUNK;
+  sy_rec** cbuf = (sy_rec**)calloc(nchunk > 0 ? nchunk : 1, sizeof(sy_rec*));
+  int64_t* ccnt = (int64_t*)calloc(nchunk + 1, sizeof(int64_t));
+  int fail = 0;
+  if (p->n_threads > 0) {
+#ifdef _OPENMP
+    omp_set_num_threads(p->n_threads);
+#endif
+  }
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t c = 0; c < nchunk; ++c) {
+    int64_t t0 = c * SY_CHUNK, t1 = t0 + SY_CHUNK < ntrk ? t0 + SY_CHUNK : ntrk;
+    sy_rec* b = (sy_rec*)malloc(sizeof(sy_rec) * (size_t)(t1 - t0) * SY_NROW);
+    if (!b) { fail = 1; continue; }
+    int64_t n = 0;
+    for (int64_t t = t0; t < t1; ++t) {
+      int k = sy_track_clusters(p, &trk[t], t, b + n);
+      f->trk_ncl[t] = k;
+      n += k;
+    }
+    cbuf[c] = b;
+    ccnt[c] = n;
+  }
+  free(trk);
+  if (fail) { for (int64_t c = 0; c < nchunk; ++c) free(cbuf[c]); free(cbuf); free(ccnt); sy_free_frame(f); return -2; }
+  int64_t nsig = 0;
+  for (int64_t c = 0; c < nchunk; ++c) nsig += ccnt[c];
+  /* per (sector,row) signal counts and the occupied w range for noise */
+  int64_t cnt[SY_NSEC * SY_NROW];
+  memset(cnt, 0, sizeof(cnt));
+  double wlo = INFINITY, whi = -INFINITY;
+  for (int64_t c = 0; c < nchunk; ++c)
+    for (int64_t i = 0; i < ccnt[c]; ++i) {
+      const sy_rec* r = &cbuf[c][i];
+      cnt[r->sector * SY_NROW + r->row]++;
+      if (r->w < wlo) wlo = r->w;
+      if (r->w > whi) whi = r->w;
+    }
+  if (!(wlo <= whi)) { wlo = 0; whi = SY_ZMAX; }
+  int64_t nnoise_sr[SY_NSEC * SY_NROW];
+  int64_t nnoise = 0;
+  for (int sr = 0; sr < SY_NSEC * SY_NROW; ++sr) {
+    sy_rng nr = sy_stream(p, SY_K_NOISE, (uint64_t)sr);
+    double x = p->noise_frac * (double)cnt[sr];
+    int64_t k = (int64_t)floor(x);
+    if (sy_u01(&nr) < x - (double)k) ++k;
+    nnoise_sr[sr] = k;
+    nnoise += k;
+  }
+  int64_t n = nsig + nnoise;
+  f->n_clusters = n;
+  size_t na = (size_t)(n > 0 ? n : 1);
+  f->sector = (uint8_t*)malloc(na);
+  f->row = (uint8_t*)malloc(na);
+  f->y = (float*)malloc(na * sizeof(float));
+  f->w = (float*)malloc(na * sizeof(float));
+  f->truth_track = (int32_t*)malloc(na * sizeof(int32_t));
+  if (p->want_truth) f->truth_state = (double*)malloc(na * 5 * sizeof(double));
+  if (!f->sector || !f->row || !f->y || !f->w || !f->truth_track || (p->want_truth && !f->truth_state)) {
+    for (int64_t c = 0; c < nchunk; ++c) free(cbuf[c]);
+    free(cbuf); free(ccnt); sy_free_frame(f); return -2;
+  }
+  {
+    int64_t o = 0;
+    for (int64_t c = 0; c < nchunk; ++c) {
+      for (int64_t i = 0; i < ccnt[c]; ++i, ++o) {
+        const sy_rec* r = &cbuf[c][i];
+        f->sector[o] = r->sector; f->row[o] = r->row; f->y[o] = r->y; f->w[o] = r->w;
+        f->truth_track[o] = r->track;
+        if (p->want_truth) memcpy(&f->truth_state[5 * o], r->truth, 5 * sizeof(double));
+      }
+      free(cbuf[c]);
+    }
+    free(cbuf); free(ccnt);
+    for (int sr = 0; sr < SY_NSEC * SY_NROW; ++sr) {
+      sy_rng nr = sy_stream(p, SY_K_NOISE, (uint64_t)sr);
+      (void)sy_u01(&nr); /* the draw used for the count above */
+      const int s = sr / SY_NROW, r = sr % SY_NROW;
+      const double ymax = sy_row_x(r) * tan(10.0 * SY_PI / 180.0);
+      for (int64_t j = 0; j < nnoise_sr[sr]; ++j, ++o) {
+        double yy = ymax * (2.0 * sy_u01(&nr) - 1.0);
+        double ww = wlo + (whi - wlo) * sy_u01(&nr);
+        f->sector[o] = (uint8_t)s; f->row[o] = (uint8_t)r;
+        f->y[o] = (float)yy; f->w[o] = (float)ww;
+        f->truth_track[o] = -1;
+        if (p->want_truth) {
+          double* tt = &f->truth_state[5 * o];
+          tt[0] = yy; tt[1] = ww; tt[2] = tt[3] = tt[4] = NAN;
+        }
+      }
+    }
+  }
+  if (p->shuffle && n > 1) {
+    sy_rng sh = sy_stream(p, SY_K_SHUFFLE, 0);
+    for (int64_t i = n - 1; i > 0; --i) {
+      int64_t j = (int64_t)(sy_next(&sh) % (uint64_t)(i + 1));
+      uint8_t t8 = f->sector[i]; f->sector[i] = f->sector[j]; f->sector[j] = t8;
+      t8 = f->row[i]; f->row[i] = f->row[j]; f->row[j] = t8;
+      float tf = f->y[i]; f->y[i] = f->y[j]; f->y[j] = tf;
+      tf = f->w[i]; f->w[i] = f->w[j]; f->w[j] = tf;
+      int32_t ti = f->truth_track[i]; f->truth_track[i] = f->truth_track[j]; f->truth_track[j] = ti;
+      if (p->want_truth) {
+        double tmp[5];
+        memcpy(tmp, &f->truth_state[5 * i], sizeof(tmp));
+        memcpy(&f->truth_state[5 * i], &f->truth_state[5 * j], sizeof(tmp));
+        memcpy(&f->truth_state[5 * j], tmp, sizeof(tmp));
+      }
+    }
+  }
+  *out = f;
+  return 0;
+}

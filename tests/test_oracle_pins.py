@@ -1,0 +1,386 @@
+"""Pins of the CPU oracle against facts fixed by mathematics, by closed forms and by construction.
+
+None of these compares the oracle with itself: each checks it against a textbook formula, a library
+routine for a special case, an exact geometric construction from the generator, brute force, or an
+invariant of the method.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import efficiency, oracle_track_list, segments
+
+KQ = -0.0029979246 * 0.5   # d(curvature)/d(q/pT) at Bz = 0.5 T, 1/cm per (c/GeV)
+
+
+# ------------------------------------------------------------------ building blocks
+
+@pytest.mark.parametrize("prec,tol", [("f64", 5e-14), ("f32", 4e-7)])
+def test_asin_matches_libm(prec, tol):
+    for t in np.concatenate([np.linspace(-0.999, 0.999, 401), [0.0999999, 0.1, 0.1000001, 1e-8]]):
+        assert abs(oracle.asin(t, precision=prec) - math.asin(t)) <= tol * max(1.0, abs(math.asin(t)))
+
+
+def test_row_geometry():
+    assert oracle.row_x(0) == 85.0
+    assert abs(oracle.row_x(151) - 245.0) < 1e-12
+    d = np.diff([oracle.row_x(r) for r in range(152)])
+    assert np.allclose(d, 160.0 / 151.0, rtol=0, atol=1e-12)
+
+
+def _helix_closed_form(P, x0, x1, kq):
+    """Exact circle geometry: direction angle phi = asin(s), centre on the left for k > 0."""
+    y0, w0, s0, tw, qpt = P
+    k = kq * qpt
+    s1 = s0 + k * (x1 - x0)
+    if abs(k) < 1e-15:
+        c0 = math.sqrt(1 - s0 * s0)
+        dy = (x1 - x0) * s0 / c0
+        arc = (x1 - x0) / c0
+    else:
+        dy = (math.sqrt(1 - s0 * s0) - math.sqrt(1 - s1 * s1)) / k
+        arc = (math.asin(s1) - math.asin(s0)) / k
+    return np.array([y0 + dy, w0 + tw * arc, s1, tw, qpt])
+
+
+@pytest.mark.parametrize("bz", [0.0, 0.5])
+def test_propagation_matches_circle(bz):
+    rng = np.random.default_rng(1)
+    p = oracle.default_params("f64", bz=bz, x0_per_row=0.0)
+    kq = -0.0029979246 * bz
+    for _ in range(300):
+        P = np.array([rng.uniform(-40, 40), rng.uniform(0, 500), rng.uniform(-0.8, 0.8),
+                      rng.uniform(-1.1, 1.1), rng.choice([-1, 1]) / rng.uniform(0.15, 10)])
+        x0 = rng.uniform(85, 245)
+        x1 = x0 + rng.choice([-1, 1]) * rng.uniform(0.5, 12)
+        rc, P1, _, _ = oracle.propagate(P, np.eye(5), x0, x1, params=p)
+        ref = _helix_closed_form(P, x0, x1, kq)
+        if abs(ref[2]) >= 0.999:
+            assert rc != 0
+            continue
+        assert rc == 0
+        assert np.allclose(P1, ref, rtol=1e-11, atol=1e-11), (P, x0, x1, P1 - ref)
+
+
+def test_propagation_jacobian_matches_finite_differences():
+    rng = np.random.default_rng(2)
+    p = oracle.default_params("f64", x0_per_row=0.0)
+    for _ in range(60):
+        P = np.array([rng.uniform(-30, 30), rng.uniform(0, 400), rng.uniform(-0.7, 0.7),
+                      rng.uniform(-1, 1), rng.choice([-1, 1]) / rng.uniform(0.15, 5)])
+        x0 = rng.uniform(85, 240)
+        dx = rng.choice([-1, 1]) * rng.uniform(0.9, 8)
+        rc, _, _, J = oracle.propagate(P, np.eye(5), x0, x0 + dx, params=p)
+        assert rc == 0
+        Jn = np.zeros((5, 5))
+        for j in range(5):
+            h = 1e-6 * max(1.0, abs(P[j]))
+            Pp, Pm = P.copy(), P.copy()
+            Pp[j] += h
+            Pm[j] -= h
+            _, a, _, _ = oracle.propagate(Pp, np.eye(5), x0, x0 + dx, params=p)
+            _, b, _, _ = oracle.propagate(Pm, np.eye(5), x0, x0 + dx, params=p)
+            Jn[:, j] = (a - b) / (2 * h)
+        assert np.allclose(J, Jn, rtol=2e-6, atol=2e-7), (J - Jn)
+
+
+def test_propagation_round_trip_and_covariance_transport():
+    rng = np.random.default_rng(3)
+    p = oracle.default_params("f64", x0_per_row=0.0)
+    for _ in range(50):
+        P = np.array([rng.uniform(-30, 30), rng.uniform(0, 400), rng.uniform(-0.6, 0.6),
+                      rng.uniform(-1, 1), rng.choice([-1, 1]) / rng.uniform(0.2, 5)])
+        A = rng.normal(size=(5, 5))
+        C = A @ A.T + 0.1 * np.eye(5)
+        x0, x1 = 100.0, 100.0 + rng.uniform(1, 20)
+        rc, P1, C1, J = oracle.propagate(P, C, x0, x1, params=p)
+        assert rc == 0
+        assert np.allclose(C1, J @ C @ J.T, rtol=1e-12, atol=1e-12)
+        assert np.allclose(C1, C1.T, rtol=0, atol=0)
+        rc, P2, C2, J2 = oracle.propagate(P1, C1, x1, x0, params=p)
+        assert rc == 0
+        assert np.allclose(P2, P, rtol=1e-11, atol=1e-11)
+        assert np.allclose(J2 @ J, np.eye(5), atol=1e-10)
+        assert np.allclose(C2, C, rtol=1e-9, atol=1e-9)
+
+
+def test_multiple_scattering_matches_highland():
+    """Process noise on (sin phi, t) for a 1 GeV/c pion, one row: PDG Highland formula."""
+    x0r = 0.03 / 152
+    p = oracle.default_params("f64", x0_per_row=x0r)
+    pt, tw, s = 0.8, 0.75, 0.2
+    P = np.array([0.0, 100.0, s, tw, 1.0 / pt])
+    C = np.zeros((5, 5))
+    # a straight step (bz = 0) leaves sin(phi) unchanged, so the noise is evaluated at s
+    p.bz = 0.0
+    rc, _, C1, _ = oracle.propagate(P, C, 100.0, 100.0 + 160.0 / 151.0, params=p)
+    assert rc == 0
+    ptot = pt * math.sqrt(1 + tw * tw)
+    beta = ptot / math.sqrt(ptot ** 2 + 0.13957039 ** 2)
+    cos_lam, cos_phi = 1 / math.sqrt(1 + tw * tw), math.sqrt(1 - s * s)
+    xx0 = x0r / (cos_lam * cos_phi)
+    th0 = 0.0136 / (beta * ptot) * math.sqrt(xx0) * (1 + 0.038 * math.log(x0r))
+    # d(phi) = theta_plane / cos(lambda), d(lambda) = theta_plane
+    var_sin = (cos_phi ** 2) * th0 ** 2 / cos_lam ** 2
+    var_t = th0 ** 2 / cos_lam ** 4
+    assert math.isclose(C1[2, 2], var_sin, rel_tol=1e-12)
+    assert math.isclose(C1[3, 3], var_t, rel_tol=1e-12)
+
+
+def test_update_equals_textbook_standard_form():
+    rng = np.random.default_rng(4)
+    p = oracle.default_params("f64")
+    H = np.zeros((2, 5)); H[0, 0] = H[1, 1] = 1
+    R = np.diag([p.sigma_y ** 2, p.sigma_w ** 2])
+    for _ in range(100):
+        A = rng.normal(size=(5, 5))
+        C = A @ A.T * rng.uniform(0.01, 1) + 0.05 * np.eye(5)
+        P = rng.normal(size=5)
+        m = P[:2] + rng.normal(scale=0.3, size=2)
+        chi2, P1, C1 = oracle.update(P, C, m[0], m[1], params=p)
+        S = H @ C @ H.T + R
+        K = C @ H.T @ np.linalg.inv(S)
+        r = m - H @ P
+        assert math.isclose(chi2, float(r @ np.linalg.solve(S, r)), rel_tol=1e-10)
+        assert np.allclose(P1, P + K @ r, rtol=1e-11, atol=1e-12)
+        C_std = C - K @ H @ C          # standard form; the oracle uses Joseph's form
+        assert np.allclose(C1, C_std, rtol=1e-9, atol=1e-12)
+        assert np.allclose(C1, C1.T, rtol=0, atol=0)
+        assert np.all(np.linalg.eigvalsh(C1) > 0)
+
+
+def test_update_scalar_weighted_mean():
+    p = oracle.default_params("f64")
+    C = np.diag([0.04, 0.09, 1, 1, 1])
+    chi2, P1, C1 = oracle.update([1.0, 2.0, 0, 0, 0], C, 1.3, 1.5, params=p)
+    r = 0.01
+    assert math.isclose(P1[0], (1.0 / 0.04 + 1.3 / r) / (1 / 0.04 + 1 / r), rel_tol=1e-13)
+    assert math.isclose(P1[1], (2.0 / 0.09 + 1.5 / r) / (1 / 0.09 + 1 / r), rel_tol=1e-13)
+    assert math.isclose(C1[0, 0], 1 / (1 / 0.04 + 1 / r), rel_tol=1e-13)
+    assert math.isclose(chi2, 0.3 ** 2 / 0.05 + 0.5 ** 2 / 0.1, rel_tol=1e-13)
+
+
+@pytest.mark.parametrize("bz", [0.0, 0.5])
+def test_seed_on_exact_circle(bz):
+    rng = np.random.default_rng(5)
+    p = oracle.default_params("f64", bz=bz)
+    kq = -0.0029979246 * bz
+    for _ in range(200):
+        qpt = rng.choice([-1, 1]) / rng.uniform(0.25, 10) if bz else 0.0
+        k = kq * qpt
+        s0, tw = rng.uniform(-0.5, 0.5), rng.uniform(-1, 1)
+        y0, w0 = rng.uniform(-20, 20), rng.uniform(0, 300)
+        x = np.sort(rng.uniform(85, 245, size=3))
+        pts = []
+        for xi in x:
+            st = _helix_closed_form([y0, w0, s0, tw, qpt], x[0], xi, kq)
+            if abs(st[2]) >= 0.999:
+                break
+            pts.append([xi, st[0], st[1]])
+        if len(pts) < 3:
+            continue
+        rc, P = oracle.seed(np.array(pts), params=p)
+        assert rc == 0
+        want = np.array([y0, w0, s0, tw, qpt])
+        assert np.allclose(P, want, rtol=1e-9, atol=1e-9), (P - want, k)
+
+
+# ------------------------------------------------------------------ neighbour finding (T3)
+
+def _tiny_rows(rng, n_per_row, rows=(10, 11, 12, 13), wspan=20.0):
+    sec, row, y, w = [], [], [], []
+    for r in rows:
+        y += list(rng.uniform(-5, 5, n_per_row))
+        w += list(rng.uniform(100, 100 + wspan, n_per_row))
+        sec += [3] * n_per_row
+        row += [r] * n_per_row
+    return (np.array(sec, np.uint8), np.array(row, np.uint8), np.array(y), np.array(w))
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("seed", range(6))
+def test_grid_neighbours_equal_brute_force(prec, seed):
+    rng = np.random.default_rng(100 + seed)
+    s, r, y, w = _tiny_rows(rng, n_per_row=20 + 30 * seed, wspan=5.0 + 10 * seed)
+    a = oracle.track(s, r, y, w, precision=prec)
+    b = oracle.track(s, r, y, w, precision=prec, brute_force=True)
+    assert np.array_equal(a.up, b.up) and np.array_equal(a.down, b.down)
+    assert (a.up >= 0).sum() > 0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_grid_neighbours_bin_edges(prec):
+    """Candidates placed exactly on, just inside and just outside the window edges."""
+    p = oracle.default_params(prec)
+    dt = np.float32 if prec == "f32" else np.float64
+    x = np.array([oracle.row_x(r, precision=prec) for r in range(4)], dtype=dt)
+    ww = dt(p.kw) * (x[2] - x[1]) + dt(p.eps)
+    wy = dt(p.ky) * (x[2] - x[1]) + dt(p.eps)
+    sec, row, y, w = [], [], [], []
+    base_w = dt(50.0)
+    for j, (dyy, dww) in enumerate([(0, 1), (0, -1), (1, 0), (-1, 0), (1, 1), (0, 0.5)]):
+        yi, wi = dt(10.0 * j), base_w
+        for rr, yy, wv in [(1, yi, wi)]:
+            sec.append(0); row.append(rr); y.append(yy); w.append(wv)
+        for rr in (0, 2):
+            for eps in (-1, 0, 1):
+                wv = wi + dt(dww) * ww
+                yy = yi + dt(dyy) * wy
+                if eps:
+                    wv = np.nextafter(wv, dt(np.inf) if eps > 0 else dt(-np.inf)) if dww else wv
+                    yy = np.nextafter(yy, dt(np.inf) if eps > 0 else dt(-np.inf)) if dyy else yy
+                sec.append(0); row.append(rr); y.append(float(yy)); w.append(float(wv))
+    s, r = np.array(sec, np.uint8), np.array(row, np.uint8)
+    a = oracle.track(s, r, np.array(y), np.array(w), precision=prec)
+    b = oracle.track(s, r, np.array(y), np.array(w), precision=prec, brute_force=True)
+    assert np.array_equal(a.up, b.up) and np.array_equal(a.down, b.down)
+
+
+def test_links_invariants():
+    f = synth.generate("pp_500")
+    res = oracle.track(f.sector, f.row, f.y, f.w, precision="f32")
+    n = f.n
+    for arr, step in ((res.up, 1), (res.down, -1), (res.up_c, 1), (res.down_c, -1)):
+        ok = arr >= 0
+        assert np.all(f.row[arr[ok]] == f.row[ok].astype(int) + step)
+        assert np.all(f.sector[arr[ok]] == f.sector[ok])
+    assert np.all((res.up[(f.row == 0) | (f.row == 151)] == -1))
+    # cleaned links are exactly the reciprocal ones
+    i = np.arange(n)
+    ok = res.up >= 0
+    recip = np.zeros(n, bool)
+    recip[ok] = res.down[res.up[ok]] == i[ok]
+    assert np.array_equal(res.up_c >= 0, recip)
+    okc = res.up_c >= 0
+    assert np.all(res.down_c[res.up_c[okc]] == i[okc])
+    # start hits: up link, no down link, chain of >= 3
+    for s in res.start:
+        assert res.up_c[s] >= 0 and res.down_c[s] < 0 and res.up_c[res.up_c[s]] >= 0
+
+
+# ------------------------------------------------------------------ whole-tracker pins (T1, T2, T4)
+
+def _noise_free(bz, seed):
+    return synth.generate("pp_500", truth=True, bz=bz, sigma_y=0.0, sigma_w=0.0, dropout=0.0,
+                          noise_frac=0.0, x0_total=0.0, seed=seed)
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_T1_zero_field_straight_tracks_exact(seed):
+    f = _noise_free(0.0, seed)
+    p = oracle.default_params("f64", bz=0.0, x0_per_row=0.0)
+    ts = f.truth_state
+    res = oracle.track(f.sector, f.row, ts[:, 0], ts[:, 1], precision="f64", params=p)
+    key, segs = segments(f)
+    want = {k for k, c in segs.items() if c >= p.nmin}
+    got = {}
+    for i in range(res.n_tracks):
+        h = res.track_hits(i)
+        ks = np.unique(key[h])
+        assert len(ks) == 1 and segs[int(ks[0])] == len(h), "cluster set not exact"
+        got[int(ks[0])] = i
+        assert np.all(np.diff(f.row[h].astype(int)) > 0)
+        ref = h[np.argmin(f.row[h])]
+        assert math.isclose(res.tr_xref[i], oracle.row_x(int(f.row[ref])), rel_tol=1e-15)
+        d = np.abs(res.tr_param[i, :4] - ts[ref, :4]) / np.maximum(1.0, np.abs(ts[ref, :4]))
+        assert d.max() < 1e-12, d
+        assert res.tr_param[i, 4] == 0.0
+    assert set(got) == want
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_T2_noise_free_helices_equal_truth(seed):
+    f = _noise_free(0.5, seed)
+    p = oracle.default_params("f64", x0_per_row=0.0)
+    ts = f.truth_state
+    res = oracle.track(f.sector, f.row, ts[:, 0], ts[:, 1], precision="f64", params=p)
+    tt = f.truth_track
+    checked = 0
+    for i in range(res.n_tracks):
+        tl = res.tr_tracklet[i]
+        hl = res.tracklet_hits(tl)
+        if len(np.unique(tt[hl])) != 1:
+            continue   # the tracklet also attached another track's hit; its fit is not pure
+        ref = hl[0]    # ascending row: the reference is the innermost tracklet hit
+        assert math.isclose(res.tr_xref[i], oracle.row_x(int(f.row[ref])), rel_tol=1e-15)
+        d = np.abs(res.tr_param[i] - ts[ref]) / np.maximum(1e-3, np.abs(ts[ref]))
+        assert d.max() < 1e-9, (i, d)
+        checked += 1
+    assert checked >= 0.98 * res.n_tracks
+    eff, nseg, clones, fakes = efficiency(f, oracle_track_list(res), min_clusters=10, pt_min=0.0)
+    assert eff > 0.98 and fakes == 0
+
+
+@pytest.mark.parametrize("cfg", ["pp_500", "pbpb_2x10000"])
+def test_T4_efficiency_above_95_percent(cfg, n_threads):
+    f = synth.generate(cfg, truth=False)
+    res = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", n_threads=n_threads)
+    eff, nseg, clones, fakes = efficiency(f, oracle_track_list(res))
+    assert nseg > 400
+    assert eff > 0.95, eff
+    assert clones <= 0.01 * nseg
+
+
+def test_fit_pulls_are_standard_normal():
+    """Smeared clusters, no scattering: (fit - truth) / sigma has mean ~0 and rms ~1 per parameter."""
+    f = synth.generate("pp_500", truth=True, noise_frac=0.0, dropout=0.0, seed=21)
+    p = oracle.default_params("f64", x0_per_row=0.0)
+    res = oracle.track(f.sector, f.row, f.y, f.w, precision="f64", params=p)
+    tt = f.truth_track
+    pulls = []
+    for i in range(res.n_tracks):
+        hl = res.tracklet_hits(res.tr_tracklet[i])
+        if len(np.unique(tt[hl])) != 1 or len(hl) < 40:
+            continue
+        ref = hl[0]
+        cov = res.tr_cov[i]
+        diag = np.array([cov[0], cov[2], cov[5], cov[9], cov[14]])
+        pulls.append((res.tr_param[i] - f.truth_state[ref]) / np.sqrt(diag))
+    pulls = np.array(pulls)
+    assert len(pulls) > 300
+    assert np.all(np.abs(pulls.mean(axis=0)) < 0.2), pulls.mean(axis=0)
+    rms = pulls.std(axis=0)
+    assert np.all((rms > 0.8) & (rms < 1.25)), rms
+
+
+def test_selection_invariants_and_canonical_order():
+    f = synth.generate("pbpb_2x10000", truth=False, mult_fixed=2000)
+    res = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", n_threads=8)
+    p = oracle.default_params("f32")
+    allhits = np.concatenate([res.track_hits(i) for i in range(res.n_tracks)])
+    assert len(np.unique(allhits)) == len(allhits), "a hit is shared by two tracks"
+    mins = []
+    for i in range(res.n_tracks):
+        h = res.track_hits(i)
+        assert len(h) >= p.nmin and len(h) == res.tr_nhits[i]
+        assert np.all(f.sector[h] == res.tr_sector[i])
+        assert np.all(np.diff(f.row[h].astype(int)) > 0)
+        tl = res.tr_tracklet[i]
+        assert 2 * len(h) >= res.tl_nhits[tl]
+        assert set(h.tolist()) <= set(res.tracklet_hits(tl).tolist())
+        mins.append((res.tr_sector[i], h.min()))
+    assert mins == sorted(mins)
+
+
+def test_input_permutation_invariance():
+    f = synth.generate("pp_500")
+    a = oracle.track(f.sector, f.row, f.y, f.w, precision="f32")
+    perm = np.random.default_rng(7).permutation(f.n)
+    b = oracle.track(f.sector[perm], f.row[perm], f.y[perm], f.w[perm], precision="f32")
+    sa = sorted(tuple(sorted(a.track_hits(i).tolist())) for i in range(a.n_tracks))
+    sb = sorted(tuple(sorted(perm[b.track_hits(i)].tolist())) for i in range(b.n_tracks))
+    assert sa == sb
+
+
+def test_malformed_input_rejected():
+    with pytest.raises(ValueError):
+        oracle.track(np.array([36], np.uint8), np.array([0], np.uint8), [0.0], [0.0])
+    with pytest.raises(ValueError):
+        oracle.track(np.array([0], np.uint8), np.array([152], np.uint8), [0.0], [0.0])
+    with pytest.raises(ValueError):
+        oracle.track(np.array([0], np.uint8), np.array([3], np.uint8), [np.nan], [0.0])
+    res = oracle.track(np.zeros(0, np.uint8), np.zeros(0, np.uint8), [], [])
+    assert res.n_tracks == 0
