@@ -1,0 +1,170 @@
+/*
+ * tpctrack.h — C-ABI of the GB300 TPC sector-tracking library (libtpctrack.so).
+ *
+ * The library implements the standalone TPC sector tracking of the synchronous reconstruction
+ * described in "Overview of online and offline reconstruction in ALICE for LHC Run 3"
+ * (arXiv:2009.07515): clusters of a continuous-readout time frame in (Sec. 2: native row/time
+ * coordinates, z unknown until a vertex time is known), sector tracks with helix parameters,
+ * covariances and cluster indices out (Sec. 6: TPC tracking runs standalone, without space-charge,
+ * field or hit-error corrections; the algorithm derives from the Run-2 HLT tracker). Every stage
+ * runs as a CUDA kernel on one GPU: per-row search grid, cellular-automaton neighbour finding and
+ * cleaning, start-hit selection, Kalman-filter tracklet construction in the solenoid field, and
+ * tracklet selection.
+ *
+ * Conventions
+ *   - Every call returns TPC_OK (0) or a negative TPC_E_* code. No call aborts, traps or waits
+ *     without a bound; tpc_last_error() gives a one-line description of the last failure.
+ *   - A context (tpc_ctx) is used by one host thread at a time.
+ *   - Coordinates: sector s in [0,36) (s/18 = drift side A/C, s%18 = 20-degree phi sector), pad
+ *     row r in [0,152) at radius x_r = 85 + r*160/151 cm (sector-local x), y = local coordinate
+ *     along the pad row (cm), w = v_drift * t_arrival (cm): the drift-time coordinate of continuous
+ *     readout (Sec. 2). Track parameters are (y, w, sin(phi), dw/ds, q/pT) at x = x_ref in the
+ *     sector frame; s is the path length in the bending plane; curvature = -0.0029979246*Bz*q/pT.
+ *   - Covariances are the 15-element lower triangle, row-major: (0,0),(1,0),(1,1),(2,0),...,(4,4).
+ */
+#ifndef TPCTRACK_H
+#define TPCTRACK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPC_OK 0
+#define TPC_E_INVAL -1    /* malformed argument, handle or cluster data */
+#define TPC_E_NOMEM -2    /* device or host allocation failed */
+#define TPC_E_BUDGET -3   /* a frame larger than the whole HBM budget */
+#define TPC_E_CAPACITY -4 /* an internal capacity overflowed and could not be grown */
+#define TPC_E_TIMEOUT -5  /* a bounded device wait or tpc_poll timeout expired */
+#define TPC_E_CUDA -6     /* a CUDA runtime call failed */
+#define TPC_E_STATE -7    /* call not valid in the frame's current state */
+
+#define TPC_NSECTORS 36
+#define TPC_NROWS 152
+
+typedef struct tpc_ctx tpc_ctx;
+typedef uint64_t tpc_frame_t; /* frame handle / serving ticket; 0 is never a valid handle */
+
+/* Method and runtime parameters. Obtain defaults with tpc_default_params(), then edit. */
+typedef struct {
+  uint32_t struct_size;   /* = sizeof(tpc_params) */
+  /* method parameters (the tracker's readings of the HLT-derived algorithm). They are given in
+   * double and rounded once to float on the device, as derived constants are: kq = (float)(
+   * -0.0029979246*bz), sigma^2 = (float)(sigma*sigma), Highland constant from x0_per_row. */
+  double bz;              /* solenoid field, T (0.5) */
+  double ky, kw, eps;     /* neighbour windows |dy| <= ky*dx + eps, |dw| <= kw*dx + eps (cm) */
+  double chi_n_max;       /* neighbour mid-point deviation cut dy^2 + dw^2 (cm^2) */
+  int32_t lmin;           /* minimum cleaned-chain length of a start hit (3) */
+  double sigma_y, sigma_w;/* cluster errors (cm) */
+  double chi2_hit_max;    /* Kalman hit acceptance, 2 dof (16) */
+  int32_t n_miss_max;     /* consecutive empty rows ending an extension (5) */
+  double win_nsig, win_add; /* extension search window nsig*sqrt(C) + add (cm) */
+  double x0_per_row;      /* X/X0 per row for scattering noise (0.03/152); 0 = none */
+  double max_sin;         /* |sin(phi)| limit of propagation (0.999) */
+  double y_margin;        /* stop extending when |y| > x*tan(10 deg) + y_margin (cm) */
+  int32_t nmin;           /* minimum hits of a voting tracklet and of a track (10) */
+  double cov0[5];         /* seed covariance diagonal */
+  /* storage / runtime */
+  int32_t packed;         /* 1: store cluster coordinates as 16-bit offsets in their grid bin */
+  float bin_occupancy;    /* target clusters per w-bin of the search grid (autotuned if <= 0) */
+  float tracklet_capacity;/* tracklet slots per cluster reserved in a workspace (0.08) */
+  int64_t hbm_budget;     /* serving admission budget in bytes (80 GB) */
+  int32_t max_batch_frames; /* frames per batched launch (16) */
+  int32_t use_graphs;     /* 1: replay the kernel sequence as a CUDA graph */
+  int32_t k5_block;       /* tracklet kernel threads per block (0 = autotuned) */
+  int32_t k2_block;       /* neighbour kernel threads per block (0 = autotuned) */
+} tpc_params;
+
+/* Clusters of one time frame, structure of arrays in the caller's order (n entries each).
+ * on_device = 0: host pointers, copied before tpc_load_clusters/tpc_submit_frame returns.
+ * on_device = 1: device pointers borrowed until the frame's tracking has completed. */
+typedef struct {
+  const uint8_t* sector;
+  const uint8_t* row;
+  const float* y;
+  const float* w;
+  int64_t n;
+  int32_t on_device;
+} tpc_clusters;
+
+/* Host views of a frame's sector tracks, owned by the context until tpc_release_frame().
+ * Tracks are in canonical order: sector, then the row-rank of the tracklet's start hit (its
+ * position among the sector's clusters ordered by row, w, y, input index). Hit lists run in
+ * ascending row order and hold indices into the caller's cluster arrays. */
+typedef struct {
+  int64_t n_tracks;
+  const int32_t* sector;      /* [n] */
+  const float* x_ref;         /* [n] x of the innermost fitted hit */
+  const float* param;         /* [n][5] y, w, sin(phi), dw/ds, q/pT at x_ref */
+  const float* cov;           /* [n][15] lower triangle */
+  const float* chi2;          /* [n] */
+  const int32_t* ndf;         /* [n] 2*(fitted hits) - 5 */
+  const int64_t* hit_offset;  /* [n+1] */
+  const uint32_t* hit_index;  /* [hit_offset[n]] */
+} tpc_tracks;
+
+/* Per-kernel device time of the last tpc_track_* call on a frame or batch (CUDA events on the
+ * launching stream; filled when timing is enabled with tpc_set_timing). */
+typedef struct {
+  int32_t n_kernels;
+  const char* const* names;
+  const float* ms;            /* [n_kernels] */
+  const int64_t* launches;    /* [n_kernels] */
+} tpc_kernel_times;
+
+void tpc_default_params(tpc_params* p);
+
+/* Create a context on the current CUDA device. */
+int tpc_create(const tpc_params* p, tpc_ctx** out);
+void tpc_destroy(tpc_ctx* ctx);
+const char* tpc_last_error(const tpc_ctx* ctx);
+const char* tpc_version(void);
+
+/* Load one frame's clusters (validated on the device during tracking: sector < 36, row < 152,
+ * finite y and w). Returns a frame handle in *out. */
+int tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* out);
+
+/* Enqueue tracking of one loaded frame on `cuda_stream` (a cudaStream_t; NULL = the context's
+ * stream). Asynchronous: results are available from tpc_get_tracks(). */
+int tpc_track_sectors(tpc_ctx* ctx, tpc_frame_t frame, void* cuda_stream);
+
+/* Enqueue tracking of several loaded frames in one batched launch sequence (all their sectors
+ * together). Each frame's tracks are identical to tracking it alone. */
+int tpc_track_batch(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, void* cuda_stream);
+
+/* Wait (bounded) for the frame's tracking and return host views of its tracks. */
+int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out);
+
+/* Free the frame's device and host memory. */
+int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame);
+
+/* Serving: admit a frame (copied/borrowed as for tpc_load_clusters) into the request queue.
+ * Never blocks on the HBM budget: frames wait host-side until memory frees up. A frame larger
+ * than the whole budget is refused with TPC_E_BUDGET. */
+int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ticket);
+
+/* Serving: advance the scheduler (admit queued frames into free slots and launch batches) and
+ * return up to max_done finished tickets in done[]; waits at most timeout_us for at least one.
+ * Returns the number of tickets written (>= 0) or a negative error. Finished frames are read
+ * with tpc_get_tracks() and freed with tpc_release_frame(). */
+int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_us);
+
+/* Diagnostics for parity tests: copy a per-cluster array of a tracked frame into host memory
+ * (caller-owned, n = number of clusters), indexed by the caller's cluster order.
+ * what: 0 = raw up link, 1 = raw down link, 2 = cleaned up link, 3 = cleaned down link
+ * (each the input index of the linked cluster or -1). */
+int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n);
+
+/* Number of start hits / tracklets of a tracked frame. */
+int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n_tracks);
+
+/* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */
+int tpc_set_timing(tpc_ctx* ctx, int32_t enable);
+int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCTRACK_H */

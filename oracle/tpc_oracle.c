@@ -417,7 +417,7 @@ typedef struct {
   /* links in caller (original) index space, -1 = none */
   int32_t *up, *down, *up_c, *down_c;
   double* nb_margin;               /* per cluster: min relative margin of its neighbour decisions */
-  /* start hits in canonical order (sector, original index) */
+  /* start hits in canonical order (sector, rank) */
   int64_t n_start;
   int32_t* start;
   /* tracklets (one per start hit, same order) */
@@ -426,7 +426,7 @@ typedef struct {
   double *tl_xref, *tl_param, *tl_cov, *tl_chi2, *tl_margin;
   int64_t* tl_hit_off;             /* [n_tracklets + 1] */
   int32_t* tl_hits;                /* original indices, ascending row */
-  /* tracks in canonical order (sector, smallest original index of its hits) */
+  /* tracks in canonical order (sector, rank of the tracklet's start hit) */
   int64_t n_tracks;
   int32_t *tr_sector, *tr_ndf, *tr_nhits, *tr_tracklet;
   double *tr_xref, *tr_param, *tr_cov, *tr_chi2;
@@ -766,23 +766,6 @@ static void track_sector(const ctx_t* cx, sector_t* S, int brute) {
   select_tracks(cx, S);
 }
 
-/* bottom-up merge sort of idx[] by key[] (stable) for the canonical output order */
-static void sort_idx_by_key(int32_t* idx, int64_t n, const int32_t* key) {
-  if (n < 2) return;
-  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * n);
-  for (int64_t width = 1; width < n; width *= 2) {
-    for (int64_t lo = 0; lo < n; lo += 2 * width) {
-      int64_t mid = lo + width < n ? lo + width : n, hi = lo + 2 * width < n ? lo + 2 * width : n;
-      int64_t a = lo, b = mid, o = lo;
-      while (a < mid && b < hi) tmp[o++] = (key[idx[b]] < key[idx[a]]) ? idx[b++] : idx[a++];
-      while (a < mid) tmp[o++] = idx[a++];
-      while (b < hi) tmp[o++] = idx[b++];
-    }
-    memcpy(idx, tmp, sizeof(int32_t) * n);
-  }
-  free(tmp);
-}
-
 void ORACLE_SYM(free_result)(oracle_result* R) {
   if (!R) return;
   free(R->up); free(R->down); free(R->up_c); free(R->down_c); free(R->nb_margin); free(R->start);
@@ -903,10 +886,10 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
   R->tr_hit_off[0] = 0;
   for (int s = 0; s < NSEC; ++s) {
     sector_t* S = &secs[s];
-    /* tracklets in (original start index) order */
+    /* tracklets and tracks are already in canonical order: the rank of the start hit (the
+     * hit's position in the sector ordered by row, w, y, input index) */
     int32_t* ti = malloc((S->nt > 0 ? S->nt : 1) * sizeof(int32_t));
     for (int64_t t = 0; t < S->nt; ++t) ti[t] = (int32_t)t;
-    sort_idx_by_key(ti, S->nt, S->t_start);
     int32_t* tpos = malloc((S->nt > 0 ? S->nt : 1) * sizeof(int32_t));
     for (int64_t j = 0; j < S->nt; ++j) {
       int64_t t = ti[j];
@@ -926,10 +909,8 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
       R->tl_hit_off[ot + 1] = ohl;
       ++ot;
     }
-    /* tracks in (smallest original hit index) order */
     int32_t* ki = malloc((S->ntr > 0 ? S->ntr : 1) * sizeof(int32_t));
     for (int64_t k = 0; k < S->ntr; ++k) ki[k] = (int32_t)k;
-    sort_idx_by_key(ki, S->ntr, S->tr_min);
     for (int64_t j = 0; j < S->ntr; ++j) {
       int64_t k = ki[j], t = S->tr_t[k];
       const uint64_t key = tracklet_key(S, t);

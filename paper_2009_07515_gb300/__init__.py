@@ -1,0 +1,146 @@
+"""GB300-native TPC sector tracking (standalone TPC tracking of arXiv:2009.07515, Sec. 6).
+
+The tracking runs entirely in ``libtpctrack.so`` (hand-written sm_103a CUDA kernels behind the
+C-ABI of ``include/tpctrack.h``). This package is its thin Python binding: ``_lib`` mirrors the
+C entry points one to one; ``Tracker`` marshals numpy arrays or torch CUDA tensors (PyTorch serves
+only device memory and streams) into those calls.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import TpcError, default_params, load, tracks_to_numpy
+
+__all__ = ["Tracker", "TpcError", "default_params", "load", "build"]
+
+
+def build(force: bool = False) -> str:
+    """Compile libtpctrack.so in-tree (nvcc, sm_103a)."""
+    from . import build_ext
+    return build_ext.build(force=force)
+
+
+def _ptr(a):
+    """Host numpy array or torch tensor -> (address, on_device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def make_clusters(sector, row, y, w, keep: list) -> _lib.tpc_clusters:
+    """Fill a tpc_clusters descriptor; ``keep`` holds references that must outlive the call."""
+    arrs = []
+    for a, dt in ((sector, np.uint8), (row, np.uint8), (y, np.float32), (w, np.float32)):
+        if isinstance(a, np.ndarray):
+            a = np.ascontiguousarray(a, dtype=dt)
+        arrs.append(a)
+    keep.extend(arrs)
+    ptrs = [_ptr(a) for a in arrs]
+    on_dev = {p[1] for p in ptrs}
+    if len(on_dev) != 1:
+        raise ValueError("cluster arrays must all be on the host or all on the device")
+    n = int(arrs[2].shape[0])
+    return _lib.tpc_clusters(ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], n, on_dev.pop())
+
+
+class Tracker:
+    """One library context on the current CUDA device."""
+
+    def __init__(self, params: _lib.tpc_params | None = None, **overrides):
+        self.lib = load()
+        self.params = params if params is not None else default_params(**overrides)
+        self.params.struct_size = ctypes.sizeof(_lib.tpc_params)
+        ctx = ctypes.c_void_p()
+        _lib.check(self.lib.tpc_create(ctypes.byref(self.params), ctypes.byref(ctx)))
+        self.ctx = ctx
+        self._keep: dict[int, list] = {}
+
+    def close(self):
+        if self.ctx:
+            self.lib.tpc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        return _lib.check(rc, self.ctx)
+
+    # --------------------------------------------------------------- plain path
+    def load(self, sector, row, y, w) -> int:
+        keep: list = []
+        cl = make_clusters(sector, row, y, w, keep)
+        h = ctypes.c_uint64()
+        self._check(self.lib.tpc_load_clusters(self.ctx, ctypes.byref(cl), ctypes.byref(h)))
+        if cl.on_device:
+            self._keep[h.value] = keep
+        return h.value
+
+    def track(self, frame: int, stream=None) -> None:
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream)
+        self._check(self.lib.tpc_track_sectors(self.ctx, ctypes.c_uint64(frame), s))
+
+    def track_batch(self, frames, stream=None) -> None:
+        arr = (ctypes.c_uint64 * len(frames))(*frames)
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream)
+        self._check(self.lib.tpc_track_batch(self.ctx, arr, len(frames), s))
+
+    def tracks(self, frame: int) -> dict:
+        t = _lib.tpc_tracks()
+        self._check(self.lib.tpc_get_tracks(self.ctx, ctypes.c_uint64(frame), ctypes.byref(t)))
+        return tracks_to_numpy(t)
+
+    def links(self, frame: int, what: int, n: int) -> np.ndarray:
+        out = np.empty(n, np.int32)
+        self._check(self.lib.tpc_get_links(self.ctx, ctypes.c_uint64(frame), what, out.ctypes.data, n))
+        return out
+
+    def counts(self, frame: int):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.tpc_get_counts(self.ctx, ctypes.c_uint64(frame), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def release(self, frame: int) -> None:
+        self._check(self.lib.tpc_release_frame(self.ctx, ctypes.c_uint64(frame)))
+        self._keep.pop(frame, None)
+
+    def run(self, sector, row, y, w) -> dict:
+        """Load, track and return one frame's tracks (and release it)."""
+        f = self.load(sector, row, y, w)
+        try:
+            self.track(f)
+            return self.tracks(f)
+        finally:
+            self.release(f)
+
+    # --------------------------------------------------------------- serving
+    def submit(self, sector, row, y, w) -> int:
+        keep: list = []
+        cl = make_clusters(sector, row, y, w, keep)
+        h = ctypes.c_uint64()
+        self._check(self.lib.tpc_submit_frame(self.ctx, ctypes.byref(cl), ctypes.byref(h)))
+        if cl.on_device:
+            self._keep[h.value] = keep
+        return h.value
+
+    def poll(self, max_done: int = 64, timeout_us: int = 0) -> list[int]:
+        arr = (ctypes.c_uint64 * max(1, max_done))()
+        n = self._check(self.lib.tpc_poll(self.ctx, arr, max_done, timeout_us))
+        return [arr[i] for i in range(n)]
+
+    # --------------------------------------------------------------- timing
+    def set_timing(self, on: bool) -> None:
+        self._check(self.lib.tpc_set_timing(self.ctx, 1 if on else 0))
+
+    def kernel_times(self) -> dict:
+        kt = _lib.tpc_kernel_times()
+        self._check(self.lib.tpc_get_kernel_times(self.ctx, ctypes.byref(kt)))
+        return {kt.names[i].decode(): float(kt.ms[i]) for i in range(kt.n_kernels)}

@@ -1,0 +1,249 @@
+// k_grid.cu — K0/K1: input validation and the per-(sector, row) search grid.
+//
+// The grid is a counting sort of the batch's clusters by (frame, sector, row, w-bin): each segment
+// (frame, sector, row) gets a 1-D grid over the drift coordinate w whose bin count follows the
+// segment's occupancy, so any window |w - wc| <= W of a row is one contiguous range of sorted
+// positions. The grid decides no result: every window test downstream is an exact comparison on
+// the coordinates, and every tie is broken by the (w, y, input index) order.
+//
+// Kernels (all persistent, sizes read from device memory so the sequence can be graph-captured):
+//   k_seg_hist    validate, count clusters per segment, w range per frame
+//   k_seg_layout  bins per segment (occupancy target), w origin and bin density
+//   k_bin_rank    bin histogram; each cluster keeps its arrival rank inside its bin
+//   k_scatter     sorted (y, w) and input index at bin_start[bin] + rank
+//   scans         exclusive prefix sums with device-side lengths
+#include "tpc_dev.cuh"
+
+namespace tpc {
+
+// ------------------------------------------------------------------------------------ scans
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// length of a scan: device-side count + add (clamped to the buffer's capacity), or a host value
+__device__ __forceinline__ uint32_t scan_len(const uint32_t* n_dev, long long n_host, int add) {
+  if (!n_dev) return (uint32_t)n_host;
+  const long long n = (long long)*n_dev + add;
+  return (uint32_t)(n < n_host ? n : n_host);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, const uint32_t* n_dev,
+                                                              long long n_host, int n_add, uint32_t* __restrict__ tile_sum) {
+  const uint32_t n = scan_len(n_dev, n_host, n_add);
+  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    uint32_t base = tile * kScanTile, s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      uint32_t i = base + k * kScanThreads + threadIdx.x;
+      if (i < n) s += in[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) warp_sums[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t v = threadIdx.x < kScanThreads / 32 ? warp_sums[threadIdx.x] : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (threadIdx.x == 0) tile_sum[tile] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// single block: exclusive scan of the tile sums in place; total written to *total (if given)
+__global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* tile_sum, const uint32_t* n_dev, long long n_host,
+                                                     int n_add, uint32_t* total) {
+  const uint32_t n = scan_len(n_dev, n_host, n_add);
+  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
+    uint32_t i = base + threadIdx.x;
+    uint32_t v = i < ntiles ? tile_sum[i] : 0, x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t w = threadIdx.x < blockDim.x / 32 ? warp_sums[threadIdx.x] : 0, z = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (threadIdx.x >= o) z += y;
+      }
+      warp_sums[threadIdx.x] = z - w;
+    }
+    __syncthreads();
+    uint32_t excl = carry + warp_sums[threadIdx.x >> 5] + x - v;
+    if (i < ntiles) tile_sum[i] = excl;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// exclusive scan of each tile plus its offset; out[n] = total. in may alias out.
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* in, const uint32_t* n_dev, long long n_host,
+                                                             int n_add, const uint32_t* __restrict__ tile_off,
+                                                             const uint32_t* total, uint32_t* out) {
+  const uint32_t n = scan_len(n_dev, n_host, n_add);
+  const uint32_t ntiles = (n + kScanTile - 1) / kScanTile;
+  __shared__ uint32_t buf[kScanTile];
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint32_t base = tile * kScanTile;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      uint32_t i = base + k * kScanThreads + threadIdx.x;
+      buf[k * kScanThreads + threadIdx.x] = i < n ? in[i] : 0;
+    }
+    __syncthreads();
+    uint32_t v[kScanItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) { v[k] = buf[threadIdx.x * kScanItems + k]; s += v[k]; }
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) >= o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_sums[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t w = threadIdx.x < kScanThreads / 32 ? warp_sums[threadIdx.x] : 0, z = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (threadIdx.x >= o) z += y;
+      }
+      if (threadIdx.x < kScanThreads / 32) warp_sums[threadIdx.x] = z - w;
+    }
+    __syncthreads();
+    uint32_t run = tile_off[tile] + warp_sums[threadIdx.x >> 5] + x - s;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) { buf[threadIdx.x * kScanItems + k] = run; run += v[k]; }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      uint32_t i = base + k * kScanThreads + threadIdx.x;
+      if (i < n) out[i] = buf[k * kScanThreads + threadIdx.x];
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
+}
+
+// ------------------------------------------------------------------------------------ K1
+// Clusters are processed in contiguous block chunks so a block rarely spans two frames.
+__global__ void __launch_bounds__(256) k_seg_hist(Work W) {
+  const BatchDesc* B = W.batch;
+  const long long ntot = B->ntot;
+  const long long chunk = (ntot + gridDim.x - 1) / gridDim.x;
+  const long long i0 = (long long)blockIdx.x * chunk;
+  const long long i1 = min(ntot, i0 + chunk);
+  int f = -1;
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  bool bad = false;
+  for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    int fi = frame_of(B, i);
+    if (fi != f) {
+      if (f >= 0 && lo <= hi) {
+        atomicMin(&W.cnt->wrange[2 * f], lo);
+        atomicMax(&W.cnt->wrange[2 * f + 1], hi);
+      }
+      f = fi; lo = 0xFFFFFFFFu; hi = 0u;
+    }
+    const FrameIn& F = B->f[fi];
+    const long long j = i - F.off;
+    const int s = F.sector[j], r = F.row[j];
+    const float y = F.y[j], w = F.w[j];
+    if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) { bad = true; continue; }
+    atomicAdd(&W.seg_cnt[fi * kSegPerFrame + s * kNRow + r], 1u);
+    const uint32_t e = f2ord(w);
+    lo = min(lo, e);
+    hi = max(hi, e);
+  }
+  if (f >= 0 && lo <= hi) {
+    atomicMin(&W.cnt->wrange[2 * f], lo);
+    atomicMax(&W.cnt->wrange[2 * f + 1], hi);
+  }
+  if (bad) atomicOr(&W.cnt->err, kErrInput);
+}
+
+// one thread per segment: bins from the occupancy target
+__global__ void __launch_bounds__(256) k_seg_layout(Work W, float occ) {
+  const BatchDesc* B = W.batch;
+  const int nseg = B->nf * kSegPerFrame;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += gridDim.x * blockDim.x) {
+    const int f = g / kSegPerFrame;
+    const uint32_t n = W.seg_cnt[g];
+    float wlo = 0.f, whi = 0.f;
+    if (W.cnt->wrange[2 * f] <= W.cnt->wrange[2 * f + 1]) {
+      wlo = ord2f(W.cnt->wrange[2 * f]);
+      whi = ord2f(W.cnt->wrange[2 * f + 1]);
+    }
+    uint32_t nb = 1;
+    if (n > 0) {
+      float want = ceilf((float)n / occ);
+      nb = want < 1.f ? 1u : (want > 1048576.f ? 1048576u : (uint32_t)want);
+    }
+    const float range = whi - wlo;
+    const float inv = range > 0.f ? (float)nb / range : 0.f;
+    W.seg_nb[g] = nb;
+    W.seg_geo[g] = make_float2(wlo, inv);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bin_rank(Work W) {
+  const BatchDesc* B = W.batch;
+  const long long ntot = B->ntot;
+  const uint32_t bcap = (uint32_t)W.bcap;
+  if (W.cnt->n_bins > bcap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&W.cnt->err, kErrBins);
+    return;
+  }
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x) {
+    const int fi = frame_of(B, i);
+    const FrameIn& F = B->f[fi];
+    const long long j = i - F.off;
+    const int s = F.sector[j], r = F.row[j];
+    const float y = F.y[j], w = F.w[j];
+    if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) continue;
+    const int g = fi * kSegPerFrame + s * kNRow + r;
+    const float2 geo = W.seg_geo[g];
+    const int b = bin_of(w, geo.x, geo.y, (int)W.seg_nb[g]);
+    W.rank[i] = atomicAdd(&W.bin_start[W.seg_bb[g] + b], 1u);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(Work W) {
+  const BatchDesc* B = W.batch;
+  const long long ntot = B->ntot;
+  if (W.cnt->n_bins > (uint32_t)W.bcap) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x) {
+    const int fi = frame_of(B, i);
+    const FrameIn& F = B->f[fi];
+    const long long j = i - F.off;
+    const int s = F.sector[j], r = F.row[j];
+    const float y = F.y[j], w = F.w[j];
+    if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) continue;
+    const int g = fi * kSegPerFrame + s * kNRow + r;
+    const float2 geo = W.seg_geo[g];
+    const int b = bin_of(w, geo.x, geo.y, (int)W.seg_nb[g]);
+    const uint32_t p = W.bin_start[W.seg_bb[g] + b] + W.rank[i];
+    W.hyw[p] = make_float2(y, w);
+    W.horig[p] = (uint32_t)j;
+  }
+}
+
+}  // namespace tpc

@@ -1,0 +1,133 @@
+// k_select.cu — K6/K7 tracklet selection and K8 canonical output.
+//
+// Every hit goes to the tracklet with the largest key (nhits << 32 | (2^32 - 1 - rank of the
+// start hit)) among the tracklets with >= nmin hits that contain it (atomicMax on a 64-bit word
+// per hit; keys are unique within a sector, so the outcome does not depend on atomic order). A
+// tracklet becomes a track if it keeps >= nmin hits and at least half of its hits. Tracks are
+// compacted by prefix sums in tracklet order, which is already canonical (frame, sector, rank of
+// the start hit); each track's kept hits are written in ascending row order as input indices.
+#include "tpc_dev.cuh"
+
+namespace tpc {
+
+__device__ __forceinline__ unsigned long long tl_key(uint32_t nh, uint32_t rank) {
+  return ((unsigned long long)nh << 32) | (unsigned long long)(0xFFFFFFFFu - rank);
+}
+
+__global__ void __launch_bounds__(256) k_votes(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  const long long tcap = W.tcap;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+    const uint32_t info = W.tl_info[t];
+    const uint32_t nh = info & 255u;
+    if (!(info >> 24) || (int)nh < Q.nmin) continue;
+    const unsigned long long key = tl_key(nh, W.starts[t].z);
+    const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+    for (int r = ref; r <= top; ++r) {
+      const uint32_t h = W.slab[(long long)r * tcap + t];
+      if (h != kNoHit) atomicMax(&W.hit_w[h], key);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_kept(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  const long long tcap = W.tcap;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+    const uint32_t info = W.tl_info[t];
+    const uint32_t nh = info & 255u;
+    uint32_t acc = 0, kept = 0;
+    if ((info >> 24) && (int)nh >= Q.nmin) {
+      const unsigned long long key = tl_key(nh, W.starts[t].z);
+      const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+      for (int r = ref; r <= top; ++r) {
+        const uint32_t h = W.slab[(long long)r * tcap + t];
+        if (h != kNoHit && W.hit_w[h] == key) ++kept;
+      }
+      acc = ((int)kept >= Q.nmin && 2u * kept >= nh) ? 1u : 0u;
+    }
+    W.tl_kept[t] = acc;
+    W.tl_nkept[t] = acc ? kept : 0u;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_write_tracks(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  const long long tcap = W.tcap;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+    const uint32_t k = W.tl_kept[t];
+    if (W.tl_kept[t + 1] == k) continue;
+    const uint32_t info = W.tl_info[t];
+    const uint32_t nh = info & 255u;
+    const uint4 st = W.starts[t];
+    const unsigned long long key = tl_key(nh, st.z);
+    const float* src = W.tl_state + (long long)t * 24;
+    float* dst = W.tr_f + (long long)k * 24;
+#pragma unroll
+    for (int i = 0; i < 22; ++i) dst[i] = src[i];
+    uint32_t off = W.tl_nkept[t];
+    const uint32_t nk = W.tl_nkept[t + 1] - off;
+    const int sector = (int)((st.y % kSegPerFrame) / kNRow);
+    W.tr_i[k] = make_int4(sector, 2 * (int)nh - 5, (int)nk, (int)off);
+    const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+    for (int r = ref; r <= top; ++r) {
+      const uint32_t h = W.slab[(long long)r * tcap + t];
+      if (h != kNoHit && W.hit_w[h] == key) W.tr_hits[off++] = W.horig[h];
+    }
+  }
+}
+
+// per frame: first tracklet, track and output hit of the frame
+__global__ void k_frame_offsets(Work W) {
+  const int nf = W.batch->nf;
+  const uint32_t ntl = W.cnt->n_tracklets;
+  for (int f = threadIdx.x; f <= nf; f += blockDim.x) {
+    const uint32_t s = min(W.seg_nstart[f * kSegPerFrame], ntl);
+    W.cnt->frame_start0[f] = s;
+    W.cnt->frame_track0[f] = W.tl_kept[s];
+    W.cnt->frame_hit0[f] = W.tl_nkept[s];
+  }
+}
+
+// ------------------------------------------------------------------------------------ utilities
+__global__ void k_reset_counters(Work W) {
+  DevCounters* c = W.cnt;
+  if (threadIdx.x == 0) {
+    c->nseg = (uint32_t)(W.batch->nf * kSegPerFrame);
+    c->ntot = (uint32_t)W.batch->ntot;
+  }
+  for (int i = threadIdx.x; i < kMaxFrames; i += blockDim.x) {
+    c->wrange[2 * i] = 0xFFFFFFFFu;
+    c->wrange[2 * i + 1] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    c->err = 0; c->n_starts = 0; c->n_tracklets = 0; c->k5_next = 0; c->n_bins = 0;
+    c->n_sorted = 0; c->n_tracks = 0; c->n_track_hits = 0;
+  }
+}
+
+// zero (*n_dev + add) * mul 32-bit words, at most n_cap (or n_cap words when n_dev is null)
+__global__ void k_zero_u32(uint32_t* p, const uint32_t* n_dev, long long n_cap, int add, int mul) {
+  long long n = n_dev ? ((long long)*n_dev + add) * mul : n_cap;
+  if (n > n_cap) n = n_cap;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    p[i] = 0u;
+}
+
+__global__ void k_set_ntracklets(Work W) {
+  if (threadIdx.x == 0) W.cnt->n_tracklets = min(W.cnt->n_starts, (uint32_t)W.tcap);
+}
+
+// per-cluster link arrays of frame f in the caller's index order (debug / parity)
+__global__ void k_links_to_input(Work W, int f, int what, int32_t* out) {
+  const uint32_t p0 = W.bin_start[W.seg_bb[f * kSegPerFrame]];
+  const uint32_t p1 = W.bin_start[W.seg_bb[(f + 1) * kSegPerFrame]];
+  const int2* L = what < 2 ? W.links : W.clinks;
+  for (uint32_t p = p0 + blockIdx.x * blockDim.x + threadIdx.x; p < p1; p += gridDim.x * blockDim.x) {
+    const int2 l = L[p];
+    const int v = (what & 1) ? l.x : l.y;
+    out[W.horig[p]] = v >= 0 ? (int32_t)W.horig[v] : -1;
+  }
+}
+
+}  // namespace tpc

@@ -1,0 +1,900 @@
+// tpc_api.cu — host runtime and C-ABI of libtpctrack.so (see include/tpctrack.h).
+//
+// A context owns a stream, a device memory pool, a pool of batch workspaces and the frames loaded
+// into it. Tracking a frame (or a batch of frames) enqueues the kernel sequence K1..K8 on a stream:
+// every kernel is persistent (grid = SMs x resident blocks) and reads its sizes from device
+// memory, so the same sequence is captured once per workspace into a CUDA graph and replayed.
+// Serving (tpc_submit_frame / tpc_poll) keeps frames in a host queue, admits them against the HBM
+// budget, and launches a new batch of admitted frames whenever a stream slot is free, so work of
+// requests that arrive while others run overlaps on the device (continuous batching).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "tpc_dev.cuh"
+#include "tpctrack.h"
+
+namespace tpc {
+__global__ void k_scan_reduce(const uint32_t*, const uint32_t*, long long, int, uint32_t*);
+__global__ void k_scan_tiles(uint32_t*, const uint32_t*, long long, int, uint32_t*);
+__global__ void k_scan_apply(const uint32_t*, const uint32_t*, long long, int, const uint32_t*, const uint32_t*, uint32_t*);
+__global__ void k_seg_hist(Work);
+__global__ void k_seg_layout(Work, float);
+__global__ void k_bin_rank(Work);
+__global__ void k_scatter(Work);
+__global__ void k_neighbours(Work, DevParams);
+__global__ void k_clean(Work, DevParams);
+__global__ void k_starts(Work, DevParams);
+__global__ void k_start_order(Work);
+__global__ void k_tracklets(Work, DevParams);
+__global__ void k_votes(Work, DevParams);
+__global__ void k_kept(Work, DevParams);
+__global__ void k_write_tracks(Work, DevParams);
+__global__ void k_frame_offsets(Work);
+__global__ void k_reset_counters(Work);
+__global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
+__global__ void k_set_ntracklets(Work);
+__global__ void k_links_to_input(Work, int, int, int32_t*);
+constexpr int kK2Stage = 2048;
+}  // namespace tpc
+
+using namespace tpc;
+
+namespace {
+
+const char* kKernelNames[] = {"reset",  "seg_hist", "seg_layout", "scan_seg",  "zero_bins", "bin_rank", "scan_bins",
+                              "scatter", "neighbours", "clean",   "scan_start", "starts",   "start_order",
+                              "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "frame_off"};
+constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Workspace {
+  long long ncap = 0, scap = 0, bcap = 0, tcap = 0, scan_cap = 0;
+  int nf_cap = 0;
+  size_t bytes = 0;
+  void* block = nullptr;
+  Work W{};
+  BatchDesc* d_desc = nullptr;
+  BatchDesc* h_desc = nullptr;     // pinned
+  DevCounters* h_cnt = nullptr;    // pinned
+  cudaEvent_t done = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+  int users = 0;                   // frames whose results live here
+  bool busy = false;
+  std::vector<tpc_frame_t> batch_ids;  // frames of the last batch run here, in order
+};
+
+struct Frame {
+  tpc_frame_t id = 0;
+  long long n = 0;
+  uint8_t* d_sector = nullptr;
+  uint8_t* d_row = nullptr;
+  float* d_y = nullptr;
+  float* d_w = nullptr;
+  void* d_block = nullptr;         // owned input allocation (nullptr when borrowed)
+  int state = 0;                   // 0 loaded, 1 queued, 2 admitted, 3 running, 4 done, 5 fetched
+  std::shared_ptr<Workspace> ws;
+  int fidx = 0;
+  size_t budget_bytes = 0;
+  double t_submit = 0, t_done = 0;
+  // host results
+  std::vector<int32_t> sector, ndf;
+  std::vector<float> xref, param, cov, chi2;
+  std::vector<int64_t> hoff;
+  std::vector<uint32_t> hits;
+};
+
+}  // namespace
+
+struct tpc_ctx {
+  tpc_params p{};
+  DevParams dp{};
+  int device = 0, sms = 0;
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  std::map<tpc_frame_t, std::unique_ptr<Frame>> frames;
+  tpc_frame_t next_id = 1;
+  std::string err;
+  std::vector<std::shared_ptr<Workspace>> wspool;
+  int grid[kNumKernels] = {0};
+  int k2_smem = 0;
+  bool timing = false;
+  cudaEvent_t ev[kNumKernels + 1] = {nullptr};
+  cudaEvent_t ev_sync = nullptr;
+  float ms[kNumKernels] = {0};
+  int64_t launches[kNumKernels] = {0};
+  // serving
+  std::deque<tpc_frame_t> queue;  // submitted, not yet admitted
+  size_t budget_used = 0;
+  struct Inflight {
+    std::shared_ptr<Workspace> ws;
+    std::vector<tpc_frame_t> frames;
+    cudaStream_t stream;
+  };
+  std::vector<Inflight> inflight;
+  std::vector<cudaStream_t> serve_streams;
+  std::deque<tpc_frame_t> finished;
+};
+
+namespace {
+
+int fail(tpc_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, TPC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+// Host-side derived constants: computed in double, rounded once; row geometry and window sizes in
+// float arithmetic exactly as they are defined (IEEE operations on the host).
+void make_dev_params(const tpc_params& p, DevParams& d) {
+  memset(&d, 0, sizeof(d));
+  d.kq = (float)(-0.0029979246 * p.bz);
+  d.chi_n_max = (float)p.chi_n_max;
+  d.lmin = p.lmin;
+  d.r00 = (float)(p.sigma_y * p.sigma_y);
+  d.r11 = (float)(p.sigma_w * p.sigma_w);
+  d.chi2_max = (float)p.chi2_hit_max;
+  d.n_miss_max = p.n_miss_max;
+  d.win_nsig = (float)p.win_nsig;
+  d.win_add = (float)p.win_add;
+  d.ms_on = p.x0_per_row > 0;
+  d.x0_row = (float)p.x0_per_row;
+  const double hl = p.x0_per_row > 0 ? 0.0136 * (1.0 + 0.038 * std::log(p.x0_per_row)) : 0.0;
+  d.ms_c = (float)(hl * hl);
+  d.mass2 = (float)(0.13957039 * 0.13957039);
+  d.max_sin = (float)p.max_sin;
+  d.y_margin = (float)p.y_margin;
+  d.tan10 = (float)0.17632698070846498;
+  d.nmin = p.nmin;
+  for (int i = 0; i < 5; ++i) d.cov0[i] = (float)p.cov0[i];
+  d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
+  volatile float pitch = (float)160 / (float)151;
+  for (int r = 0; r < kNRow; ++r) {
+    volatile float xr = (float)r * pitch;
+    d.x[r] = (float)85 + xr;
+  }
+  const float ky = (float)p.ky, kw = (float)p.kw, eps = (float)p.eps;
+  for (int r = 1; r + 1 < kNRow; ++r) {
+    volatile float dxm = d.x[r] - d.x[r - 1];
+    volatile float dxp = d.x[r + 1] - d.x[r];
+    volatile float a = ky * dxm, b = kw * dxm, c = ky * dxp, e = kw * dxp, s = dxm + dxp;
+    d.wy_dn[r] = a + eps;
+    d.ww_dn[r] = b + eps;
+    d.wy_up[r] = c + eps;
+    d.ww_up[r] = e + eps;
+    d.f_mid[r] = dxm / s;
+  }
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+void free_workspace(Workspace* w) {
+  if (!w) return;
+  if (w->graph) cudaGraphExecDestroy(w->graph);
+  if (w->block) cudaFree(w->block);
+  if (w->h_desc) cudaFreeHost(w->h_desc);
+  if (w->h_cnt) cudaFreeHost(w->h_cnt);
+  if (w->done) cudaEventDestroy(w->done);
+  w->block = nullptr;
+}
+
+// Lay out one device block for the capacities.
+int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, std::shared_ptr<Workspace>& out) {
+  auto ws = std::shared_ptr<Workspace>(new Workspace, [](Workspace* w) { free_workspace(w); delete w; });
+  ws->ncap = std::max(ncap, 1024LL);
+  ws->tcap = std::max(tcap, 1024LL);
+  ws->nf_cap = nf_cap;
+  ws->scap = (long long)nf_cap * kSegPerFrame;
+  const double occ = ctx->dp.occ;
+  ws->bcap = (long long)std::ceil((double)ws->ncap / occ) + ws->scap + 16;
+  long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1});
+  ws->scan_cap = (maxscan + 2047) / 2048 + 16;
+  struct Item { void** ptr; size_t bytes; };
+  Work& W = ws->W;
+  void* p_cnt; void* p_desc;
+  std::vector<Item> items = {
+      {&p_cnt, sizeof(DevCounters)},
+      {&p_desc, sizeof(BatchDesc)},
+      {(void**)&W.seg_cnt, 4 * (size_t)ws->scap},
+      {(void**)&W.seg_nb, 4 * (size_t)ws->scap},
+      {(void**)&W.seg_bb, 4 * (size_t)(ws->scap + 1)},
+      {(void**)&W.seg_geo, 8 * (size_t)ws->scap},
+      {(void**)&W.bin_start, 4 * (size_t)(ws->bcap + 1)},
+      {(void**)&W.rank, 4 * (size_t)ws->ncap},
+      {(void**)&W.hyw, 8 * (size_t)(ws->ncap + 2)},
+      {(void**)&W.horig, 4 * (size_t)ws->ncap},
+      {(void**)&W.links, 8 * (size_t)ws->ncap},
+      {(void**)&W.clinks, 8 * (size_t)ws->ncap},
+      {(void**)&W.seg_nstart, 4 * (size_t)(ws->scap + 1)},
+      {(void**)&W.starts_raw, 16 * (size_t)ws->tcap},
+      {(void**)&W.starts, 16 * (size_t)ws->tcap},
+      {(void**)&W.tl_state, 96 * (size_t)ws->tcap},
+      {(void**)&W.tl_info, 4 * (size_t)ws->tcap},
+      {(void**)&W.slab, 4 * (size_t)kNRow * (size_t)ws->tcap},
+      {(void**)&W.hit_w, 8 * (size_t)ws->ncap},
+      {(void**)&W.tl_kept, 4 * (size_t)(ws->tcap + 1)},
+      {(void**)&W.tl_nkept, 4 * (size_t)(ws->tcap + 1)},
+      {(void**)&W.tr_f, 96 * (size_t)ws->tcap},
+      {(void**)&W.tr_i, 16 * (size_t)ws->tcap},
+      {(void**)&W.tr_hits, 4 * (size_t)ws->ncap},
+      {(void**)&W.scan_tmp, 4 * (size_t)ws->scan_cap},
+  };
+  size_t total = 0;
+  std::vector<size_t> offs;
+  for (auto& it : items) { offs.push_back(total); total = align_up(total + it.bytes, 256); }
+  ws->bytes = total;
+  cudaError_t e = cudaMalloc(&ws->block, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TPC_E_NOMEM, "workspace allocation of " + std::to_string(total) + " bytes failed");
+  }
+  for (size_t k = 0; k < items.size(); ++k) *items[k].ptr = (char*)ws->block + offs[k];
+  W.cnt = (DevCounters*)p_cnt;
+  ws->d_desc = (BatchDesc*)p_desc;
+  W.batch = ws->d_desc;
+  W.ncap = ws->ncap; W.scap = ws->scap; W.bcap = ws->bcap; W.tcap = ws->tcap; W.scan_tmp_cap = ws->scan_cap;
+  CK(cudaMallocHost(&ws->h_desc, sizeof(BatchDesc)));
+  CK(cudaMallocHost(&ws->h_cnt, sizeof(DevCounters)));
+  memset(ws->h_desc, 0, sizeof(BatchDesc));
+  memset(ws->h_cnt, 0, sizeof(DevCounters));
+  CK(cudaEventCreateWithFlags(&ws->done, cudaEventDisableTiming));
+  out = ws;
+  return TPC_OK;
+}
+
+int wait_ws(tpc_ctx* ctx, Workspace& ws, double timeout_s);
+void release_ws_user(tpc_ctx* ctx, Frame* f);
+
+// Workspace from the pool (a free one large enough), else a new one.
+int get_workspace(tpc_ctx* ctx, long long ntot, int nf, std::shared_ptr<Workspace>& out) {
+  const long long tneed = (long long)std::ceil((double)ntot * ctx->p.tracklet_capacity) + 1024;
+  for (auto& w : ctx->wspool)
+    if (!w->busy && w->users == 0 && w->ncap >= ntot && w->tcap >= tneed && w->nf_cap >= nf) {
+      out = w;
+      return TPC_OK;
+    }
+  // a busy workspace without result holders becomes free once its run ends: wait (bounded)
+  for (auto& w : ctx->wspool)
+    if (w->busy && w->users == 0 && w->ncap >= ntot && w->tcap >= tneed && w->nf_cap >= nf) {
+      int rc = wait_ws(ctx, *w, 120.0);
+      if (rc) return rc;
+      out = w;
+      return TPC_OK;
+    }
+  // drop idle workspaces that are too small
+  ctx->wspool.erase(std::remove_if(ctx->wspool.begin(), ctx->wspool.end(),
+                                   [](const std::shared_ptr<Workspace>& w) { return !w->busy && w->users == 0; }),
+                    ctx->wspool.end());
+  int nfc = std::max(nf, 1);
+  std::shared_ptr<Workspace> ws;
+  int rc = alloc_workspace(ctx, ntot + ntot / 8 + 1024, tneed + tneed / 8, nfc, ws);
+  if (rc) return rc;
+  ctx->wspool.push_back(ws);
+  out = ws;
+  return TPC_OK;
+}
+
+struct Launcher {
+  tpc_ctx* ctx;
+  cudaStream_t s;
+  bool timing;
+  int k = 0;
+  void begin(int idx) {
+    k = idx;
+    if (timing) cudaEventRecord(ctx->ev[idx], s);
+  }
+};
+
+// Enqueue the whole kernel sequence for the batch described in ws->h_desc (already uploaded).
+int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
+  Work W = ws.W;
+  const DevParams& Q = ctx->dp;
+  DevCounters* C = W.cnt;
+  const int G = ctx->sms;
+  int ki = 0;
+  auto mark = [&](int idx) {
+    if (timing) cudaEventRecord(ctx->ev[idx], s);
+  };
+  // scan lengths are device-side counts clamped to the buffer capacity n_cap
+  auto scan = [&](const uint32_t* in, uint32_t* out, const uint32_t* n_dev, long long n_host, uint32_t* total) {
+    k_scan_reduce<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp);
+    k_scan_tiles<<<1, 1024, 0, s>>>(W.scan_tmp, n_dev, n_host, 0, total);
+    k_scan_apply<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp, total, out);
+  };
+  mark(ki++);  // reset
+  k_reset_counters<<<1, 128, 0, s>>>(W);
+  k_zero_u32<<<G, 256, 0, s>>>(W.seg_cnt, &C->nseg, W.scap, 0, 1);
+  mark(ki++);  // seg_hist
+  k_seg_hist<<<4 * G, 256, 0, s>>>(W);
+  mark(ki++);  // seg_layout
+  k_seg_layout<<<G, 256, 0, s>>>(W, Q.occ);
+  mark(ki++);  // scan_seg
+  scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
+  mark(ki++);  // zero_bins
+  k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
+  mark(ki++);  // bin_rank
+  k_bin_rank<<<8 * G, 256, 0, s>>>(W);
+  mark(ki++);  // scan_bins
+  scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
+  mark(ki++);  // scatter
+  k_scatter<<<8 * G, 256, 0, s>>>(W);
+  mark(ki++);  // neighbours
+  k_neighbours<<<ctx->grid[8], 256, ctx->k2_smem, s>>>(W, Q);
+  mark(ki++);  // clean
+  k_clean<<<4 * G, 256, 0, s>>>(W, Q);
+  mark(ki++);  // scan_start
+  scan(W.seg_nstart, W.seg_nstart, &C->nseg, W.scap, &C->n_starts);
+  mark(ki++);  // starts
+  k_starts<<<4 * G, 256, 0, s>>>(W, Q);
+  k_set_ntracklets<<<1, 32, 0, s>>>(W);
+  mark(ki++);  // start_order
+  k_start_order<<<2 * G, 256, 0, s>>>(W);
+  mark(ki++);  // tracklets
+  k_tracklets<<<ctx->grid[13], 128, 0, s>>>(W, Q);
+  mark(ki++);  // zero_w
+  k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
+  mark(ki++);  // votes
+  k_votes<<<4 * G, 256, 0, s>>>(W, Q);
+  mark(ki++);  // kept
+  k_kept<<<4 * G, 256, 0, s>>>(W, Q);
+  mark(ki++);  // scan_kept
+  scan(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks);
+  scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
+  mark(ki++);  // write_tracks
+  k_write_tracks<<<4 * G, 256, 0, s>>>(W, Q);
+  mark(ki++);  // frame_off
+  k_frame_offsets<<<1, 128, 0, s>>>(W);
+  if (timing) cudaEventRecord(ctx->ev[kNumKernels], s);
+  cudaMemcpyAsync(ws.h_cnt, W.cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  return TPC_OK;
+}
+
+int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::shared_ptr<Workspace>& ws_out) {
+  // The same batch tracked again on the same workspace (e.g. a frame re-tracked in a loop): the
+  // descriptor in device memory is already right and the stream orders the runs.
+  {
+    std::shared_ptr<Workspace> same = fr[0]->ws;
+    bool reuse = same && same->batch_ids.size() == fr.size();
+    for (size_t k = 0; reuse && k < fr.size(); ++k) reuse = fr[k]->ws == same && same->batch_ids[k] == fr[k]->id;
+    if (reuse) {
+      same->busy = true;
+      int rc = TPC_OK;
+      if (ctx->p.use_graphs && !ctx->timing && same->graph) CK(cudaGraphLaunch(same->graph, s));
+      else rc = enqueue_sequence(ctx, *same, s, ctx->timing);
+      if (rc) return rc;
+      CK(cudaEventRecord(same->done, s));
+      for (Frame* f : fr) f->state = 3;
+      ws_out = same;
+      return TPC_OK;
+    }
+  }
+  for (Frame* f : fr) release_ws_user(ctx, f);
+  long long ntot = 0;
+  for (auto* f : fr) ntot += f->n;
+  std::shared_ptr<Workspace> ws;
+  int rc = get_workspace(ctx, ntot, (int)fr.size(), ws);
+  if (rc) return rc;
+  ws->batch_ids.clear();
+  for (auto* f : fr) ws->batch_ids.push_back(f->id);
+  BatchDesc* d = ws->h_desc;
+  memset(d, 0, sizeof(BatchDesc));
+  d->nf = (int)fr.size();
+  long long off = 0;
+  for (size_t k = 0; k < fr.size(); ++k) {
+    FrameIn& fi = d->f[k];
+    fi.sector = fr[k]->d_sector; fi.row = fr[k]->d_row; fi.y = fr[k]->d_y; fi.w = fr[k]->d_w;
+    fi.n = fr[k]->n; fi.off = off;
+    off += fr[k]->n;
+  }
+  d->ntot = ntot;
+  ws->busy = true;
+  CK(cudaMemcpyAsync(ws->d_desc, d, sizeof(BatchDesc), cudaMemcpyHostToDevice, s));
+  const bool timing = ctx->timing;
+  if (ctx->p.use_graphs && !timing) {
+    // one graph per workspace; its kernels read every size from the descriptor in device memory
+    if (!ws->graph) {
+      cudaStream_t cs = s;
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_sequence(ctx, *ws, cs, false);
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (rc) return rc;
+      if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ws->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(ws->graph, s));
+  } else {
+    rc = enqueue_sequence(ctx, *ws, s, timing);
+    if (rc) return rc;
+  }
+  CK(cudaEventRecord(ws->done, s));
+  for (size_t k = 0; k < fr.size(); ++k) {
+    fr[k]->ws = ws;
+    fr[k]->fidx = (int)k;
+    fr[k]->state = 3;
+    ws->users++;
+  }
+  ws_out = ws;
+  return TPC_OK;
+}
+
+// bounded wait for a workspace's run; collects the kernel times when timing is on
+int wait_ws(tpc_ctx* ctx, Workspace& ws, double timeout_s) {
+  const double t0 = now_s();
+  for (;;) {
+    cudaError_t e = cudaEventQuery(ws.done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(ctx, TPC_E_CUDA, std::string("device: ") + cudaGetErrorString(e));
+    if (now_s() - t0 > timeout_s) return fail(ctx, TPC_E_TIMEOUT, "tracking did not complete in time");
+    std::this_thread::yield();
+  }
+  ws.busy = false;
+  if (ctx->timing) {
+    for (int k = 0; k < kNumKernels; ++k) {
+      float m = 0;
+      if (cudaEventElapsedTime(&m, ctx->ev[k], ctx->ev[k + 1]) == cudaSuccess) {
+        ctx->ms[k] = m;
+        ctx->launches[k] = 1;
+      }
+    }
+  }
+  return TPC_OK;
+}
+
+int check_ws_errors(tpc_ctx* ctx, const Workspace& ws) {
+  const DevCounters& c = *ws.h_cnt;
+  if (c.err & kErrInput) return fail(ctx, TPC_E_INVAL, "malformed cluster (sector >= 36, row >= 152 or non-finite y/w)");
+  if (c.err & kErrTimeout) return fail(ctx, TPC_E_TIMEOUT, "a bounded shared-memory copy wait expired");
+  if (c.err & (kErrBins | kErrTracks)) return fail(ctx, TPC_E_CAPACITY, "grid or output capacity exceeded");
+  return TPC_OK;
+}
+
+Frame* find_frame(tpc_ctx* ctx, tpc_frame_t h) {
+  auto it = ctx->frames.find(h);
+  return it == ctx->frames.end() ? nullptr : it->second.get();
+}
+
+int fetch_results(tpc_ctx* ctx, Frame* f) {
+  Workspace& ws = *f->ws;
+  const DevCounters& c = *ws.h_cnt;
+  const int k = f->fidx;
+  const uint32_t t0 = c.frame_track0[k], t1 = c.frame_track0[k + 1];
+  const uint32_t h0 = c.frame_hit0[k], h1 = c.frame_hit0[k + 1];
+  const size_t nt = t1 - t0, nh = h1 - h0;
+  std::vector<float> trf(nt * 24);
+  std::vector<int4> tri(nt);
+  f->hits.resize(nh);
+  if (nt) {
+    CK(cudaMemcpyAsync(trf.data(), ws.W.tr_f + (size_t)t0 * 24, nt * 96, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(tri.data(), ws.W.tr_i + t0, nt * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (nh) CK(cudaMemcpyAsync(f->hits.data(), ws.W.tr_hits + h0, nh * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  f->sector.resize(nt); f->ndf.resize(nt); f->xref.resize(nt); f->chi2.resize(nt);
+  f->param.resize(nt * 5); f->cov.resize(nt * 15); f->hoff.resize(nt + 1);
+  for (size_t i = 0; i < nt; ++i) {
+    const float* s = &trf[i * 24];
+    for (int j = 0; j < 5; ++j) f->param[i * 5 + j] = s[j];
+    for (int j = 0; j < 15; ++j) f->cov[i * 15 + j] = s[5 + j];
+    f->chi2[i] = s[20];
+    f->xref[i] = s[21];
+    f->sector[i] = tri[i].x;
+    f->ndf[i] = tri[i].y;
+    f->hoff[i] = (int64_t)((uint32_t)tri[i].w - h0);
+  }
+  f->hoff[nt] = (int64_t)nh;
+  f->state = 5;
+  return TPC_OK;
+}
+
+void release_ws_user(tpc_ctx* ctx, Frame* f) {
+  if (f->ws) {
+    f->ws->users--;
+    f->ws.reset();
+  }
+  (void)ctx;
+}
+
+int load_frame(tpc_ctx* ctx, const tpc_clusters* cl, Frame*& out) {
+  if (!cl || cl->n < 0 || cl->n >= (1LL << 31)) return fail(ctx, TPC_E_INVAL, "bad cluster descriptor");
+  if (cl->n > 0 && (!cl->sector || !cl->row || !cl->y || !cl->w)) return fail(ctx, TPC_E_INVAL, "null cluster array");
+  auto f = std::make_unique<Frame>();
+  f->n = cl->n;
+  if (cl->on_device) {
+    f->d_sector = (uint8_t*)cl->sector; f->d_row = (uint8_t*)cl->row;
+    f->d_y = (float*)cl->y; f->d_w = (float*)cl->w;
+  } else {
+    const size_t n = (size_t)cl->n;
+    const size_t o1 = align_up(n, 256), o2 = o1 + align_up(n, 256), o3 = o2 + align_up(4 * n, 256);
+    const size_t bytes = o3 + align_up(4 * n, 256) + 256;
+    cudaError_t e = cudaMallocFromPoolAsync(&f->d_block, bytes, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, TPC_E_NOMEM, "input allocation failed"); }
+    char* b = (char*)f->d_block;
+    f->d_sector = (uint8_t*)b; f->d_row = (uint8_t*)(b + o1); f->d_y = (float*)(b + o2); f->d_w = (float*)(b + o3);
+    if (n) {
+      CK(cudaMemcpyAsync(f->d_sector, cl->sector, n, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(f->d_row, cl->row, n, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(f->d_y, cl->y, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync(f->d_w, cl->w, 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+    }
+  }
+  f->id = ctx->next_id++;
+  out = f.get();
+  ctx->frames[f->id] = std::move(f);
+  return TPC_OK;
+}
+
+void drop_frame(tpc_ctx* ctx, Frame* f) {
+  if (f->d_block) cudaFreeAsync(f->d_block, ctx->stream);
+  release_ws_user(ctx, f);
+  ctx->frames.erase(f->id);
+}
+
+size_t frame_budget_bytes(const tpc_ctx* ctx, long long n) {
+  // input 10 B + grid/links/weights/output ~46 B per cluster, tracklets ~860 B per slot
+  return (size_t)n * (10 + 46) + (size_t)(n * ctx->p.tracklet_capacity * 860.0) + ((size_t)1 << 20);
+}
+
+}  // namespace
+
+// ============================================================================== C-ABI
+extern "C" {
+
+void tpc_default_params(tpc_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(tpc_params);
+  p->bz = 0.5;
+  p->ky = 2.0; p->kw = 2.4; p->eps = 0.5;
+  p->chi_n_max = 0.2;
+  p->lmin = 3;
+  p->sigma_y = 0.1; p->sigma_w = 0.1;
+  p->chi2_hit_max = 16.0;
+  p->n_miss_max = 5;
+  p->win_nsig = 3.0; p->win_add = 0.3;
+  p->x0_per_row = 0.03 / 152.0;
+  p->max_sin = 0.999;
+  p->y_margin = 1.0;
+  p->nmin = 10;
+  p->cov0[0] = 1.0; p->cov0[1] = 1.0; p->cov0[2] = 1.0; p->cov0[3] = 1.0; p->cov0[4] = 100.0;
+  p->packed = 0;
+  p->bin_occupancy = 2.0f;
+  p->tracklet_capacity = 0.08f;
+  p->hbm_budget = 80LL << 30;
+  p->max_batch_frames = 16;
+  p->use_graphs = 1;
+  p->k5_block = 128;
+  p->k2_block = 256;
+}
+
+const char* tpc_version(void) { return "tpctrack 0.1 (sm_103a)"; }
+
+int tpc_create(const tpc_params* p, tpc_ctx** out) {
+  if (!out) return TPC_E_INVAL;
+  *out = nullptr;
+  tpc_ctx* ctx = new tpc_ctx();
+  if (p) {
+    if (p->struct_size != sizeof(tpc_params)) { delete ctx; return TPC_E_INVAL; }
+    ctx->p = *p;
+  } else {
+    tpc_default_params(&ctx->p);
+  }
+  if (ctx->p.nmin < 1 || ctx->p.lmin < 3 || ctx->p.n_miss_max < 1 || !(ctx->p.tracklet_capacity > 0) ||
+      ctx->p.max_batch_frames < 1 || ctx->p.max_batch_frames > kMaxFrames) {
+    delete ctx;
+    return TPC_E_INVAL;
+  }
+  make_dev_params(ctx->p, ctx->dp);
+  int rc = TPC_OK;
+  do {
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "no CUDA device"); break; }
+    e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "device query failed"); break; }
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = TPC_E_CUDA; break; }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "memory pool"); break; }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    for (int k = 0; k <= kNumKernels; ++k) cudaEventCreate(&ctx->ev[k]);
+    cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming);
+    ctx->k2_smem = (2 * (kK2Stage + 2)) * (int)sizeof(float2);
+    cudaFuncSetAttribute(k_neighbours, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->k2_smem);
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours, 256, ctx->k2_smem);
+    ctx->grid[8] = ctx->sms * std::max(nb, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets, 128, 0);
+    ctx->grid[13] = ctx->sms * std::max(nb, 1);
+    for (int k = 0; k < 2; ++k) {
+      cudaStream_t s;
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      ctx->serve_streams.push_back(s);
+    }
+    if (cudaGetLastError() != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "context setup failed"); break; }
+  } while (0);
+  if (rc) { tpc_destroy(ctx); return rc; }
+  *out = ctx;
+  return TPC_OK;
+}
+
+void tpc_destroy(tpc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto s : ctx->serve_streams) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  for (auto& kv : ctx->frames)
+    if (kv.second->d_block) cudaFreeAsync(kv.second->d_block, ctx->stream);
+  ctx->frames.clear();
+  ctx->inflight.clear();
+  ctx->wspool.clear();
+  if (ctx->stream) { cudaStreamSynchronize(ctx->stream); cudaStreamDestroy(ctx->stream); }
+  for (int k = 0; k <= kNumKernels; ++k)
+    if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+  if (ctx->ev_sync) cudaEventDestroy(ctx->ev_sync);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+}
+
+const char* tpc_last_error(const tpc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* out) {
+  if (!ctx || !out) return TPC_E_INVAL;
+  Frame* f = nullptr;
+  int rc = load_frame(ctx, clusters, f);
+  if (rc) return rc;
+  *out = f->id;
+  return TPC_OK;
+}
+
+int tpc_track_batch(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, void* cuda_stream) {
+  if (!ctx || !frames || n_frames < 1 || n_frames > kMaxFrames) return fail(ctx, TPC_E_INVAL, "bad frame list");
+  std::vector<Frame*> fr;
+  for (int k = 0; k < n_frames; ++k) {
+    Frame* f = find_frame(ctx, frames[k]);
+    if (!f) return fail(ctx, TPC_E_INVAL, "unknown frame handle");
+    if (f->state == 1 || f->state == 2) return fail(ctx, TPC_E_STATE, "frame is queued for serving");
+    for (Frame* g : fr)
+      if (g == f) return fail(ctx, TPC_E_INVAL, "frame listed twice");
+    fr.push_back(f);
+  }
+  // The kernels run on the context's stream (graph capture needs a non-default stream); work the
+  // caller queued on its own stream (e.g. producing borrowed device inputs) is waited for first,
+  // and the caller's stream waits for the tracking.
+  cudaStream_t user = (cudaStream_t)cuda_stream;
+  if (user) {
+    CK(cudaEventRecord(ctx->ev_sync, user));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_sync, 0));
+  }
+  std::shared_ptr<Workspace> ws;
+  int rc = run_batch(ctx, fr, ctx->stream, ws);
+  if (rc) return rc;
+  if (user) CK(cudaStreamWaitEvent(user, ws->done, 0));
+  return TPC_OK;
+}
+
+int tpc_track_sectors(tpc_ctx* ctx, tpc_frame_t frame, void* cuda_stream) {
+  return tpc_track_batch(ctx, &frame, 1, cuda_stream);
+}
+
+int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out) {
+  if (!ctx || !out) return TPC_E_INVAL;
+  Frame* f = find_frame(ctx, frame);
+  if (!f) return fail(ctx, TPC_E_INVAL, "unknown frame handle");
+  if (f->state < 3) return fail(ctx, TPC_E_STATE, "frame has not been tracked");
+  if (f->state < 5) {
+    int rc = wait_ws(ctx, *f->ws, 120.0);
+    if (rc) return rc;
+    rc = check_ws_errors(ctx, *f->ws);
+    if (rc) return rc;
+    if (f->ws->h_cnt->n_starts > (uint32_t)f->ws->tcap) {
+      // tracklet capacity overflow: track this frame again alone with room for every start hit
+      const float old = ctx->p.tracklet_capacity;
+      ctx->p.tracklet_capacity = std::max(old, 1.25f * (float)f->ws->h_cnt->n_starts / (float)std::max(1LL, f->n));
+      release_ws_user(ctx, f);
+      f->ws.reset();
+      std::vector<Frame*> one{f};
+      std::shared_ptr<Workspace> ws;
+      rc = run_batch(ctx, one, ctx->stream, ws);
+      ctx->p.tracklet_capacity = old;
+      if (rc) return rc;
+      rc = wait_ws(ctx, *f->ws, 120.0);
+      if (rc) return rc;
+      rc = check_ws_errors(ctx, *f->ws);
+      if (rc) return rc;
+      if (f->ws->h_cnt->n_starts > (uint32_t)f->ws->tcap) return fail(ctx, TPC_E_CAPACITY, "tracklet capacity");
+    }
+    rc = fetch_results(ctx, f);
+    if (rc) return rc;
+  }
+  out->n_tracks = (int64_t)f->sector.size();
+  out->sector = f->sector.data();
+  out->x_ref = f->xref.data();
+  out->param = f->param.data();
+  out->cov = f->cov.data();
+  out->chi2 = f->chi2.data();
+  out->ndf = f->ndf.data();
+  out->hit_offset = f->hoff.data();
+  out->hit_index = f->hits.data();
+  return TPC_OK;
+}
+
+int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n_tracks) {
+  if (!ctx) return TPC_E_INVAL;
+  Frame* f = find_frame(ctx, frame);
+  if (!f || !f->ws) return fail(ctx, TPC_E_STATE, "frame has no tracking results");
+  int rc = wait_ws(ctx, *f->ws, 120.0);
+  if (rc) return rc;
+  const DevCounters& c = *f->ws->h_cnt;
+  if (n_start) *n_start = (int64_t)(c.frame_start0[f->fidx + 1] - c.frame_start0[f->fidx]);
+  if (n_tracks) *n_tracks = (int64_t)(c.frame_track0[f->fidx + 1] - c.frame_track0[f->fidx]);
+  return TPC_OK;
+}
+
+int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n) {
+  if (!ctx || !host_out || what < 0 || what > 3) return TPC_E_INVAL;
+  Frame* f = find_frame(ctx, frame);
+  if (!f || !f->ws) return fail(ctx, TPC_E_STATE, "frame has no tracking results");
+  if (n != f->n) return fail(ctx, TPC_E_INVAL, "length mismatch");
+  int rc = wait_ws(ctx, *f->ws, 120.0);
+  if (rc) return rc;
+  int32_t* d = nullptr;
+  CK(cudaMallocAsync((void**)&d, 4 * (size_t)std::max<int64_t>(n, 1), ctx->stream));
+  CK(cudaMemsetAsync(d, 0xFF, 4 * (size_t)std::max<int64_t>(n, 1), ctx->stream));
+  k_links_to_input<<<ctx->sms * 2, 256, 0, ctx->stream>>>(f->ws->W, f->fidx, what, d);
+  CK(cudaMemcpyAsync(host_out, d, 4 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaFreeAsync(d, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TPC_OK;
+}
+
+int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame) {
+  if (!ctx) return TPC_E_INVAL;
+  Frame* f = find_frame(ctx, frame);
+  if (!f) return fail(ctx, TPC_E_INVAL, "unknown frame handle");
+  if (f->state == 3 && f->ws) {
+    int rc = wait_ws(ctx, *f->ws, 120.0);
+    if (rc) return rc;
+  }
+  if (f->state == 1) {
+    auto it = std::find(ctx->queue.begin(), ctx->queue.end(), frame);
+    if (it != ctx->queue.end()) ctx->queue.erase(it);
+  }
+  if (f->budget_bytes) {
+    ctx->budget_used -= std::min(ctx->budget_used, f->budget_bytes);
+    f->budget_bytes = 0;
+  }
+  drop_frame(ctx, f);
+  return TPC_OK;
+}
+
+// ------------------------------------------------------------------------------ serving
+int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ticket) {
+  if (!ctx || !ticket || !clusters) return TPC_E_INVAL;
+  const size_t need = frame_budget_bytes(ctx, clusters->n);
+  if ((long long)need > ctx->p.hbm_budget) return fail(ctx, TPC_E_BUDGET, "frame larger than the HBM budget");
+  Frame* f = nullptr;
+  int rc = load_frame(ctx, clusters, f);
+  if (rc) return rc;
+  f->state = 1;
+  f->t_submit = now_s();
+  f->budget_bytes = 0;
+  ctx->queue.push_back(f->id);
+  *ticket = f->id;
+  return TPC_OK;
+}
+
+namespace {
+int serve_step(tpc_ctx* ctx) {
+  // retire finished batches
+  for (size_t k = 0; k < ctx->inflight.size();) {
+    auto& b = ctx->inflight[k];
+    cudaError_t e = cudaEventQuery(b.ws->done);
+    if (e == cudaErrorNotReady) { ++k; continue; }
+    if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("device: ") + cudaGetErrorString(e));
+    b.ws->busy = false;
+    const double t = now_s();
+    for (auto id : b.frames) {
+      Frame* f = find_frame(ctx, id);
+      if (!f) continue;
+      f->state = 4;
+      f->t_done = t;
+      ctx->finished.push_back(id);
+    }
+    ctx->inflight.erase(ctx->inflight.begin() + (long)k);
+  }
+  // launch a new batch of admitted frames into a free stream slot
+  while (ctx->inflight.size() < ctx->serve_streams.size() && !ctx->queue.empty()) {
+    std::vector<Frame*> batch;
+    std::vector<tpc_frame_t> ids;
+    while (!ctx->queue.empty() && (int)batch.size() < ctx->p.max_batch_frames) {
+      Frame* f = find_frame(ctx, ctx->queue.front());
+      if (!f) { ctx->queue.pop_front(); continue; }
+      const size_t need = frame_budget_bytes(ctx, f->n);
+      if (ctx->budget_used + need > (size_t)ctx->p.hbm_budget) break;  // wait for memory to free up
+      ctx->budget_used += need;
+      f->budget_bytes = need;
+      f->state = 2;
+      batch.push_back(f);
+      ids.push_back(f->id);
+      ctx->queue.pop_front();
+    }
+    if (batch.empty()) break;
+    cudaStream_t s = nullptr;
+    for (auto cand : ctx->serve_streams) {
+      bool used = false;
+      for (auto& b : ctx->inflight) used |= b.stream == cand;
+      if (!used) { s = cand; break; }
+    }
+    // inputs were uploaded on the context stream
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaEventRecord(e, ctx->stream));
+    CK(cudaStreamWaitEvent(s, e, 0));
+    cudaEventDestroy(e);
+    std::shared_ptr<Workspace> ws;
+    int rc = run_batch(ctx, batch, s, ws);
+    if (rc) return rc;
+    ctx->inflight.push_back({ws, ids, s});
+  }
+  return TPC_OK;
+}
+}  // namespace
+
+int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_us) {
+  if (!ctx || (max_done > 0 && !done) || max_done < 0) return TPC_E_INVAL;
+  const double t0 = now_s();
+  for (;;) {
+    int rc = serve_step(ctx);
+    if (rc) return rc;
+    if (!ctx->finished.empty() || (ctx->inflight.empty() && ctx->queue.empty())) break;
+    if ((now_s() - t0) * 1e6 >= timeout_us) break;
+    std::this_thread::yield();
+  }
+  int k = 0;
+  while (k < max_done && !ctx->finished.empty()) {
+    done[k++] = ctx->finished.front();
+    ctx->finished.pop_front();
+  }
+  return k;
+}
+
+int tpc_set_timing(tpc_ctx* ctx, int32_t enable) {
+  if (!ctx) return TPC_E_INVAL;
+  ctx->timing = enable != 0;
+  return TPC_OK;
+}
+
+int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out) {
+  if (!ctx || !out) return TPC_E_INVAL;
+  out->n_kernels = kNumKernels;
+  out->names = kKernelNames;
+  out->ms = ctx->ms;
+  out->launches = ctx->launches;
+  return TPC_OK;
+}
+
+}  // extern "C"

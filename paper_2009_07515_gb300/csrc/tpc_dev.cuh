@@ -1,0 +1,358 @@
+// tpc_dev.cuh — device-side definitions shared by the tracking kernels (sm_103a).
+//
+// Layout of one batch in HBM (all frames of a batch share one workspace; every array is indexed by
+// a batch-global "sorted position" p of a cluster after the grid build):
+//   hyw[p]      float2 (y, w) of the cluster at sorted position p (FP32 storage)
+//   horig[p]    uint32 index of the cluster in its frame's input arrays
+//   segments    g = frame*5472 + sector*152 + row; seg_bb[g] = first bin, seg_nb[g] bins,
+//               seg_geo[g] = (w_lo, bins per cm) of the segment's 1-D grid in the drift coordinate w
+//   bin_start[b] sorted position of the first cluster of bin b (exclusive prefix over all bins), so a
+//               window [w0, w1] of a row is one contiguous position range
+//   links[p]    int2 (down, up) raw neighbour links; clinks[p] the cleaned (reciprocal) links
+//   starts[t]   start hits in canonical order (frame, sector, row-rank)
+//   slab[r*tcap + t]  sorted position of tracklet t's hit in row r (0xFFFFFFFF: none), written for
+//               rows [ref_row, top_row]
+//
+// The Kalman arithmetic below is written so that every float result is the same sequence of
+// correctly rounded operations as the method's plain definition (compiled with -fmad=false, IEEE
+// division and square root): products with exact zeros and ones of the Jacobian and of I - KH are
+// skipped, the remaining terms are summed in the same order.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tpc {
+
+constexpr int kNSec = 36;
+constexpr int kNRow = 152;
+constexpr int kSegPerFrame = kNSec * kNRow;  // 5472
+constexpr int kMaxFrames = 64;               // frames per batched launch
+constexpr uint32_t kNoHit = 0xFFFFFFFFu;
+
+// error bits (device error word)
+constexpr uint32_t kErrInput = 1u;      // malformed cluster (sector/row range, non-finite)
+constexpr uint32_t kErrTracklets = 2u;  // tracklet capacity exceeded
+constexpr uint32_t kErrBins = 4u;       // bin capacity exceeded
+constexpr uint32_t kErrTimeout = 8u;    // bounded mbarrier wait expired
+constexpr uint32_t kErrTracks = 16u;    // output hit capacity exceeded
+
+struct DevParams {
+  float kq;                      // d(curvature)/d(q/pT)
+  float chi_n_max;
+  int lmin;
+  float r00, r11;                // measurement variances
+  float chi2_max;
+  int n_miss_max;
+  float win_nsig, win_add;
+  int ms_on;
+  float x0_row, ms_c, mass2;
+  float max_sin, y_margin, tan10;
+  int nmin;
+  float cov0[5];
+  float occ;                     // target clusters per w bin
+  float x[kNRow];                // row radii
+  // neighbour windows per row r (valid for 1 <= r <= 150)
+  float wy_dn[kNRow], ww_dn[kNRow], wy_up[kNRow], ww_up[kNRow], f_mid[kNRow];
+};
+
+struct FrameIn {
+  const uint8_t* sector;
+  const uint8_t* row;
+  const float* y;
+  const float* w;
+  long long n;
+  long long off;  // first batch-global input index of this frame
+};
+
+struct BatchDesc {
+  int nf;
+  int pad_;
+  long long ntot;
+  FrameIn f[kMaxFrames];
+};
+
+// Counters and per-batch scalars in device memory (zeroed at the start of each run).
+struct DevCounters {
+  uint32_t nseg;          // frames * 5472 (from the batch descriptor)
+  uint32_t ntot;          // clusters of the batch
+  uint32_t err;
+  uint32_t n_starts;      // start hits found (may exceed tcap: overflow)
+  uint32_t n_tracklets;   // min(n_starts, tcap)
+  uint32_t k5_next;       // work counter of the tracklet kernel
+  uint32_t n_bins;        // total bins of the batch
+  uint32_t n_sorted;      // clusters placed in the grid
+  uint32_t n_tracks;
+  uint32_t n_track_hits;
+  uint32_t wrange[2 * kMaxFrames];  // per frame (min, max) of w, order-preserving encoding
+  uint32_t frame_start0[kMaxFrames + 1];  // first start index of each frame
+  uint32_t frame_track0[kMaxFrames + 1];  // first track index of each frame
+  uint32_t frame_hit0[kMaxFrames + 1];    // first output hit of each frame
+};
+
+// Workspace pointers (device arrays), sized by capacities.
+struct Work {
+  DevCounters* cnt;
+  const BatchDesc* batch;
+  // grid
+  uint32_t* seg_cnt;     // [scap]
+  uint32_t* seg_nb;      // [scap]  -> scanned in place into seg_bb
+  uint32_t* seg_bb;      // [scap + 1]
+  float2* seg_geo;       // [scap]
+  uint32_t* bin_start;   // [bcap + 1]
+  uint32_t* rank;        // [ncap]
+  float2* hyw;           // [ncap + 2]
+  uint32_t* horig;       // [ncap]
+  // links
+  int2* links;           // [ncap]
+  int2* clinks;          // [ncap]
+  uint32_t* seg_nstart;  // [scap + 1] -> scanned
+  uint4* starts_raw;     // [tcap] (hit, seg, bin, -)
+  uint4* starts;         // [tcap] (hit, seg, rank-in-sector, -)
+  // tracklets
+  float* tl_state;       // [tcap][24]: P[5], C[15], chi2, x_ref, -, -
+  uint32_t* tl_info;     // [tcap]: nhits | ref_row << 8 | top_row << 16 | ok << 24
+  uint32_t* slab;        // [kNRow][tcap]
+  unsigned long long* hit_w;  // [ncap]
+  uint32_t* tl_kept;     // [tcap + 1] -> scanned (track index)
+  uint32_t* tl_nkept;    // [tcap + 1] -> scanned (hit offset)
+  // tracks
+  float* tr_f;           // [tcap][24] track fit: P[5], C[15], chi2, x_ref
+  int4* tr_i;            // [tcap] (sector, ndf, kept hits, first output hit)
+  uint32_t* tr_hits;     // [ncap] output hits (frame-local input indices)
+  // scan scratch
+  uint32_t* scan_tmp;    // [scan_tmp_cap]
+  long long ncap, scap, bcap, tcap, scan_tmp_cap;
+};
+
+// ------------------------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// bin of w in a segment grid with nb bins starting at wlo, inv bins per cm (monotone in w)
+__device__ __forceinline__ int bin_of(float w, float wlo, float inv, int nb) {
+  float t = (w - wlo) * inv;
+  if (!(t > 0.f)) return 0;
+  if (t >= (float)nb) return nb - 1;
+  return (int)t;
+}
+
+// conservative widening of a window for the bin lookup (rounding of w +- W)
+__device__ __forceinline__ float win_pad(float wc, float W) {
+  return fabsf(wc) * 1.0e-6f + W * 1.0e-6f + 1.0e-6f;
+}
+
+// row-order key comparison: (w, y, input index) lexicographic
+__device__ __forceinline__ bool key_less(float wa, float ya, uint32_t oa, float wb, float yb, uint32_t ob) {
+  if (wa < wb) return true;
+  if (wa > wb) return false;
+  if (ya < yb) return true;
+  if (ya > yb) return false;
+  return oa < ob;
+}
+
+__device__ __forceinline__ int frame_of(const BatchDesc* B, long long i) {
+  int lo = 0, hi = B->nf - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (B->f[mid].off <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------------------------ KF math
+// asin(t): half-angle reduction t -> t / sqrt(2 (1 + sqrt(1 - t^2))) until |t| < 0.1, then the
+// Maclaurin series of asin(t)/t to t^10 (only correctly rounded operations, no library call)
+__device__ __forceinline__ float asin_series_ratio(float t) {
+  const float t2 = t * t;
+  return 1.0f + t2 * ((float)0.16666666666666666 +
+                      t2 * ((float)0.075 +
+                            t2 * ((float)0.044642857142857144 +
+                                  t2 * ((float)0.030381944444444444 +
+                                        t2 * (float)0.022372159090909092))));
+}
+__device__ __forceinline__ float asin_hr(float t) {
+  float scale = 1.0f;
+  for (int it = 0; it < 40 && fabsf(t) >= (float)0.1; ++it) {
+    t = t / sqrtf(2.0f * (1.0f + sqrtf(1.0f - t * t)));
+    scale = scale * 2.0f;
+  }
+  return scale * t * asin_series_ratio(t);
+}
+__device__ __forceinline__ float arc_ratio(float t) {
+  if (fabsf(t) < (float)0.1) return asin_series_ratio(t);
+  return asin_hr(t) / t;
+}
+__device__ __forceinline__ float arc_ratio_deriv(float t) {
+  if (fabsf(t) < (float)0.1) {
+    const float t2 = t * t;
+    return t * ((float)0.3333333333333333 +
+                t2 * ((float)0.3 +
+                      t2 * ((float)0.26785714285714285 +
+                            t2 * ((float)0.24305555555555555 + t2 * (float)0.22372159090909091))));
+  }
+  return (1.0f / sqrtf(1.0f - t * t) - arc_ratio(t)) / t;
+}
+
+// lower-triangular packed covariance index
+__host__ __device__ constexpr int lt(int i, int k) { return i >= k ? i * (i + 1) / 2 + k : k * (k + 1) / 2 + i; }
+
+// Exact helix transport with scattering noise. Returns false if |sin(phi)| would reach max_sin.
+__device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float* C, float x0, float x1) {
+  const float dx = x1 - x0;
+  const float k = Q.kq * P[4];
+  const float s0 = P[2];
+  const float s1 = s0 + k * dx;
+  if (!(fabsf(s1) < Q.max_sin)) return false;
+  const float c0 = sqrtf(1.0f - s0 * s0);
+  const float c1 = sqrtf(1.0f - s1 * s1);
+  const float N = s0 + s1, D = c0 + c1;
+  const float dy = dx * (N / D);
+  const float l = sqrtf(dx * dx + dy * dy);
+  const float t = l * k * 0.5f;
+  float a = l * arc_ratio(t);
+  if (dx < 0.f) a = -a;
+  const float tw = P[3];
+  const float DD = D * D;
+  const float dy_ds0 = dx * (2.0f / D + N * (s0 / c0 + s1 / c1) / DD);
+  const float dy_dk = dx * dx * (1.0f / D + N * s1 / (c1 * DD));
+  float da_dl = 1.0f / sqrtf(1.0f - t * t);
+  float da_dk = l * l * 0.5f * arc_ratio_deriv(t);
+  if (dx < 0.f) { da_dl = -da_dl; da_dk = -da_dk; }
+  const float dl_ds0 = dy * dy_ds0 / l;
+  const float dl_dk = dy * dy_dk / l;
+  const float J02 = dy_ds0;
+  const float J04 = dy_dk * Q.kq;
+  const float J12 = tw * (da_dl * dl_ds0);
+  const float J13 = a;
+  const float J14 = tw * (da_dl * dl_dk + da_dk) * Q.kq;
+  const float J24 = dx * Q.kq;
+  P[0] = P[0] + dy;
+  P[1] = P[1] + tw * a;
+  P[2] = s1;
+  // T = J C
+  float T[5][5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    T[0][c] = (C[lt(0, c)] + J02 * C[lt(2, c)]) + J04 * C[lt(4, c)];
+    T[1][c] = ((C[lt(1, c)] + J12 * C[lt(2, c)]) + J13 * C[lt(3, c)]) + J14 * C[lt(4, c)];
+    T[2][c] = C[lt(2, c)] + J24 * C[lt(4, c)];
+    T[3][c] = C[lt(3, c)];
+    T[4][c] = C[lt(4, c)];
+  }
+  // O = T J^T (lower triangle)
+  float O[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    O[lt(i, 0)] = (T[i][0] + T[i][2] * J02) + T[i][4] * J04;
+    if (i >= 1) O[lt(i, 1)] = ((T[i][1] + T[i][2] * J12) + T[i][3] * J13) + T[i][4] * J14;
+    if (i >= 2) O[lt(i, 2)] = T[i][2] + T[i][4] * J24;
+    if (i >= 3) O[lt(i, 3)] = T[i][3];
+    if (i >= 4) O[lt(i, 4)] = T[i][4];
+  }
+  if (Q.ms_on && P[4] != 0.f) {
+    const float one_tw2 = 1.0f + tw * tw;
+    const float pathf = sqrtf(one_tw2) / c1;
+    const float xx0 = Q.x0_row * pathf;
+    const float p2 = one_tw2 / (P[4] * P[4]);
+    const float beta2 = p2 / (p2 + Q.mass2);
+    const float th2 = Q.ms_c * xx0 / (beta2 * p2);
+    O[lt(2, 2)] = O[lt(2, 2)] + th2 * (c1 * c1) * one_tw2;
+    O[lt(3, 3)] = O[lt(3, 3)] + th2 * one_tw2 * one_tw2;
+  }
+#pragma unroll
+  for (int i = 0; i < 15; ++i) C[i] = O[i];
+  return true;
+}
+
+__device__ __forceinline__ float kf_chi2(const DevParams& Q, const float* P, const float* C, float ym, float wm) {
+  const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
+  const float det = S00 * S11 - S01 * S10;
+  if (!(det > 0.f)) return __int_as_float(0x7f800000);
+  const float i00 = S11 / det, i01 = -S01 / det, i10 = -S10 / det, i11 = S00 / det;
+  const float r0 = ym - P[0], r1 = wm - P[1];
+  return r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
+}
+
+__device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C, float ym, float wm) {
+  const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
+  const float det = S00 * S11 - S01 * S10;
+  const float i00 = S11 / det, i01 = -S01 / det, i10 = -S10 / det, i11 = S00 / det;
+  float K[5][2];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float ci0 = C[lt(i, 0)], ci1 = C[lt(i, 1)];
+    K[i][0] = ci0 * i00 + ci1 * i10;
+    K[i][1] = ci0 * i01 + ci1 * i11;
+  }
+  const float r0 = ym - P[0], r1 = wm - P[1];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) P[i] = P[i] + (K[i][0] * r0 + K[i][1] * r1);
+  // A = I - K H: only the first two columns differ from the identity
+  float A[5][2];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    A[i][0] = (i == 0 ? 1.0f : 0.0f) - K[i][0];
+    A[i][1] = (i == 1 ? 1.0f : 0.0f) - K[i][1];
+  }
+  // T = A C: rows i, columns 0, 1 and (for i >= 2) the diagonal-block column k <= i
+  float T0[5], T1[5], Tk[15];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    T0[i] = A[i][0] * C[lt(0, 0)] + A[i][1] * C[lt(1, 0)];
+    T1[i] = A[i][0] * C[lt(0, 1)] + A[i][1] * C[lt(1, 1)];
+    if (i >= 2) {
+      T0[i] = T0[i] + C[lt(i, 0)];
+      T1[i] = T1[i] + C[lt(i, 1)];
+    }
+  }
+#pragma unroll
+  for (int i = 2; i < 5; ++i)
+#pragma unroll
+    for (int k = 2; k <= i; ++k) Tk[lt(i, k)] = (A[i][0] * C[lt(0, k)] + A[i][1] * C[lt(1, k)]) + C[lt(i, k)];
+  float KR[5][2];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    KR[i][0] = K[i][0] * Q.r00;
+    KR[i][1] = K[i][1] * Q.r11;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int k = 0; k <= i; ++k) {
+      float o = T0[i] * A[k][0] + T1[i] * A[k][1];
+      if (k >= 2) o = o + Tk[lt(i, k)];
+      C[lt(i, k)] = o + (KR[i][0] * K[k][0] + KR[i][1] * K[k][1]);
+    }
+}
+
+// Seed from the first, middle and last chain hits (x, y, w): circle through them in (x, y), state
+// at the first hit, dw/ds from the end points over the arc.
+__device__ __forceinline__ bool kf_seed(const DevParams& Q, const float h[3][3], float* P) {
+  const float ax = h[1][0] - h[0][0], ay = h[1][1] - h[0][1];
+  const float bx = h[2][0] - h[0][0], by = h[2][1] - h[0][1];
+  const float cx = h[2][0] - h[1][0], cy = h[2][1] - h[1][1];
+  const float cross = ax * by - ay * bx;
+  const float d01 = sqrtf(ax * ax + ay * ay);
+  const float d02 = sqrtf(bx * bx + by * by);
+  const float d12 = sqrtf(cx * cx + cy * cy);
+  const float k = 2.0f * cross / (d01 * d02 * d12);
+  const float sg = k * d02 * 0.5f;
+  if (!(fabsf(sg) < 1.0f)) return false;
+  const float cg = sqrtf(1.0f - sg * sg);
+  const float sphi = (by * cg - bx * sg) / d02;
+  if (!(fabsf(sphi) < Q.max_sin)) return false;
+  const float arc = d02 * arc_ratio(sg);
+  P[0] = h[0][1];
+  P[1] = h[0][2];
+  P[2] = sphi;
+  P[3] = (h[2][2] - h[0][2]) / arc;
+  P[4] = Q.kq != 0.f ? k / Q.kq : 0.0f;
+  return true;
+}
+
+}  // namespace tpc

@@ -362,7 +362,9 @@ def test_selection_invariants_and_canonical_order():
         assert 2 * len(h) >= res.tl_nhits[tl]
         assert set(h.tolist()) <= set(res.tracklet_hits(tl).tolist())
         mins.append((res.tr_sector[i], h.min()))
-    assert mins == sorted(mins)
+    # canonical order: sector, then rank of the start hit (ascending tracklet index in the sector)
+    key = [(res.tr_sector[i], res.tr_tracklet[i]) for i in range(res.n_tracks)]
+    assert key == sorted(key)
 
 
 def test_input_permutation_invariance():
