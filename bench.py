@@ -1,0 +1,306 @@
+"""Throughput benchmark of GB300 TPC sector tracking (clusters tracked per second).
+
+One step = one pass of the whole tracking path (grid, neighbours, cleaning, start hits, tracklet
+construction, selection, canonical output) over one synthetic time frame already resident in HBM.
+Default workload: the overlapping Pb-Pb-like frame of two central-like collisions of 10000
+primaries each (about 3 M clusters, FP32 storage). The L2 cache (129 MB) is flushed before each
+timed step by writing a 512 MB buffer; each step is timed with CUDA events on the stream the
+tracking runs on, and the flush lies outside the timed interval.
+
+Keys beyond the base contract:
+  e2e           the same metric through the C-ABI with host buffers: every step copies the frame's
+                clusters from pinned host memory, tracks, and reads the tracks back
+  roofline      the dominant kernel, algorithmic bytes per launch / its event-timed duration against
+                the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle (FP32) on the machine's host cores, on a bounded sample
+  kernels_ms    per-kernel device time of one step (CUDA events between launches)
+  --impl reference   times the CPU oracle as the reference arm (this method has no other code)
+Multi-GPU (torchrun): frames are independent, so every rank tracks its own replica of the
+workload on its own GPU with no collective in the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TPC clusters tracked/s"
+UNIT = "clusters/s"
+
+# Roofline accounting (derivations in the design doc):
+#  - memory-bound kernels: algorithmic bytes per cluster counted from the data layout, e.g. the
+#    neighbour search reads its row's (y, w) and the two adjacent rows once (3 x 8 B) and writes
+#    the links (8 B);
+#  - the tracklet kernel is bound by FP32 issue: algorithmic flops = row steps (device counter) x
+#    FLOPS_PER_STEP, the add/sub/mul/div/sqrt operations of one helix propagation with scattering
+#    noise, one chi2 and one Joseph-form update, counted from their definition; peak = 152 SMs x
+#    128 FP32 lanes x 2 flops (FMA) x the maximum SM clock.
+ALG_BYTES_PER_CLUSTER = {"neighbours": 32.0, "clean": 24.0, "seg_hist": 10.0, "bin_rank": 10.0,
+                         "scatter": 30.0, "starts": 12.0}
+FLOPS_PER_STEP = 480.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(np.max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline(frame, n_threads: int, budget_s: float = 20.0) -> dict:
+    """The FP32 oracle on the host cores over whole sectors of the frame (sectors are independent),
+    as many sectors as fit about `budget_s` seconds on `n_threads` threads."""
+    import oracle
+    sec = frame.sector
+    m1 = sec == 0
+    t0 = time.perf_counter()
+    oracle.track(sec[m1], frame.row[m1], frame.y[m1], frame.w[m1], precision="f32", n_threads=1)
+    per_sector = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(36, max(1, budget_s * n_threads / per_sector)))
+    m = sec < k
+    t0 = time.perf_counter()
+    oracle.track(sec[m], frame.row[m], frame.y[m], frame.w[m], precision="f32", n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    n = int(m.sum())
+    return {"value": n / dt, "unit": UNIT, "cores": int(n_threads), "kind": "oracle",
+            "sample": f"sectors 0-{k - 1} of the workload frame ({n} clusters), FP32 oracle, {dt:.2f} s"}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle, timed on the host cores, on bounded samples of the workload."""
+    if rank != 0:
+        return
+    import synth
+    frame = synth.generate(args.workload)
+    cores = os.cpu_count() or 1
+    budget = max(1.0, 60.0 / max(1, args.steps))
+    for _ in range(args.warmup):
+        cpu_baseline(frame, cores, budget_s=budget / 4)
+    times = []
+    for _ in range(args.steps):
+        times.append(cpu_baseline(frame, cores, budget_s=budget))
+    vals = [t["value"] for t in times]
+    value = float(np.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "parallelism": "host threads over sectors"},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": times[0]["sample"], "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="pbpb_2x10000")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    import paper_2009_07515_gb300 as tpc
+
+    frame = synth.generate(args.workload)
+    n = frame.n
+    tr = tpc.Tracker()
+    # inputs resident in HBM
+    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
+    h = tr.load(*d_in)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        tr.track(h, stream)
+    res = tr.tracks(h)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident, L2 flushed before each step)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            tr.track(h, stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    dev_ms = _max_over_ranks(dev_ms, ws)
+    ms_per_step = dev_ms / args.steps
+    value = n * ws * args.steps / (dev_ms / 1e3)
+    res = tr.tracks(h)
+
+    # ---- per-kernel times (eager launches with events between kernels)
+    tr.set_timing(True)
+    kt_runs = []
+    for _ in range(5):
+        flush.zero_()
+        tr.track(h)
+        tr.tracks(h)
+        kt_runs.append(tr.kernel_times())
+    tr.set_timing(False)
+    kernels = {k: float(np.median([r[k] for r in kt_runs])) for k in kt_runs[0]}
+    launches_per_step = int(sum(tr.kernel_times(launches=True).values()))
+    stats = tr.stats(h)
+    dominant = max(kernels, key=kernels.get)
+    hbm_peak, peak_src = _peaks()
+    if dominant == "tracklets":
+        flops = stats["steps"] * FLOPS_PER_STEP
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        achieved = flops / (kernels[dominant] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None, "peak_source": "derived (FP32 lanes x 2 x max SM clock)",
+                    "alg_flops_per_launch": flops, "row_steps": stats["steps"]}
+    else:
+        alg = ALG_BYTES_PER_CLUSTER.get(dominant, 32.0) * n
+        achieved = alg / (kernels[dominant] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                    "alg_bytes_per_launch": alg}
+
+    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
+    h2d = int(sum(p.numel() * p.element_size() for p in pin))
+    for _ in range(2):
+        tr.run(*[p.numpy() for p in pin])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        out = tr.run(*[p.numpy() for p in pin])
+        d2h = int(sum(np.asarray(v).nbytes for k, v in out.items() if k != "n_tracks"))
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": n * ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "clusters_per_frame": n, "tracks_per_frame": int(res["n_tracks"]),
+                       "tracklets_per_frame": int(stats.get("tracklets", 0)), "storage": "fp32", "l2": "flushed (512 MB write) before each step",
+                       "parallelism": f"replicas x{ws}"},
+            "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
+            "kernels_ms": kernels}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(frame, os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tr.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

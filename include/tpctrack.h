@@ -110,8 +110,8 @@ typedef struct {
 typedef struct {
   int32_t n_kernels;
   const char* const* names;
-  const float* ms;            /* [n_kernels] */
-  const int64_t* launches;    /* [n_kernels] */
+  const float* ms;            /* [n_kernels] device time of each stage */
+  const int64_t* launches;    /* [n_kernels] kernel launches of each stage */
 } tpc_kernel_times;
 
 void tpc_default_params(tpc_params* p);
@@ -157,8 +157,14 @@ int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_
  * (each the input index of the linked cluster or -1). */
 int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n);
 
-/* Number of start hits / tracklets of a tracked frame. */
+/* Number of start hits and of tracks of a tracked frame. */
 int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n_tracks);
+
+/* Device counters of the batch a frame was tracked in, for diagnostics and roofline accounting:
+ * out[0..n) = clusters, clusters in the grid, grid bins, start hits, tracklets, tracklet row steps,
+ * hits fitted by tracklets, tracks, track hits, device error bits. Returns the number of counters
+ * available (>= 0) or a negative error. */
+int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable);

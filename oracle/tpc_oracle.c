@@ -226,21 +226,23 @@ static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real 
   const real c0 = SQRT((real)1 - s0 * s0);
   const real c1 = SQRT((real)1 - s1 * s1);
   const real N = s0 + s1, D = c0 + c1;
-  const real dy = dx * (N / D);                 /* chord relation of a circle */
+  const real iD = (real)1 / D;
+  const real dy = dx * (N * iD);                /* chord relation of a circle */
   const real l = SQRT(dx * dx + dy * dy);       /* chord length in the xy plane */
   const real t = l * k * (real)0.5;             /* sin of half the turning angle */
   real a = l * arc_ratio(t);                    /* arc length */
   if (dx < 0) a = -a;
   const real tw = P[3];
+  const real ic0 = (real)1 / c0, ic1 = (real)1 / c1, il = (real)1 / l;
   /* Jacobian d(y1, w1, s1, t, q/pT) / d(y0, w0, s0, t, q/pT) */
-  const real DD = D * D;
-  const real dy_ds0 = dx * ((real)2 / D + N * (s0 / c0 + s1 / c1) / DD);
-  const real dy_dk = dx * dx * ((real)1 / D + N * s1 / (c1 * DD));
+  const real iDD = iD * iD;
+  const real dy_ds0 = dx * ((real)2 * iD + N * (s0 * ic0 + s1 * ic1) * iDD);
+  const real dy_dk = dx * dx * (iD + N * s1 * ic1 * iDD);
   real da_dl = (real)1 / SQRT((real)1 - t * t);
   real da_dk = l * l * (real)0.5 * arc_ratio_deriv(t); /* at fixed chord */
   if (dx < 0) { da_dl = -da_dl; da_dk = -da_dk; }
-  const real dl_ds0 = dy * dy_ds0 / l;
-  const real dl_dk = dy * dy_dk / l;
+  const real dl_ds0 = dy * dy_ds0 * il;
+  const real dl_dk = dy * dy_dk * il;
   real J[5][5];
   memset(J, 0, sizeof(J));
   for (int i = 0; i < 5; ++i) J[i][i] = 1;
@@ -261,14 +263,13 @@ static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real 
   mat_mul5_bt(T, J, O);
   mirror_lower(O);
   /* multiple scattering: theta0^2 on the direction; var(sin phi) = c^2 (1+t^2) th^2,
-   * var(t) = (1+t^2)^2 th^2 */
+   * var(t) = (1+t^2)^2 th^2; with q2 = 1/p^2 = (q/pT)^2/(1+t^2), 1/(beta p)^2 = q2 (1 + m^2 q2) */
   if (cx->ms_on && P[4] != 0) {
     const real one_tw2 = (real)1 + tw * tw;
-    const real pathf = SQRT(one_tw2) / c1;
+    const real pathf = SQRT(one_tw2) * ic1;
     const real xx0 = cx->x0_row * pathf;
-    const real p2 = one_tw2 / (P[4] * P[4]);
-    const real beta2 = p2 / (p2 + cx->mass2);
-    const real th2 = cx->ms_c * xx0 / (beta2 * p2);
+    const real q2 = P[4] * P[4] / one_tw2;
+    const real th2 = cx->ms_c * xx0 * q2 * ((real)1 + cx->mass2 * q2);
     O[2][2] = O[2][2] + th2 * (c1 * c1) * one_tw2;
     O[3][3] = O[3][3] + th2 * one_tw2 * one_tw2;
   }
@@ -281,7 +282,8 @@ static real kf_chi2(const ctx_t* cx, const real P[5], real C[5][5], real ym, rea
   const real S00 = C[0][0] + cx->r00, S01 = C[0][1], S10 = C[1][0], S11 = C[1][1] + cx->r11;
   const real det = S00 * S11 - S01 * S10;
   if (!(det > 0)) return (real)INFINITY;
-  const real i00 = S11 / det, i01 = -S01 / det, i10 = -S10 / det, i11 = S00 / det;
+  const real idet = (real)1 / det;
+  const real i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   const real r0 = ym - P[0], r1 = wm - P[1];
   return r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
 }
@@ -293,8 +295,9 @@ static void kf_update(const ctx_t* cx, real P[5], real C[5][5], real ym, real wm
   S[0][0] = C[0][0] + cx->r00; S[0][1] = C[0][1] + 0;
   S[1][0] = C[1][0] + 0;       S[1][1] = C[1][1] + cx->r11;
   const real det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
-  Si[0][0] = S[1][1] / det; Si[0][1] = -S[0][1] / det;
-  Si[1][0] = -S[1][0] / det; Si[1][1] = S[0][0] / det;
+  const real idet = (real)1 / det;
+  Si[0][0] = S[1][1] * idet; Si[0][1] = -S[0][1] * idet;
+  Si[1][0] = -S[1][0] * idet; Si[1][1] = S[0][0] * idet;
   real K[5][2];
   for (int i = 0; i < 5; ++i)
     for (int l = 0; l < 2; ++l) {

@@ -108,6 +108,14 @@ class Tracker:
         self._check(self.lib.tpc_get_counts(self.ctx, ctypes.c_uint64(frame), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
 
+    STAT_NAMES = ("clusters", "sorted", "bins", "starts", "tracklets", "steps", "tracklet_hits", "tracks",
+                  "track_hits", "err")
+
+    def stats(self, frame: int) -> dict:
+        out = (ctypes.c_int64 * len(self.STAT_NAMES))()
+        n = self._check(self.lib.tpc_get_stats(self.ctx, ctypes.c_uint64(frame), out, len(self.STAT_NAMES)))
+        return {self.STAT_NAMES[i]: int(out[i]) for i in range(min(n, len(self.STAT_NAMES)))}
+
     def release(self, frame: int) -> None:
         self._check(self.lib.tpc_release_frame(self.ctx, ctypes.c_uint64(frame)))
         self._keep.pop(frame, None)
@@ -140,7 +148,9 @@ class Tracker:
     def set_timing(self, on: bool) -> None:
         self._check(self.lib.tpc_set_timing(self.ctx, 1 if on else 0))
 
-    def kernel_times(self) -> dict:
+    def kernel_times(self, launches: bool = False) -> dict:
         kt = _lib.tpc_kernel_times()
         self._check(self.lib.tpc_get_kernel_times(self.ctx, ctypes.byref(kt)))
+        if launches:
+            return {kt.names[i].decode(): int(kt.launches[i]) for i in range(kt.n_kernels)}
         return {kt.names[i].decode(): float(kt.ms[i]) for i in range(kt.n_kernels)}

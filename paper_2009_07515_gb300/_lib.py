@@ -1,7 +1,7 @@
 """ctypes binding of libtpctrack.so — argument marshalling only.
 
 Every function here has the name and meaning of the C entry point in ``include/tpctrack.h``; all
-tracking work runs in the library's CUDA kernels. The library must have been built (``build.py``);
+tracking work runs in the library's CUDA kernels. The library must have been built (``build_ext.py``);
 loading fails loudly otherwise, there is no fallback.
 """
 from __future__ import annotations
@@ -109,6 +109,7 @@ SIGNATURES = [
     ("tpc_poll", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_int32]),
     ("tpc_get_links", ctypes.c_int, [_ctx_p, _frame, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64]),
     ("tpc_get_counts", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+    ("tpc_get_stats", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("tpc_set_timing", ctypes.c_int, [_ctx_p, ctypes.c_int32]),
     ("tpc_get_kernel_times", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_kernel_times)]),
 ]
@@ -122,7 +123,7 @@ def load(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"libtpctrack.so is not built ({path}); run paper_2009_07515_gb300/build.py")
+        raise ImportError(f"libtpctrack.so is not built ({path}); run paper_2009_07515_gb300/build_ext.py")
     lib = ctypes.CDLL(path)
     for name, res, args in SIGNATURES:
         fn = getattr(lib, name)

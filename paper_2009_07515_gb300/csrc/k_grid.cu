@@ -1,14 +1,15 @@
 // k_grid.cu — K0/K1: input validation and the per-(sector, row) search grid.
 //
-// The grid is a counting sort of the batch's clusters by (frame, sector, row, w-bin): each segment
-// (frame, sector, row) gets a 1-D grid over the drift coordinate w whose bin count follows the
-// segment's occupancy, so any window |w - wc| <= W of a row is one contiguous range of sorted
-// positions. The grid decides no result: every window test downstream is an exact comparison on
-// the coordinates, and every tie is broken by the (w, y, input index) order.
+// The grid is a counting sort of the batch's clusters by (frame, sector, row, w-bin, y-bin): each
+// segment (frame, sector, row) gets a 2-D grid over the drift coordinate w and the pad-row
+// coordinate y with about `occ` clusters per bin and bins shaped like the neighbour window, so a
+// window of a row is one contiguous range of sorted positions per w-column it touches. The grid
+// decides no result: every window test downstream is an exact comparison on the coordinates, and
+// every tie is broken by the (w, y, input index) order.
 //
 // Kernels (all persistent, sizes read from device memory so the sequence can be graph-captured):
 //   k_seg_hist    validate, count clusters per segment, w range per frame
-//   k_seg_layout  bins per segment (occupancy target), w origin and bin density
+//   k_seg_layout  bins per segment (occupancy target), bin origins and densities in w and y
 //   k_bin_rank    bin histogram; each cluster keeps its arrival rank inside its bin
 //   k_scatter     sorted (y, w) and input index at bin_start[bin] + rank
 //   scans         exclusive prefix sums with device-side lengths
@@ -180,28 +181,44 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
   if (bad) atomicOr(&W.cnt->err, kErrInput);
 }
 
-// one thread per segment: bins from the occupancy target
-__global__ void __launch_bounds__(256) k_seg_layout(Work W, float occ) {
+// one thread per segment: a grid of ~n/occ bins, nw x ny, with bins shaped like the neighbour
+// window (w/y size ratio `aspect`)
+__global__ void __launch_bounds__(256) k_seg_layout(Work W, DevParams Q) {
   const BatchDesc* B = W.batch;
   const int nseg = B->nf * kSegPerFrame;
   for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < nseg; g += gridDim.x * blockDim.x) {
-    const int f = g / kSegPerFrame;
+    const int f = g / kSegPerFrame, r = (g % kSegPerFrame) % kNRow;
     const uint32_t n = W.seg_cnt[g];
     float wlo = 0.f, whi = 0.f;
     if (W.cnt->wrange[2 * f] <= W.cnt->wrange[2 * f + 1]) {
       wlo = ord2f(W.cnt->wrange[2 * f]);
       whi = ord2f(W.cnt->wrange[2 * f + 1]);
     }
-    uint32_t nb = 1;
+    const float wext = whi - wlo, yext = 2.f * Q.yext[r];
+    uint32_t nbins = 1;
     if (n > 0) {
-      float want = ceilf((float)n / occ);
-      nb = want < 1.f ? 1u : (want > 1048576.f ? 1048576u : (uint32_t)want);
+      const float want = ceilf((float)n / Q.occ);
+      nbins = want < 1.f ? 1u : (want > 4194304.f ? 4194304u : (uint32_t)want);
     }
-    const float range = whi - wlo;
-    const float inv = range > 0.f ? (float)nb / range : 0.f;
-    W.seg_nb[g] = nb;
-    W.seg_geo[g] = make_float2(wlo, inv);
+    uint32_t ny = 1;
+    if (wext > 0.f && nbins > 1) {
+      const float fy = sqrtf((float)nbins * (yext / wext) * Q.aspect);
+      ny = fy < 1.f ? 1u : (fy > 64.f ? 64u : (uint32_t)(fy + 0.5f));
+      if (ny > nbins) ny = nbins;
+    }
+    const uint32_t nw = (nbins + ny - 1) / ny;
+    W.seg_nb[g] = nw * ny;
+    W.seg_dim[g] = make_uint2(nw, ny);
+    W.seg_geo[g] = make_float4(wlo, wext > 0.f ? (float)nw / wext : 0.f, -Q.yext[r], (float)ny / yext);
   }
+}
+
+__device__ __forceinline__ uint32_t seg_bin(const Work& W, int g, float y, float w) {
+  const uint2 dim = W.seg_dim[g];
+  const float4 geo = W.seg_geo[g];
+  const int iw = bin_of(w, geo.x, geo.y, (int)dim.x);
+  const int iy = bin_of(y, geo.z, geo.w, (int)dim.y);
+  return W.seg_bb[g] + (uint32_t)(iw * (int)dim.y + iy);
 }
 
 __global__ void __launch_bounds__(256) k_bin_rank(Work W) {
@@ -220,9 +237,7 @@ __global__ void __launch_bounds__(256) k_bin_rank(Work W) {
     const float y = F.y[j], w = F.w[j];
     if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) continue;
     const int g = fi * kSegPerFrame + s * kNRow + r;
-    const float2 geo = W.seg_geo[g];
-    const int b = bin_of(w, geo.x, geo.y, (int)W.seg_nb[g]);
-    W.rank[i] = atomicAdd(&W.bin_start[W.seg_bb[g] + b], 1u);
+    W.rank[i] = atomicAdd(&W.bin_start[seg_bin(W, g, y, w)], 1u);
   }
 }
 
@@ -238,9 +253,7 @@ __global__ void __launch_bounds__(256) k_scatter(Work W) {
     const float y = F.y[j], w = F.w[j];
     if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) continue;
     const int g = fi * kSegPerFrame + s * kNRow + r;
-    const float2 geo = W.seg_geo[g];
-    const int b = bin_of(w, geo.x, geo.y, (int)W.seg_nb[g]);
-    const uint32_t p = W.bin_start[W.seg_bb[g] + b] + W.rank[i];
+    const uint32_t p = W.bin_start[seg_bin(W, g, y, w)] + W.rank[i];
     W.hyw[p] = make_float2(y, w);
     W.horig[p] = (uint32_t)j;
   }

@@ -4,11 +4,12 @@
 // (d in row r-1, u in row r+1) inside the slope windows that minimises the mid-point deviation
 // chi_n = (y_i - y_mid)^2 + (w_i - w_mid)^2, accepted if chi_n <= chi_n_max; ties go to the
 // smaller (w, y, input index) of d, then of u. A CTA takes one segment (frame, sector, row) at a
-// time in chunks of blockDim hits; for each chunk the windows of the two adjacent rows are one
-// contiguous range each, which thread 0 stages into shared memory with 1-D bulk TMA copies
-// (cp.async.bulk, completion on an mbarrier; no multicast). Each thread then scans its own
-// candidate sub-ranges out of shared memory. A range too large for the stage is read from global
-// memory instead (same arithmetic, same result).
+// time; each warp takes 32 consecutive hits of it. The w-columns of the two adjacent rows that the
+// 32 windows touch are one contiguous range each, which lane 0 stages into the warp's shared-memory
+// slots with 1-D bulk TMA copies (cp.async.bulk, completion on the warp's mbarrier; no multicast).
+// Each lane then scans its own candidate bins (one contiguous range per w-column) out of shared
+// memory. A range too large for a slot is read from global memory instead (same arithmetic, same
+// result).
 //
 // K3 keeps only reciprocal links and counts start hits per segment; K4 writes the start hits
 // (cleaned up link, no down link, chain of >= lmin hits) by a block-wide ballot/scan compaction in
@@ -18,7 +19,6 @@
 
 namespace tpc {
 
-constexpr int kK2Stage = 2048;  // staged hits per adjacent row (float2)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -75,32 +75,71 @@ __device__ __forceinline__ bool pair_key_less(const Work& W, int d, int u, int b
   return key_less(a.y, a.x, W.horig[u], b.y, b.x, W.horig[bu]);
 }
 
-__device__ __forceinline__ void row_range(const Work& W, int g, float lo, float hi, int& p0, int& p1) {
+// positions of the w-columns of segment g touched by |w - wc| <= W for wc in [lo, hi]
+__device__ __forceinline__ void column_range(const Work& W, int g, float lo, float hi, int& p0, int& p1) {
+  const uint2 dim = W.seg_dim[g];
+  const float4 geo = W.seg_geo[g];
   const uint32_t bb = W.seg_bb[g];
-  const int nb = (int)W.seg_nb[g];
-  const float2 geo = W.seg_geo[g];
-  const int b0 = bin_of(lo, geo.x, geo.y, nb), b1 = bin_of(hi, geo.x, geo.y, nb);
-  p0 = (int)W.bin_start[bb + b0];
-  p1 = (int)W.bin_start[bb + b1 + 1];
+  const int iw0 = bin_of(lo, geo.x, geo.y, (int)dim.x), iw1 = bin_of(hi, geo.x, geo.y, (int)dim.x);
+  p0 = (int)W.bin_start[bb + (uint32_t)(iw0 * (int)dim.y)];
+  p1 = (int)W.bin_start[bb + (uint32_t)((iw1 + 1) * (int)dim.y)];
+}
+
+// One warp takes 32 consecutive hits of a row; lane 0 stages the w-columns of rows r-1 and r+1
+// that the 32 windows touch into the warp's own shared-memory slots (two bulk copies, one mbarrier
+// per warp), so warps never wait for one another. Each lane then walks its window's bins as one
+// flat loop (the w-columns one after the other), first over row r+1, keeping the candidates that
+// pass the window in a per-lane shared-memory list, then over row r-1, pairing each passing
+// candidate with the listed ones.
+constexpr int kK2Warps = 8;
+constexpr int kK2Slot = 192;  // staged hits per adjacent row per warp (float2)
+constexpr int kK2UCap = 6;    // listed row r+1 candidates per lane (more: rescan the row)
+
+// flat cursor over the bins of a grid window: w-columns iw0..iw1, y-bins iy0..iy1 of each
+struct WinCursor {
+  int cw, p, pe;
+};
+__device__ __forceinline__ void cursor_col(const Work& W, const GridWin& q, WinCursor& c) {
+  const uint32_t col = q.bb + (uint32_t)(c.cw * q.ny);
+  c.p = (int)W.bin_start[col + q.iy0];
+  c.pe = (int)W.bin_start[col + q.iy1 + 1];
+}
+// next position of the window, or -1
+__device__ __forceinline__ int cursor_next(const Work& W, const GridWin& q, WinCursor& c) {
+  while (c.p >= c.pe) {
+    if (c.cw >= q.iw1) return -1;
+    ++c.cw;
+    cursor_col(W, q, c);
+  }
+  return c.p++;
+}
+
+__device__ __forceinline__ void pair_step(const Work& W, float yi, float wi, float fm, const float2 hd, int d,
+                                          const float2 hu, int u, float& best, int& bd, int& bu) {
+  const float py = hd.x + (hu.x - hd.x) * fm;
+  const float pw = hd.y + (hu.y - hd.y) * fm;
+  const float ey = yi - py, ew = wi - pw;
+  const float chi = ey * ey + ew * ew;
+  bool better;
+  if (bd < 0 || chi < best) better = true;
+  else if (chi > best) better = false;
+  else better = pair_key_less(W, d, u, bd, bu);
+  if (better) { best = chi; bd = d; bu = u; }
 }
 
 __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q) {
-  extern __shared__ __align__(16) float2 k2_smem[];
-  float2* stage_dn = k2_smem;
-  float2* stage_up = k2_smem + kK2Stage + 2;
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ float red_lo[8], red_hi[8];
-  __shared__ int st_base[2], st_count[2];
-  __shared__ int s_abort;
+  __shared__ __align__(16) float2 stage[kK2Warps][2][kK2Slot + 2];
+  __shared__ float2 ucand[kK2Warps][kK2UCap][32];
+  __shared__ int upos[kK2Warps][kK2UCap][32];
+  __shared__ __align__(8) uint64_t bar[kK2Warps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const BatchDesc* B = W.batch;
   const int nseg = B->nf * kSegPerFrame;
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    s_abort = 0;
-  }
-  __syncthreads();
+  if (lane == 0) mbar_init(&bar[warp], 1);
+  __syncwarp();
   uint32_t parity = 0;
-  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+  bool aborted = false;
+  for (int g = blockIdx.x; g < nseg && !aborted; g += gridDim.x) {
     const int r = (g % kSegPerFrame) % kNRow;
     const int a = (int)W.bin_start[W.seg_bb[g]];
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
@@ -110,80 +149,86 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q) {
     }
     const float wy_dn = Q.wy_dn[r], ww_dn = Q.ww_dn[r], wy_up = Q.wy_up[r], ww_up = Q.ww_up[r];
     const float fm = Q.f_mid[r];
-    for (int c0 = a; c0 < b; c0 += blockDim.x) {
-      const int i = c0 + threadIdx.x;
+    for (int c0 = a + 32 * warp; c0 < b; c0 += 32 * kK2Warps) {
+      const int i = c0 + lane;
       const bool valid = i < b;
-      float2 hi = valid ? W.hyw[i] : make_float2(0.f, 0.f);
-      // chunk w range (block reduction)
+      const float2 hi = valid ? W.hyw[i] : make_float2(0.f, 0.f);
       float lo_w = valid ? hi.y : 3.0e38f, hi_w = valid ? hi.y : -3.0e38f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         lo_w = fminf(lo_w, __shfl_xor_sync(0xffffffffu, lo_w, o));
         hi_w = fmaxf(hi_w, __shfl_xor_sync(0xffffffffu, hi_w, o));
       }
-      if ((threadIdx.x & 31) == 0) { red_lo[threadIdx.x >> 5] = lo_w; red_hi[threadIdx.x >> 5] = hi_w; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float l = red_lo[0], h = red_hi[0];
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { l = fminf(l, red_lo[k]); h = fmaxf(h, red_hi[k]); }
-        const float amax = fmaxf(fabsf(l), fabsf(h));
+      // lane 0: ranges of the adjacent rows, then the copies
+      int base0 = 0, cnt0 = 0, base1 = 0, cnt1 = 0;
+      if (lane == 0) {
+        const float amax = fmaxf(fabsf(lo_w), fabsf(hi_w));
         uint32_t bytes = 0;
-        for (int side = 0; side < 2; ++side) {
-          const float Ww = side == 0 ? ww_dn : ww_up;
-          const float pad = win_pad(amax, Ww);
-          int p0, p1;
-          row_range(W, g + (side == 0 ? -1 : 1), (l - Ww) - pad, (h + Ww) + pad, p0, p1);
-          const int q0 = p0 & ~1, q1 = (p1 + 1) & ~1;
-          if (q1 > q0 && q1 - q0 <= kK2Stage) {
-            st_base[side] = q0;
-            st_count[side] = q1 - q0;
-            bytes += (uint32_t)(q1 - q0) * 8u;
-          } else {
-            st_base[side] = 0;
-            st_count[side] = 0;
-          }
-        }
-        mbar_arrive_expect_tx(&bar, bytes);
-        if (st_count[0]) tma_load_1d(stage_dn, W.hyw + st_base[0], (uint32_t)st_count[0] * 8u, &bar);
-        if (st_count[1]) tma_load_1d(stage_up, W.hyw + st_base[1], (uint32_t)st_count[1] * 8u, &bar);
+        int p0, p1;
+        column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), p0, p1);
+        int q0 = p0 & ~1, q1 = (p1 + 1) & ~1;
+        if (q1 > q0 && q1 - q0 <= kK2Slot) { base0 = q0; cnt0 = q1 - q0; bytes += (uint32_t)cnt0 * 8u; }
+        column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), p0, p1);
+        q0 = p0 & ~1; q1 = (p1 + 1) & ~1;
+        if (q1 > q0 && q1 - q0 <= kK2Slot) { base1 = q0; cnt1 = q1 - q0; bytes += (uint32_t)cnt1 * 8u; }
+        // the slots were read by this warp's previous chunk (generic proxy): order before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&bar[warp], bytes);
+        if (cnt0) tma_load_1d(stage[warp][0], W.hyw + base0, (uint32_t)cnt0 * 8u, &bar[warp]);
+        if (cnt1) tma_load_1d(stage[warp][1], W.hyw + base1, (uint32_t)cnt1 * 8u, &bar[warp]);
       }
-      __syncthreads();
-      if (!mbar_wait_bounded(&bar, parity)) {
-        if (threadIdx.x == 0) { atomicOr(&W.cnt->err, kErrTimeout); s_abort = 1; }
+      base0 = __shfl_sync(0xffffffffu, base0, 0);
+      cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
+      base1 = __shfl_sync(0xffffffffu, base1, 0);
+      cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
+      if (!mbar_wait_bounded(&bar[warp], parity)) {
+        // give the copies in flight a second bounded wait before leaving
+        (void)mbar_wait_bounded(&bar[warp], parity);
+        if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
+        aborted = true;
+        break;
       }
       parity ^= 1u;
-      RowView vd{stage_dn, st_base[0], st_count[0]};
-      RowView vu{stage_up, st_base[1], st_count[1]};
+      const RowView vd{stage[warp][0], base0, cnt0};
+      const RowView vu{stage[warp][1], base1, cnt1};
       if (valid) {
         const float yi = hi.x, wi = hi.y;
-        int dp0, dp1, up0, up1;
-        row_range(W, g - 1, (wi - ww_dn) - win_pad(wi, ww_dn), (wi + ww_dn) + win_pad(wi, ww_dn), dp0, dp1);
-        row_range(W, g + 1, (wi - ww_up) - win_pad(wi, ww_up), (wi + ww_up) + win_pad(wi, ww_up), up0, up1);
+        const GridWin qd = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g - 1, yi, wi, wy_dn, ww_dn);
+        const GridWin qu = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g + 1, yi, wi, wy_up, ww_up);
+        // row r+1 candidates inside the window
+        int nu = 0;
+        WinCursor cu{qu.iw0, 0, 0};
+        cursor_col(W, qu, cu);
+        for (int u; (u = cursor_next(W, qu, cu)) >= 0;) {
+          const float2 hu = load_hit(W, vu, u);
+          if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+          if (nu < kK2UCap) { ucand[warp][nu][lane] = hu; upos[warp][nu][lane] = u; }
+          ++nu;
+        }
         float best = __int_as_float(0x7f800000);
         int bd = -1, bu = -1;
-        for (int d = dp0; d < dp1; ++d) {
-          const float2 hd = load_hit(W, vd, d);
-          if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
-          for (int u = up0; u < up1; ++u) {
-            const float2 hu = load_hit(W, vu, u);
-            if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-            const float py = hd.x + (hu.x - hd.x) * fm;
-            const float pw = hd.y + (hu.y - hd.y) * fm;
-            const float ey = yi - py, ew = wi - pw;
-            const float chi = ey * ey + ew * ew;
-            bool better;
-            if (bd < 0 || chi < best) better = true;
-            else if (chi > best) better = false;
-            else better = pair_key_less(W, d, u, bd, bu);
-            if (better) { best = chi; bd = d; bu = u; }
+        if (nu > 0) {
+          WinCursor cd{qd.iw0, 0, 0};
+          cursor_col(W, qd, cd);
+          for (int d; (d = cursor_next(W, qd, cd)) >= 0;) {
+            const float2 hd = load_hit(W, vd, d);
+            if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
+            if (nu <= kK2UCap) {
+              for (int k = 0; k < nu; ++k) pair_step(W, yi, wi, fm, hd, d, ucand[warp][k][lane], upos[warp][k][lane], best, bd, bu);
+            } else {
+              WinCursor c2{qu.iw0, 0, 0};
+              cursor_col(W, qu, c2);
+              for (int u; (u = cursor_next(W, qu, c2)) >= 0;) {
+                const float2 hu = load_hit(W, vu, u);
+                if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+                pair_step(W, yi, wi, fm, hd, d, hu, u, best, bd, bu);
+              }
+            }
           }
         }
         W.links[i] = (bd >= 0 && best <= Q.chi_n_max) ? make_int2(bd, bu) : make_int2(-1, -1);
       }
-      // the stage is rewritten by the async proxy next: order the generic reads before it
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (s_abort) return;
+      __syncwarp();
     }
   }
 }
@@ -244,8 +289,8 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
     uint32_t out = W.seg_nstart[g];
     const uint32_t bb = W.seg_bb[g];
-    const int nb = (int)W.seg_nb[g];
-    const float2 geo = W.seg_geo[g];
+    const uint2 dim = W.seg_dim[g];
+    const float4 geo = W.seg_geo[g];
     for (int c0 = a; c0 < b; c0 += blockDim.x) {
       const int i = c0 + threadIdx.x;
       bool st = false;
@@ -270,7 +315,8 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
         const uint32_t pos = out + (uint32_t)warp_off[warp] + (uint32_t)__popc(m & ((1u << lane) - 1u));
         if (pos < tcap) {
           const float w = W.hyw[i].y;
-          W.starts_raw[pos] = make_uint4((uint32_t)i, (uint32_t)g, bb + (uint32_t)bin_of(w, geo.x, geo.y, nb), 0u);
+          const uint32_t col = bb + (uint32_t)(bin_of(w, geo.x, geo.y, (int)dim.x) * (int)dim.y);
+          W.starts_raw[pos] = make_uint4((uint32_t)i, (uint32_t)g, col, 0u);
         }
       }
       out += (uint32_t)s_total;
@@ -279,19 +325,21 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
   }
 }
 
-// K4b: canonical order of start hits and their rank in the sector (rows, then (w, y, input index))
+// K4b: canonical order of start hits and their rank in the sector (rows, then (w, y, input index)).
+// A w-column holds every hit of its w range, so hits of earlier columns are smaller; only the hits
+// of the start's own column are compared one by one.
 __global__ void __launch_bounds__(256) k_start_order(Work W) {
   const uint32_t n = min(W.cnt->n_starts, (uint32_t)W.tcap);
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const uint4 e = W.starts_raw[p];
     const int i = (int)e.x, g = (int)e.y;
-    const uint32_t Bn = e.z;
+    const uint32_t col = e.z;
     const float2 hi = W.hyw[i];
     const uint32_t oi = W.horig[i];
-    // run of start entries sharing the bin (contiguous in sorted order)
+    // run of start entries sharing the w-column (contiguous in sorted order)
     uint32_t lo = p, hiq = p;
-    while (lo > 0 && W.starts_raw[lo - 1].z == Bn) --lo;
-    while (hiq + 1 < n && W.starts_raw[hiq + 1].z == Bn) ++hiq;
+    while (lo > 0 && W.starts_raw[lo - 1].z == col) --lo;
+    while (hiq + 1 < n && W.starts_raw[hiq + 1].z == col) ++hiq;
     uint32_t before = 0;
     for (uint32_t q = lo; q <= hiq; ++q) {
       if (q == p) continue;
@@ -299,20 +347,18 @@ __global__ void __launch_bounds__(256) k_start_order(Work W) {
       const float2 hj = W.hyw[j];
       if (key_less(hj.y, hj.x, W.horig[j], hi.y, hi.x, oi)) ++before;
     }
-    // rank of the hit within its bin, row and sector
-    const uint32_t b0 = W.bin_start[Bn], b1 = W.bin_start[Bn + 1];
-    uint32_t inbin = 0;
-    for (uint32_t h = b0; h < b1; ++h) {
+    // rank of the hit within its row and sector
+    const uint32_t ny = W.seg_dim[g].y;
+    const uint32_t c0 = W.bin_start[col], c1 = W.bin_start[col + ny];
+    uint32_t incol = 0;
+    for (uint32_t h = c0; h < c1; ++h) {
       if ((int)h == i) continue;
       const float2 hh = W.hyw[h];
-      if (key_less(hh.y, hh.x, W.horig[h], hi.y, hi.x, oi)) ++inbin;
+      if (key_less(hh.y, hh.x, W.horig[h], hi.y, hi.x, oi)) ++incol;
     }
     const int r = (g % kSegPerFrame) % kNRow;
-    const uint32_t seg_first = W.bin_start[W.seg_bb[g]];
     const uint32_t sec_first = W.bin_start[W.seg_bb[g - r]];
-    const uint32_t rank = (b0 - sec_first) + inbin;
-    (void)seg_first;
-    W.starts[lo + before] = make_uint4((uint32_t)i, (uint32_t)g, rank, 0u);
+    W.starts[lo + before] = make_uint4((uint32_t)i, (uint32_t)g, (c0 - sec_first) + incol, 0u);
   }
 }
 

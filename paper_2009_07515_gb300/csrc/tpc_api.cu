@@ -27,13 +27,14 @@ __global__ void k_scan_reduce(const uint32_t*, const uint32_t*, long long, int, 
 __global__ void k_scan_tiles(uint32_t*, const uint32_t*, long long, int, uint32_t*);
 __global__ void k_scan_apply(const uint32_t*, const uint32_t*, long long, int, const uint32_t*, const uint32_t*, uint32_t*);
 __global__ void k_seg_hist(Work);
-__global__ void k_seg_layout(Work, float);
+__global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
 __global__ void k_scatter(Work);
 __global__ void k_neighbours(Work, DevParams);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_starts(Work, DevParams);
 __global__ void k_start_order(Work);
+__global__ void k_chains(Work);
 __global__ void k_tracklets(Work, DevParams);
 __global__ void k_votes(Work, DevParams);
 __global__ void k_kept(Work, DevParams);
@@ -43,7 +44,6 @@ __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_set_ntracklets(Work);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
-constexpr int kK2Stage = 2048;
 }  // namespace tpc
 
 using namespace tpc;
@@ -52,7 +52,7 @@ namespace {
 
 const char* kKernelNames[] = {"reset",  "seg_hist", "seg_layout", "scan_seg",  "zero_bins", "bin_rank", "scan_bins",
                               "scatter", "neighbours", "clean",   "scan_start", "starts",   "start_order",
-                              "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "frame_off"};
+                              "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "frame_off"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 double now_s() {
@@ -108,13 +108,13 @@ struct tpc_ctx {
   tpc_frame_t next_id = 1;
   std::string err;
   std::vector<std::shared_ptr<Workspace>> wspool;
-  int grid[kNumKernels] = {0};
-  int k2_smem = 0;
+  int grid_neighbours = 0, grid_tracklets = 0;
   bool timing = false;
   cudaEvent_t ev[kNumKernels + 1] = {nullptr};
   cudaEvent_t ev_sync = nullptr;
   float ms[kNumKernels] = {0};
   int64_t launches[kNumKernels] = {0};
+  int64_t stage_launches[kNumKernels] = {0};
   // serving
   std::deque<tpc_frame_t> queue;  // submitted, not yet admitted
   size_t budget_used = 0;
@@ -182,6 +182,8 @@ void make_dev_params(const tpc_params& p, DevParams& d) {
     d.ww_up[r] = e + eps;
     d.f_mid[r] = dxm / s;
   }
+  for (int r = 0; r < kNRow; ++r) d.yext[r] = d.x[r] * d.tan10 + 1.0f;
+  d.aspect = (float)((p.kw * (160.0 / 151.0) + p.eps) / (p.ky * (160.0 / 151.0) + p.eps));
 }
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -204,7 +206,8 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   ws->nf_cap = nf_cap;
   ws->scap = (long long)nf_cap * kSegPerFrame;
   const double occ = ctx->dp.occ;
-  ws->bcap = (long long)std::ceil((double)ws->ncap / occ) + ws->scap + 16;
+  // a segment grid has nw * ny <= 2 * ceil(n / occ) bins (ny <= bins)
+  ws->bcap = 2 * ((long long)std::ceil((double)ws->ncap / occ) + ws->scap) + 16;
   long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1});
   ws->scan_cap = (maxscan + 2047) / 2048 + 16;
   struct Item { void** ptr; size_t bytes; };
@@ -216,7 +219,8 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.seg_cnt, 4 * (size_t)ws->scap},
       {(void**)&W.seg_nb, 4 * (size_t)ws->scap},
       {(void**)&W.seg_bb, 4 * (size_t)(ws->scap + 1)},
-      {(void**)&W.seg_geo, 8 * (size_t)ws->scap},
+      {(void**)&W.seg_dim, 8 * (size_t)ws->scap},
+      {(void**)&W.seg_geo, 16 * (size_t)ws->scap},
       {(void**)&W.bin_start, 4 * (size_t)(ws->bcap + 1)},
       {(void**)&W.rank, 4 * (size_t)ws->ncap},
       {(void**)&W.hyw, 8 * (size_t)(ws->ncap + 2)},
@@ -226,6 +230,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.seg_nstart, 4 * (size_t)(ws->scap + 1)},
       {(void**)&W.starts_raw, 16 * (size_t)ws->tcap},
       {(void**)&W.starts, 16 * (size_t)ws->tcap},
+      {(void**)&W.chains, 16 * (size_t)ws->tcap},
       {(void**)&W.tl_state, 96 * (size_t)ws->tcap},
       {(void**)&W.tl_info, 4 * (size_t)ws->tcap},
       {(void**)&W.slab, 4 * (size_t)kNRow * (size_t)ws->tcap},
@@ -310,58 +315,65 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   DevCounters* C = W.cnt;
   const int G = ctx->sms;
   int ki = 0;
+  int nl = 0;  // kernel launches of the current stage
   auto mark = [&](int idx) {
+    if (idx > 0) ctx->stage_launches[idx - 1] = nl;
+    nl = 0;
     if (timing) cudaEventRecord(ctx->ev[idx], s);
   };
   // scan lengths are device-side counts clamped to the buffer capacity n_cap
   auto scan = [&](const uint32_t* in, uint32_t* out, const uint32_t* n_dev, long long n_host, uint32_t* total) {
+    nl += 3;
     k_scan_reduce<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp);
     k_scan_tiles<<<1, 1024, 0, s>>>(W.scan_tmp, n_dev, n_host, 0, total);
     k_scan_apply<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp, total, out);
   };
   mark(ki++);  // reset
-  k_reset_counters<<<1, 128, 0, s>>>(W);
-  k_zero_u32<<<G, 256, 0, s>>>(W.seg_cnt, &C->nseg, W.scap, 0, 1);
+  ++nl; k_reset_counters<<<1, 128, 0, s>>>(W);
+  ++nl; k_zero_u32<<<G, 256, 0, s>>>(W.seg_cnt, &C->nseg, W.scap, 0, 1);
   mark(ki++);  // seg_hist
-  k_seg_hist<<<4 * G, 256, 0, s>>>(W);
+  ++nl; k_seg_hist<<<4 * G, 256, 0, s>>>(W);
   mark(ki++);  // seg_layout
-  k_seg_layout<<<G, 256, 0, s>>>(W, Q.occ);
+  ++nl; k_seg_layout<<<G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_seg
   scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
   mark(ki++);  // zero_bins
-  k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
+  ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
   mark(ki++);  // bin_rank
-  k_bin_rank<<<8 * G, 256, 0, s>>>(W);
+  ++nl; k_bin_rank<<<8 * G, 256, 0, s>>>(W);
   mark(ki++);  // scan_bins
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
   mark(ki++);  // scatter
-  k_scatter<<<8 * G, 256, 0, s>>>(W);
+  ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W);
   mark(ki++);  // neighbours
-  k_neighbours<<<ctx->grid[8], 256, ctx->k2_smem, s>>>(W, Q);
+  ++nl; k_neighbours<<<ctx->grid_neighbours, 256, 0, s>>>(W, Q);
   mark(ki++);  // clean
-  k_clean<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_start
   scan(W.seg_nstart, W.seg_nstart, &C->nseg, W.scap, &C->n_starts);
   mark(ki++);  // starts
-  k_starts<<<4 * G, 256, 0, s>>>(W, Q);
-  k_set_ntracklets<<<1, 32, 0, s>>>(W);
+  ++nl; k_starts<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_set_ntracklets<<<1, 32, 0, s>>>(W);
   mark(ki++);  // start_order
-  k_start_order<<<2 * G, 256, 0, s>>>(W);
+  ++nl; k_start_order<<<2 * G, 256, 0, s>>>(W);
+  mark(ki++);  // chains
+  ++nl; k_chains<<<4 * G, 256, 0, s>>>(W);
   mark(ki++);  // tracklets
-  k_tracklets<<<ctx->grid[13], 128, 0, s>>>(W, Q);
+  ++nl; k_tracklets<<<ctx->grid_tracklets, 128, 0, s>>>(W, Q);
   mark(ki++);  // zero_w
-  k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
+  ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
   mark(ki++);  // votes
-  k_votes<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_votes<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // kept
-  k_kept<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_kept<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_kept
   scan(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks);
   scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
   mark(ki++);  // write_tracks
-  k_write_tracks<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_write_tracks<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // frame_off
-  k_frame_offsets<<<1, 128, 0, s>>>(W);
+  ++nl; k_frame_offsets<<<1, 128, 0, s>>>(W);
+  ctx->stage_launches[kNumKernels - 1] = nl;
   if (timing) cudaEventRecord(ctx->ev[kNumKernels], s);
   cudaMemcpyAsync(ws.h_cnt, W.cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaGetLastError();
@@ -454,10 +466,7 @@ int wait_ws(tpc_ctx* ctx, Workspace& ws, double timeout_s) {
   if (ctx->timing) {
     for (int k = 0; k < kNumKernels; ++k) {
       float m = 0;
-      if (cudaEventElapsedTime(&m, ctx->ev[k], ctx->ev[k + 1]) == cudaSuccess) {
-        ctx->ms[k] = m;
-        ctx->launches[k] = 1;
-      }
+      if (cudaEventElapsedTime(&m, ctx->ev[k], ctx->ev[k + 1]) == cudaSuccess) ctx->ms[k] = m;
     }
   }
   return TPC_OK;
@@ -623,13 +632,11 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     for (int k = 0; k <= kNumKernels; ++k) cudaEventCreate(&ctx->ev[k]);
     cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming);
-    ctx->k2_smem = (2 * (kK2Stage + 2)) * (int)sizeof(float2);
-    cudaFuncSetAttribute(k_neighbours, cudaFuncAttributeMaxDynamicSharedMemorySize, ctx->k2_smem);
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours, 256, ctx->k2_smem);
-    ctx->grid[8] = ctx->sms * std::max(nb, 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours, 256, 0);
+    ctx->grid_neighbours = ctx->sms * std::max(nb, 1);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets, 128, 0);
-    ctx->grid[13] = ctx->sms * std::max(nb, 1);
+    ctx->grid_tracklets = ctx->sms * std::max(nb, 1);
     for (int k = 0; k < 2; ++k) {
       cudaStream_t s;
       cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -752,6 +759,21 @@ int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n
   if (n_start) *n_start = (int64_t)(c.frame_start0[f->fidx + 1] - c.frame_start0[f->fidx]);
   if (n_tracks) *n_tracks = (int64_t)(c.frame_track0[f->fidx + 1] - c.frame_track0[f->fidx]);
   return TPC_OK;
+}
+
+int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n) {
+  if (!ctx || !out || n < 0) return TPC_E_INVAL;
+  Frame* f = find_frame(ctx, frame);
+  if (!f || !f->ws) return fail(ctx, TPC_E_STATE, "frame has no tracking results");
+  int rc = wait_ws(ctx, *f->ws, 120.0);
+  if (rc) return rc;
+  const DevCounters& c = *f->ws->h_cnt;
+  const int64_t v[] = {(int64_t)c.ntot, (int64_t)c.n_sorted, (int64_t)c.n_bins, (int64_t)c.n_starts,
+                       (int64_t)c.n_tracklets, (int64_t)c.n_steps, (int64_t)c.n_tracklet_hits, (int64_t)c.n_tracks,
+                       (int64_t)c.n_track_hits, (int64_t)c.err};
+  const int nv = (int)(sizeof(v) / sizeof(v[0]));
+  for (int k = 0; k < n && k < nv; ++k) out[k] = v[k];
+  return nv;
 }
 
 int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n) {
@@ -890,6 +912,7 @@ int tpc_set_timing(tpc_ctx* ctx, int32_t enable) {
 
 int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out) {
   if (!ctx || !out) return TPC_E_INVAL;
+  for (int k = 0; k < kNumKernels; ++k) ctx->launches[k] = ctx->stage_launches[k];
   out->n_kernels = kNumKernels;
   out->names = kKernelNames;
   out->ms = ctx->ms;

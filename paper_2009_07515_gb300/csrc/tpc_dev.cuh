@@ -4,10 +4,12 @@
 // a batch-global "sorted position" p of a cluster after the grid build):
 //   hyw[p]      float2 (y, w) of the cluster at sorted position p (FP32 storage)
 //   horig[p]    uint32 index of the cluster in its frame's input arrays
-//   segments    g = frame*5472 + sector*152 + row; seg_bb[g] = first bin, seg_nb[g] bins,
-//               seg_geo[g] = (w_lo, bins per cm) of the segment's 1-D grid in the drift coordinate w
-//   bin_start[b] sorted position of the first cluster of bin b (exclusive prefix over all bins), so a
-//               window [w0, w1] of a row is one contiguous position range
+//   segments    g = frame*5472 + sector*152 + row; seg_bb[g] = first bin, seg_dim[g] = (nw, ny),
+//               seg_geo[g] = (w_lo, w-bins per cm, y_lo, y-bins per cm) of the segment's 2-D grid
+//               over the drift coordinate w and the pad-row coordinate y; bin = iw * ny + iy
+//   bin_start[b] sorted position of the first cluster of bin b (exclusive prefix over all bins), so
+//               a w-column (all y of one w bin) is one contiguous position range, and a window is
+//               one contiguous range per w-column it touches
 //   links[p]    int2 (down, up) raw neighbour links; clinks[p] the cleaned (reciprocal) links
 //   starts[t]   start hits in canonical order (frame, sector, row-rank)
 //   slab[r*tcap + t]  sorted position of tracklet t's hit in row r (0xFFFFFFFF: none), written for
@@ -49,10 +51,12 @@ struct DevParams {
   float max_sin, y_margin, tan10;
   int nmin;
   float cov0[5];
-  float occ;                     // target clusters per w bin
+  float occ;                     // target clusters per grid bin
+  float aspect;                  // w/y extent of a grid bin (the neighbour window's aspect)
   float x[kNRow];                // row radii
   // neighbour windows per row r (valid for 1 <= r <= 150)
   float wy_dn[kNRow], ww_dn[kNRow], wy_up[kNRow], ww_up[kNRow], f_mid[kNRow];
+  float yext[kNRow];             // half extent of the grid in y: x * tan(10 deg) + 1 cm
 };
 
 struct FrameIn {
@@ -83,6 +87,8 @@ struct DevCounters {
   uint32_t n_sorted;      // clusters placed in the grid
   uint32_t n_tracks;
   uint32_t n_track_hits;
+  unsigned long long n_steps;         // tracklet row steps (propagations + candidate checks)
+  unsigned long long n_tracklet_hits; // hits fitted by all tracklets
   uint32_t wrange[2 * kMaxFrames];  // per frame (min, max) of w, order-preserving encoding
   uint32_t frame_start0[kMaxFrames + 1];  // first start index of each frame
   uint32_t frame_track0[kMaxFrames + 1];  // first track index of each frame
@@ -95,9 +101,10 @@ struct Work {
   const BatchDesc* batch;
   // grid
   uint32_t* seg_cnt;     // [scap]
-  uint32_t* seg_nb;      // [scap]  -> scanned in place into seg_bb
+  uint32_t* seg_nb;      // [scap]  bins of the segment (nw * ny), scanned into seg_bb
   uint32_t* seg_bb;      // [scap + 1]
-  float2* seg_geo;       // [scap]
+  uint2* seg_dim;        // [scap] (nw, ny)
+  float4* seg_geo;       // [scap] (w_lo, w-bins per cm, y_lo, y-bins per cm)
   uint32_t* bin_start;   // [bcap + 1]
   uint32_t* rank;        // [ncap]
   float2* hyw;           // [ncap + 2]
@@ -106,8 +113,9 @@ struct Work {
   int2* links;           // [ncap]
   int2* clinks;          // [ncap]
   uint32_t* seg_nstart;  // [scap + 1] -> scanned
-  uint4* starts_raw;     // [tcap] (hit, seg, bin, -)
+  uint4* starts_raw;     // [tcap] (hit, seg, first bin of its w-column, -)
   uint4* starts;         // [tcap] (hit, seg, rank-in-sector, -)
+  int4* chains;          // [tcap] (middle hit, last hit, chain length, -)
   // tracklets
   float* tl_state;       // [tcap][24]: P[5], C[15], chi2, x_ref, -, -
   uint32_t* tl_info;     // [tcap]: nhits | ref_row << 8 | top_row << 16 | ok << 24
@@ -133,12 +141,34 @@ __device__ __forceinline__ float ord2f(uint32_t u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
 }
 
-// bin of w in a segment grid with nb bins starting at wlo, inv bins per cm (monotone in w)
-__device__ __forceinline__ int bin_of(float w, float wlo, float inv, int nb) {
-  float t = (w - wlo) * inv;
+// bin of v along one grid axis with nb bins starting at lo, inv bins per cm (monotone in v)
+__device__ __forceinline__ int bin_of(float v, float lo, float inv, int nb) {
+  float t = (v - lo) * inv;
   if (!(t > 0.f)) return 0;
   if (t >= (float)nb) return nb - 1;
   return (int)t;
+}
+
+// Window of a segment grid: w-columns [iw0, iw1], y-bins [iy0, iy1], for |w - wc| <= Ww and
+// |y - yc| <= Wy (widened by a hair: the exact window test is done on the coordinates).
+struct GridWin {
+  int iw0, iw1, iy0, iy1, ny;
+  uint32_t bb;
+};
+__device__ __forceinline__ float win_pad(float c, float W);
+__device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const uint2* seg_dim, const float4* seg_geo,
+                                               int g, float yc, float wc, float Wy, float Ww) {
+  GridWin q;
+  const uint2 dim = seg_dim[g];
+  const float4 geo = seg_geo[g];
+  q.bb = seg_bb[g];
+  q.ny = (int)dim.y;
+  const float pw = win_pad(wc, Ww), py = win_pad(yc, Wy);
+  q.iw0 = bin_of((wc - Ww) - pw, geo.x, geo.y, (int)dim.x);
+  q.iw1 = bin_of((wc + Ww) + pw, geo.x, geo.y, (int)dim.x);
+  q.iy0 = bin_of((yc - Wy) - py, geo.z, geo.w, (int)dim.y);
+  q.iy1 = bin_of((yc + Wy) + py, geo.z, geo.w, (int)dim.y);
+  return q;
 }
 
 // conservative widening of a window for the bin lookup (rounding of w +- W)
@@ -211,20 +241,22 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
   const float c0 = sqrtf(1.0f - s0 * s0);
   const float c1 = sqrtf(1.0f - s1 * s1);
   const float N = s0 + s1, D = c0 + c1;
-  const float dy = dx * (N / D);
+  const float iD = 1.0f / D;
+  const float dy = dx * (N * iD);
   const float l = sqrtf(dx * dx + dy * dy);
   const float t = l * k * 0.5f;
   float a = l * arc_ratio(t);
   if (dx < 0.f) a = -a;
   const float tw = P[3];
-  const float DD = D * D;
-  const float dy_ds0 = dx * (2.0f / D + N * (s0 / c0 + s1 / c1) / DD);
-  const float dy_dk = dx * dx * (1.0f / D + N * s1 / (c1 * DD));
+  const float ic0 = 1.0f / c0, ic1 = 1.0f / c1, il = 1.0f / l;
+  const float iDD = iD * iD;
+  const float dy_ds0 = dx * (2.0f * iD + N * (s0 * ic0 + s1 * ic1) * iDD);
+  const float dy_dk = dx * dx * (iD + N * s1 * ic1 * iDD);
   float da_dl = 1.0f / sqrtf(1.0f - t * t);
   float da_dk = l * l * 0.5f * arc_ratio_deriv(t);
   if (dx < 0.f) { da_dl = -da_dl; da_dk = -da_dk; }
-  const float dl_ds0 = dy * dy_ds0 / l;
-  const float dl_dk = dy * dy_dk / l;
+  const float dl_ds0 = dy * dy_ds0 * il;
+  const float dl_dk = dy * dy_dk * il;
   const float J02 = dy_ds0;
   const float J04 = dy_dk * Q.kq;
   const float J12 = tw * (da_dl * dl_ds0);
@@ -256,11 +288,10 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
   }
   if (Q.ms_on && P[4] != 0.f) {
     const float one_tw2 = 1.0f + tw * tw;
-    const float pathf = sqrtf(one_tw2) / c1;
+    const float pathf = sqrtf(one_tw2) * ic1;
     const float xx0 = Q.x0_row * pathf;
-    const float p2 = one_tw2 / (P[4] * P[4]);
-    const float beta2 = p2 / (p2 + Q.mass2);
-    const float th2 = Q.ms_c * xx0 / (beta2 * p2);
+    const float q2 = P[4] * P[4] / one_tw2;
+    const float th2 = Q.ms_c * xx0 * q2 * (1.0f + Q.mass2 * q2);
     O[lt(2, 2)] = O[lt(2, 2)] + th2 * (c1 * c1) * one_tw2;
     O[lt(3, 3)] = O[lt(3, 3)] + th2 * one_tw2 * one_tw2;
   }
@@ -273,7 +304,8 @@ __device__ __forceinline__ float kf_chi2(const DevParams& Q, const float* P, con
   const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
   const float det = S00 * S11 - S01 * S10;
   if (!(det > 0.f)) return __int_as_float(0x7f800000);
-  const float i00 = S11 / det, i01 = -S01 / det, i10 = -S10 / det, i11 = S00 / det;
+  const float idet = 1.0f / det;
+  const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   const float r0 = ym - P[0], r1 = wm - P[1];
   return r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
 }
@@ -281,7 +313,8 @@ __device__ __forceinline__ float kf_chi2(const DevParams& Q, const float* P, con
 __device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C, float ym, float wm) {
   const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
   const float det = S00 * S11 - S01 * S10;
-  const float i00 = S11 / det, i01 = -S01 / det, i10 = -S10 / det, i11 = S00 / det;
+  const float idet = 1.0f / det;
+  const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   float K[5][2];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
