@@ -216,7 +216,10 @@ def main():
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
     h = tr.load(*d_in)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the tracking kernels are launched on it, and the step
+    # events are recorded on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
 
     for _ in range(args.warmup):
         tr.track(h, stream)

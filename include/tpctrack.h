@@ -73,8 +73,11 @@ typedef struct {
   int64_t hbm_budget;     /* serving admission budget in bytes (80 GB) */
   int32_t max_batch_frames; /* frames per batched launch (16) */
   int32_t use_graphs;     /* 1: replay the kernel sequence as a CUDA graph */
-  int32_t k5_block;       /* tracklet kernel threads per block (0 = autotuned) */
-  int32_t k2_block;       /* neighbour kernel threads per block (0 = autotuned) */
+  int32_t k2_tma;         /* 1: neighbour search stages adjacent rows in shared memory with bulk
+                             TMA copies; 0: it reads them through L1 (same results) */
+  int32_t k5_occupancy;   /* tracklet kernel variant: resident 128-thread blocks per SM it is
+                             compiled for (4 or 8; 0 = the autotuned choice) */
+  int32_t k5_longest_first; /* 1: tracklets are processed longest chain first (same results) */
 } tpc_params;
 
 /* Clusters of one time frame, structure of arrays in the caller's order (n entries each).

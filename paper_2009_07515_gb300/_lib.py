@@ -51,8 +51,9 @@ class tpc_params(ctypes.Structure):
         ("hbm_budget", ctypes.c_int64),
         ("max_batch_frames", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
-        ("k5_block", ctypes.c_int32),
-        ("k2_block", ctypes.c_int32),
+        ("k2_tma", ctypes.c_int32),
+        ("k5_occupancy", ctypes.c_int32),
+        ("k5_longest_first", ctypes.c_int32),
     ]
 
 

@@ -174,7 +174,16 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
     lo = min(lo, e);
     hi = max(hi, e);
   }
-  if (f >= 0 && lo <= hi) {
+  // lanes of a warp on the same frame combine their range first: one atomic pair per warp
+  const unsigned same = __match_any_sync(0xffffffffu, f);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint32_t lo2 = __shfl_xor_sync(0xffffffffu, lo, o), hi2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const int f2 = __shfl_xor_sync(0xffffffffu, f, o);
+    if (f2 == f) { lo = min(lo, lo2); hi = max(hi, hi2); }
+  }
+  const int leader = __ffs(same) - 1;
+  if ((int)(threadIdx.x & 31) == leader && f >= 0 && lo <= hi) {
     atomicMin(&W.cnt->wrange[2 * f], lo);
     atomicMax(&W.cnt->wrange[2 * f + 1], hi);
   }

@@ -127,19 +127,22 @@ __device__ __forceinline__ void pair_step(const Work& W, float yi, float wi, flo
   if (better) { best = chi; bd = d; bu = u; }
 }
 
-__global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q) {
+__global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use_tma) {
   __shared__ __align__(16) float2 stage[kK2Warps][2][kK2Slot + 2];
   __shared__ float2 ucand[kK2Warps][kK2UCap][32];
   __shared__ int upos[kK2Warps][kK2UCap][32];
   __shared__ __align__(8) uint64_t bar[kK2Warps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const BatchDesc* B = W.batch;
-  const int nseg = B->nf * kSegPerFrame;
   if (lane == 0) mbar_init(&bar[warp], 1);
   __syncwarp();
+  __shared__ int s_item;
   uint32_t parity = 0;
   bool aborted = false;
-  for (int g = blockIdx.x; g < nseg && !aborted; g += gridDim.x) {
+  for (;;) {
+    if (__syncthreads_or(aborted)) break;  // a timed-out copy wait ends the whole block
+    const int g = next_segment(&W.cnt->seg_next[0], B->nf, &s_item);
+    if (g < 0) break;
     const int r = (g % kSegPerFrame) % kNRow;
     const int a = (int)W.bin_start[W.seg_bb[g]];
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
@@ -167,10 +170,10 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q) {
         int p0, p1;
         column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), p0, p1);
         int q0 = p0 & ~1, q1 = (p1 + 1) & ~1;
-        if (q1 > q0 && q1 - q0 <= kK2Slot) { base0 = q0; cnt0 = q1 - q0; bytes += (uint32_t)cnt0 * 8u; }
+        if (use_tma && q1 > q0 && q1 - q0 <= kK2Slot) { base0 = q0; cnt0 = q1 - q0; bytes += (uint32_t)cnt0 * 8u; }
         column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), p0, p1);
         q0 = p0 & ~1; q1 = (p1 + 1) & ~1;
-        if (q1 > q0 && q1 - q0 <= kK2Slot) { base1 = q0; cnt1 = q1 - q0; bytes += (uint32_t)cnt1 * 8u; }
+        if (use_tma && q1 > q0 && q1 - q0 <= kK2Slot) { base1 = q0; cnt1 = q1 - q0; bytes += (uint32_t)cnt1 * 8u; }
         // the slots were read by this warp's previous chunk (generic proxy): order before the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bar[warp], bytes);
@@ -182,12 +185,12 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q) {
       base1 = __shfl_sync(0xffffffffu, base1, 0);
       cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
       if (!mbar_wait_bounded(&bar[warp], parity)) {
-        // give the copies in flight a second bounded wait before leaving
+        // give the copies in flight a second bounded wait, then stop using the stage
         (void)mbar_wait_bounded(&bar[warp], parity);
         if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
         aborted = true;
-        break;
       }
+      if (aborted) break;
       parity ^= 1u;
       const RowView vd{stage[warp][0], base0, cnt0};
       const RowView vu{stage[warp][1], base1, cnt1};
@@ -256,9 +259,11 @@ __device__ __forceinline__ int block_sum(int v, int* red) {
 
 __global__ void __launch_bounds__(256) k_clean(Work W, DevParams Q) {
   __shared__ int red[8];
+  __shared__ int s_item;
   const BatchDesc* B = W.batch;
-  const int nseg = B->nf * kSegPerFrame;
-  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+  for (;;) {
+    const int g = next_segment(&W.cnt->seg_next[1], B->nf, &s_item);
+    if (g < 0) break;
     const int a = (int)W.bin_start[W.seg_bb[g]];
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
     int count = 0;
@@ -280,11 +285,13 @@ __global__ void __launch_bounds__(256) k_clean(Work W, DevParams Q) {
 __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
   __shared__ int warp_off[8];
   __shared__ int s_total;
+  __shared__ int s_item;
   const BatchDesc* B = W.batch;
-  const int nseg = B->nf * kSegPerFrame;
   const uint32_t tcap = (uint32_t)W.tcap;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+  for (;;) {
+    const int g = next_segment(&W.cnt->seg_next[2], B->nf, &s_item);
+    if (g < 0) break;
     const int a = (int)W.bin_start[W.seg_bb[g]];
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
     uint32_t out = W.seg_nstart[g];

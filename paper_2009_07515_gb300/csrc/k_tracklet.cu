@@ -34,6 +34,29 @@ __global__ void __launch_bounds__(256) k_chains(Work W) {
       if ((m & 1) == 0) mid = W.clinks[mid].y;
     }
     W.chains[t] = make_int4(mid, head, m, 0);
+    if (W.len_cnt) atomicAdd(&W.len_cnt[kNRow - m], 1u);
+  }
+}
+
+// Processing order of the tracklet kernel: longest chain first (a counting sort by chain length;
+// the order inside a bucket is arbitrary, and no result depends on it: every tracklet reads only
+// the grid and the links and writes only its own outputs). It shortens the tail where few lanes
+// still run long tracklets.
+__global__ void k_length_offsets(Work W) {
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int k = 0; k <= kNRow; ++k) {
+      const uint32_t c = W.len_cnt[k];
+      W.len_cnt[k] = s;
+      s += c;
+    }
+  }
+}
+__global__ void __launch_bounds__(256) k_length_scatter(Work W) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+    const int m = W.chains[t].z;
+    W.order[atomicAdd(&W.len_cnt[kNRow - m], 1u)] = t;
   }
 }
 
@@ -88,7 +111,8 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
   return best;
 }
 
-__global__ void __launch_bounds__(128) k_tracklets(Work W, DevParams Q) {
+template <int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams Q, int ordered) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const long long tcap = W.tcap;
   float P[5], C[15], SP[5], SC[15];
@@ -108,7 +132,7 @@ __global__ void __launch_bounds__(128) k_tracklets(Work W, DevParams Q) {
         }
         break;
       }
-      t = (int)tn;
+      t = ordered ? (int)W.order[tn] : (int)tn;
       const uint4 st = W.starts[t];
       const int4 ch = W.chains[t];
       const int g = (int)st.y;
@@ -221,6 +245,18 @@ __global__ void __launch_bounds__(128) k_tracklets(Work W, DevParams Q) {
       }
     }
   }
+}
+
+// host-side launchers (the kernel templates stay in this translation unit)
+void launch_tracklets(int variant, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
+  if (variant == 8) k_tracklets<8><<<grid, 128, 0, s>>>(W, Q, ordered);
+  else k_tracklets<4><<<grid, 128, 0, s>>>(W, Q, ordered);
+}
+int tracklets_blocks_per_sm(int variant) {
+  int nb = 0;
+  if (variant == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<8>, 128, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<4>, 128, 0);
+  return nb;
 }
 
 }  // namespace tpc

@@ -30,12 +30,15 @@ __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
 __global__ void k_scatter(Work);
-__global__ void k_neighbours(Work, DevParams);
+__global__ void k_neighbours(Work, DevParams, int);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_starts(Work, DevParams);
 __global__ void k_start_order(Work);
 __global__ void k_chains(Work);
-__global__ void k_tracklets(Work, DevParams);
+__global__ void k_length_offsets(Work);
+__global__ void k_length_scatter(Work);
+void launch_tracklets(int variant, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered);
+int tracklets_blocks_per_sm(int variant);
 __global__ void k_votes(Work, DevParams);
 __global__ void k_kept(Work, DevParams);
 __global__ void k_write_tracks(Work, DevParams);
@@ -108,7 +111,7 @@ struct tpc_ctx {
   tpc_frame_t next_id = 1;
   std::string err;
   std::vector<std::shared_ptr<Workspace>> wspool;
-  int grid_neighbours = 0, grid_tracklets = 0;
+  int grid_neighbours = 0, grid_tracklets = 0, k5_variant = 4;
   bool timing = false;
   cudaEvent_t ev[kNumKernels + 1] = {nullptr};
   cudaEvent_t ev_sync = nullptr;
@@ -231,6 +234,8 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.starts_raw, 16 * (size_t)ws->tcap},
       {(void**)&W.starts, 16 * (size_t)ws->tcap},
       {(void**)&W.chains, 16 * (size_t)ws->tcap},
+      {(void**)&W.order, 4 * (size_t)ws->tcap},
+      {(void**)&W.len_cnt, 4 * (size_t)(kNRow + 2)},
       {(void**)&W.tl_state, 96 * (size_t)ws->tcap},
       {(void**)&W.tl_info, 4 * (size_t)ws->tcap},
       {(void**)&W.slab, 4 * (size_t)kNRow * (size_t)ws->tcap},
@@ -346,7 +351,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // scatter
   ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W);
   mark(ki++);  // neighbours
-  ++nl; k_neighbours<<<ctx->grid_neighbours, 256, 0, s>>>(W, Q);
+  ++nl; k_neighbours<<<ctx->grid_neighbours, 256, 0, s>>>(W, Q, ctx->p.k2_tma);
   mark(ki++);  // clean
   ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_start
@@ -357,9 +362,17 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // start_order
   ++nl; k_start_order<<<2 * G, 256, 0, s>>>(W);
   mark(ki++);  // chains
-  ++nl; k_chains<<<4 * G, 256, 0, s>>>(W);
+  const bool ordered = ctx->p.k5_longest_first != 0;
+  if (ordered) { ++nl; k_zero_u32<<<1, 256, 0, s>>>(W.len_cnt, nullptr, kNRow + 1, 0, 1); }
+  Work Wc = W;
+  if (!ordered) Wc.len_cnt = nullptr;
+  ++nl; k_chains<<<4 * G, 256, 0, s>>>(Wc);
+  if (ordered) {
+    ++nl; k_length_offsets<<<1, 32, 0, s>>>(W);
+    ++nl; k_length_scatter<<<4 * G, 256, 0, s>>>(W);
+  }
   mark(ki++);  // tracklets
-  ++nl; k_tracklets<<<ctx->grid_tracklets, 128, 0, s>>>(W, Q);
+  ++nl; launch_tracklets(ctx->k5_variant, ctx->grid_tracklets, s, W, Q, ordered ? 1 : 0);
   mark(ki++);  // zero_w
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
   mark(ki++);  // votes
@@ -425,7 +438,8 @@ int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::
   if (ctx->p.use_graphs && !timing) {
     // one graph per workspace; its kernels read every size from the descriptor in device memory
     if (!ws->graph) {
-      cudaStream_t cs = s;
+      // capture on the context's (non-default) stream; replays may go to any stream
+      cudaStream_t cs = ctx->stream;
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
       rc = enqueue_sequence(ctx, *ws, cs, false);
@@ -594,8 +608,9 @@ void tpc_default_params(tpc_params* p) {
   p->hbm_budget = 80LL << 30;
   p->max_batch_frames = 16;
   p->use_graphs = 1;
-  p->k5_block = 128;
-  p->k2_block = 256;
+  p->k2_tma = 1;
+  p->k5_occupancy = 8;
+  p->k5_longest_first = 0;
 }
 
 const char* tpc_version(void) { return "tpctrack 0.1 (sm_103a)"; }
@@ -635,7 +650,8 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     int nb = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours, 256, 0);
     ctx->grid_neighbours = ctx->sms * std::max(nb, 1);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets, 128, 0);
+    ctx->k5_variant = ctx->p.k5_occupancy == 4 ? 4 : 8;
+    nb = tracklets_blocks_per_sm(ctx->k5_variant);
     ctx->grid_tracklets = ctx->sms * std::max(nb, 1);
     for (int k = 0; k < 2; ++k) {
       cudaStream_t s;
@@ -688,19 +704,15 @@ int tpc_track_batch(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, v
       if (g == f) return fail(ctx, TPC_E_INVAL, "frame listed twice");
     fr.push_back(f);
   }
-  // The kernels run on the context's stream (graph capture needs a non-default stream); work the
-  // caller queued on its own stream (e.g. producing borrowed device inputs) is waited for first,
-  // and the caller's stream waits for the tracking.
-  cudaStream_t user = (cudaStream_t)cuda_stream;
-  if (user) {
-    CK(cudaEventRecord(ctx->ev_sync, user));
-    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_sync, 0));
+  // The kernels run on the caller's stream (NULL: the context's stream), after the uploads that
+  // tpc_load_clusters queued on the context's stream.
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  if (s != ctx->stream) {
+    CK(cudaEventRecord(ctx->ev_sync, ctx->stream));
+    CK(cudaStreamWaitEvent(s, ctx->ev_sync, 0));
   }
   std::shared_ptr<Workspace> ws;
-  int rc = run_batch(ctx, fr, ctx->stream, ws);
-  if (rc) return rc;
-  if (user) CK(cudaStreamWaitEvent(user, ws->done, 0));
-  return TPC_OK;
+  return run_batch(ctx, fr, s, ws);
 }
 
 int tpc_track_sectors(tpc_ctx* ctx, tpc_frame_t frame, void* cuda_stream) {

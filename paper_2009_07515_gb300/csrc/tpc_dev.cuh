@@ -83,6 +83,7 @@ struct DevCounters {
   uint32_t n_starts;      // start hits found (may exceed tcap: overflow)
   uint32_t n_tracklets;   // min(n_starts, tcap)
   uint32_t k5_next;       // work counter of the tracklet kernel
+  uint32_t seg_next[3];   // segment work counters of the neighbour, cleaning and start kernels
   uint32_t n_bins;        // total bins of the batch
   uint32_t n_sorted;      // clusters placed in the grid
   uint32_t n_tracks;
@@ -116,6 +117,8 @@ struct Work {
   uint4* starts_raw;     // [tcap] (hit, seg, first bin of its w-column, -)
   uint4* starts;         // [tcap] (hit, seg, rank-in-sector, -)
   int4* chains;          // [tcap] (middle hit, last hit, chain length, -)
+  uint32_t* order;       // [tcap] processing order of the tracklet kernel (longest chain first)
+  uint32_t* len_cnt;     // [kNRow + 1] chain-length histogram, then bucket cursors
   // tracklets
   float* tl_state;       // [tcap][24]: P[5], C[15], chi2, x_ref, -, -
   uint32_t* tl_info;     // [tcap]: nhits | ref_row << 8 | top_row << 16 | ok << 24
@@ -183,6 +186,26 @@ __device__ __forceinline__ bool key_less(float wa, float ya, uint32_t oa, float 
   if (ya < yb) return true;
   if (ya > yb) return false;
   return oa < ob;
+}
+
+// Segment work item k -> segment: rows 1..150 first, inner (denser) rows first, all sectors and
+// frames of a row together; the boundary rows 0 and 151 last.
+__device__ __forceinline__ int segment_of_item(int k, int nf) {
+  const int per_row = nf * kNSec;
+  int ri = k / per_row;
+  const int rest = k - ri * per_row;
+  const int f = rest / kNSec, sec = rest - f * kNSec;
+  const int r = ri < kNRow - 2 ? ri + 1 : (ri == kNRow - 2 ? 0 : kNRow - 1);
+  return f * kSegPerFrame + sec * kNRow + r;
+}
+
+// Dynamic segment assignment: thread 0 of the block takes the next work item.
+__device__ __forceinline__ int next_segment(uint32_t* counter, int nf, int* s_item) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
+  __syncthreads();
+  const int k = *s_item;
+  return k < nf * kSegPerFrame ? segment_of_item(k, nf) : -1;
 }
 
 __device__ __forceinline__ int frame_of(const BatchDesc* B, long long i) {
