@@ -173,6 +173,33 @@ int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n);
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable);
 int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 
+/* Largest frame (clusters) that tpc_links_static() accepts. */
+#define TPC_STATIC_MAX_CLUSTERS 262144
+
+/* Cleaned neighbour links of one frame, computed without allocating any device memory. The paper
+ * has no counterpart to this call; it exists for callers that cannot allocate device memory at the
+ * moment they call: code running while another allocator (e.g. a framework's caching allocator)
+ * owns the device's memory, code under a real-time or allocation-free rule (cudaMalloc/cudaFree
+ * synchronise the device and may fail), or code that must not enter the allocator from where it
+ * runs. It runs the search-grid, neighbour and cleaning kernels of tpc_track_sectors() on one frame,
+ * with all of their scratch in one fixed-size array that is part of the library's device image
+ * (about 10.3 MiB, held on every GPU that loads the library until the process exits), and writes the
+ * same cleaned links that tpc_get_links(what = 2 / 3) returns after tracking the frame.
+ *   p         method parameters (NULL: defaults); bin_occupancy below 1 is refused (TPC_E_CAPACITY)
+ *   clusters  one frame, on_device = 1 (device pointers, caller-owned, read during the call)
+ *   up, down  caller-owned device arrays of clusters->n int32: the input index of the linked
+ *             cluster in the next / previous row, or -1
+ *   cuda_stream  stream to run on (NULL: the legacy default stream)
+ * Returns TPC_OK once the links are written (the call waits, at most two minutes, for its kernels),
+ * TPC_E_CAPACITY if clusters->n > TPC_STATIC_MAX_CLUSTERS, TPC_E_INVAL for bad arguments or
+ * malformed clusters, TPC_E_TIMEOUT, or TPC_E_CUDA. All calls share the one scratch array, which
+ * keeps the previous call's contents (each call clears what must start at zero); calls that overlap
+ * on the GPU, from two host threads or on two streams, race on it and must be serialised by the
+ * caller. The first call on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * creates its completion event; make that first call before any stream capture. */
+int tpc_links_static(const tpc_params* p, const tpc_clusters* clusters, int32_t* up, int32_t* down,
+                     void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

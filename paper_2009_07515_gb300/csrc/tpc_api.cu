@@ -49,6 +49,53 @@ __global__ void k_set_ntracklets(Work);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
 }  // namespace tpc
 
+namespace tpc {
+// Host-side derived constants: computed in double, rounded once; row geometry and window sizes in
+// float arithmetic exactly as they are defined (IEEE operations on the host).
+void make_dev_params(const tpc_params& p, DevParams& d) {
+  memset(&d, 0, sizeof(d));
+  d.kq = (float)(-0.0029979246 * p.bz);
+  d.chi_n_max = (float)p.chi_n_max;
+  d.lmin = p.lmin;
+  d.r00 = (float)(p.sigma_y * p.sigma_y);
+  d.r11 = (float)(p.sigma_w * p.sigma_w);
+  d.chi2_max = (float)p.chi2_hit_max;
+  d.n_miss_max = p.n_miss_max;
+  d.win_nsig = (float)p.win_nsig;
+  d.win_add = (float)p.win_add;
+  d.ms_on = p.x0_per_row > 0;
+  d.x0_row = (float)p.x0_per_row;
+  const double hl = p.x0_per_row > 0 ? 0.0136 * (1.0 + 0.038 * std::log(p.x0_per_row)) : 0.0;
+  d.ms_c = (float)(hl * hl);
+  d.mass2 = (float)(0.13957039 * 0.13957039);
+  d.max_sin = (float)p.max_sin;
+  d.y_margin = (float)p.y_margin;
+  d.tan10 = (float)0.17632698070846498;
+  d.nmin = p.nmin;
+  for (int i = 0; i < 5; ++i) d.cov0[i] = (float)p.cov0[i];
+  d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
+  volatile float pitch = (float)160 / (float)151;
+  for (int r = 0; r < kNRow; ++r) {
+    volatile float xr = (float)r * pitch;
+    d.x[r] = (float)85 + xr;
+  }
+  const float ky = (float)p.ky, kw = (float)p.kw, eps = (float)p.eps;
+  for (int r = 1; r + 1 < kNRow; ++r) {
+    volatile float dxm = d.x[r] - d.x[r - 1];
+    volatile float dxp = d.x[r + 1] - d.x[r];
+    volatile float a = ky * dxm, b = kw * dxm, c = ky * dxp, e = kw * dxp, s = dxm + dxp;
+    d.wy_dn[r] = a + eps;
+    d.ww_dn[r] = b + eps;
+    d.wy_up[r] = c + eps;
+    d.ww_up[r] = e + eps;
+    d.f_mid[r] = dxm / s;
+  }
+  for (int r = 0; r < kNRow; ++r) d.yext[r] = d.x[r] * d.tan10 + 1.0f;
+  d.aspect = (float)((p.kw * (160.0 / 151.0) + p.eps) / (p.ky * (160.0 / 151.0) + p.eps));
+}
+
+}  // namespace tpc
+
 using namespace tpc;
 
 namespace {
@@ -144,50 +191,6 @@ int fail(tpc_ctx* c, int code, const std::string& msg) {
     if (e_ != cudaSuccess)                                                                \
       return fail(ctx, TPC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
   } while (0)
-
-// Host-side derived constants: computed in double, rounded once; row geometry and window sizes in
-// float arithmetic exactly as they are defined (IEEE operations on the host).
-void make_dev_params(const tpc_params& p, DevParams& d) {
-  memset(&d, 0, sizeof(d));
-  d.kq = (float)(-0.0029979246 * p.bz);
-  d.chi_n_max = (float)p.chi_n_max;
-  d.lmin = p.lmin;
-  d.r00 = (float)(p.sigma_y * p.sigma_y);
-  d.r11 = (float)(p.sigma_w * p.sigma_w);
-  d.chi2_max = (float)p.chi2_hit_max;
-  d.n_miss_max = p.n_miss_max;
-  d.win_nsig = (float)p.win_nsig;
-  d.win_add = (float)p.win_add;
-  d.ms_on = p.x0_per_row > 0;
-  d.x0_row = (float)p.x0_per_row;
-  const double hl = p.x0_per_row > 0 ? 0.0136 * (1.0 + 0.038 * std::log(p.x0_per_row)) : 0.0;
-  d.ms_c = (float)(hl * hl);
-  d.mass2 = (float)(0.13957039 * 0.13957039);
-  d.max_sin = (float)p.max_sin;
-  d.y_margin = (float)p.y_margin;
-  d.tan10 = (float)0.17632698070846498;
-  d.nmin = p.nmin;
-  for (int i = 0; i < 5; ++i) d.cov0[i] = (float)p.cov0[i];
-  d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
-  volatile float pitch = (float)160 / (float)151;
-  for (int r = 0; r < kNRow; ++r) {
-    volatile float xr = (float)r * pitch;
-    d.x[r] = (float)85 + xr;
-  }
-  const float ky = (float)p.ky, kw = (float)p.kw, eps = (float)p.eps;
-  for (int r = 1; r + 1 < kNRow; ++r) {
-    volatile float dxm = d.x[r] - d.x[r - 1];
-    volatile float dxp = d.x[r + 1] - d.x[r];
-    volatile float a = ky * dxm, b = kw * dxm, c = ky * dxp, e = kw * dxp, s = dxm + dxp;
-    d.wy_dn[r] = a + eps;
-    d.ww_dn[r] = b + eps;
-    d.wy_up[r] = c + eps;
-    d.ww_up[r] = e + eps;
-    d.f_mid[r] = dxm / s;
-  }
-  for (int r = 0; r < kNRow; ++r) d.yext[r] = d.x[r] * d.tan10 + 1.0f;
-  d.aspect = (float)((p.kw * (160.0 / 151.0) + p.eps) / (p.ky * (160.0 / 151.0) + p.eps));
-}
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -302,16 +305,6 @@ int get_workspace(tpc_ctx* ctx, long long ntot, int nf, std::shared_ptr<Workspac
   return TPC_OK;
 }
 
-struct Launcher {
-  tpc_ctx* ctx;
-  cudaStream_t s;
-  bool timing;
-  int k = 0;
-  void begin(int idx) {
-    k = idx;
-    if (timing) cudaEventRecord(ctx->ev[idx], s);
-  }
-};
 
 // Enqueue the whole kernel sequence for the batch described in ws->h_desc (already uploaded).
 int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
