@@ -183,7 +183,7 @@ int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
  * synchronise the device and may fail), or code that must not enter the allocator from where it
  * runs. It runs the search-grid, neighbour and cleaning kernels of tpc_track_sectors() on one frame,
  * with all of their scratch in one fixed-size array that is part of the library's device image
- * (about 10.3 MiB, held on every GPU that loads the library until the process exits), and writes the
+ * (about 17.9 MiB, held on every GPU that loads the library until the process exits), and writes the
  * same cleaned links that tpc_get_links(what = 2 / 3) returns after tracking the frame.
  *   p         method parameters (NULL: defaults); bin_occupancy below 1 is refused (TPC_E_CAPACITY)
  *   clusters  one frame, on_device = 1 (device pointers, caller-owned, read during the call)

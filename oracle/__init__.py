@@ -23,6 +23,7 @@ _lock = threading.Lock()
 _libs: dict = {}
 
 BRUTE_FORCE = 1
+PACKED = 2
 
 
 def _lib_path(precision: str) -> str:
@@ -113,6 +114,7 @@ def _load(precision: str):
     f.restype = ctypes.c_double
     f = getattr(lib, pre + "seed"); f.argtypes = [_P(Params), _f64p, _f64p]; f.restype = ctypes.c_int
     f = getattr(lib, pre + "asin"); f.argtypes = [ctypes.c_double]; f.restype = ctypes.c_double
+    f = getattr(lib, pre + "pack"); f.argtypes = [_f64p, _f64p]; f.restype = None
     f = getattr(lib, pre + "row_x"); f.argtypes = [ctypes.c_int]; f.restype = ctypes.c_double
     _libs[precision] = lib
     return lib
@@ -184,7 +186,7 @@ def _copy(ptr, n, dtype, shape=None):
 
 
 def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = None,
-          brute_force: bool = False, n_threads: int = 0) -> Result:
+          brute_force: bool = False, packed: bool = False, n_threads: int = 0) -> Result:
     """Run the oracle tracker on one frame (clusters in caller order)."""
     lib = _load(precision)
     pre = f"oracle_{precision}_"
@@ -201,7 +203,7 @@ def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = 
     rc = getattr(lib, pre + "track")(
         ctypes.byref(params), n, sector.ctypes.data_as(_P(ctypes.c_uint8)),
         row.ctypes.data_as(_P(ctypes.c_uint8)), y.ctypes.data_as(_f64p), w.ctypes.data_as(_f64p),
-        BRUTE_FORCE if brute_force else 0, int(n_threads), ctypes.byref(rp))
+        (BRUTE_FORCE if brute_force else 0) | (PACKED if packed else 0), int(n_threads), ctypes.byref(rp))
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
     try:
@@ -271,6 +273,13 @@ def seed(h, *, precision="f64", params: Params | None = None):
 
 def asin(t: float, *, precision="f64") -> float:
     return getattr(_load(precision), f"oracle_{precision}_asin")(float(t))
+
+
+def pack(y: float, w: float, *, precision="f32"):
+    """(y, w) read back through the 16-bit cluster storage format."""
+    a, b = ctypes.c_double(y), ctypes.c_double(w)
+    getattr(_load(precision), f"oracle_{precision}_pack")(ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
 
 
 def row_x(r: int, *, precision="f64") -> float:

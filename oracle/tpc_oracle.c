@@ -43,10 +43,12 @@
 #ifdef ORACLE_F32
 typedef float real;
 #define SQRT sqrtf
+#define RINT rintf
 #define ORACLE_SYM(name) oracle_f32_##name
 #else
 typedef double real;
 #define SQRT sqrt
+#define RINT rint
 #define ORACLE_SYM(name) oracle_f64_##name
 #endif
 
@@ -135,6 +137,20 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
 
 static inline real absr(real v) { return v < 0 ? -v : v; }
 
+/* 16-bit fixed-point cluster storage (Sec. 4 of the paper: custom formats that keep only the bits
+ * the intrinsic resolution needs). y is stored as qy = rint((y + 64) * 512) clamped to [0, 65535],
+ * read back as qy / 512 - 64; w is stored as a 16-bit offset, in steps of 2^-9 cm, from the lower
+ * edge of its search-grid bin (bins are aligned power-of-two widths of at most 128 cm), which reads
+ * back as rint(512 w) / 512 whatever the bin. Both read-back values are exact floats for
+ * |w| < 32768 cm; the tracker then sees only them. */
+static void pack_roundtrip(real* y, real* w) {
+  real qy = RINT((*y + (real)64) * (real)512);
+  if (qy < 0) qy = 0;
+  if (qy > 65535) qy = 65535;
+  *y = qy * ((real)1 / (real)512) - (real)64;
+  *w = RINT(*w * (real)512) * ((real)1 / (real)512);
+}
+
 /* Relative distance of a decision variable from its cut, for tracing disagreements. */
 static inline void note_margin(double* m, real value, real cut) {
   if (!m) return;
@@ -183,6 +199,14 @@ static real arc_ratio_deriv(real t) {
 }
 
 double ORACLE_SYM(asin)(double t) { return (double)asin_hr((real)t); }
+
+/* the 16-bit storage round trip of one cluster's (y, w) */
+void ORACLE_SYM(pack)(double* y, double* w) {
+  real a = (real)*y, b = (real)*w;
+  pack_roundtrip(&a, &b);
+  *y = a;
+  *w = b;
+}
 
 /* ------------------------------------------------------------------------------------------------
  * Small dense linear algebra (5x5), written out plainly.
@@ -438,6 +462,8 @@ typedef struct {
 } oracle_result;
 
 #define ORACLE_BRUTE_FORCE 1
+#define ORACLE_PACKED 2
+
 
 typedef struct {
   int64_t n;                 /* clusters of this sector */
@@ -788,7 +814,8 @@ static void free_sector(sector_t* S) {
 }
 
 /* Track one frame. Inputs: n clusters in caller order (sector, row, y, w); y and w are given in
- * double and rounded to REAL on entry. flags: ORACLE_BRUTE_FORCE scans whole rows in the neighbour
+ * double and rounded to REAL on entry. flags: ORACLE_PACKED reads them back through the 16-bit
+ * storage format first; ORACLE_BRUTE_FORCE scans whole rows in the neighbour
  * search instead of the sorted-w index. n_threads > 0 runs sectors in parallel (sectors are
  * independent). Returns 0, or -1 for malformed input, -2 for allocation failure. */
 int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, const uint8_t* row,
@@ -825,6 +852,7 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
       sector_t* S = &secs[sector[i]];
       int64_t o = fill[sector[i]][row[i]]++;
       S->orig[o] = (int32_t)i; S->y[o] = (real)y[i]; S->w[o] = (real)w[i];
+      if (flags & ORACLE_PACKED) pack_roundtrip(&S->y[o], &S->w[o]);
     }
   }
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)

@@ -145,6 +145,34 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* in,
 }
 
 // ------------------------------------------------------------------------------------ K1
+// One input cluster, validated; in the 16-bit storage its coordinates are replaced by their
+// read-back values (y = rint(512 (y + 64)) / 512 - 64 clamped, w = rint(512 w) / 512), which the
+// grid bins and every later kernel then use. The storage needs |w| < 32768 cm.
+struct InHit {
+  int g;
+  float y, w;
+  bool ok;
+};
+__device__ __forceinline__ InHit read_input(const BatchDesc* B, int packed, long long i, int& fi, long long& j) {
+  fi = frame_of(B, i);
+  const FrameIn& F = B->f[fi];
+  j = i - F.off;
+  InHit h;
+  const int s = F.sector[j], r = F.row[j];
+  h.y = F.y[j];
+  h.w = F.w[j];
+  h.ok = s < kNSec && r < kNRow && isfinite(h.y) && isfinite(h.w);
+  if (h.ok && packed) {
+    h.ok = fabsf(h.w) < 32767.0f;
+    float qy = rintf((h.y + 64.0f) * 512.0f);
+    qy = fminf(fmaxf(qy, 0.0f), 65535.0f);
+    h.y = qy * (1.0f / 512.0f) - 64.0f;
+    h.w = rintf(h.w * 512.0f) * (1.0f / 512.0f);
+  }
+  h.g = fi * kSegPerFrame + s * kNRow + r;
+  return h;
+}
+
 // Clusters are processed in contiguous block chunks so a block rarely spans two frames.
 __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
   const BatchDesc* B = W.batch;
@@ -156,7 +184,9 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
   uint32_t lo = 0xFFFFFFFFu, hi = 0u;
   bool bad = false;
   for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    int fi = frame_of(B, i);
+    int fi;
+    long long j;
+    const InHit h = read_input(B, W.packed, i, fi, j);
     if (fi != f) {
       if (f >= 0 && lo <= hi) {
         atomicMin(&W.cnt->wrange[2 * f], lo);
@@ -164,13 +194,9 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
       }
       f = fi; lo = 0xFFFFFFFFu; hi = 0u;
     }
-    const FrameIn& F = B->f[fi];
-    const long long j = i - F.off;
-    const int s = F.sector[j], r = F.row[j];
-    const float y = F.y[j], w = F.w[j];
-    if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) { bad = true; continue; }
-    atomicAdd(&W.seg_cnt[fi * kSegPerFrame + s * kNRow + r], 1u);
-    const uint32_t e = f2ord(w);
+    if (!h.ok) { bad = true; continue; }
+    atomicAdd(&W.seg_cnt[h.g], 1u);
+    const uint32_t e = f2ord(h.w);
     lo = min(lo, e);
     hi = max(hi, e);
   }
@@ -190,8 +216,11 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
   if (bad) atomicOr(&W.cnt->err, kErrInput);
 }
 
-// one thread per segment: a grid of ~n/occ bins, nw x ny, with bins shaped like the neighbour
-// window (w/y size ratio `aspect`)
+// One thread per segment: a grid of ~n/occ bins, nw x ny, bins shaped like the neighbour window
+// (w/y size ratio `aspect`). The w-columns have a power-of-two width 2^k cm (-3 <= k <= 7, nearest
+// to the occupancy target) and are aligned to multiples of it, so a cluster's 16-bit w offset
+// from its column's lower edge always fits. A segment has at most 4 ceil(n/occ) + 260 bins, or 513
+// in the 16-bit storage when a sparse segment spans the whole w range.
 __global__ void __launch_bounds__(256) k_seg_layout(Work W, DevParams Q) {
   const BatchDesc* B = W.batch;
   const int nseg = B->nf * kSegPerFrame;
@@ -215,19 +244,34 @@ __global__ void __launch_bounds__(256) k_seg_layout(Work W, DevParams Q) {
       ny = fy < 1.f ? 1u : (fy > 64.f ? 64u : (uint32_t)(fy + 0.5f));
       if (ny > nbins) ny = nbins;
     }
-    const uint32_t nw = (nbins + ny - 1) / ny;
+    // column width: the power of two nearest (in log) to the occupancy's width; coarser while a
+    // sparse segment would get many more columns than bins (up to 128 cm in the 16-bit storage,
+    // where |w| < 32768 cm keeps it below 513 columns)
+    const float bw_want = wext > 0.f ? wext / (float)((nbins + ny - 1) / ny) : 128.f;
+    const int kmax = W.packed ? 7 : 30;
+    int k = 7;
+    while (k > -3 && ldexpf(1.41421356f, k - 1) > bw_want) --k;
+    int iw0 = (int)floorf(ldexpf(wlo, -k)), iw1 = (int)floorf(ldexpf(whi, -k));
+    while ((uint32_t)(iw1 - iw0 + 1) > max(4u * nbins, 64u) + 16u && k < kmax) {
+      ++k;
+      iw0 = (int)floorf(ldexpf(wlo, -k));
+      iw1 = (int)floorf(ldexpf(whi, -k));
+    }
+    const uint32_t nw = (uint32_t)(iw1 - iw0 + 1);
+    const uint32_t budget = 4u * nbins + 260u;
+    if (nw * ny > budget) ny = max(1u, budget / nw);
     W.seg_nb[g] = nw * ny;
-    W.seg_dim[g] = make_uint2(nw, ny);
-    W.seg_geo[g] = make_float4(wlo, wext > 0.f ? (float)nw / wext : 0.f, -Q.yext[r], (float)ny / yext);
+    W.seg_dim[g] = make_int4((int)nw, (int)ny, iw0, k + 9);
+    W.seg_geo[g] = make_float4(ldexpf((float)iw0, k), ldexpf(1.0f, -k), -Q.yext[r], (float)ny / yext);
   }
 }
 
-__device__ __forceinline__ uint32_t seg_bin(const Work& W, int g, float y, float w) {
-  const uint2 dim = W.seg_dim[g];
+__device__ __forceinline__ uint32_t seg_bin(const Work& W, int g, float y, float w, int& iw) {
+  const int4 dim = W.seg_dim[g];
   const float4 geo = W.seg_geo[g];
-  const int iw = bin_of(w, geo.x, geo.y, (int)dim.x);
-  const int iy = bin_of(y, geo.z, geo.w, (int)dim.y);
-  return W.seg_bb[g] + (uint32_t)(iw * (int)dim.y + iy);
+  iw = bin_of(w, geo.x, geo.y, dim.x);
+  const int iy = bin_of(y, geo.z, geo.w, dim.y);
+  return W.seg_bb[g] + (uint32_t)(iw * dim.y + iy);
 }
 
 __global__ void __launch_bounds__(256) k_bin_rank(Work W) {
@@ -239,14 +283,11 @@ __global__ void __launch_bounds__(256) k_bin_rank(Work W) {
     return;
   }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x) {
-    const int fi = frame_of(B, i);
-    const FrameIn& F = B->f[fi];
-    const long long j = i - F.off;
-    const int s = F.sector[j], r = F.row[j];
-    const float y = F.y[j], w = F.w[j];
-    if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) continue;
-    const int g = fi * kSegPerFrame + s * kNRow + r;
-    W.rank[i] = atomicAdd(&W.bin_start[seg_bin(W, g, y, w)], 1u);
+    int fi, iw;
+    long long j;
+    const InHit h = read_input(B, W.packed, i, fi, j);
+    if (!h.ok) continue;
+    W.rank[i] = atomicAdd(&W.bin_start[seg_bin(W, h.g, h.y, h.w, iw)], 1u);
   }
 }
 
@@ -255,15 +296,20 @@ __global__ void __launch_bounds__(256) k_scatter(Work W) {
   const long long ntot = B->ntot;
   if (W.cnt->n_bins > (uint32_t)W.bcap) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x) {
-    const int fi = frame_of(B, i);
-    const FrameIn& F = B->f[fi];
-    const long long j = i - F.off;
-    const int s = F.sector[j], r = F.row[j];
-    const float y = F.y[j], w = F.w[j];
-    if (s >= kNSec || r >= kNRow || !isfinite(y) || !isfinite(w)) continue;
-    const int g = fi * kSegPerFrame + s * kNRow + r;
-    const uint32_t p = W.bin_start[seg_bin(W, g, y, w)] + W.rank[i];
-    W.hyw[p] = make_float2(y, w);
+    int fi, iw;
+    long long j;
+    const InHit h = read_input(B, W.packed, i, fi, j);
+    if (!h.ok) continue;
+    const uint32_t p = W.bin_start[seg_bin(W, h.g, h.y, h.w, iw)] + W.rank[i];
+    if (W.packed) {
+      const int4 dim = W.seg_dim[h.g];
+      const uint32_t qy = (uint32_t)rintf((h.y + 64.0f) * 512.0f);
+      const int qw = (int)rintf(h.w * 512.0f) - col_base(dim.z, dim.w, iw);
+      W.hq[p] = qy | ((uint32_t)qw << 16);
+      W.hcol[p] = (uint16_t)iw;
+    } else {
+      W.hyw[p] = make_float2(h.y, h.w);
+    }
     W.horig[p] = (uint32_t)j;
   }
 }

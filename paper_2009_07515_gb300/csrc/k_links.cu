@@ -53,36 +53,41 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
-// Find the best (d, u) pair of hit (yi, wi, oi); rows given as [p0, p1) position ranges, each read
-// from shared memory (stage, base) when the range lies inside the stage, else from global memory.
+// A row range staged in shared memory: positions [base, base + count) (FP32 float2 records, or
+// 16-bit uint32 records); positions outside it are read from global memory.
 struct RowView {
-  const float2* stage;
-  int base, count;  // staged positions [base, base + count)
+  const void* stage;
+  int base, count;
 };
 
-__device__ __forceinline__ float2 load_hit(const Work& W, const RowView& v, int p) {
-  if (p >= v.base && p < v.base + v.count) return v.stage[p - v.base];
+template <bool kPacked>
+__device__ __forceinline__ float2 load_cand(const Work& W, const RowView& v, int p, int cbase) {
+  if (kPacked) {
+    const uint32_t q = (p >= v.base && p < v.base + v.count) ? ((const uint32_t*)v.stage)[p - v.base] : W.hq[p];
+    return unpack_hit(q, cbase);
+  }
+  if (p >= v.base && p < v.base + v.count) return ((const float2*)v.stage)[p - v.base];
   return W.hyw[p];
 }
 
-__device__ __forceinline__ bool pair_key_less(const Work& W, int d, int u, int bd, int bu) {
-  // tie of chi_n: smaller (w, y, input index) of d, then of u
-  if (d != bd) {
-    const float2 a = W.hyw[d], b = W.hyw[bd];
-    return key_less(a.y, a.x, W.horig[d], b.y, b.x, W.horig[bd]);
-  }
-  const float2 a = W.hyw[u], b = W.hyw[bu];
-  return key_less(a.y, a.x, W.horig[u], b.y, b.x, W.horig[bu]);
+// tie of chi_n: smaller (w, y, input index) of d, then of u (d, bd in segment gd; u, bu in gu)
+template <bool kPacked>
+__device__ __forceinline__ bool pair_key_less(const Work& W, int gd, int gu, int d, int u, int bd, int bu) {
+  const int g = d != bd ? gd : gu;
+  const int x = d != bd ? d : u, y = d != bd ? bd : bu;
+  const float2 a = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, x);
+  const float2 b = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, y);
+  return key_less(a.y, a.x, W.horig[x], b.y, b.x, W.horig[y]);
 }
 
 // positions of the w-columns of segment g touched by |w - wc| <= W for wc in [lo, hi]
 __device__ __forceinline__ void column_range(const Work& W, int g, float lo, float hi, int& p0, int& p1) {
-  const uint2 dim = W.seg_dim[g];
+  const int4 dim = W.seg_dim[g];
   const float4 geo = W.seg_geo[g];
   const uint32_t bb = W.seg_bb[g];
-  const int iw0 = bin_of(lo, geo.x, geo.y, (int)dim.x), iw1 = bin_of(hi, geo.x, geo.y, (int)dim.x);
-  p0 = (int)W.bin_start[bb + (uint32_t)(iw0 * (int)dim.y)];
-  p1 = (int)W.bin_start[bb + (uint32_t)((iw1 + 1) * (int)dim.y)];
+  const int iw0 = bin_of(lo, geo.x, geo.y, dim.x), iw1 = bin_of(hi, geo.x, geo.y, dim.x);
+  p0 = (int)W.bin_start[bb + (uint32_t)(iw0 * dim.y)];
+  p1 = (int)W.bin_start[bb + (uint32_t)((iw1 + 1) * dim.y)];
 }
 
 // One warp takes 32 consecutive hits of a row; lane 0 stages the w-columns of rows r-1 and r+1
@@ -92,17 +97,18 @@ __device__ __forceinline__ void column_range(const Work& W, int g, float lo, flo
 // pass the window in a per-lane shared-memory list, then over row r-1, pairing each passing
 // candidate with the listed ones.
 constexpr int kK2Warps = 8;
-constexpr int kK2Slot = 192;  // staged hits per adjacent row per warp (float2)
+constexpr int kK2Slot = 192;  // staged FP32 records per adjacent row per warp (twice as many 16-bit)
 constexpr int kK2UCap = 6;    // listed row r+1 candidates per lane (more: rescan the row)
 
 // flat cursor over the bins of a grid window: w-columns iw0..iw1, y-bins iy0..iy1 of each
 struct WinCursor {
-  int cw, p, pe;
+  int cw, p, pe, base;
 };
 __device__ __forceinline__ void cursor_col(const Work& W, const GridWin& q, WinCursor& c) {
   const uint32_t col = q.bb + (uint32_t)(c.cw * q.ny);
   c.p = (int)W.bin_start[col + q.iy0];
   c.pe = (int)W.bin_start[col + q.iy1 + 1];
+  c.base = col_base(q.cw0, q.cshift, c.cw);
 }
 // next position of the window, or -1
 __device__ __forceinline__ int cursor_next(const Work& W, const GridWin& q, WinCursor& c) {
@@ -114,8 +120,10 @@ __device__ __forceinline__ int cursor_next(const Work& W, const GridWin& q, WinC
   return c.p++;
 }
 
-__device__ __forceinline__ void pair_step(const Work& W, float yi, float wi, float fm, const float2 hd, int d,
-                                          const float2 hu, int u, float& best, int& bd, int& bu) {
+template <bool kPacked>
+__device__ __forceinline__ void pair_step(const Work& W, int gd, int gu, float yi, float wi, float fm,
+                                          const float2 hd, int d, const float2 hu, int u, float& best, int& bd,
+                                          int& bu) {
   const float py = hd.x + (hu.x - hd.x) * fm;
   const float pw = hd.y + (hu.y - hd.y) * fm;
   const float ey = yi - py, ew = wi - pw;
@@ -123,20 +131,24 @@ __device__ __forceinline__ void pair_step(const Work& W, float yi, float wi, flo
   bool better;
   if (bd < 0 || chi < best) better = true;
   else if (chi > best) better = false;
-  else better = pair_key_less(W, d, u, bd, bu);
+  else better = pair_key_less<kPacked>(W, gd, gu, d, u, bd, bu);
   if (better) { best = chi; bd = d; bu = u; }
 }
 
+template <bool kPacked>
 __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use_tma) {
-  __shared__ __align__(16) float2 stage[kK2Warps][2][kK2Slot + 2];
+  constexpr int kRec = kPacked ? 4 : 8;       // bytes per staged record
+  constexpr int kAlign = 16 / kRec;           // records per 16 bytes
+  constexpr int kSlot = kPacked ? 2 * kK2Slot : kK2Slot;
+  __shared__ __align__(16) float2 stage_mem[kK2Warps][2][kK2Slot + 2];
   __shared__ float2 ucand[kK2Warps][kK2UCap][32];
   __shared__ int upos[kK2Warps][kK2UCap][32];
   __shared__ __align__(8) uint64_t bar[kK2Warps];
+  __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const BatchDesc* B = W.batch;
   if (lane == 0) mbar_init(&bar[warp], 1);
   __syncwarp();
-  __shared__ int s_item;
   uint32_t parity = 0;
   bool aborted = false;
   for (;;) {
@@ -155,7 +167,7 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
     for (int c0 = a + 32 * warp; c0 < b; c0 += 32 * kK2Warps) {
       const int i = c0 + lane;
       const bool valid = i < b;
-      const float2 hi = valid ? W.hyw[i] : make_float2(0.f, 0.f);
+      const float2 hi = valid ? hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, i) : make_float2(0.f, 0.f);
       float lo_w = valid ? hi.y : 3.0e38f, hi_w = valid ? hi.y : -3.0e38f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -169,16 +181,18 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
         uint32_t bytes = 0;
         int p0, p1;
         column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), p0, p1);
-        int q0 = p0 & ~1, q1 = (p1 + 1) & ~1;
-        if (use_tma && q1 > q0 && q1 - q0 <= kK2Slot) { base0 = q0; cnt0 = q1 - q0; bytes += (uint32_t)cnt0 * 8u; }
+        int q0 = p0 & ~(kAlign - 1), q1 = (p1 + kAlign - 1) & ~(kAlign - 1);
+        if (use_tma && q1 > q0 && q1 - q0 <= kSlot) { base0 = q0; cnt0 = q1 - q0; bytes += (uint32_t)(cnt0 * kRec); }
         column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), p0, p1);
-        q0 = p0 & ~1; q1 = (p1 + 1) & ~1;
-        if (use_tma && q1 > q0 && q1 - q0 <= kK2Slot) { base1 = q0; cnt1 = q1 - q0; bytes += (uint32_t)cnt1 * 8u; }
+        q0 = p0 & ~(kAlign - 1);
+        q1 = (p1 + kAlign - 1) & ~(kAlign - 1);
+        if (use_tma && q1 > q0 && q1 - q0 <= kSlot) { base1 = q0; cnt1 = q1 - q0; bytes += (uint32_t)(cnt1 * kRec); }
         // the slots were read by this warp's previous chunk (generic proxy): order before the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bar[warp], bytes);
-        if (cnt0) tma_load_1d(stage[warp][0], W.hyw + base0, (uint32_t)cnt0 * 8u, &bar[warp]);
-        if (cnt1) tma_load_1d(stage[warp][1], W.hyw + base1, (uint32_t)cnt1 * 8u, &bar[warp]);
+        const char* src = kPacked ? (const char*)W.hq : (const char*)W.hyw;
+        if (cnt0) tma_load_1d(stage_mem[warp][0], src + (size_t)base0 * kRec, (uint32_t)(cnt0 * kRec), &bar[warp]);
+        if (cnt1) tma_load_1d(stage_mem[warp][1], src + (size_t)base1 * kRec, (uint32_t)(cnt1 * kRec), &bar[warp]);
       }
       base0 = __shfl_sync(0xffffffffu, base0, 0);
       cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
@@ -192,18 +206,18 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
       }
       if (aborted) break;
       parity ^= 1u;
-      const RowView vd{stage[warp][0], base0, cnt0};
-      const RowView vu{stage[warp][1], base1, cnt1};
+      const RowView vd{stage_mem[warp][0], base0, cnt0};
+      const RowView vu{stage_mem[warp][1], base1, cnt1};
       if (valid) {
         const float yi = hi.x, wi = hi.y;
         const GridWin qd = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g - 1, yi, wi, wy_dn, ww_dn);
         const GridWin qu = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g + 1, yi, wi, wy_up, ww_up);
         // row r+1 candidates inside the window
         int nu = 0;
-        WinCursor cu{qu.iw0, 0, 0};
+        WinCursor cu{qu.iw0, 0, 0, 0};
         cursor_col(W, qu, cu);
         for (int u; (u = cursor_next(W, qu, cu)) >= 0;) {
-          const float2 hu = load_hit(W, vu, u);
+          const float2 hu = load_cand<kPacked>(W, vu, u, cu.base);
           if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
           if (nu < kK2UCap) { ucand[warp][nu][lane] = hu; upos[warp][nu][lane] = u; }
           ++nu;
@@ -211,20 +225,22 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
         float best = __int_as_float(0x7f800000);
         int bd = -1, bu = -1;
         if (nu > 0) {
-          WinCursor cd{qd.iw0, 0, 0};
+          WinCursor cd{qd.iw0, 0, 0, 0};
           cursor_col(W, qd, cd);
           for (int d; (d = cursor_next(W, qd, cd)) >= 0;) {
-            const float2 hd = load_hit(W, vd, d);
+            const float2 hd = load_cand<kPacked>(W, vd, d, cd.base);
             if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
             if (nu <= kK2UCap) {
-              for (int k = 0; k < nu; ++k) pair_step(W, yi, wi, fm, hd, d, ucand[warp][k][lane], upos[warp][k][lane], best, bd, bu);
+              for (int k = 0; k < nu; ++k)
+                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, ucand[warp][k][lane], upos[warp][k][lane], best,
+                                   bd, bu);
             } else {
-              WinCursor c2{qu.iw0, 0, 0};
+              WinCursor c2{qu.iw0, 0, 0, 0};
               cursor_col(W, qu, c2);
               for (int u; (u = cursor_next(W, qu, c2)) >= 0;) {
-                const float2 hu = load_hit(W, vu, u);
+                const float2 hu = load_cand<kPacked>(W, vu, u, c2.base);
                 if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-                pair_step(W, yi, wi, fm, hd, d, hu, u, best, bd, bu);
+                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
               }
             }
           }
@@ -234,6 +250,17 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
       __syncwarp();
     }
   }
+}
+
+void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma) {
+  if (packed) k_neighbours<true><<<grid, 256, 0, s>>>(W, Q, use_tma);
+  else k_neighbours<false><<<grid, 256, 0, s>>>(W, Q, use_tma);
+}
+int neighbours_blocks_per_sm(int packed) {
+  int nb = 0;
+  if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false>, 256, 0);
+  return nb;
 }
 
 // ------------------------------------------------------------------------------------ K3
@@ -296,7 +323,7 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
     uint32_t out = W.seg_nstart[g];
     const uint32_t bb = W.seg_bb[g];
-    const uint2 dim = W.seg_dim[g];
+    const int4 dim = W.seg_dim[g];
     const float4 geo = W.seg_geo[g];
     for (int c0 = a; c0 < b; c0 += blockDim.x) {
       const int i = c0 + threadIdx.x;
@@ -321,8 +348,8 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
       if (st) {
         const uint32_t pos = out + (uint32_t)warp_off[warp] + (uint32_t)__popc(m & ((1u << lane) - 1u));
         if (pos < tcap) {
-          const float w = W.hyw[i].y;
-          const uint32_t col = bb + (uint32_t)(bin_of(w, geo.x, geo.y, (int)dim.x) * (int)dim.y);
+          const int iw = W.packed ? (int)W.hcol[i] : bin_of(W.hyw[i].y, geo.x, geo.y, dim.x);
+          const uint32_t col = bb + (uint32_t)(iw * dim.y);
           W.starts_raw[pos] = make_uint4((uint32_t)i, (uint32_t)g, col, 0u);
         }
       }
@@ -335,13 +362,18 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
 // K4b: canonical order of start hits and their rank in the sector (rows, then (w, y, input index)).
 // A w-column holds every hit of its w range, so hits of earlier columns are smaller; only the hits
 // of the start's own column are compared one by one.
+__device__ __forceinline__ float2 hit_any(const Work& W, int g, int p) {
+  return W.packed ? hit_by_index<true>(W.hyw, W.hq, W.hcol, W.seg_dim, g, p)
+                  : hit_by_index<false>(W.hyw, W.hq, W.hcol, W.seg_dim, g, p);
+}
+
 __global__ void __launch_bounds__(256) k_start_order(Work W) {
   const uint32_t n = min(W.cnt->n_starts, (uint32_t)W.tcap);
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
     const uint4 e = W.starts_raw[p];
     const int i = (int)e.x, g = (int)e.y;
     const uint32_t col = e.z;
-    const float2 hi = W.hyw[i];
+    const float2 hi = hit_any(W, g, i);
     const uint32_t oi = W.horig[i];
     // run of start entries sharing the w-column (contiguous in sorted order)
     uint32_t lo = p, hiq = p;
@@ -351,16 +383,16 @@ __global__ void __launch_bounds__(256) k_start_order(Work W) {
     for (uint32_t q = lo; q <= hiq; ++q) {
       if (q == p) continue;
       const int j = (int)W.starts_raw[q].x;
-      const float2 hj = W.hyw[j];
+      const float2 hj = hit_any(W, g, j);
       if (key_less(hj.y, hj.x, W.horig[j], hi.y, hi.x, oi)) ++before;
     }
     // rank of the hit within its row and sector
-    const uint32_t ny = W.seg_dim[g].y;
+    const uint32_t ny = (uint32_t)W.seg_dim[g].y;
     const uint32_t c0 = W.bin_start[col], c1 = W.bin_start[col + ny];
     uint32_t incol = 0;
     for (uint32_t h = c0; h < c1; ++h) {
       if ((int)h == i) continue;
-      const float2 hh = W.hyw[h];
+      const float2 hh = hit_any(W, g, (int)h);
       if (key_less(hh.y, hh.x, W.horig[h], hi.y, hi.x, oi)) ++incol;
     }
     const int r = (g % kSegPerFrame) % kNRow;

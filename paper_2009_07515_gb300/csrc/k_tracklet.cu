@@ -71,8 +71,9 @@ __device__ __forceinline__ void reset_cov(const DevParams& Q, float* C) {
 }
 
 // smallest-chi2 hit of segment g inside the window around the predicted (y, w); -1 if none
+template <bool kPacked>
 __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int g, const float* P, const float* C,
-                                          float& chi_out) {
+                                          float& chi_out, float2& hit_out) {
   const float wy = Q.win_nsig * sqrtf(C[lt(0, 0)]) + Q.win_add;
   const float ww = Q.win_nsig * sqrtf(C[lt(1, 1)]) + Q.win_add;
   const GridWin q = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g, P[0], P[1], wy, ww);
@@ -84,34 +85,34 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
   const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   int best = -1;
   float bchi = __int_as_float(0x7f800000);
+  float2 bc = make_float2(0.f, 0.f);
   for (int cw = q.iw0; cw <= q.iw1; ++cw) {
-  const uint32_t col = q.bb + (uint32_t)(cw * q.ny);
-  const int p1 = (int)W.bin_start[col + q.iy1 + 1];
-  for (int h = (int)W.bin_start[col + q.iy0]; h < p1; ++h) {
-    const float2 c = W.hyw[h];
-    if (!(fabsf(c.x - P[0]) <= wy && fabsf(c.y - P[1]) <= ww)) continue;
-    float chi;
-    if (pd) {
-      const float r0 = c.x - P[0], r1 = c.y - P[1];
-      chi = r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
-    } else {
-      chi = __int_as_float(0x7f800000);
+    const uint32_t col = q.bb + (uint32_t)(cw * q.ny);
+    const int base = col_base(q.cw0, q.cshift, cw);
+    const int p1 = (int)W.bin_start[col + q.iy1 + 1];
+    for (int h = (int)W.bin_start[col + q.iy0]; h < p1; ++h) {
+      const float2 c = hit_in_col<kPacked>(W.hyw, W.hq, h, base);
+      if (!(fabsf(c.x - P[0]) <= wy && fabsf(c.y - P[1]) <= ww)) continue;
+      float chi;
+      if (pd) {
+        const float r0 = c.x - P[0], r1 = c.y - P[1];
+        chi = r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
+      } else {
+        chi = __int_as_float(0x7f800000);
+      }
+      bool better;
+      if (best < 0 || chi < bchi) better = true;
+      else if (chi > bchi) better = false;
+      else better = key_less(c.y, c.x, W.horig[h], bc.y, bc.x, W.horig[best]);
+      if (better) { best = h; bchi = chi; bc = c; }
     }
-    bool better;
-    if (best < 0 || chi < bchi) better = true;
-    else if (chi > bchi) better = false;
-    else {
-      const float2 o = W.hyw[best];
-      better = key_less(c.y, c.x, W.horig[h], o.y, o.x, W.horig[best]);
-    }
-    if (better) { best = h; bchi = chi; }
-  }
   }
   chi_out = bchi;
+  hit_out = bc;
   return best;
 }
 
-template <int kMinBlocks>
+template <int kMinBlocks, bool kPacked>
 __global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams Q, int ordered) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const long long tcap = W.tcap;
@@ -138,7 +139,9 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams
       const int g = (int)st.y;
       r0 = (g % kSegPerFrame) % kNRow;
       gb = g - r0;
-      const float2 a = W.hyw[st.x], b = W.hyw[ch.x], c = W.hyw[ch.y];
+      const float2 a = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, (int)st.x);
+      const float2 b = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r0 + ch.z / 2, ch.x);
+      const float2 c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r0 + ch.z - 1, ch.y);
       float hh[3][3];
       hh[0][0] = Q.x[r0];                hh[0][1] = a.x; hh[0][2] = a.y;
       hh[1][0] = Q.x[r0 + ch.z / 2];     hh[1][1] = b.x; hh[1][2] = b.y;
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams
     if (!stop) {
       int hit = -1;
       float chi = __int_as_float(0x7f800000);
+      float2 c = make_float2(0.f, 0.f);
       bool searched = false;
       if (!inward && chain >= 0) {
         hit = chain;
@@ -176,12 +180,11 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams
         hit = s == kNoHit ? -1 : (int)s;
       } else {
         searched = true;
-        hit = search_row(W, Q, gb + r, P, C, chi);
+        hit = search_row<kPacked>(W, Q, gb + r, P, C, chi, c);
       }
-      float2 c = make_float2(0.f, 0.f);
-      if (hit >= 0) {
-        c = W.hyw[hit];
-        if (!searched) chi = kf_chi2(Q, P, C, c.x, c.y);
+      if (hit >= 0 && !searched) {
+        c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, hit);
+        chi = kf_chi2(Q, P, C, c.x, c.y);
       }
       const bool acc = hit >= 0 && chi <= Q.chi2_max;
       if (acc) {
@@ -248,14 +251,25 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams
 }
 
 // host-side launchers (the kernel templates stay in this translation unit)
-void launch_tracklets(int variant, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
-  if (variant == 8) k_tracklets<8><<<grid, 128, 0, s>>>(W, Q, ordered);
-  else k_tracklets<4><<<grid, 128, 0, s>>>(W, Q, ordered);
+void launch_tracklets(int variant, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
+                      int ordered) {
+  if (variant == 8) {
+    if (packed) k_tracklets<8, true><<<grid, 128, 0, s>>>(W, Q, ordered);
+    else k_tracklets<8, false><<<grid, 128, 0, s>>>(W, Q, ordered);
+  } else {
+    if (packed) k_tracklets<4, true><<<grid, 128, 0, s>>>(W, Q, ordered);
+    else k_tracklets<4, false><<<grid, 128, 0, s>>>(W, Q, ordered);
+  }
 }
-int tracklets_blocks_per_sm(int variant) {
+int tracklets_blocks_per_sm(int variant, int packed) {
   int nb = 0;
-  if (variant == 8) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<8>, 128, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<4>, 128, 0);
+  if (variant == 8) {
+    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<8, true>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<8, false>, 128, 0);
+  } else {
+    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<4, true>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<4, false>, 128, 0);
+  }
   return nb;
 }
 

@@ -30,15 +30,17 @@ __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
 __global__ void k_scatter(Work);
-__global__ void k_neighbours(Work, DevParams, int);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_starts(Work, DevParams);
 __global__ void k_start_order(Work);
 __global__ void k_chains(Work);
 __global__ void k_length_offsets(Work);
 __global__ void k_length_scatter(Work);
-void launch_tracklets(int variant, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered);
-int tracklets_blocks_per_sm(int variant);
+void launch_tracklets(int variant, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
+                      int ordered);
+int tracklets_blocks_per_sm(int variant, int packed);
+void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
+int neighbours_blocks_per_sm(int packed);
 __global__ void k_votes(Work, DevParams);
 __global__ void k_kept(Work, DevParams);
 __global__ void k_write_tracks(Work, DevParams);
@@ -212,8 +214,8 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   ws->nf_cap = nf_cap;
   ws->scap = (long long)nf_cap * kSegPerFrame;
   const double occ = ctx->dp.occ;
-  // a segment grid has nw * ny <= 2 * ceil(n / occ) bins (ny <= bins)
-  ws->bcap = 2 * ((long long)std::ceil((double)ws->ncap / occ) + ws->scap) + 16;
+  // a segment grid has at most 4 ceil(n / occ) + 260 bins, 513 in the 16-bit storage (k_seg_layout)
+  ws->bcap = 4 * ((long long)std::ceil((double)ws->ncap / occ) + ws->scap) + (ctx->p.packed ? 520 : 264) * ws->scap + 16;
   long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1});
   ws->scan_cap = (maxscan + 2047) / 2048 + 16;
   struct Item { void** ptr; size_t bytes; };
@@ -225,11 +227,13 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.seg_cnt, 4 * (size_t)ws->scap},
       {(void**)&W.seg_nb, 4 * (size_t)ws->scap},
       {(void**)&W.seg_bb, 4 * (size_t)(ws->scap + 1)},
-      {(void**)&W.seg_dim, 8 * (size_t)ws->scap},
+      {(void**)&W.seg_dim, 16 * (size_t)ws->scap},
       {(void**)&W.seg_geo, 16 * (size_t)ws->scap},
       {(void**)&W.bin_start, 4 * (size_t)(ws->bcap + 1)},
       {(void**)&W.rank, 4 * (size_t)ws->ncap},
-      {(void**)&W.hyw, 8 * (size_t)(ws->ncap + 2)},
+      {(void**)&W.hyw, ctx->p.packed ? 0 : 8 * (size_t)(ws->ncap + 2)},
+      {(void**)&W.hq, ctx->p.packed ? 4 * (size_t)(ws->ncap + 4) : 0},
+      {(void**)&W.hcol, ctx->p.packed ? 2 * (size_t)ws->ncap : 0},
       {(void**)&W.horig, 4 * (size_t)ws->ncap},
       {(void**)&W.links, 8 * (size_t)ws->ncap},
       {(void**)&W.clinks, 8 * (size_t)ws->ncap},
@@ -264,6 +268,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   ws->d_desc = (BatchDesc*)p_desc;
   W.batch = ws->d_desc;
   W.ncap = ws->ncap; W.scap = ws->scap; W.bcap = ws->bcap; W.tcap = ws->tcap; W.scan_tmp_cap = ws->scan_cap;
+  W.packed = ctx->p.packed ? 1 : 0;
   CK(cudaMallocHost(&ws->h_desc, sizeof(BatchDesc)));
   CK(cudaMallocHost(&ws->h_cnt, sizeof(DevCounters)));
   memset(ws->h_desc, 0, sizeof(BatchDesc));
@@ -344,7 +349,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // scatter
   ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W);
   mark(ki++);  // neighbours
-  ++nl; k_neighbours<<<ctx->grid_neighbours, 256, 0, s>>>(W, Q, ctx->p.k2_tma);
+  ++nl; launch_neighbours(ctx->p.packed, ctx->grid_neighbours, s, W, Q, ctx->p.k2_tma);
   mark(ki++);  // clean
   ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_start
@@ -365,7 +370,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
     ++nl; k_length_scatter<<<4 * G, 256, 0, s>>>(W);
   }
   mark(ki++);  // tracklets
-  ++nl; launch_tracklets(ctx->k5_variant, ctx->grid_tracklets, s, W, Q, ordered ? 1 : 0);
+  ++nl; launch_tracklets(ctx->k5_variant, ctx->p.packed, ctx->grid_tracklets, s, W, Q, ordered ? 1 : 0);
   mark(ki++);  // zero_w
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
   mark(ki++);  // votes
@@ -640,11 +645,10 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     for (int k = 0; k <= kNumKernels; ++k) cudaEventCreate(&ctx->ev[k]);
     cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming);
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours, 256, 0);
+    int nb = neighbours_blocks_per_sm(ctx->p.packed);
     ctx->grid_neighbours = ctx->sms * std::max(nb, 1);
     ctx->k5_variant = ctx->p.k5_occupancy == 4 ? 4 : 8;
-    nb = tracklets_blocks_per_sm(ctx->k5_variant);
+    nb = tracklets_blocks_per_sm(ctx->k5_variant, ctx->p.packed);
     ctx->grid_tracklets = ctx->sms * std::max(nb, 1);
     for (int k = 0; k < 2; ++k) {
       cudaStream_t s;

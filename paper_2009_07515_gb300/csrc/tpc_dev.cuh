@@ -2,11 +2,16 @@
 //
 // Layout of one batch in HBM (all frames of a batch share one workspace; every array is indexed by
 // a batch-global "sorted position" p of a cluster after the grid build):
-//   hyw[p]      float2 (y, w) of the cluster at sorted position p (FP32 storage)
+//   hyw[p]      float2 (y, w) of the cluster at sorted position p (FP32 storage), or
+//   hq[p]       uint32 (qy | qw << 16) in the 16-bit storage: y = qy/512 - 64 and w = (column base +
+//               qw)/512, qw the offset in 2^-9 cm from the lower edge of the cluster's grid column;
+//               hcol[p] (uint16) that column, for reads by position
 //   horig[p]    uint32 index of the cluster in its frame's input arrays
-//   segments    g = frame*5472 + sector*152 + row; seg_bb[g] = first bin, seg_dim[g] = (nw, ny),
-//               seg_geo[g] = (w_lo, w-bins per cm, y_lo, y-bins per cm) of the segment's 2-D grid
-//               over the drift coordinate w and the pad-row coordinate y; bin = iw * ny + iy
+//   segments    g = frame*5472 + sector*152 + row; seg_bb[g] = first bin, seg_dim[g] = (nw, ny,
+//               iw0, k + 9), seg_geo[g] = (w_lo, w-bins per cm, y_lo, y-bins per cm) of the
+//               segment's 2-D grid over the drift coordinate w and the pad-row coordinate y;
+//               bin = iw * ny + iy; w-columns have width 2^k cm (-3 <= k <= 7) and are aligned to
+//               multiples of it (column iw starts at (iw0 + iw) * 2^k cm)
 //   bin_start[b] sorted position of the first cluster of bin b (exclusive prefix over all bins), so
 //               a w-column (all y of one w bin) is one contiguous position range, and a window is
 //               one contiguous range per w-column it touches
@@ -104,11 +109,13 @@ struct Work {
   uint32_t* seg_cnt;     // [scap]
   uint32_t* seg_nb;      // [scap]  bins of the segment (nw * ny), scanned into seg_bb
   uint32_t* seg_bb;      // [scap + 1]
-  uint2* seg_dim;        // [scap] (nw, ny)
+  int4* seg_dim;         // [scap] (nw, ny, iw0, k + 9)
   float4* seg_geo;       // [scap] (w_lo, w-bins per cm, y_lo, y-bins per cm)
   uint32_t* bin_start;   // [bcap + 1]
   uint32_t* rank;        // [ncap]
-  float2* hyw;           // [ncap + 2]
+  float2* hyw;           // [ncap + 2] FP32 storage
+  uint32_t* hq;          // [ncap + 4] 16-bit storage
+  uint16_t* hcol;        // [ncap]     16-bit storage: grid column of each position
   uint32_t* horig;       // [ncap]
   // links
   int2* links;           // [ncap]
@@ -133,6 +140,7 @@ struct Work {
   // scan scratch
   uint32_t* scan_tmp;    // [scan_tmp_cap]
   long long ncap, scap, bcap, tcap, scan_tmp_cap;
+  int packed;            // 1: 16-bit cluster storage (hq, hcol), 0: FP32 (hyw)
 };
 
 // ------------------------------------------------------------------------------------ helpers
@@ -155,17 +163,19 @@ __device__ __forceinline__ int bin_of(float v, float lo, float inv, int nb) {
 // Window of a segment grid: w-columns [iw0, iw1], y-bins [iy0, iy1], for |w - wc| <= Ww and
 // |y - yc| <= Wy (widened by a hair: the exact window test is done on the coordinates).
 struct GridWin {
-  int iw0, iw1, iy0, iy1, ny;
+  int iw0, iw1, iy0, iy1, ny, cw0, cshift;  // cw0, cshift: column base of iw = (cw0 + iw) << cshift
   uint32_t bb;
 };
 __device__ __forceinline__ float win_pad(float c, float W);
-__device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const uint2* seg_dim, const float4* seg_geo,
+__device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const int4* seg_dim, const float4* seg_geo,
                                                int g, float yc, float wc, float Wy, float Ww) {
   GridWin q;
-  const uint2 dim = seg_dim[g];
+  const int4 dim = seg_dim[g];
   const float4 geo = seg_geo[g];
   q.bb = seg_bb[g];
-  q.ny = (int)dim.y;
+  q.ny = dim.y;
+  q.cw0 = dim.z;
+  q.cshift = dim.w;
   const float pw = win_pad(wc, Ww), py = win_pad(yc, Wy);
   q.iw0 = bin_of((wc - Ww) - pw, geo.x, geo.y, (int)dim.x);
   q.iw1 = bin_of((wc + Ww) + pw, geo.x, geo.y, (int)dim.x);
@@ -177,6 +187,29 @@ __device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const uin
 // conservative widening of a window for the bin lookup (rounding of w +- W)
 __device__ __forceinline__ float win_pad(float wc, float W) {
   return fabsf(wc) * 1.0e-6f + W * 1.0e-6f + 1.0e-6f;
+}
+
+// ---- 16-bit storage. Column base in units of 2^-9 cm; y = qy/512 - 64, w = (base + qw)/512: both
+// exact floats for |w| < 32768 cm, equal to rint(512 w)/512 whatever the column.
+__device__ __forceinline__ int col_base(int cw0, int cshift, int iw) { return (cw0 + iw) * (1 << cshift); }
+__device__ __forceinline__ float2 unpack_hit(uint32_t q, int base) {
+  return make_float2((float)(q & 0xFFFFu) * (1.0f / 512.0f) - 64.0f, (float)(base + (int)(q >> 16)) * (1.0f / 512.0f));
+}
+// (y, w) of position p whose column base is known
+template <bool kPacked>
+__device__ __forceinline__ float2 hit_in_col(const float2* hyw, const uint32_t* hq, int p, int base) {
+  if (kPacked) return unpack_hit(hq[p], base);
+  return hyw[p];
+}
+// (y, w) of position p of segment g (reads the column of p in the 16-bit storage)
+template <bool kPacked>
+__device__ __forceinline__ float2 hit_by_index(const float2* hyw, const uint32_t* hq, const uint16_t* hcol,
+                                               const int4* seg_dim, int g, int p) {
+  if (kPacked) {
+    const int4 d = seg_dim[g];
+    return unpack_hit(hq[p], col_base(d.z, d.w, (int)hcol[p]));
+  }
+  return hyw[p];
 }
 
 // row-order key comparison: (w, y, input index) lexicographic

@@ -9,7 +9,7 @@
 // arrays the caller provides.
 //
 // The array is part of the library's device image: every GPU that loads the library holds it
-// (kStaticScratchBytes, about 10.3 MiB) until the process exits. Calls share it and it keeps the last
+// (kStaticScratchBytes, about 17.9 MiB) until the process exits. Calls share it and it keeps the last
 // call's contents; everything the kernels need zeroed is cleared by the call itself. Two calls that
 // overlap on the GPU (from two host threads, or on two streams) race on it and must be serialised by
 // the caller.
@@ -33,12 +33,12 @@ __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
 __global__ void k_scatter(Work);
-__global__ void k_neighbours(Work, DevParams, int);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
 void make_dev_params(const tpc_params& p, DevParams& d);
+void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
 }  // namespace tpc
 
 using namespace tpc;
@@ -65,7 +65,7 @@ constexpr StaticLayout static_layout(long long ncap, long long bcap) {
   L.seg_cnt = o;    o = al(o + 4 * (size_t)scap);
   L.seg_nb = o;     o = al(o + 4 * (size_t)scap);
   L.seg_bb = o;     o = al(o + 4 * (size_t)(scap + 1));
-  L.seg_dim = o;    o = al(o + 8 * (size_t)scap);
+  L.seg_dim = o;    o = al(o + 16 * (size_t)scap);
   L.seg_geo = o;    o = al(o + 16 * (size_t)scap);
   L.bin_start = o;  o = al(o + 4 * (size_t)(bcap + 1));
   L.rank = o;       o = al(o + 4 * (size_t)ncap);
@@ -79,9 +79,10 @@ constexpr StaticLayout static_layout(long long ncap, long long bcap) {
   return L;
 }
 
-// bins of a frame's grid: at most 2 * (n / occupancy + segments) (see k_seg_layout)
+// bins of a frame's grid (FP32 storage): at most 4 ceil(n / occupancy) + 260 per segment (see
+// k_seg_layout)
 constexpr long long static_bcap(long long n, double occ) {
-  return 2 * ((long long)((double)n / occ) + 1 + kSegPerFrame) + 16;
+  return 4 * ((long long)((double)n / occ) + 1 + kSegPerFrame) + 264LL * kSegPerFrame + 16;
 }
 
 constexpr size_t kStaticScratchBytes = static_layout(kStaticMaxClusters, static_bcap(kStaticMaxClusters, kStaticMinOccupancy)).total;
@@ -134,6 +135,7 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
     tpc_default_params(&p);
   }
   if (p.bin_occupancy <= 0.f) p.bin_occupancy = 2.0f;
+  if (p.packed) return TPC_E_INVAL;  // FP32 cluster storage only
   if (p.bin_occupancy < kStaticMinOccupancy) return TPC_E_CAPACITY;  // finer grids need more bins
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) { cudaGetLastError(); return TPC_E_CUDA; }
@@ -157,7 +159,7 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   W.seg_cnt = (uint32_t*)(b + L.seg_cnt);
   W.seg_nb = (uint32_t*)(b + L.seg_nb);
   W.seg_bb = (uint32_t*)(b + L.seg_bb);
-  W.seg_dim = (uint2*)(b + L.seg_dim);
+  W.seg_dim = (int4*)(b + L.seg_dim);
   W.seg_geo = (float4*)(b + L.seg_geo);
   W.bin_start = (uint32_t*)(b + L.bin_start);
   W.rank = (uint32_t*)(b + L.rank);
@@ -203,7 +205,7 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   k_bin_rank<<<8 * G, 256, 0, s>>>(W);
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
   k_scatter<<<8 * G, 256, 0, s>>>(W);
-  k_neighbours<<<4 * G, 256, 0, s>>>(W, Q, p.k2_tma);
+  launch_neighbours(0, 4 * G, s, W, Q, p.k2_tma);
   k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   if (n > 0) {
     cudaMemsetAsync(up, 0xFF, 4 * (size_t)n, s);

@@ -76,6 +76,15 @@ def run_gpu(tracker, f):
     return res, links
 
 
+@pytest.fixture(scope="module")
+def tracker16(torch_cuda):
+    import paper_2009_07515_gb300 as tpc
+    tpc.build()
+    t = tpc.Tracker(packed=1)
+    yield t
+    t.close()
+
+
 @pytest.mark.parametrize("cfg", ["pp_500", "pbpb_2x10000"])
 def test_links_and_tracks_match_fp32_oracle(tracker, cfg, n_threads):
     f = synth.generate(cfg)
@@ -89,6 +98,18 @@ def test_links_and_tracks_match_fp32_oracle(tracker, cfg, n_threads):
         assert len(diff) <= 1e-4 * f.n
     gi, oi = compare_tracks(gpu, orc)
     assert gpu["n_tracks"] > 500
+
+
+@pytest.mark.parametrize("cfg", ["pp_500", "pbpb_2x10000", "batch16"])
+def test_16bit_storage_matches_oracle_on_read_back_clusters(tracker16, cfg, n_threads):
+    """16-bit cluster storage: the GPU equals the FP32 oracle run on the read-back coordinates."""
+    f = synth.generate(cfg)
+    gpu, links = run_gpu(tracker16, f)
+    orc = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", packed=True, n_threads=n_threads)
+    for k, name in enumerate(("up", "down", "up_c", "down_c")):
+        diff = np.flatnonzero(links[k] != getattr(orc, name))
+        assert np.all(orc.nb_margin[diff] < 1e-5), f"{name}: {len(diff)} untraced link differences"
+    compare_tracks(gpu, orc)
 
 
 def test_error_against_fp64_oracle(tracker, n_threads):

@@ -386,3 +386,30 @@ def test_malformed_input_rejected():
         oracle.track(np.array([0], np.uint8), np.array([3], np.uint8), [np.nan], [0.0])
     res = oracle.track(np.zeros(0, np.uint8), np.zeros(0, np.uint8), [], [])
     assert res.n_tracks == 0
+
+
+# ------------------------------------------------------------------ 16-bit cluster storage
+
+def test_16bit_read_back_is_a_fixed_point_grid():
+    """y and w read back on 2^-9 cm grids (within half a step), exactly representable, idempotent."""
+    rng = np.random.default_rng(8)
+    for _ in range(2000):
+        y, w = rng.uniform(-63.9, 63.9), rng.uniform(-200.0, 32000.0)
+        y1, w1 = oracle.pack(np.float32(y), np.float32(w))
+        # half a step, plus the float rounding of y + 64 before the rounding to the step
+        assert abs(y1 - np.float32(y)) <= 2.0 ** -10 + 1e-5 and abs(w1 - np.float32(w)) <= 2.0 ** -10 + 1e-5
+        assert (y1 + 64) * 512 == int((y1 + 64) * 512) and w1 * 512 == int(w1 * 512)
+        assert oracle.pack(y1, w1) == (y1, w1)
+    assert oracle.pack(80.0, 1.0)[0] == 64 - 2.0 ** -9 and oracle.pack(-80.0, 1.0)[0] == -64.0
+
+
+def test_16bit_storage_keeps_efficiency(n_threads):
+    f = synth.generate("pbpb_2x10000", mult_fixed=4000)
+    a = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", n_threads=n_threads)
+    b = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", packed=True, n_threads=n_threads)
+    ea, _, _, _ = efficiency(f, oracle_track_list(a))
+    eb, _, _, _ = efficiency(f, oracle_track_list(b))
+    assert eb > 0.95 and abs(ea - eb) < 0.005
+    sa = {tuple(a.track_hits(i)) for i in range(a.n_tracks)}
+    sb = {tuple(b.track_hits(i)) for i in range(b.n_tracks)}
+    assert len(sa & sb) > 0.97 * len(sa)
