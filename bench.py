@@ -155,6 +155,71 @@ def cpu_baseline(frame, n_threads: int, budget_s: float = 20.0) -> dict:
             "sample": f"sectors 0-{k - 1} of the workload frame ({n} clusters), FP32 oracle, {dt:.2f} s"}
 
 
+def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_frames: int, loads, seed: int = 5,
+                      budget_gb: float = 80.0):
+    """Frame p50/p99 latency and throughput, served (continuous batching, tpc_submit_frame/tpc_poll)
+    against plain one-frame-at-a-time tracking (load, track, read back), for a Poisson stream of
+    frames with collision counts uniform in 1..max_collisions (drawn from a pool of generated frames).
+    Loads are arrival rates relative to the plain path's mean service rate. Latency = time from a
+    frame's arrival to its tracks being readable on the host."""
+    rng = np.random.default_rng(seed)
+    colls = rng.integers(1, max_collisions + 1, pool_size)
+    pool = [synth.generate("serve", n_collisions=int(c), frame_id=i) for i, c in enumerate(colls)]
+    plain = tpc.Tracker()
+    for f in pool[:2]:
+        plain.run(f.sector, f.row, f.y, f.w)
+    t0 = time.perf_counter()
+    for f in pool:
+        plain.run(f.sector, f.row, f.y, f.w)
+    service = (time.perf_counter() - t0) / pool_size
+    out = {"workload": f"Poisson stream, frames of U{{1..{max_collisions}}} collisions (pool of {pool_size})",
+           "mean_plain_service_ms": service * 1e3, "budget_gb": budget_gb, "points": []}
+    srv = tpc.Tracker(hbm_budget=int(budget_gb * (1 << 30)))
+    for load in loads:
+        lam = load / service
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n_frames))
+        pick = rng.integers(0, pool_size, n_frames)
+        clusters = float(sum(pool[k].n for k in pick))
+        # plain: one frame at a time in arrival order
+        lat = []
+        t0 = time.perf_counter()
+        for a, k in zip(arrivals, pick):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            f = pool[k]
+            plain.run(f.sector, f.row, f.y, f.w)
+            lat.append(time.perf_counter() - t0 - a)
+        plain_span = (time.perf_counter() - t0) - arrivals[0]
+        # served: submit on arrival, poll continuously
+        done, sub = {}, {}
+        i = 0
+        t0 = time.perf_counter()
+        while len(done) < n_frames:
+            now = time.perf_counter() - t0
+            while i < n_frames and arrivals[i] <= now:
+                f = pool[pick[i]]
+                tk = srv.submit(f.sector, f.row, f.y, f.w)
+                sub[tk] = arrivals[i]
+                i += 1
+            wait_us = int(max(0.0, (arrivals[i] - now) * 1e6)) if i < n_frames else 200000
+            for tk in srv.poll(64, min(wait_us, 200000)):
+                srv.tracks(tk)
+                done[tk] = time.perf_counter() - t0
+                srv.release(tk)
+        srv_lat = [done[t] - sub[t] for t in done]
+        served_span = max(done.values()) - arrivals[0]
+        pt = {"load": load, "rate_per_s": lam, "frames": n_frames,
+              "plain": {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                        "clusters_per_s": clusters / plain_span},
+              "served": {"p50_ms": float(np.percentile(srv_lat, 50) * 1e3),
+                         "p99_ms": float(np.percentile(srv_lat, 99) * 1e3), "clusters_per_s": clusters / served_span}}
+        out["points"].append(pt)
+    plain.close()
+    srv.close()
+    return out
+
+
 def run_reference(args, ws, rank):
     """Reference arm: the CPU oracle, timed on the host cores, on bounded samples of the workload."""
     if rank != 0:
@@ -188,6 +253,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="pbpb_2x10000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-collisions", type=int, default=40,
+                    help="serving stream: collisions per frame uniform in 1..N (570 = full-size frames)")
+    ap.add_argument("--serve-loads", default="0.9", help="comma-separated arrival rates / plain service rate")
+    ap.add_argument("--serve-frames", type=int, default=80)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     ws, rank, local = _dist()
@@ -295,6 +365,11 @@ def main():
                        "parallelism": f"replicas x{ws}"},
             "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "kernels_ms": kernels}
+    tr.release(h)
+    if not args.no_serving:
+        line["serving"] = serving_benchmark(
+            tpc, synth, max_collisions=args.serve_collisions, pool_size=12, n_frames=args.serve_frames,
+            loads=[float(x) for x in args.serve_loads.split(",")], seed=5 + rank)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(frame, os.cpu_count() or 1)
     if rank == 0:

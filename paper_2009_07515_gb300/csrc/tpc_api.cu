@@ -139,7 +139,8 @@ struct Frame {
   int state = 0;                   // 0 loaded, 1 queued, 2 admitted, 3 running, 4 done, 5 fetched
   std::shared_ptr<Workspace> ws;
   int fidx = 0;
-  size_t budget_bytes = 0;
+  std::vector<char> host_copy;      // serving: clusters submitted from host memory, until admitted
+  bool served = false;
   double t_submit = 0, t_done = 0;
   // host results
   std::vector<int32_t> sector, ndf;
@@ -167,16 +168,17 @@ struct tpc_ctx {
   float ms[kNumKernels] = {0};
   int64_t launches[kNumKernels] = {0};
   int64_t stage_launches[kNumKernels] = {0};
-  // serving
+  // serving: each stream slot owns one workspace of slot_clusters clusters carved from the HBM
+  // budget; a batch is the queued frames that fit it, launched as soon as the slot is free
   std::deque<tpc_frame_t> queue;  // submitted, not yet admitted
-  size_t budget_used = 0;
-  struct Inflight {
+  struct Slot {
+    cudaStream_t stream = nullptr;
     std::shared_ptr<Workspace> ws;
     std::vector<tpc_frame_t> frames;
-    cudaStream_t stream;
+    bool busy = false;
   };
-  std::vector<Inflight> inflight;
-  std::vector<cudaStream_t> serve_streams;
+  std::vector<Slot> slots;
+  long long slot_clusters = 0;
   std::deque<tpc_frame_t> finished;
 };
 
@@ -206,8 +208,9 @@ void free_workspace(Workspace* w) {
   w->block = nullptr;
 }
 
-// Lay out one device block for the capacities.
-int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, std::shared_ptr<Workspace>& out) {
+// Lay out one device block for the capacities (dry: only compute its size into *dry_bytes).
+int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, std::shared_ptr<Workspace>& out,
+                    size_t* dry_bytes = nullptr) {
   auto ws = std::shared_ptr<Workspace>(new Workspace, [](Workspace* w) { free_workspace(w); delete w; });
   ws->ncap = std::max(ncap, 1024LL);
   ws->tcap = std::max(tcap, 1024LL);
@@ -258,6 +261,10 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   std::vector<size_t> offs;
   for (auto& it : items) { offs.push_back(total); total = align_up(total + it.bytes, 256); }
   ws->bytes = total;
+  if (dry_bytes) {
+    *dry_bytes = total;
+    return TPC_OK;
+  }
   cudaError_t e = cudaMalloc(&ws->block, total);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -280,6 +287,14 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
 
 int wait_ws(tpc_ctx* ctx, Workspace& ws, double timeout_s);
 void release_ws_user(tpc_ctx* ctx, Frame* f);
+
+size_t workspace_bytes(tpc_ctx* ctx, long long ncap, int nf_cap) {
+  std::shared_ptr<Workspace> ws;
+  size_t b = 0;
+  const long long tcap = (long long)std::ceil((double)ncap * ctx->p.tracklet_capacity) + 1024;
+  alloc_workspace(ctx, ncap, tcap, nf_cap, ws, &b);
+  return b;
+}
 
 // Workspace from the pool (a free one large enough), else a new one.
 int get_workspace(tpc_ctx* ctx, long long ntot, int nf, std::shared_ptr<Workspace>& out) {
@@ -392,10 +407,11 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   return TPC_OK;
 }
 
-int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::shared_ptr<Workspace>& ws_out) {
+int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::shared_ptr<Workspace>& ws_out,
+              std::shared_ptr<Workspace> fixed = nullptr) {
   // The same batch tracked again on the same workspace (e.g. a frame re-tracked in a loop): the
   // descriptor in device memory is already right and the stream orders the runs.
-  {
+  if (!fixed) {
     std::shared_ptr<Workspace> same = fr[0]->ws;
     bool reuse = same && same->batch_ids.size() == fr.size();
     for (size_t k = 0; reuse && k < fr.size(); ++k) reuse = fr[k]->ws == same && same->batch_ids[k] == fr[k]->id;
@@ -414,8 +430,9 @@ int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::
   for (Frame* f : fr) release_ws_user(ctx, f);
   long long ntot = 0;
   for (auto* f : fr) ntot += f->n;
-  std::shared_ptr<Workspace> ws;
-  int rc = get_workspace(ctx, ntot, (int)fr.size(), ws);
+  std::shared_ptr<Workspace> ws = fixed;
+  int rc = TPC_OK;
+  if (!ws) rc = get_workspace(ctx, ntot, (int)fr.size(), ws);
   if (rc) return rc;
   ws->batch_ids.clear();
   for (auto* f : fr) ws->batch_ids.push_back(f->id);
@@ -573,10 +590,6 @@ void drop_frame(tpc_ctx* ctx, Frame* f) {
   ctx->frames.erase(f->id);
 }
 
-size_t frame_budget_bytes(const tpc_ctx* ctx, long long n) {
-  // input 10 B + grid/links/weights/output ~46 B per cluster, tracklets ~860 B per slot
-  return (size_t)n * (10 + 46) + (size_t)(n * ctx->p.tracklet_capacity * 860.0) + ((size_t)1 << 20);
-}
 
 }  // namespace
 
@@ -650,10 +663,18 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     ctx->k5_variant = ctx->p.k5_occupancy == 4 ? 4 : 8;
     nb = tracklets_blocks_per_sm(ctx->k5_variant, ctx->p.packed);
     ctx->grid_tracklets = ctx->sms * std::max(nb, 1);
-    for (int k = 0; k < 2; ++k) {
-      cudaStream_t s;
-      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-      ctx->serve_streams.push_back(s);
+    ctx->slots.resize(2);
+    for (auto& sl : ctx->slots) cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    // slot capacity: the largest batch whose workspace and inputs fit half of the HBM budget
+    {
+      const size_t half = (size_t)std::max<int64_t>(ctx->p.hbm_budget, 1 << 20) / ctx->slots.size();
+      long long lo = 0, hi = 1LL << 31;
+      while (lo < hi) {
+        const long long mid = lo + (hi - lo + 1) / 2;
+        const size_t need = workspace_bytes(ctx, mid, ctx->p.max_batch_frames) + (size_t)mid * 10;
+        if (need <= half) lo = mid; else hi = mid - 1;
+      }
+      ctx->slot_clusters = lo;
     }
     if (cudaGetLastError() != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "context setup failed"); break; }
   } while (0);
@@ -665,11 +686,15 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
 void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  for (auto s : ctx->serve_streams) { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+  for (auto& sl : ctx->slots) {
+    if (!sl.stream) continue;
+    cudaStreamSynchronize(sl.stream);
+    cudaStreamDestroy(sl.stream);
+  }
   for (auto& kv : ctx->frames)
     if (kv.second->d_block) cudaFreeAsync(kv.second->d_block, ctx->stream);
   ctx->frames.clear();
-  ctx->inflight.clear();
+  ctx->slots.clear();
   ctx->wspool.clear();
   if (ctx->stream) { cudaStreamSynchronize(ctx->stream); cudaStreamDestroy(ctx->stream); }
   for (int k = 0; k <= kNumKernels; ++k)
@@ -814,10 +839,7 @@ int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame) {
     auto it = std::find(ctx->queue.begin(), ctx->queue.end(), frame);
     if (it != ctx->queue.end()) ctx->queue.erase(it);
   }
-  if (f->budget_bytes) {
-    ctx->budget_used -= std::min(ctx->budget_used, f->budget_bytes);
-    f->budget_bytes = 0;
-  }
+  if (f->served && (f->state == 2 || f->state == 3)) return fail(ctx, TPC_E_STATE, "frame is being tracked");
   drop_frame(ctx, f);
   return TPC_OK;
 }
@@ -825,71 +847,128 @@ int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame) {
 // ------------------------------------------------------------------------------ serving
 int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ticket) {
   if (!ctx || !ticket || !clusters) return TPC_E_INVAL;
-  const size_t need = frame_budget_bytes(ctx, clusters->n);
-  if ((long long)need > ctx->p.hbm_budget) return fail(ctx, TPC_E_BUDGET, "frame larger than the HBM budget");
-  Frame* f = nullptr;
-  int rc = load_frame(ctx, clusters, f);
-  if (rc) return rc;
+  if (clusters->n < 0 || clusters->n >= (1LL << 31)) return fail(ctx, TPC_E_INVAL, "bad cluster descriptor");
+  if (clusters->n > 0 && (!clusters->sector || !clusters->row || !clusters->y || !clusters->w))
+    return fail(ctx, TPC_E_INVAL, "null cluster array");
+  if (clusters->n > ctx->slot_clusters) return fail(ctx, TPC_E_BUDGET, "frame larger than a serving slot of the HBM budget");
+  auto fr = std::make_unique<Frame>();
+  Frame* f = fr.get();
+  f->n = clusters->n;
+  f->served = true;
+  if (clusters->on_device) {
+    f->d_sector = (uint8_t*)clusters->sector; f->d_row = (uint8_t*)clusters->row;
+    f->d_y = (float*)clusters->y; f->d_w = (float*)clusters->w;
+  } else {
+    // kept on the host until admission: queued frames hold no device memory
+    const size_t n = (size_t)f->n;
+    f->host_copy.resize(10 * n + 1);
+    char* h = f->host_copy.data();
+    memcpy(h, clusters->sector, n);
+    memcpy(h + n, clusters->row, n);
+    memcpy(h + 2 * n, clusters->y, 4 * n);
+    memcpy(h + 6 * n, clusters->w, 4 * n);
+  }
+  f->id = ctx->next_id++;
   f->state = 1;
   f->t_submit = now_s();
-  f->budget_bytes = 0;
   ctx->queue.push_back(f->id);
   *ticket = f->id;
+  ctx->frames[f->id] = std::move(fr);
   return TPC_OK;
 }
 
 namespace {
+// upload a queued host frame on the slot's stream
+int upload_frame(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
+  if (f->host_copy.empty() || f->d_block) return TPC_OK;
+  const size_t n = (size_t)f->n;
+  const size_t o1 = align_up(n, 256), o2 = o1 + align_up(n, 256), o3 = o2 + align_up(4 * n, 256);
+  const size_t bytes = o3 + align_up(4 * n, 256) + 256;
+  cudaError_t e = cudaMallocFromPoolAsync(&f->d_block, bytes, ctx->pool, s);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, TPC_E_NOMEM, "input allocation failed"); }
+  char* b = (char*)f->d_block;
+  f->d_sector = (uint8_t*)b; f->d_row = (uint8_t*)(b + o1); f->d_y = (float*)(b + o2); f->d_w = (float*)(b + o3);
+  if (n) {
+    const char* h = f->host_copy.data();
+    CK(cudaMemcpyAsync(f->d_sector, h, n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f->d_row, h + n, n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f->d_y, h + 2 * n, 4 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f->d_w, h + 6 * n, 4 * n, cudaMemcpyHostToDevice, s));
+  }
+  return TPC_OK;
+}
+
 int serve_step(tpc_ctx* ctx) {
-  // retire finished batches
-  for (size_t k = 0; k < ctx->inflight.size();) {
-    auto& b = ctx->inflight[k];
-    cudaError_t e = cudaEventQuery(b.ws->done);
-    if (e == cudaErrorNotReady) { ++k; continue; }
+  // retire finished batches: results to the host, inputs and the slot's workspace freed
+  for (auto& sl : ctx->slots) {
+    if (!sl.busy) continue;
+    cudaError_t e = cudaEventQuery(sl.ws->done);
+    if (e == cudaErrorNotReady) continue;
     if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("device: ") + cudaGetErrorString(e));
-    b.ws->busy = false;
-    const double t = now_s();
-    for (auto id : b.frames) {
+    sl.ws->busy = false;
+    const DevCounters& c = *sl.ws->h_cnt;
+    const bool overflow = c.n_starts > (uint32_t)sl.ws->tcap || (c.err & (kErrBins | kErrTracks));
+    int rc = overflow ? TPC_OK : check_ws_errors(ctx, *sl.ws);
+    for (auto id : sl.frames) {
       Frame* f = find_frame(ctx, id);
       if (!f) continue;
-      f->state = 4;
-      f->t_done = t;
+      if (!overflow && rc == TPC_OK) {
+        rc = fetch_results(ctx, f);
+      } else if (overflow) {
+        // capacity overflow of the batch: track this frame alone (its own workspace) and fetch
+        release_ws_user(ctx, f);
+        const float old = ctx->p.tracklet_capacity;
+        ctx->p.tracklet_capacity = std::max(old, 1.25f * (float)c.n_starts / (float)std::max(1LL, f->n));
+        std::vector<Frame*> one{f};
+        std::shared_ptr<Workspace> ws;
+        rc = run_batch(ctx, one, ctx->stream, ws);
+        ctx->p.tracklet_capacity = old;
+        if (!rc) rc = wait_ws(ctx, *f->ws, 120.0);
+        if (!rc) rc = check_ws_errors(ctx, *f->ws);
+        if (!rc) rc = fetch_results(ctx, f);
+      }
+      if (rc) return rc;
+      release_ws_user(ctx, f);
+      if (f->d_block) { cudaFreeAsync(f->d_block, sl.stream); f->d_block = nullptr; }
+      f->host_copy.clear();
+      f->host_copy.shrink_to_fit();
+      f->state = 5;
+      f->t_done = now_s();
       ctx->finished.push_back(id);
     }
-    ctx->inflight.erase(ctx->inflight.begin() + (long)k);
+    sl.frames.clear();
+    sl.busy = false;
   }
-  // launch a new batch of admitted frames into a free stream slot
-  while (ctx->inflight.size() < ctx->serve_streams.size() && !ctx->queue.empty()) {
+  // launch: every free slot takes the queued frames that fit it, in arrival order
+  for (auto& sl : ctx->slots) {
+    if (sl.busy || ctx->queue.empty()) continue;
     std::vector<Frame*> batch;
-    std::vector<tpc_frame_t> ids;
+    long long n = 0;
     while (!ctx->queue.empty() && (int)batch.size() < ctx->p.max_batch_frames) {
       Frame* f = find_frame(ctx, ctx->queue.front());
       if (!f) { ctx->queue.pop_front(); continue; }
-      const size_t need = frame_budget_bytes(ctx, f->n);
-      if (ctx->budget_used + need > (size_t)ctx->p.hbm_budget) break;  // wait for memory to free up
-      ctx->budget_used += need;
-      f->budget_bytes = need;
-      f->state = 2;
+      if (n + f->n > ctx->slot_clusters) break;
+      n += f->n;
       batch.push_back(f);
-      ids.push_back(f->id);
       ctx->queue.pop_front();
     }
     if (batch.empty()) break;
-    cudaStream_t s = nullptr;
-    for (auto cand : ctx->serve_streams) {
-      bool used = false;
-      for (auto& b : ctx->inflight) used |= b.stream == cand;
-      if (!used) { s = cand; break; }
+    if (!sl.ws) {
+      const long long tcap = (long long)std::ceil((double)ctx->slot_clusters * ctx->p.tracklet_capacity) + 1024;
+      int rc = alloc_workspace(ctx, ctx->slot_clusters, tcap, ctx->p.max_batch_frames, sl.ws);
+      if (rc) return rc;
     }
-    // inputs were uploaded on the context stream
-    cudaEvent_t e;
-    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    CK(cudaEventRecord(e, ctx->stream));
-    CK(cudaStreamWaitEvent(s, e, 0));
-    cudaEventDestroy(e);
+    for (Frame* f : batch) {
+      int rc = upload_frame(ctx, f, sl.stream);
+      if (rc) return rc;
+      f->state = 2;
+    }
     std::shared_ptr<Workspace> ws;
-    int rc = run_batch(ctx, batch, s, ws);
+    int rc = run_batch(ctx, batch, sl.stream, ws, sl.ws);
     if (rc) return rc;
-    ctx->inflight.push_back({ws, ids, s});
+    sl.frames.clear();
+    for (Frame* f : batch) sl.frames.push_back(f->id);
+    sl.busy = true;
   }
   return TPC_OK;
 }
@@ -901,7 +980,9 @@ int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_
   for (;;) {
     int rc = serve_step(ctx);
     if (rc) return rc;
-    if (!ctx->finished.empty() || (ctx->inflight.empty() && ctx->queue.empty())) break;
+    bool busy = false;
+    for (auto& sl : ctx->slots) busy |= sl.busy;
+    if (!ctx->finished.empty() || (!busy && ctx->queue.empty())) break;
     if ((now_s() - t0) * 1e6 >= timeout_us) break;
     std::this_thread::yield();
   }

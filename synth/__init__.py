@@ -145,9 +145,9 @@ CONFIGS = {
     "batch16": dict(seed=3, n_collisions=-1, poisson_mean=5.0, mult_fixed=0, t_zero=0,
                     frame_us=100.0, x0_total=0.03),
     # full-size synchronous frame: 570 collisions over 128 orbits; the frame ends with the last orbit,
-    # so tracks of collisions in its last 90 us are cut (Sec. 2)
+    # so tracks of collisions in its last 90 us are cut (Sec. 2); clusters in generation order
     "full_570": dict(seed=4, n_collisions=570, mult_fixed=0, t_zero=0, frame_us=128 * ORBIT_US,
-                     tail_us=0.0, x0_total=0.03),
+                     tail_us=0.0, x0_total=0.03, shuffle=0),
     # serving stream frame: n_collisions set by the caller, 20 us per collision at 50 kHz
     "serve": dict(seed=5, n_collisions=1, mult_fixed=0, t_zero=0, frame_us=20.0, x0_total=0.03),
 }

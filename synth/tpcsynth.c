@@ -132,6 +132,13 @@ typedef struct {
   int q, coll;
 } sy_track;
 
+/* compact per-cluster record kept per chunk until the frame is assembled (truth kept apart) */
+typedef struct {
+  float y, w;
+  int32_t track;
+  uint8_t sector, row;
+} sy_crec;
+
 /* Propagate one primary and emit its clusters into out[] (<= SY_NROW records). */
 static int sy_track_clusters(const synth_params* p, const sy_track* t, int64_t tid, sy_rec* out) {
   sy_rng rng = sy_stream(p, SY_K_TRACK, (uint64_t)tid);
@@ -301,7 +308,8 @@ int synth_generate(const synth_params* p, synth_frame** out) {
   free(mult);
   /* signal clusters, in chunks of tracks (deterministic order) */
   int64_t nchunk = (ntrk + SY_CHUNK - 1) / SY_CHUNK;
-  sy_rec** cbuf = (sy_rec**)calloc(nchunk > 0 ? nchunk : 1, sizeof(sy_rec*));
+  sy_crec** cbuf = (sy_crec**)calloc(nchunk > 0 ? nchunk : 1, sizeof(sy_crec*));
+  double** tbuf = (double**)calloc(nchunk > 0 ? nchunk : 1, sizeof(double*));
   int64_t* ccnt = (int64_t*)calloc(nchunk + 1, sizeof(int64_t));
   int fail = 0;
   if (p->n_threads > 0) {
@@ -320,11 +328,24 @@ int synth_generate(const synth_params* p, synth_frame** out) {
       f->trk_ncl[t] = k;
       n += k;
     }
-    cbuf[c] = b;
+    sy_crec* cb = (sy_crec*)malloc(sizeof(sy_crec) * (size_t)(n > 0 ? n : 1));
+    double* tb = p->want_truth ? (double*)malloc(sizeof(double) * 5 * (size_t)(n > 0 ? n : 1)) : NULL;
+    if (!cb || (p->want_truth && !tb)) { free(b); free(cb); free(tb); fail = 1; continue; }
+    for (int64_t i = 0; i < n; ++i) {
+      cb[i].y = b[i].y; cb[i].w = b[i].w; cb[i].track = b[i].track;
+      cb[i].sector = b[i].sector; cb[i].row = b[i].row;
+      if (tb) memcpy(&tb[5 * i], b[i].truth, 5 * sizeof(double));
+    }
+    free(b);
+    cbuf[c] = cb;
+    tbuf[c] = tb;
     ccnt[c] = n;
   }
   free(trk);
-  if (fail) { for (int64_t c = 0; c < nchunk; ++c) free(cbuf[c]); free(cbuf); free(ccnt); sy_free_frame(f); return -2; }
+  if (fail) {
+    for (int64_t c = 0; c < nchunk; ++c) { free(cbuf[c]); free(tbuf[c]); }
+    free(cbuf); free(tbuf); free(ccnt); sy_free_frame(f); return -2;
+  }
   int64_t nsig = 0;
   for (int64_t c = 0; c < nchunk; ++c) nsig += ccnt[c];
   /* per (sector,row) signal counts and the occupied w range for noise */
@@ -333,7 +354,7 @@ int synth_generate(const synth_params* p, synth_frame** out) {
   double wlo = INFINITY, whi = -INFINITY;
   for (int64_t c = 0; c < nchunk; ++c)
     for (int64_t i = 0; i < ccnt[c]; ++i) {
-      const sy_rec* r = &cbuf[c][i];
+      const sy_crec* r = &cbuf[c][i];
       cnt[r->sector * SY_NROW + r->row]++;
       if (r->w < wlo) wlo = r->w;
       if (r->w > whi) whi = r->w;
@@ -359,21 +380,22 @@ int synth_generate(const synth_params* p, synth_frame** out) {
   f->truth_track = (int32_t*)malloc(na * sizeof(int32_t));
   if (p->want_truth) f->truth_state = (double*)malloc(na * 5 * sizeof(double));
   if (!f->sector || !f->row || !f->y || !f->w || !f->truth_track || (p->want_truth && !f->truth_state)) {
-    for (int64_t c = 0; c < nchunk; ++c) free(cbuf[c]);
-    free(cbuf); free(ccnt); sy_free_frame(f); return -2;
+    for (int64_t c = 0; c < nchunk; ++c) { free(cbuf[c]); free(tbuf[c]); }
+    free(cbuf); free(tbuf); free(ccnt); sy_free_frame(f); return -2;
   }
   {
     int64_t o = 0;
     for (int64_t c = 0; c < nchunk; ++c) {
       for (int64_t i = 0; i < ccnt[c]; ++i, ++o) {
-        const sy_rec* r = &cbuf[c][i];
+        const sy_crec* r = &cbuf[c][i];
         f->sector[o] = r->sector; f->row[o] = r->row; f->y[o] = r->y; f->w[o] = r->w;
         f->truth_track[o] = r->track;
-        if (p->want_truth) memcpy(&f->truth_state[5 * o], r->truth, 5 * sizeof(double));
+        if (p->want_truth) memcpy(&f->truth_state[5 * o], &tbuf[c][5 * i], 5 * sizeof(double));
       }
       free(cbuf[c]);
+      free(tbuf[c]);
     }
-    free(cbuf); free(ccnt);
+    free(cbuf); free(tbuf); free(ccnt);
     for (int sr = 0; sr < SY_NSEC * SY_NROW; ++sr) {
       sy_rng nr = sy_stream(p, SY_K_NOISE, (uint64_t)sr);
       (void)sy_u01(&nr); /* the draw used for the count above */

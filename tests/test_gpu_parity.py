@@ -185,21 +185,47 @@ def test_batch_alone_vs_in_the_mix(tracker):
         tracker.release(h)
 
 
-def test_serving_results_equal_plain(tracker):
-    frames = [synth.generate("serve", n_collisions=int(c), frame_id=i) for i, c in enumerate([3, 1, 7, 2, 5, 1])]
+def test_serving_results_equal_plain(tracker, torch_cuda):
+    """Continuous batching: each frame's tracks are identical alone and in the mix."""
+    import paper_2009_07515_gb300 as tpc
+    frames = [synth.generate("serve", n_collisions=int(c), frame_id=i) for i, c in enumerate([3, 1, 7, 2, 5, 1, 4, 6])]
     plain = [tracker.run(f.sector, f.row, f.y, f.w) for f in frames]
-    tickets = [tracker.submit(f.sector, f.row, f.y, f.w) for f in frames]
+    srv = tpc.Tracker(hbm_budget=3 << 30, max_batch_frames=3)
+    tickets = []
     done = []
+    for f in frames:  # arrivals interleaved with polls: later frames join while earlier ones run
+        tickets.append(srv.submit(f.sector, f.row, f.y, f.w))
+        done += srv.poll(64, 0)
     for _ in range(10000):
-        done += tracker.poll(64, 100000)
+        done += srv.poll(64, 100000)
         if len(done) == len(tickets):
             break
     assert sorted(done) == sorted(tickets)
     for t, p in zip(tickets, plain):
-        s = tracker.tracks(t)
+        s = srv.tracks(t)
         for k in p:
             assert np.array_equal(np.asarray(p[k]), np.asarray(s[k])), k
-        tracker.release(t)
+        srv.release(t)
+    srv.close()
+
+
+def test_serving_refuses_frames_beyond_the_budget(torch_cuda):
+    import paper_2009_07515_gb300 as tpc
+    srv = tpc.Tracker(hbm_budget=64 << 20)
+    f = synth.generate("pbpb_2x10000", mult_fixed=3000)
+    with pytest.raises(tpc.TpcError) as e:
+        srv.submit(f.sector, f.row, f.y, f.w)
+    assert e.value.code == tpc._lib.TPC_E_BUDGET
+    small = synth.generate("pp_500")
+    t = srv.submit(small.sector, small.row, small.y, small.w)
+    got = []
+    for _ in range(1000):
+        got += srv.poll(8, 100000)
+        if got:
+            break
+    assert got == [t] and srv.tracks(t)["n_tracks"] > 500
+    srv.release(t)
+    srv.close()
 
 
 def test_tracklet_capacity_regrows(torch_cuda):
