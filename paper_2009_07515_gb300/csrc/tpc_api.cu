@@ -141,6 +141,7 @@ struct Frame {
   int fidx = 0;
   std::vector<char> host_copy;      // serving: clusters submitted from host memory, until admitted
   bool served = false;
+  size_t input_bytes = 0;           // serving: device input counted against the waiting-input reserve
   double t_submit = 0, t_done = 0;
   // host results
   std::vector<int32_t> sector, ndf;
@@ -179,6 +180,7 @@ struct tpc_ctx {
   };
   std::vector<Slot> slots;
   long long slot_clusters = 0;
+  size_t queued_input_bytes = 0;    // device inputs of submitted frames not yet retired
   std::deque<tpc_frame_t> finished;
 };
 
@@ -499,6 +501,17 @@ int wait_ws(tpc_ctx* ctx, Workspace& ws, double timeout_s) {
     }
   }
   return TPC_OK;
+}
+
+int wait_event(tpc_ctx* ctx, cudaEvent_t e, double timeout_s) {
+  const double t0 = now_s();
+  for (;;) {
+    const cudaError_t q = cudaEventQuery(e);
+    if (q == cudaSuccess) return TPC_OK;
+    if (q != cudaErrorNotReady) return fail(ctx, TPC_E_CUDA, std::string("device: ") + cudaGetErrorString(q));
+    if (now_s() - t0 > timeout_s) return fail(ctx, TPC_E_TIMEOUT, "copy did not complete in time");
+    std::this_thread::yield();
+  }
 }
 
 int check_ws_errors(tpc_ctx* ctx, const Workspace& ws) {
@@ -839,6 +852,8 @@ int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame) {
     auto it = std::find(ctx->queue.begin(), ctx->queue.end(), frame);
     if (it != ctx->queue.end()) ctx->queue.erase(it);
   }
+  ctx->queued_input_bytes -= std::min(ctx->queued_input_bytes, f->input_bytes);
+  f->input_bytes = 0;
   if (f->served && (f->state == 2 || f->state == 3)) return fail(ctx, TPC_E_STATE, "frame is being tracked");
   drop_frame(ctx, f);
   return TPC_OK;
@@ -855,11 +870,29 @@ int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ti
   Frame* f = fr.get();
   f->n = clusters->n;
   f->served = true;
+  const size_t in_bytes = (size_t)f->n * 10;
   if (clusters->on_device) {
     f->d_sector = (uint8_t*)clusters->sector; f->d_row = (uint8_t*)clusters->row;
     f->d_y = (float*)clusters->y; f->d_w = (float*)clusters->w;
+  } else if (ctx->queued_input_bytes + in_bytes <= (size_t)(ctx->p.hbm_budget / 8)) {
+    // uploaded now (inputs of waiting frames may use an eighth of the budget); the copy ends
+    // before return, so the caller's buffers are free again
+    Frame* tmp = nullptr;
+    int rc = load_frame(ctx, clusters, tmp);
+    if (rc) return rc;
+    CK(cudaEventRecord(ctx->ev_sync, ctx->stream));
+    rc = wait_event(ctx, ctx->ev_sync, 120.0);
+    if (rc) return rc;
+    tmp->served = true;
+    tmp->input_bytes = in_bytes;
+    ctx->queued_input_bytes += in_bytes;
+    tmp->state = 1;
+    tmp->t_submit = now_s();
+    ctx->queue.push_back(tmp->id);
+    *ticket = tmp->id;
+    return TPC_OK;
   } else {
-    // kept on the host until admission: queued frames hold no device memory
+    // kept on the host until admission: this frame holds no device memory while it waits
     const size_t n = (size_t)f->n;
     f->host_copy.resize(10 * n + 1);
     char* h = f->host_copy.data();
@@ -930,6 +963,8 @@ int serve_step(tpc_ctx* ctx) {
       if (rc) return rc;
       release_ws_user(ctx, f);
       if (f->d_block) { cudaFreeAsync(f->d_block, sl.stream); f->d_block = nullptr; }
+      ctx->queued_input_bytes -= std::min(ctx->queued_input_bytes, f->input_bytes);
+      f->input_bytes = 0;
       f->host_copy.clear();
       f->host_copy.shrink_to_fit();
       f->state = 5;
@@ -958,6 +993,8 @@ int serve_step(tpc_ctx* ctx) {
       int rc = alloc_workspace(ctx, ctx->slot_clusters, tcap, ctx->p.max_batch_frames, sl.ws);
       if (rc) return rc;
     }
+    CK(cudaEventRecord(ctx->ev_sync, ctx->stream));  // uploads made at submit time
+    CK(cudaStreamWaitEvent(sl.stream, ctx->ev_sync, 0));
     for (Frame* f : batch) {
       int rc = upload_frame(ctx, f, sl.stream);
       if (rc) return rc;

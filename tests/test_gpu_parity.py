@@ -211,8 +211,8 @@ def test_serving_results_equal_plain(tracker, torch_cuda):
 
 def test_serving_refuses_frames_beyond_the_budget(torch_cuda):
     import paper_2009_07515_gb300 as tpc
-    srv = tpc.Tracker(hbm_budget=64 << 20)
-    f = synth.generate("pbpb_2x10000", mult_fixed=3000)
+    srv = tpc.Tracker(hbm_budget=256 << 20, max_batch_frames=1)
+    f = synth.generate("pbpb_2x10000")
     with pytest.raises(tpc.TpcError) as e:
         srv.submit(f.sector, f.row, f.y, f.w)
     assert e.value.code == tpc._lib.TPC_E_BUDGET
