@@ -56,7 +56,7 @@ typedef struct {
   double bz;              /* solenoid field, T (0.5) */
   double ky, kw, eps;     /* neighbour windows |dy| <= ky*dx + eps, |dw| <= kw*dx + eps (cm) */
   double chi_n_max;       /* neighbour mid-point deviation cut dy^2 + dw^2 (cm^2) */
-  int32_t lmin;           /* minimum cleaned-chain length of a start hit (3) */
+  int32_t lmin;           /* minimum cleaned-chain length of a start hit (6) */
   double sigma_y, sigma_w;/* cluster errors (cm) */
   double chi2_hit_max;    /* Kalman hit acceptance, 2 dof (16) */
   int32_t n_miss_max;     /* consecutive empty rows ending an extension (5) */

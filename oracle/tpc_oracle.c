@@ -78,7 +78,7 @@ void ORACLE_SYM(default_params)(oracle_params* p) {
   p->bz = 0.5;
   p->ky = 2.0; p->kw = 2.4; p->eps = 0.5;
   p->chi_n_max = 0.2;
-  p->lmin = 3;
+  p->lmin = 6;
   p->sigma_y = 0.1; p->sigma_w = 0.1;
   p->chi2_hit_max = 16.0;
   p->n_miss_max = 5;
