@@ -3,10 +3,12 @@
 // K2 (cellular-automaton neighbour finding): for every hit i of row r (1 <= r <= 150) the pair
 // (d in row r-1, u in row r+1) inside the slope windows that minimises the mid-point deviation
 // chi_n = (y_i - y_mid)^2 + (w_i - w_mid)^2, accepted if chi_n <= chi_n_max; ties go to the
-// smaller (w, y, input index) of d, then of u. A CTA takes one segment (frame, sector, row) at a
-// time; each warp takes 32 consecutive hits of it. The w-columns of the two adjacent rows that the
-// 32 windows touch are one contiguous range each, which lane 0 stages into the warp's shared-memory
-// slots with 1-D bulk TMA copies (cp.async.bulk, completion on the warp's mbarrier; no multicast).
+// smaller (w, y, input index) of d, then of u. Work is split into chunks of 32 consecutive hits of
+// one segment (frame, sector, row), listed in segment work-item order (inner rows first) by
+// k_chunk_count / scan / k_chunk_fill; each warp takes the next chunk from a device counter, so warps
+// never wait for one another. The w-columns of the two adjacent rows that the 32 windows touch are
+// one contiguous range each, which lane 0 stages into the warp's shared-memory slots with 1-D bulk
+// TMA copies (cp.async.bulk, completion on the warp's mbarrier; no multicast).
 // Each lane then scans its own candidate bins (one contiguous range per w-column) out of shared
 // memory. A range too large for a slot is read from global memory instead (same arithmetic, same
 // result).
@@ -135,6 +137,28 @@ __device__ __forceinline__ void pair_step(const Work& W, int gd, int gu, float y
   if (better) { best = chi; bd = d; bu = u; }
 }
 
+// chunks of 32 hits of every segment work item (rows 0 and 151 too: their links are cleared)
+__global__ void __launch_bounds__(256) k_chunk_count(Work W) {
+  const int nf = W.batch->nf;
+  const uint32_t nseg = W.cnt->nseg;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
+    const int g = segment_of_item((int)k, nf);
+    const uint32_t a = W.bin_start[W.seg_bb[g]], b = W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
+    W.k2_off[k] = (b - a + 31u) / 32u;
+  }
+}
+// (segment, first position) of every chunk, from the scanned counts
+__global__ void __launch_bounds__(256) k_chunk_fill(Work W) {
+  const int nf = W.batch->nf;
+  const uint32_t nseg = W.cnt->nseg;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
+    const int g = segment_of_item((int)k, nf);
+    const uint32_t a = W.bin_start[W.seg_bb[g]];
+    const uint32_t c1 = W.k2_off[k + 1] < (uint32_t)W.k2cap ? W.k2_off[k + 1] : (uint32_t)W.k2cap;
+    for (uint32_t j = W.k2_off[k]; j < c1; ++j) W.k2_tab[j] = make_uint2((uint32_t)g, a + 32u * (j - W.k2_off[k]));
+  }
+}
+
 template <bool kPacked>
 __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use_tma) {
   constexpr int kRec = kPacked ? 4 : 8;       // bytes per staged record
@@ -144,27 +168,29 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
   __shared__ float2 ucand[kK2Warps][kK2UCap][32];
   __shared__ int upos[kK2Warps][kK2UCap][32];
   __shared__ __align__(8) uint64_t bar[kK2Warps];
-  __shared__ int s_item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const BatchDesc* B = W.batch;
   if (lane == 0) mbar_init(&bar[warp], 1);
   __syncwarp();
   uint32_t parity = 0;
-  bool aborted = false;
+  const uint32_t nch = W.cnt->n_chunks < (uint32_t)W.k2cap ? W.cnt->n_chunks : (uint32_t)W.k2cap;
+  // lane 0 takes the next chunk one iteration ahead, so the atomic's latency overlaps the work
+  uint32_t k_next = 0;
+  if (lane == 0) k_next = atomicAdd(&W.cnt->k2_next, 1u);
   for (;;) {
-    if (__syncthreads_or(aborted)) break;  // a timed-out copy wait ends the whole block
-    const int g = next_segment(&W.cnt->seg_next[0], B->nf, &s_item);
-    if (g < 0) break;
+    const uint32_t k = __shfl_sync(0xffffffffu, k_next, 0);
+    if (k >= nch) break;
+    const uint2 e = W.k2_tab[k];
+    if (lane == 0) k_next = atomicAdd(&W.cnt->k2_next, 1u);
+    const int g = (int)e.x, c0 = (int)e.y;
     const int r = (g % kSegPerFrame) % kNRow;
-    const int a = (int)W.bin_start[W.seg_bb[g]];
     const int b = (int)W.bin_start[W.seg_bb[g] + W.seg_nb[g]];
     if (r == 0 || r == kNRow - 1) {
-      for (int i = a + threadIdx.x; i < b; i += blockDim.x) W.links[i] = make_int2(-1, -1);
+      if (c0 + lane < b) W.links[c0 + lane] = make_int2(-1, -1);
       continue;
     }
     const float wy_dn = Q.wy_dn[r], ww_dn = Q.ww_dn[r], wy_up = Q.wy_up[r], ww_up = Q.ww_up[r];
     const float fm = Q.f_mid[r];
-    for (int c0 = a + 32 * warp; c0 < b; c0 += 32 * kK2Warps) {
+    {
       const int i = c0 + lane;
       const bool valid = i < b;
       const float2 hi = valid ? hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, i) : make_float2(0.f, 0.f);
@@ -198,13 +224,14 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
       cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
       base1 = __shfl_sync(0xffffffffu, base1, 0);
       cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
-      if (!mbar_wait_bounded(&bar[warp], parity)) {
-        // give the copies in flight a second bounded wait, then stop using the stage
-        (void)mbar_wait_bounded(&bar[warp], parity);
+      const bool ok = mbar_wait_bounded(&bar[warp], parity);
+      if (!__all_sync(0xffffffffu, ok)) {
+        // give the copies in flight a second bounded wait, then this warp stops (its stage is not
+        // used again; the other warps go on)
+        if (!ok) (void)mbar_wait_bounded(&bar[warp], parity);
         if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
-        aborted = true;
+        break;
       }
-      if (aborted) break;
       parity ^= 1u;
       const RowView vd{stage_mem[warp][0], base0, cnt0};
       const RowView vu{stage_mem[warp][1], base1, cnt1};

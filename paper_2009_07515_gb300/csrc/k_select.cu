@@ -102,7 +102,7 @@ __global__ void k_reset_counters(Work W) {
   }
   if (threadIdx.x == 0) {
     c->err = 0; c->n_starts = 0; c->n_tracklets = 0; c->k5_next = 0; c->n_bins = 0;
-    c->seg_next[0] = 0; c->seg_next[1] = 0; c->seg_next[2] = 0;
+    c->seg_next[0] = 0; c->seg_next[1] = 0; c->seg_next[2] = 0; c->n_chunks = 0; c->k2_next = 0;
     c->n_sorted = 0; c->n_tracks = 0; c->n_track_hits = 0; c->n_steps = 0; c->n_tracklet_hits = 0;
   }
 }

@@ -30,6 +30,8 @@ __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
 __global__ void k_scatter(Work);
+__global__ void k_chunk_count(Work);
+__global__ void k_chunk_fill(Work);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_starts(Work, DevParams);
 __global__ void k_start_order(Work);
@@ -240,6 +242,8 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.hq, ctx->p.packed ? 4 * (size_t)(ws->ncap + 4) : 0},
       {(void**)&W.hcol, ctx->p.packed ? 2 * (size_t)ws->ncap : 0},
       {(void**)&W.horig, 4 * (size_t)ws->ncap},
+      {(void**)&W.k2_off, 4 * (size_t)(ws->scap + 1)},
+      {(void**)&W.k2_tab, 8 * (size_t)(ws->ncap / 32 + ws->scap + 1)},
       {(void**)&W.links, 8 * (size_t)ws->ncap},
       {(void**)&W.clinks, 8 * (size_t)ws->ncap},
       {(void**)&W.seg_nstart, 4 * (size_t)(ws->scap + 1)},
@@ -277,6 +281,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   ws->d_desc = (BatchDesc*)p_desc;
   W.batch = ws->d_desc;
   W.ncap = ws->ncap; W.scap = ws->scap; W.bcap = ws->bcap; W.tcap = ws->tcap; W.scan_tmp_cap = ws->scan_cap;
+  W.k2cap = ws->ncap / 32 + ws->scap + 1;
   W.packed = ctx->p.packed ? 1 : 0;
   CK(cudaMallocHost(&ws->h_desc, sizeof(BatchDesc)));
   CK(cudaMallocHost(&ws->h_cnt, sizeof(DevCounters)));
@@ -366,6 +371,9 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // scatter
   ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W);
   mark(ki++);  // neighbours
+  ++nl; k_chunk_count<<<G, 256, 0, s>>>(W);
+  scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);
+  ++nl; k_chunk_fill<<<G, 256, 0, s>>>(W);
   ++nl; launch_neighbours(ctx->p.packed, ctx->grid_neighbours, s, W, Q, ctx->p.k2_tma);
   mark(ki++);  // clean
   ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);

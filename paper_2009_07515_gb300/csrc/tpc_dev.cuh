@@ -89,6 +89,8 @@ struct DevCounters {
   uint32_t n_tracklets;   // min(n_starts, tcap)
   uint32_t k5_next;       // work counter of the tracklet kernel
   uint32_t seg_next[3];   // segment work counters of the neighbour, cleaning and start kernels
+  uint32_t n_chunks;      // 32-hit chunks of the neighbour kernel
+  uint32_t k2_next;       // chunk work counter of the neighbour kernel
   uint32_t n_bins;        // total bins of the batch
   uint32_t n_sorted;      // clusters placed in the grid
   uint32_t n_tracks;
@@ -118,6 +120,8 @@ struct Work {
   uint16_t* hcol;        // [ncap]     16-bit storage: grid column of each position
   uint32_t* horig;       // [ncap]
   // links
+  uint32_t* k2_off;      // [scap + 1] 32-hit chunks of every segment work item, scanned
+  uint2* k2_tab;         // [k2cap] (segment, first position) of every chunk, in work-item order
   int2* links;           // [ncap]
   int2* clinks;          // [ncap]
   uint32_t* seg_nstart;  // [scap + 1] -> scanned
@@ -139,7 +143,7 @@ struct Work {
   uint32_t* tr_hits;     // [ncap] output hits (frame-local input indices)
   // scan scratch
   uint32_t* scan_tmp;    // [scan_tmp_cap]
-  long long ncap, scap, bcap, tcap, scan_tmp_cap;
+  long long ncap, scap, bcap, tcap, scan_tmp_cap, k2cap;
   int packed;            // 1: 16-bit cluster storage (hq, hcol), 0: FP32 (hyw)
 };
 

@@ -39,6 +39,8 @@ __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
 void make_dev_params(const tpc_params& p, DevParams& d);
 void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
+__global__ void k_chunk_count(Work);
+__global__ void k_chunk_fill(Work);
 }  // namespace tpc
 
 using namespace tpc;
@@ -52,7 +54,7 @@ constexpr size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct StaticLayout {
   size_t cnt, desc, seg_cnt, seg_nb, seg_bb, seg_dim, seg_geo, bin_start, rank, hyw, horig, links, clinks,
-      seg_nstart, scan_tmp, total;
+      seg_nstart, scan_tmp, k2_off, k2_tab, total;
 };
 
 constexpr StaticLayout static_layout(long long ncap, long long bcap) {
@@ -75,6 +77,8 @@ constexpr StaticLayout static_layout(long long ncap, long long bcap) {
   L.clinks = o;     o = al(o + 8 * (size_t)ncap);
   L.seg_nstart = o; o = al(o + 4 * (size_t)(scap + 1));
   L.scan_tmp = o;   o = al(o + 4 * (size_t)ntiles);
+  L.k2_off = o;     o = al(o + 4 * (size_t)(scap + 1));
+  L.k2_tab = o;     o = al(o + 8 * (size_t)(ncap / 32 + scap + 1));
   L.total = o;
   return L;
 }
@@ -169,11 +173,14 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   W.clinks = (int2*)(b + L.clinks);
   W.seg_nstart = (uint32_t*)(b + L.seg_nstart);
   W.scan_tmp = (uint32_t*)(b + L.scan_tmp);
+  W.k2_off = (uint32_t*)(b + L.k2_off);
+  W.k2_tab = (uint2*)(b + L.k2_tab);
   W.ncap = kStaticMaxClusters;
   W.scap = kSegPerFrame;
   W.bcap = bcap;
   W.tcap = 0;
   W.scan_tmp_cap = (bcap + 1 + 2047) / 2048 + 16;
+  W.k2cap = kStaticMaxClusters / 32 + kSegPerFrame + 1;
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the frame descriptor, copied from the stack (a pageable source: the copy is staged before return)
@@ -205,6 +212,9 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   k_bin_rank<<<8 * G, 256, 0, s>>>(W);
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
   k_scatter<<<8 * G, 256, 0, s>>>(W);
+  k_chunk_count<<<G, 256, 0, s>>>(W);
+  scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);
+  k_chunk_fill<<<G, 256, 0, s>>>(W);
   launch_neighbours(0, 4 * G, s, W, Q, p.k2_tma);
   k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   if (n > 0) {
