@@ -288,6 +288,9 @@ def main():
     ap.add_argument("--serve-loads", default="0.9", help="comma-separated arrival rates / plain service rate")
     ap.add_argument("--serve-frames", type=int, default=80)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
+    ap.add_argument("--shape", default="",
+                    help='launch shape as JSON tpc_params overrides, e.g. \'{"k5_block": 64}\' (no autotuning)')
     ap.add_argument("--profile-only", action="store_true",
                     help="only track the workload warmup + steps times (eager launches), for ncu captures")
     args = ap.parse_args()
@@ -313,7 +316,8 @@ def main():
 
     frame = synth.generate(args.workload)
     n = frame.n
-    tr = tpc.Tracker()
+    shape = json.loads(args.shape) if args.shape else {}
+    tr = tpc.Tracker(**shape)
     # inputs resident in HBM
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
     h = tr.load(*d_in)
@@ -332,6 +336,13 @@ def main():
                           "runs": args.warmup + args.steps}), flush=True)
         tr.close()
         return
+    tuned = None
+    if not shape and not args.no_autotune:
+        # the library's autotuner picks the launch shapes on this workload (results do not depend
+        # on them); the chosen shape is reported in config.launch_shape
+        rep = tr.autotune([h], reps=3)
+        tuned = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
+        tuned["configs_timed"] = len(rep["entries"])
     for _ in range(args.warmup):
         tr.track(h, stream)
     res = tr.tracks(h)
@@ -360,7 +371,7 @@ def main():
     kt_runs = []
     for _ in range(5):
         flush.zero_()
-        tr.track(h)
+        tr.track(h, stream)
         tr.tracks(h)
         kt_runs.append(tr.kernel_times())
     tr.set_timing(False)
@@ -405,7 +416,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "clusters_per_frame": n, "tracks_per_frame": int(res["n_tracks"]),
                        "tracklets_per_frame": int(stats.get("tracklets", 0)), "storage": "fp32", "l2": "flushed (512 MB write) before each step",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"replicas x{ws}",
+                       "launch_shape": tuned if tuned is not None else (shape or "default"),
+                       "autotuned": tuned is not None},
             "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "kernels_ms": kernels}
     tr.release(h)

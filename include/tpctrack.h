@@ -68,16 +68,25 @@ typedef struct {
   double cov0[5];         /* seed covariance diagonal */
   /* storage / runtime */
   int32_t packed;         /* 1: store cluster coordinates as 16-bit offsets in their grid bin */
-  float bin_occupancy;    /* target clusters per w-bin of the search grid (autotuned if <= 0) */
+  float bin_occupancy;    /* target clusters per bin of the search grid (2); a launch-shape knob */
   float tracklet_capacity;/* tracklet slots per cluster reserved in a workspace (0.08) */
   int64_t hbm_budget;     /* serving admission budget in bytes (80 GB) */
   int32_t max_batch_frames; /* frames per batched launch (16) */
   int32_t use_graphs;     /* 1: replay the kernel sequence as a CUDA graph */
+  /* launch shapes: no result depends on them; tpc_autotune() picks them by timing */
+  int32_t k2_warps;       /* neighbour search: warps per block, each on 32 hits of one row at a
+                             time (4 or 8) */
   int32_t k2_tma;         /* 1: neighbour search stages adjacent rows in shared memory with bulk
-                             TMA copies; 0: it reads them through L1 (same results) */
-  int32_t k5_occupancy;   /* tracklet kernel variant: resident 128-thread blocks per SM it is
-                             compiled for (4 or 8; 0 = the autotuned choice) */
-  int32_t k5_longest_first; /* 1: tracklets are processed longest chain first (same results) */
+                             TMA copies; 0: it reads them through L1 */
+  int32_t k5_block;       /* tracklet construction: threads per block, one tracklet per thread at
+                             a time (64, 128 or 256) */
+  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64 or 128) */
+  int32_t k5_blocks_per_sm; /* tracklet blocks launched per SM (0 = all that fit); with k5_block
+                             it sets how many tracklets each warp builds */
+  int32_t k5_order;       /* tracklet processing order: 0 canonical, 1 longest chain first,
+                             2 innermost start row first */
+  int32_t autotune;       /* 1: the first tpc_track_batch / tpc_track_sectors call runs
+                             tpc_autotune() on its batch first (0) */
 } tpc_params;
 
 /* Clusters of one time frame, structure of arrays in the caller's order (n entries each).
@@ -170,6 +179,29 @@ int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n
 int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */
+/* ---- autotuning of the launch shapes (the batched persistent path's rows-per-block and
+ * tracklets-per-warp choices). One timed configuration: */
+typedef struct {
+  float bin_occupancy;
+  int32_t k2_warps, k2_tma, k5_block, k5_regs, k5_blocks_per_sm, k5_order;
+  float ms;        /* median device time of the stages the knob being tuned acts on */
+  float total_ms;  /* median device time of the whole sequence */
+  int32_t stage;   /* what ms measures: 0 all stages, 1 neighbour search, 2 chains + tracklets */
+} tpc_tune_entry;
+typedef struct {
+  int32_t n_entries;               /* configurations timed, in the order they were timed */
+  const tpc_tune_entry* entries;   /* owned by the context until the next tpc_autotune call */
+  int32_t best;                    /* index of the chosen configuration (now the context's) */
+} tpc_tune_report;
+/* Times launch shapes on the given frames (a batch, as tpc_track_batch runs it) and keeps the
+ * fastest for the context's later runs. Coordinate descent, each candidate run reps + 1 times (the
+ * first discarded, median of the rest) with events between stages on the context's stream:
+ * bin_occupancy in {1, 2, 4} on the whole sequence; then (k2_warps, k2_tma) on the neighbour
+ * search; then (k5_block, k5_regs), k5_order and k5_blocks_per_sm on chains + tracklets. Results of
+ * the frames are those of any shape. Blocks until done. Errors: TPC_E_INVAL (bad list, reps < 1),
+ * TPC_E_STATE (a frame queued for serving), or any error tpc_track_batch returns. */
+int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int32_t reps, tpc_tune_report* out);
+
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable);
 int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 

@@ -93,6 +93,19 @@ class Tracker:
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream)
         self._check(self.lib.tpc_track_batch(self.ctx, arr, len(frames), s))
 
+    TUNE_KEYS = ("bin_occupancy", "k2_warps", "k2_tma", "k5_block", "k5_regs", "k5_blocks_per_sm", "k5_order",
+                 "ms", "total_ms", "stage")
+
+    def autotune(self, frames, reps: int = 3) -> dict:
+        """Time launch shapes on a batch (tpc_autotune) and keep the fastest. Returns the timed
+        configurations (``entries``, in timing order) and the chosen one (``best``)."""
+        frames = [frames] if isinstance(frames, int) else list(frames)
+        arr = (ctypes.c_uint64 * len(frames))(*frames)
+        rep = _lib.tpc_tune_report()
+        self._check(self.lib.tpc_autotune(self.ctx, arr, len(frames), int(reps), ctypes.byref(rep)))
+        entries = [{k: getattr(rep.entries[i], k) for k in self.TUNE_KEYS} for i in range(rep.n_entries)]
+        return {"entries": entries, "best": entries[rep.best] if rep.best >= 0 else None}
+
     def tracks(self, frame: int) -> dict:
         t = _lib.tpc_tracks()
         self._check(self.lib.tpc_get_tracks(self.ctx, ctypes.c_uint64(frame), ctypes.byref(t)))

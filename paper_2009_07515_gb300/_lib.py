@@ -51,9 +51,13 @@ class tpc_params(ctypes.Structure):
         ("hbm_budget", ctypes.c_int64),
         ("max_batch_frames", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
+        ("k2_warps", ctypes.c_int32),
         ("k2_tma", ctypes.c_int32),
-        ("k5_occupancy", ctypes.c_int32),
-        ("k5_longest_first", ctypes.c_int32),
+        ("k5_block", ctypes.c_int32),
+        ("k5_regs", ctypes.c_int32),
+        ("k5_blocks_per_sm", ctypes.c_int32),
+        ("k5_order", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -91,6 +95,25 @@ class tpc_kernel_times(ctypes.Structure):
     ]
 
 
+class tpc_tune_entry(ctypes.Structure):
+    _fields_ = [
+        ("bin_occupancy", ctypes.c_float),
+        ("k2_warps", ctypes.c_int32), ("k2_tma", ctypes.c_int32), ("k5_block", ctypes.c_int32),
+        ("k5_regs", ctypes.c_int32), ("k5_blocks_per_sm", ctypes.c_int32), ("k5_order", ctypes.c_int32),
+        ("ms", ctypes.c_float),
+        ("total_ms", ctypes.c_float),
+        ("stage", ctypes.c_int32),
+    ]
+
+
+class tpc_tune_report(ctypes.Structure):
+    _fields_ = [
+        ("n_entries", ctypes.c_int32),
+        ("entries", ctypes.POINTER(tpc_tune_entry)),
+        ("best", ctypes.c_int32),
+    ]
+
+
 _ctx_p = ctypes.c_void_p
 _frame = ctypes.c_uint64
 
@@ -111,6 +134,8 @@ SIGNATURES = [
     ("tpc_get_links", ctypes.c_int, [_ctx_p, _frame, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64]),
     ("tpc_get_counts", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("tpc_get_stats", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
+    ("tpc_autotune", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(tpc_tune_report)]),
     ("tpc_set_timing", ctypes.c_int, [_ctx_p, ctypes.c_int32]),
     ("tpc_get_kernel_times", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_kernel_times)]),
     ("tpc_links_static", ctypes.c_int, [ctypes.POINTER(tpc_params), ctypes.POINTER(tpc_clusters), ctypes.c_void_p,

@@ -98,7 +98,6 @@ __device__ __forceinline__ void column_range(const Work& W, int g, float lo, flo
 // flat loop (the w-columns one after the other), first over row r+1, keeping the candidates that
 // pass the window in a per-lane shared-memory list, then over row r-1, pairing each passing
 // candidate with the listed ones.
-constexpr int kK2Warps = 8;
 constexpr int kK2Slot = 192;  // staged FP32 records per adjacent row per warp (twice as many 16-bit)
 constexpr int kK2UCap = 6;    // listed row r+1 candidates per lane (more: rescan the row)
 
@@ -159,15 +158,15 @@ __global__ void __launch_bounds__(256) k_chunk_fill(Work W) {
   }
 }
 
-template <bool kPacked>
-__global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use_tma) {
+template <bool kPacked, int kWarps>
+__global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q, int use_tma) {
   constexpr int kRec = kPacked ? 4 : 8;       // bytes per staged record
   constexpr int kAlign = 16 / kRec;           // records per 16 bytes
   constexpr int kSlot = kPacked ? 2 * kK2Slot : kK2Slot;
-  __shared__ __align__(16) float2 stage_mem[kK2Warps][2][kK2Slot + 2];
-  __shared__ float2 ucand[kK2Warps][kK2UCap][32];
-  __shared__ int upos[kK2Warps][kK2UCap][32];
-  __shared__ __align__(8) uint64_t bar[kK2Warps];
+  __shared__ __align__(16) float2 stage_mem[kWarps][2][kK2Slot + 2];
+  __shared__ float2 ucand[kWarps][kK2UCap][32];
+  __shared__ int upos[kWarps][kK2UCap][32];
+  __shared__ __align__(8) uint64_t bar[kWarps];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) mbar_init(&bar[warp], 1);
   __syncwarp();
@@ -279,14 +278,28 @@ __global__ void __launch_bounds__(256) k_neighbours(Work W, DevParams Q, int use
   }
 }
 
-void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma) {
-  if (packed) k_neighbours<true><<<grid, 256, 0, s>>>(W, Q, use_tma);
-  else k_neighbours<false><<<grid, 256, 0, s>>>(W, Q, use_tma);
+// warps per block: 4 or 8 (32-hit row chunks a block works on at a time)
+bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma) {
+  if (warps == 4) {
+    if (packed) k_neighbours<true, 4><<<grid, 128, 0, s>>>(W, Q, use_tma);
+    else k_neighbours<false, 4><<<grid, 128, 0, s>>>(W, Q, use_tma);
+  } else if (warps == 8) {
+    if (packed) k_neighbours<true, 8><<<grid, 256, 0, s>>>(W, Q, use_tma);
+    else k_neighbours<false, 8><<<grid, 256, 0, s>>>(W, Q, use_tma);
+  } else {
+    return false;
+  }
+  return true;
 }
-int neighbours_blocks_per_sm(int packed) {
+int neighbours_blocks_per_sm(int packed, int warps) {
   int nb = 0;
-  if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true>, 256, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false>, 256, 0);
+  if (warps == 4) {
+    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true, 4>, 128, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false, 4>, 128, 0);
+  } else if (warps == 8) {
+    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true, 8>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false, 8>, 256, 0);
+  }
   return nb;
 }
 

@@ -21,8 +21,16 @@
 
 namespace tpc {
 
+// Processing-order key of a tracklet (a counting sort over kNRow + 1 buckets): order 1 takes the
+// longest chains first, order 2 the innermost start rows first (a start row predicts the row
+// steps: the outward pass runs from it to the track's end, the inward pass back over the track).
+__device__ __forceinline__ int order_key(const Work& W, int order, uint32_t t, int m) {
+  if (order == 1) return kNRow - m;
+  return ((int)W.starts[t].y % kSegPerFrame) % kNRow;
+}
+
 // (middle hit, last hit, chain length) of every start hit
-__global__ void __launch_bounds__(256) k_chains(Work W) {
+__global__ void __launch_bounds__(256) k_chains(Work W, int order) {
   const uint32_t ntl = W.cnt->n_tracklets;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
     int head = (int)W.starts[t].x, mid = head, m = 1;
@@ -34,14 +42,13 @@ __global__ void __launch_bounds__(256) k_chains(Work W) {
       if ((m & 1) == 0) mid = W.clinks[mid].y;
     }
     W.chains[t] = make_int4(mid, head, m, 0);
-    if (W.len_cnt) atomicAdd(&W.len_cnt[kNRow - m], 1u);
+    if (order) atomicAdd(&W.len_cnt[order_key(W, order, t, m)], 1u);
   }
 }
 
-// Processing order of the tracklet kernel: longest chain first (a counting sort by chain length;
-// the order inside a bucket is arbitrary, and no result depends on it: every tracklet reads only
-// the grid and the links and writes only its own outputs). It shortens the tail where few lanes
-// still run long tracklets.
+// Processing order of the tracklet kernel (order_key; the order inside a bucket is arbitrary, and
+// no result depends on it: every tracklet reads only the grid and the links and writes only its
+// own outputs). Long tracklets first shorten the tail where few lanes still run.
 __global__ void k_length_offsets(Work W) {
   if (threadIdx.x == 0) {
     uint32_t s = 0;
@@ -52,12 +59,10 @@ __global__ void k_length_offsets(Work W) {
     }
   }
 }
-__global__ void __launch_bounds__(256) k_length_scatter(Work W) {
+__global__ void __launch_bounds__(256) k_length_scatter(Work W, int order) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
-    const int m = W.chains[t].z;
-    W.order[atomicAdd(&W.len_cnt[kNRow - m], 1u)] = t;
-  }
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x)
+    W.order[atomicAdd(&W.len_cnt[order_key(W, order, t, W.chains[t].z)], 1u)] = t;
 }
 
 __device__ __forceinline__ void reset_cov(const DevParams& Q, float* C) {
@@ -112,8 +117,10 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
   return best;
 }
 
-template <int kMinBlocks, bool kPacked>
-__global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams Q, int ordered) {
+// kThreads threads per block, compiled for kRegs registers per thread (the resident blocks per SM
+// follow: 65536 / (kThreads * kRegs))
+template <int kThreads, int kRegs, bool kPacked>
+__global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_tracklets(Work W, DevParams Q, int ordered) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const long long tcap = W.tcap;
   float P[5], C[15], SP[5], SC[15];
@@ -250,27 +257,39 @@ __global__ void __launch_bounds__(128, kMinBlocks) k_tracklets(Work W, DevParams
   }
 }
 
-// host-side launchers (the kernel templates stay in this translation unit)
-void launch_tracklets(int variant, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
+// host-side launchers (the kernel templates stay in this translation unit). Shapes: threads per
+// block 64, 128 or 256, each compiled for 64 or 128 registers per thread.
+template <int kT, int kR>
+static void launch_shape(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
+  if (packed) k_tracklets<kT, kR, true><<<grid, kT, 0, s>>>(W, Q, ordered);
+  else k_tracklets<kT, kR, false><<<grid, kT, 0, s>>>(W, Q, ordered);
+}
+template <int kT, int kR>
+static int shape_blocks(int packed) {
+  int nb = 0;
+  if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<kT, kR, true>, kT, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<kT, kR, false>, kT, 0);
+  return nb;
+}
+// false for a shape that is not compiled
+bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
                       int ordered) {
-  if (variant == 8) {
-    if (packed) k_tracklets<8, true><<<grid, 128, 0, s>>>(W, Q, ordered);
-    else k_tracklets<8, false><<<grid, 128, 0, s>>>(W, Q, ordered);
-  } else {
-    if (packed) k_tracklets<4, true><<<grid, 128, 0, s>>>(W, Q, ordered);
-    else k_tracklets<4, false><<<grid, 128, 0, s>>>(W, Q, ordered);
+  const bool r64 = regs <= 64;
+  switch (threads) {
+    case 64: r64 ? launch_shape<64, 64>(packed, grid, s, W, Q, ordered) : launch_shape<64, 128>(packed, grid, s, W, Q, ordered); return true;
+    case 128: r64 ? launch_shape<128, 64>(packed, grid, s, W, Q, ordered) : launch_shape<128, 128>(packed, grid, s, W, Q, ordered); return true;
+    case 256: r64 ? launch_shape<256, 64>(packed, grid, s, W, Q, ordered) : launch_shape<256, 128>(packed, grid, s, W, Q, ordered); return true;
+    default: return false;
   }
 }
-int tracklets_blocks_per_sm(int variant, int packed) {
-  int nb = 0;
-  if (variant == 8) {
-    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<8, true>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<8, false>, 128, 0);
-  } else {
-    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<4, true>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<4, false>, 128, 0);
+int tracklets_blocks_per_sm(int threads, int regs, int packed) {
+  const bool r64 = regs <= 64;
+  switch (threads) {
+    case 64: return r64 ? shape_blocks<64, 64>(packed) : shape_blocks<64, 128>(packed);
+    case 128: return r64 ? shape_blocks<128, 64>(packed) : shape_blocks<128, 128>(packed);
+    case 256: return r64 ? shape_blocks<256, 64>(packed) : shape_blocks<256, 128>(packed);
+    default: return 0;
   }
-  return nb;
 }
 
 }  // namespace tpc

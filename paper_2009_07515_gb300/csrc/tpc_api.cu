@@ -35,14 +35,14 @@ __global__ void k_chunk_fill(Work);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_starts(Work, DevParams);
 __global__ void k_start_order(Work);
-__global__ void k_chains(Work);
+__global__ void k_chains(Work, int);
 __global__ void k_length_offsets(Work);
-__global__ void k_length_scatter(Work);
-void launch_tracklets(int variant, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
+__global__ void k_length_scatter(Work, int);
+bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
                       int ordered);
-int tracklets_blocks_per_sm(int variant, int packed);
-void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
-int neighbours_blocks_per_sm(int packed);
+int tracklets_blocks_per_sm(int threads, int regs, int packed);
+bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
+int neighbours_blocks_per_sm(int packed, int warps);
 __global__ void k_votes(Work, DevParams);
 __global__ void k_kept(Work, DevParams);
 __global__ void k_write_tracks(Work, DevParams);
@@ -109,12 +109,25 @@ const char* kKernelNames[] = {"reset",  "seg_hist", "seg_layout", "scan_seg",  "
                               "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "frame_off"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
+// Launch shape: the knobs that change the speed of the sequence, never its results.
+struct Shape {
+  float occ = 2.0f;      // grid bin occupancy
+  int k2_warps = 8, k2_tma = 1;
+  int k5_block = 128, k5_regs = 64, k5_bps = 0, k5_order = 0;
+  bool operator==(const Shape& o) const {
+    return occ == o.occ && k2_warps == o.k2_warps && k2_tma == o.k2_tma && k5_block == o.k5_block &&
+           k5_regs == o.k5_regs && k5_bps == o.k5_bps && k5_order == o.k5_order;
+  }
+};
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 struct Workspace {
   long long ncap = 0, scap = 0, bcap = 0, tcap = 0, scan_cap = 0;
+  Shape shape;                     // launch shape of the captured graph (occ fixed at allocation)
+  DevParams dp{};                  // the context's parameters with this workspace's occupancy
   int nf_cap = 0;
   size_t bytes = 0;
   void* block = nullptr;
@@ -164,7 +177,10 @@ struct tpc_ctx {
   tpc_frame_t next_id = 1;
   std::string err;
   std::vector<std::shared_ptr<Workspace>> wspool;
-  int grid_neighbours = 0, grid_tracklets = 0, k5_variant = 4;
+  Shape shape;                     // launch shape of the next runs (parameters or autotuned)
+  bool tuned = false;
+  std::vector<tpc_tune_entry> tune_entries;
+  std::map<long long, int> blocks_cache;  // resident blocks per SM of each kernel shape
   bool timing = false;
   cudaEvent_t ev[kNumKernels + 1] = {nullptr};
   cudaEvent_t ev_sync = nullptr;
@@ -220,7 +236,10 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   ws->tcap = std::max(tcap, 1024LL);
   ws->nf_cap = nf_cap;
   ws->scap = (long long)nf_cap * kSegPerFrame;
-  const double occ = ctx->dp.occ;
+  ws->shape = ctx->shape;
+  ws->dp = ctx->dp;
+  ws->dp.occ = ctx->shape.occ;
+  const double occ = ws->dp.occ;
   // a segment grid has at most 4 ceil(n / occ) + 260 bins, 513 in the 16-bit storage (k_seg_layout)
   ws->bcap = 4 * ((long long)std::ceil((double)ws->ncap / occ) + ws->scap) + (ctx->p.packed ? 520 : 264) * ws->scap + 16;
   long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1});
@@ -307,13 +326,15 @@ size_t workspace_bytes(tpc_ctx* ctx, long long ncap, int nf_cap) {
 int get_workspace(tpc_ctx* ctx, long long ntot, int nf, std::shared_ptr<Workspace>& out) {
   const long long tneed = (long long)std::ceil((double)ntot * ctx->p.tracklet_capacity) + 1024;
   for (auto& w : ctx->wspool)
-    if (!w->busy && w->users == 0 && w->ncap >= ntot && w->tcap >= tneed && w->nf_cap >= nf) {
+    if (!w->busy && w->users == 0 && w->ncap >= ntot && w->tcap >= tneed && w->nf_cap >= nf &&
+        w->dp.occ == ctx->shape.occ) {
       out = w;
       return TPC_OK;
     }
   // a busy workspace without result holders becomes free once its run ends: wait (bounded)
   for (auto& w : ctx->wspool)
-    if (w->busy && w->users == 0 && w->ncap >= ntot && w->tcap >= tneed && w->nf_cap >= nf) {
+    if (w->busy && w->users == 0 && w->ncap >= ntot && w->tcap >= tneed && w->nf_cap >= nf &&
+        w->dp.occ == ctx->shape.occ) {
       int rc = wait_ws(ctx, *w, 120.0);
       if (rc) return rc;
       out = w;
@@ -334,9 +355,20 @@ int get_workspace(tpc_ctx* ctx, long long ntot, int nf, std::shared_ptr<Workspac
 
 
 // Enqueue the whole kernel sequence for the batch described in ws->h_desc (already uploaded).
+// resident blocks per SM of a kernel shape (cached: the occupancy query is not free)
+int blocks_per_sm(tpc_ctx* ctx, int kernel, int a, int b) {
+  const long long key = ((long long)kernel << 40) | ((long long)a << 20) | ((long long)b << 1) | (ctx->p.packed ? 1 : 0);
+  auto it = ctx->blocks_cache.find(key);
+  if (it != ctx->blocks_cache.end()) return it->second;
+  const int nb = kernel == 0 ? neighbours_blocks_per_sm(ctx->p.packed, a) : tracklets_blocks_per_sm(a, b, ctx->p.packed);
+  ctx->blocks_cache[key] = nb;
+  return nb;
+}
+
 int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   Work W = ws.W;
-  const DevParams& Q = ctx->dp;
+  const DevParams& Q = ws.dp;
+  const Shape& sh = ws.shape;
   DevCounters* C = W.cnt;
   const int G = ctx->sms;
   int ki = 0;
@@ -374,7 +406,8 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   ++nl; k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);
   ++nl; k_chunk_fill<<<G, 256, 0, s>>>(W);
-  ++nl; launch_neighbours(ctx->p.packed, ctx->grid_neighbours, s, W, Q, ctx->p.k2_tma);
+  ++nl; launch_neighbours(ctx->p.packed, sh.k2_warps, G * std::max(blocks_per_sm(ctx, 0, sh.k2_warps, 0), 1), s, W, Q,
+                          sh.k2_tma);
   mark(ki++);  // clean
   ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_start
@@ -385,17 +418,19 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // start_order
   ++nl; k_start_order<<<2 * G, 256, 0, s>>>(W);
   mark(ki++);  // chains
-  const bool ordered = ctx->p.k5_longest_first != 0;
-  if (ordered) { ++nl; k_zero_u32<<<1, 256, 0, s>>>(W.len_cnt, nullptr, kNRow + 1, 0, 1); }
-  Work Wc = W;
-  if (!ordered) Wc.len_cnt = nullptr;
-  ++nl; k_chains<<<4 * G, 256, 0, s>>>(Wc);
-  if (ordered) {
+  const int order = sh.k5_order;
+  if (order) { ++nl; k_zero_u32<<<1, 256, 0, s>>>(W.len_cnt, nullptr, kNRow + 1, 0, 1); }
+  ++nl; k_chains<<<4 * G, 256, 0, s>>>(W, order);
+  if (order) {
     ++nl; k_length_offsets<<<1, 32, 0, s>>>(W);
-    ++nl; k_length_scatter<<<4 * G, 256, 0, s>>>(W);
+    ++nl; k_length_scatter<<<4 * G, 256, 0, s>>>(W, order);
   }
   mark(ki++);  // tracklets
-  ++nl; launch_tracklets(ctx->k5_variant, ctx->p.packed, ctx->grid_tracklets, s, W, Q, ordered ? 1 : 0);
+  {
+    const int nb = std::max(blocks_per_sm(ctx, 1, sh.k5_block, sh.k5_regs), 1);
+    const int bps = sh.k5_bps > 0 ? std::min(sh.k5_bps, nb) : nb;
+    ++nl; launch_tracklets(sh.k5_block, sh.k5_regs, ctx->p.packed, G * bps, s, W, Q, order ? 1 : 0);
+  }
   mark(ki++);  // zero_w
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
   mark(ki++);  // votes
@@ -417,19 +452,50 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   return TPC_OK;
 }
 
+// A workspace's graph is valid for the launch shape it was captured with; occupancy is fixed by
+// its allocation (a workspace of another occupancy is never handed out for a shape).
+void set_shape(Workspace& ws, const Shape& want) {
+  Shape sh = want;
+  sh.occ = ws.dp.occ;
+  if (ws.shape == sh) return;
+  if (ws.graph) cudaGraphExecDestroy(ws.graph);
+  ws.graph = nullptr;
+  ws.shape = sh;
+}
+
+// The kernel sequence on stream s: a replay of the workspace's graph (captured on first use, on
+// the context's non-default stream; replays may go to any stream), or eager launches when graphs
+// are off or per-stage timing is on.
+int launch_ws(tpc_ctx* ctx, Workspace& ws, cudaStream_t s) {
+  if (!ctx->p.use_graphs || ctx->timing) return enqueue_sequence(ctx, ws, s, ctx->timing);
+  if (!ws.graph) {
+    cudaStream_t cs = ctx->stream;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_sequence(ctx, ws, cs, false);
+    cudaError_t e = cudaStreamEndCapture(cs, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ws.graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  CK(cudaGraphLaunch(ws.graph, s));
+  return TPC_OK;
+}
+
 int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::shared_ptr<Workspace>& ws_out,
               std::shared_ptr<Workspace> fixed = nullptr) {
   // The same batch tracked again on the same workspace (e.g. a frame re-tracked in a loop): the
   // descriptor in device memory is already right and the stream orders the runs.
   if (!fixed) {
     std::shared_ptr<Workspace> same = fr[0]->ws;
-    bool reuse = same && same->batch_ids.size() == fr.size();
+    bool reuse = same && same->batch_ids.size() == fr.size() && same->dp.occ == ctx->shape.occ;
     for (size_t k = 0; reuse && k < fr.size(); ++k) reuse = fr[k]->ws == same && same->batch_ids[k] == fr[k]->id;
     if (reuse) {
       same->busy = true;
-      int rc = TPC_OK;
-      if (ctx->p.use_graphs && !ctx->timing && same->graph) CK(cudaGraphLaunch(same->graph, s));
-      else rc = enqueue_sequence(ctx, *same, s, ctx->timing);
+      set_shape(*same, ctx->shape);
+      int rc = launch_ws(ctx, *same, s);
       if (rc) return rc;
       CK(cudaEventRecord(same->done, s));
       for (Frame* f : fr) f->state = 3;
@@ -459,27 +525,9 @@ int run_batch(tpc_ctx* ctx, const std::vector<Frame*>& fr, cudaStream_t s, std::
   d->ntot = ntot;
   ws->busy = true;
   CK(cudaMemcpyAsync(ws->d_desc, d, sizeof(BatchDesc), cudaMemcpyHostToDevice, s));
-  const bool timing = ctx->timing;
-  if (ctx->p.use_graphs && !timing) {
-    // one graph per workspace; its kernels read every size from the descriptor in device memory
-    if (!ws->graph) {
-      // capture on the context's (non-default) stream; replays may go to any stream
-      cudaStream_t cs = ctx->stream;
-      cudaGraph_t g;
-      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-      rc = enqueue_sequence(ctx, *ws, cs, false);
-      cudaError_t e = cudaStreamEndCapture(cs, &g);
-      if (rc) return rc;
-      if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&ws->graph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    }
-    CK(cudaGraphLaunch(ws->graph, s));
-  } else {
-    rc = enqueue_sequence(ctx, *ws, s, timing);
-    if (rc) return rc;
-  }
+  set_shape(*ws, ctx->shape);
+  rc = launch_ws(ctx, *ws, s);
+  if (rc) return rc;
   CK(cudaEventRecord(ws->done, s));
   for (size_t k = 0; k < fr.size(); ++k) {
     fr[k]->ws = ws;
@@ -640,9 +688,13 @@ void tpc_default_params(tpc_params* p) {
   p->hbm_budget = 80LL << 30;
   p->max_batch_frames = 16;
   p->use_graphs = 1;
+  p->k2_warps = 8;
   p->k2_tma = 1;
-  p->k5_occupancy = 8;
-  p->k5_longest_first = 0;
+  p->k5_block = 128;
+  p->k5_regs = 64;
+  p->k5_blocks_per_sm = 0;
+  p->k5_order = 0;
+  p->autotune = 0;
 }
 
 const char* tpc_version(void) { return "tpctrack 0.1 (sm_103a)"; }
@@ -657,11 +709,21 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   } else {
     tpc_default_params(&ctx->p);
   }
-  if (ctx->p.nmin < 1 || ctx->p.lmin < 3 || ctx->p.n_miss_max < 1 || !(ctx->p.tracklet_capacity > 0) ||
-      ctx->p.max_batch_frames < 1 || ctx->p.max_batch_frames > kMaxFrames) {
+  const tpc_params& q = ctx->p;
+  if (q.nmin < 1 || q.lmin < 3 || q.n_miss_max < 1 || !(q.tracklet_capacity > 0) || q.max_batch_frames < 1 ||
+      q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
+      (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 128) ||
+      q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 2 || q.bin_occupancy > 64.0f) {
     delete ctx;
     return TPC_E_INVAL;
   }
+  ctx->shape.occ = q.bin_occupancy > 0 ? q.bin_occupancy : 2.0f;
+  ctx->shape.k2_warps = q.k2_warps;
+  ctx->shape.k2_tma = q.k2_tma ? 1 : 0;
+  ctx->shape.k5_block = q.k5_block;
+  ctx->shape.k5_regs = q.k5_regs;
+  ctx->shape.k5_bps = q.k5_blocks_per_sm;
+  ctx->shape.k5_order = q.k5_order;
   make_dev_params(ctx->p, ctx->dp);
   int rc = TPC_OK;
   do {
@@ -679,11 +741,6 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     for (int k = 0; k <= kNumKernels; ++k) cudaEventCreate(&ctx->ev[k]);
     cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming);
-    int nb = neighbours_blocks_per_sm(ctx->p.packed);
-    ctx->grid_neighbours = ctx->sms * std::max(nb, 1);
-    ctx->k5_variant = ctx->p.k5_occupancy == 4 ? 4 : 8;
-    nb = tracklets_blocks_per_sm(ctx->k5_variant, ctx->p.packed);
-    ctx->grid_tracklets = ctx->sms * std::max(nb, 1);
     ctx->slots.resize(2);
     for (auto& sl : ctx->slots) cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     // slot capacity: the largest batch whose workspace and inputs fit half of the HBM budget
@@ -753,6 +810,10 @@ int tpc_track_batch(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, v
   if (s != ctx->stream) {
     CK(cudaEventRecord(ctx->ev_sync, ctx->stream));
     CK(cudaStreamWaitEvent(s, ctx->ev_sync, 0));
+  }
+  if (ctx->p.autotune && !ctx->tuned) {
+    int rc = tpc_autotune(ctx, frames, n_frames, 3, nullptr);
+    if (rc) return rc;
   }
   std::shared_ptr<Workspace> ws;
   return run_batch(ctx, fr, s, ws);
@@ -996,6 +1057,7 @@ int serve_step(tpc_ctx* ctx) {
       ctx->queue.pop_front();
     }
     if (batch.empty()) break;
+    if (sl.ws && sl.ws->dp.occ != ctx->shape.occ) sl.ws.reset();  // retuned grid occupancy
     if (!sl.ws) {
       const long long tcap = (long long)std::ceil((double)ctx->slot_clusters * ctx->p.tracklet_capacity) + 1024;
       int rc = alloc_workspace(ctx, ctx->slot_clusters, tcap, ctx->p.max_batch_frames, sl.ws);
@@ -1037,6 +1099,120 @@ int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_
     ctx->finished.pop_front();
   }
   return k;
+}
+
+int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int32_t reps, tpc_tune_report* out) {
+  if (!ctx || !frames || n_frames < 1 || n_frames > kMaxFrames || reps < 1) return fail(ctx, TPC_E_INVAL, "bad tuning request");
+  std::vector<Frame*> fr;
+  for (int k = 0; k < n_frames; ++k) {
+    Frame* f = find_frame(ctx, frames[k]);
+    if (!f) return fail(ctx, TPC_E_INVAL, "unknown frame handle");
+    if (f->state == 1 || f->state == 2 || f->served) return fail(ctx, TPC_E_STATE, "frame is queued for serving");
+    for (Frame* g : fr)
+      if (g == f) return fail(ctx, TPC_E_INVAL, "frame listed twice");
+    fr.push_back(f);
+  }
+  ctx->tune_entries.clear();
+  const bool old_timing = ctx->timing;
+  const Shape start = ctx->shape;
+  ctx->timing = true;  // eager launches with events between stages on the context's stream
+  const int i_nb = 8, i_ch = 13, i_tl = 14;  // stage indices: neighbours, chains, tracklets
+  // time one shape: median over reps runs (after one discarded run) of the stage group and total
+  auto measure = [&](const Shape& sh, int stage, float& obj) -> int {
+    for (const auto& e : ctx->tune_entries) {
+      Shape o;
+      o.occ = e.bin_occupancy; o.k2_warps = e.k2_warps; o.k2_tma = e.k2_tma; o.k5_block = e.k5_block;
+      o.k5_regs = e.k5_regs; o.k5_bps = e.k5_blocks_per_sm; o.k5_order = e.k5_order;
+      if (o == sh && e.stage == stage) { obj = e.ms; return TPC_OK; }
+    }
+    ctx->shape = sh;
+    std::vector<float> vo, vt;
+    for (int r = 0; r <= reps; ++r) {
+      std::shared_ptr<Workspace> ws;
+      int rc = run_batch(ctx, fr, ctx->stream, ws);
+      if (!rc) rc = wait_ws(ctx, *ws, 120.0);
+      if (!rc) rc = check_ws_errors(ctx, *ws);
+      if (rc) return rc;
+      if (r == 0) continue;
+      float tot = 0;
+      for (int k = 0; k < kNumKernels; ++k) tot += ctx->ms[k];
+      vt.push_back(tot);
+      vo.push_back(stage == 0 ? tot : stage == 1 ? ctx->ms[i_nb] : ctx->ms[i_ch] + ctx->ms[i_tl]);
+    }
+    std::sort(vo.begin(), vo.end());
+    std::sort(vt.begin(), vt.end());
+    tpc_tune_entry e{};
+    e.bin_occupancy = sh.occ; e.k2_warps = sh.k2_warps; e.k2_tma = sh.k2_tma; e.k5_block = sh.k5_block;
+    e.k5_regs = sh.k5_regs; e.k5_blocks_per_sm = sh.k5_bps; e.k5_order = sh.k5_order;
+    e.ms = vo[vo.size() / 2];
+    e.total_ms = vt[vt.size() / 2];
+    e.stage = stage;
+    ctx->tune_entries.push_back(e);
+    obj = e.ms;
+    return TPC_OK;
+  };
+  Shape best = start;
+  int best_idx = -1;
+  // one knob group: time every candidate, keep the fastest on the group's stages
+  auto descend = [&](const std::vector<Shape>& cands, int stage) -> int {
+    float bo = 0;
+    int rc = measure(best, stage, bo);
+    if (rc) return rc;
+    Shape bs = best;
+    for (const Shape& c : cands) {
+      float o = 0;
+      rc = measure(c, stage, o);
+      if (rc) return rc;
+      if (o < bo) { bo = o; bs = c; }
+    }
+    best = bs;
+    return TPC_OK;
+  };
+  int rc = TPC_OK;
+  do {
+    std::vector<Shape> c;
+    for (float occ : {1.0f, 2.0f, 4.0f}) { Shape t = best; t.occ = occ; c.push_back(t); }
+    if ((rc = descend(c, 0))) break;
+    c.clear();
+    for (int w : {4, 8})
+      for (int tma : {0, 1}) { Shape t = best; t.k2_warps = w; t.k2_tma = tma; c.push_back(t); }
+    if ((rc = descend(c, 1))) break;
+    c.clear();
+    for (int b : {64, 128, 256})
+      for (int r : {64, 128}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_bps = 0; c.push_back(t); }
+    if ((rc = descend(c, 2))) break;
+    c.clear();
+    for (int o : {0, 1, 2}) { Shape t = best; t.k5_order = o; c.push_back(t); }
+    if ((rc = descend(c, 2))) break;
+    c.clear();
+    const int nb = std::max(blocks_per_sm(ctx, 1, best.k5_block, best.k5_regs), 1);
+    for (int q : {4, 3, 2, 1}) {  // all resident blocks, then 3/4, 1/2, 1/4 of them
+      Shape t = best;
+      t.k5_bps = q == 4 ? 0 : std::max(nb * q / 4, 1);
+      c.push_back(t);
+    }
+    if ((rc = descend(c, 2))) break;
+  } while (0);
+  ctx->timing = old_timing;
+  if (rc) {
+    ctx->shape = start;
+    return rc;
+  }
+  ctx->shape = best;
+  ctx->tuned = true;
+  for (size_t k = 0; k < ctx->tune_entries.size(); ++k) {
+    const auto& e = ctx->tune_entries[k];
+    if (e.bin_occupancy == best.occ && e.k2_warps == best.k2_warps && e.k2_tma == best.k2_tma &&
+        e.k5_block == best.k5_block && e.k5_regs == best.k5_regs && e.k5_blocks_per_sm == best.k5_bps &&
+        e.k5_order == best.k5_order)
+      best_idx = (int)k;
+  }
+  if (out) {
+    out->n_entries = (int32_t)ctx->tune_entries.size();
+    out->entries = ctx->tune_entries.data();
+    out->best = best_idx;
+  }
+  return TPC_OK;
 }
 
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable) {

@@ -38,7 +38,7 @@ __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
 void make_dev_params(const tpc_params& p, DevParams& d);
-void launch_neighbours(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
+bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
 __global__ void k_chunk_count(Work);
 __global__ void k_chunk_fill(Work);
 }  // namespace tpc
@@ -215,7 +215,7 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);
   k_chunk_fill<<<G, 256, 0, s>>>(W);
-  launch_neighbours(0, 4 * G, s, W, Q, p.k2_tma);
+  launch_neighbours(0, p.k2_warps == 4 ? 4 : 8, 4 * G, s, W, Q, p.k2_tma);
   k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   if (n > 0) {
     cudaMemsetAsync(up, 0xFF, 4 * (size_t)n, s);

@@ -1,0 +1,100 @@
+"""Launch shapes and the autotuner: no result depends on the shape the kernels run with.
+
+Every shape the autotuner can pick (grid occupancy, neighbour-search warps per block and staging,
+tracklet block size, registers, blocks per SM and processing order) must give bit-identical links
+and tracks; the autotuner must report what it timed and leave the results unchanged.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    dict(bin_occupancy=1.0),
+    dict(bin_occupancy=4.0),
+    dict(k2_warps=4),
+    dict(k2_tma=0),
+    dict(k5_block=64, k5_regs=64),
+    dict(k5_block=64, k5_regs=128),
+    dict(k5_block=128, k5_regs=128),
+    dict(k5_block=256, k5_regs=64),
+    dict(k5_block=256, k5_regs=128),
+    dict(k5_blocks_per_sm=1),
+    dict(k5_order=1),
+    dict(k5_order=2, k5_blocks_per_sm=2),
+]
+
+
+@pytest.fixture(scope="module")
+def frame():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2009_07515_gb300 as tpc
+    tpc.build()
+    f = synth.generate("pbpb_2x10000")
+    m = f.sector < 8  # about 0.66 M clusters: many chunks, segments and tracklet waves
+    return f.sector[m], f.row[m], f.y[m], f.w[m]
+
+
+def run(frame, **params):
+    import paper_2009_07515_gb300 as tpc
+    tr = tpc.Tracker(**params)
+    try:
+        h = tr.load(*frame)
+        tr.track(h)
+        res = tr.tracks(h)
+        links = [tr.links(h, k, len(frame[2])) for k in range(4)]
+        return res, links
+    finally:
+        tr.close()
+
+
+@pytest.fixture(scope="module")
+def reference(frame):
+    return run(frame)
+
+
+def assert_same(a, b):
+    ra, la = a
+    rb, lb = b
+    for k in range(4):
+        assert np.array_equal(la[k], lb[k]), f"links {k} differ"
+    assert ra["n_tracks"] == rb["n_tracks"]
+    for key in ("sector", "ndf", "hit_offset", "hit_index"):
+        assert np.array_equal(ra[key], rb[key]), key
+    for key in ("x_ref", "param", "cov", "chi2"):
+        assert np.array_equal(ra[key].view(np.uint32), rb[key].view(np.uint32)), key
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda d: ",".join(f"{k}={v}" for k, v in d.items()))
+def test_every_launch_shape_gives_identical_results(frame, reference, shape):
+    assert_same(run(frame, **shape), reference)
+
+
+def test_autotune_reports_and_keeps_results(frame, reference):
+    import paper_2009_07515_gb300 as tpc
+    tr = tpc.Tracker()
+    try:
+        h = tr.load(*frame)
+        rep = tr.autotune([h], reps=1)
+        entries = rep["entries"]
+        assert len(entries) >= 12
+        assert rep["best"] is not None and rep["best"] in entries
+        assert all(e["ms"] > 0 and e["total_ms"] >= e["ms"] * 0.999 for e in entries)
+        assert {e["stage"] for e in entries} == {0, 1, 2}
+        # the chosen shape is the fastest of those timed for the last knob group
+        last = [e for e in entries if e["stage"] == 2]
+        assert rep["best"]["ms"] <= min(e["ms"] for e in last) * 1.0001
+        tr.track(h)
+        res = tr.tracks(h)
+        links = [tr.links(h, k, len(frame[2])) for k in range(4)]
+        assert_same((res, links), reference)
+    finally:
+        tr.close()
+
+
+def test_autotune_on_first_call(frame, reference):
+    assert_same(run(frame, autotune=1), reference)
