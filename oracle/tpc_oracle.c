@@ -44,11 +44,13 @@
 typedef float real;
 #define SQRT sqrtf
 #define RINT rintf
+#define FMA fmaf
 #define ORACLE_SYM(name) oracle_f32_##name
 #else
 typedef double real;
 #define SQRT sqrt
 #define RINT rint
+#define FMA fma
 #define ORACLE_SYM(name) oracle_f64_##name
 #endif
 
@@ -165,13 +167,14 @@ static inline void note_margin(double* m, real value, real cut) {
  *   asin(t)/t = 1 + t^2/6 + 3t^4/40 + 5t^6/112 + 35t^8/1152 + 63t^10/2816 + ...   for |t| < 0.1,
  *   sin(a/2) = sin(a) / sqrt(2 (1 + cos a))  ->  asin(t) = 2 asin(t / sqrt(2 (1 + sqrt(1 - t^2)))).
  * ---------------------------------------------------------------------------------------------- */
-static real asin_series_ratio(real t) {
-  real t2 = t * t;
-  return (real)1 +
-         t2 * ((real)0.16666666666666666 +
-               t2 * ((real)0.075 +
-                     t2 * ((real)0.044642857142857144 +
-                           t2 * ((real)0.030381944444444444 + t2 * (real)0.022372159090909092))));
+static real asin_series_ratio(real t) { /* Horner, one fused multiply-add per coefficient */
+  const real t2 = t * t;
+  real p = (real)0.022372159090909092;
+  p = FMA(t2, p, (real)0.030381944444444444);
+  p = FMA(t2, p, (real)0.044642857142857144);
+  p = FMA(t2, p, (real)0.075);
+  p = FMA(t2, p, (real)0.16666666666666666);
+  return FMA(t2, p, (real)1);
 }
 static real asin_hr(real t) {
   real scale = (real)1;
@@ -189,11 +192,13 @@ static real arc_ratio(real t) {
 /* d/dt (asin(t)/t) */
 static real arc_ratio_deriv(real t) {
   if (absr(t) < (real)0.1) {
-    real t2 = t * t;
-    return t * ((real)0.3333333333333333 +
-                t2 * ((real)0.3 +
-                      t2 * ((real)0.26785714285714285 +
-                            t2 * ((real)0.24305555555555555 + t2 * (real)0.22372159090909091))));
+    const real t2 = t * t;
+    real p = (real)0.22372159090909091;
+    p = FMA(t2, p, (real)0.24305555555555555);
+    p = FMA(t2, p, (real)0.26785714285714285);
+    p = FMA(t2, p, (real)0.3);
+    p = FMA(t2, p, (real)0.3333333333333333);
+    return t * p;
   }
   return ((real)1 / SQRT((real)1 - t * t) - arc_ratio(t)) / t;
 }
@@ -209,13 +214,14 @@ void ORACLE_SYM(pack)(double* y, double* w) {
 }
 
 /* ------------------------------------------------------------------------------------------------
- * Small dense linear algebra (5x5), written out plainly.
+ * Small dense linear algebra (5x5), written out plainly. Every sum of products in the Kalman
+ * filter accumulates with a fused multiply-add (one rounding per term), in index order.
  * ---------------------------------------------------------------------------------------------- */
 static void mat_mul5(real A[5][5], real B[5][5], real O[5][5]) {
   for (int i = 0; i < 5; ++i)
     for (int k = 0; k < 5; ++k) {
       real acc = 0;
-      for (int j = 0; j < 5; ++j) acc += A[i][j] * B[j][k];
+      for (int j = 0; j < 5; ++j) acc = FMA(A[i][j], B[j][k], acc);
       O[i][k] = acc;
     }
 }
@@ -223,7 +229,7 @@ static void mat_mul5_bt(real A[5][5], real B[5][5], real O[5][5]) { /* O = A * B
   for (int i = 0; i < 5; ++i)
     for (int k = 0; k < 5; ++k) {
       real acc = 0;
-      for (int j = 0; j < 5; ++j) acc += A[i][j] * B[k][j];
+      for (int j = 0; j < 5; ++j) acc = FMA(A[i][j], B[k][j], acc);
       O[i][k] = acc;
     }
 }
@@ -309,7 +315,8 @@ static real kf_chi2(const ctx_t* cx, const real P[5], real C[5][5], real ym, rea
   const real idet = (real)1 / det;
   const real i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   const real r0 = ym - P[0], r1 = wm - P[1];
-  return r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
+  const real u0 = FMA(i01, r1, i00 * r0), u1 = FMA(i11, r1, i10 * r0); /* S^-1 r */
+  return FMA(r1, u1, r0 * u0);
 }
 
 /* Kalman update with measurement (ym, wm): gain K = C H^T S^-1, Joseph form
@@ -326,20 +333,20 @@ static void kf_update(const ctx_t* cx, real P[5], real C[5][5], real ym, real wm
   for (int i = 0; i < 5; ++i)
     for (int l = 0; l < 2; ++l) {
       real acc = 0;
-      for (int m = 0; m < 2; ++m) acc += C[i][m] * Si[m][l]; /* (C H^T)[i][m] = C[i][m] */
+      for (int m = 0; m < 2; ++m) acc = FMA(C[i][m], Si[m][l], acc); /* (C H^T)[i][m] = C[i][m] */
       K[i][l] = acc;
     }
   const real r[2] = {ym - P[0], wm - P[1]};
   for (int i = 0; i < 5; ++i) {
     real acc = 0;
-    for (int l = 0; l < 2; ++l) acc += K[i][l] * r[l];
+    for (int l = 0; l < 2; ++l) acc = FMA(K[i][l], r[l], acc);
     P[i] = P[i] + acc;
   }
   real A[5][5], T[5][5], O[5][5];
   for (int i = 0; i < 5; ++i)
     for (int j = 0; j < 5; ++j) {
       real kh = 0;
-      for (int l = 0; l < 2; ++l) kh += K[i][l] * (real)(l == j ? 1 : 0); /* (K H)[i][j] */
+      for (int l = 0; l < 2; ++l) kh = FMA(K[i][l], (real)(l == j ? 1 : 0), kh); /* (K H)[i][j] */
       A[i][j] = (real)(i == j ? 1 : 0) - kh;
     }
   mat_mul5(A, C, T);
@@ -347,14 +354,14 @@ static void kf_update(const ctx_t* cx, real P[5], real C[5][5], real ym, real wm
   real KR[5][2];
   for (int i = 0; i < 5; ++i) {
     real acc0 = 0, acc1 = 0;
-    acc0 += K[i][0] * cx->r00; acc0 += K[i][1] * (real)0;
-    acc1 += K[i][0] * (real)0; acc1 += K[i][1] * cx->r11;
+    acc0 = FMA(K[i][0], cx->r00, acc0); acc0 = FMA(K[i][1], (real)0, acc0);
+    acc1 = FMA(K[i][0], (real)0, acc1); acc1 = FMA(K[i][1], cx->r11, acc1);
     KR[i][0] = acc0; KR[i][1] = acc1;
   }
   for (int i = 0; i < 5; ++i)
     for (int k = 0; k < 5; ++k) {
       real acc = 0;
-      for (int b = 0; b < 2; ++b) acc += KR[i][b] * K[k][b];
+      for (int b = 0; b < 2; ++b) acc = FMA(KR[i][b], K[k][b], acc);
       O[i][k] = O[i][k] + acc;
     }
   mirror_lower(O);

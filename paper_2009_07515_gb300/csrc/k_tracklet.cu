@@ -101,7 +101,7 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
       float chi;
       if (pd) {
         const float r0 = c.x - P[0], r1 = c.y - P[1];
-        chi = r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
+        chi = __fmaf_rn(r1, __fmaf_rn(i11, r1, i10 * r0), r0 * __fmaf_rn(i01, r1, i00 * r0));
       } else {
         chi = __int_as_float(0x7f800000);
       }

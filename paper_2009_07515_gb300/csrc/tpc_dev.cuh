@@ -257,13 +257,14 @@ __device__ __forceinline__ int frame_of(const BatchDesc* B, long long i) {
 // ------------------------------------------------------------------------------------ KF math
 // asin(t): half-angle reduction t -> t / sqrt(2 (1 + sqrt(1 - t^2))) until |t| < 0.1, then the
 // Maclaurin series of asin(t)/t to t^10 (only correctly rounded operations, no library call)
-__device__ __forceinline__ float asin_series_ratio(float t) {
+__device__ __forceinline__ float asin_series_ratio(float t) {  // Horner with fused multiply-adds
   const float t2 = t * t;
-  return 1.0f + t2 * ((float)0.16666666666666666 +
-                      t2 * ((float)0.075 +
-                            t2 * ((float)0.044642857142857144 +
-                                  t2 * ((float)0.030381944444444444 +
-                                        t2 * (float)0.022372159090909092))));
+  float p = (float)0.022372159090909092;
+  p = __fmaf_rn(t2, p, (float)0.030381944444444444);
+  p = __fmaf_rn(t2, p, (float)0.044642857142857144);
+  p = __fmaf_rn(t2, p, (float)0.075);
+  p = __fmaf_rn(t2, p, (float)0.16666666666666666);
+  return __fmaf_rn(t2, p, 1.0f);
 }
 __device__ __forceinline__ float asin_hr(float t) {
   float scale = 1.0f;
@@ -280,10 +281,12 @@ __device__ __forceinline__ float arc_ratio(float t) {
 __device__ __forceinline__ float arc_ratio_deriv(float t) {
   if (fabsf(t) < (float)0.1) {
     const float t2 = t * t;
-    return t * ((float)0.3333333333333333 +
-                t2 * ((float)0.3 +
-                      t2 * ((float)0.26785714285714285 +
-                            t2 * ((float)0.24305555555555555 + t2 * (float)0.22372159090909091))));
+    float p = (float)0.22372159090909091;
+    p = __fmaf_rn(t2, p, (float)0.24305555555555555);
+    p = __fmaf_rn(t2, p, (float)0.26785714285714285);
+    p = __fmaf_rn(t2, p, (float)0.3);
+    p = __fmaf_rn(t2, p, (float)0.3333333333333333);
+    return t * p;
   }
   return (1.0f / sqrtf(1.0f - t * t) - arc_ratio(t)) / t;
 }
@@ -326,13 +329,13 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
   P[0] = P[0] + dy;
   P[1] = P[1] + tw * a;
   P[2] = s1;
-  // T = J C
+  // T = J C: the nonzero terms of the index-ordered fused multiply-add sums of the dense product
   float T[5][5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    T[0][c] = (C[lt(0, c)] + J02 * C[lt(2, c)]) + J04 * C[lt(4, c)];
-    T[1][c] = ((C[lt(1, c)] + J12 * C[lt(2, c)]) + J13 * C[lt(3, c)]) + J14 * C[lt(4, c)];
-    T[2][c] = C[lt(2, c)] + J24 * C[lt(4, c)];
+    T[0][c] = __fmaf_rn(J04, C[lt(4, c)], __fmaf_rn(J02, C[lt(2, c)], C[lt(0, c)]));
+    T[1][c] = __fmaf_rn(J14, C[lt(4, c)], __fmaf_rn(J13, C[lt(3, c)], __fmaf_rn(J12, C[lt(2, c)], C[lt(1, c)])));
+    T[2][c] = __fmaf_rn(J24, C[lt(4, c)], C[lt(2, c)]);
     T[3][c] = C[lt(3, c)];
     T[4][c] = C[lt(4, c)];
   }
@@ -340,9 +343,9 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
   float O[15];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    O[lt(i, 0)] = (T[i][0] + T[i][2] * J02) + T[i][4] * J04;
-    if (i >= 1) O[lt(i, 1)] = ((T[i][1] + T[i][2] * J12) + T[i][3] * J13) + T[i][4] * J14;
-    if (i >= 2) O[lt(i, 2)] = T[i][2] + T[i][4] * J24;
+    O[lt(i, 0)] = __fmaf_rn(T[i][4], J04, __fmaf_rn(T[i][2], J02, T[i][0]));
+    if (i >= 1) O[lt(i, 1)] = __fmaf_rn(T[i][4], J14, __fmaf_rn(T[i][3], J13, __fmaf_rn(T[i][2], J12, T[i][1])));
+    if (i >= 2) O[lt(i, 2)] = __fmaf_rn(T[i][4], J24, T[i][2]);
     if (i >= 3) O[lt(i, 3)] = T[i][3];
     if (i >= 4) O[lt(i, 4)] = T[i][4];
   }
@@ -367,7 +370,8 @@ __device__ __forceinline__ float kf_chi2(const DevParams& Q, const float* P, con
   const float idet = 1.0f / det;
   const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   const float r0 = ym - P[0], r1 = wm - P[1];
-  return r0 * (i00 * r0 + i01 * r1) + r1 * (i10 * r0 + i11 * r1);
+  const float u0 = __fmaf_rn(i01, r1, i00 * r0), u1 = __fmaf_rn(i11, r1, i10 * r0);
+  return __fmaf_rn(r1, u1, r0 * u0);
 }
 
 __device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C, float ym, float wm) {
@@ -379,12 +383,12 @@ __device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
     const float ci0 = C[lt(i, 0)], ci1 = C[lt(i, 1)];
-    K[i][0] = ci0 * i00 + ci1 * i10;
-    K[i][1] = ci0 * i01 + ci1 * i11;
+    K[i][0] = __fmaf_rn(ci1, i10, ci0 * i00);
+    K[i][1] = __fmaf_rn(ci1, i11, ci0 * i01);
   }
   const float r0 = ym - P[0], r1 = wm - P[1];
 #pragma unroll
-  for (int i = 0; i < 5; ++i) P[i] = P[i] + (K[i][0] * r0 + K[i][1] * r1);
+  for (int i = 0; i < 5; ++i) P[i] = P[i] + __fmaf_rn(K[i][1], r1, K[i][0] * r0);
   // A = I - K H: only the first two columns differ from the identity
   float A[5][2];
 #pragma unroll
@@ -396,8 +400,8 @@ __device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C
   float T0[5], T1[5], Tk[15];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    T0[i] = A[i][0] * C[lt(0, 0)] + A[i][1] * C[lt(1, 0)];
-    T1[i] = A[i][0] * C[lt(0, 1)] + A[i][1] * C[lt(1, 1)];
+    T0[i] = __fmaf_rn(A[i][1], C[lt(1, 0)], A[i][0] * C[lt(0, 0)]);
+    T1[i] = __fmaf_rn(A[i][1], C[lt(1, 1)], A[i][0] * C[lt(0, 1)]);
     if (i >= 2) {
       T0[i] = T0[i] + C[lt(i, 0)];
       T1[i] = T1[i] + C[lt(i, 1)];
@@ -406,7 +410,7 @@ __device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C
 #pragma unroll
   for (int i = 2; i < 5; ++i)
 #pragma unroll
-    for (int k = 2; k <= i; ++k) Tk[lt(i, k)] = (A[i][0] * C[lt(0, k)] + A[i][1] * C[lt(1, k)]) + C[lt(i, k)];
+    for (int k = 2; k <= i; ++k) Tk[lt(i, k)] = __fmaf_rn(A[i][1], C[lt(1, k)], A[i][0] * C[lt(0, k)]) + C[lt(i, k)];
   float KR[5][2];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
@@ -417,9 +421,9 @@ __device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C
   for (int i = 0; i < 5; ++i)
 #pragma unroll
     for (int k = 0; k <= i; ++k) {
-      float o = T0[i] * A[k][0] + T1[i] * A[k][1];
+      float o = __fmaf_rn(T1[i], A[k][1], T0[i] * A[k][0]);
       if (k >= 2) o = o + Tk[lt(i, k)];
-      C[lt(i, k)] = o + (KR[i][0] * K[k][0] + KR[i][1] * K[k][1]);
+      C[lt(i, k)] = o + __fmaf_rn(KR[i][1], K[k][1], KR[i][0] * K[k][0]);
     }
 }
 
