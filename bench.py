@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "TPC clusters tracked/s"
 UNIT = "clusters/s"
 
-# Roofline accounting (derivations in the design doc):
+# Roofline accounting:
 #  - memory-bound kernels: algorithmic bytes per cluster counted from the data layout, e.g. the
 #    neighbour search reads its row's (y, w) and the two adjacent rows once (3 x 8 B) and writes
 #    the links (8 B);
@@ -47,6 +47,7 @@ UNIT = "clusters/s"
 ALG_BYTES_PER_CLUSTER = {"neighbours": 32.0, "clean": 24.0, "seg_hist": 10.0, "bin_rank": 10.0,
                          "scatter": 30.0, "starts": 12.0}
 FLOPS_PER_STEP = 480.0
+E2E_WINDOW = 3  # frames in flight in the end-to-end measurement
 
 
 def _recorded_traffic(kernel: str, workload: str):
@@ -174,7 +175,7 @@ def cpu_baseline(frame, n_threads: int, budget_s: float = 20.0) -> dict:
 
 
 def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_frames: int, loads, seed: int = 5,
-                      budget_gb: float = 80.0):
+                      budget_gb: float = 80.0, params: dict | None = None):
     """Frame p50/p99 latency and throughput, served (continuous batching, tpc_submit_frame/tpc_poll)
     against plain one-frame-at-a-time tracking (load, track, read back), for a Poisson stream of
     frames with collision counts uniform in 1..max_collisions (drawn from a pool of generated frames).
@@ -188,7 +189,8 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
     for f in pool:
         for k in ("sector", "row", "y", "w"):
             setattr(f, k, torch.from_numpy(np.ascontiguousarray(getattr(f, k))).pin_memory().numpy())
-    plain = tpc.Tracker()
+    params = params or {}
+    plain = tpc.Tracker(**params)
     for f in pool[:2]:
         plain.run(f.sector, f.row, f.y, f.w)
     t0 = time.perf_counter()
@@ -197,7 +199,7 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
     service = (time.perf_counter() - t0) / pool_size
     out = {"workload": f"Poisson stream, frames of U{{1..{max_collisions}}} collisions (pool of {pool_size})",
            "mean_plain_service_ms": service * 1e3, "budget_gb": budget_gb, "points": []}
-    srv = tpc.Tracker(hbm_budget=int(budget_gb * (1 << 30)))
+    srv = tpc.Tracker(hbm_budget=int(budget_gb * (1 << 30)), **params)
     # warm-up: slot workspaces allocated and their graphs captured before timing
     warm = [srv.submit(f.sector, f.row, f.y, f.w) for f in pool[:6]]
     got = []
@@ -265,6 +267,183 @@ def run_reference(args, ws, rank):
         times.append(cpu_baseline(frame, cores, budget_s=budget))
     vals = [t["value"] for t in times]
     value = float(np.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "parallelism": "host threads over sectors"},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": times[0]["sample"], "value": value},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="pbpb_2x10000")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-collisions", type=int, default=40,
+                    help="serving stream: collisions per frame uniform in 1..N (570 = full-size frames)")
+    ap.add_argument("--serve-loads", default="0.9", help="comma-separated arrival rates / plain service rate")
+    ap.add_argument("--serve-frames", type=int, default=80)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
+    ap.add_argument("--shape", default="",
+                    help='launch shape as JSON tpc_params overrides, e.g. \'{"k5_block": 64}\' (no autotuning)')
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only track the workload warmup + steps times (eager launches), for ncu captures")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    ws, rank, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import torch
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import synth
+    import paper_2009_07515_gb300 as tpc
+
+    frame = synth.generate(args.workload)
+    n = frame.n
+    shape = json.loads(args.shape) if args.shape else {}
+    tr = tpc.Tracker(**shape)
+    # inputs resident in HBM
+    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
+    h = tr.load(*d_in)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    # a dedicated (non-default) stream: the tracking kernels are launched on it, and the step
+    # events are recorded on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+
+    if args.profile_only:
+        tr.set_timing(True)  # eager launches, one kernel per launch for the profiler
+        for _ in range(args.warmup + args.steps):
+            tr.track(h, stream)
+            tr.tracks(h)
+        print(json.dumps({"profile_only": True, "workload": args.workload, "clusters": n,
+                          "runs": args.warmup + args.steps}), flush=True)
+        tr.close()
+        return
+    tuned = None
+    tuned_params = dict(shape)
+    if not shape and not args.no_autotune:
+        # the library's autotuner picks the launch shapes on this workload (results do not depend
+        # on them); the chosen shape is reported in config.launch_shape
+        rep = tr.autotune([h], reps=3)
+        tuned = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
+        tuned_params = dict(tuned)
+        tuned["configs_timed"] = len(rep["entries"])
+    for _ in range(args.warmup):
+        tr.track(h, stream)
+    res = tr.tracks(h)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident, L2 flushed before each step)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            tr.track(h, stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    dev_ms = _max_over_ranks(dev_ms, ws)
+    ms_per_step = dev_ms / args.steps
+    value = n * ws * args.steps / (dev_ms / 1e3)
+    res = tr.tracks(h)
+
+    # ---- per-kernel times (eager launches with events between kernels)
+    tr.set_timing(True)
+    kt_runs = []
+    for _ in range(5):
+        flush.zero_()
+        tr.track(h, stream)
+        tr.tracks(h)
+        kt_runs.append(tr.kernel_times())
+    tr.set_timing(False)
+    kernels = {k: float(np.median([r[k] for r in kt_runs])) for k in kt_runs[0]}
+    launches_per_step = int(sum(tr.kernel_times(launches=True).values()))
+    stats = tr.stats(h)
+    dominant = max(kernels, key=kernels.get)
+    hbm_peak, peak_src = _peaks()
+    if dominant == "tracklets":
+        flops = stats["steps"] * FLOPS_PER_STEP
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        achieved = flops / (kernels[dominant] / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": _recorded_traffic(dominant, args.workload),
+                    "peak_source": "derived (FP32 lanes x 2 x max SM clock)",
+                    "alg_flops_per_launch": flops, "row_steps": stats["steps"]}
+    else:
+        alg = ALG_BYTES_PER_CLUSTER.get(dominant, 32.0) * n
+        achieved = alg / (kernels[dominant] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": _recorded_traffic(dominant, args.workload),
+                    "peak_source": peak_src,
+                    "alg_bytes_per_launch": alg}
+
+    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region.
+    # Pipelined, as a production loop drives the serving calls: every step submits the frame from
+    # pinned host memory (uploaded at submit) and every finished frame's tracks are read back to
+    # the host and released; up to E2E_WINDOW frames are in flight, so the upload and read-back of
+    # one frame overlap the tracking of another. The synchronous path (load, track, read back, one
+    # frame at a time) is reported beside it as e2e.sync_value.
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
+    pin_np = [p.numpy() for p in pin]
+    h2d = int(sum(p.numel() * p.element_size() for p in pin))
+    e2e_tr = tpc.Tracker(**tuned_params)
+
+    def pipelined(k: int) -> int:
+        done = sub = inflight = d2h = 0
+        while done < k:
+            while sub < k and inflight < E2E_WINDOW:
+                e2e_tr.submit(*pin_np)
+                sub += 1
+                inflight += 1
+            for t in e2e_tr.poll(64, 200000):
+                out = e2e_tr.tracks(t)
+                d2h = int(sum(np.asarray(v).nbytes for kk, v in out.items() if kk != "n_tracks"))
+                e2e_tr.release(t)
+                done += 1
+                inflight -= 1
+        return d2h
+
+    pipelined(2 * E2E_WINDOW)  # warm-up: slot workspaces and their graphs
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    d2h = pipelined(args.steps)
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_tr.close()
+    for _ in range(2):
+        tr.run(*pin_np)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        tr.run(*pin_np)
+    sync_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = {"value": n * ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "mode": f"pipelined submit/poll, {E2E_WINDOW} frames in flight",
+           "sync_value": n * ws * args.steps / sync_s}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -425,7 +604,7 @@ def main():
     if not args.no_serving:
         line["serving"] = serving_benchmark(
             tpc, synth, max_collisions=args.serve_collisions, pool_size=12, n_frames=args.serve_frames,
-            loads=[float(x) for x in args.serve_loads.split(",")], seed=5 + rank)
+            loads=[float(x) for x in args.serve_loads.split(",")], seed=5 + rank, params=tuned_params)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(frame, os.cpu_count() or 1)
     if rank == 0:

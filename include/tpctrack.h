@@ -5,7 +5,7 @@
  * described in "Overview of online and offline reconstruction in ALICE for LHC Run 3"
  * (arXiv:2009.07515): clusters of a continuous-readout time frame in (Sec. 2: native row/time
  * coordinates, z unknown until a vertex time is known), sector tracks with helix parameters,
- * covariances and cluster indices out (Sec. 6: TPC tracking runs standalone, without space-charge,
+ * covariances and cluster indices out (Sec. 5: TPC tracking runs standalone, without space-charge,
  * field or hit-error corrections; the algorithm derives from the Run-2 HLT tracker). Every stage
  * runs as a CUDA kernel on one GPU: per-row search grid, cellular-automaton neighbour finding and
  * cleaning, start-hit selection, Kalman-filter tracklet construction in the solenoid field, and

@@ -5,7 +5,7 @@
  * benchmark may load this. The product path never calls it and shares no code with it.
  *
  * What it computes: the standalone TPC sector tracking of the paper's synchronous reconstruction
- * (Sec. 6: the TPC tracking runs first standalone, without space-charge, field or hit-error
+ * (Sec. 5: the TPC tracking runs first standalone, without space-charge, field or hit-error
  * corrections, on clusters whose z is unknown in continuous readout, Sec. 2; the algorithm is
  * derived from the Run-2 HLT tracker). The paper names the method but defers its steps to the HLT
  * papers it cites, so each step below states the reading this project takes:
@@ -139,7 +139,7 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
 
 static inline real absr(real v) { return v < 0 ? -v : v; }
 
-/* 16-bit fixed-point cluster storage (Sec. 4 of the paper: custom formats that keep only the bits
+/* 16-bit fixed-point cluster storage (Sec. 3 of the paper: custom formats that keep only the bits
  * the intrinsic resolution needs). y is stored as qy = rint((y + 64) * 512) clamped to [0, 65535],
  * read back as qy / 512 - 64; w is stored as a 16-bit offset, in steps of 2^-9 cm, from the lower
  * edge of its search-grid bin (bins are aligned power-of-two widths of at most 128 cm), which reads
