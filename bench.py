@@ -50,22 +50,34 @@ FLOPS_PER_STEP = 480.0
 E2E_WINDOW = 3  # frames in flight in the end-to-end measurement
 
 
-def _recorded_traffic(kernel: str, workload: str):
+def _recorded_traffic(kernel: str, workload: str, shape: dict, method_defaults: dict):
     """DRAM bytes per launch of `kernel` from the committed ncu record (profiles/traffic.json), or None
-    when there is none for this workload or a source it was taken from has changed since."""
+    when there is none for this workload and launch shape, the method defaults differ, or a source
+    the kernel is built from has changed since the capture."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         rec = json.load(fh).get(kernel)
-    if not rec or rec.get("workload") != workload:
+    if not rec or rec.get("workload") != workload or rec.get("method_defaults") != method_defaults:
+        return None
+    if any(rec.get("launch_shape", {}).get(k) != v for k, v in shape.items() if k in rec.get("launch_shape", {})):
+        return None
+    if set(rec.get("launch_shape", {})) != {k for k in shape if k in rec.get("launch_shape", {})} or not shape:
         return None
     h = hashlib.sha256()
     for src in rec["sources"]:
         with open(os.path.join(ROOT, src), "rb") as fh:
             h.update(fh.read())
     return float(rec["dram_bytes_per_launch"]) if h.hexdigest() == rec["sources_sha256"] else None
+
+
+def _method_defaults(tpc) -> dict:
+    p = tpc.default_params()
+    keys = ("bz", "ky", "kw", "eps", "chi_n_max", "lmin", "sigma_y", "sigma_w", "chi2_hit_max", "n_miss_max",
+            "win_nsig", "win_add", "x0_per_row", "max_sin", "y_margin", "nmin", "cov0", "packed")
+    return {k: (list(getattr(p, k)) if k == "cov0" else getattr(p, k)) for k in keys}
 
 
 def _peaks():
@@ -144,9 +156,16 @@ def _max_over_ranks(x: float, ws: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, steps: int, seconds: float, ws: int) -> float:
+    """Replicas: every rank processes its own copy of the workload; the job's throughput is the
+    units of all ranks over the slowest rank's time."""
+    return units_per_rank * ws * steps / _max_over_ranks(seconds, ws)
 
 
 def _barrier(ws: int):
@@ -365,9 +384,9 @@ def main():
         torch.cuda.synchronize()
     _barrier(ws)
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    value = whole_job_value(n, args.steps, dev_ms / 1e3, ws)
     dev_ms = _max_over_ranks(dev_ms, ws)
     ms_per_step = dev_ms / args.steps
-    value = n * ws * args.steps / (dev_ms / 1e3)
     res = tr.tracks(h)
 
     # ---- per-kernel times (eager launches with events between kernels)
@@ -389,14 +408,16 @@ def main():
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         achieved = flops / (kernels[dominant] / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": _recorded_traffic(dominant, args.workload),
+                    "frac": achieved / peak, "traffic": _recorded_traffic(dominant, args.workload, tuned_params,
+                                                                       _method_defaults(tpc)),
                     "peak_source": "derived (FP32 lanes x 2 x max SM clock)",
                     "alg_flops_per_launch": flops, "row_steps": stats["steps"]}
     else:
         alg = ALG_BYTES_PER_CLUSTER.get(dominant, 32.0) * n
         achieved = alg / (kernels[dominant] / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": _recorded_traffic(dominant, args.workload),
+                    "frac": achieved / hbm_peak, "traffic": _recorded_traffic(dominant, args.workload, tuned_params,
+                                                                       _method_defaults(tpc)),
                     "peak_source": peak_src,
                     "alg_bytes_per_launch": alg}
 
@@ -443,152 +464,6 @@ def main():
     e2e = {"value": n * ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "mode": f"pipelined submit/poll, {E2E_WINDOW} frames in flight",
            "sync_value": n * ws * args.steps / sync_s}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "parallelism": "host threads over sectors"},
-            "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": times[0]["sample"], "value": value},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pbpb_2x10000")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-collisions", type=int, default=40,
-                    help="serving stream: collisions per frame uniform in 1..N (570 = full-size frames)")
-    ap.add_argument("--serve-loads", default="0.9", help="comma-separated arrival rates / plain service rate")
-    ap.add_argument("--serve-frames", type=int, default=80)
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
-    ap.add_argument("--shape", default="",
-                    help='launch shape as JSON tpc_params overrides, e.g. \'{"k5_block": 64}\' (no autotuning)')
-    ap.add_argument("--profile-only", action="store_true",
-                    help="only track the workload warmup + steps times (eager launches), for ncu captures")
-    args = ap.parse_args()
-    args.warmup = max(3, args.warmup)
-    ws, rank, local = _dist()
-    if args.impl == "reference":
-        run_reference(args, ws, rank)
-        return
-
-    import torch
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    import __graft_entry__
-    __graft_entry__.build()
-    import synth
-    import paper_2009_07515_gb300 as tpc
-
-    frame = synth.generate(args.workload)
-    n = frame.n
-    shape = json.loads(args.shape) if args.shape else {}
-    tr = tpc.Tracker(**shape)
-    # inputs resident in HBM
-    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
-    h = tr.load(*d_in)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    # a dedicated (non-default) stream: the tracking kernels are launched on it, and the step
-    # events are recorded on it
-    stream = torch.cuda.Stream(device=dev)
-    torch.cuda.set_stream(stream)
-
-    if args.profile_only:
-        tr.set_timing(True)  # eager launches, one kernel per launch for the profiler
-        for _ in range(args.warmup + args.steps):
-            tr.track(h, stream)
-            tr.tracks(h)
-        print(json.dumps({"profile_only": True, "workload": args.workload, "clusters": n,
-                          "runs": args.warmup + args.steps}), flush=True)
-        tr.close()
-        return
-    tuned = None
-    if not shape and not args.no_autotune:
-        # the library's autotuner picks the launch shapes on this workload (results do not depend
-        # on them); the chosen shape is reported in config.launch_shape
-        rep = tr.autotune([h], reps=3)
-        tuned = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
-        tuned["configs_timed"] = len(rep["entries"])
-    for _ in range(args.warmup):
-        tr.track(h, stream)
-    res = tr.tracks(h)
-    torch.cuda.synchronize()
-
-    # ---- device-timed steps (inputs resident, L2 flushed before each step)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    _barrier(ws)
-    torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            tr.track(h, stream)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-    _barrier(ws)
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    dev_ms = _max_over_ranks(dev_ms, ws)
-    ms_per_step = dev_ms / args.steps
-    value = n * ws * args.steps / (dev_ms / 1e3)
-    res = tr.tracks(h)
-
-    # ---- per-kernel times (eager launches with events between kernels)
-    tr.set_timing(True)
-    kt_runs = []
-    for _ in range(5):
-        flush.zero_()
-        tr.track(h, stream)
-        tr.tracks(h)
-        kt_runs.append(tr.kernel_times())
-    tr.set_timing(False)
-    kernels = {k: float(np.median([r[k] for r in kt_runs])) for k in kt_runs[0]}
-    launches_per_step = int(sum(tr.kernel_times(launches=True).values()))
-    stats = tr.stats(h)
-    dominant = max(kernels, key=kernels.get)
-    hbm_peak, peak_src = _peaks()
-    if dominant == "tracklets":
-        flops = stats["steps"] * FLOPS_PER_STEP
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        achieved = flops / (kernels[dominant] / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": _recorded_traffic(dominant, args.workload),
-                    "peak_source": "derived (FP32 lanes x 2 x max SM clock)",
-                    "alg_flops_per_launch": flops, "row_steps": stats["steps"]}
-    else:
-        alg = ALG_BYTES_PER_CLUSTER.get(dominant, 32.0) * n
-        achieved = alg / (kernels[dominant] / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": _recorded_traffic(dominant, args.workload),
-                    "peak_source": peak_src,
-                    "alg_bytes_per_launch": alg}
-
-    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region
-    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
-    h2d = int(sum(p.numel() * p.element_size() for p in pin))
-    for _ in range(2):
-        tr.run(*[p.numpy() for p in pin])
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    d2h = 0
-    for _ in range(args.steps):
-        out = tr.run(*[p.numpy() for p in pin])
-        d2h = int(sum(np.asarray(v).nbytes for k, v in out.items() if k != "n_tracks"))
-    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": n * ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

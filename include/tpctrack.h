@@ -178,7 +178,6 @@ int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n
  * available (>= 0) or a negative error. */
 int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n);
 
-/* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */
 /* ---- autotuning of the launch shapes (the batched persistent path's rows-per-block and
  * tracklets-per-warp choices). One timed configuration: */
 typedef struct {
@@ -202,8 +201,20 @@ typedef struct {
  * TPC_E_STATE (a frame queued for serving), or any error tpc_track_batch returns. */
 int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int32_t reps, tpc_tune_report* out);
 
+/* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable);
 int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
+
+/* Diagnostic of the kernels' bounded waits (no counterpart in the paper). Every device-side wait of
+ * the library (the neighbour search waits on shared-memory barriers for its staging copies) gives
+ * up after a time limit, records a timeout in a device status word and returns, so a lost copy
+ * becomes TPC_E_TIMEOUT on the host instead of a hang. This call exercises that path: one warp
+ * waits on a barrier whose announced transfer is never issued, with a limit of limit_us
+ * microseconds of device time (1 .. 10^6). Returns TPC_E_TIMEOUT when the wait ran out (the
+ * expected outcome), TPC_OK if it completed, TPC_E_INVAL for a limit out of range, TPC_E_CUDA on a
+ * CUDA error. Nothing is left in flight; the device and every context stay usable. Runs on
+ * cuda_stream (NULL: the legacy default stream) and waits for it. */
+int tpc_check_wait_timeout(int32_t limit_us, void* cuda_stream);
 
 /* Largest frame (clusters) that tpc_links_static() accepts. */
 #define TPC_STATIC_MAX_CLUSTERS 262144

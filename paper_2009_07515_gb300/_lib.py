@@ -136,6 +136,7 @@ SIGNATURES = [
     ("tpc_get_stats", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("tpc_autotune", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_int32,
                                     ctypes.POINTER(tpc_tune_report)]),
+    ("tpc_check_wait_timeout", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
     ("tpc_set_timing", ctypes.c_int, [_ctx_p, ctypes.c_int32]),
     ("tpc_get_kernel_times", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_kernel_times)]),
     ("tpc_links_static", ctypes.c_int, [ctypes.POINTER(tpc_params), ctypes.POINTER(tpc_clusters), ctypes.c_void_p,

@@ -46,13 +46,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait (about a second of device time at most)
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: gives up after limit_ns of device time (the staging copies: one second)
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
+  const unsigned long long t0 = global_ns();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 255u) == 255u && clock64() - t0 > 2000000000LL) return false;
+    if ((it & 255u) == 255u && global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// Diagnostic of the bounded wait: one warp waits on a barrier whose announced transfer is never
+// issued, so the phase cannot complete; the wait gives up after limit_ns and the warp records it in
+// *status (1: timed out, 0: completed) and exits. No copy is in flight at any time.
+__global__ void __launch_bounds__(32) k_wait_probe(uint32_t* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_arrive_expect_tx(&bar, 16u);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+  const bool all = __all_sync(0xffffffffu, ok);
+  if (threadIdx.x == 0) *status = all ? 0u : 1u;
+}
+void launch_wait_probe(uint32_t* status, unsigned long long limit_ns, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(status, limit_ns);
 }
 
 // A row range staged in shared memory: positions [base, base + count) (FP32 float2 records, or

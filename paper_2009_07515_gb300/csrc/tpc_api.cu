@@ -43,6 +43,7 @@ bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t 
 int tracklets_blocks_per_sm(int threads, int regs, int packed);
 bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
 int neighbours_blocks_per_sm(int packed, int warps);
+void launch_wait_probe(uint32_t* status, unsigned long long limit_ns, cudaStream_t s);
 __global__ void k_votes(Work, DevParams);
 __global__ void k_kept(Work, DevParams);
 __global__ void k_write_tracks(Work, DevParams);
@@ -1213,6 +1214,24 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     out->best = best_idx;
   }
   return TPC_OK;
+}
+
+int tpc_check_wait_timeout(int32_t limit_us, void* cuda_stream) {
+  if (limit_us < 1 || limit_us > 1000000) return TPC_E_INVAL;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  uint32_t* d = nullptr;
+  if (cudaMalloc((void**)&d, sizeof(uint32_t)) != cudaSuccess) { cudaGetLastError(); return TPC_E_CUDA; }
+  uint32_t st = 2;
+  cudaError_t e = cudaMemsetAsync(d, 0xFF, sizeof(uint32_t), s);
+  if (e == cudaSuccess) {
+    launch_wait_probe(d, 1000ull * (unsigned long long)limit_us, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&st, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d);
+  if (e != cudaSuccess) { cudaGetLastError(); return TPC_E_CUDA; }
+  return st == 1u ? TPC_E_TIMEOUT : st == 0u ? TPC_OK : TPC_E_CUDA;
 }
 
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable) {

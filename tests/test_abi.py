@@ -78,3 +78,9 @@ def test_launch_shape_parameters_are_validated(lib):
     p = _lib.default_params()
     assert (p.k2_warps, p.k2_tma, p.k5_block, p.k5_regs, p.k5_blocks_per_sm, p.k5_order, p.autotune) == (8, 1, 128, 64, 0, 0, 0)
     assert lib.tpc_autotune(None, None, 0, 1, None) == _lib.TPC_E_INVAL
+
+
+def test_wait_diagnostic_validates_its_limit(lib):
+    from paper_2009_07515_gb300 import _lib
+    assert lib.tpc_check_wait_timeout(0, None) == _lib.TPC_E_INVAL
+    assert lib.tpc_check_wait_timeout(2000000, None) == _lib.TPC_E_INVAL
