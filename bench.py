@@ -271,6 +271,56 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
     return out
 
 
+def batched_benchmark(tpc, synth, torch, *, n_frames: int = 16, steps: int = 5, packed: bool = True) -> dict:
+    """The batched path: n_frames frames of uneven occupancy (Poisson(5) collisions, exponential
+    multiplicity) tracked by one batched graph launch (tpc_track_batch) with launch shapes autotuned
+    on the batch, against the same frames tracked one at a time; inputs resident, L2 flushed before
+    each step, device time by CUDA events on the tracking stream."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    frames = [synth.generate("batch16", frame_id=i) for i in range(n_frames)]
+    total = int(sum(f.n for f in frames))
+    tr = tpc.Tracker(packed=1 if packed else 0)
+    d_in = [[torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (f.sector, f.row, f.y, f.w)] for f in frames]
+    hs = [tr.load(*d) for d in d_in]
+    rep = tr.autotune(hs, reps=2)
+    shape = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(run) -> float:
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            run()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        return ms / steps
+
+    batch_ms = timed(lambda: tr.track_batch(hs, stream))
+    batch_tracks = int(sum(tr.tracks(h, copy=False)["n_tracks"] for h in hs))
+
+    def one_by_one():
+        for h in hs:
+            tr.track(h, stream)
+
+    single_ms = timed(one_by_one)
+    single_tracks = int(sum(tr.tracks(h, copy=False)["n_tracks"] for h in hs))
+    tr.close()
+    return {"workload": f"{n_frames} frames of batch16 (Poisson(5) collisions, Exp(2500) multiplicity capped at 12000)",
+            "clusters": total, "frame_clusters_min": int(min(f.n for f in frames)),
+            "frame_clusters_max": int(max(f.n for f in frames)), "storage": "16-bit" if packed else "fp32",
+            "launch_shape": shape, "batched_ms": batch_ms, "batched_clusters_per_s": total / (batch_ms / 1e3),
+            "one_at_a_time_ms": single_ms, "one_at_a_time_clusters_per_s": total / (single_ms / 1e3),
+            "tracks": batch_tracks, "tracks_equal": batch_tracks == single_tracks}
+
+
 def run_reference(args, ws, rank):
     """Reference arm: the CPU oracle, timed on the host cores, on bounded samples of the workload."""
     if rank != 0:
@@ -309,6 +359,9 @@ def main():
     ap.add_argument("--serve-loads", default="0.9", help="comma-separated arrival rates / plain service rate")
     ap.add_argument("--serve-frames", type=int, default=80)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 16-frame batched-path measurement")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "packed"],
+                    help="cluster storage of the main workload: FP32 or 16-bit fixed point")
     ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
     ap.add_argument("--shape", default="",
                     help='launch shape as JSON tpc_params overrides, e.g. \'{"k5_block": 64}\' (no autotuning)')
@@ -338,7 +391,8 @@ def main():
     frame = synth.generate(args.workload)
     n = frame.n
     shape = json.loads(args.shape) if args.shape else {}
-    tr = tpc.Tracker(**shape)
+    storage = {"packed": 1} if args.storage == "packed" else {}
+    tr = tpc.Tracker(**shape, **storage)
     # inputs resident in HBM
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
     h = tr.load(*d_in)
@@ -430,7 +484,7 @@ def main():
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
     pin_np = [p.numpy() for p in pin]
     h2d = int(sum(p.numel() * p.element_size() for p in pin))
-    e2e_tr = tpc.Tracker(**tuned_params)
+    e2e_tr = tpc.Tracker(**tuned_params, **storage)
 
     def pipelined(k: int) -> int:
         done = sub = inflight = d2h = 0
@@ -440,7 +494,7 @@ def main():
                 sub += 1
                 inflight += 1
             for t in e2e_tr.poll(64, 200000):
-                out = e2e_tr.tracks(t)
+                out = e2e_tr.tracks(t, copy=False)  # views of the read-back tracks, until release
                 d2h = int(sum(np.asarray(v).nbytes for kk, v in out.items() if kk != "n_tracks"))
                 e2e_tr.release(t)
                 done += 1
@@ -469,13 +523,16 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "clusters_per_frame": n, "tracks_per_frame": int(res["n_tracks"]),
-                       "tracklets_per_frame": int(stats.get("tracklets", 0)), "storage": "fp32", "l2": "flushed (512 MB write) before each step",
+                       "tracklets_per_frame": int(stats.get("tracklets", 0)),
+                       "storage": "16-bit fixed point" if storage else "fp32", "l2": "flushed (512 MB write) before each step",
                        "parallelism": f"replicas x{ws}",
                        "launch_shape": tuned if tuned is not None else (shape or "default"),
                        "autotuned": tuned is not None},
             "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "kernels_ms": kernels}
     tr.release(h)
+    if not args.no_batched:
+        line["batched"] = batched_benchmark(tpc, synth, torch)
     if not args.no_serving:
         line["serving"] = serving_benchmark(
             tpc, synth, max_collisions=args.serve_collisions, pool_size=12, n_frames=args.serve_frames,

@@ -66,9 +66,11 @@ typedef struct {
   double y_margin;        /* stop extending when |y| > x*tan(10 deg) + y_margin (cm) */
   int32_t nmin;           /* minimum hits of a voting tracklet and of a track (10) */
   double cov0[5];         /* seed covariance diagonal */
+  int32_t ext_stop;       /* 1: a tracklet's outward extension ends once it accepts the start hit of
+                             another tracklet, whose tracklet covers the rows beyond (1) */
   /* storage / runtime */
   int32_t packed;         /* 1: store cluster coordinates as 16-bit offsets in their grid bin */
-  float bin_occupancy;    /* target clusters per bin of the search grid (2); a launch-shape knob */
+  float bin_occupancy;    /* target clusters per bin of the search grid (1); a launch-shape knob */
   float tracklet_capacity;/* tracklet slots per cluster reserved in a workspace (0.08) */
   int64_t hbm_budget;     /* serving admission budget in bytes (80 GB) */
   int32_t max_batch_frames; /* frames per batched launch (16) */
@@ -76,15 +78,17 @@ typedef struct {
   /* launch shapes: no result depends on them; tpc_autotune() picks them by timing */
   int32_t k2_warps;       /* neighbour search: warps per block, each on 32 hits of one row at a
                              time (4 or 8) */
-  int32_t k2_tma;         /* 1: neighbour search stages adjacent rows in shared memory with bulk
-                             TMA copies; 0: it reads them through L1 */
+  int32_t k2_tma;         /* neighbour search reads of the adjacent rows: 0 through L1, each lane
+                             walking its window's bins; 1 staged in shared memory by bulk TMA
+                             copies, each lane walking its bins; 2 staged, and scanned once by the
+                             whole warp with per-lane candidate lists */
   int32_t k5_block;       /* tracklet construction: threads per block, one tracklet per thread at
                              a time (64, 128 or 256) */
-  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64 or 128) */
+  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64, 80, 128) */
   int32_t k5_blocks_per_sm; /* tracklet blocks launched per SM (0 = all that fit); with k5_block
                              it sets how many tracklets each warp builds */
   int32_t k5_order;       /* tracklet processing order: 0 canonical, 1 longest chain first,
-                             2 innermost start row first */
+                             2 innermost start row first, 3 outermost start row first */
   int32_t autotune;       /* 1: the first tpc_track_batch / tpc_track_sectors call runs
                              tpc_autotune() on its batch first (0) */
 } tpc_params;
@@ -195,10 +199,11 @@ typedef struct {
 /* Times launch shapes on the given frames (a batch, as tpc_track_batch runs it) and keeps the
  * fastest for the context's later runs. Coordinate descent, each candidate run reps + 1 times (the
  * first discarded, median of the rest) with events between stages on the context's stream:
- * bin_occupancy in {1, 2, 4} on the whole sequence; then (k2_warps, k2_tma) on the neighbour
- * search; then (k5_block, k5_regs), k5_order and k5_blocks_per_sm on chains + tracklets. Results of
- * the frames are those of any shape. Blocks until done. Errors: TPC_E_INVAL (bad list, reps < 1),
- * TPC_E_STATE (a frame queued for serving), or any error tpc_track_batch returns. */
+ * bin_occupancy in {1, 2, 4} on the whole sequence; then k2_warps in {4, 8} x k2_tma in {0, 1, 2}
+ * on the neighbour search; then (k5_block, k5_regs), k5_order and k5_blocks_per_sm on chains +
+ * tracklets. Results of the frames are those of any shape. Blocks until done. Errors: TPC_E_INVAL
+ * (bad list, reps < 1), TPC_E_STATE (a frame queued for serving), or any error tpc_track_batch
+ * returns. */
 int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int32_t reps, tpc_tune_report* out);
 
 /* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */

@@ -62,6 +62,7 @@ class Params(ctypes.Structure):
         ("y_margin", ctypes.c_double),
         ("nmin", ctypes.c_int32),
         ("cov0", ctypes.c_double * 5),
+        ("ext_stop", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:

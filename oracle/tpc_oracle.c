@@ -17,15 +17,17 @@
  *   4. start hits: heads of cleaned chains (up link, no down link) of at least lmin hits;
  *   5. tracklet construction: 3-point circle seed, Kalman filter (exact helix propagation in the
  *      solenoid field, multiple-scattering noise, Joseph-form update) along the chain, outward
- *      extension by row-by-row search, then an inward refit (covariance reset) through the found
- *      hits and inward extension;
+ *      extension by row-by-row search (ending, with ext_stop, right after it accepts the start hit
+ *      of another tracklet, which covers the rows beyond), then an inward refit (covariance reset)
+ *      through the found hits and inward extension;
  *   6. tracklet selection: each hit goes to the tracklet with the largest (nhits, -start index) key;
  *      a tracklet becomes a track if it keeps >= nmin hits and at least half of its hits.
  *
  * Precision: compiled twice, REAL = double (FP64 oracle) and REAL = float (FP32 oracle), with
- * -ffp-contract=off and no fast-math. Only +, -, *, /, sqrt are used on REAL values; asin is
- * evaluated by half-angle argument reduction and its Maclaurin series (oracle_asin), so every REAL
- * result is a fixed sequence of correctly rounded operations.
+ * -ffp-contract=off and no fast-math. Only +, -, *, /, sqrt and fused multiply-add (every sum of
+ * products of the Kalman filter accumulates with one fma per term, in index order) are used on REAL
+ * values; asin is evaluated by half-angle argument reduction and its Maclaurin series
+ * (oracle_asin), so every REAL result is a fixed sequence of correctly rounded operations.
  *
  * Coordinates: sector s in [0,36) (s/18 = drift side, s%18 = phi sector), row r in [0,152) at
  * x_r = 85 + r * 160/151 cm (sector-local, radial), y along the pad row, w = v_d * t_arrival.
@@ -74,6 +76,7 @@ typedef struct {
   double y_margin;    /* stop when |y| > x*tan(10 deg) + y_margin */
   int32_t nmin;       /* minimum hits of a voting tracklet and of a track */
   double cov0[5];     /* initial diagonal covariance of the seed */
+  int32_t ext_stop;   /* 1: an outward extension ends at an accepted start hit of another chain */
 } oracle_params;
 
 void ORACLE_SYM(default_params)(oracle_params* p) {
@@ -90,6 +93,7 @@ void ORACLE_SYM(default_params)(oracle_params* p) {
   p->y_margin = 1.0;
   p->nmin = 10;
   p->cov0[0] = 1.0; p->cov0[1] = 1.0; p->cov0[2] = 1.0; p->cov0[3] = 1.0; p->cov0[4] = 100.0;
+  p->ext_stop = 1;
 }
 
 typedef struct {
@@ -107,6 +111,7 @@ typedef struct {
   real cov0[5];
   real x[NROW];
   int want_margins;
+  int ext_stop;
 } ctx_t;
 
 static void make_ctx(const oracle_params* p, ctx_t* c) {
@@ -133,6 +138,7 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
   c->tan10 = (real)0.17632698070846498;
   c->nmin = p->nmin;
   for (int i = 0; i < 5; ++i) c->cov0[i] = (real)p->cov0[i];
+  c->ext_stop = p->ext_stop;
   for (int r = 0; r < NROW; ++r) c->x[r] = (real)85 + (real)r * ((real)160 / (real)151);
   c->want_margins = 1;
 }
@@ -491,6 +497,7 @@ typedef struct {
   int32_t* tr_nk;            /* kept hits */
   int32_t* tr_min;           /* smallest original index among kept hits */
   uint64_t* weight;          /* per local hit */
+  uint8_t* is_start;         /* per local hit: 1 for the start hit of a tracklet */
 } sector_t;
 
 /* Each row is ordered by (w, y, original index). A hit's position in this order (its "rank") is
@@ -688,6 +695,8 @@ static void build_tracklet(const ctx_t* cx, sector_t* S, int64_t h0, int r0) {
       top = r;
       memcpy(Ptop, P, sizeof(Ptop));
       memcpy(Ctop, C, sizeof(Ctop));
+      /* the extension reached another chain's start hit: that tracklet covers the rest outward */
+      if (cx->ext_stop && r >= r0 + mlen && S->is_start[hit]) break;
     } else {
       ++nmiss;
       if (r >= r0 + mlen && nmiss >= cx->n_miss_max) break;
@@ -790,15 +799,19 @@ static void select_tracks(const ctx_t* cx, sector_t* S) {
 static void track_sector(const ctx_t* cx, sector_t* S, int brute) {
   find_neighbours(cx, S, brute);
   clean_links(S);
-  /* start hits in (row, w, orig) order; tracklets are built independently of each other */
+  /* start hits: head of a cleaned chain of at least lmin hits */
+  S->is_start = (uint8_t*)calloc(S->n > 0 ? S->n : 1, 1);
   for (int r = 1; r + 1 < NROW; ++r)
     for (int64_t i = S->row_start[r]; i < S->row_start[r + 1]; ++i) {
       if (!(S->upc[i] >= 0 && S->dnc[i] < 0)) continue;
       int len = 1;
       for (int64_t h = S->upc[i]; h >= 0 && len < cx->lmin; h = S->upc[h]) ++len;
-      if (len < cx->lmin) continue;
-      build_tracklet(cx, S, i, r);
+      S->is_start[i] = len >= cx->lmin;
     }
+  /* tracklets in start-hit (row, w, y, orig) order; built independently of each other */
+  for (int r = 1; r + 1 < NROW; ++r)
+    for (int64_t i = S->row_start[r]; i < S->row_start[r + 1]; ++i)
+      if (S->is_start[i]) build_tracklet(cx, S, i, r);
   select_tracks(cx, S);
 }
 
@@ -817,7 +830,7 @@ static void free_sector(sector_t* S) {
   free(S->orig); free(S->y); free(S->w); free(S->up); free(S->dn); free(S->upc); free(S->dnc);
   free(S->nbm); free(S->t_start); free(S->t_rank); free(S->t_nhits); free(S->t_ndf); free(S->t_rref); free(S->t_rtop);
   free(S->t_ok); free(S->t_x); free(S->t_p); free(S->t_c); free(S->t_chi2); free(S->t_m);
-  free(S->t_slots); free(S->tr_t); free(S->tr_nk); free(S->tr_min); free(S->weight);
+  free(S->t_slots); free(S->tr_t); free(S->tr_nk); free(S->tr_min); free(S->weight); free(S->is_start);
 }
 
 /* Track one frame. Inputs: n clusters in caller order (sector, row, y, w); y and w are given in

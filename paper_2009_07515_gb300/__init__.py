@@ -106,10 +106,12 @@ class Tracker:
         entries = [{k: getattr(rep.entries[i], k) for k in self.TUNE_KEYS} for i in range(rep.n_entries)]
         return {"entries": entries, "best": entries[rep.best] if rep.best >= 0 else None}
 
-    def tracks(self, frame: int) -> dict:
+    def tracks(self, frame: int, copy: bool = True) -> dict:
+        """The frame's tracks (tpc_get_tracks). copy=False returns views of the library's result
+        block, valid until the frame is released."""
         t = _lib.tpc_tracks()
         self._check(self.lib.tpc_get_tracks(self.ctx, ctypes.c_uint64(frame), ctypes.byref(t)))
-        return tracks_to_numpy(t)
+        return tracks_to_numpy(t, copy=copy)
 
     def links(self, frame: int, what: int, n: int) -> np.ndarray:
         out = np.empty(n, np.int32)

@@ -45,6 +45,7 @@ class tpc_params(ctypes.Structure):
         ("y_margin", ctypes.c_double),
         ("nmin", ctypes.c_int32),
         ("cov0", ctypes.c_double * 5),
+        ("ext_stop", ctypes.c_int32),
         ("packed", ctypes.c_int32),
         ("bin_occupancy", ctypes.c_float),
         ("tracklet_capacity", ctypes.c_float),
@@ -189,13 +190,17 @@ def default_params(**overrides) -> tpc_params:
     return p
 
 
-def tracks_to_numpy(t: tpc_tracks) -> dict:
+def tracks_to_numpy(t: tpc_tracks, copy: bool = True) -> dict:
+    """numpy arrays of a tpc_tracks view: copies (default), or views of the library's page-locked
+    result block that stay valid until the frame is released."""
     n = int(t.n_tracks)
 
     def arr(ptr, count, dtype, shape=None):
         if count == 0:
             return np.zeros(shape if shape else (0,), dtype)
-        a = np.ctypeslib.as_array(ptr, shape=(count,)).copy()
+        a = np.ctypeslib.as_array(ptr, shape=(count,))
+        if copy:
+            a = a.copy()
         return a.reshape(shape) if shape else a
 
     off = arr(t.hit_offset, n + 1, np.int64) if n else np.zeros(1, np.int64)

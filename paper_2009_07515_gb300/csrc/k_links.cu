@@ -107,24 +107,57 @@ __device__ __forceinline__ bool pair_key_less(const Work& W, int gd, int gu, int
   return key_less(a.y, a.x, W.horig[x], b.y, b.x, W.horig[y]);
 }
 
-// positions of the w-columns of segment g touched by |w - wc| <= W for wc in [lo, hi]
-__device__ __forceinline__ void column_range(const Work& W, int g, float lo, float hi, int& p0, int& p1) {
+// positions [p0, p1) of the w-columns of segment g touched by |w - wc| <= W for wc in [lo, hi]; iw0
+// is the first of those columns
+__device__ __forceinline__ void column_range(const Work& W, int g, float lo, float hi, int& p0, int& p1, int& iw0) {
   const int4 dim = W.seg_dim[g];
   const float4 geo = W.seg_geo[g];
   const uint32_t bb = W.seg_bb[g];
-  const int iw0 = bin_of(lo, geo.x, geo.y, dim.x), iw1 = bin_of(hi, geo.x, geo.y, dim.x);
+  iw0 = bin_of(lo, geo.x, geo.y, dim.x);
+  const int iw1 = bin_of(hi, geo.x, geo.y, dim.x);
   p0 = (int)W.bin_start[bb + (uint32_t)(iw0 * dim.y)];
   p1 = (int)W.bin_start[bb + (uint32_t)((iw1 + 1) * dim.y)];
 }
 
-// One warp takes 32 consecutive hits of a row; lane 0 stages the w-columns of rows r-1 and r+1
-// that the 32 windows touch into the warp's own shared-memory slots (two bulk copies, one mbarrier
-// per warp), so warps never wait for one another. Each lane then walks its window's bins as one
-// flat loop (the w-columns one after the other), first over row r+1, keeping the candidates that
-// pass the window in a per-lane shared-memory list, then over row r-1, pairing each passing
-// candidate with the listed ones.
-constexpr int kK2Slot = 192;  // staged FP32 records per adjacent row per warp (twice as many 16-bit)
-constexpr int kK2UCap = 6;    // listed row r+1 candidates per lane (more: rescan the row)
+// One warp takes 32 consecutive hits of a row (a chunk); with use_tma >= 1 lane 0 stages the
+// w-columns of rows r-1 and r+1 that the 32 windows touch into the warp's own shared-memory slots
+// (two bulk copies, one mbarrier per warp), so warps never wait for one another.
+//   use_tma 0, 1: each lane walks its own window's bins (reading staged records from shared memory
+//                 and the rest through L1), listing its row r+1 candidates, then pairs each row r-1
+//                 candidate with the list;
+//   use_tma 2:    when both ranges are staged, the warp scans each staged range once, all lanes
+//                 together (one candidate per iteration, broadcast from shared memory): a lane whose
+//                 window holds the candidate appends it to its own list; each lane then pairs its
+//                 two lists. A lane whose list overflows walks its own bins instead.
+// All modes give the same result: the grid only bounds the candidates, the exact window test decides.
+constexpr int kK2Slot = 256;  // staged FP32 records per adjacent row per warp (twice as many 16-bit)
+constexpr int kK2Cap = 6;     // listed candidates per lane and adjacent row
+
+// Shared memory of one warp, by staging mode: the mbarrier (16 B), the two staging slots (modes 1
+// and 2; 16-byte aligned, bulk-copy destinations), the per-lane row r+1 candidate list, and the
+// row r-1 list (mode 2).
+constexpr int kK2ListBytes = kK2Cap * 32 * (8 + 4);
+__host__ __device__ constexpr int k2_warp_bytes(int mode) {
+  return 16 + (mode >= 1 ? 2 * (kK2Slot + 2) * 8 : 0) + (mode == 2 ? 2 : 1) * kK2ListBytes;
+}
+struct K2Warp {
+  uint64_t* bar;
+  float2* stage[2];  // [0] row r-1, [1] row r+1
+  float2* cand[2];   // [side][n * 32 + lane]
+  int* pos[2];
+  __device__ K2Warp(unsigned char* base, int mode) {
+    bar = reinterpret_cast<uint64_t*>(base);
+    unsigned char* p = base + 16;
+    stage[0] = reinterpret_cast<float2*>(p);
+    stage[1] = stage[0] + (kK2Slot + 2);
+    if (mode >= 1) p += 2 * (kK2Slot + 2) * 8;
+    cand[1] = reinterpret_cast<float2*>(p);
+    pos[1] = reinterpret_cast<int*>(p + kK2Cap * 32 * 8);
+    p += kK2ListBytes;
+    cand[0] = reinterpret_cast<float2*>(p);  // used in mode 2 only
+    pos[0] = reinterpret_cast<int*>(p + kK2Cap * 32 * 8);
+  }
+};
 
 // flat cursor over the bins of a grid window: w-columns iw0..iw1, y-bins iy0..iy1 of each
 struct WinCursor {
@@ -161,6 +194,45 @@ __device__ __forceinline__ void pair_step(const Work& W, int gd, int gu, float y
   if (better) { best = chi; bd = d; bu = u; }
 }
 
+// Converged scan of the staged positions [p0, p1) of segment gs (staged from position base): every
+// lane tests every candidate against its own window and lists the ones inside; returns the lane's
+// count (entries beyond kK2Cap are counted, not kept).
+template <bool kPacked>
+__device__ __forceinline__ int scan_staged(const Work& W, K2Warp& S, int side, int gs, int p0, int p1, int base,
+                                           int iw0, bool valid, float yi, float wi, float wy, float ww, int lane) {
+  int n = 0;
+  int cbase = 0, next = 0, iw = iw0, ny = 0, cw0 = 0, cshift = 0;
+  uint32_t bb = 0;
+  if (kPacked && p0 < p1) {
+    const int4 dim = W.seg_dim[gs];
+    bb = W.seg_bb[gs];
+    ny = dim.y; cw0 = dim.z; cshift = dim.w;
+    cbase = col_base(cw0, cshift, iw);
+    next = (int)W.bin_start[bb + (uint32_t)((iw + 1) * ny)];
+  }
+  for (int p = p0; p < p1; ++p) {
+    float2 h;
+    if (kPacked) {
+      while (p >= next) {  // next w-column (warp-uniform)
+        ++iw;
+        cbase = col_base(cw0, cshift, iw);
+        next = (int)W.bin_start[bb + (uint32_t)((iw + 1) * ny)];
+      }
+      h = unpack_hit(reinterpret_cast<const uint32_t*>(S.stage[side])[p - base], cbase);
+    } else {
+      h = S.stage[side][p - base];
+    }
+    if (valid && fabsf(h.x - yi) <= wy && fabsf(h.y - wi) <= ww) {
+      if (n < kK2Cap) {
+        S.cand[side][n * 32 + lane] = h;
+        S.pos[side][n * 32 + lane] = p;
+      }
+      ++n;
+    }
+  }
+  return n;
+}
+
 // chunks of 32 hits of every segment work item (rows 0 and 151 too: their links are cleared)
 __global__ void __launch_bounds__(256) k_chunk_count(Work W) {
   const int nf = W.batch->nf;
@@ -188,12 +260,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q,
   constexpr int kRec = kPacked ? 4 : 8;       // bytes per staged record
   constexpr int kAlign = 16 / kRec;           // records per 16 bytes
   constexpr int kSlot = kPacked ? 2 * kK2Slot : kK2Slot;
-  __shared__ __align__(16) float2 stage_mem[kWarps][2][kK2Slot + 2];
-  __shared__ float2 ucand[kWarps][kK2UCap][32];
-  __shared__ int upos[kWarps][kK2UCap][32];
-  __shared__ __align__(8) uint64_t bar[kWarps];
+  extern __shared__ __align__(16) unsigned char k2_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) mbar_init(&bar[warp], 1);
+  K2Warp S(k2_smem + warp * k2_warp_bytes(use_tma), use_tma);
+  if (lane == 0) mbar_init(S.bar, 1);
   __syncwarp();
   uint32_t parity = 0;
   const uint32_t nch = W.cnt->n_chunks < (uint32_t)W.k2cap ? W.cnt->n_chunks : (uint32_t)W.k2cap;
@@ -214,116 +284,153 @@ __global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q,
     }
     const float wy_dn = Q.wy_dn[r], ww_dn = Q.ww_dn[r], wy_up = Q.wy_up[r], ww_up = Q.ww_up[r];
     const float fm = Q.f_mid[r];
-    {
-      const int i = c0 + lane;
-      const bool valid = i < b;
-      const float2 hi = valid ? hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, i) : make_float2(0.f, 0.f);
-      float lo_w = valid ? hi.y : 3.0e38f, hi_w = valid ? hi.y : -3.0e38f;
+    const int i = c0 + lane;
+    const bool valid = i < b;
+    const float2 hi = valid ? hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, i) : make_float2(0.f, 0.f);
+    float lo_w = valid ? hi.y : 3.0e38f, hi_w = valid ? hi.y : -3.0e38f;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        lo_w = fminf(lo_w, __shfl_xor_sync(0xffffffffu, lo_w, o));
-        hi_w = fmaxf(hi_w, __shfl_xor_sync(0xffffffffu, hi_w, o));
-      }
-      // lane 0: ranges of the adjacent rows, then the copies
-      int base0 = 0, cnt0 = 0, base1 = 0, cnt1 = 0;
-      if (lane == 0) {
-        const float amax = fmaxf(fabsf(lo_w), fabsf(hi_w));
-        uint32_t bytes = 0;
-        int p0, p1;
-        column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), p0, p1);
-        int q0 = p0 & ~(kAlign - 1), q1 = (p1 + kAlign - 1) & ~(kAlign - 1);
-        if (use_tma && q1 > q0 && q1 - q0 <= kSlot) { base0 = q0; cnt0 = q1 - q0; bytes += (uint32_t)(cnt0 * kRec); }
-        column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), p0, p1);
-        q0 = p0 & ~(kAlign - 1);
-        q1 = (p1 + kAlign - 1) & ~(kAlign - 1);
-        if (use_tma && q1 > q0 && q1 - q0 <= kSlot) { base1 = q0; cnt1 = q1 - q0; bytes += (uint32_t)(cnt1 * kRec); }
-        // the slots were read by this warp's previous chunk (generic proxy): order before the copies
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive_expect_tx(&bar[warp], bytes);
-        const char* src = kPacked ? (const char*)W.hq : (const char*)W.hyw;
-        if (cnt0) tma_load_1d(stage_mem[warp][0], src + (size_t)base0 * kRec, (uint32_t)(cnt0 * kRec), &bar[warp]);
-        if (cnt1) tma_load_1d(stage_mem[warp][1], src + (size_t)base1 * kRec, (uint32_t)(cnt1 * kRec), &bar[warp]);
-      }
-      base0 = __shfl_sync(0xffffffffu, base0, 0);
-      cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
-      base1 = __shfl_sync(0xffffffffu, base1, 0);
-      cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
-      const bool ok = mbar_wait_bounded(&bar[warp], parity);
-      if (!__all_sync(0xffffffffu, ok)) {
-        // give the copies in flight a second bounded wait, then this warp stops (its stage is not
-        // used again; the other warps go on)
-        if (!ok) (void)mbar_wait_bounded(&bar[warp], parity);
-        if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
-        break;
-      }
-      parity ^= 1u;
-      const RowView vd{stage_mem[warp][0], base0, cnt0};
-      const RowView vu{stage_mem[warp][1], base1, cnt1};
-      if (valid) {
-        const float yi = hi.x, wi = hi.y;
-        const GridWin qd = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g - 1, yi, wi, wy_dn, ww_dn);
-        const GridWin qu = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g + 1, yi, wi, wy_up, ww_up);
-        // row r+1 candidates inside the window
-        int nu = 0;
-        WinCursor cu{qu.iw0, 0, 0, 0};
-        cursor_col(W, qu, cu);
-        for (int u; (u = cursor_next(W, qu, cu)) >= 0;) {
-          const float2 hu = load_cand<kPacked>(W, vu, u, cu.base);
-          if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-          if (nu < kK2UCap) { ucand[warp][nu][lane] = hu; upos[warp][nu][lane] = u; }
-          ++nu;
+    for (int o = 16; o > 0; o >>= 1) {
+      lo_w = fminf(lo_w, __shfl_xor_sync(0xffffffffu, lo_w, o));
+      hi_w = fmaxf(hi_w, __shfl_xor_sync(0xffffffffu, hi_w, o));
+    }
+    // lane 0: ranges of the adjacent rows, then the copies
+    int rng[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per side: p0, p1, iw0, staged base
+    int cnt0 = 0, cnt1 = 0, conv = 0;
+    if (lane == 0) {
+      const float amax = fmaxf(fabsf(lo_w), fabsf(hi_w));
+      uint32_t bytes = 0;
+      column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), rng[0], rng[1],
+                   rng[2]);
+      int q0 = rng[0] & ~(kAlign - 1), q1 = (rng[1] + kAlign - 1) & ~(kAlign - 1);
+      const bool st0 = use_tma && q1 > q0 && q1 - q0 <= kSlot;
+      if (st0) { rng[3] = q0; cnt0 = q1 - q0; bytes += (uint32_t)(cnt0 * kRec); }
+      column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), rng[4], rng[5],
+                   rng[6]);
+      q0 = rng[4] & ~(kAlign - 1);
+      q1 = (rng[5] + kAlign - 1) & ~(kAlign - 1);
+      const bool st1 = use_tma && q1 > q0 && q1 - q0 <= kSlot;
+      if (st1) { rng[7] = q0; cnt1 = q1 - q0; bytes += (uint32_t)(cnt1 * kRec); }
+      conv = use_tma == 2 && (st0 || rng[1] <= rng[0]) && (st1 || rng[5] <= rng[4]);
+      // the slots were read by this warp's previous chunk (generic proxy): order before the copies
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive_expect_tx(S.bar, bytes);
+      const char* src = kPacked ? (const char*)W.hq : (const char*)W.hyw;
+      if (cnt0) tma_load_1d(S.stage[0], src + (size_t)rng[3] * kRec, (uint32_t)(cnt0 * kRec), S.bar);
+      if (cnt1) tma_load_1d(S.stage[1], src + (size_t)rng[7] * kRec, (uint32_t)(cnt1 * kRec), S.bar);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) rng[j] = __shfl_sync(0xffffffffu, rng[j], 0);
+    cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
+    cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
+    conv = __shfl_sync(0xffffffffu, conv, 0);
+    const bool ok = mbar_wait_bounded(S.bar, parity);
+    if (!__all_sync(0xffffffffu, ok)) {
+      // give the copies in flight a second bounded wait, then this warp stops (its stage is not
+      // used again; the other warps go on)
+      if (!ok) (void)mbar_wait_bounded(S.bar, parity);
+      if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
+      break;
+    }
+    parity ^= 1u;
+    const float yi = hi.x, wi = hi.y;
+    float best = __int_as_float(0x7f800000);
+    int bd = -1, bu = -1;
+    bool own_walk = !conv;
+    if (conv) {
+      const int nd = scan_staged<kPacked>(W, S, 0, g - 1, rng[0], rng[1], rng[3], rng[2], valid, yi, wi, wy_dn, ww_dn, lane);
+      const int nu = scan_staged<kPacked>(W, S, 1, g + 1, rng[4], rng[5], rng[7], rng[6], valid, yi, wi, wy_up, ww_up, lane);
+      if (nd > kK2Cap || nu > kK2Cap) {
+        own_walk = true;
+      } else {
+        for (int a = 0; a < nd; ++a) {
+          const float2 hd = S.cand[0][a * 32 + lane];
+          const int d = S.pos[0][a * 32 + lane];
+          for (int c = 0; c < nu; ++c)
+            pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, S.cand[1][c * 32 + lane], S.pos[1][c * 32 + lane],
+                               best, bd, bu);
         }
-        float best = __int_as_float(0x7f800000);
-        int bd = -1, bu = -1;
-        if (nu > 0) {
-          WinCursor cd{qd.iw0, 0, 0, 0};
-          cursor_col(W, qd, cd);
-          for (int d; (d = cursor_next(W, qd, cd)) >= 0;) {
-            const float2 hd = load_cand<kPacked>(W, vd, d, cd.base);
-            if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
-            if (nu <= kK2UCap) {
-              for (int k = 0; k < nu; ++k)
-                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, ucand[warp][k][lane], upos[warp][k][lane], best,
-                                   bd, bu);
-            } else {
-              WinCursor c2{qu.iw0, 0, 0, 0};
-              cursor_col(W, qu, c2);
-              for (int u; (u = cursor_next(W, qu, c2)) >= 0;) {
-                const float2 hu = load_cand<kPacked>(W, vu, u, c2.base);
-                if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
-              }
+      }
+    }
+    if (valid && own_walk) {
+      const RowView vd{S.stage[0], rng[3], cnt0};
+      const RowView vu{S.stage[1], rng[7], cnt1};
+      const GridWin qd = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g - 1, yi, wi, wy_dn, ww_dn);
+      const GridWin qu = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g + 1, yi, wi, wy_up, ww_up);
+      // row r+1 candidates inside the window
+      int nu = 0;
+      WinCursor cu{qu.iw0, 0, 0, 0};
+      cursor_col(W, qu, cu);
+      for (int u; (u = cursor_next(W, qu, cu)) >= 0;) {
+        const float2 hu = load_cand<kPacked>(W, vu, u, cu.base);
+        if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+        if (nu < kK2Cap) { S.cand[1][nu * 32 + lane] = hu; S.pos[1][nu * 32 + lane] = u; }
+        ++nu;
+      }
+      if (nu > 0) {
+        WinCursor cd{qd.iw0, 0, 0, 0};
+        cursor_col(W, qd, cd);
+        for (int d; (d = cursor_next(W, qd, cd)) >= 0;) {
+          const float2 hd = load_cand<kPacked>(W, vd, d, cd.base);
+          if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
+          if (nu <= kK2Cap) {
+            for (int c = 0; c < nu; ++c)
+              pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, S.cand[1][c * 32 + lane],
+                                 S.pos[1][c * 32 + lane], best, bd, bu);
+          } else {
+            WinCursor c2{qu.iw0, 0, 0, 0};
+            cursor_col(W, qu, c2);
+            for (int u; (u = cursor_next(W, qu, c2)) >= 0;) {
+              const float2 hu = load_cand<kPacked>(W, vu, u, c2.base);
+              if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+              pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
             }
           }
         }
-        W.links[i] = (bd >= 0 && best <= Q.chi_n_max) ? make_int2(bd, bu) : make_int2(-1, -1);
       }
-      __syncwarp();
     }
+    if (valid) W.links[i] = (bd >= 0 && best <= Q.chi_n_max) ? make_int2(bd, bu) : make_int2(-1, -1);
+    __syncwarp();
   }
 }
 
-// warps per block: 4 or 8 (32-hit row chunks a block works on at a time)
-bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma) {
+template <bool kPacked, int kWarps>
+static void prepare_k2() {
+  cudaFuncSetAttribute(k_neighbours<kPacked, kWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       kWarps * k2_warp_bytes(2));
+}
+// Dynamic shared memory limits of the neighbour kernels (once per process and device, before any
+// launch or graph capture).
+void prepare_neighbours() {
+  prepare_k2<false, 4>();
+  prepare_k2<false, 8>();
+  prepare_k2<true, 4>();
+  prepare_k2<true, 8>();
+}
+
+// warps per block: 4 or 8 (32-hit row chunks a block works on at a time); mode: k2_tma (0, 1, 2)
+bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int mode) {
+  if (mode < 0 || mode > 2) return false;
+  const size_t smem = (size_t)warps * k2_warp_bytes(mode);
   if (warps == 4) {
-    if (packed) k_neighbours<true, 4><<<grid, 128, 0, s>>>(W, Q, use_tma);
-    else k_neighbours<false, 4><<<grid, 128, 0, s>>>(W, Q, use_tma);
+    if (packed) k_neighbours<true, 4><<<grid, 128, smem, s>>>(W, Q, mode);
+    else k_neighbours<false, 4><<<grid, 128, smem, s>>>(W, Q, mode);
   } else if (warps == 8) {
-    if (packed) k_neighbours<true, 8><<<grid, 256, 0, s>>>(W, Q, use_tma);
-    else k_neighbours<false, 8><<<grid, 256, 0, s>>>(W, Q, use_tma);
+    if (packed) k_neighbours<true, 8><<<grid, 256, smem, s>>>(W, Q, mode);
+    else k_neighbours<false, 8><<<grid, 256, smem, s>>>(W, Q, mode);
   } else {
     return false;
   }
   return true;
 }
-int neighbours_blocks_per_sm(int packed, int warps) {
+int neighbours_blocks_per_sm(int packed, int warps, int mode) {
   int nb = 0;
+  const size_t smem = (size_t)warps * k2_warp_bytes(mode);
   if (warps == 4) {
-    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true, 4>, 128, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false, 4>, 128, 0);
+    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true, 4>, 128, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false, 4>, 128, smem);
   } else if (warps == 8) {
-    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true, 8>, 256, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false, 8>, 256, 0);
+    if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<true, 8>, 256, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_neighbours<false, 8>, 256, smem);
   }
   return nb;
 }
@@ -401,6 +508,7 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
           st = len >= Q.lmin;
         }
       }
+      if (i < b) W.is_start[i] = st ? 1 : 0;
       const uint32_t m = __ballot_sync(0xffffffffu, st);
       if (lane == 0) warp_off[warp] = __popc(m);
       __syncthreads();

@@ -11,7 +11,8 @@
 //   out     outward, one row per step: the candidate is the chain hit while the chain lasts, then
 //           the hit of smallest chi2 in the row's grid window nsig*sqrt(C)+add; Joseph-form update
 //           when chi2 <= chi2_max; stop after n_miss_max empty rows past the chain, on
-//           |sin(phi)| >= max_sin, or when |y| leaves the row by more than y_margin;
+//           |sin(phi)| >= max_sin, when |y| leaves the row by more than y_margin, or (ext_stop)
+//           right after accepting the start hit of another tracklet;
 //   in      inward from the outermost hit with the covariance reset: refit the outward hits row
 //           by row, then search below the chain start the same way; the state at the last
 //           accepted hit is the tracklet's fit at x_ref.
@@ -22,11 +23,13 @@
 namespace tpc {
 
 // Processing-order key of a tracklet (a counting sort over kNRow + 1 buckets): order 1 takes the
-// longest chains first, order 2 the innermost start rows first (a start row predicts the row
-// steps: the outward pass runs from it to the track's end, the inward pass back over the track).
+// longest chains first, order 2 the innermost start rows first, order 3 the outermost start rows
+// first (the outermost chain of a track runs to its end and back over the whole track when an
+// extension stops at the next tracklet's start hit).
 __device__ __forceinline__ int order_key(const Work& W, int order, uint32_t t, int m) {
   if (order == 1) return kNRow - m;
-  return ((int)W.starts[t].y % kSegPerFrame) % kNRow;
+  const int r0 = ((int)W.starts[t].y % kSegPerFrame) % kNRow;
+  return order == 3 ? kNRow - 1 - r0 : r0;
 }
 
 // (middle hit, last hit, chain length) of every start hit
@@ -207,6 +210,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
           ref = r;
         } else {
           top = r;
+          // the extension reached another tracklet's start hit: that tracklet covers the rows beyond
+          if (searched && Q.ext_stop && W.is_start[hit]) stop = true;
         }
       } else {
         nmiss += 1;
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
 }
 
 // host-side launchers (the kernel templates stay in this translation unit). Shapes: threads per
-// block 64, 128 or 256, each compiled for 64 or 128 registers per thread.
+// block 64, 128 or 256, each compiled for 64, 80 or 128 registers per thread.
 template <int kT, int kR>
 static void launch_shape(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
   if (packed) k_tracklets<kT, kR, true><<<grid, kT, 0, s>>>(W, Q, ordered);
@@ -274,22 +279,25 @@ static int shape_blocks(int packed) {
 // false for a shape that is not compiled
 bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
                       int ordered) {
-  const bool r64 = regs <= 64;
-  switch (threads) {
-    case 64: r64 ? launch_shape<64, 64>(packed, grid, s, W, Q, ordered) : launch_shape<64, 128>(packed, grid, s, W, Q, ordered); return true;
-    case 128: r64 ? launch_shape<128, 64>(packed, grid, s, W, Q, ordered) : launch_shape<128, 128>(packed, grid, s, W, Q, ordered); return true;
-    case 256: r64 ? launch_shape<256, 64>(packed, grid, s, W, Q, ordered) : launch_shape<256, 128>(packed, grid, s, W, Q, ordered); return true;
-    default: return false;
+#define TPC_K5_SHAPE(T, R)                                      \
+  if (threads == T && regs == R) {                              \
+    launch_shape<T, R>(packed, grid, s, W, Q, ordered);         \
+    return true;                                                \
   }
+  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 80) TPC_K5_SHAPE(64, 128)
+  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 80) TPC_K5_SHAPE(128, 128)
+  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 80) TPC_K5_SHAPE(256, 128)
+#undef TPC_K5_SHAPE
+  return false;
 }
 int tracklets_blocks_per_sm(int threads, int regs, int packed) {
-  const bool r64 = regs <= 64;
-  switch (threads) {
-    case 64: return r64 ? shape_blocks<64, 64>(packed) : shape_blocks<64, 128>(packed);
-    case 128: return r64 ? shape_blocks<128, 64>(packed) : shape_blocks<128, 128>(packed);
-    case 256: return r64 ? shape_blocks<256, 64>(packed) : shape_blocks<256, 128>(packed);
-    default: return 0;
-  }
+#define TPC_K5_SHAPE(T, R) \
+  if (threads == T && regs == R) return shape_blocks<T, R>(packed);
+  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 80) TPC_K5_SHAPE(64, 128)
+  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 80) TPC_K5_SHAPE(128, 128)
+  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 80) TPC_K5_SHAPE(256, 128)
+#undef TPC_K5_SHAPE
+  return 0;
 }
 
 }  // namespace tpc

@@ -42,7 +42,8 @@ bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t 
                       int ordered);
 int tracklets_blocks_per_sm(int threads, int regs, int packed);
 bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
-int neighbours_blocks_per_sm(int packed, int warps);
+int neighbours_blocks_per_sm(int packed, int warps, int mode);
+void prepare_neighbours();
 void launch_wait_probe(uint32_t* status, unsigned long long limit_ns, cudaStream_t s);
 __global__ void k_votes(Work, DevParams);
 __global__ void k_kept(Work, DevParams);
@@ -78,6 +79,7 @@ void make_dev_params(const tpc_params& p, DevParams& d) {
   d.tan10 = (float)0.17632698070846498;
   d.nmin = p.nmin;
   for (int i = 0; i < 5; ++i) d.cov0[i] = (float)p.cov0[i];
+  d.ext_stop = p.ext_stop ? 1 : 0;
   d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
   volatile float pitch = (float)160 / (float)151;
   for (int r = 0; r < kNRow; ++r) {
@@ -159,11 +161,54 @@ struct Frame {
   bool served = false;
   size_t input_bytes = 0;           // serving: device input counted against the waiting-input reserve
   double t_submit = 0, t_done = 0;
-  // host results
-  std::vector<int32_t> sector, ndf;
-  std::vector<float> xref, param, cov, chi2;
-  std::vector<int64_t> hoff;
-  std::vector<uint32_t> hits;
+  // host results: views into one page-locked block (from the context's pinned cache)
+  void* res = nullptr;
+  size_t res_cap = 0;
+  int64_t n_tracks = 0;
+  int32_t *sector = nullptr, *ndf = nullptr;
+  float *xref = nullptr, *param = nullptr, *cov = nullptr, *chi2 = nullptr;
+  int64_t* hoff = nullptr;
+  uint32_t* hits = nullptr;
+};
+
+// Page-locked host blocks for results, cached by capacity (powers of two from 1 MiB), so a frame's
+// read-back is a direct DMA into memory that stays valid until the frame is released.
+struct PinnedCache {
+  std::multimap<size_t, void*> free_blocks;
+  size_t cached = 0;
+  static constexpr size_t kMaxCached = size_t(4) << 30;
+  void* get(size_t need, size_t& cap) {
+    auto it = free_blocks.lower_bound(need);
+    if (it != free_blocks.end() && it->first <= 2 * need + (size_t(1) << 20)) {
+      cap = it->first;
+      void* p = it->second;
+      cached -= cap;
+      free_blocks.erase(it);
+      return p;
+    }
+    cap = size_t(1) << 20;
+    while (cap < need) cap <<= 1;
+    void* p = nullptr;
+    if (cudaMallocHost(&p, cap) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, size_t cap) {
+    if (!p) return;
+    if (cached + cap > kMaxCached) {
+      cudaFreeHost(p);
+      return;
+    }
+    free_blocks.emplace(cap, p);
+    cached += cap;
+  }
+  void clear() {
+    for (auto& kv : free_blocks) cudaFreeHost(kv.second);
+    free_blocks.clear();
+    cached = 0;
+  }
 };
 
 }  // namespace
@@ -201,6 +246,7 @@ struct tpc_ctx {
   long long slot_clusters = 0;
   size_t queued_input_bytes = 0;    // device inputs of submitted frames not yet retired
   std::deque<tpc_frame_t> finished;
+  PinnedCache pinned;               // result blocks of fetched frames
 };
 
 namespace {
@@ -266,6 +312,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.k2_tab, 8 * (size_t)(ws->ncap / 32 + ws->scap + 1)},
       {(void**)&W.links, 8 * (size_t)ws->ncap},
       {(void**)&W.clinks, 8 * (size_t)ws->ncap},
+      {(void**)&W.is_start, (size_t)ws->ncap},
       {(void**)&W.seg_nstart, 4 * (size_t)(ws->scap + 1)},
       {(void**)&W.starts_raw, 16 * (size_t)ws->tcap},
       {(void**)&W.starts, 16 * (size_t)ws->tcap},
@@ -361,7 +408,7 @@ int blocks_per_sm(tpc_ctx* ctx, int kernel, int a, int b) {
   const long long key = ((long long)kernel << 40) | ((long long)a << 20) | ((long long)b << 1) | (ctx->p.packed ? 1 : 0);
   auto it = ctx->blocks_cache.find(key);
   if (it != ctx->blocks_cache.end()) return it->second;
-  const int nb = kernel == 0 ? neighbours_blocks_per_sm(ctx->p.packed, a) : tracklets_blocks_per_sm(a, b, ctx->p.packed);
+  const int nb = kernel == 0 ? neighbours_blocks_per_sm(ctx->p.packed, a, b) : tracklets_blocks_per_sm(a, b, ctx->p.packed);
   ctx->blocks_cache[key] = nb;
   return nb;
 }
@@ -407,8 +454,8 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   ++nl; k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);
   ++nl; k_chunk_fill<<<G, 256, 0, s>>>(W);
-  ++nl; launch_neighbours(ctx->p.packed, sh.k2_warps, G * std::max(blocks_per_sm(ctx, 0, sh.k2_warps, 0), 1), s, W, Q,
-                          sh.k2_tma);
+  ++nl; launch_neighbours(ctx->p.packed, sh.k2_warps, G * std::max(blocks_per_sm(ctx, 0, sh.k2_warps, sh.k2_tma), 1), s,
+                          W, Q, sh.k2_tma);
   mark(ki++);  // clean
   ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_start
@@ -584,6 +631,15 @@ Frame* find_frame(tpc_ctx* ctx, tpc_frame_t h) {
   return it == ctx->frames.end() ? nullptr : it->second.get();
 }
 
+void release_results(tpc_ctx* ctx, Frame* f) {
+  ctx->pinned.put(f->res, f->res_cap);
+  f->res = nullptr;
+  f->res_cap = 0;
+  f->n_tracks = 0;
+}
+
+// The frame's tracks into one page-locked block: the device records (fit rows, track info) and the
+// hit list are copied by DMA, then the fit rows are split into the output arrays.
 int fetch_results(tpc_ctx* ctx, Frame* f) {
   Workspace& ws = *f->ws;
   const DevCounters& c = *ws.h_cnt;
@@ -591,17 +647,33 @@ int fetch_results(tpc_ctx* ctx, Frame* f) {
   const uint32_t t0 = c.frame_track0[k], t1 = c.frame_track0[k + 1];
   const uint32_t h0 = c.frame_hit0[k], h1 = c.frame_hit0[k + 1];
   const size_t nt = t1 - t0, nh = h1 - h0;
-  std::vector<float> trf(nt * 24);
-  std::vector<int4> tri(nt);
-  f->hits.resize(nh);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_trf = take(nt * 96), o_tri = take(nt * 16), o_hits = take(nh * 4), o_sec = take(nt * 4),
+               o_ndf = take(nt * 4), o_xref = take(nt * 4), o_chi2 = take(nt * 4), o_par = take(nt * 20),
+               o_cov = take(nt * 60), o_hoff = take((nt + 1) * 8);
+  release_results(ctx, f);
+  size_t cap = 0;
+  char* b = (char*)ctx->pinned.get(off, cap);
+  if (!b) return fail(ctx, TPC_E_NOMEM, "page-locked result allocation failed");
+  f->res = b;
+  f->res_cap = cap;
+  const float* trf = (const float*)(b + o_trf);
+  const int4* tri = (const int4*)(b + o_tri);
+  f->hits = (uint32_t*)(b + o_hits);
   if (nt) {
-    CK(cudaMemcpyAsync(trf.data(), ws.W.tr_f + (size_t)t0 * 24, nt * 96, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(tri.data(), ws.W.tr_i + t0, nt * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + o_trf, ws.W.tr_f + (size_t)t0 * 24, nt * 96, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + o_tri, ws.W.tr_i + t0, nt * 16, cudaMemcpyDeviceToHost, ctx->stream));
   }
-  if (nh) CK(cudaMemcpyAsync(f->hits.data(), ws.W.tr_hits + h0, nh * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  if (nh) CK(cudaMemcpyAsync(f->hits, ws.W.tr_hits + h0, nh * 4, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  f->sector.resize(nt); f->ndf.resize(nt); f->xref.resize(nt); f->chi2.resize(nt);
-  f->param.resize(nt * 5); f->cov.resize(nt * 15); f->hoff.resize(nt + 1);
+  f->sector = (int32_t*)(b + o_sec);
+  f->ndf = (int32_t*)(b + o_ndf);
+  f->xref = (float*)(b + o_xref);
+  f->chi2 = (float*)(b + o_chi2);
+  f->param = (float*)(b + o_par);
+  f->cov = (float*)(b + o_cov);
+  f->hoff = (int64_t*)(b + o_hoff);
   for (size_t i = 0; i < nt; ++i) {
     const float* s = &trf[i * 24];
     for (int j = 0; j < 5; ++j) f->param[i * 5 + j] = s[j];
@@ -613,6 +685,7 @@ int fetch_results(tpc_ctx* ctx, Frame* f) {
     f->hoff[i] = (int64_t)((uint32_t)tri[i].w - h0);
   }
   f->hoff[nt] = (int64_t)nh;
+  f->n_tracks = (int64_t)nt;
   f->state = 5;
   return TPC_OK;
 }
@@ -656,6 +729,7 @@ int load_frame(tpc_ctx* ctx, const tpc_clusters* cl, Frame*& out) {
 
 void drop_frame(tpc_ctx* ctx, Frame* f) {
   if (f->d_block) cudaFreeAsync(f->d_block, ctx->stream);
+  release_results(ctx, f);
   release_ws_user(ctx, f);
   ctx->frames.erase(f->id);
 }
@@ -683,8 +757,9 @@ void tpc_default_params(tpc_params* p) {
   p->y_margin = 1.0;
   p->nmin = 10;
   p->cov0[0] = 1.0; p->cov0[1] = 1.0; p->cov0[2] = 1.0; p->cov0[3] = 1.0; p->cov0[4] = 100.0;
+  p->ext_stop = 1;
   p->packed = 0;
-  p->bin_occupancy = 2.0f;
+  p->bin_occupancy = 1.0f;
   p->tracklet_capacity = 0.08f;
   p->hbm_budget = 80LL << 30;
   p->max_batch_frames = 16;
@@ -692,9 +767,9 @@ void tpc_default_params(tpc_params* p) {
   p->k2_warps = 8;
   p->k2_tma = 1;
   p->k5_block = 128;
-  p->k5_regs = 64;
+  p->k5_regs = 80;
   p->k5_blocks_per_sm = 0;
-  p->k5_order = 0;
+  p->k5_order = 1;
   p->autotune = 0;
 }
 
@@ -713,14 +788,15 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   const tpc_params& q = ctx->p;
   if (q.nmin < 1 || q.lmin < 3 || q.n_miss_max < 1 || !(q.tracklet_capacity > 0) || q.max_batch_frames < 1 ||
       q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
-      (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 128) ||
-      q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 2 || q.bin_occupancy > 64.0f) {
+      (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 80 && q.k5_regs != 128) ||
+      q.k2_tma < 0 || q.k2_tma > 2 ||
+      q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f) {
     delete ctx;
     return TPC_E_INVAL;
   }
   ctx->shape.occ = q.bin_occupancy > 0 ? q.bin_occupancy : 2.0f;
   ctx->shape.k2_warps = q.k2_warps;
-  ctx->shape.k2_tma = q.k2_tma ? 1 : 0;
+  ctx->shape.k2_tma = q.k2_tma;
   ctx->shape.k5_block = q.k5_block;
   ctx->shape.k5_regs = q.k5_regs;
   ctx->shape.k5_bps = q.k5_blocks_per_sm;
@@ -733,6 +809,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "device query failed"); break; }
     if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = TPC_E_CUDA; break; }
+    prepare_neighbours();
     cudaMemPoolProps props{};
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
@@ -770,9 +847,12 @@ void tpc_destroy(tpc_ctx* ctx) {
     cudaStreamSynchronize(sl.stream);
     cudaStreamDestroy(sl.stream);
   }
-  for (auto& kv : ctx->frames)
+  for (auto& kv : ctx->frames) {
     if (kv.second->d_block) cudaFreeAsync(kv.second->d_block, ctx->stream);
+    if (kv.second->res) cudaFreeHost(kv.second->res);
+  }
   ctx->frames.clear();
+  ctx->pinned.clear();
   ctx->slots.clear();
   ctx->wspool.clear();
   if (ctx->stream) { cudaStreamSynchronize(ctx->stream); cudaStreamDestroy(ctx->stream); }
@@ -854,15 +934,16 @@ int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out) {
     rc = fetch_results(ctx, f);
     if (rc) return rc;
   }
-  out->n_tracks = (int64_t)f->sector.size();
-  out->sector = f->sector.data();
-  out->x_ref = f->xref.data();
-  out->param = f->param.data();
-  out->cov = f->cov.data();
-  out->chi2 = f->chi2.data();
-  out->ndf = f->ndf.data();
-  out->hit_offset = f->hoff.data();
-  out->hit_index = f->hits.data();
+  static const int64_t zero_offset = 0;
+  out->n_tracks = f->n_tracks;
+  out->sector = f->sector;
+  out->x_ref = f->xref;
+  out->param = f->param;
+  out->cov = f->cov;
+  out->chi2 = f->chi2;
+  out->ndf = f->ndf;
+  out->hit_offset = f->hoff ? f->hoff : &zero_offset;
+  out->hit_index = f->hits;
   return TPC_OK;
 }
 
@@ -1176,14 +1257,14 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     if ((rc = descend(c, 0))) break;
     c.clear();
     for (int w : {4, 8})
-      for (int tma : {0, 1}) { Shape t = best; t.k2_warps = w; t.k2_tma = tma; c.push_back(t); }
+      for (int tma : {0, 1, 2}) { Shape t = best; t.k2_warps = w; t.k2_tma = tma; c.push_back(t); }
     if ((rc = descend(c, 1))) break;
     c.clear();
     for (int b : {64, 128, 256})
-      for (int r : {64, 128}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_bps = 0; c.push_back(t); }
+      for (int r : {64, 80, 128}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_bps = 0; c.push_back(t); }
     if ((rc = descend(c, 2))) break;
     c.clear();
-    for (int o : {0, 1, 2}) { Shape t = best; t.k5_order = o; c.push_back(t); }
+    for (int o : {0, 1, 2, 3}) { Shape t = best; t.k5_order = o; c.push_back(t); }
     if ((rc = descend(c, 2))) break;
     c.clear();
     const int nb = std::max(blocks_per_sm(ctx, 1, best.k5_block, best.k5_regs), 1);

@@ -55,6 +55,7 @@ struct DevParams {
   float x0_row, ms_c, mass2;
   float max_sin, y_margin, tan10;
   int nmin;
+  int ext_stop;
   float cov0[5];
   float occ;                     // target clusters per grid bin
   float aspect;                  // w/y extent of a grid bin (the neighbour window's aspect)
@@ -124,6 +125,7 @@ struct Work {
   uint2* k2_tab;         // [k2cap] (segment, first position) of every chunk, in work-item order
   int2* links;           // [ncap]
   int2* clinks;          // [ncap]
+  uint8_t* is_start;     // [ncap] 1 at the start hit of a tracklet
   uint32_t* seg_nstart;  // [scap + 1] -> scanned
   uint4* starts_raw;     // [tcap] (hit, seg, first bin of its w-column, -)
   uint4* starts;         // [tcap] (hit, seg, rank-in-sector, -)

@@ -40,6 +40,7 @@ __global__ void k_links_to_input(Work, int, int, int32_t*);
 void make_dev_params(const tpc_params& p, DevParams& d);
 bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
 __global__ void k_chunk_count(Work);
+void prepare_neighbours();
 __global__ void k_chunk_fill(Work);
 }  // namespace tpc
 
@@ -212,10 +213,11 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   k_bin_rank<<<8 * G, 256, 0, s>>>(W);
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
   k_scatter<<<8 * G, 256, 0, s>>>(W);
+  prepare_neighbours();
   k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);
   k_chunk_fill<<<G, 256, 0, s>>>(W);
-  launch_neighbours(0, p.k2_warps == 4 ? 4 : 8, 4 * G, s, W, Q, p.k2_tma);
+  launch_neighbours(0, p.k2_warps == 4 ? 4 : 8, 4 * G, s, W, Q, p.k2_tma >= 0 && p.k2_tma <= 2 ? p.k2_tma : 1);
   k_clean<<<4 * G, 256, 0, s>>>(W, Q);
   if (n > 0) {
     cudaMemsetAsync(up, 0xFF, 4 * (size_t)n, s);

@@ -12,17 +12,22 @@ import synth
 pytestmark = pytest.mark.gpu
 
 SHAPES = [
-    dict(bin_occupancy=1.0),
+    dict(bin_occupancy=2.0),
     dict(bin_occupancy=4.0),
     dict(k2_warps=4),
     dict(k2_tma=0),
+    dict(k2_tma=2),
+    dict(k2_tma=2, k2_warps=4, bin_occupancy=4.0),
     dict(k5_block=64, k5_regs=64),
     dict(k5_block=64, k5_regs=128),
     dict(k5_block=128, k5_regs=128),
+    dict(k5_block=128, k5_regs=80),
+    dict(k5_block=64, k5_regs=80, k5_order=1),
     dict(k5_block=256, k5_regs=64),
     dict(k5_block=256, k5_regs=128),
     dict(k5_blocks_per_sm=1),
     dict(k5_order=1),
+    dict(k5_order=3),
     dict(k5_order=2, k5_blocks_per_sm=2),
 ]
 
