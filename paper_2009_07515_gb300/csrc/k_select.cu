@@ -14,16 +14,25 @@ __device__ __forceinline__ unsigned long long tl_key(uint32_t nh, uint32_t rank)
   return ((unsigned long long)nh << 32) | (unsigned long long)(0xFFFFFFFFu - rank);
 }
 
+// One warp per tracklet (grid-stride over tracklets): the lanes take the tracklet's rows 32 at a
+// time, so the row loop's dependent loads (slab entry, then the hit's word) overlap across lanes.
+__device__ __forceinline__ uint32_t warp_global(int& lane) {
+  lane = threadIdx.x & 31;
+  return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
 __global__ void __launch_bounds__(256) k_votes(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const long long tcap = W.tcap;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+  int lane;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
     const uint32_t info = W.tl_info[t];
     const uint32_t nh = info & 255u;
     if (!(info >> 24) || (int)nh < Q.nmin) continue;
     const unsigned long long key = tl_key(nh, W.starts[t].z);
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
-    for (int r = ref; r <= top; ++r) {
+    for (int r = ref + lane; r <= top; r += 32) {
       const uint32_t h = W.slab[(long long)r * tcap + t];
       if (h != kNoHit) atomicMax(&W.hit_w[h], key);
     }
@@ -33,46 +42,65 @@ __global__ void __launch_bounds__(256) k_votes(Work W, DevParams Q) {
 __global__ void __launch_bounds__(256) k_kept(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const long long tcap = W.tcap;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+  int lane;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
     const uint32_t info = W.tl_info[t];
     const uint32_t nh = info & 255u;
     uint32_t acc = 0, kept = 0;
     if ((info >> 24) && (int)nh >= Q.nmin) {
       const unsigned long long key = tl_key(nh, W.starts[t].z);
       const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
-      for (int r = ref; r <= top; ++r) {
-        const uint32_t h = W.slab[(long long)r * tcap + t];
-        if (h != kNoHit && W.hit_w[h] == key) ++kept;
+      for (int r0 = ref; r0 <= top; r0 += 32) {
+        const int r = r0 + lane;
+        bool mine = false;
+        if (r <= top) {
+          const uint32_t h = W.slab[(long long)r * tcap + t];
+          mine = h != kNoHit && W.hit_w[h] == key;
+        }
+        kept += (uint32_t)__popc(__ballot_sync(0xffffffffu, mine));
       }
       acc = ((int)kept >= Q.nmin && 2u * kept >= nh) ? 1u : 0u;
     }
-    W.tl_kept[t] = acc;
-    W.tl_nkept[t] = acc ? kept : 0u;
+    if (lane == 0) {
+      W.tl_kept[t] = acc;
+      W.tl_nkept[t] = acc ? kept : 0u;
+    }
   }
 }
 
 __global__ void __launch_bounds__(256) k_write_tracks(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const long long tcap = W.tcap;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+  int lane;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
     const uint32_t k = W.tl_kept[t];
     if (W.tl_kept[t + 1] == k) continue;
     const uint32_t info = W.tl_info[t];
     const uint32_t nh = info & 255u;
     const uint4 st = W.starts[t];
     const unsigned long long key = tl_key(nh, st.z);
-    const float* src = W.tl_state + (long long)t * 24;
-    float* dst = W.tr_f + (long long)k * 24;
-#pragma unroll
-    for (int i = 0; i < 22; ++i) dst[i] = src[i];
+    if (lane < 22) W.tr_f[(long long)k * 24 + lane] = W.tl_state[(long long)t * 24 + lane];
     uint32_t off = W.tl_nkept[t];
-    const uint32_t nk = W.tl_nkept[t + 1] - off;
-    const int sector = (int)((st.y % kSegPerFrame) / kNRow);
-    W.tr_i[k] = make_int4(sector, 2 * (int)nh - 5, (int)nk, (int)off);
+    if (lane == 0) {
+      const uint32_t nk = W.tl_nkept[t + 1] - off;
+      const int sector = (int)((st.y % kSegPerFrame) / kNRow);
+      W.tr_i[k] = make_int4(sector, 2 * (int)nh - 5, (int)nk, (int)off);
+    }
+    // kept hits in ascending row order: ballot over each group of 32 rows
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
-    for (int r = ref; r <= top; ++r) {
-      const uint32_t h = W.slab[(long long)r * tcap + t];
-      if (h != kNoHit && W.hit_w[h] == key) W.tr_hits[off++] = W.horig[h];
+    for (int r0 = ref; r0 <= top; r0 += 32) {
+      const int r = r0 + lane;
+      uint32_t h = kNoHit;
+      bool mine = false;
+      if (r <= top) {
+        h = W.slab[(long long)r * tcap + t];
+        mine = h != kNoHit && W.hit_w[h] == key;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, mine);
+      if (mine) W.tr_hits[off + (uint32_t)__popc(m & ((1u << lane) - 1u))] = W.horig[h];
+      off += (uint32_t)__popc(m);
     }
   }
 }

@@ -482,14 +482,14 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // zero_w
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
   mark(ki++);  // votes
-  ++nl; k_votes<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_votes<<<8 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // kept
-  ++nl; k_kept<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_kept<<<8 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_kept
   scan(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks);
   scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
   mark(ki++);  // write_tracks
-  ++nl; k_write_tracks<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_write_tracks<<<8 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // frame_off
   ++nl; k_frame_offsets<<<1, 128, 0, s>>>(W);
   ctx->stage_launches[kNumKernels - 1] = nl;
