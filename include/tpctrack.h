@@ -89,6 +89,8 @@ typedef struct {
                              it sets how many tracklets each warp builds */
   int32_t k5_order;       /* tracklet processing order: 0 canonical, 1 longest chain first,
                              2 innermost start row first, 3 outermost start row first */
+  int32_t sel_lanes;      /* tracklet selection: lanes per tracklet, 32 (a warp takes its rows 32
+                             at a time) or 1 (a warp takes a tile of 32 tracklets row by row) */
   int32_t autotune;       /* 1: the first tpc_track_batch / tpc_track_sectors call runs
                              tpc_autotune() on its batch first (0) */
 } tpc_params;
@@ -186,10 +188,11 @@ int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n);
  * tracklets-per-warp choices). One timed configuration: */
 typedef struct {
   float bin_occupancy;
-  int32_t k2_warps, k2_tma, k5_block, k5_regs, k5_blocks_per_sm, k5_order;
+  int32_t k2_warps, k2_tma, k5_block, k5_regs, k5_blocks_per_sm, k5_order, sel_lanes;
   float ms;        /* median device time of the stages the knob being tuned acts on */
   float total_ms;  /* median device time of the whole sequence */
-  int32_t stage;   /* what ms measures: 0 all stages, 1 neighbour search, 2 chains + tracklets */
+  int32_t stage;   /* what ms measures: 0 all stages, 1 neighbour search, 2 chains + tracklets,
+                      3 votes + kept + write_tracks */
 } tpc_tune_entry;
 typedef struct {
   int32_t n_entries;               /* configurations timed, in the order they were timed */
@@ -201,7 +204,8 @@ typedef struct {
  * first discarded, median of the rest) with events between stages on the context's stream:
  * bin_occupancy in {1, 2, 4} on the whole sequence; then k2_warps in {4, 8} x k2_tma in {0, 1, 2}
  * on the neighbour search; then (k5_block, k5_regs), k5_order and k5_blocks_per_sm on chains +
- * tracklets. Results of the frames are those of any shape. Blocks until done. Errors: TPC_E_INVAL
+ * tracklets; then sel_lanes in {1, 32} on the selection. Results of the frames are those of any
+ * shape. Blocks until done. Errors: TPC_E_INVAL
  * (bad list, reps < 1), TPC_E_STATE (a frame queued for serving), or any error tpc_track_batch
  * returns. */
 int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int32_t reps, tpc_tune_report* out);

@@ -58,6 +58,7 @@ class tpc_params(ctypes.Structure):
         ("k5_regs", ctypes.c_int32),
         ("k5_blocks_per_sm", ctypes.c_int32),
         ("k5_order", ctypes.c_int32),
+        ("sel_lanes", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
     ]
 
@@ -101,6 +102,7 @@ class tpc_tune_entry(ctypes.Structure):
         ("bin_occupancy", ctypes.c_float),
         ("k2_warps", ctypes.c_int32), ("k2_tma", ctypes.c_int32), ("k5_block", ctypes.c_int32),
         ("k5_regs", ctypes.c_int32), ("k5_blocks_per_sm", ctypes.c_int32), ("k5_order", ctypes.c_int32),
+        ("sel_lanes", ctypes.c_int32),
         ("ms", ctypes.c_float),
         ("total_ms", ctypes.c_float),
         ("stage", ctypes.c_int32),

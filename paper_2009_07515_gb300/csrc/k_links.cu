@@ -13,9 +13,9 @@
 // memory. A range too large for a slot is read from global memory instead (same arithmetic, same
 // result).
 //
-// K3 keeps only reciprocal links and counts start hits per segment; K4 writes the start hits
-// (cleaned up link, no down link, chain of >= lmin hits) by a block-wide ballot/scan compaction in
-// sorted order; K4b puts the start hits into canonical order (frame, sector, row-rank) and computes
+// K3 keeps only reciprocal links, marks the start hits (cleaned up link, no down link, chain of
+// >= lmin hits) and counts them per segment; K4 writes the start hits by a block-wide ballot/scan
+// compaction in sorted order; K4b puts the start hits into canonical order (frame, sector, row-rank) and computes
 // each start hit's rank, the tie-break of the tracklet selection key.
 #include "tpc_dev.cuh"
 
@@ -469,11 +469,14 @@ __global__ void __launch_bounds__(256) k_clean(Work W, DevParams Q) {
     for (int i = a + threadIdx.x; i < b; i += blockDim.x) {
       const int u = clean_up(W.links, i), d = clean_dn(W.links, i);
       W.clinks[i] = make_int2(d, u);
+      bool st = false;
       if (u >= 0 && d < 0) {
         int len = 2;
         for (int h = clean_up(W.links, u); h >= 0 && len < Q.lmin; h = clean_up(W.links, h)) ++len;
-        if (len >= Q.lmin) ++count;
+        st = len >= Q.lmin;
       }
+      count += st ? 1 : 0;
+      if (W.is_start) W.is_start[i] = st ? 1 : 0;
     }
     const int tot = block_sum(count, red);
     if (threadIdx.x == 0) W.seg_nstart[g] = (uint32_t)tot;
@@ -499,16 +502,7 @@ __global__ void __launch_bounds__(256) k_starts(Work W, DevParams Q) {
     const float4 geo = W.seg_geo[g];
     for (int c0 = a; c0 < b; c0 += blockDim.x) {
       const int i = c0 + threadIdx.x;
-      bool st = false;
-      if (i < b) {
-        const int2 c = W.clinks[i];
-        if (c.y >= 0 && c.x < 0) {
-          int len = 2;
-          for (int h = W.clinks[c.y].y; h >= 0 && len < Q.lmin; h = W.clinks[h].y) ++len;
-          st = len >= Q.lmin;
-        }
-      }
-      if (i < b) W.is_start[i] = st ? 1 : 0;
+      const bool st = i < b && W.is_start[i];  // set by k_clean
       const uint32_t m = __ballot_sync(0xffffffffu, st);
       if (lane == 0) warp_off[warp] = __popc(m);
       __syncthreads();

@@ -15,15 +15,15 @@ __device__ __forceinline__ unsigned long long tl_key(uint32_t nh, uint32_t rank)
 }
 
 // One warp per tracklet (grid-stride over tracklets): the lanes take the tracklet's rows 32 at a
-// time, so the row loop's dependent loads (slab entry, then the hit's word) overlap across lanes.
+// time, so the row loop's dependent loads (slab entry, then the hit's word) overlap across lanes;
+// the 32 tracklets of a slab tile go to consecutive warps, which share its lines in L2.
 __device__ __forceinline__ uint32_t warp_global(int& lane) {
   lane = threadIdx.x & 31;
   return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 }
 
-__global__ void __launch_bounds__(256) k_votes(Work W, DevParams Q) {
+__global__ void __launch_bounds__(256) k_votes_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  const long long tcap = W.tcap;
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
@@ -33,15 +33,14 @@ __global__ void __launch_bounds__(256) k_votes(Work W, DevParams Q) {
     const unsigned long long key = tl_key(nh, W.starts[t].z);
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     for (int r = ref + lane; r <= top; r += 32) {
-      const uint32_t h = W.slab[(long long)r * tcap + t];
+      const uint32_t h = W.slab[slab_at(t, r)];
       if (h != kNoHit) atomicMax(&W.hit_w[h], key);
     }
   }
 }
 
-__global__ void __launch_bounds__(256) k_kept(Work W, DevParams Q) {
+__global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  const long long tcap = W.tcap;
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
@@ -55,7 +54,7 @@ __global__ void __launch_bounds__(256) k_kept(Work W, DevParams Q) {
         const int r = r0 + lane;
         bool mine = false;
         if (r <= top) {
-          const uint32_t h = W.slab[(long long)r * tcap + t];
+          const uint32_t h = W.slab[slab_at(t, r)];
           mine = h != kNoHit && W.hit_w[h] == key;
         }
         kept += (uint32_t)__popc(__ballot_sync(0xffffffffu, mine));
@@ -69,9 +68,8 @@ __global__ void __launch_bounds__(256) k_kept(Work W, DevParams Q) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_write_tracks(Work W, DevParams Q) {
+__global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  const long long tcap = W.tcap;
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
@@ -95,7 +93,7 @@ __global__ void __launch_bounds__(256) k_write_tracks(Work W, DevParams Q) {
       uint32_t h = kNoHit;
       bool mine = false;
       if (r <= top) {
-        h = W.slab[(long long)r * tcap + t];
+        h = W.slab[slab_at(t, r)];
         mine = h != kNoHit && W.hit_w[h] == key;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
@@ -103,6 +101,117 @@ __global__ void __launch_bounds__(256) k_write_tracks(Work W, DevParams Q) {
       off += (uint32_t)__popc(m);
     }
   }
+}
+
+// One thread per tracklet, the warp's 32 tracklets one slab tile: the lanes walk the union of
+// their row ranges together, so every slab read of the warp is one 128-byte line (better than a
+// warp per tracklet when the slab is far larger than the L2).
+struct RowRange {
+  int lo, hi;  // warp-wide union of the lanes' [ref, top] (empty: lo > hi)
+};
+__device__ __forceinline__ RowRange warp_rows(bool on, int ref, int top) {
+  int lo = on ? ref : kNRow, hi = on ? top : -1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  return RowRange{lo, hi};
+}
+
+__global__ void __launch_bounds__(256) k_votes_thread(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
+    const uint32_t t = t0 + (threadIdx.x & 31u);
+    const uint32_t info = t < ntl ? W.tl_info[t] : 0u;
+    const uint32_t nh = info & 255u;
+    const bool on = (info >> 24) && (int)nh >= Q.nmin;
+    const unsigned long long key = on ? tl_key(nh, W.starts[t].z) : 0ull;
+    const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+    const RowRange rr = warp_rows(on, ref, top);
+    for (int r = rr.lo; r <= rr.hi; ++r) {
+      if (!on || r < ref || r > top) continue;
+      const uint32_t h = W.slab[slab_at(t, r)];
+      if (h != kNoHit) atomicMax(&W.hit_w[h], key);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_kept_thread(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
+    const uint32_t t = t0 + (threadIdx.x & 31u);
+    const uint32_t info = t < ntl ? W.tl_info[t] : 0u;
+    const uint32_t nh = info & 255u;
+    const bool on = (info >> 24) && (int)nh >= Q.nmin;
+    const unsigned long long key = on ? tl_key(nh, W.starts[t].z) : 0ull;
+    const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+    const RowRange rr = warp_rows(on, ref, top);
+    uint32_t kept = 0;
+    for (int r = rr.lo; r <= rr.hi; ++r) {
+      if (!on || r < ref || r > top) continue;
+      const uint32_t h = W.slab[slab_at(t, r)];
+      if (h != kNoHit && W.hit_w[h] == key) ++kept;
+    }
+    const uint32_t acc = (on && (int)kept >= Q.nmin && 2u * kept >= nh) ? 1u : 0u;
+    if (t < ntl) {
+      W.tl_kept[t] = acc;
+      W.tl_nkept[t] = acc ? kept : 0u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
+    const uint32_t t = t0 + (threadIdx.x & 31u);
+    bool on = false;
+    uint32_t k = 0;
+    if (t < ntl) {
+      k = W.tl_kept[t];
+      on = W.tl_kept[t + 1] != k;
+    }
+    uint32_t info = 0, off = 0;
+    unsigned long long key = 0;
+    if (on) {
+      info = W.tl_info[t];
+      const uint32_t nh = info & 255u;
+      const uint4 st = W.starts[t];
+      key = tl_key(nh, st.z);
+      const float* src = W.tl_state + (long long)t * 24;
+      float* dst = W.tr_f + (long long)k * 24;
+#pragma unroll
+      for (int i = 0; i < 22; ++i) dst[i] = src[i];
+      off = W.tl_nkept[t];
+      const uint32_t nk = W.tl_nkept[t + 1] - off;
+      const int sector = (int)((st.y % kSegPerFrame) / kNRow);
+      W.tr_i[k] = make_int4(sector, 2 * (int)nh - 5, (int)nk, (int)off);
+    }
+    const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+    const RowRange rr = warp_rows(on, ref, top);
+    for (int r = rr.lo; r <= rr.hi; ++r) {
+      if (!on || r < ref || r > top) continue;
+      const uint32_t h = W.slab[slab_at(t, r)];
+      if (h != kNoHit && W.hit_w[h] == key) W.tr_hits[off++] = W.horig[h];
+    }
+  }
+}
+
+// selection kernels of the chosen mode (lanes per tracklet: 32 or 1)
+void launch_votes(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q) {
+  if (lanes == 1) k_votes_thread<<<grid, 256, 0, s>>>(W, Q);
+  else k_votes_warp<<<grid, 256, 0, s>>>(W, Q);
+}
+void launch_kept(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q) {
+  if (lanes == 1) k_kept_thread<<<grid, 256, 0, s>>>(W, Q);
+  else k_kept_warp<<<grid, 256, 0, s>>>(W, Q);
+}
+void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q) {
+  if (lanes == 1) k_write_tracks_thread<<<grid, 256, 0, s>>>(W, Q);
+  else k_write_tracks_warp<<<grid, 256, 0, s>>>(W, Q);
 }
 
 // per frame: first tracklet, track and output hit of the frame

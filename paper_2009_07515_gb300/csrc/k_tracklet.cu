@@ -22,6 +22,12 @@
 
 namespace tpc {
 
+// row radius x_r = 85 + r * (160/151) cm, evaluated with the same two rounded float operations as
+// the host table (a per-lane row index into a parameter table would serialise the warp's loads)
+__device__ __forceinline__ float row_x(const DevParams& Q, int r) {
+  return __fadd_rn(85.0f, __fmul_rn((float)r, Q.pitch));
+}
+
 // Processing-order key of a tracklet (a counting sort over kNRow + 1 buckets): order 1 takes the
 // longest chains first, order 2 the innermost start rows first, order 3 the outermost start rows
 // first (the outermost chain of a track runs to its end and back over the whole track when an
@@ -125,7 +131,6 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
 template <int kThreads, int kRegs, bool kPacked>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_tracklets(Work W, DevParams Q, int ordered) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  const long long tcap = W.tcap;
   float P[5], C[15], SP[5], SC[15];
   float chi2sum = 0.f;
   int t = -1, r = 0, r0 = 0, top = -1, ref = -1, nmiss = 0, nh = 0, chain = -1, gb = 0;
@@ -173,9 +178,9 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
     bool stop = false;
     const bool prop = inward ? (r < top) : (r > r0);
     if (prop) {
-      const float xf = Q.x[inward ? r + 1 : r - 1];
-      if (!kf_propagate(Q, P, C, xf, Q.x[r])) stop = true;
-      else if (fabsf(P[0]) > Q.x[r] * Q.tan10 + Q.y_margin) stop = true;
+      const float xf = row_x(Q, inward ? r + 1 : r - 1);
+      if (!kf_propagate(Q, P, C, xf, row_x(Q, r))) stop = true;
+      else if (fabsf(P[0]) > row_x(Q, r) * Q.tan10 + Q.y_margin) stop = true;
     }
     if (!stop) {
       int hit = -1;
@@ -186,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         hit = chain;
         chain = W.clinks[hit].y;
       } else if (inward && r >= r0) {
-        const uint32_t s = W.slab[(long long)r * tcap + t];
+        const uint32_t s = W.slab[slab_at((uint32_t)t, r)];
         hit = s == kNoHit ? -1 : (int)s;
       } else {
         searched = true;
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         nmiss += 1;
         if (searched && nmiss >= Q.n_miss_max) stop = true;
       }
-      W.slab[(long long)r * tcap + t] = acc ? (uint32_t)hit : kNoHit;
+      W.slab[slab_at((uint32_t)t, r)] = acc ? (uint32_t)hit : kNoHit;
       r += inward ? -1 : 1;
       if (r < 0 || r >= kNRow) stop = true;
     }

@@ -45,9 +45,9 @@ bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Wo
 int neighbours_blocks_per_sm(int packed, int warps, int mode);
 void prepare_neighbours();
 void launch_wait_probe(uint32_t* status, unsigned long long limit_ns, cudaStream_t s);
-__global__ void k_votes(Work, DevParams);
-__global__ void k_kept(Work, DevParams);
-__global__ void k_write_tracks(Work, DevParams);
+void launch_votes(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
+void launch_kept(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
+void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
 __global__ void k_frame_offsets(Work);
 __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
@@ -82,6 +82,7 @@ void make_dev_params(const tpc_params& p, DevParams& d) {
   d.ext_stop = p.ext_stop ? 1 : 0;
   d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
   volatile float pitch = (float)160 / (float)151;
+  d.pitch = pitch;
   for (int r = 0; r < kNRow; ++r) {
     volatile float xr = (float)r * pitch;
     d.x[r] = (float)85 + xr;
@@ -117,9 +118,10 @@ struct Shape {
   float occ = 2.0f;      // grid bin occupancy
   int k2_warps = 8, k2_tma = 1;
   int k5_block = 128, k5_regs = 64, k5_bps = 0, k5_order = 0;
+  int sel_lanes = 32;
   bool operator==(const Shape& o) const {
     return occ == o.occ && k2_warps == o.k2_warps && k2_tma == o.k2_tma && k5_block == o.k5_block &&
-           k5_regs == o.k5_regs && k5_bps == o.k5_bps && k5_order == o.k5_order;
+           k5_regs == o.k5_regs && k5_bps == o.k5_bps && k5_order == o.k5_order && sel_lanes == o.sel_lanes;
   }
 };
 
@@ -280,7 +282,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
                     size_t* dry_bytes = nullptr) {
   auto ws = std::shared_ptr<Workspace>(new Workspace, [](Workspace* w) { free_workspace(w); delete w; });
   ws->ncap = std::max(ncap, 1024LL);
-  ws->tcap = std::max(tcap, 1024LL);
+  ws->tcap = (std::max(tcap, 1024LL) + 31) / 32 * 32;  // whole slab tiles
   ws->nf_cap = nf_cap;
   ws->scap = (long long)nf_cap * kSegPerFrame;
   ws->shape = ctx->shape;
@@ -482,14 +484,14 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // zero_w
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
   mark(ki++);  // votes
-  ++nl; k_votes<<<8 * G, 256, 0, s>>>(W, Q);
+  ++nl; launch_votes(sh.sel_lanes, 8 * G, s, W, Q);
   mark(ki++);  // kept
-  ++nl; k_kept<<<8 * G, 256, 0, s>>>(W, Q);
+  ++nl; launch_kept(sh.sel_lanes, 8 * G, s, W, Q);
   mark(ki++);  // scan_kept
   scan(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks);
   scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
   mark(ki++);  // write_tracks
-  ++nl; k_write_tracks<<<8 * G, 256, 0, s>>>(W, Q);
+  ++nl; launch_write_tracks(sh.sel_lanes, 8 * G, s, W, Q);
   mark(ki++);  // frame_off
   ++nl; k_frame_offsets<<<1, 128, 0, s>>>(W);
   ctx->stage_launches[kNumKernels - 1] = nl;
@@ -770,6 +772,7 @@ void tpc_default_params(tpc_params* p) {
   p->k5_regs = 80;
   p->k5_blocks_per_sm = 0;
   p->k5_order = 1;
+  p->sel_lanes = 32;
   p->autotune = 0;
 }
 
@@ -789,7 +792,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   if (q.nmin < 1 || q.lmin < 3 || q.n_miss_max < 1 || !(q.tracklet_capacity > 0) || q.max_batch_frames < 1 ||
       q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
       (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 80 && q.k5_regs != 128) ||
-      q.k2_tma < 0 || q.k2_tma > 2 ||
+      q.k2_tma < 0 || q.k2_tma > 2 || (q.sel_lanes != 1 && q.sel_lanes != 32) ||
       q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f) {
     delete ctx;
     return TPC_E_INVAL;
@@ -801,6 +804,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   ctx->shape.k5_regs = q.k5_regs;
   ctx->shape.k5_bps = q.k5_blocks_per_sm;
   ctx->shape.k5_order = q.k5_order;
+  ctx->shape.sel_lanes = q.sel_lanes;
   make_dev_params(ctx->p, ctx->dp);
   int rc = TPC_OK;
   do {
@@ -1198,13 +1202,13 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
   const bool old_timing = ctx->timing;
   const Shape start = ctx->shape;
   ctx->timing = true;  // eager launches with events between stages on the context's stream
-  const int i_nb = 8, i_ch = 13, i_tl = 14;  // stage indices: neighbours, chains, tracklets
+  const int i_nb = 8, i_ch = 13, i_tl = 14, i_vo = 16, i_ke = 17, i_wt = 19;  // stage indices
   // time one shape: median over reps runs (after one discarded run) of the stage group and total
   auto measure = [&](const Shape& sh, int stage, float& obj) -> int {
     for (const auto& e : ctx->tune_entries) {
       Shape o;
       o.occ = e.bin_occupancy; o.k2_warps = e.k2_warps; o.k2_tma = e.k2_tma; o.k5_block = e.k5_block;
-      o.k5_regs = e.k5_regs; o.k5_bps = e.k5_blocks_per_sm; o.k5_order = e.k5_order;
+      o.k5_regs = e.k5_regs; o.k5_bps = e.k5_blocks_per_sm; o.k5_order = e.k5_order; o.sel_lanes = e.sel_lanes;
       if (o == sh && e.stage == stage) { obj = e.ms; return TPC_OK; }
     }
     ctx->shape = sh;
@@ -1219,13 +1223,16 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
       float tot = 0;
       for (int k = 0; k < kNumKernels; ++k) tot += ctx->ms[k];
       vt.push_back(tot);
-      vo.push_back(stage == 0 ? tot : stage == 1 ? ctx->ms[i_nb] : ctx->ms[i_ch] + ctx->ms[i_tl]);
+      vo.push_back(stage == 0   ? tot
+                   : stage == 1 ? ctx->ms[i_nb]
+                   : stage == 2 ? ctx->ms[i_ch] + ctx->ms[i_tl]
+                                : ctx->ms[i_vo] + ctx->ms[i_ke] + ctx->ms[i_wt]);
     }
     std::sort(vo.begin(), vo.end());
     std::sort(vt.begin(), vt.end());
     tpc_tune_entry e{};
     e.bin_occupancy = sh.occ; e.k2_warps = sh.k2_warps; e.k2_tma = sh.k2_tma; e.k5_block = sh.k5_block;
-    e.k5_regs = sh.k5_regs; e.k5_blocks_per_sm = sh.k5_bps; e.k5_order = sh.k5_order;
+    e.k5_regs = sh.k5_regs; e.k5_blocks_per_sm = sh.k5_bps; e.k5_order = sh.k5_order; e.sel_lanes = sh.sel_lanes;
     e.ms = vo[vo.size() / 2];
     e.total_ms = vt[vt.size() / 2];
     e.stage = stage;
@@ -1274,6 +1281,9 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
       c.push_back(t);
     }
     if ((rc = descend(c, 2))) break;
+    c.clear();
+    for (int lanes : {1, 32}) { Shape t = best; t.sel_lanes = lanes; c.push_back(t); }
+    if ((rc = descend(c, 3))) break;
   } while (0);
   ctx->timing = old_timing;
   if (rc) {
@@ -1286,7 +1296,7 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     const auto& e = ctx->tune_entries[k];
     if (e.bin_occupancy == best.occ && e.k2_warps == best.k2_warps && e.k2_tma == best.k2_tma &&
         e.k5_block == best.k5_block && e.k5_regs == best.k5_regs && e.k5_blocks_per_sm == best.k5_bps &&
-        e.k5_order == best.k5_order)
+        e.k5_order == best.k5_order && e.sel_lanes == best.sel_lanes)
       best_idx = (int)k;
   }
   if (out) {

@@ -17,13 +17,15 @@
 //               one contiguous range per w-column it touches
 //   links[p]    int2 (down, up) raw neighbour links; clinks[p] the cleaned (reciprocal) links
 //   starts[t]   start hits in canonical order (frame, sector, row-rank)
-//   slab[r*tcap + t]  sorted position of tracklet t's hit in row r (0xFFFFFFFF: none), written for
-//               rows [ref_row, top_row]
+//   slab        sorted position of tracklet t's hit in row r (0xFFFFFFFF: none), written for rows
+//               [ref_row, top_row]; tiles of 32 tracklets x 152 rows (slab_at): one tracklet's rows
+//               lie in one 19-kB tile (one page), shared in L2 by the warps of its 32 tracklets
 //
 // The Kalman arithmetic below is written so that every float result is the same sequence of
 // correctly rounded operations as the method's plain definition (compiled with -fmad=false, IEEE
-// division and square root): products with exact zeros and ones of the Jacobian and of I - KH are
-// skipped, the remaining terms are summed in the same order.
+// division and square root, explicit fused multiply-adds where the definition accumulates a sum of
+// products): products with exact zeros and ones of the Jacobian and of I - KH are skipped, the
+// remaining terms are accumulated in the same order.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -60,6 +62,7 @@ struct DevParams {
   float occ;                     // target clusters per grid bin
   float aspect;                  // w/y extent of a grid bin (the neighbour window's aspect)
   float x[kNRow];                // row radii
+  float pitch;                   // row pitch (float)160 / (float)151
   // neighbour windows per row r (valid for 1 <= r <= 150)
   float wy_dn[kNRow], ww_dn[kNRow], wy_up[kNRow], ww_up[kNRow], f_mid[kNRow];
   float yext[kNRow];             // half extent of the grid in y: x * tan(10 deg) + 1 cm
@@ -291,6 +294,11 @@ __device__ __forceinline__ float arc_ratio_deriv(float t) {
     return t * p;
   }
   return (1.0f / sqrtf(1.0f - t * t) - arc_ratio(t)) / t;
+}
+
+// slab index of tracklet t, row r: tiles of 32 tracklets x kNRow rows
+__host__ __device__ __forceinline__ long long slab_at(uint32_t t, int r) {
+  return ((long long)(t >> 5) * kNRow + r) * 32 + (long long)(t & 31u);
 }
 
 // lower-triangular packed covariance index

@@ -29,6 +29,7 @@ SHAPES = [
     dict(k5_order=1),
     dict(k5_order=3),
     dict(k5_order=2, k5_blocks_per_sm=2),
+    dict(sel_lanes=1),
 ]
 
 
@@ -89,9 +90,9 @@ def test_autotune_reports_and_keeps_results(frame, reference):
         assert len(entries) >= 12
         assert rep["best"] is not None and rep["best"] in entries
         assert all(e["ms"] > 0 and e["total_ms"] >= e["ms"] * 0.999 for e in entries)
-        assert {e["stage"] for e in entries} == {0, 1, 2}
+        assert {e["stage"] for e in entries} == {0, 1, 2, 3}
         # the chosen shape is the fastest of those timed for the last knob group
-        last = [e for e in entries if e["stage"] == 2]
+        last = [e for e in entries if e["stage"] == 3]
         assert rep["best"]["ms"] <= min(e["ms"] for e in last) * 1.0001
         tr.track(h)
         res = tr.tracks(h)
