@@ -210,11 +210,19 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
             setattr(f, k, torch.from_numpy(np.ascontiguousarray(getattr(f, k))).pin_memory().numpy())
     params = params or {}
     plain = tpc.Tracker(**params)
+
+    def plain_run(f):
+        # one frame at a time: upload, track, read the tracks back (views of the read-back block)
+        h = plain.load(f.sector, f.row, f.y, f.w)
+        plain.track(h)
+        plain.tracks(h, copy=False)
+        plain.release(h)
+
     for f in pool[:2]:
-        plain.run(f.sector, f.row, f.y, f.w)
+        plain_run(f)
     t0 = time.perf_counter()
     for f in pool:
-        plain.run(f.sector, f.row, f.y, f.w)
+        plain_run(f)
     service = (time.perf_counter() - t0) / pool_size
     out = {"workload": f"Poisson stream, frames of U{{1..{max_collisions}}} collisions (pool of {pool_size})",
            "mean_plain_service_ms": service * 1e3, "budget_gb": budget_gb, "points": []}
@@ -238,8 +246,7 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
             now = time.perf_counter() - t0
             if now < a:
                 time.sleep(a - now)
-            f = pool[k]
-            plain.run(f.sector, f.row, f.y, f.w)
+            plain_run(pool[k])
             lat.append(time.perf_counter() - t0 - a)
         plain_span = (time.perf_counter() - t0) - arrivals[0]
         # served: submit on arrival, poll continuously
@@ -255,7 +262,7 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
                 i += 1
             wait_us = int(max(0.0, (arrivals[i] - now) * 1e6)) if i < n_frames else 200000
             for tk in srv.poll(64, min(wait_us, 200000)):
-                srv.tracks(tk)
+                srv.tracks(tk, copy=False)
                 done[tk] = time.perf_counter() - t0
                 srv.release(tk)
         srv_lat = [done[t] - sub[t] for t in done]

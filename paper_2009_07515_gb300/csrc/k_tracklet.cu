@@ -87,16 +87,10 @@ __device__ __forceinline__ void reset_cov(const DevParams& Q, float* C) {
 // smallest-chi2 hit of segment g inside the window around the predicted (y, w); -1 if none
 template <bool kPacked>
 __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int g, const float* P, const float* C,
-                                          float& chi_out, float2& hit_out) {
+                                          const SInv& V, float& chi_out, float2& hit_out) {
   const float wy = Q.win_nsig * sqrtf(C[lt(0, 0)]) + Q.win_add;
   const float ww = Q.win_nsig * sqrtf(C[lt(1, 1)]) + Q.win_add;
   const GridWin q = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g, P[0], P[1], wy, ww);
-  // chi2 pieces depend on C only
-  const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
-  const float det = S00 * S11 - S01 * S10;
-  const bool pd = det > 0.f;
-  const float idet = 1.0f / det;
-  const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
   int best = -1;
   float bchi = __int_as_float(0x7f800000);
   float2 bc = make_float2(0.f, 0.f);
@@ -107,13 +101,7 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
     for (int h = (int)W.bin_start[col + q.iy0]; h < p1; ++h) {
       const float2 c = hit_in_col<kPacked>(W.hyw, W.hq, h, base);
       if (!(fabsf(c.x - P[0]) <= wy && fabsf(c.y - P[1]) <= ww)) continue;
-      float chi;
-      if (pd) {
-        const float r0 = c.x - P[0], r1 = c.y - P[1];
-        chi = __fmaf_rn(r1, __fmaf_rn(i11, r1, i10 * r0), r0 * __fmaf_rn(i01, r1, i00 * r0));
-      } else {
-        chi = __int_as_float(0x7f800000);
-      }
+      const float chi = kf_chi2(V, P, c.x, c.y);
       bool better;
       if (best < 0 || chi < bchi) better = true;
       else if (chi > bchi) better = false;
@@ -187,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
       float chi = __int_as_float(0x7f800000);
       float2 c = make_float2(0.f, 0.f);
       bool searched = false;
+      const SInv V = kf_sinv(Q, C);
       if (!inward && chain >= 0) {
         hit = chain;
         chain = W.clinks[hit].y;
@@ -195,15 +184,15 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         hit = s == kNoHit ? -1 : (int)s;
       } else {
         searched = true;
-        hit = search_row<kPacked>(W, Q, gb + r, P, C, chi, c);
+        hit = search_row<kPacked>(W, Q, gb + r, P, C, V, chi, c);
       }
       if (hit >= 0 && !searched) {
         c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, hit);
-        chi = kf_chi2(Q, P, C, c.x, c.y);
+        chi = kf_chi2(V, P, c.x, c.y);
       }
       const bool acc = hit >= 0 && chi <= Q.chi2_max;
       if (acc) {
-        kf_update(Q, P, C, c.x, c.y);
+        kf_update(Q, V, P, C, c.x, c.y);
 #pragma unroll
         for (int i = 0; i < 5; ++i) SP[i] = P[i];
 #pragma unroll

@@ -373,22 +373,29 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
   return true;
 }
 
-__device__ __forceinline__ float kf_chi2(const DevParams& Q, const float* P, const float* C, float ym, float wm) {
+// Inverse of the residual covariance S = H C H^T + R of the current state; pd: det S > 0. The chi2
+// of every candidate of a row and the update use the same inverse (the same operations as
+// computing it for each of them).
+struct SInv {
+  float i00, i01, i10, i11;
+  bool pd;
+};
+__device__ __forceinline__ SInv kf_sinv(const DevParams& Q, const float* C) {
   const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
   const float det = S00 * S11 - S01 * S10;
-  if (!(det > 0.f)) return __int_as_float(0x7f800000);
   const float idet = 1.0f / det;
-  const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
+  return SInv{S11 * idet, -S01 * idet, -S10 * idet, S00 * idet, det > 0.f};
+}
+// chi2 of a measurement (ym, wm): +inf when S is not positive definite
+__device__ __forceinline__ float kf_chi2(const SInv& V, const float* P, float ym, float wm) {
+  if (!V.pd) return __int_as_float(0x7f800000);
   const float r0 = ym - P[0], r1 = wm - P[1];
-  const float u0 = __fmaf_rn(i01, r1, i00 * r0), u1 = __fmaf_rn(i11, r1, i10 * r0);
+  const float u0 = __fmaf_rn(V.i01, r1, V.i00 * r0), u1 = __fmaf_rn(V.i11, r1, V.i10 * r0);
   return __fmaf_rn(r1, u1, r0 * u0);
 }
 
-__device__ __forceinline__ void kf_update(const DevParams& Q, float* P, float* C, float ym, float wm) {
-  const float S00 = C[0] + Q.r00, S01 = C[1], S10 = C[1], S11 = C[2] + Q.r11;
-  const float det = S00 * S11 - S01 * S10;
-  const float idet = 1.0f / det;
-  const float i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
+__device__ __forceinline__ void kf_update(const DevParams& Q, const SInv& V, float* P, float* C, float ym, float wm) {
+  const float i00 = V.i00, i01 = V.i01, i10 = V.i10, i11 = V.i11;
   float K[5][2];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
