@@ -87,14 +87,16 @@ struct RowView {
   int base, count;
 };
 
+
+// candidate record at position p: from the stage when the side is staged (then every window of the
+// chunk lies inside it), else from global memory
 template <bool kPacked>
-__device__ __forceinline__ float2 load_cand(const Work& W, const RowView& v, int p, int cbase) {
-  if (kPacked) {
-    const uint32_t q = (p >= v.base && p < v.base + v.count) ? ((const uint32_t*)v.stage)[p - v.base] : W.hq[p];
-    return unpack_hit(q, cbase);
+__device__ __forceinline__ float2 cand_at(const Work& W, const RowView& v, bool staged, int p, int cbase) {
+  if (staged) {
+    if (kPacked) return unpack_hit(reinterpret_cast<const uint32_t*>(v.stage)[p - v.base], cbase);
+    return reinterpret_cast<const float2*>(v.stage)[p - v.base];
   }
-  if (p >= v.base && p < v.base + v.count) return ((const float2*)v.stage)[p - v.base];
-  return W.hyw[p];
+  return kPacked ? unpack_hit(W.hq[p], cbase) : W.hyw[p];
 }
 
 // tie of chi_n: smaller (w, y, input index) of d, then of u (d, bd in segment gd; u, bu in gu)
@@ -122,8 +124,9 @@ __device__ __forceinline__ void column_range(const Work& W, int g, float lo, flo
 // One warp takes 32 consecutive hits of a row (a chunk); with use_tma >= 1 lane 0 stages the
 // w-columns of rows r-1 and r+1 that the 32 windows touch into the warp's own shared-memory slots
 // (two bulk copies, one mbarrier per warp), so warps never wait for one another.
-//   use_tma 0, 1: each lane walks its own window's bins (reading staged records from shared memory
-//                 and the rest through L1), listing its row r+1 candidates, then pairs each row r-1
+//   use_tma 0, 1: each lane walks its own window, column by column and position by position
+//                 (from the stage when its side is staged: the union of the 32 windows lies inside
+//                 it; through L1 otherwise), listing its row r+1 candidates, then pairs each row r-1
 //                 candidate with the list;
 //   use_tma 2:    when both ranges are staged, the warp scans each staged range once, all lanes
 //                 together (one candidate per iteration, broadcast from shared memory): a lane whose
@@ -158,26 +161,6 @@ struct K2Warp {
     pos[0] = reinterpret_cast<int*>(p + kK2Cap * 32 * 8);
   }
 };
-
-// flat cursor over the bins of a grid window: w-columns iw0..iw1, y-bins iy0..iy1 of each
-struct WinCursor {
-  int cw, p, pe, base;
-};
-__device__ __forceinline__ void cursor_col(const Work& W, const GridWin& q, WinCursor& c) {
-  const uint32_t col = q.bb + (uint32_t)(c.cw * q.ny);
-  c.p = (int)W.bin_start[col + q.iy0];
-  c.pe = (int)W.bin_start[col + q.iy1 + 1];
-  c.base = col_base(q.cw0, q.cshift, c.cw);
-}
-// next position of the window, or -1
-__device__ __forceinline__ int cursor_next(const Work& W, const GridWin& q, WinCursor& c) {
-  while (c.p >= c.pe) {
-    if (c.cw >= q.iw1) return -1;
-    ++c.cw;
-    cursor_col(W, q, c);
-  }
-  return c.p++;
-}
 
 template <bool kPacked>
 __device__ __forceinline__ void pair_step(const Work& W, int gd, int gu, float yi, float wi, float fm,
@@ -354,35 +337,46 @@ __global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q,
     if (valid && own_walk) {
       const RowView vd{S.stage[0], rng[3], cnt0};
       const RowView vu{S.stage[1], rng[7], cnt1};
+      // a staged side holds every window of the chunk (the union of the 32 windows' columns)
+      const bool sd = cnt0 > 0, su = cnt1 > 0;
       const GridWin qd = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g - 1, yi, wi, wy_dn, ww_dn);
       const GridWin qu = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g + 1, yi, wi, wy_up, ww_up);
       // row r+1 candidates inside the window
       int nu = 0;
-      WinCursor cu{qu.iw0, 0, 0, 0};
-      cursor_col(W, qu, cu);
-      for (int u; (u = cursor_next(W, qu, cu)) >= 0;) {
-        const float2 hu = load_cand<kPacked>(W, vu, u, cu.base);
-        if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-        if (nu < kK2Cap) { S.cand[1][nu * 32 + lane] = hu; S.pos[1][nu * 32 + lane] = u; }
-        ++nu;
+      for (int cw = qu.iw0; cw <= qu.iw1; ++cw) {
+        const uint32_t col = qu.bb + (uint32_t)(cw * qu.ny);
+        const int pe = (int)W.bin_start[col + qu.iy1 + 1];
+        const int cb = col_base(qu.cw0, qu.cshift, cw);
+        for (int u = (int)W.bin_start[col + qu.iy0]; u < pe; ++u) {
+          const float2 hu = cand_at<kPacked>(W, vu, su, u, cb);
+          if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+          if (nu < kK2Cap) { S.cand[1][nu * 32 + lane] = hu; S.pos[1][nu * 32 + lane] = u; }
+          ++nu;
+        }
       }
       if (nu > 0) {
-        WinCursor cd{qd.iw0, 0, 0, 0};
-        cursor_col(W, qd, cd);
-        for (int d; (d = cursor_next(W, qd, cd)) >= 0;) {
-          const float2 hd = load_cand<kPacked>(W, vd, d, cd.base);
-          if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
-          if (nu <= kK2Cap) {
-            for (int c = 0; c < nu; ++c)
-              pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, S.cand[1][c * 32 + lane],
-                                 S.pos[1][c * 32 + lane], best, bd, bu);
-          } else {
-            WinCursor c2{qu.iw0, 0, 0, 0};
-            cursor_col(W, qu, c2);
-            for (int u; (u = cursor_next(W, qu, c2)) >= 0;) {
-              const float2 hu = load_cand<kPacked>(W, vu, u, c2.base);
-              if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-              pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
+        for (int cwd = qd.iw0; cwd <= qd.iw1; ++cwd) {
+          const uint32_t cold = qd.bb + (uint32_t)(cwd * qd.ny);
+          const int ped = (int)W.bin_start[cold + qd.iy1 + 1];
+          const int cbd = col_base(qd.cw0, qd.cshift, cwd);
+          for (int d = (int)W.bin_start[cold + qd.iy0]; d < ped; ++d) {
+            const float2 hd = cand_at<kPacked>(W, vd, sd, d, cbd);
+            if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
+            if (nu <= kK2Cap) {
+              for (int c = 0; c < nu; ++c)
+                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, S.cand[1][c * 32 + lane],
+                                   S.pos[1][c * 32 + lane], best, bd, bu);
+            } else {
+              for (int cw = qu.iw0; cw <= qu.iw1; ++cw) {
+                const uint32_t col = qu.bb + (uint32_t)(cw * qu.ny);
+                const int pe = (int)W.bin_start[col + qu.iy1 + 1];
+                const int cb = col_base(qu.cw0, qu.cshift, cw);
+                for (int u = (int)W.bin_start[col + qu.iy0]; u < pe; ++u) {
+                  const float2 hu = cand_at<kPacked>(W, vu, su, u, cb);
+                  if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+                  pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
+                }
+              }
             }
           }
         }
