@@ -84,7 +84,7 @@ typedef struct {
                              whole warp with per-lane candidate lists */
   int32_t k5_block;       /* tracklet construction: threads per block, one tracklet per thread at
                              a time (64, 128 or 256) */
-  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64, 80, 128) */
+  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64, 72, 80) */
   int32_t k5_blocks_per_sm; /* tracklet blocks launched per SM (0 = all that fit); with k5_block
                              it sets how many tracklets each warp builds */
   int32_t k5_order;       /* tracklet processing order: 0 canonical, 1 longest chain first,

@@ -119,7 +119,10 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
 template <int kThreads, int kRegs, bool kPacked>
 __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_tracklets(Work W, DevParams Q, int ordered) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  float P[5], C[15], SP[5], SC[15];
+  float P[5], C[15];
+  // state at the last accepted hit, kept in shared memory (one column per thread) to save registers
+  __shared__ float sv[20][kThreads];
+  const int tid = threadIdx.x;
   float chi2sum = 0.f;
   int t = -1, r = 0, r0 = 0, top = -1, ref = -1, nmiss = 0, nh = 0, chain = -1, gb = 0;
   uint32_t steps = 0;
@@ -194,9 +197,9 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
       if (acc) {
         kf_update(Q, V, P, C, c.x, c.y);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) SP[i] = P[i];
+        for (int i = 0; i < 5; ++i) sv[i][tid] = P[i];
 #pragma unroll
-        for (int i = 0; i < 15; ++i) SC[i] = C[i];
+        for (int i = 0; i < 15; ++i) sv[5 + i][tid] = C[i];
         nmiss = 0;
         if (inward) {
           nh += 1;
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         }
         // inward: start again from the outermost hit with the covariance reset
 #pragma unroll
-        for (int i = 0; i < 5; ++i) P[i] = SP[i];
+        for (int i = 0; i < 5; ++i) P[i] = sv[i][tid];
         reset_cov(Q, C);
         inward = true;
         r = top;
@@ -238,9 +241,9 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         if (ref >= 0) {
           float* o = W.tl_state + (long long)t * 24;
 #pragma unroll
-          for (int i = 0; i < 5; ++i) o[i] = SP[i];
+          for (int i = 0; i < 5; ++i) o[i] = sv[i][tid];
 #pragma unroll
-          for (int i = 0; i < 15; ++i) o[5 + i] = SC[i];
+          for (int i = 0; i < 15; ++i) o[5 + i] = sv[5 + i][tid];
           o[20] = chi2sum;
           o[21] = Q.x[ref];
           W.tl_info[t] = (uint32_t)nh | ((uint32_t)ref << 8) | ((uint32_t)top << 16) | (1u << 24);
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
 }
 
 // host-side launchers (the kernel templates stay in this translation unit). Shapes: threads per
-// block 64, 128 or 256, each compiled for 64, 80 or 128 registers per thread.
+// block 64, 128 or 256, each compiled for 64, 72 or 80 registers per thread.
 template <int kT, int kR>
 static void launch_shape(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
   if (packed) k_tracklets<kT, kR, true><<<grid, kT, 0, s>>>(W, Q, ordered);
@@ -278,18 +281,18 @@ bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t 
     launch_shape<T, R>(packed, grid, s, W, Q, ordered);         \
     return true;                                                \
   }
-  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 80) TPC_K5_SHAPE(64, 128)
-  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 80) TPC_K5_SHAPE(128, 128)
-  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 80) TPC_K5_SHAPE(256, 128)
+  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 72) TPC_K5_SHAPE(64, 80)
+  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 72) TPC_K5_SHAPE(128, 80)
+  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 72) TPC_K5_SHAPE(256, 80)
 #undef TPC_K5_SHAPE
   return false;
 }
 int tracklets_blocks_per_sm(int threads, int regs, int packed) {
 #define TPC_K5_SHAPE(T, R) \
   if (threads == T && regs == R) return shape_blocks<T, R>(packed);
-  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 80) TPC_K5_SHAPE(64, 128)
-  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 80) TPC_K5_SHAPE(128, 128)
-  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 80) TPC_K5_SHAPE(256, 128)
+  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 72) TPC_K5_SHAPE(64, 80)
+  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 72) TPC_K5_SHAPE(128, 80)
+  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 72) TPC_K5_SHAPE(256, 80)
 #undef TPC_K5_SHAPE
   return 0;
 }

@@ -791,7 +791,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   const tpc_params& q = ctx->p;
   if (q.nmin < 1 || q.lmin < 3 || q.n_miss_max < 1 || !(q.tracklet_capacity > 0) || q.max_batch_frames < 1 ||
       q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
-      (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 80 && q.k5_regs != 128) ||
+      (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 72 && q.k5_regs != 80) ||
       q.k2_tma < 0 || q.k2_tma > 2 || (q.sel_lanes != 1 && q.sel_lanes != 32) ||
       q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f) {
     delete ctx;
@@ -1268,7 +1268,7 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     if ((rc = descend(c, 1))) break;
     c.clear();
     for (int b : {64, 128, 256})
-      for (int r : {64, 80, 128}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_bps = 0; c.push_back(t); }
+      for (int r : {64, 72, 80}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_bps = 0; c.push_back(t); }
     if ((rc = descend(c, 2))) break;
     c.clear();
     for (int o : {0, 1, 2, 3}) { Shape t = best; t.k5_order = o; c.push_back(t); }

@@ -19,12 +19,12 @@ SHAPES = [
     dict(k2_tma=2),
     dict(k2_tma=2, k2_warps=4, bin_occupancy=4.0),
     dict(k5_block=64, k5_regs=64),
-    dict(k5_block=64, k5_regs=128),
-    dict(k5_block=128, k5_regs=128),
+    dict(k5_block=64, k5_regs=72),
+    dict(k5_block=128, k5_regs=72),
     dict(k5_block=128, k5_regs=80),
     dict(k5_block=64, k5_regs=80, k5_order=1),
     dict(k5_block=256, k5_regs=64),
-    dict(k5_block=256, k5_regs=128),
+    dict(k5_block=256, k5_regs=72),
     dict(k5_blocks_per_sm=1),
     dict(k5_order=1),
     dict(k5_order=3),
