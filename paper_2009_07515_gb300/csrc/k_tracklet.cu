@@ -98,15 +98,25 @@ __device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int
     const uint32_t col = q.bb + (uint32_t)(cw * q.ny);
     const int base = col_base(q.cw0, q.cshift, cw);
     const int p1 = (int)W.bin_start[col + q.iy1 + 1];
-    for (int h = (int)W.bin_start[col + q.iy0]; h < p1; ++h) {
-      const float2 c = hit_in_col<kPacked>(W.hyw, W.hq, h, base);
-      if (!(fabsf(c.x - P[0]) <= wy && fabsf(c.y - P[1]) <= ww)) continue;
-      const float chi = kf_chi2(V, P, c.x, c.y);
-      bool better;
-      if (best < 0 || chi < bchi) better = true;
-      else if (chi > bchi) better = false;
-      else better = key_less(c.y, c.x, W.horig[h], bc.y, bc.x, W.horig[best]);
-      if (better) { best = h; bchi = chi; bc = c; }
+    for (int h0 = (int)W.bin_start[col + q.iy0]; h0 < p1; h0 += 4) {
+      // up to four candidates per memory round trip: the coordinates are loaded together, then
+      // tested in position order
+      float2 cb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        cb[u] = h0 + u < p1 ? hit_in_col<kPacked>(W.hyw, W.hq, h0 + u, base) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int h = h0 + u;
+        const float2 c = cb[u];
+        if (h >= p1 || !(fabsf(c.x - P[0]) <= wy && fabsf(c.y - P[1]) <= ww)) continue;
+        const float chi = kf_chi2(V, P, c.x, c.y);
+        bool better;
+        if (best < 0 || chi < bchi) better = true;
+        else if (chi > bchi) better = false;
+        else better = key_less(c.y, c.x, W.horig[h], bc.y, bc.x, W.horig[best]);
+        if (better) { best = h; bchi = chi; bc = c; }
+      }
     }
   }
   chi_out = bchi;
