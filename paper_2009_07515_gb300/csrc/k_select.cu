@@ -16,7 +16,7 @@ __device__ __forceinline__ unsigned long long tl_key(uint32_t nh, uint32_t rank)
 
 // One warp per tracklet (grid-stride over tracklets): the lanes take the tracklet's rows 32 at a
 // time, so the row loop's dependent loads (slab entry, then the hit's word) overlap across lanes;
-// the 32 tracklets of a slab tile go to consecutive warps, which share its lines in L2.
+// a tracklet's rows are consecutive slab words, so each pass reads one or two 128-byte lines.
 __device__ __forceinline__ uint32_t warp_global(int& lane) {
   lane = threadIdx.x & 31;
   return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
   }
 }
 
-// One thread per tracklet, the warp's 32 tracklets one slab tile: the lanes walk the union of
-// their row ranges together, so every slab read of the warp is one 128-byte line (better than a
-// warp per tracklet when the slab is far larger than the L2).
+// One thread per tracklet, 32 consecutive tracklets per warp: the lanes walk the union of their
+// row ranges together (a slab read of the warp touches one line per lane; the autotuner keeps
+// this variant for frames where it measures faster).
 struct RowRange {
   int lo, hi;  // warp-wide union of the lanes' [ref, top] (empty: lo > hi)
 };

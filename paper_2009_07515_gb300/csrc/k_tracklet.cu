@@ -38,40 +38,80 @@ __device__ __forceinline__ int order_key(const Work& W, int order, uint32_t t, i
   return order == 3 ? kNRow - 1 - r0 : r0;
 }
 
+// Adds n to counter[key] once per group of lanes of the warp with the same key; returns the value
+// before this lane's share (lanes of a group take consecutive values in lane order). All 32 lanes
+// call it; lanes with take = false add nothing.
+__device__ __forceinline__ uint32_t warp_add(uint32_t* counter, int key, bool take) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, take ? key : -1);
+  const int leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (take && lane == leader) base = atomicAdd(&counter[key], (uint32_t)__popc(peers));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+}
+
 // (middle hit, last hit, chain length) of every start hit
 __global__ void __launch_bounds__(256) k_chains(Work W, int order) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
-    int head = (int)W.starts[t].x, mid = head, m = 1;
-    for (;;) {
-      const int nx = W.clinks[head].y;
-      if (nx < 0 || m >= kNRow) break;
-      head = nx;
-      ++m;
-      if ((m & 1) == 0) mid = W.clinks[mid].y;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane takes part in the aggregated count
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
+    const uint32_t t = t0 + (threadIdx.x & 31u);
+    int m = 0;
+    if (t < ntl) {
+      int head = (int)W.starts[t].x, mid = head;
+      m = 1;
+      for (;;) {
+        const int nx = W.clinks[head].y;
+        if (nx < 0 || m >= kNRow) break;
+        head = nx;
+        ++m;
+        if ((m & 1) == 0) mid = W.clinks[mid].y;
+      }
+      W.chains[t] = make_int4(mid, head, m, 0);
     }
-    W.chains[t] = make_int4(mid, head, m, 0);
-    if (order) atomicAdd(&W.len_cnt[order_key(W, order, t, m)], 1u);
+    if (order) (void)warp_add(W.len_cnt, t < ntl ? order_key(W, order, t, m) : 0, t < ntl);
   }
 }
 
 // Processing order of the tracklet kernel (order_key; the order inside a bucket is arbitrary, and
 // no result depends on it: every tracklet reads only the grid and the links and writes only its
 // own outputs). Long tracklets first shorten the tail where few lanes still run.
-__global__ void k_length_offsets(Work W) {
-  if (threadIdx.x == 0) {
-    uint32_t s = 0;
-    for (int k = 0; k <= kNRow; ++k) {
-      const uint32_t c = W.len_cnt[k];
-      W.len_cnt[k] = s;
-      s += c;
-    }
+// One warp: exclusive scan of the kNRow + 1 bucket counts.
+__global__ void __launch_bounds__(32) k_length_offsets(Work W) {
+  constexpr int kPer = (kNRow + 1 + 31) / 32;
+  const int lane = threadIdx.x;
+  uint32_t c[kPer], s = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int k = lane * kPer + j;
+    c[j] = k <= kNRow ? W.len_cnt[k] : 0u;
+    s += c[j];
+  }
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  uint32_t run = x - s;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int k = lane * kPer + j;
+    if (k <= kNRow) W.len_cnt[k] = run;
+    run += c[j];
   }
 }
 __global__ void __launch_bounds__(256) k_length_scatter(Work W, int order) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x)
-    W.order[atomicAdd(&W.len_cnt[order_key(W, order, t, W.chains[t].z)], 1u)] = t;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
+    const uint32_t t = t0 + (threadIdx.x & 31u);
+    const bool ok = t < ntl;
+    const uint32_t slot = warp_add(W.len_cnt, ok ? order_key(W, order, t, W.chains[t].z) : 0, ok);
+    if (ok) W.order[slot] = t;
+  }
 }
 
 __device__ __forceinline__ void reset_cov(const DevParams& Q, float* C) {

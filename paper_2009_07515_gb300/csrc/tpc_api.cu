@@ -282,7 +282,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
                     size_t* dry_bytes = nullptr) {
   auto ws = std::shared_ptr<Workspace>(new Workspace, [](Workspace* w) { free_workspace(w); delete w; });
   ws->ncap = std::max(ncap, 1024LL);
-  ws->tcap = (std::max(tcap, 1024LL) + 31) / 32 * 32;  // whole slab tiles
+  ws->tcap = (std::max(tcap, 1024LL) + 31) / 32 * 32;  // whole warps of tracklets
   ws->nf_cap = nf_cap;
   ws->scap = (long long)nf_cap * kSegPerFrame;
   ws->shape = ctx->shape;

@@ -18,8 +18,10 @@
 //   links[p]    int2 (down, up) raw neighbour links; clinks[p] the cleaned (reciprocal) links
 //   starts[t]   start hits in canonical order (frame, sector, row-rank)
 //   slab        sorted position of tracklet t's hit in row r (0xFFFFFFFF: none), written for rows
-//               [ref_row, top_row]; tiles of 32 tracklets x 152 rows (slab_at): one tracklet's rows
-//               lie in one 19-kB tile (one page), shared in L2 by the warps of its 32 tracklets
+//               [ref_row, top_row]; tracklet-major (slab_at): a lane's stores over successive row
+//               steps fill consecutive words, so a 32-byte sector is completed by one lane rather
+//               than by partial writes of eight tracklets, and a warp reads a tracklet's rows
+//               coalesced
 //
 // The Kalman arithmetic below is written so that every float result is the same sequence of
 // correctly rounded operations as the method's plain definition (compiled with -fmad=false, IEEE
@@ -296,9 +298,9 @@ __device__ __forceinline__ float arc_ratio_deriv(float t) {
   return (1.0f / sqrtf(1.0f - t * t) - arc_ratio(t)) / t;
 }
 
-// slab index of tracklet t, row r: tiles of 32 tracklets x kNRow rows
+// slab index of tracklet t, row r: kNRow consecutive words per tracklet
 __host__ __device__ __forceinline__ long long slab_at(uint32_t t, int r) {
-  return ((long long)(t >> 5) * kNRow + r) * 32 + (long long)(t & 31u);
+  return (long long)t * kNRow + r;
 }
 
 // lower-triangular packed covariance index
