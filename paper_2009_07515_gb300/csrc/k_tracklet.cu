@@ -1,23 +1,25 @@
 // k_tracklet.cu — K5 tracklet construction (helix Kalman filter in the solenoid field).
 //
-// k_chains walks each start hit's cleaned chain once (length, middle and last hit), so the
-// tracklet kernel seeds without pointer chasing.
+// k_chains walks each start hit's cleaned chain once (length, middle and last hit) and writes the
+// chain's hits into the tracklet's slab rows, so the tracklet kernel seeds and follows the chain
+// without pointer chasing (the outward chain steps read slab rows at known addresses, like the
+// inward refit).
 //
 // k_tracklets: one lane builds one tracklet at a time; a lane that finishes takes the next start
 // hit from a device work counter (persistent kernel, grid = SMs x resident blocks). The loop body
 // has one propagation and one update shared by both directions, so lanes of a warp that are in
 // different phases still execute the same Kalman instructions together. Steps of one tracklet:
 //   seed    circle through the first, middle and last chain hits, covariance diag(cov0);
-//   out     outward, one row per step: the candidate is the chain hit while the chain lasts, then
-//           the hit of smallest chi2 in the row's grid window nsig*sqrt(C)+add; Joseph-form update
-//           when chi2 <= chi2_max; stop after n_miss_max empty rows past the chain, on
-//           |sin(phi)| >= max_sin, when |y| leaves the row by more than y_margin, or (ext_stop)
-//           right after accepting the start hit of another tracklet;
+//   out     outward, one row per step: the candidate is the chain hit (from the slab) while the
+//           chain lasts, then the hit of smallest chi2 in the row's grid window
+//           nsig*sqrt(C)+add; Joseph-form update when chi2 <= chi2_max; stop after n_miss_max
+//           empty rows past the chain, on |sin(phi)| >= max_sin, when |y| leaves the row by more
+//           than y_margin, or (ext_stop) right after accepting the start hit of another tracklet;
 //   in      inward from the outermost hit with the covariance reset: refit the outward hits row
 //           by row, then search below the chain start the same way; the state at the last
 //           accepted hit is the tracklet's fit at x_ref.
 // Output per tracklet: fit (P, C, chi2, x_ref), counts, and its hit in every row of
-// [ref_row, top_row] in the row-major slab.
+// [ref_row, top_row] in the tracklet-major slab.
 #include "tpc_dev.cuh"
 
 namespace tpc {
@@ -51,7 +53,7 @@ __device__ __forceinline__ uint32_t warp_add(uint32_t* counter, int key, bool ta
   return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
 }
 
-// (middle hit, last hit, chain length) of every start hit
+// (middle hit, last hit, chain length) of every start hit; the chain hits go to slab rows r0 .. r0+m-1
 __global__ void __launch_bounds__(256) k_chains(Work W, int order) {
   const uint32_t ntl = W.cnt->n_tracklets;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -60,12 +62,16 @@ __global__ void __launch_bounds__(256) k_chains(Work W, int order) {
     const uint32_t t = t0 + (threadIdx.x & 31u);
     int m = 0;
     if (t < ntl) {
-      int head = (int)W.starts[t].x, mid = head;
+      const uint4 st = W.starts[t];
+      const int r0 = ((int)st.y % kSegPerFrame) % kNRow;
+      int head = (int)st.x, mid = head;
       m = 1;
+      W.slab[slab_at(t, r0)] = (uint32_t)head;
       for (;;) {
         const int nx = W.clinks[head].y;
         if (nx < 0 || m >= kNRow) break;
         head = nx;
+        W.slab[slab_at(t, r0 + m)] = (uint32_t)head;
         ++m;
         if ((m & 1) == 0) mid = W.clinks[mid].y;
       }
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
   __shared__ float sv[20][kThreads];
   const int tid = threadIdx.x;
   float chi2sum = 0.f;
-  int t = -1, r = 0, r0 = 0, top = -1, ref = -1, nmiss = 0, nh = 0, chain = -1, gb = 0;
+  int t = -1, r = 0, r0 = 0, top = -1, ref = -1, nmiss = 0, nh = 0, mlen = 0, gb = 0;
   uint32_t steps = 0;
   unsigned long long all_steps = 0, all_hits = 0;
   bool inward = false, active = false;
@@ -210,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
       r = r0;
       top = -1;
       nmiss = 0;
-      chain = (int)st.x;
+      mlen = ch.z;
       inward = false;
       active = true;
     }
@@ -229,10 +235,8 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
       float2 c = make_float2(0.f, 0.f);
       bool searched = false;
       const SInv V = kf_sinv(Q, C);
-      if (!inward && chain >= 0) {
-        hit = chain;
-        chain = W.clinks[hit].y;
-      } else if (inward && r >= r0) {
+      if (inward ? r >= r0 : r < r0 + mlen) {
+        // a chain hit (outward; written by k_chains) or the outward result (inward)
         const uint32_t s = W.slab[slab_at((uint32_t)t, r)];
         hit = s == kNoHit ? -1 : (int)s;
       } else {
