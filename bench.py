@@ -427,6 +427,8 @@ def main():
         tuned = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
         tuned_params = dict(tuned)
         tuned["configs_timed"] = len(rep["entries"])
+        for e in rep["entries"]:  # the tuner's log goes to stderr; stdout keeps the one result line
+            print("tune", json.dumps(e), file=sys.stderr)
     for _ in range(args.warmup):
         tr.track(h, stream)
     res = tr.tracks(h)
