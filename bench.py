@@ -370,6 +370,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "packed"],
                     help="cluster storage of the main workload: FP32 or 16-bit fixed point")
     ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
+    ap.add_argument("--e2e-window", type=int, default=E2E_WINDOW, help="frames in flight in the end-to-end measurement")
     ap.add_argument("--shape", default="",
                     help='launch shape as JSON tpc_params overrides, e.g. \'{"k5_block": 64}\' (no autotuning)')
     ap.add_argument("--profile-only", action="store_true",
@@ -498,7 +499,7 @@ def main():
     def pipelined(k: int) -> int:
         done = sub = inflight = d2h = 0
         while done < k:
-            while sub < k and inflight < E2E_WINDOW:
+            while sub < k and inflight < args.e2e_window:
                 e2e_tr.submit(*pin_np)
                 sub += 1
                 inflight += 1
@@ -510,7 +511,7 @@ def main():
                 inflight -= 1
         return d2h
 
-    pipelined(2 * E2E_WINDOW)  # warm-up: slot workspaces and their graphs
+    pipelined(2 * args.e2e_window)  # warm-up: slot workspaces and their graphs
     torch.cuda.synchronize()
     _barrier(ws)
     t0 = time.perf_counter()
@@ -525,7 +526,7 @@ def main():
         tr.run(*pin_np)
     sync_s = _max_over_ranks(time.perf_counter() - t0, ws)
     e2e = {"value": n * ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "mode": f"pipelined submit/poll, {E2E_WINDOW} frames in flight",
+           "d2h_bytes_per_step": d2h, "mode": f"pipelined submit/poll, {args.e2e_window} frames in flight",
            "sync_value": n * ws * args.steps / sync_s}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -173,13 +173,20 @@ __device__ __forceinline__ InHit read_input(const BatchDesc* B, int packed, long
   return h;
 }
 
-// Clusters are processed in contiguous block chunks so a block rarely spans two frames.
-__global__ void __launch_bounds__(256) k_seg_hist(Work W) {
+// Clusters are processed in contiguous block chunks (one block per SM), so a block rarely spans
+// two frames. Each block counts the segments of its first frame in shared memory and adds its
+// nonzero counts to the global ones at the end (a few global atomics per segment instead of one
+// per cluster); clusters of a later frame in its chunk are counted in global memory directly.
+__global__ void __launch_bounds__(kHistThreads) k_seg_hist(Work W) {
+  __shared__ uint32_t hist[kSegPerFrame];
   const BatchDesc* B = W.batch;
   const long long ntot = B->ntot;
   const long long chunk = (ntot + gridDim.x - 1) / gridDim.x;
   const long long i0 = (long long)blockIdx.x * chunk;
   const long long i1 = min(ntot, i0 + chunk);
+  for (int k = threadIdx.x; k < kSegPerFrame; k += blockDim.x) hist[k] = 0u;
+  const int f0 = i0 < ntot ? frame_of(B, i0) : 0;
+  __syncthreads();
   int f = -1;
   uint32_t lo = 0xFFFFFFFFu, hi = 0u;
   bool bad = false;
@@ -195,7 +202,8 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
       f = fi; lo = 0xFFFFFFFFu; hi = 0u;
     }
     if (!h.ok) { bad = true; continue; }
-    atomicAdd(&W.seg_cnt[h.g], 1u);
+    if (fi == f0) atomicAdd(&hist[h.g - f0 * kSegPerFrame], 1u);
+    else atomicAdd(&W.seg_cnt[h.g], 1u);
     const uint32_t e = f2ord(h.w);
     lo = min(lo, e);
     hi = max(hi, e);
@@ -214,6 +222,10 @@ __global__ void __launch_bounds__(256) k_seg_hist(Work W) {
     atomicMax(&W.cnt->wrange[2 * f + 1], hi);
   }
   if (bad) atomicOr(&W.cnt->err, kErrInput);
+  __syncthreads();
+  if (i0 < ntot)
+    for (int k = threadIdx.x; k < kSegPerFrame; k += blockDim.x)
+      if (hist[k]) atomicAdd(&W.seg_cnt[f0 * kSegPerFrame + k], hist[k]);
 }
 
 // One thread per segment: a grid of ~n/occ bins, nw x ny, bins shaped like the neighbour window

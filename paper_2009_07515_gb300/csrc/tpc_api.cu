@@ -156,7 +156,7 @@ struct Frame {
   float* d_y = nullptr;
   float* d_w = nullptr;
   void* d_block = nullptr;         // owned input allocation (nullptr when borrowed)
-  int state = 0;                   // 0 loaded, 1 queued, 2 admitted, 3 running, 4 done, 5 fetched
+  int state = 0;                   // 0 loaded, 1 queued, 2 admitted, 3 running, 4 results in copy, 5 fetched
   std::shared_ptr<Workspace> ws;
   int fidx = 0;
   std::vector<char> host_copy;      // serving: clusters submitted from host memory, until admitted
@@ -171,6 +171,8 @@ struct Frame {
   float *xref = nullptr, *param = nullptr, *cov = nullptr, *chi2 = nullptr;
   int64_t* hoff = nullptr;
   uint32_t* hits = nullptr;
+  size_t fetch_nt = 0, fetch_nh = 0;  // tracks and hits copied into res (split by fetch_finish)
+  uint32_t fetch_h0 = 0;              // the frame's first hit in the batch's hit list
 };
 
 // Page-locked host blocks for results, cached by capacity (powers of two from 1 MiB), so a frame's
@@ -249,6 +251,14 @@ struct tpc_ctx {
   size_t queued_input_bytes = 0;    // device inputs of submitted frames not yet retired
   std::deque<tpc_frame_t> finished;
   PinnedCache pinned;               // result blocks of fetched frames
+  // serving: result copies in flight (one event per retired batch, recorded on its slot's stream
+  // after the copies; the slot's next batch is queued behind them)
+  struct Fetching {
+    cudaEvent_t ev = nullptr;
+    std::vector<tpc_frame_t> frames;
+  };
+  std::deque<Fetching> fetching;
+  std::vector<cudaEvent_t> spare_events;
 };
 
 namespace {
@@ -439,7 +449,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   ++nl; k_reset_counters<<<1, 128, 0, s>>>(W);
   ++nl; k_zero_u32<<<G, 256, 0, s>>>(W.seg_cnt, &C->nseg, W.scap, 0, 1);
   mark(ki++);  // seg_hist
-  ++nl; k_seg_hist<<<4 * G, 256, 0, s>>>(W);
+  ++nl; k_seg_hist<<<G, kHistThreads, 0, s>>>(W);
   mark(ki++);  // seg_layout
   ++nl; k_seg_layout<<<G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_seg
@@ -640,42 +650,65 @@ void release_results(tpc_ctx* ctx, Frame* f) {
   f->n_tracks = 0;
 }
 
-// The frame's tracks into one page-locked block: the device records (fit rows, track info) and the
-// hit list are copied by DMA, then the fit rows are split into the output arrays.
-int fetch_results(tpc_ctx* ctx, Frame* f) {
+// Layout of a frame's results in its page-locked block: the device records (fit rows, track
+// info) and the hit list as copied, then the output arrays split from the fit rows.
+struct ResLayout {
+  size_t trf, tri, hits, sec, ndf, xref, chi2, par, cov, hoff, bytes;
+};
+ResLayout res_layout(size_t nt, size_t nh) {
+  ResLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
+  L.trf = take(nt * 96); L.tri = take(nt * 16); L.hits = take(nh * 4); L.sec = take(nt * 4);
+  L.ndf = take(nt * 4); L.xref = take(nt * 4); L.chi2 = take(nt * 4); L.par = take(nt * 20);
+  L.cov = take(nt * 60); L.hoff = take((nt + 1) * 8);
+  L.bytes = off;
+  return L;
+}
+
+// The frame's tracks into one page-locked block, step 1: the DMA of the device records, queued on
+// stream s (work queued after it on s may reuse the workspace). The frame's batch has finished.
+int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   Workspace& ws = *f->ws;
   const DevCounters& c = *ws.h_cnt;
   const int k = f->fidx;
   const uint32_t t0 = c.frame_track0[k], t1 = c.frame_track0[k + 1];
   const uint32_t h0 = c.frame_hit0[k], h1 = c.frame_hit0[k + 1];
   const size_t nt = t1 - t0, nh = h1 - h0;
-  size_t off = 0;
-  auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
-  const size_t o_trf = take(nt * 96), o_tri = take(nt * 16), o_hits = take(nh * 4), o_sec = take(nt * 4),
-               o_ndf = take(nt * 4), o_xref = take(nt * 4), o_chi2 = take(nt * 4), o_par = take(nt * 20),
-               o_cov = take(nt * 60), o_hoff = take((nt + 1) * 8);
+  const ResLayout L = res_layout(nt, nh);
   release_results(ctx, f);
   size_t cap = 0;
-  char* b = (char*)ctx->pinned.get(off, cap);
+  char* b = (char*)ctx->pinned.get(L.bytes, cap);
   if (!b) return fail(ctx, TPC_E_NOMEM, "page-locked result allocation failed");
   f->res = b;
   f->res_cap = cap;
-  const float* trf = (const float*)(b + o_trf);
-  const int4* tri = (const int4*)(b + o_tri);
-  f->hits = (uint32_t*)(b + o_hits);
+  f->fetch_nt = nt;
+  f->fetch_nh = nh;
+  f->fetch_h0 = h0;
   if (nt) {
-    CK(cudaMemcpyAsync(b + o_trf, ws.W.tr_f + (size_t)t0 * 24, nt * 96, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(b + o_tri, ws.W.tr_i + t0, nt * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b + L.trf, ws.W.tr_f + (size_t)t0 * 24, nt * 96, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b + L.tri, ws.W.tr_i + t0, nt * 16, cudaMemcpyDeviceToHost, s));
   }
-  if (nh) CK(cudaMemcpyAsync(f->hits, ws.W.tr_hits + h0, nh * 4, cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  f->sector = (int32_t*)(b + o_sec);
-  f->ndf = (int32_t*)(b + o_ndf);
-  f->xref = (float*)(b + o_xref);
-  f->chi2 = (float*)(b + o_chi2);
-  f->param = (float*)(b + o_par);
-  f->cov = (float*)(b + o_cov);
-  f->hoff = (int64_t*)(b + o_hoff);
+  if (nh) CK(cudaMemcpyAsync(b + L.hits, ws.W.tr_hits + h0, nh * 4, cudaMemcpyDeviceToHost, s));
+  return TPC_OK;
+}
+
+// Step 2, once the copies have completed: the fit rows split into the output arrays.
+void fetch_finish(Frame* f) {
+  const size_t nt = f->fetch_nt, nh = f->fetch_nh;
+  const uint32_t h0 = f->fetch_h0;
+  const ResLayout L = res_layout(nt, nh);
+  char* b = (char*)f->res;
+  const float* trf = (const float*)(b + L.trf);
+  const int4* tri = (const int4*)(b + L.tri);
+  f->hits = (uint32_t*)(b + L.hits);
+  f->sector = (int32_t*)(b + L.sec);
+  f->ndf = (int32_t*)(b + L.ndf);
+  f->xref = (float*)(b + L.xref);
+  f->chi2 = (float*)(b + L.chi2);
+  f->param = (float*)(b + L.par);
+  f->cov = (float*)(b + L.cov);
+  f->hoff = (int64_t*)(b + L.hoff);
   for (size_t i = 0; i < nt; ++i) {
     const float* s = &trf[i * 24];
     for (int j = 0; j < 5; ++j) f->param[i * 5 + j] = s[j];
@@ -689,6 +722,34 @@ int fetch_results(tpc_ctx* ctx, Frame* f) {
   f->hoff[nt] = (int64_t)nh;
   f->n_tracks = (int64_t)nt;
   f->state = 5;
+}
+
+int fetch_results(tpc_ctx* ctx, Frame* f) {
+  int rc = fetch_enqueue(ctx, f, ctx->stream);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));
+  fetch_finish(f);
+  return TPC_OK;
+}
+
+// Finished result copies of retired batches: split the fit rows and hand the frames to tpc_poll
+// (wait: block until every copy in flight has completed).
+int finish_fetches(tpc_ctx* ctx, bool wait) {
+  while (!ctx->fetching.empty()) {
+    auto& fe = ctx->fetching.front();
+    cudaError_t e = wait ? cudaEventSynchronize(fe.ev) : cudaEventQuery(fe.ev);
+    if (e == cudaErrorNotReady) break;
+    if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("device: ") + cudaGetErrorString(e));
+    for (auto id : fe.frames) {
+      Frame* f = find_frame(ctx, id);
+      if (!f) continue;
+      fetch_finish(f);
+      f->t_done = now_s();
+      ctx->finished.push_back(id);
+    }
+    ctx->spare_events.push_back(fe.ev);
+    ctx->fetching.pop_front();
+  }
   return TPC_OK;
 }
 
@@ -730,6 +791,8 @@ int load_frame(tpc_ctx* ctx, const tpc_clusters* cl, Frame*& out) {
 }
 
 void drop_frame(tpc_ctx* ctx, Frame* f) {
+  auto it = std::find(ctx->finished.begin(), ctx->finished.end(), f->id);
+  if (it != ctx->finished.end()) ctx->finished.erase(it);
   if (f->d_block) cudaFreeAsync(f->d_block, ctx->stream);
   release_results(ctx, f);
   release_ws_user(ctx, f);
@@ -858,6 +921,10 @@ void tpc_destroy(tpc_ctx* ctx) {
   ctx->frames.clear();
   ctx->pinned.clear();
   ctx->slots.clear();
+  for (auto& fe : ctx->fetching) cudaEventDestroy(fe.ev);
+  for (auto ev : ctx->spare_events) cudaEventDestroy(ev);
+  ctx->fetching.clear();
+  ctx->spare_events.clear();
   ctx->wspool.clear();
   if (ctx->stream) { cudaStreamSynchronize(ctx->stream); cudaStreamDestroy(ctx->stream); }
   for (int k = 0; k <= kNumKernels; ++k)
@@ -912,6 +979,10 @@ int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out) {
   if (!ctx || !out) return TPC_E_INVAL;
   Frame* f = find_frame(ctx, frame);
   if (!f) return fail(ctx, TPC_E_INVAL, "unknown frame handle");
+  if (f->state == 4) {  // served, results in copy
+    int rc = finish_fetches(ctx, true);
+    if (rc) return rc;
+  }
   if (f->state < 3) return fail(ctx, TPC_E_STATE, "frame has not been tracked");
   if (f->state < 5) {
     int rc = wait_ws(ctx, *f->ws, 120.0);
@@ -999,6 +1070,10 @@ int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame) {
   if (!ctx) return TPC_E_INVAL;
   Frame* f = find_frame(ctx, frame);
   if (!f) return fail(ctx, TPC_E_INVAL, "unknown frame handle");
+  if (f->state == 4) {  // served, results in copy: the copy completes before its block is reused
+    int rc = finish_fetches(ctx, true);
+    if (rc) return rc;
+  }
   if (f->state == 3 && f->ws) {
     int rc = wait_ws(ctx, *f->ws, 120.0);
     if (rc) return rc;
@@ -1086,8 +1161,19 @@ int upload_frame(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   return TPC_OK;
 }
 
+// The input and the workspace reference of a retired frame (its results are fetched or in copy).
+void retire_inputs(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
+  release_ws_user(ctx, f);
+  if (f->d_block) { cudaFreeAsync(f->d_block, s); f->d_block = nullptr; }
+  ctx->queued_input_bytes -= std::min(ctx->queued_input_bytes, f->input_bytes);
+  f->input_bytes = 0;
+  f->host_copy.clear();
+  f->host_copy.shrink_to_fit();
+}
+
 int serve_step(tpc_ctx* ctx) {
-  // retire finished batches: results to the host, inputs and the slot's workspace freed
+  // retire finished batches: the results' copies are queued on the slot's stream (its next batch
+  // runs behind them), inputs and workspace references are freed
   for (auto& sl : ctx->slots) {
     if (!sl.busy) continue;
     cudaError_t e = cudaEventQuery(sl.ws->done);
@@ -1096,35 +1182,49 @@ int serve_step(tpc_ctx* ctx) {
     sl.ws->busy = false;
     const DevCounters& c = *sl.ws->h_cnt;
     const bool overflow = c.n_starts > (uint32_t)sl.ws->tcap || (c.err & (kErrBins | kErrTracks));
-    int rc = overflow ? TPC_OK : check_ws_errors(ctx, *sl.ws);
-    for (auto id : sl.frames) {
-      Frame* f = find_frame(ctx, id);
-      if (!f) continue;
-      if (!overflow && rc == TPC_OK) {
-        rc = fetch_results(ctx, f);
-      } else if (overflow) {
-        // capacity overflow of the batch: track this frame alone (its own workspace) and fetch
+    if (!overflow) {
+      int rc = check_ws_errors(ctx, *sl.ws);
+      if (rc) return rc;
+      tpc_ctx::Fetching fe;
+      for (auto id : sl.frames) {
+        Frame* f = find_frame(ctx, id);
+        if (!f) continue;
+        rc = fetch_enqueue(ctx, f, sl.stream);
+        if (rc) return rc;
+        retire_inputs(ctx, f, sl.stream);
+        f->state = 4;
+        fe.frames.push_back(id);
+      }
+      if (ctx->spare_events.empty()) {
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        ctx->spare_events.push_back(ev);
+      }
+      fe.ev = ctx->spare_events.back();
+      ctx->spare_events.pop_back();
+      CK(cudaEventRecord(fe.ev, sl.stream));
+      ctx->fetching.push_back(std::move(fe));
+    } else {
+      // capacity overflow of the batch: track each frame alone (its own workspace) and fetch
+      for (auto id : sl.frames) {
+        Frame* f = find_frame(ctx, id);
+        if (!f) continue;
         release_ws_user(ctx, f);
         const float old = ctx->p.tracklet_capacity;
         ctx->p.tracklet_capacity = std::max(old, 1.25f * (float)c.n_starts / (float)std::max(1LL, f->n));
         std::vector<Frame*> one{f};
         std::shared_ptr<Workspace> ws;
-        rc = run_batch(ctx, one, ctx->stream, ws);
+        int rc = run_batch(ctx, one, ctx->stream, ws);
         ctx->p.tracklet_capacity = old;
         if (!rc) rc = wait_ws(ctx, *f->ws, 120.0);
         if (!rc) rc = check_ws_errors(ctx, *f->ws);
         if (!rc) rc = fetch_results(ctx, f);
+        if (rc) return rc;
+        retire_inputs(ctx, f, sl.stream);
+        f->state = 5;
+        f->t_done = now_s();
+        ctx->finished.push_back(id);
       }
-      if (rc) return rc;
-      release_ws_user(ctx, f);
-      if (f->d_block) { cudaFreeAsync(f->d_block, sl.stream); f->d_block = nullptr; }
-      ctx->queued_input_bytes -= std::min(ctx->queued_input_bytes, f->input_bytes);
-      f->input_bytes = 0;
-      f->host_copy.clear();
-      f->host_copy.shrink_to_fit();
-      f->state = 5;
-      f->t_done = now_s();
-      ctx->finished.push_back(id);
     }
     sl.frames.clear();
     sl.busy = false;
@@ -1143,7 +1243,10 @@ int serve_step(tpc_ctx* ctx) {
       ctx->queue.pop_front();
     }
     if (batch.empty()) break;
-    if (sl.ws && sl.ws->dp.occ != ctx->shape.occ) sl.ws.reset();  // retuned grid occupancy
+    if (sl.ws && sl.ws->dp.occ != ctx->shape.occ) {  // retuned grid occupancy
+      CK(cudaStreamSynchronize(sl.stream));            // result copies from the old workspace done
+      sl.ws.reset();
+    }
     if (!sl.ws) {
       const long long tcap = (long long)std::ceil((double)ctx->slot_clusters * ctx->p.tracklet_capacity) + 1024;
       int rc = alloc_workspace(ctx, ctx->slot_clusters, tcap, ctx->p.max_batch_frames, sl.ws);
@@ -1163,7 +1266,8 @@ int serve_step(tpc_ctx* ctx) {
     for (Frame* f : batch) sl.frames.push_back(f->id);
     sl.busy = true;
   }
-  return TPC_OK;
+  // last, so that a free slot was relaunched before the host splits fetched results
+  return finish_fetches(ctx, false);
 }
 }  // namespace
 
@@ -1173,7 +1277,7 @@ int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_
   for (;;) {
     int rc = serve_step(ctx);
     if (rc) return rc;
-    bool busy = false;
+    bool busy = !ctx->fetching.empty();
     for (auto& sl : ctx->slots) busy |= sl.busy;
     if (!ctx->finished.empty() || (!busy && ctx->queue.empty())) break;
     if ((now_s() - t0) * 1e6 >= timeout_us) break;

@@ -38,6 +38,7 @@ constexpr int kNSec = 36;
 constexpr int kNRow = 152;
 constexpr int kSegPerFrame = kNSec * kNRow;  // 5472
 constexpr int kMaxFrames = 64;               // frames per batched launch
+constexpr int kHistThreads = 1024;           // threads per block of the segment histogram
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
 
 // error bits (device error word)

@@ -206,7 +206,7 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   };
   k_reset_counters<<<1, 128, 0, s>>>(W);
   k_zero_u32<<<G, 256, 0, s>>>(W.seg_cnt, &C->nseg, W.scap, 0, 1);
-  k_seg_hist<<<4 * G, 256, 0, s>>>(W);
+  k_seg_hist<<<G, kHistThreads, 0, s>>>(W);
   k_seg_layout<<<G, 256, 0, s>>>(W, Q);
   scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
   k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
