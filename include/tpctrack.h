@@ -202,7 +202,7 @@ typedef struct {
 /* Times launch shapes on the given frames (a batch, as tpc_track_batch runs it) and keeps the
  * fastest for the context's later runs. Coordinate descent, each candidate run reps + 1 times (the
  * first discarded, median of the rest) with events between stages on the context's stream:
- * bin_occupancy in {1, 2, 4} on the whole sequence; then k2_warps in {4, 8} x k2_tma in {0, 1, 2}
+ * bin_occupancy in {0.35, 0.5, 0.7, 1, 2} on the whole sequence; then k2_warps in {4, 8} x k2_tma in {0, 1, 2}
  * on the neighbour search; then (k5_block, k5_regs), k5_order and k5_blocks_per_sm on chains +
  * tracklets; then sel_lanes in {1, 32} on the selection. Results of the frames are those of any
  * shape. Blocks until done. Errors: TPC_E_INVAL

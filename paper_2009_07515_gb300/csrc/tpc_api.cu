@@ -263,6 +263,9 @@ struct tpc_ctx {
 
 namespace {
 
+// grid occupancies the autotuner times, finest first
+constexpr float kTunerOccupancies[] = {0.35f, 0.5f, 0.7f, 1.0f, 2.0f};
+
 int fail(tpc_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -888,8 +891,11 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming);
     ctx->slots.resize(2);
     for (auto& sl : ctx->slots) cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    // slot capacity: the largest batch whose workspace and inputs fit half of the HBM budget
+    // slot capacity: the largest batch whose workspace and inputs fit half of the HBM budget at
+    // the finest grid the autotuner may choose (the grid's bin arrays grow as the occupancy falls)
     {
+      const float occ0 = ctx->shape.occ;
+      ctx->shape.occ = std::min(occ0, kTunerOccupancies[0]);
       const size_t half = (size_t)std::max<int64_t>(ctx->p.hbm_budget, 1 << 20) / ctx->slots.size();
       long long lo = 0, hi = 1LL << 31;
       while (lo < hi) {
@@ -898,6 +904,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
         if (need <= half) lo = mid; else hi = mid - 1;
       }
       ctx->slot_clusters = lo;
+      ctx->shape.occ = occ0;
     }
     if (cudaGetLastError() != cudaSuccess) { rc = fail(ctx, TPC_E_CUDA, "context setup failed"); break; }
   } while (0);
@@ -1364,7 +1371,7 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
   int rc = TPC_OK;
   do {
     std::vector<Shape> c;
-    for (float occ : {1.0f, 2.0f, 4.0f}) { Shape t = best; t.occ = occ; c.push_back(t); }
+    for (float occ : kTunerOccupancies) { Shape t = best; t.occ = occ; c.push_back(t); }
     if ((rc = descend(c, 0))) break;
     c.clear();
     for (int w : {4, 8})

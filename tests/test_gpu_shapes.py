@@ -12,6 +12,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 SHAPES = [
+    dict(bin_occupancy=0.35),
     dict(bin_occupancy=2.0),
     dict(bin_occupancy=4.0),
     dict(k2_warps=4),
