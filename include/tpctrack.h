@@ -163,8 +163,10 @@ int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame);
  * than the whole budget is refused with TPC_E_BUDGET. */
 int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ticket);
 
-/* Serving: advance the scheduler (admit queued frames into free slots and launch batches) and
- * return up to max_done finished tickets in done[]; waits at most timeout_us for at least one.
+/* Serving: advance the scheduler (retire finished batches, queueing their results' copies; admit
+ * queued frames into free slots, a batch growing only while it holds at most 2^21 clusters, and
+ * launch it) and return up to max_done finished tickets in done[] (frames whose results are on the
+ * host); waits at most timeout_us for at least one.
  * Returns the number of tickets written (>= 0) or a negative error. Finished frames are read
  * with tpc_get_tracks() and freed with tpc_release_frame(). */
 int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_us);

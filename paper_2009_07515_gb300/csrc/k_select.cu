@@ -79,12 +79,18 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
     const uint32_t nh = info & 255u;
     const uint4 st = W.starts[t];
     const unsigned long long key = tl_key(nh, st.z);
-    if (lane < 22) W.tr_f[(long long)k * 24 + lane] = W.tl_state[(long long)t * 24 + lane];
+    if (lane < 22) {
+      const float v = W.tl_state[(long long)t * 24 + lane];
+      if (lane < 5) W.tr_param[(long long)k * 5 + lane] = v;
+      else if (lane < 20) W.tr_cov[(long long)k * 15 + (lane - 5)] = v;
+      else if (lane == 20) W.tr_chi2[k] = v;
+      else W.tr_xref[k] = v;
+    }
     uint32_t off = W.tl_nkept[t];
     if (lane == 0) {
-      const uint32_t nk = W.tl_nkept[t + 1] - off;
-      const int sector = (int)((st.y % kSegPerFrame) / kNRow);
-      W.tr_i[k] = make_int4(sector, 2 * (int)nh - 5, (int)nk, (int)off);
+      W.tr_sector[k] = (int)((st.y % kSegPerFrame) / kNRow);
+      W.tr_ndf[k] = 2 * (int)nh - 5;
+      W.tr_hoff[k] = (long long)off;
     }
     // kept hits in ascending row order: ballot over each group of 32 rows
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
@@ -182,13 +188,16 @@ __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q
       const uint4 st = W.starts[t];
       key = tl_key(nh, st.z);
       const float* src = W.tl_state + (long long)t * 24;
-      float* dst = W.tr_f + (long long)k * 24;
 #pragma unroll
-      for (int i = 0; i < 22; ++i) dst[i] = src[i];
+      for (int i = 0; i < 5; ++i) W.tr_param[(long long)k * 5 + i] = src[i];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) W.tr_cov[(long long)k * 15 + i] = src[5 + i];
+      W.tr_chi2[k] = src[20];
+      W.tr_xref[k] = src[21];
       off = W.tl_nkept[t];
-      const uint32_t nk = W.tl_nkept[t + 1] - off;
-      const int sector = (int)((st.y % kSegPerFrame) / kNRow);
-      W.tr_i[k] = make_int4(sector, 2 * (int)nh - 5, (int)nk, (int)off);
+      W.tr_sector[k] = (int)((st.y % kSegPerFrame) / kNRow);
+      W.tr_ndf[k] = 2 * (int)nh - 5;
+      W.tr_hoff[k] = (long long)off;
     }
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     const RowRange rr = warp_rows(on, ref, top);

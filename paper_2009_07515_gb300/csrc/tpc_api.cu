@@ -263,6 +263,9 @@ struct tpc_ctx {
 
 namespace {
 
+// serving: queued frames join one batch only up to this many clusters (a larger frame goes alone)
+constexpr long long kServeBatchClusters = 1LL << 21;
+
 // grid occupancies the autotuner times, finest first
 constexpr float kTunerOccupancies[] = {0.35f, 0.5f, 0.7f, 1.0f, 2.0f};
 
@@ -340,8 +343,13 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.hit_w, 8 * (size_t)ws->ncap},
       {(void**)&W.tl_kept, 4 * (size_t)(ws->tcap + 1)},
       {(void**)&W.tl_nkept, 4 * (size_t)(ws->tcap + 1)},
-      {(void**)&W.tr_f, 96 * (size_t)ws->tcap},
-      {(void**)&W.tr_i, 16 * (size_t)ws->tcap},
+      {(void**)&W.tr_param, 20 * (size_t)ws->tcap},
+      {(void**)&W.tr_cov, 60 * (size_t)ws->tcap},
+      {(void**)&W.tr_chi2, 4 * (size_t)ws->tcap},
+      {(void**)&W.tr_xref, 4 * (size_t)ws->tcap},
+      {(void**)&W.tr_sector, 4 * (size_t)ws->tcap},
+      {(void**)&W.tr_ndf, 4 * (size_t)ws->tcap},
+      {(void**)&W.tr_hoff, 8 * (size_t)ws->tcap},
       {(void**)&W.tr_hits, 4 * (size_t)ws->ncap},
       {(void**)&W.scan_tmp, 4 * (size_t)ws->scan_cap},
   };
@@ -653,23 +661,22 @@ void release_results(tpc_ctx* ctx, Frame* f) {
   f->n_tracks = 0;
 }
 
-// Layout of a frame's results in its page-locked block: the device records (fit rows, track
-// info) and the hit list as copied, then the output arrays split from the fit rows.
+// Layout of a frame's results in its page-locked block: the output arrays, each copied from the
+// workspace's track arrays as one block.
 struct ResLayout {
-  size_t trf, tri, hits, sec, ndf, xref, chi2, par, cov, hoff, bytes;
+  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, bytes;
 };
 ResLayout res_layout(size_t nt, size_t nh) {
   ResLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
-  L.trf = take(nt * 96); L.tri = take(nt * 16); L.hits = take(nh * 4); L.sec = take(nt * 4);
-  L.ndf = take(nt * 4); L.xref = take(nt * 4); L.chi2 = take(nt * 4); L.par = take(nt * 20);
-  L.cov = take(nt * 60); L.hoff = take((nt + 1) * 8);
+  L.hits = take(nh * 4); L.sec = take(nt * 4); L.ndf = take(nt * 4); L.xref = take(nt * 4);
+  L.chi2 = take(nt * 4); L.par = take(nt * 20); L.cov = take(nt * 60); L.hoff = take((nt + 1) * 8);
   L.bytes = off;
   return L;
 }
 
-// The frame's tracks into one page-locked block, step 1: the DMA of the device records, queued on
+// The frame's tracks into one page-locked block, step 1: the DMA of the track arrays, queued on
 // stream s (work queued after it on s may reuse the workspace). The frame's batch has finished.
 int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   Workspace& ws = *f->ws;
@@ -688,22 +695,26 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   f->fetch_nt = nt;
   f->fetch_nh = nh;
   f->fetch_h0 = h0;
-  if (nt) {
-    CK(cudaMemcpyAsync(b + L.trf, ws.W.tr_f + (size_t)t0 * 24, nt * 96, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(b + L.tri, ws.W.tr_i + t0, nt * 16, cudaMemcpyDeviceToHost, s));
-  }
-  if (nh) CK(cudaMemcpyAsync(b + L.hits, ws.W.tr_hits + h0, nh * 4, cudaMemcpyDeviceToHost, s));
+  const Work& W = ws.W;
+  const auto d2h = [&](size_t o, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
+  };
+  CK(d2h(L.par, W.tr_param + (size_t)t0 * 5, nt * 20));
+  CK(d2h(L.cov, W.tr_cov + (size_t)t0 * 15, nt * 60));
+  CK(d2h(L.chi2, W.tr_chi2 + t0, nt * 4));
+  CK(d2h(L.xref, W.tr_xref + t0, nt * 4));
+  CK(d2h(L.sec, W.tr_sector + t0, nt * 4));
+  CK(d2h(L.ndf, W.tr_ndf + t0, nt * 4));
+  CK(d2h(L.hoff, W.tr_hoff + t0, nt * 8));
+  CK(d2h(L.hits, W.tr_hits + h0, nh * 4));
   return TPC_OK;
 }
 
-// Step 2, once the copies have completed: the fit rows split into the output arrays.
+// Step 2, once the copies have completed: the arrays' views, hit offsets made frame-relative.
 void fetch_finish(Frame* f) {
   const size_t nt = f->fetch_nt, nh = f->fetch_nh;
-  const uint32_t h0 = f->fetch_h0;
   const ResLayout L = res_layout(nt, nh);
   char* b = (char*)f->res;
-  const float* trf = (const float*)(b + L.trf);
-  const int4* tri = (const int4*)(b + L.tri);
   f->hits = (uint32_t*)(b + L.hits);
   f->sector = (int32_t*)(b + L.sec);
   f->ndf = (int32_t*)(b + L.ndf);
@@ -712,16 +723,8 @@ void fetch_finish(Frame* f) {
   f->param = (float*)(b + L.par);
   f->cov = (float*)(b + L.cov);
   f->hoff = (int64_t*)(b + L.hoff);
-  for (size_t i = 0; i < nt; ++i) {
-    const float* s = &trf[i * 24];
-    for (int j = 0; j < 5; ++j) f->param[i * 5 + j] = s[j];
-    for (int j = 0; j < 15; ++j) f->cov[i * 15 + j] = s[5 + j];
-    f->chi2[i] = s[20];
-    f->xref[i] = s[21];
-    f->sector[i] = tri[i].x;
-    f->ndf[i] = tri[i].y;
-    f->hoff[i] = (int64_t)((uint32_t)tri[i].w - h0);
-  }
+  if (f->fetch_h0)
+    for (size_t i = 0; i < nt; ++i) f->hoff[i] -= (int64_t)f->fetch_h0;
   f->hoff[nt] = (int64_t)nh;
   f->n_tracks = (int64_t)nt;
   f->state = 5;
@@ -1236,7 +1239,9 @@ int serve_step(tpc_ctx* ctx) {
     sl.frames.clear();
     sl.busy = false;
   }
-  // launch: every free slot takes the queued frames that fit it, in arrival order
+  // launch: every free slot takes queued frames in arrival order. A batch grows only while it stays
+  // small: a frame of a few million clusters fills the GPU alone, and putting two of them in one
+  // batch would serialise work that two slots run side by side (and delay the first one's result).
   for (auto& sl : ctx->slots) {
     if (sl.busy || ctx->queue.empty()) continue;
     std::vector<Frame*> batch;
@@ -1245,6 +1250,7 @@ int serve_step(tpc_ctx* ctx) {
       Frame* f = find_frame(ctx, ctx->queue.front());
       if (!f) { ctx->queue.pop_front(); continue; }
       if (n + f->n > ctx->slot_clusters) break;
+      if (!batch.empty() && n + f->n > kServeBatchClusters) break;
       n += f->n;
       batch.push_back(f);
       ctx->queue.pop_front();

@@ -141,13 +141,18 @@ struct Work {
   // tracklets
   float* tl_state;       // [tcap][24]: P[5], C[15], chi2, x_ref, -, -
   uint32_t* tl_info;     // [tcap]: nhits | ref_row << 8 | top_row << 16 | ok << 24
-  uint32_t* slab;        // [kNRow][tcap]
+  uint32_t* slab;        // [tcap][kNRow] (slab_at)
   unsigned long long* hit_w;  // [ncap]
   uint32_t* tl_kept;     // [tcap + 1] -> scanned (track index)
   uint32_t* tl_nkept;    // [tcap + 1] -> scanned (hit offset)
-  // tracks
-  float* tr_f;           // [tcap][24] track fit: P[5], C[15], chi2, x_ref
-  int4* tr_i;            // [tcap] (sector, ndf, kept hits, first output hit)
+  // tracks, in the layout of the host's output arrays (each copied to the host as one block)
+  float* tr_param;       // [tcap][5] fit state at x_ref
+  float* tr_cov;         // [tcap][15] its covariance (lower triangle)
+  float* tr_chi2;        // [tcap]
+  float* tr_xref;        // [tcap]
+  int32_t* tr_sector;    // [tcap]
+  int32_t* tr_ndf;       // [tcap]
+  long long* tr_hoff;    // [tcap] first output hit of the track in the batch's hit list
   uint32_t* tr_hits;     // [ncap] output hits (frame-local input indices)
   // scan scratch
   uint32_t* scan_tmp;    // [scan_tmp_cap]
