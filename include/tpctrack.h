@@ -68,6 +68,9 @@ typedef struct {
   double cov0[5];         /* seed covariance diagonal */
   int32_t ext_stop;       /* 1: a tracklet's outward extension ends once it accepts the start hit of
                              another tracklet, whose tracklet covers the rows beyond (1) */
+  double drift_length;    /* drift length L, cm: a cluster of a collision at time t_c has
+                             w = v_d t_c + L - |z| (250) */
+  double drift_velocity;  /* v_d, cm per microsecond (250/90) */
   /* storage / runtime */
   int32_t packed;         /* 1: store cluster coordinates as 16-bit offsets in their grid bin */
   float bin_occupancy;    /* target clusters per bin of the search grid (1); a launch-shape knob */
@@ -121,6 +124,11 @@ typedef struct {
   const int32_t* ndf;         /* [n] 2*(fitted hits) - 5 */
   const int64_t* hit_offset;  /* [n+1] */
   const uint32_t* hit_index;  /* [hit_offset[n]] */
+  const float* beam;          /* [n][5] the fit transported to the beam line x = 0 without material
+                                 (Sec. 5): y0, w0, var(w0), then for a primary from z = 0 its
+                                 collision time t0 = (w0 - L)/v_d (us) and its z at x_ref,
+                                 +-(w0 - w_ref) (+ on side A); all NaN where the transport fails
+                                 (|sin(phi)| reaches max_sin before x = 0) */
 } tpc_tracks;
 
 /* Per-kernel device time of the last tpc_track_* call on a frame or batch (CUDA events on the

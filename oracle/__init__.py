@@ -63,6 +63,8 @@ class Params(ctypes.Structure):
         ("nmin", ctypes.c_int32),
         ("cov0", ctypes.c_double * 5),
         ("ext_stop", ctypes.c_int32),
+        ("drift_length", ctypes.c_double),
+        ("drift_velocity", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -90,6 +92,7 @@ class _Result(ctypes.Structure):
         ("n_tracks", ctypes.c_int64),
         ("tr_sector", _i32p), ("tr_ndf", _i32p), ("tr_nhits", _i32p), ("tr_tracklet", _i32p),
         ("tr_xref", _f64p), ("tr_param", _f64p), ("tr_cov", _f64p), ("tr_chi2", _f64p),
+        ("tr_beam", _f64p),
         ("tr_hit_off", _i64p), ("tr_hits", _i32p),
     ]
 
@@ -117,6 +120,9 @@ def _load(precision: str):
     f = getattr(lib, pre + "asin"); f.argtypes = [ctypes.c_double]; f.restype = ctypes.c_double
     f = getattr(lib, pre + "pack"); f.argtypes = [_f64p, _f64p]; f.restype = None
     f = getattr(lib, pre + "row_x"); f.argtypes = [ctypes.c_int]; f.restype = ctypes.c_double
+    f = getattr(lib, pre + "beamline")
+    f.argtypes = [_P(Params), _f64p, _f64p, ctypes.c_double, ctypes.c_int, _f64p]
+    f.restype = None
     _libs[precision] = lib
     return lib
 
@@ -165,6 +171,7 @@ class Result:
     tr_param: np.ndarray
     tr_cov: np.ndarray
     tr_chi2: np.ndarray
+    tr_beam: np.ndarray     # [n_tracks, 5]: y0, w0, var(w0), t0 (us), z_ref (NaN: no transport)
     tr_hit_off: np.ndarray
     tr_hits: np.ndarray
 
@@ -231,6 +238,7 @@ def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = 
             tr_param=_copy(R.tr_param, 5 * ntr, np.float64, (ntr, 5)),
             tr_cov=_copy(R.tr_cov, 15 * ntr, np.float64, (ntr, 15)),
             tr_chi2=_copy(R.tr_chi2, ntr, np.float64),
+            tr_beam=_copy(R.tr_beam, 5 * ntr, np.float64, (ntr, 5)),
             tr_hit_off=tr_off, tr_hits=_copy(R.tr_hits, int(tr_off[-1]), np.int32))
     finally:
         getattr(lib, pre + "free_result")(rp)
@@ -281,6 +289,20 @@ def pack(y: float, w: float, *, precision="f32"):
     a, b = ctypes.c_double(y), ctypes.c_double(w)
     getattr(_load(precision), f"oracle_{precision}_pack")(ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
+
+
+def beamline(P, C, x_ref: float, sector: int, *, precision="f64", params: Params | None = None) -> np.ndarray:
+    """Step 7 for one fit (P, full 5x5 C at x_ref): (y0, w0, var(w0), t0, z_ref), NaN if the
+    transport to x = 0 fails."""
+    lib = _load(precision)
+    params = params or default_params(precision)
+    P = np.ascontiguousarray(np.asarray(P, dtype=np.float64).reshape(5))
+    C = np.ascontiguousarray(np.asarray(C, dtype=np.float64).reshape(25))
+    out = np.zeros(5)
+    getattr(lib, f"oracle_{precision}_beamline")(ctypes.byref(params), P.ctypes.data_as(_f64p),
+                                                 C.ctypes.data_as(_f64p), float(x_ref), int(sector),
+                                                 out.ctypes.data_as(_f64p))
+    return out
 
 
 def row_x(r: int, *, precision="f64") -> float:

@@ -21,7 +21,13 @@
  *      of another tracklet, which covers the rows beyond), then an inward refit (covariance reset)
  *      through the found hits and inward extension;
  *   6. tracklet selection: each hit goes to the tracklet with the largest (nhits, -start index) key;
- *      a tracklet becomes a track if it keeps >= nmin hits and at least half of its hits.
+ *      a tracklet becomes a track if it keeps >= nmin hits and at least half of its hits;
+ *   7. beam line (Sec. 5: track seeds are extrapolated to the beam line, and the most likely z is
+ *      computed assuming a primary from a vertex at the origin): each track's fit is transported
+ *      by the same exact helix step, without scattering, from x_ref to the plane x = 0 through the
+ *      beam axis; there y0 and the drift coordinate w0 (with its variance) are read. A primary from
+ *      z = 0 has w0 = v_d t_c + L (continuous readout, Sec. 2: w = v_d t_c + L - |z|), so its
+ *      collision time is t0 = (w0 - L) / v_d and its z at x_ref is +-(w0 - w_ref) by drift side.
  *
  * Precision: compiled twice, REAL = double (FP64 oracle) and REAL = float (FP32 oracle), with
  * -ffp-contract=off and no fast-math. Only +, -, *, /, sqrt and fused multiply-add (every sum of
@@ -77,6 +83,8 @@ typedef struct {
   int32_t nmin;       /* minimum hits of a voting tracklet and of a track */
   double cov0[5];     /* initial diagonal covariance of the seed */
   int32_t ext_stop;   /* 1: an outward extension ends at an accepted start hit of another chain */
+  double drift_length;   /* cm, L: w of a cluster at the central membrane minus v_d t_c */
+  double drift_velocity; /* cm per microsecond */
 } oracle_params;
 
 void ORACLE_SYM(default_params)(oracle_params* p) {
@@ -94,6 +102,8 @@ void ORACLE_SYM(default_params)(oracle_params* p) {
   p->nmin = 10;
   p->cov0[0] = 1.0; p->cov0[1] = 1.0; p->cov0[2] = 1.0; p->cov0[3] = 1.0; p->cov0[4] = 100.0;
   p->ext_stop = 1;
+  p->drift_length = 250.0;
+  p->drift_velocity = 250.0 / 90.0;
 }
 
 typedef struct {
@@ -112,6 +122,7 @@ typedef struct {
   real x[NROW];
   int want_margins;
   int ext_stop;
+  real drift_len, vdrift;
 } ctx_t;
 
 static void make_ctx(const oracle_params* p, ctx_t* c) {
@@ -139,6 +150,8 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
   c->nmin = p->nmin;
   for (int i = 0; i < 5; ++i) c->cov0[i] = (real)p->cov0[i];
   c->ext_stop = p->ext_stop;
+  c->drift_len = (real)p->drift_length;
+  c->vdrift = (real)p->drift_velocity;
   for (int r = 0; r < NROW; ++r) c->x[r] = (real)85 + (real)r * ((real)160 / (real)151);
   c->want_margins = 1;
 }
@@ -401,6 +414,28 @@ static int kf_seed(const ctx_t* cx, const real h[3][3], real P[5], double* m) {
   return 0;
 }
 
+/* Step 7, beam line: the track's fit (P, C at x_ref) transported to x = 0 without scattering; out =
+ * (y0, w0, var(w0), t0 = (w0 - L) / v_d, z_ref = +-(w0 - w_ref), + on side A); all NaN when the
+ * transport fails (|sin phi| reaches max_sin on the way). */
+static void beamline(const ctx_t* cx, const real P[5], real C[5][5], real x_ref, int sector, real out[5]) {
+  ctx_t c0 = *cx;
+  c0.ms_on = 0;
+  real Pb[5], Cb[5][5];
+  memcpy(Pb, P, sizeof(Pb));
+  memcpy(Cb, C, sizeof(Cb));
+  if (kf_propagate(&c0, Pb, Cb, x_ref, (real)0, NULL, NULL)) {
+    for (int i = 0; i < 5; ++i) out[i] = (real)NAN;
+    return;
+  }
+  const real w0 = Pb[1];
+  const real dz = w0 - P[1];
+  out[0] = Pb[0];
+  out[1] = w0;
+  out[2] = Cb[1][1];
+  out[3] = (w0 - cx->drift_len) / cx->vdrift;
+  out[4] = sector < NSEC / 2 ? dz : -dz;
+}
+
 /* ------------------------------------------------------------------------------------------------
  * Exported unit entry points (for the pins): one propagation, one update, one seed.
  * State/covariance exchange in double: P[5], C[25] (row-major full matrix).
@@ -441,6 +476,16 @@ int ORACLE_SYM(seed)(const oracle_params* p, const double* h9, double* P) {
   for (int i = 0; i < 5; ++i) P[i] = rc ? NAN : (double)Pr[i];
   return rc;
 }
+void ORACLE_SYM(beamline)(const oracle_params* p, const double* P, const double* C, double x_ref, int sector,
+                          double* out) {
+  ctx_t cx;
+  make_ctx(p, &cx);
+  real Pr[5], Cr[5][5], o[5];
+  for (int i = 0; i < 5; ++i) Pr[i] = (real)P[i];
+  for (int i = 0; i < 25; ++i) Cr[i / 5][i % 5] = (real)C[i];
+  beamline(&cx, Pr, Cr, (real)x_ref, sector, o);
+  for (int i = 0; i < 5; ++i) out[i] = (double)o[i];
+}
 double ORACLE_SYM(row_x)(int r) {
   ctx_t cx;
   oracle_params p;
@@ -470,6 +515,7 @@ typedef struct {
   int64_t n_tracks;
   int32_t *tr_sector, *tr_ndf, *tr_nhits, *tr_tracklet;
   double *tr_xref, *tr_param, *tr_cov, *tr_chi2;
+  double* tr_beam;                 /* [n_tracks][5] step 7: y0, w0, var(w0), t0, z_ref */
   int64_t* tr_hit_off;
   int32_t* tr_hits;                /* original indices, ascending row */
 } oracle_result;
@@ -823,6 +869,7 @@ void ORACLE_SYM(free_result)(oracle_result* R) {
   free(R->tl_chi2); free(R->tl_margin); free(R->tl_hit_off); free(R->tl_hits);
   free(R->tr_sector); free(R->tr_ndf); free(R->tr_nhits); free(R->tr_tracklet); free(R->tr_xref);
   free(R->tr_param); free(R->tr_cov); free(R->tr_chi2); free(R->tr_hit_off); free(R->tr_hits);
+  free(R->tr_beam);
   free(R);
 }
 
@@ -930,6 +977,7 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
   R->tr_nhits = malloc(ra * sizeof(int32_t)); R->tr_tracklet = malloc(ra * sizeof(int32_t));
   R->tr_xref = malloc(ra * sizeof(double)); R->tr_param = malloc(ra * 5 * sizeof(double));
   R->tr_cov = malloc(ra * 15 * sizeof(double)); R->tr_chi2 = malloc(ra * sizeof(double));
+  R->tr_beam = malloc(ra * 5 * sizeof(double));
   R->tr_hit_off = malloc((ntr + 1) * sizeof(int64_t));
   R->tr_hits = malloc((nhr > 0 ? nhr : 1) * sizeof(int32_t));
   int64_t ot = 0, otr = 0, ohl = 0, ohr = 0;
@@ -970,6 +1018,14 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
       R->tr_xref[otr] = S->t_x[t]; R->tr_chi2[otr] = S->t_chi2[t];
       for (int i = 0; i < 5; ++i) R->tr_param[otr * 5 + i] = S->t_p[t * 5 + i];
       for (int i = 0; i < 15; ++i) R->tr_cov[otr * 15 + i] = S->t_c[t * 15 + i];
+      {
+        real Pt[5], Ct[5][5], ob[5];
+        for (int i = 0; i < 5; ++i) Pt[i] = S->t_p[t * 5 + i];
+        for (int i = 0; i < 5; ++i)
+          for (int k2 = 0; k2 <= i; ++k2) Ct[i][k2] = Ct[k2][i] = S->t_c[t * 15 + i * (i + 1) / 2 + k2];
+        beamline(&cx, Pt, Ct, S->t_x[t], s, ob);
+        for (int i = 0; i < 5; ++i) R->tr_beam[otr * 5 + i] = (double)ob[i];
+      }
       for (int r = 0; r < NROW; ++r) {
         int32_t h = S->t_slots[t * NROW + r];
         if (h >= 0 && S->weight[h] == key) R->tr_hits[ohr++] = S->orig[h];

@@ -46,6 +46,8 @@ class tpc_params(ctypes.Structure):
         ("nmin", ctypes.c_int32),
         ("cov0", ctypes.c_double * 5),
         ("ext_stop", ctypes.c_int32),
+        ("drift_length", ctypes.c_double),
+        ("drift_velocity", ctypes.c_double),
         ("packed", ctypes.c_int32),
         ("bin_occupancy", ctypes.c_float),
         ("tracklet_capacity", ctypes.c_float),
@@ -85,6 +87,7 @@ class tpc_tracks(ctypes.Structure):
         ("ndf", ctypes.POINTER(ctypes.c_int32)),
         ("hit_offset", ctypes.POINTER(ctypes.c_int64)),
         ("hit_index", ctypes.POINTER(ctypes.c_uint32)),
+        ("beam", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -209,4 +212,5 @@ def tracks_to_numpy(t: tpc_tracks, copy: bool = True) -> dict:
     return dict(n_tracks=n, sector=arr(t.sector, n, np.int32), x_ref=arr(t.x_ref, n, np.float32),
                 param=arr(t.param, 5 * n, np.float32, (n, 5)), cov=arr(t.cov, 15 * n, np.float32, (n, 15)),
                 chi2=arr(t.chi2, n, np.float32), ndf=arr(t.ndf, n, np.int32), hit_offset=off,
-                hit_index=arr(t.hit_index, int(off[-1]), np.uint32))
+                hit_index=arr(t.hit_index, int(off[-1]), np.uint32),
+                beam=arr(t.beam, 5 * n, np.float32, (n, 5)))

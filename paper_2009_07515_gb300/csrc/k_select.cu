@@ -223,6 +223,39 @@ void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, con
   else k_write_tracks_warp<<<grid, 256, 0, s>>>(W, Q);
 }
 
+// K9 beam line (Sec. 5: track seeds are extrapolated to the beam line, and the most likely z is
+// computed assuming a primary from a vertex at the origin). One thread per track: its fit at
+// x_ref is transported by the exact helix step, without scattering noise, to the plane x = 0
+// through the beam axis. Out: y0, w0, var(w0) there; for a primary from z = 0 (continuous
+// readout: w = v_d t_c + L - |z|, so w0 = v_d t_c + L) the collision time t0 = (w0 - L) / v_d and
+// the track's z at x_ref, +-(w0 - w_ref) by drift side (+ on side A); NaN where the transport
+// fails.
+__global__ void __launch_bounds__(256) k_beamline(Work W, DevParams Q) {
+  const uint32_t ntr = W.cnt->n_tracks;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < ntr; k += gridDim.x * blockDim.x) {
+    float P[5], C[15];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) P[i] = W.tr_param[(long long)k * 5 + i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) C[i] = W.tr_cov[(long long)k * 15 + i];
+    const float w_ref = P[1];
+    float* o = W.tr_beam + (long long)k * 5;
+    if (!kf_propagate(Q, P, C, W.tr_xref[k], 0.0f, false)) {
+      const float nan = __int_as_float(0x7fc00000);
+#pragma unroll
+      for (int i = 0; i < 5; ++i) o[i] = nan;
+      continue;
+    }
+    const float w0 = P[1];
+    const float dz = w0 - w_ref;
+    o[0] = P[0];
+    o[1] = w0;
+    o[2] = C[lt(1, 1)];
+    o[3] = (w0 - Q.drift_len) / Q.vdrift;
+    o[4] = W.tr_sector[k] < kNSec / 2 ? dz : -dz;
+  }
+}
+
 // per frame: first tracklet, track and output hit of the frame
 __global__ void k_frame_offsets(Work W) {
   const int nf = W.batch->nf;

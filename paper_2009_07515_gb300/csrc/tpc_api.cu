@@ -49,6 +49,7 @@ void launch_votes(int lanes, int grid, cudaStream_t s, const Work& W, const DevP
 void launch_kept(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
 void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
 __global__ void k_frame_offsets(Work);
+__global__ void k_beamline(Work, DevParams);
 __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_set_ntracklets(Work);
@@ -80,6 +81,8 @@ void make_dev_params(const tpc_params& p, DevParams& d) {
   d.nmin = p.nmin;
   for (int i = 0; i < 5; ++i) d.cov0[i] = (float)p.cov0[i];
   d.ext_stop = p.ext_stop ? 1 : 0;
+  d.drift_len = (float)p.drift_length;
+  d.vdrift = (float)p.drift_velocity;
   d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
   volatile float pitch = (float)160 / (float)151;
   d.pitch = pitch;
@@ -110,7 +113,8 @@ namespace {
 
 const char* kKernelNames[] = {"reset",  "seg_hist", "seg_layout", "scan_seg",  "zero_bins", "bin_rank", "scan_bins",
                               "scatter", "neighbours", "clean",   "scan_start", "starts",   "start_order",
-                              "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "frame_off"};
+                              "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "beamline",
+                              "frame_off"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 // Launch shape: the knobs that change the speed of the sequence, never its results.
@@ -168,7 +172,7 @@ struct Frame {
   size_t res_cap = 0;
   int64_t n_tracks = 0;
   int32_t *sector = nullptr, *ndf = nullptr;
-  float *xref = nullptr, *param = nullptr, *cov = nullptr, *chi2 = nullptr;
+  float *xref = nullptr, *param = nullptr, *cov = nullptr, *chi2 = nullptr, *beam = nullptr;
   int64_t* hoff = nullptr;
   uint32_t* hits = nullptr;
   size_t fetch_nt = 0, fetch_nh = 0;  // tracks and hits copied into res (split by fetch_finish)
@@ -350,6 +354,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.tr_sector, 4 * (size_t)ws->tcap},
       {(void**)&W.tr_ndf, 4 * (size_t)ws->tcap},
       {(void**)&W.tr_hoff, 8 * (size_t)ws->tcap},
+      {(void**)&W.tr_beam, 20 * (size_t)ws->tcap},
       {(void**)&W.tr_hits, 4 * (size_t)ws->ncap},
       {(void**)&W.scan_tmp, 4 * (size_t)ws->scan_cap},
   };
@@ -513,6 +518,8 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
   mark(ki++);  // write_tracks
   ++nl; launch_write_tracks(sh.sel_lanes, 8 * G, s, W, Q);
+  mark(ki++);  // beamline
+  ++nl; k_beamline<<<2 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // frame_off
   ++nl; k_frame_offsets<<<1, 128, 0, s>>>(W);
   ctx->stage_launches[kNumKernels - 1] = nl;
@@ -664,7 +671,7 @@ void release_results(tpc_ctx* ctx, Frame* f) {
 // Layout of a frame's results in its page-locked block: the output arrays, each copied from the
 // workspace's track arrays as one block.
 struct ResLayout {
-  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, bytes;
+  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, beam, bytes;
 };
 ResLayout res_layout(size_t nt, size_t nh) {
   ResLayout L{};
@@ -672,6 +679,7 @@ ResLayout res_layout(size_t nt, size_t nh) {
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
   L.hits = take(nh * 4); L.sec = take(nt * 4); L.ndf = take(nt * 4); L.xref = take(nt * 4);
   L.chi2 = take(nt * 4); L.par = take(nt * 20); L.cov = take(nt * 60); L.hoff = take((nt + 1) * 8);
+  L.beam = take(nt * 20);
   L.bytes = off;
   return L;
 }
@@ -706,6 +714,7 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   CK(d2h(L.sec, W.tr_sector + t0, nt * 4));
   CK(d2h(L.ndf, W.tr_ndf + t0, nt * 4));
   CK(d2h(L.hoff, W.tr_hoff + t0, nt * 8));
+  CK(d2h(L.beam, W.tr_beam + (size_t)t0 * 5, nt * 20));
   CK(d2h(L.hits, W.tr_hits + h0, nh * 4));
   return TPC_OK;
 }
@@ -723,6 +732,7 @@ void fetch_finish(Frame* f) {
   f->param = (float*)(b + L.par);
   f->cov = (float*)(b + L.cov);
   f->hoff = (int64_t*)(b + L.hoff);
+  f->beam = (float*)(b + L.beam);
   if (f->fetch_h0)
     for (size_t i = 0; i < nt; ++i) f->hoff[i] -= (int64_t)f->fetch_h0;
   f->hoff[nt] = (int64_t)nh;
@@ -829,6 +839,8 @@ void tpc_default_params(tpc_params* p) {
   p->nmin = 10;
   p->cov0[0] = 1.0; p->cov0[1] = 1.0; p->cov0[2] = 1.0; p->cov0[3] = 1.0; p->cov0[4] = 100.0;
   p->ext_stop = 1;
+  p->drift_length = 250.0;
+  p->drift_velocity = 250.0 / 90.0;
   p->packed = 0;
   p->bin_occupancy = 1.0f;
   p->tracklet_capacity = 0.08f;
@@ -1029,6 +1041,7 @@ int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out) {
   out->ndf = f->ndf;
   out->hit_offset = f->hoff ? f->hoff : &zero_offset;
   out->hit_index = f->hits;
+  out->beam = f->beam;
   return TPC_OK;
 }
 

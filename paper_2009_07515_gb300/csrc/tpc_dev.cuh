@@ -61,6 +61,7 @@ struct DevParams {
   float max_sin, y_margin, tan10;
   int nmin;
   int ext_stop;
+  float drift_len, vdrift;       // L (cm) and v_d (cm/us) of the continuous-readout drift coordinate
   float cov0[5];
   float occ;                     // target clusters per grid bin
   float aspect;                  // w/y extent of a grid bin (the neighbour window's aspect)
@@ -153,6 +154,7 @@ struct Work {
   int32_t* tr_sector;    // [tcap]
   int32_t* tr_ndf;       // [tcap]
   long long* tr_hoff;    // [tcap] first output hit of the track in the batch's hit list
+  float* tr_beam;        // [tcap][5] beam-line extrapolation (K9)
   uint32_t* tr_hits;     // [ncap] output hits (frame-local input indices)
   // scan scratch
   uint32_t* scan_tmp;    // [scan_tmp_cap]
@@ -313,7 +315,8 @@ __host__ __device__ __forceinline__ long long slab_at(uint32_t t, int r) {
 __host__ __device__ constexpr int lt(int i, int k) { return i >= k ? i * (i + 1) / 2 + k : k * (k + 1) / 2 + i; }
 
 // Exact helix transport with scattering noise. Returns false if |sin(phi)| would reach max_sin.
-__device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float* C, float x0, float x1) {
+__device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float* C, float x0, float x1,
+                                             bool scatter = true) {
   const float dx = x1 - x0;
   const float k = Q.kq * P[4];
   const float s0 = P[2];
@@ -367,7 +370,7 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
     if (i >= 3) O[lt(i, 3)] = T[i][3];
     if (i >= 4) O[lt(i, 4)] = T[i][4];
   }
-  if (Q.ms_on && P[4] != 0.f) {
+  if (scatter && Q.ms_on && P[4] != 0.f) {
     const float one_tw2 = 1.0f + tw * tw;
     const float pathf = sqrtf(one_tw2) * ic1;
     const float xx0 = Q.x0_row * pathf;

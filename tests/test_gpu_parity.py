@@ -64,6 +64,11 @@ def compare_tracks(gpu, orc, *, frac=0.999, margin=1e-5):
         np.testing.assert_allclose(gpu["param"][gi], orc.tr_param[oi], rtol=1e-4, atol=1e-6)
         np.testing.assert_allclose(gpu["cov"][gi], orc.tr_cov[oi], rtol=1e-3, atol=1e-9)
         np.testing.assert_allclose(gpu["chi2"][gi], orc.tr_chi2[oi], rtol=1e-3, atol=1e-5)
+        # beam line (y0, w0, var(w0), t0, z_ref): same transport of the same fit, NaN where it fails
+        gb, ob = gpu["beam"][gi].astype(np.float64), orc.tr_beam[oi]
+        assert np.array_equal(np.isnan(gb), np.isnan(ob))
+        for c, (rtol, atol) in enumerate(((1e-4, 1e-4), (1e-4, 1e-4), (1e-3, 1e-9), (1e-4, 1e-4), (1e-4, 1e-4))):
+            np.testing.assert_allclose(gb[:, c], ob[:, c], rtol=rtol, atol=atol, equal_nan=True)
     return gi, oi
 
 
@@ -131,6 +136,11 @@ def test_error_against_fp64_oracle(tracker, n_threads):
     # FP32 rounding only: far below the fit's own uncertainty
     assert np.all(np.median(pull, axis=0) < 0.01)
     assert np.all(np.quantile(pull, 0.99, axis=0) < 0.2)
+    # beam-line collision time: FP32 error far below its own uncertainty sqrt(var(w0)) / v_d
+    ok = np.isfinite(o64.tr_beam[oi, 3]) & np.isfinite(gpu["beam"][gi, 3])
+    assert ok.mean() > 0.95
+    t_pull = np.abs(gpu["beam"][gi, 3][ok] - o64.tr_beam[oi, 3][ok]) / (np.sqrt(o64.tr_beam[oi, 2][ok]) / (250.0 / 90.0))
+    assert np.median(t_pull) < 0.01 and np.quantile(t_pull, 0.99) < 0.2
 
 
 def test_edge_cases(tracker):
