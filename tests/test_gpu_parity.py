@@ -191,7 +191,7 @@ def test_batch_alone_vs_in_the_mix(tracker):
     for h, a in zip(hs, alone):
         b = tracker.tracks(h)
         for k in a:
-            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k]), equal_nan=True), k
         tracker.release(h)
 
 
@@ -246,7 +246,7 @@ def test_tracklet_capacity_regrows(torch_cuda):
     small.close()
     b = tpc.Tracker().run(f.sector, f.row, f.y, f.w)
     for k in a:
-        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+        assert np.array_equal(np.asarray(a[k]), np.asarray(b[k]), equal_nan=True), k
 
 
 def test_device_resident_input(tracker, torch_cuda):

@@ -72,7 +72,7 @@ def assert_same(a, b):
     assert ra["n_tracks"] == rb["n_tracks"]
     for key in ("sector", "ndf", "hit_offset", "hit_index"):
         assert np.array_equal(ra[key], rb[key]), key
-    for key in ("x_ref", "param", "cov", "chi2"):
+    for key in ("x_ref", "param", "cov", "chi2", "beam"):
         assert np.array_equal(ra[key].view(np.uint32), rb[key].view(np.uint32)), key
 
 
