@@ -214,7 +214,7 @@ def test_serving_results_equal_plain(tracker, torch_cuda):
     for t, p in zip(tickets, plain):
         s = srv.tracks(t)
         for k in p:
-            assert np.array_equal(np.asarray(p[k]), np.asarray(s[k])), k
+            assert np.array_equal(np.asarray(p[k]), np.asarray(s[k]), equal_nan=True), k
         srv.release(t)
     srv.close()
 
@@ -260,4 +260,4 @@ def test_device_resident_input(tracker, torch_cuda):
     dev = tracker.tracks(h)
     tracker.release(h)
     for k in host:
-        assert np.array_equal(np.asarray(host[k]), np.asarray(dev[k])), k
+        assert np.array_equal(np.asarray(host[k]), np.asarray(dev[k]), equal_nan=True), k
