@@ -51,26 +51,34 @@ E2E_WINDOW = 3  # frames in flight in the end-to-end measurement
 
 
 def _recorded_traffic(kernel: str, workload: str, shape: dict, method_defaults: dict):
-    """DRAM bytes per launch of `kernel` from the committed ncu record (profiles/traffic.json), or None
-    when there is none for this workload and launch shape, the method defaults differ, or a source
-    the kernel is built from has changed since the capture."""
+    """(DRAM bytes per launch of `kernel`, launch shape of the capture) from the committed ncu record
+    (profiles/traffic.json), or (None, None) when there is none for this workload, the method
+    defaults differ, or a source the kernel is built from has changed since the capture. The launch
+    shape changes no source: the caller reports the capture's shape beside the figure when it
+    differs from the timed one."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
-        return None
+        return None, None
     with open(p) as fh:
         rec = json.load(fh).get(kernel)
     if not rec or rec.get("workload") != workload or rec.get("method_defaults") != method_defaults:
-        return None
-    if any(rec.get("launch_shape", {}).get(k) != v for k, v in shape.items() if k in rec.get("launch_shape", {})):
-        return None
-    if set(rec.get("launch_shape", {})) != {k for k in shape if k in rec.get("launch_shape", {})} or not shape:
-        return None
+        return None, None
     h = hashlib.sha256()
     for src in rec["sources"]:
         with open(os.path.join(ROOT, src), "rb") as fh:
             h.update(fh.read())
-    return float(rec["dram_bytes_per_launch"]) if h.hexdigest() == rec["sources_sha256"] else None
+    if h.hexdigest() != rec["sources_sha256"]:
+        return None, None
+    return float(rec["dram_bytes_per_launch"]), rec.get("launch_shape")
+
+
+def _traffic_fields(kernel: str, workload: str, shape: dict, method_defaults: dict) -> dict:
+    traffic, cap_shape = _recorded_traffic(kernel, workload, shape, method_defaults)
+    out = {"traffic": traffic}
+    if traffic is not None and cap_shape != shape:
+        out["traffic_launch_shape"] = cap_shape  # the capture's shape; the timed one is config.launch_shape
+    return out
 
 
 def _method_defaults(tpc) -> dict:
@@ -472,16 +480,16 @@ def main():
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         achieved = flops / (kernels[dominant] / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": _recorded_traffic(dominant, args.workload, tuned_params,
-                                                                       _method_defaults(tpc)),
+                    "frac": achieved / peak, **_traffic_fields(dominant, args.workload, tuned_params,
+                                                               _method_defaults(tpc)),
                     "peak_source": "derived (FP32 lanes x 2 x max SM clock)",
                     "alg_flops_per_launch": flops, "row_steps": stats["steps"]}
     else:
         alg = ALG_BYTES_PER_CLUSTER.get(dominant, 32.0) * n
         achieved = alg / (kernels[dominant] / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": _recorded_traffic(dominant, args.workload, tuned_params,
-                                                                       _method_defaults(tpc)),
+                    "frac": achieved / hbm_peak, **_traffic_fields(dominant, args.workload, tuned_params,
+                                                                   _method_defaults(tpc)),
                     "peak_source": peak_src,
                     "alg_bytes_per_launch": alg}
 
