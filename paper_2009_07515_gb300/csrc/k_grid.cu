@@ -144,6 +144,72 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const uint32_t* in,
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
 }
 
+// Single-launch exclusive scan for arrays of a small capacity: block b scans array b of up to two
+// (in[b] may alias out[b]); each thread takes 4 consecutive entries of every 4096-entry tile, and a
+// running carry joins the tiles. out[n] = total, *total = total.
+struct SmallScan {
+  const uint32_t* in[2];
+  uint32_t* out[2];
+  const uint32_t* n_dev[2];
+  long long n_host[2];
+  uint32_t* total[2];
+};
+constexpr int kSmallScanThreads = 1024;
+__global__ void __launch_bounds__(kSmallScanThreads) k_scan_small(SmallScan a) {
+  const int b = blockIdx.x;
+  const uint32_t n = scan_len(a.n_dev[b], a.n_host[b], 0);
+  const uint32_t* in = a.in[b];
+  uint32_t* out = a.out[b];
+  __shared__ uint32_t warp_sums[kSmallScanThreads / 32];
+  __shared__ uint32_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0;
+  __syncthreads();
+  constexpr int kItems = 4;
+  constexpr uint32_t kTile = kSmallScanThreads * kItems;
+  for (uint32_t base = 0; base < n; base += kTile) {
+    const uint32_t i0 = base + (uint32_t)kItems * threadIdx.x;
+    uint32_t v[kItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      v[k] = i0 + k < n ? in[i0 + k] : 0u;
+      sum += v[k];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = warp_sums[lane];
+      uint32_t z = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= o) z += y;
+      }
+      warp_sums[lane] = z - w;  // exclusive prefix of the warps' sums
+    }
+    __syncthreads();
+    uint32_t run = s_carry + warp_sums[warp] + (x - sum);
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) {
+      if (i0 + k < n) out[i0 + k] = run;
+      run += v[k];
+    }
+    __syncthreads();  // every thread has read s_carry and warp_sums
+    if (threadIdx.x == kSmallScanThreads - 1) s_carry = run;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[n] = s_carry;
+    if (a.total[b]) *a.total[b] = s_carry;
+  }
+}
+
 // ------------------------------------------------------------------------------------ K1
 // One input cluster, validated; in the 16-bit storage its coordinates are replaced by their
 // read-back values (y = rint(512 (y + 64)) / 512 - 64 clamped, w = rint(512 w) / 512), which the

@@ -26,6 +26,14 @@ namespace tpc {
 __global__ void k_scan_reduce(const uint32_t*, const uint32_t*, long long, int, uint32_t*);
 __global__ void k_scan_tiles(uint32_t*, const uint32_t*, long long, int, uint32_t*);
 __global__ void k_scan_apply(const uint32_t*, const uint32_t*, long long, int, const uint32_t*, const uint32_t*, uint32_t*);
+struct SmallScan {
+  const uint32_t* in[2];
+  uint32_t* out[2];
+  const uint32_t* n_dev[2];
+  long long n_host[2];
+  uint32_t* total[2];
+};
+__global__ void k_scan_small(SmallScan);
 __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
@@ -267,6 +275,10 @@ struct tpc_ctx {
 
 namespace {
 
+// exclusive scans of at most this many entries (by capacity: the per-segment scans of workspaces of
+// up to 11 frames) run as one single-block launch; larger ones are faster as reduce / scan / apply
+constexpr long long kSmallScanCap = 1LL << 16;
+
 // serving: queued frames join one batch only up to this many clusters (a larger frame goes alone)
 constexpr long long kServeBatchClusters = 1LL << 21;
 
@@ -455,7 +467,19 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
     if (timing) cudaEventRecord(ctx->ev[idx], s);
   };
   // scan lengths are device-side counts clamped to the buffer capacity n_cap
+  // Exclusive scans: arrays of a small capacity in one single-block launch (two of them in one
+  // launch where the sequence has a pair), larger ones by reduce / tile scan / apply.
+  auto scan2 = [&](const uint32_t* in0, uint32_t* out0, const uint32_t* n0, long long h0, uint32_t* t0,
+                   const uint32_t* in1, uint32_t* out1, const uint32_t* n1, long long h1, uint32_t* t1) {
+    SmallScan a{{in0, in1}, {out0, out1}, {n0, n1}, {h0, h1}, {t0, t1}};
+    nl += 1;
+    k_scan_small<<<in1 ? 2 : 1, 1024, 0, s>>>(a);
+  };
   auto scan = [&](const uint32_t* in, uint32_t* out, const uint32_t* n_dev, long long n_host, uint32_t* total) {
+    if (n_host <= kSmallScanCap) {
+      scan2(in, out, n_dev, n_host, total, nullptr, nullptr, nullptr, 0, nullptr);
+      return;
+    }
     nl += 3;
     k_scan_reduce<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp);
     k_scan_tiles<<<1, 1024, 0, s>>>(W.scan_tmp, n_dev, n_host, 0, total);
@@ -514,8 +538,13 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // kept
   ++nl; launch_kept(sh.sel_lanes, 8 * G, s, W, Q);
   mark(ki++);  // scan_kept
-  scan(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks);
-  scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
+  if (W.tcap <= kSmallScanCap) {
+    scan2(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks, W.tl_nkept, W.tl_nkept, &C->n_tracklets,
+          W.tcap, &C->n_track_hits);
+  } else {
+    scan(W.tl_kept, W.tl_kept, &C->n_tracklets, W.tcap, &C->n_tracks);
+    scan(W.tl_nkept, W.tl_nkept, &C->n_tracklets, W.tcap, &C->n_track_hits);
+  }
   mark(ki++);  // write_tracks
   ++nl; launch_write_tracks(sh.sel_lanes, 8 * G, s, W, Q);
   mark(ki++);  // beamline
