@@ -223,6 +223,18 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
     // ---- one row step (both directions)
     ++steps;
     bool stop = false;
+    // a known candidate (chain hit outward, outward result inward): its loads are issued before the
+    // propagation, whose arithmetic then covers their latency
+    const bool known = inward ? r >= r0 : r < r0 + mlen;
+    int khit = -1;
+    float2 kc = make_float2(0.f, 0.f);
+    if (known) {
+      const uint32_t s = W.slab[slab_at((uint32_t)t, r)];
+      if (s != kNoHit) {
+        khit = (int)s;
+        kc = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, khit);
+      }
+    }
     const bool prop = inward ? (r < top) : (r > r0);
     if (prop) {
       const float xf = row_x(Q, inward ? r + 1 : r - 1);
@@ -235,17 +247,13 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
       float2 c = make_float2(0.f, 0.f);
       bool searched = false;
       const SInv V = kf_sinv(Q, C);
-      if (inward ? r >= r0 : r < r0 + mlen) {
-        // a chain hit (outward; written by k_chains) or the outward result (inward)
-        const uint32_t s = W.slab[slab_at((uint32_t)t, r)];
-        hit = s == kNoHit ? -1 : (int)s;
+      if (known) {
+        hit = khit;
+        c = kc;
+        if (hit >= 0) chi = kf_chi2(V, P, c.x, c.y);
       } else {
         searched = true;
         hit = search_row<kPacked>(W, Q, gb + r, P, C, V, chi, c);
-      }
-      if (hit >= 0 && !searched) {
-        c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, hit);
-        chi = kf_chi2(V, P, c.x, c.y);
       }
       const bool acc = hit >= 0 && chi <= Q.chi2_max;
       if (acc) {
