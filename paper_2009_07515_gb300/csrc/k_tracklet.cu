@@ -132,11 +132,12 @@ __device__ __forceinline__ void reset_cov(const DevParams& Q, float* C) {
 
 // smallest-chi2 hit of segment g inside the window around the predicted (y, w); -1 if none
 template <bool kPacked>
-__device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, int g, const float* P, const float* C,
-                                          const SInv& V, float& chi_out, float2& hit_out) {
+__device__ __forceinline__ int search_row(const Work& W, const DevParams& Q, const int4 sdim, const float4 sgeo,
+                                          uint32_t sbb, const float* P, const float* C, const SInv& V, float& chi_out,
+                                          float2& hit_out) {
   const float wy = Q.win_nsig * sqrtf(C[lt(0, 0)]) + Q.win_add;
   const float ww = Q.win_nsig * sqrtf(C[lt(1, 1)]) + Q.win_add;
-  const GridWin q = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g, P[0], P[1], wy, ww);
+  const GridWin q = grid_window_from(sdim, sgeo, sbb, P[0], P[1], wy, ww);
   int best = -1;
   float bchi = __int_as_float(0x7f800000);
   float2 bc = make_float2(0.f, 0.f);
@@ -223,17 +224,25 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
     // ---- one row step (both directions)
     ++steps;
     bool stop = false;
-    // a known candidate (chain hit outward, outward result inward): its loads are issued before the
-    // propagation, whose arithmetic then covers their latency
+    // loads whose addresses are known before the propagation are issued first, so its arithmetic
+    // covers their latency: a known candidate (chain hit outward, outward result inward), or the
+    // grid geometry of the row to search
     const bool known = inward ? r >= r0 : r < r0 + mlen;
     int khit = -1;
     float2 kc = make_float2(0.f, 0.f);
+    int4 sdim = make_int4(0, 0, 0, 0);
+    float4 sgeo = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t sbb = 0;
     if (known) {
       const uint32_t s = W.slab[slab_at((uint32_t)t, r)];
       if (s != kNoHit) {
         khit = (int)s;
         kc = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, khit);
       }
+    } else {
+      sdim = W.seg_dim[gb + r];
+      sgeo = W.seg_geo[gb + r];
+      sbb = W.seg_bb[gb + r];
     }
     const bool prop = inward ? (r < top) : (r > r0);
     if (prop) {
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         if (hit >= 0) chi = kf_chi2(V, P, c.x, c.y);
       } else {
         searched = true;
-        hit = search_row<kPacked>(W, Q, gb + r, P, C, V, chi, c);
+        hit = search_row<kPacked>(W, Q, sdim, sgeo, sbb, P, C, V, chi, c);
       }
       const bool acc = hit >= 0 && chi <= Q.chi2_max;
       if (acc) {

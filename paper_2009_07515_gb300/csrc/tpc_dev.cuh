@@ -186,12 +186,10 @@ struct GridWin {
   uint32_t bb;
 };
 __device__ __forceinline__ float win_pad(float c, float W);
-__device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const int4* seg_dim, const float4* seg_geo,
-                                               int g, float yc, float wc, float Wy, float Ww) {
+__device__ __forceinline__ GridWin grid_window_from(const int4 dim, const float4 geo, uint32_t bb, float yc, float wc,
+                                                    float Wy, float Ww) {
   GridWin q;
-  const int4 dim = seg_dim[g];
-  const float4 geo = seg_geo[g];
-  q.bb = seg_bb[g];
+  q.bb = bb;
   q.ny = dim.y;
   q.cw0 = dim.z;
   q.cshift = dim.w;
@@ -201,6 +199,10 @@ __device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const int
   q.iy0 = bin_of((yc - Wy) - py, geo.z, geo.w, (int)dim.y);
   q.iy1 = bin_of((yc + Wy) + py, geo.z, geo.w, (int)dim.y);
   return q;
+}
+__device__ __forceinline__ GridWin grid_window(const uint32_t* seg_bb, const int4* seg_dim, const float4* seg_geo,
+                                               int g, float yc, float wc, float Wy, float Ww) {
+  return grid_window_from(seg_dim[g], seg_geo[g], seg_bb[g], yc, wc, Wy, Ww);
 }
 
 // conservative widening of a window for the bin lookup (rounding of w +- W)
