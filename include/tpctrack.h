@@ -71,6 +71,9 @@ typedef struct {
   double drift_length;    /* drift length L, cm: a cluster of a collision at time t_c has
                              w = v_d t_c + L - |z| (250) */
   double drift_velocity;  /* v_d, cm per microsecond (250/90) */
+  double keep_vy, keep_vw;/* compression, strategy B (Sec. 3): clusters within +-keep_vy in y and
+                             +-keep_vw in w of a good track's predicted position are kept (1, 1 cm) */
+  double keep_qpt_max;    /* a good track has |q/pT| <= keep_qpt_max, i.e. pT >= 50 MeV/c (20) */
   /* storage / runtime */
   int32_t packed;         /* 1: store cluster coordinates as 16-bit offsets in their grid bin */
   float bin_occupancy;    /* target clusters per bin of the search grid (1); a launch-shape knob */
@@ -78,6 +81,8 @@ typedef struct {
   int64_t hbm_budget;     /* serving admission budget in bytes (80 GB) */
   int32_t max_batch_frames; /* frames per batched launch (16) */
   int32_t use_graphs;     /* 1: replay the kernel sequence as a CUDA graph */
+  int32_t compress;       /* 1: also compute the compression inputs (track-model residuals, strategy-B
+                             keep mask; tpc_tracks.residual, tpc_get_keep_mask) (0) */
   /* launch shapes: no result depends on them; tpc_autotune() picks them by timing */
   int32_t k2_warps;       /* neighbour search: warps per block, each on 32 hits of one row at a
                              time (4 or 8) */
@@ -129,6 +134,12 @@ typedef struct {
                                  collision time t0 = (w0 - L)/v_d (us) and its z at x_ref,
                                  +-(w0 - w_ref) (+ on side A); all NaN where the transport fails
                                  (|sin(phi)| reaches max_sin before x = 0) */
+  /* compression inputs (Sec. 3), NULL unless tpc_params.compress: each track's fit is transported
+   * row by row (state only, no scattering) from x_ref; hit i of the track is stored as
+   * q(hit) - q(prediction) at its row, q(v) = rint(512 v) in units of 2^-9 cm, for i < n_pred, and
+   * as q(hit) beyond (the transport failed there). A decoder with the same arithmetic restores q(hit). */
+  const int32_t* residual;    /* [hit_offset[n]][2] (y, w) */
+  const int32_t* n_pred;      /* [n] */
 } tpc_tracks;
 
 /* Per-kernel device time of the last tpc_track_* call on a frame or batch (CUDA events on the
@@ -184,6 +195,13 @@ int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_
  * what: 0 = raw up link, 1 = raw down link, 2 = cleaned up link, 3 = cleaned down link
  * (each the input index of the linked cluster or -1). */
 int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n);
+
+/* Compression, strategy B (Sec. 3: every hit not in the vicinity of a good track is removed): copy
+ * the keep mask of a tracked frame into host memory (caller-owned, n = number of clusters), indexed
+ * by the caller's cluster order: 1 = kept (a hit of a good track, or within +-(keep_vy, keep_vw) of a
+ * good track's predicted position at its row), 0 = removed. Needs tpc_params.compress = 1 (else
+ * TPC_E_STATE). */
+int tpc_get_keep_mask(tpc_ctx* ctx, tpc_frame_t frame, uint8_t* host_out, int64_t n);
 
 /* Number of start hits and of tracks of a tracked frame. */
 int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n_tracks);

@@ -65,6 +65,8 @@ class Params(ctypes.Structure):
         ("ext_stop", ctypes.c_int32),
         ("drift_length", ctypes.c_double),
         ("drift_velocity", ctypes.c_double),
+        ("keep_vy", ctypes.c_double), ("keep_vw", ctypes.c_double),
+        ("keep_qpt_max", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -93,6 +95,7 @@ class _Result(ctypes.Structure):
         ("tr_sector", _i32p), ("tr_ndf", _i32p), ("tr_nhits", _i32p), ("tr_tracklet", _i32p),
         ("tr_xref", _f64p), ("tr_param", _f64p), ("tr_cov", _f64p), ("tr_chi2", _f64p),
         ("tr_beam", _f64p),
+        ("tr_res", _i32p), ("tr_npred", _i32p), ("keep", _P(ctypes.c_uint8)),
         ("tr_hit_off", _i64p), ("tr_hits", _i32p),
     ]
 
@@ -172,6 +175,9 @@ class Result:
     tr_cov: np.ndarray
     tr_chi2: np.ndarray
     tr_beam: np.ndarray     # [n_tracks, 5]: y0, w0, var(w0), t0 (us), z_ref (NaN: no transport)
+    tr_res: np.ndarray      # [track hits, 2] int32: q(hit) - q(prediction), or q(hit) past n_pred
+    tr_npred: np.ndarray    # [n_tracks] hits stored as residuals
+    keep: np.ndarray        # [n_clusters] uint8: 1 = kept by strategy B
     tr_hit_off: np.ndarray
     tr_hits: np.ndarray
 
@@ -239,6 +245,9 @@ def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = 
             tr_cov=_copy(R.tr_cov, 15 * ntr, np.float64, (ntr, 15)),
             tr_chi2=_copy(R.tr_chi2, ntr, np.float64),
             tr_beam=_copy(R.tr_beam, 5 * ntr, np.float64, (ntr, 5)),
+            tr_res=_copy(R.tr_res, 2 * int(tr_off[-1]), np.int32, (int(tr_off[-1]), 2)),
+            tr_npred=_copy(R.tr_npred, ntr, np.int32),
+            keep=_copy(R.keep, n, np.uint8),
             tr_hit_off=tr_off, tr_hits=_copy(R.tr_hits, int(tr_off[-1]), np.int32))
     finally:
         getattr(lib, pre + "free_result")(rp)

@@ -27,7 +27,15 @@
  *      by the same exact helix step, without scattering, from x_ref to the plane x = 0 through the
  *      beam axis; there y0 and the drift coordinate w0 (with its variance) are read. A primary from
  *      z = 0 has w0 = v_d t_c + L (continuous readout, Sec. 2: w = v_d t_c + L - |z|), so its
- *      collision time is t0 = (w0 - L) / v_d and its z at x_ref is +-(w0 - w_ref) by drift side.
+ *      collision time is t0 = (w0 - L) / v_d and its z at x_ref is +-(w0 - w_ref) by drift side;
+ *   8. compression inputs (Sec. 3: hits of good tracks are stored as residuals to the extrapolated
+ *      track position; strategy B removes every hit not in the vicinity of a good track): each
+ *      track's fit is transported row by row (state only, no scattering) from x_ref to its last
+ *      hit's row. At every row a good track (|q/pT| <= keep_qpt_max) protects the row's clusters
+ *      within +-(keep_vy, keep_vw) of its predicted (y, w); at a row with one of its hits the hit
+ *      is stored as q(hit) - q(prediction), q(v) = rint(512 v) (the 2^-9 cm quantum of the 16-bit
+ *      storage). A decoder with the same arithmetic restores q(hit) exactly. If the transport
+ *      fails, the remaining hits are stored as q(hit) (n_pred counts the predicted ones).
  *
  * Precision: compiled twice, REAL = double (FP64 oracle) and REAL = float (FP32 oracle), with
  * -ffp-contract=off and no fast-math. Only +, -, *, /, sqrt and fused multiply-add (every sum of
@@ -85,6 +93,8 @@ typedef struct {
   int32_t ext_stop;   /* 1: an outward extension ends at an accepted start hit of another chain */
   double drift_length;   /* cm, L: w of a cluster at the central membrane minus v_d t_c */
   double drift_velocity; /* cm per microsecond */
+  double keep_vy, keep_vw; /* strategy-B vicinity of a good track's prediction (cm) */
+  double keep_qpt_max;     /* good track: |q/pT| <= this (c/GeV) */
 } oracle_params;
 
 void ORACLE_SYM(default_params)(oracle_params* p) {
@@ -104,6 +114,9 @@ void ORACLE_SYM(default_params)(oracle_params* p) {
   p->ext_stop = 1;
   p->drift_length = 250.0;
   p->drift_velocity = 250.0 / 90.0;
+  p->keep_vy = 1.0;
+  p->keep_vw = 1.0;
+  p->keep_qpt_max = 20.0;
 }
 
 typedef struct {
@@ -123,6 +136,7 @@ typedef struct {
   int want_margins;
   int ext_stop;
   real drift_len, vdrift;
+  real keep_vy, keep_vw, keep_qpt_max;
 } ctx_t;
 
 static void make_ctx(const oracle_params* p, ctx_t* c) {
@@ -152,6 +166,9 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
   c->ext_stop = p->ext_stop;
   c->drift_len = (real)p->drift_length;
   c->vdrift = (real)p->drift_velocity;
+  c->keep_vy = (real)p->keep_vy;
+  c->keep_vw = (real)p->keep_vw;
+  c->keep_qpt_max = (real)p->keep_qpt_max;
   for (int r = 0; r < NROW; ++r) c->x[r] = (real)85 + (real)r * ((real)160 / (real)151);
   c->want_margins = 1;
 }
@@ -323,6 +340,28 @@ static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real 
     O[3][3] = O[3][3] + th2 * one_tw2 * one_tw2;
   }
   memcpy(C, O, sizeof(O));
+  return 0;
+}
+
+/* The state part of kf_propagate alone (the same operations): step 8's predictions. */
+static int propagate_state(const ctx_t* cx, real P[5], real x0, real x1) {
+  const real dx = x1 - x0;
+  const real k = cx->kq * P[4];
+  const real s0 = P[2];
+  const real s1 = s0 + k * dx;
+  if (!(absr(s1) < cx->max_sin)) return 1;
+  const real c0 = SQRT((real)1 - s0 * s0);
+  const real c1 = SQRT((real)1 - s1 * s1);
+  const real N = s0 + s1, D = c0 + c1;
+  const real iD = (real)1 / D;
+  const real dy = dx * (N * iD);
+  const real l = SQRT(dx * dx + dy * dy);
+  const real t = l * k * (real)0.5;
+  real a = l * arc_ratio(t);
+  if (dx < 0) a = -a;
+  P[0] = P[0] + dy;
+  P[1] = P[1] + P[3] * a;
+  P[2] = s1;
   return 0;
 }
 
@@ -516,6 +555,9 @@ typedef struct {
   int32_t *tr_sector, *tr_ndf, *tr_nhits, *tr_tracklet;
   double *tr_xref, *tr_param, *tr_cov, *tr_chi2;
   double* tr_beam;                 /* [n_tracks][5] step 7: y0, w0, var(w0), t0, z_ref */
+  int32_t* tr_res;                 /* [total track hits][2] step 8: residuals (or absolute) */
+  int32_t* tr_npred;               /* [n_tracks] step 8: hits stored as residuals */
+  uint8_t* keep;                   /* [n_clusters] step 8: strategy-B protection */
   int64_t* tr_hit_off;
   int32_t* tr_hits;                /* original indices, ascending row */
 } oracle_result;
@@ -568,6 +610,48 @@ static int64_t row_lower_bound(const sector_t* S, int r, real v) {
     if (S->w[mid] < v) lo = mid + 1; else hi = mid;
   }
   return lo;
+}
+
+/* Step 8 for track t (tracklet key `key`): residuals res[2 i], res[2 i + 1] of its i-th hit (ascending
+ * rows), the number of predicted hits, and the protection of the clusters near a good track. */
+static int32_t quant(real v) { return (int32_t)RINT(v * (real)512); }
+static void compress_track(const ctx_t* cx, const sector_t* S, int64_t t, uint64_t key, int32_t* res,
+                           int32_t* npred, uint8_t* keep) {
+  real P[5];
+  for (int i = 0; i < 5; ++i) P[i] = S->t_p[t * 5 + i];
+  const int r0 = S->t_rref[t];
+  int last = -1;
+  for (int r = NROW - 1; r >= 0 && last < 0; --r) {
+    const int32_t h = S->t_slots[t * NROW + r];
+    if (h >= 0 && S->weight[h] == key) last = r;
+  }
+  const int good = absr(P[4]) <= cx->keep_qpt_max;
+  int ok = 1, n = 0, np = 0;
+  for (int r = r0; r <= last; ++r) {
+    if (ok && r > r0 && propagate_state(cx, P, cx->x[r - 1], cx->x[r])) ok = 0;
+    if (ok && good) {
+      /* the row's clusters within the vicinity (exact test; the w range searched is widened by
+       * the rounding of w +- vw) */
+      const real pad = absr(P[1]) * (real)1e-6 + cx->keep_vw * (real)1e-6 + (real)1e-6;
+      const real lo = (P[1] - cx->keep_vw) - pad, hi = (P[1] + cx->keep_vw) + pad;
+      for (int64_t i = row_lower_bound(S, r, lo); i < S->row_start[r + 1] && S->w[i] <= hi; ++i)
+        if (absr(S->w[i] - P[1]) <= cx->keep_vw && absr(S->y[i] - P[0]) <= cx->keep_vy) keep[i] = 1;
+    }
+    const int32_t h = S->t_slots[t * NROW + r];
+    if (h >= 0 && S->weight[h] == key) {
+      if (good) keep[h] = 1;
+      if (ok) {
+        res[2 * n] = quant(S->y[h]) - quant(P[0]);
+        res[2 * n + 1] = quant(S->w[h]) - quant(P[1]);
+        ++np;
+      } else {
+        res[2 * n] = quant(S->y[h]);
+        res[2 * n + 1] = quant(S->w[h]);
+      }
+      ++n;
+    }
+  }
+  *npred = np;
 }
 
 /* candidates in row rr of hit (yi, wi) within |dy| <= wy, |dw| <= ww: index range to scan */
@@ -869,7 +953,7 @@ void ORACLE_SYM(free_result)(oracle_result* R) {
   free(R->tl_chi2); free(R->tl_margin); free(R->tl_hit_off); free(R->tl_hits);
   free(R->tr_sector); free(R->tr_ndf); free(R->tr_nhits); free(R->tr_tracklet); free(R->tr_xref);
   free(R->tr_param); free(R->tr_cov); free(R->tr_chi2); free(R->tr_hit_off); free(R->tr_hits);
-  free(R->tr_beam);
+  free(R->tr_beam); free(R->tr_res); free(R->tr_npred); free(R->keep);
   free(R);
 }
 
@@ -978,6 +1062,9 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
   R->tr_xref = malloc(ra * sizeof(double)); R->tr_param = malloc(ra * 5 * sizeof(double));
   R->tr_cov = malloc(ra * 15 * sizeof(double)); R->tr_chi2 = malloc(ra * sizeof(double));
   R->tr_beam = malloc(ra * 5 * sizeof(double));
+  R->tr_npred = malloc(ra * sizeof(int32_t));
+  R->tr_res = malloc((nhr > 0 ? nhr : 1) * 2 * sizeof(int32_t));
+  R->keep = calloc(na, 1);
   R->tr_hit_off = malloc((ntr + 1) * sizeof(int64_t));
   R->tr_hits = malloc((nhr > 0 ? nhr : 1) * sizeof(int32_t));
   int64_t ot = 0, otr = 0, ohl = 0, ohr = 0;
@@ -1010,6 +1097,7 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
     }
     int32_t* ki = malloc((S->ntr > 0 ? S->ntr : 1) * sizeof(int32_t));
     for (int64_t k = 0; k < S->ntr; ++k) ki[k] = (int32_t)k;
+    uint8_t* keep_local = calloc(S->n > 0 ? S->n : 1, 1);
     for (int64_t j = 0; j < S->ntr; ++j) {
       int64_t k = ki[j], t = S->tr_t[k];
       const uint64_t key = tracklet_key(S, t);
@@ -1026,6 +1114,7 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
         beamline(&cx, Pt, Ct, S->t_x[t], s, ob);
         for (int i = 0; i < 5; ++i) R->tr_beam[otr * 5 + i] = (double)ob[i];
       }
+      compress_track(&cx, S, t, key, R->tr_res + 2 * ohr, &R->tr_npred[otr], keep_local);
       for (int r = 0; r < NROW; ++r) {
         int32_t h = S->t_slots[t * NROW + r];
         if (h >= 0 && S->weight[h] == key) R->tr_hits[ohr++] = S->orig[h];
@@ -1033,6 +1122,8 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
       R->tr_hit_off[otr + 1] = ohr;
       ++otr;
     }
+    for (int64_t i = 0; i < S->n; ++i) R->keep[S->orig[i]] = keep_local[i];
+    free(keep_local);
     free(ti); free(tpos); free(ki);
     free_sector(S);
   }

@@ -118,6 +118,12 @@ class Tracker:
         self._check(self.lib.tpc_get_links(self.ctx, ctypes.c_uint64(frame), what, out.ctypes.data, n))
         return out
 
+    def keep_mask(self, frame: int, n: int) -> np.ndarray:
+        """Strategy-B keep mask of a tracked frame (1 = kept), in the caller's cluster order."""
+        out = np.empty(n, np.uint8)
+        self._check(self.lib.tpc_get_keep_mask(self.ctx, ctypes.c_uint64(frame), out.ctypes.data, n))
+        return out
+
     def counts(self, frame: int):
         a, b = ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.tpc_get_counts(self.ctx, ctypes.c_uint64(frame), ctypes.byref(a), ctypes.byref(b)))

@@ -48,12 +48,16 @@ class tpc_params(ctypes.Structure):
         ("ext_stop", ctypes.c_int32),
         ("drift_length", ctypes.c_double),
         ("drift_velocity", ctypes.c_double),
+        ("keep_vy", ctypes.c_double),
+        ("keep_vw", ctypes.c_double),
+        ("keep_qpt_max", ctypes.c_double),
         ("packed", ctypes.c_int32),
         ("bin_occupancy", ctypes.c_float),
         ("tracklet_capacity", ctypes.c_float),
         ("hbm_budget", ctypes.c_int64),
         ("max_batch_frames", ctypes.c_int32),
         ("use_graphs", ctypes.c_int32),
+        ("compress", ctypes.c_int32),
         ("k2_warps", ctypes.c_int32),
         ("k2_tma", ctypes.c_int32),
         ("k5_block", ctypes.c_int32),
@@ -88,6 +92,8 @@ class tpc_tracks(ctypes.Structure):
         ("hit_offset", ctypes.POINTER(ctypes.c_int64)),
         ("hit_index", ctypes.POINTER(ctypes.c_uint32)),
         ("beam", ctypes.POINTER(ctypes.c_float)),
+        ("residual", ctypes.POINTER(ctypes.c_int32)),
+        ("n_pred", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -138,6 +144,7 @@ SIGNATURES = [
     ("tpc_submit_frame", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_clusters), ctypes.POINTER(_frame)]),
     ("tpc_poll", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_int32]),
     ("tpc_get_links", ctypes.c_int, [_ctx_p, _frame, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64]),
+    ("tpc_get_keep_mask", ctypes.c_int, [_ctx_p, _frame, ctypes.c_void_p, ctypes.c_int64]),
     ("tpc_get_counts", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     ("tpc_get_stats", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32]),
     ("tpc_autotune", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_int32,
@@ -213,4 +220,7 @@ def tracks_to_numpy(t: tpc_tracks, copy: bool = True) -> dict:
                 param=arr(t.param, 5 * n, np.float32, (n, 5)), cov=arr(t.cov, 15 * n, np.float32, (n, 15)),
                 chi2=arr(t.chi2, n, np.float32), ndf=arr(t.ndf, n, np.int32), hit_offset=off,
                 hit_index=arr(t.hit_index, int(off[-1]), np.uint32),
-                beam=arr(t.beam, 5 * n, np.float32, (n, 5)))
+                beam=arr(t.beam, 5 * n, np.float32, (n, 5)),
+                **({} if not t.residual else
+                   dict(residual=arr(t.residual, 2 * int(off[-1]), np.int32, (int(off[-1]), 2)),
+                        n_pred=arr(t.n_pred, n, np.int32))))

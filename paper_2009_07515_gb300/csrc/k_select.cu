@@ -223,6 +223,72 @@ void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, con
   else k_write_tracks_warp<<<grid, 256, 0, s>>>(W, Q);
 }
 
+// K10 compression inputs (Sec. 3: hits of good tracks are stored as residuals to the extrapolated
+// track position; strategy B removes every hit not in the vicinity of a good track). One thread
+// per track: its fit is transported row by row (state only, no scattering) from x_ref to its last
+// hit's row. At every row a good track (|q/pT| <= keep_qpt_max) protects the row's clusters within
+// +-(keep_vy, keep_vw) of its prediction; each of its hits is stored as q(hit) - q(prediction),
+// q(v) = rint(512 v), or as q(hit) once the transport has failed (n_pred counts the predicted).
+__device__ __forceinline__ int32_t quant512(float v) { return (int32_t)rintf(v * 512.0f); }
+template <bool kPacked>
+__device__ __forceinline__ void mark_vicinity(const Work& W, const DevParams& Q, int g, float yp, float wp,
+                                              long long off) {
+  const GridWin q = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g, yp, wp, Q.keep_vy, Q.keep_vw);
+  for (int cw = q.iw0; cw <= q.iw1; ++cw) {
+    const uint32_t col = q.bb + (uint32_t)(cw * q.ny);
+    const int base = col_base(q.cw0, q.cshift, cw);
+    const int p1 = (int)W.bin_start[col + q.iy1 + 1];
+    for (int p = (int)W.bin_start[col + q.iy0]; p < p1; ++p) {
+      const float2 c = hit_in_col<kPacked>(W.hyw, W.hq, p, base);
+      if (fabsf(c.y - wp) <= Q.keep_vw && fabsf(c.x - yp) <= Q.keep_vy) W.keep[off + W.horig[p]] = 1;
+    }
+  }
+}
+template <bool kPacked>
+__global__ void __launch_bounds__(128) k_compress(Work W, DevParams Q) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+    const uint32_t k = W.tl_kept[t];
+    if (W.tl_kept[t + 1] == k) continue;
+    const uint32_t info = W.tl_info[t];
+    const uint4 st = W.starts[t];
+    const unsigned long long key = tl_key(info & 255u, st.z);
+    const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
+    const int g0 = (int)st.y, gb = g0 - (g0 % kSegPerFrame) % kNRow;
+    const long long off = W.batch->f[g0 / kSegPerFrame].off;
+    int last = -1;
+    for (int r = top; r >= ref && last < 0; --r) {
+      const uint32_t h = W.slab[slab_at(t, r)];
+      if (h != kNoHit && W.hit_w[h] == key) last = r;
+    }
+    float P[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) P[i] = W.tl_state[(long long)t * 24 + i];
+    const bool good = fabsf(P[4]) <= Q.keep_qpt_max;
+    bool ok = true;
+    int n = 0, np = 0;
+    int32_t* res = W.tr_res + 2 * (long long)W.tl_nkept[t];
+    for (int r = ref; r <= last; ++r) {
+      if (ok && r > ref && !kf_propagate_state(Q, P, row_x(Q, r - 1), row_x(Q, r))) ok = false;
+      if (ok && good) mark_vicinity<kPacked>(W, Q, gb + r, P[0], P[1], off);
+      const uint32_t h = W.slab[slab_at(t, r)];
+      if (h != kNoHit && W.hit_w[h] == key) {
+        if (good) W.keep[off + W.horig[h]] = 1;
+        const float2 c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, (int)h);
+        res[2 * n] = ok ? quant512(c.x) - quant512(P[0]) : quant512(c.x);
+        res[2 * n + 1] = ok ? quant512(c.y) - quant512(P[1]) : quant512(c.y);
+        np += ok ? 1 : 0;
+        ++n;
+      }
+    }
+    W.tr_npred[k] = np;
+  }
+}
+void launch_compress(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q) {
+  if (packed) k_compress<true><<<grid, 128, 0, s>>>(W, Q);
+  else k_compress<false><<<grid, 128, 0, s>>>(W, Q);
+}
+
 // K9 beam line (Sec. 5: track seeds are extrapolated to the beam line, and the most likely z is
 // computed assuming a primary from a vertex at the origin). One thread per track: its fit at
 // x_ref is transported by the exact helix step, without scattering noise, to the plane x = 0

@@ -24,11 +24,6 @@
 
 namespace tpc {
 
-// row radius x_r = 85 + r * (160/151) cm, evaluated with the same two rounded float operations as
-// the host table (a per-lane row index into a parameter table would serialise the warp's loads)
-__device__ __forceinline__ float row_x(const DevParams& Q, int r) {
-  return __fadd_rn(85.0f, __fmul_rn((float)r, Q.pitch));
-}
 
 // Processing-order key of a tracklet (a counting sort over kNRow + 1 buckets): order 1 takes the
 // longest chains first, order 2 the innermost start rows first, order 3 the outermost start rows

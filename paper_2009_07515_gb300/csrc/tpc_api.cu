@@ -56,6 +56,7 @@ void launch_wait_probe(uint32_t* status, unsigned long long limit_ns, cudaStream
 void launch_votes(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
 void launch_kept(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
 void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
+void launch_compress(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q);
 __global__ void k_frame_offsets(Work);
 __global__ void k_beamline(Work, DevParams);
 __global__ void k_reset_counters(Work);
@@ -91,6 +92,9 @@ void make_dev_params(const tpc_params& p, DevParams& d) {
   d.ext_stop = p.ext_stop ? 1 : 0;
   d.drift_len = (float)p.drift_length;
   d.vdrift = (float)p.drift_velocity;
+  d.keep_vy = (float)p.keep_vy;
+  d.keep_vw = (float)p.keep_vw;
+  d.keep_qpt_max = (float)p.keep_qpt_max;
   d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
   volatile float pitch = (float)160 / (float)151;
   d.pitch = pitch;
@@ -121,7 +125,7 @@ namespace {
 
 const char* kKernelNames[] = {"reset",  "seg_hist", "seg_layout", "scan_seg",  "zero_bins", "bin_rank", "scan_bins",
                               "scatter", "neighbours", "clean",   "scan_start", "starts",   "start_order",
-                              "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "beamline",
+                              "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "compress", "beamline",
                               "frame_off"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
@@ -181,6 +185,8 @@ struct Frame {
   int64_t n_tracks = 0;
   int32_t *sector = nullptr, *ndf = nullptr;
   float *xref = nullptr, *param = nullptr, *cov = nullptr, *chi2 = nullptr, *beam = nullptr;
+  int32_t *residual = nullptr, *n_pred = nullptr;
+  bool fetch_compress = false;
   int64_t* hoff = nullptr;
   uint32_t* hits = nullptr;
   size_t fetch_nt = 0, fetch_nh = 0;  // tracks and hits copied into res (split by fetch_finish)
@@ -324,6 +330,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   // a segment grid has at most 4 ceil(n / occ) + 260 bins, 513 in the 16-bit storage (k_seg_layout)
   ws->bcap = 4 * ((long long)std::ceil((double)ws->ncap / occ) + ws->scap) + (ctx->p.packed ? 520 : 264) * ws->scap + 16;
   long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1});
+  const bool compress = ctx->p.compress != 0;  // compression inputs (K10)
   ws->scan_cap = (maxscan + 2047) / 2048 + 16;
   struct Item { void** ptr; size_t bytes; };
   Work& W = ws->W;
@@ -367,6 +374,9 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.tr_ndf, 4 * (size_t)ws->tcap},
       {(void**)&W.tr_hoff, 8 * (size_t)ws->tcap},
       {(void**)&W.tr_beam, 20 * (size_t)ws->tcap},
+      {(void**)&W.tr_res, compress ? 8 * (size_t)ws->ncap : 0},
+      {(void**)&W.tr_npred, compress ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.keep, compress ? (size_t)(ws->ncap + 3) / 4 * 4 : 0},
       {(void**)&W.tr_hits, 4 * (size_t)ws->ncap},
       {(void**)&W.scan_tmp, 4 * (size_t)ws->scan_cap},
   };
@@ -384,6 +394,11 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
     return fail(ctx, TPC_E_NOMEM, "workspace allocation of " + std::to_string(total) + " bytes failed");
   }
   for (size_t k = 0; k < items.size(); ++k) *items[k].ptr = (char*)ws->block + offs[k];
+  if (!compress) {
+    W.tr_res = nullptr;
+    W.tr_npred = nullptr;
+    W.keep = nullptr;
+  }
   W.cnt = (DevCounters*)p_cnt;
   ws->d_desc = (BatchDesc*)p_desc;
   W.batch = ws->d_desc;
@@ -547,6 +562,11 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   }
   mark(ki++);  // write_tracks
   ++nl; launch_write_tracks(sh.sel_lanes, 8 * G, s, W, Q);
+  mark(ki++);  // compress
+  if (W.tr_res) {
+    ++nl; k_zero_u32<<<2 * G, 256, 0, s>>>((uint32_t*)W.keep, nullptr, (W.ncap + 3) / 4, 0, 1);
+    ++nl; launch_compress(ctx->p.packed, 4 * G, s, W, Q);
+  }
   mark(ki++);  // beamline
   ++nl; k_beamline<<<2 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // frame_off
@@ -700,15 +720,17 @@ void release_results(tpc_ctx* ctx, Frame* f) {
 // Layout of a frame's results in its page-locked block: the output arrays, each copied from the
 // workspace's track arrays as one block.
 struct ResLayout {
-  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, beam, bytes;
+  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, beam, res, npred, bytes;
 };
-ResLayout res_layout(size_t nt, size_t nh) {
+ResLayout res_layout(size_t nt, size_t nh, bool compress) {
   ResLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
   L.hits = take(nh * 4); L.sec = take(nt * 4); L.ndf = take(nt * 4); L.xref = take(nt * 4);
   L.chi2 = take(nt * 4); L.par = take(nt * 20); L.cov = take(nt * 60); L.hoff = take((nt + 1) * 8);
   L.beam = take(nt * 20);
+  L.res = take(compress ? nh * 8 : 0);
+  L.npred = take(compress ? nt * 4 : 0);
   L.bytes = off;
   return L;
 }
@@ -722,7 +744,8 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   const uint32_t t0 = c.frame_track0[k], t1 = c.frame_track0[k + 1];
   const uint32_t h0 = c.frame_hit0[k], h1 = c.frame_hit0[k + 1];
   const size_t nt = t1 - t0, nh = h1 - h0;
-  const ResLayout L = res_layout(nt, nh);
+  const bool compress = ws.W.tr_res != nullptr;
+  const ResLayout L = res_layout(nt, nh, compress);
   release_results(ctx, f);
   size_t cap = 0;
   char* b = (char*)ctx->pinned.get(L.bytes, cap);
@@ -732,6 +755,7 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   f->fetch_nt = nt;
   f->fetch_nh = nh;
   f->fetch_h0 = h0;
+  f->fetch_compress = compress;
   const Work& W = ws.W;
   const auto d2h = [&](size_t o, const void* src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
@@ -745,13 +769,17 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   CK(d2h(L.hoff, W.tr_hoff + t0, nt * 8));
   CK(d2h(L.beam, W.tr_beam + (size_t)t0 * 5, nt * 20));
   CK(d2h(L.hits, W.tr_hits + h0, nh * 4));
+  if (compress) {
+    CK(d2h(L.res, W.tr_res + 2 * (size_t)h0, nh * 8));
+    CK(d2h(L.npred, W.tr_npred + t0, nt * 4));
+  }
   return TPC_OK;
 }
 
 // Step 2, once the copies have completed: the arrays' views, hit offsets made frame-relative.
 void fetch_finish(Frame* f) {
   const size_t nt = f->fetch_nt, nh = f->fetch_nh;
-  const ResLayout L = res_layout(nt, nh);
+  const ResLayout L = res_layout(nt, nh, f->fetch_compress);
   char* b = (char*)f->res;
   f->hits = (uint32_t*)(b + L.hits);
   f->sector = (int32_t*)(b + L.sec);
@@ -762,6 +790,8 @@ void fetch_finish(Frame* f) {
   f->cov = (float*)(b + L.cov);
   f->hoff = (int64_t*)(b + L.hoff);
   f->beam = (float*)(b + L.beam);
+  f->residual = f->fetch_compress ? (int32_t*)(b + L.res) : nullptr;
+  f->n_pred = f->fetch_compress ? (int32_t*)(b + L.npred) : nullptr;
   if (f->fetch_h0)
     for (size_t i = 0; i < nt; ++i) f->hoff[i] -= (int64_t)f->fetch_h0;
   f->hoff[nt] = (int64_t)nh;
@@ -870,6 +900,9 @@ void tpc_default_params(tpc_params* p) {
   p->ext_stop = 1;
   p->drift_length = 250.0;
   p->drift_velocity = 250.0 / 90.0;
+  p->keep_vy = 1.0;
+  p->keep_vw = 1.0;
+  p->keep_qpt_max = 20.0;
   p->packed = 0;
   p->bin_occupancy = 1.0f;
   p->tracklet_capacity = 0.08f;
@@ -1071,6 +1104,8 @@ int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out) {
   out->hit_offset = f->hoff ? f->hoff : &zero_offset;
   out->hit_index = f->hits;
   out->beam = f->beam;
+  out->residual = f->residual;
+  out->n_pred = f->n_pred;
   return TPC_OK;
 }
 
@@ -1099,6 +1134,22 @@ int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n) {
   const int nv = (int)(sizeof(v) / sizeof(v[0]));
   for (int k = 0; k < n && k < nv; ++k) out[k] = v[k];
   return nv;
+}
+
+int tpc_get_keep_mask(tpc_ctx* ctx, tpc_frame_t frame, uint8_t* host_out, int64_t n) {
+  if (!ctx || !host_out) return TPC_E_INVAL;
+  Frame* f = find_frame(ctx, frame);
+  if (!f || !f->ws) return fail(ctx, TPC_E_STATE, "frame has no tracking results");
+  if (!f->ws->W.keep) return fail(ctx, TPC_E_STATE, "the context does not compute compression inputs");
+  if (n != f->n) return fail(ctx, TPC_E_INVAL, "length mismatch");
+  int rc = wait_ws(ctx, *f->ws, 120.0);
+  if (rc) return rc;
+  if (n) {
+    const long long off = f->ws->h_desc->f[f->fidx].off;
+    CK(cudaMemcpyAsync(host_out, f->ws->W.keep + off, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return TPC_OK;
 }
 
 int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n) {

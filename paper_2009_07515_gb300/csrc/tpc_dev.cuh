@@ -62,6 +62,8 @@ struct DevParams {
   int nmin;
   int ext_stop;
   float drift_len, vdrift;       // L (cm) and v_d (cm/us) of the continuous-readout drift coordinate
+  float keep_vy, keep_vw;        // strategy-B vicinity of a good track's prediction (cm)
+  float keep_qpt_max;            // good track: |q/pT| <= this
   float cov0[5];
   float occ;                     // target clusters per grid bin
   float aspect;                  // w/y extent of a grid bin (the neighbour window's aspect)
@@ -155,6 +157,9 @@ struct Work {
   int32_t* tr_ndf;       // [tcap]
   long long* tr_hoff;    // [tcap] first output hit of the track in the batch's hit list
   float* tr_beam;        // [tcap][5] beam-line extrapolation (K9)
+  int32_t* tr_res;       // [ncap][2] compression residuals of the output hits (K10; null: off)
+  int32_t* tr_npred;     // [tcap] output hits stored as residuals (K10)
+  uint8_t* keep;         // [ncap] strategy-B protection per batch input index (K10)
   uint32_t* tr_hits;     // [ncap] output hits (frame-local input indices)
   // scan scratch
   uint32_t* scan_tmp;    // [scan_tmp_cap]
@@ -383,6 +388,34 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& Q, float* P, float
   }
 #pragma unroll
   for (int i = 0; i < 15; ++i) C[i] = O[i];
+  return true;
+}
+
+// row radius x_r = 85 + r * (160/151) cm, evaluated with the same two rounded float operations as
+// the host table (a per-lane row index into a parameter table would serialise the warp's loads)
+__device__ __forceinline__ float row_x(const DevParams& Q, int r) {
+  return __fadd_rn(85.0f, __fmul_rn((float)r, Q.pitch));
+}
+
+// The state part of kf_propagate alone, the same operations (the compression step's predictions).
+__device__ __forceinline__ bool kf_propagate_state(const DevParams& Q, float* P, float x0, float x1) {
+  const float dx = x1 - x0;
+  const float k = Q.kq * P[4];
+  const float s0 = P[2];
+  const float s1 = s0 + k * dx;
+  if (!(fabsf(s1) < Q.max_sin)) return false;
+  const float c0 = sqrtf(1.0f - s0 * s0);
+  const float c1 = sqrtf(1.0f - s1 * s1);
+  const float N = s0 + s1, D = c0 + c1;
+  const float iD = 1.0f / D;
+  const float dy = dx * (N * iD);
+  const float l = sqrtf(dx * dx + dy * dy);
+  const float t = l * k * 0.5f;
+  float a = l * arc_ratio(t);
+  if (dx < 0.f) a = -a;
+  P[0] = P[0] + dy;
+  P[1] = P[1] + P[3] * a;
+  P[2] = s1;
   return true;
 }
 

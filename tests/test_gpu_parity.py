@@ -261,3 +261,29 @@ def test_device_resident_input(tracker, torch_cuda):
     tracker.release(h)
     for k in host:
         assert np.array_equal(np.asarray(host[k]), np.asarray(dev[k]), equal_nan=True), k
+
+
+@pytest.mark.parametrize("packed", [0, 1], ids=["fp32", "16bit"])
+@pytest.mark.parametrize("cfg", ["pp_500", "pbpb_2x10000"])
+def test_compression_inputs_match_oracle(torch_cuda, cfg, packed, n_threads):
+    """Track-model residuals, predicted-hit counts and the strategy-B keep mask (Sec. 3) of the
+    GPU path equal the FP32 oracle's exactly: the same transport of the same fits, integer outputs."""
+    import paper_2009_07515_gb300 as tpc
+    tr = tpc.Tracker(compress=1, packed=packed)
+    try:
+        f = synth.generate(cfg)
+        h = tr.load(f.sector, f.row, f.y, f.w)
+        tr.track(h)
+        gpu = tr.tracks(h)
+        keep = tr.keep_mask(h, f.n)
+        tr.release(h)
+    finally:
+        tr.close()
+    orc = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", packed=bool(packed), n_threads=n_threads)
+    gi, oi = compare_tracks(gpu, orc)
+    assert np.array_equal(gpu["n_pred"][gi], orc.tr_npred[oi])
+    goff, ooff = gpu["hit_offset"], orc.tr_hit_off
+    for g, o in zip(gi, oi):
+        assert np.array_equal(gpu["residual"][goff[g]:goff[g + 1]], orc.tr_res[ooff[o]:ooff[o + 1]]), (g, o)
+    assert np.array_equal(keep, orc.keep)
+    assert 0.5 < keep.mean() < 1.0
