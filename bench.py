@@ -286,6 +286,44 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
     return out
 
 
+def compression_benchmark(tpc, torch, d_in, tuned_params: dict, storage: dict, n: int, reps: int = 5) -> dict:
+    """The compression inputs of the bench frame (Sec. 3), measured apart from the tracking step:
+    the device time of the residual / keep-mask stage, the fraction of clusters strategy B keeps,
+    and the empirical entropy (bits per hit) of the stored residuals against the absolute
+    positions of the same hits, both in 2^-9 cm steps."""
+    tr = tpc.Tracker(compress=1, **tuned_params, **storage)
+    try:
+        h = tr.load(*d_in)
+        tr.set_timing(True)
+        times = []
+        for _ in range(reps):
+            tr.track(h)
+            tr.tracks(h, copy=False)
+            times.append(tr.kernel_times()["compress"])
+        tr.set_timing(False)
+        res = tr.tracks(h)
+        keep = tr.keep_mask(h, n)
+    finally:
+        tr.close()
+    off, npred = res["hit_offset"], res["n_pred"]
+    pred = np.concatenate([np.arange(off[i], off[i] + npred[i]) for i in range(len(npred))]) if len(npred) else \
+        np.zeros(0, np.int64)
+
+    def bits(v):
+        _, c = np.unique(v, return_counts=True)
+        p = c / c.sum()
+        return float(-(p * np.log2(p)).sum())
+
+    hits = res["hit_index"][pred].astype(np.int64)
+    y = d_in[2].cpu().numpy()[hits].astype(np.float64)
+    w = d_in[3].cpu().numpy()[hits].astype(np.float64)
+    r = res["residual"][pred]
+    return {"kernel_ms": float(np.median(times)), "kept_fraction": float(keep.mean()),
+            "hits_predicted": int(len(pred)),
+            "bits_per_hit": {"residual_y": bits(r[:, 0]), "residual_w": bits(r[:, 1]),
+                             "absolute_y": bits(np.rint(y * 512)), "absolute_w": bits(np.rint(w * 512))}}
+
+
 def batched_benchmark(tpc, synth, torch, *, n_frames: int = 16, steps: int = 5, packed: bool = True) -> dict:
     """The batched path: n_frames frames of uneven occupancy (Poisson(5) collisions, exponential
     multiplicity) tracked by one batched graph launch (tpc_track_batch) with launch shapes autotuned
@@ -375,6 +413,7 @@ def main():
     ap.add_argument("--serve-frames", type=int, default=80)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-frame batched-path measurement")
+    ap.add_argument("--no-compression", action="store_true", help="skip the compression-inputs measurement")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "packed"],
                     help="cluster storage of the main workload: FP32 or 16-bit fixed point")
     ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
@@ -549,6 +588,8 @@ def main():
             "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
             "kernels_ms": kernels}
     tr.release(h)
+    if not args.no_compression:
+        line["compression"] = compression_benchmark(tpc, torch, d_in, tuned_params, storage, n)
     if not args.no_batched:
         line["batched"] = batched_benchmark(tpc, synth, torch)
     if not args.no_serving:

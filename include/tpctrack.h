@@ -135,7 +135,7 @@ typedef struct {
                                  +-(w0 - w_ref) (+ on side A); all NaN where the transport fails
                                  (|sin(phi)| reaches max_sin before x = 0) */
   /* compression inputs (Sec. 3), NULL unless tpc_params.compress: each track's fit is transported
-   * row by row (state only, no scattering) from x_ref; hit i of the track is stored as
+   * (state only, no scattering) from x_ref directly to each row it spans; hit i of the track is stored as
    * q(hit) - q(prediction) at its row, q(v) = rint(512 v) in units of 2^-9 cm, for i < n_pred, and
    * as q(hit) beyond (the transport failed there). A decoder with the same arithmetic restores q(hit). */
   const int32_t* residual;    /* [hit_offset[n]][2] (y, w) */

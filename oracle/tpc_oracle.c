@@ -30,8 +30,10 @@
  *      collision time is t0 = (w0 - L) / v_d and its z at x_ref is +-(w0 - w_ref) by drift side;
  *   8. compression inputs (Sec. 3: hits of good tracks are stored as residuals to the extrapolated
  *      track position; strategy B removes every hit not in the vicinity of a good track): each
- *      track's fit is transported row by row (state only, no scattering) from x_ref to its last
- *      hit's row. At every row a good track (|q/pT| <= keep_qpt_max) protects the row's clusters
+ *      track's fit is transported (state only, no scattering) from x_ref directly to every row up
+ *      to its last hit's row, one exact helix step per row (rows independent; once a transport
+ *      fails, |sin phi| only grows further out, so every later one fails too). At every row a
+ *      good track (|q/pT| <= keep_qpt_max) protects the row's clusters
  *      within +-(keep_vy, keep_vw) of its predicted (y, w); at a row with one of its hits the hit
  *      is stored as q(hit) - q(prediction), q(v) = rint(512 v) (the 2^-9 cm quantum of the 16-bit
  *      storage). A decoder with the same arithmetic restores q(hit) exactly. If the transport
@@ -628,21 +630,23 @@ static void compress_track(const ctx_t* cx, const sector_t* S, int64_t t, uint64
   const int good = absr(P[4]) <= cx->keep_qpt_max;
   int ok = 1, n = 0, np = 0;
   for (int r = r0; r <= last; ++r) {
-    if (ok && r > r0 && propagate_state(cx, P, cx->x[r - 1], cx->x[r])) ok = 0;
+    real Pr[5];
+    for (int i = 0; i < 5; ++i) Pr[i] = P[i];
+    if (ok && r > r0 && propagate_state(cx, Pr, cx->x[r0], cx->x[r])) ok = 0;
     if (ok && good) {
       /* the row's clusters within the vicinity (exact test; the w range searched is widened by
        * the rounding of w +- vw) */
-      const real pad = absr(P[1]) * (real)1e-6 + cx->keep_vw * (real)1e-6 + (real)1e-6;
-      const real lo = (P[1] - cx->keep_vw) - pad, hi = (P[1] + cx->keep_vw) + pad;
+      const real pad = absr(Pr[1]) * (real)1e-6 + cx->keep_vw * (real)1e-6 + (real)1e-6;
+      const real lo = (Pr[1] - cx->keep_vw) - pad, hi = (Pr[1] + cx->keep_vw) + pad;
       for (int64_t i = row_lower_bound(S, r, lo); i < S->row_start[r + 1] && S->w[i] <= hi; ++i)
-        if (absr(S->w[i] - P[1]) <= cx->keep_vw && absr(S->y[i] - P[0]) <= cx->keep_vy) keep[i] = 1;
+        if (absr(S->w[i] - Pr[1]) <= cx->keep_vw && absr(S->y[i] - Pr[0]) <= cx->keep_vy) keep[i] = 1;
     }
     const int32_t h = S->t_slots[t * NROW + r];
     if (h >= 0 && S->weight[h] == key) {
       if (good) keep[h] = 1;
       if (ok) {
-        res[2 * n] = quant(S->y[h]) - quant(P[0]);
-        res[2 * n + 1] = quant(S->w[h]) - quant(P[1]);
+        res[2 * n] = quant(S->y[h]) - quant(Pr[0]);
+        res[2 * n + 1] = quant(S->w[h]) - quant(Pr[1]);
         ++np;
       } else {
         res[2 * n] = quant(S->y[h]);

@@ -224,11 +224,12 @@ void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, con
 }
 
 // K10 compression inputs (Sec. 3: hits of good tracks are stored as residuals to the extrapolated
-// track position; strategy B removes every hit not in the vicinity of a good track). One thread
-// per track: its fit is transported row by row (state only, no scattering) from x_ref to its last
-// hit's row. At every row a good track (|q/pT| <= keep_qpt_max) protects the row's clusters within
-// +-(keep_vy, keep_vw) of its prediction; each of its hits is stored as q(hit) - q(prediction),
-// q(v) = rint(512 v), or as q(hit) once the transport has failed (n_pred counts the predicted).
+// track position; strategy B removes every hit not in the vicinity of a good track). One warp per
+// track, its lanes on 32 rows at a time: the fit is transported (state only, no scattering) from
+// x_ref directly to each row up to the last hit's row. At every row a good track (|q/pT| <=
+// keep_qpt_max) protects the row's clusters within +-(keep_vy, keep_vw) of its prediction; each of
+// its hits is stored as q(hit) - q(prediction), q(v) = rint(512 v), or as q(hit) from the first row
+// whose transport fails on (n_pred counts the predicted hits).
 __device__ __forceinline__ int32_t quant512(float v) { return (int32_t)rintf(v * 512.0f); }
 template <bool kPacked>
 __device__ __forceinline__ void mark_vicinity(const Work& W, const DevParams& Q, int g, float yp, float wp,
@@ -245,9 +246,11 @@ __device__ __forceinline__ void mark_vicinity(const Work& W, const DevParams& Q,
   }
 }
 template <bool kPacked>
-__global__ void __launch_bounds__(128) k_compress(Work W, DevParams Q) {
+__global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntl; t += gridDim.x * blockDim.x) {
+  int lane;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
     const uint32_t k = W.tl_kept[t];
     if (W.tl_kept[t + 1] == k) continue;
     const uint32_t info = W.tl_info[t];
@@ -256,37 +259,61 @@ __global__ void __launch_bounds__(128) k_compress(Work W, DevParams Q) {
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     const int g0 = (int)st.y, gb = g0 - (g0 % kSegPerFrame) % kNRow;
     const long long off = W.batch->f[g0 / kSegPerFrame].off;
-    int last = -1;
-    for (int r = top; r >= ref && last < 0; --r) {
-      const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit && W.hit_w[h] == key) last = r;
-    }
-    float P[5];
+    float P0[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) P[i] = W.tl_state[(long long)t * 24 + i];
-    const bool good = fabsf(P[4]) <= Q.keep_qpt_max;
-    bool ok = true;
-    int n = 0, np = 0;
+    for (int i = 0; i < 5; ++i) P0[i] = W.tl_state[(long long)t * 24 + i];
+    const bool good = fabsf(P0[4]) <= Q.keep_qpt_max;
+    const float x0 = row_x(Q, ref);
+    // the last row with a hit of the track
+    int last = -1;
+    for (int c0 = ref; c0 <= top; c0 += 32) {
+      const int r = c0 + lane;
+      bool mine = false;
+      if (r <= top) {
+        const uint32_t h = W.slab[slab_at(t, r)];
+        mine = h != kNoHit && W.hit_w[h] == key;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, mine);
+      if (m) last = c0 + 31 - __clz((int)m);
+    }
     int32_t* res = W.tr_res + 2 * (long long)W.tl_nkept[t];
-    for (int r = ref; r <= last; ++r) {
-      if (ok && r > ref && !kf_propagate_state(Q, P, row_x(Q, r - 1), row_x(Q, r))) ok = false;
+    uint32_t n = 0, np = 0;
+    bool failed = false;  // a transport failed at an earlier row
+    for (int c0 = ref; c0 <= last; c0 += 32) {
+      const int r = c0 + lane;
+      const bool in = r <= last;
+      float P[5];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) P[i] = P0[i];
+      bool ok = in && (r == ref || kf_propagate_state(Q, P, x0, row_x(Q, r)));
+      // from the first failing row on, no row is predicted
+      const uint32_t fail = __ballot_sync(0xffffffffu, in && !ok);
+      if (failed || (fail & ((2u << lane) - 1u))) ok = false;
       if (ok && good) mark_vicinity<kPacked>(W, Q, gb + r, P[0], P[1], off);
-      const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit && W.hit_w[h] == key) {
+      bool mine = false;
+      uint32_t h = kNoHit;
+      if (in) {
+        h = W.slab[slab_at(t, r)];
+        mine = h != kNoHit && W.hit_w[h] == key;
+      }
+      const uint32_t m = __ballot_sync(0xffffffffu, mine);
+      if (mine) {
         if (good) W.keep[off + W.horig[h]] = 1;
         const float2 c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r, (int)h);
-        res[2 * n] = ok ? quant512(c.x) - quant512(P[0]) : quant512(c.x);
-        res[2 * n + 1] = ok ? quant512(c.y) - quant512(P[1]) : quant512(c.y);
-        np += ok ? 1 : 0;
-        ++n;
+        const uint32_t o = n + (uint32_t)__popc(m & ((1u << lane) - 1u));
+        res[2 * o] = ok ? quant512(c.x) - quant512(P[0]) : quant512(c.x);
+        res[2 * o + 1] = ok ? quant512(c.y) - quant512(P[1]) : quant512(c.y);
       }
+      n += (uint32_t)__popc(m);
+      np += (uint32_t)__popc(__ballot_sync(0xffffffffu, mine && ok));
+      failed = failed || fail != 0u;
     }
-    W.tr_npred[k] = np;
+    if (lane == 0) W.tr_npred[k] = (int32_t)np;
   }
 }
 void launch_compress(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q) {
-  if (packed) k_compress<true><<<grid, 128, 0, s>>>(W, Q);
-  else k_compress<false><<<grid, 128, 0, s>>>(W, Q);
+  if (packed) k_compress<true><<<grid, 256, 0, s>>>(W, Q);
+  else k_compress<false><<<grid, 256, 0, s>>>(W, Q);
 }
 
 // K9 beam line (Sec. 5: track seeds are extrapolated to the beam line, and the most likely z is

@@ -1,9 +1,10 @@
 """Pins of the oracle's compression inputs (Sec. 3: hits of good tracks are stored as residuals to
 the extrapolated track position; strategy B removes every hit not in the vicinity of a good track).
 
-Each track's fit is transported row by row (state only, no scattering) from x_ref; a hit is stored
-as q(hit) - q(prediction), q(v) = rint(512 v); a good track (|q/pT| <= 20) protects the clusters
-within +-(1 cm, 1 cm) of its prediction at every row it spans. These tests check the residuals
+Each track's fit is transported (state only, no scattering) from x_ref directly to every row it
+spans, one exact helix step per row; a hit is stored as q(hit) - q(prediction), q(v) = rint(512 v);
+a good track (|q/pT| <= 20) protects the clusters within +-(1 cm, 1 cm) of its prediction at every
+row it spans. These tests check the residuals
 against exact tracks, the entropy claim, the keep mask against brute force over all clusters, and
 the decoding of the residuals.
 """
@@ -67,7 +68,7 @@ def _full(cov15):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_keep_mask_and_decoding_match_brute_force(prec):
-    """On a small frame: predictions by repeated single-row transports (the unit entry point),
+    """On a small frame: predictions by one transport from x_ref to each row (the unit entry point),
     every cluster tested against every good track's window at its rows (brute force over the
     whole frame), and the residuals decoded back to the hits' quantized positions."""
     f = synth.generate("pp_500", mult_fixed=60, seed=43)
@@ -86,12 +87,13 @@ def test_keep_mask_and_decoding_match_brute_force(prec):
         hrows = f.row[hits].astype(int)
         r0 = int(round((res.tr_xref[i] - 85.0) / (160.0 / 151.0)))
         assert abs(rows_x[r0] - res.tr_xref[i]) < 1e-9
-        P = res.tr_param[i].copy()
-        good = abs(P[4]) <= 20.0
+        P0 = res.tr_param[i].copy()
+        good = abs(P0[4]) <= 20.0
         ok, n = True, 0
         for r in range(r0, hrows[-1] + 1):
+            P = P0
             if ok and r > r0:
-                rc, P, _, _ = oracle.propagate(P, np.eye(5), rows_x[r - 1], rows_x[r], precision=prec, params=p_noms)
+                rc, P, _, _ = oracle.propagate(P0, np.eye(5), rows_x[r0], rows_x[r], precision=prec, params=p_noms)
                 ok = rc == 0
             if ok and good:
                 m = (f.sector == res.tr_sector[i]) & (f.row == r)
