@@ -287,3 +287,38 @@ def test_compression_inputs_match_oracle(torch_cuda, cfg, packed, n_threads):
         assert np.array_equal(gpu["residual"][goff[g]:goff[g + 1]], orc.tr_res[ooff[o]:ooff[o + 1]]), (g, o)
     assert np.array_equal(keep, orc.keep)
     assert 0.5 < keep.mean() < 1.0
+
+
+def test_compression_edge_cases(torch_cuda):
+    """Compression inputs on an empty frame, a frame with no tracks, and a context without them."""
+    import paper_2009_07515_gb300 as tpc
+    tr = tpc.Tracker(compress=1)
+    try:
+        z8, zf = np.zeros(0, np.uint8), np.zeros(0, np.float32)
+        h = tr.load(z8, z8, zf, zf)
+        tr.track(h)
+        res = tr.tracks(h)
+        assert res["n_tracks"] == 0 and res["residual"].shape == (0, 2) and len(res["n_pred"]) == 0
+        assert len(tr.keep_mask(h, 0)) == 0
+        tr.release(h)
+        g = synth.generate("pp_500", seed=9)
+        noise = g.truth_track < 0
+        h = tr.load(g.sector[noise], g.row[noise], g.y[noise], g.w[noise])
+        tr.track(h)
+        keep = tr.keep_mask(h, int(noise.sum()))
+        orc = oracle.track(g.sector[noise], g.row[noise], g.y[noise], g.w[noise], precision="f32")
+        assert np.array_equal(keep, orc.keep)
+        tr.release(h)
+    finally:
+        tr.close()
+    plain = tpc.Tracker()
+    try:
+        f = synth.generate("pp_500", mult_fixed=50)
+        h = plain.load(f.sector, f.row, f.y, f.w)
+        plain.track(h)
+        assert "residual" not in plain.tracks(h)
+        with pytest.raises(tpc.TpcError) as e:
+            plain.keep_mask(h, f.n)
+        assert e.value.code == tpc._lib.TPC_E_STATE
+    finally:
+        plain.close()
