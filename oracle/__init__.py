@@ -3,9 +3,9 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import this
 package. The product path (``paper_2009_07515_gb300``) never imports it and shares no code with it.
 
-``tpc_oracle.c`` is compiled twice with gcc (``-ffp-contract=off``, no fast-math): REAL = double
-(``precision="f64"``) and REAL = float (``precision="f32"``). The step-by-step definition of what it
-computes is in the header of ``tpc_oracle.c``.
+``tpc_oracle.c`` (sector tracking) and ``cf_oracle.c`` (cluster finding from digits) are compiled
+twice with gcc (``-ffp-contract=off``, no fast-math): REAL = double (``precision="f64"``) and REAL =
+float (``precision="f32"``). The step-by-step definition of what each computes is in its header.
 """
 from __future__ import annotations
 
@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tpc_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "cf_oracle.c")]
 _lock = threading.Lock()
 _libs: dict = {}
 
@@ -36,11 +37,11 @@ def build(force: bool = False) -> None:
         for prec in ("f32", "f64"):
             out = _lib_path(prec)
             if (not force and os.path.exists(out)
-                    and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+                    and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in _SRCS)):
                 continue
             tmp = out + f".tmp{os.getpid()}"
             cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-                   "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+                   "-fPIC", "-shared"] + _SRCS + ["-o", tmp, "-lm"]
             if prec == "f32":
                 cmd.insert(1, "-DORACLE_F32")
             subprocess.run(cmd, check=True)
@@ -100,6 +101,22 @@ class _Result(ctypes.Structure):
     ]
 
 
+class CFParams(ctypes.Structure):
+    _fields_ = [
+        ("pad_pitch", ctypes.c_double), ("time_bin_w", ctypes.c_double),
+        ("q_peak_min", ctypes.c_int32), ("q_total_min", ctypes.c_int32),
+    ]
+
+
+class _CFResult(ctypes.Structure):
+    _fields_ = [
+        ("n_clusters", ctypes.c_int64),
+        ("sector", _i32p), ("row", _i32p), ("pad", _i32p), ("time", _i32p), ("digit", _i64p),
+        ("q_tot", _i64p), ("q_max", _i32p),
+        ("y", _f64p), ("w", _f64p), ("sigma_pad", _f64p), ("sigma_time", _f64p),
+    ]
+
+
 def _load(precision: str):
     if precision not in ("f32", "f64"):
         raise ValueError("precision must be 'f32' or 'f64'")
@@ -126,6 +143,13 @@ def _load(precision: str):
     f = getattr(lib, pre + "beamline")
     f.argtypes = [_P(Params), _f64p, _f64p, ctypes.c_double, ctypes.c_int, _f64p]
     f.restype = None
+    f = getattr(lib, pre + "cf_default_params"); f.argtypes = [_P(CFParams)]; f.restype = None
+    f = getattr(lib, pre + "n_pads"); f.argtypes = [ctypes.c_double, ctypes.c_int]; f.restype = ctypes.c_int
+    f = getattr(lib, pre + "find_clusters")
+    f.argtypes = [_P(CFParams), ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32, ctypes.c_int,
+                                                                           _P(_P(_CFResult))]
+    f.restype = ctypes.c_int
+    f = getattr(lib, pre + "free_cf_result"); f.argtypes = [_P(_CFResult)]; f.restype = None
     _libs[precision] = lib
     return lib
 
@@ -316,3 +340,46 @@ def beamline(P, C, x_ref: float, sector: int, *, precision="f64", params: Params
 
 def row_x(r: int, *, precision="f64") -> float:
     return getattr(_load(precision), f"oracle_{precision}_row_x")(int(r))
+
+
+# ---------------------------------------------------------------- cluster finding (cf_oracle.c)
+
+def cf_default_params(precision: str = "f64", **overrides) -> CFParams:
+    p = CFParams()
+    getattr(_load(precision), f"oracle_{precision}_cf_default_params")(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def n_pads(r: int, pad_pitch: float = 0.4) -> int:
+    return getattr(_load("f64"), "oracle_f64_n_pads")(float(pad_pitch), int(r))
+
+
+def find_clusters(sector, row, pad, time, adc, n_time: int, *, precision: str = "f32",
+                  params: CFParams | None = None, n_threads: int = 0) -> dict:
+    """Clusters of a frame's digits, in the input order of their peak digits (arrays of a dict).
+    Raises ValueError when the oracle rejects the input (a cell out of range, a zero charge or two
+    digits in one cell)."""
+    lib = _load(precision)
+    pre = f"oracle_{precision}_"
+    params = params or cf_default_params(precision)
+    a = [np.ascontiguousarray(x, dtype=dt) for x, dt in
+         ((sector, np.uint8), (row, np.uint8), (pad, np.uint16), (time, np.uint16), (adc, np.uint16))]
+    n = int(a[0].shape[0])
+    rp = _P(_CFResult)()
+    rc = getattr(lib, pre + "find_clusters")(ctypes.byref(params), n, *(x.ctypes.data for x in a), int(n_time),
+                                             int(n_threads), ctypes.byref(rp))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the digits (code {rc})")
+    try:
+        R = rp.contents
+        m = int(R.n_clusters)
+        out = dict(n_clusters=m, sector=_copy(R.sector, m, np.int32), row=_copy(R.row, m, np.int32),
+                   pad=_copy(R.pad, m, np.int32), time=_copy(R.time, m, np.int32),
+                   digit=_copy(R.digit, m, np.int64), q_tot=_copy(R.q_tot, m, np.int64),
+                   q_max=_copy(R.q_max, m, np.int32), y=_copy(R.y, m, np.float64), w=_copy(R.w, m, np.float64),
+                   sigma_pad=_copy(R.sigma_pad, m, np.float64), sigma_time=_copy(R.sigma_time, m, np.float64))
+    finally:
+        getattr(lib, pre + "free_cf_result")(rp)
+    return out

@@ -12,6 +12,10 @@ and names the workloads of this project:
                       exponential multiplicity, about 1.7e8 clusters;
 * ``serve``         — a serving-stream frame with ``n_collisions`` given by the caller.
 
+``digitize`` turns a frame's clusters into the zero-suppressed pad x time-bin digits a cluster finder
+starts from (``DIGIT_DEFAULTS``: 0.4 cm pads, 0.2 us time bins, 0.3 cm charge spread, log-normal
+cluster charge, 2-ADC threshold, 10-bit saturation).
+
 Common laws (Sec. 2 and 6.1 of the paper describe the continuous-readout frames these stand in for):
 pT log-uniform in [0.1, 10] GeV, |eta| < 0.9, phi uniform, q = +-1, Bz = 0.5 T, sigma_y = sigma_w =
 0.1 cm, 2% row-crossing inefficiency, 5% uniform noise clusters per (sector, row).
@@ -108,6 +112,13 @@ def _load():
         lib.synth_generate.restype = ctypes.c_int
         lib.synth_free.argtypes = [ctypes.POINTER(_Frame)]
         lib.synth_free.restype = None
+        lib.synth_digitize.argtypes = [ctypes.POINTER(SynthDigitParams), ctypes.c_int64] + [ctypes.c_void_p] * 4 + \
+            [ctypes.POINTER(ctypes.POINTER(_Digits))]
+        lib.synth_digitize.restype = ctypes.c_int
+        lib.synth_free_digits.argtypes = [ctypes.POINTER(_Digits)]
+        lib.synth_free_digits.restype = None
+        lib.synth_npads.argtypes = [ctypes.c_double, ctypes.c_int]
+        lib.synth_npads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -151,6 +162,89 @@ CONFIGS = {
     # serving stream frame: n_collisions set by the caller, 20 us per collision at 50 kHz
     "serve": dict(seed=5, n_collisions=1, mult_fixed=0, t_zero=0, frame_us=20.0, x0_total=0.03),
 }
+
+
+DIGIT_DEFAULTS = dict(seed=11, pad_pitch=0.4, time_bin_w=VDRIFT_CM_PER_US * 0.2, sigma_pad=0.3, sigma_time=0.3,
+                      q_median=60.0, q_log_sigma=0.4, adc_threshold=2, adc_max=1023, shuffle=0, n_threads=0)
+
+
+class SynthDigitParams(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("pad_pitch", ctypes.c_double), ("time_bin_w", ctypes.c_double),
+        ("sigma_pad", ctypes.c_double), ("sigma_time", ctypes.c_double),
+        ("q_median", ctypes.c_double), ("q_log_sigma", ctypes.c_double),
+        ("adc_threshold", ctypes.c_int32), ("adc_max", ctypes.c_int32),
+        ("shuffle", ctypes.c_int32), ("n_threads", ctypes.c_int32),
+    ]
+
+
+class _Digits(ctypes.Structure):
+    _fields_ = [
+        ("n_digits", ctypes.c_int64),
+        ("n_time", ctypes.c_int32),
+        ("sector", ctypes.POINTER(ctypes.c_uint8)),
+        ("row", ctypes.POINTER(ctypes.c_uint8)),
+        ("pad", ctypes.POINTER(ctypes.c_uint16)),
+        ("time", ctypes.POINTER(ctypes.c_uint16)),
+        ("adc", ctypes.POINTER(ctypes.c_uint16)),
+        ("truth_cluster", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+@dataclass
+class Digits:
+    """Zero-suppressed digits of one frame (SoA, caller order) and the generator's truth."""
+    sector: np.ndarray          # uint8 [n]
+    row: np.ndarray             # uint8 [n]
+    pad: np.ndarray             # uint16 [n]: 0 .. n_pads(row) - 1
+    time: np.ndarray            # uint16 [n]: time bin, 0 .. n_time - 1
+    adc: np.ndarray             # uint16 [n]: charge, >= adc_threshold
+    truth_cluster: np.ndarray   # int32 [n]: cluster with the largest deposit in the cell
+    n_time: int
+    params: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.adc.shape[0])
+
+
+def n_pads(row: int, pad_pitch: float = DIGIT_DEFAULTS["pad_pitch"]) -> int:
+    """Pads of a row: 2 ceil(x_r tan(10 deg) / pitch) (the generator's geometry)."""
+    return int(_load().synth_npads(ctypes.c_double(pad_pitch), int(row)))
+
+
+def digitize(frame: Frame, **overrides) -> Digits:
+    """Digits of a frame's clusters (each cluster spreads its charge over pads x time bins)."""
+    p = dict(DIGIT_DEFAULTS)
+    p.update(overrides)
+    lib = _load()
+    sp = SynthDigitParams(**{k: p[k] for k, _ in SynthDigitParams._fields_})
+    dp = ctypes.POINTER(_Digits)()
+    c = [np.ascontiguousarray(a) for a in (frame.sector, frame.row, frame.y, frame.w)]
+    rc = lib.synth_digitize(ctypes.byref(sp), frame.n, *(a.ctypes.data for a in c), ctypes.byref(dp))
+    if rc != 0:
+        raise RuntimeError(f"synth_digitize failed ({rc})")
+    try:
+        d = dp.contents
+        n = int(d.n_digits)
+
+        def arr(ptr, dtype):
+            if n == 0:
+                return np.zeros(0, dtype)
+            return np.ctypeslib.as_array(ptr, shape=(n,)).view(dtype).copy()
+
+        return Digits(sector=arr(d.sector, np.uint8), row=arr(d.row, np.uint8), pad=arr(d.pad, np.uint16),
+                      time=arr(d.time, np.uint16), adc=arr(d.adc, np.uint16),
+                      truth_cluster=arr(d.truth_cluster, np.int32), n_time=int(d.n_time), params=p)
+    finally:
+        lib.synth_free_digits(dp)
+
+
+def generate_digits(config: str | None = None, *, digit_overrides: dict | None = None, **overrides):
+    """(frame, digits) of a named workload: the frame's clusters digitized with ``DIGIT_DEFAULTS``."""
+    f = generate(config, **overrides)
+    return f, digitize(f, **(digit_overrides or {}))
 
 
 def params_for(config: str | None = None, **overrides) -> dict:

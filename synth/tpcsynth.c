@@ -434,3 +434,211 @@ int synth_generate(const synth_params* p, synth_frame** out) {
   *out = f;
   return 0;
 }
+
+/* ------------------------------------------------------------------------------------------------
+ * Digits: the pad-row readout a cluster finder starts from (Sec. 2: the TPC records, per pad, the
+ * charge in 0.2 us time bins, zero-suppressed). Each cluster of a frame spreads a log-normal charge
+ * over the pads and time bins of its (sector, row) with a Gaussian of widths (sigma_pad, sigma_time)
+ * centred at its (y, w); charges of overlapping clusters add; a cell becomes a digit when its
+ * rounded charge reaches adc_threshold, saturating at adc_max.
+ *
+ * Cell geometry: row r has n_pads(r) = 2 ceil(x_r tan(10 deg) / pad_pitch) pads; pad k spans
+ * y in [(k - n/2) p, (k + 1 - n/2) p); time bin j spans w in [j dw, (j + 1) dw), dw = time_bin_w.
+ * Digits come out grouped by (sector, row), each group in (time, pad) order (the order in which a
+ * row's readout is assembled), or in a seeded random order (shuffle). truth_cluster names the
+ * cluster with the largest deposit in the cell.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct {
+  uint64_t seed;
+  double pad_pitch, time_bin_w;     /* cm */
+  double sigma_pad, sigma_time;     /* cm */
+  double q_median, q_log_sigma;     /* cluster charge: q_median * exp(q_log_sigma * N(0,1)), ADC */
+  int32_t adc_threshold, adc_max;
+  int32_t shuffle;
+  int32_t n_threads;
+} synth_digit_params;
+
+typedef struct {
+  int64_t n_digits;
+  int32_t n_time;                   /* 1 + the largest time bin of any digit */
+  uint8_t* sector;
+  uint8_t* row;
+  uint16_t* pad;
+  uint16_t* time;
+  uint16_t* adc;
+  int32_t* truth_cluster;
+} synth_digits;
+
+enum { SY_K_CHARGE = 5, SY_K_DSHUFFLE = 6 };
+#define SY_FOOT 3 /* cells deposited on each side of the cluster's own cell */
+
+static sy_rng sy_dstream(uint64_t seed, uint64_t kind, uint64_t id) {
+  sy_rng r;
+  r.s = sy_mix(seed * 0x9E3779B97F4A7C15ULL + 0x2545F4914F6CDD1DULL) ^ sy_mix((kind << 58) ^ (id + 1));
+  return r;
+}
+
+int synth_npads(double pitch, int r) {
+  return 2 * (int)ceil(sy_row_x(r) * tan(10.0 * SY_PI / 180.0) / pitch);
+}
+
+/* fraction of a unit Gaussian charge at mean mu, width s, deposited in [a, b) */
+static inline double sy_frac(double a, double b, double mu, double s) {
+  const double k = 1.0 / (s * sqrt(2.0));
+  return 0.5 * (erf((b - mu) * k) - erf((a - mu) * k));
+}
+
+void synth_free_digits(synth_digits* d) {
+  if (!d) return;
+  free(d->sector); free(d->row); free(d->pad); free(d->time); free(d->adc); free(d->truth_cluster);
+  free(d);
+}
+
+typedef struct { uint16_t pad, time, adc; int32_t truth; } sy_drec;
+
+int synth_digitize(const synth_digit_params* p, int64_t n, const uint8_t* sector, const uint8_t* row,
+                   const float* y, const float* w, synth_digits** out) {
+  const int G = SY_NSEC * SY_NROW;
+  if (!p || !out || n < 0 || p->pad_pitch <= 0 || p->time_bin_w <= 0 || p->adc_threshold < 1 ||
+      p->adc_max < p->adc_threshold || p->adc_max > 65535)
+    return -1;
+  *out = NULL;
+  int64_t* gstart = (int64_t*)calloc((size_t)G + 1, sizeof(int64_t));
+  int64_t* order = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  sy_drec** gbuf = (sy_drec**)calloc((size_t)G, sizeof(sy_drec*));
+  int64_t* gcnt = (int64_t*)calloc((size_t)G, sizeof(int64_t));
+  int32_t* gtmax = (int32_t*)calloc((size_t)G, sizeof(int32_t));
+  if (!gstart || !order || !gbuf || !gcnt || !gtmax) {
+    free(gstart); free(order); free(gbuf); free(gcnt); free(gtmax);
+    return -2;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    if (sector[i] >= SY_NSEC || row[i] >= SY_NROW) { free(gstart); free(order); free(gbuf); free(gcnt); free(gtmax); return -1; }
+    ++gstart[sector[i] * SY_NROW + row[i] + 1];
+  }
+  for (int g = 0; g < G; ++g) gstart[g + 1] += gstart[g];
+  {
+    int64_t* fill = (int64_t*)malloc((size_t)G * sizeof(int64_t));
+    if (!fill) { free(gstart); free(order); free(gbuf); free(gcnt); free(gtmax); return -2; }
+    memcpy(fill, gstart, (size_t)G * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) order[fill[sector[i] * SY_NROW + row[i]]++] = i;
+    free(fill);
+  }
+  int failed = 0;
+#ifdef _OPENMP
+  if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : failed)
+#endif
+  for (int g = 0; g < G; ++g) {
+    const int64_t b = gstart[g], e = gstart[g + 1];
+    if (b == e) continue;
+    const int r = g % SY_NROW;
+    const int np = synth_npads(p->pad_pitch, r);
+    const double half = 0.5 * (double)np;
+    int64_t jlo = INT64_MAX, jhi = INT64_MIN;
+    for (int64_t q = b; q < e; ++q) {
+      const int64_t j = (int64_t)floor((double)w[order[q]] / p->time_bin_w);
+      if (j < jlo) jlo = j;
+      if (j > jhi) jhi = j;
+    }
+    jlo -= SY_FOOT; jhi += SY_FOOT;
+    if (jlo < 0) jlo = 0;
+    if (jhi > 65534) jhi = 65534;
+    if (jhi < jlo) continue;
+    const int64_t nt = jhi - jlo + 1;
+    double* q = (double*)calloc((size_t)(np * nt), sizeof(double));
+    double* qbest = (double*)calloc((size_t)(np * nt), sizeof(double));
+    int32_t* who = (int32_t*)malloc((size_t)(np * nt) * sizeof(int32_t));
+    if (!q || !qbest || !who) { free(q); free(qbest); free(who); failed = 1; continue; }
+    for (int64_t c = b; c < e; ++c) {
+      const int64_t i = order[c];
+      sy_rng rr = sy_dstream(p->seed, SY_K_CHARGE, (uint64_t)i);
+      const double Q = p->q_median * exp(p->q_log_sigma * sy_gauss(&rr));
+      const double yc = (double)y[i], wc = (double)w[i];
+      const int64_t kc = (int64_t)floor(yc / p->pad_pitch + half);
+      const int64_t jc = (int64_t)floor(wc / p->time_bin_w);
+      double fk[2 * SY_FOOT + 1], fj[2 * SY_FOOT + 1];
+      for (int d = -SY_FOOT; d <= SY_FOOT; ++d) {
+        const double k = (double)(kc + d), j = (double)(jc + d);
+        fk[d + SY_FOOT] = sy_frac((k - half) * p->pad_pitch, (k + 1.0 - half) * p->pad_pitch, yc, p->sigma_pad);
+        fj[d + SY_FOOT] = sy_frac(j * p->time_bin_w, (j + 1.0) * p->time_bin_w, wc, p->sigma_time);
+      }
+      for (int dj = -SY_FOOT; dj <= SY_FOOT; ++dj) {
+        const int64_t j = jc + dj;
+        if (j < jlo || j > jhi) continue;
+        for (int dk = -SY_FOOT; dk <= SY_FOOT; ++dk) {
+          const int64_t k = kc + dk;
+          if (k < 0 || k >= np) continue;
+          const double dq = Q * fk[dk + SY_FOOT] * fj[dj + SY_FOOT];
+          const int64_t cell = (j - jlo) * np + k;
+          q[cell] += dq;
+          if (dq > qbest[cell]) { qbest[cell] = dq; who[cell] = (int32_t)i; }
+        }
+      }
+    }
+    int64_t cnt = 0;
+    for (int64_t cell = 0; cell < np * nt; ++cell)
+      if ((int64_t)floor(q[cell] + 0.5) >= p->adc_threshold) ++cnt;
+    sy_drec* buf = (sy_drec*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(sy_drec));
+    if (!buf) { free(q); free(qbest); free(who); failed = 1; continue; }
+    int64_t o = 0;
+    int32_t tmax = 0;
+    for (int64_t cell = 0; cell < np * nt; ++cell) {
+      int64_t a = (int64_t)floor(q[cell] + 0.5);
+      if (a < p->adc_threshold) continue;
+      if (a > p->adc_max) a = p->adc_max;
+      const int64_t j = jlo + cell / np;
+      buf[o].pad = (uint16_t)(cell % np);
+      buf[o].time = (uint16_t)j;
+      buf[o].adc = (uint16_t)a;
+      buf[o].truth = who[cell];
+      if ((int32_t)j > tmax) tmax = (int32_t)j;
+      ++o;
+    }
+    gbuf[g] = buf;
+    gcnt[g] = cnt;
+    gtmax[g] = cnt > 0 ? tmax + 1 : 0;
+    free(q); free(qbest); free(who);
+  }
+  int64_t total = 0;
+  int32_t ntime = 0;
+  for (int g = 0; g < G; ++g) { total += gcnt[g]; if (gtmax[g] > ntime) ntime = gtmax[g]; }
+  synth_digits* d = (synth_digits*)calloc(1, sizeof(synth_digits));
+  const size_t na = (size_t)(total > 0 ? total : 1);
+  if (d) {
+    d->sector = (uint8_t*)malloc(na); d->row = (uint8_t*)malloc(na);
+    d->pad = (uint16_t*)malloc(na * 2); d->time = (uint16_t*)malloc(na * 2); d->adc = (uint16_t*)malloc(na * 2);
+    d->truth_cluster = (int32_t*)malloc(na * 4);
+  }
+  if (failed || !d || !d->sector || !d->row || !d->pad || !d->time || !d->adc || !d->truth_cluster) {
+    for (int g = 0; g < G; ++g) free(gbuf[g]);
+    free(gstart); free(order); free(gbuf); free(gcnt); free(gtmax); synth_free_digits(d);
+    return -2;
+  }
+  d->n_digits = total;
+  d->n_time = ntime;
+  int64_t o = 0;
+  for (int g = 0; g < G; ++g) {
+    for (int64_t k = 0; k < gcnt[g]; ++k, ++o) {
+      d->sector[o] = (uint8_t)(g / SY_NROW); d->row[o] = (uint8_t)(g % SY_NROW);
+      d->pad[o] = gbuf[g][k].pad; d->time[o] = gbuf[g][k].time; d->adc[o] = gbuf[g][k].adc;
+      d->truth_cluster[o] = gbuf[g][k].truth;
+    }
+    free(gbuf[g]);
+  }
+  free(gstart); free(order); free(gbuf); free(gcnt); free(gtmax);
+  if (p->shuffle && total > 1) {
+    sy_rng sh = sy_dstream(p->seed, SY_K_DSHUFFLE, 0);
+    for (int64_t i = total - 1; i > 0; --i) {
+      const int64_t j = (int64_t)(sy_next(&sh) % (uint64_t)(i + 1));
+      uint8_t t8 = d->sector[i]; d->sector[i] = d->sector[j]; d->sector[j] = t8;
+      t8 = d->row[i]; d->row[i] = d->row[j]; d->row[j] = t8;
+      uint16_t t16 = d->pad[i]; d->pad[i] = d->pad[j]; d->pad[j] = t16;
+      t16 = d->time[i]; d->time[i] = d->time[j]; d->time[j] = t16;
+      t16 = d->adc[i]; d->adc[i] = d->adc[j]; d->adc[j] = t16;
+      int32_t t32 = d->truth_cluster[i]; d->truth_cluster[i] = d->truth_cluster[j]; d->truth_cluster[j] = t32;
+    }
+  }
+  *out = d;
+  return 0;
+}
