@@ -242,6 +242,79 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable);
 int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 
+/* ---- cluster finding from digits (Table 1 of Sec. 6.2 times it as the first GPU step of the
+ * synchronous reconstruction; Sec. 2: the TPC records, per pad, the charge of every time bin, and a
+ * pad row's clusters are reconstructed from these zero-suppressed digits). The paper names the step
+ * but not its rules; the library computes:
+ *   cells     row r has n_pads(r) = 2 ceil(x_r tan(10 deg) / pad_pitch) pads; pad k spans
+ *             y in [(k - n_pads/2) pad_pitch, (k + 1 - n_pads/2) pad_pitch); time bin j spans
+ *             w in [j time_bin_w, (j + 1) time_bin_w). q(s, r, k, j) = the charge of the digit in
+ *             that cell, 0 where there is none or outside the row.
+ *   peak      a digit c with q_c >= q_peak_min that beats each of its 8 neighbours n in the 3x3
+ *             window: q_n < q_c, or q_n = q_c and n comes later in (time, pad) order (dj > 0, or
+ *             dj = 0 and dk > 0); a plateau of equal charges has one peak, its first cell.
+ *   cluster   the 3x3 window around a peak plus each cell of the surrounding 5x5 ring whose charge
+ *             does not exceed that of the window cell next to it on the way to the peak (the +-2
+ *             coordinates stepped one cell inwards); kept if Q = sum of charges >= q_total_min.
+ *   values    from the integer sums Q, Sk = sum q dk, Sj = sum q dj, Skk = sum q dk^2,
+ *             Sjj = sum q dj^2 (dk, dj relative to the peak), in FP32 with IEEE operations in this
+ *             order: mk = Sk/Q, mj = Sj/Q; y = ((k + mk) - (n_pads/2 - 0.5)) * pad_pitch;
+ *             w = ((j + mj) + 0.5) * time_bin_w; sigma_pad = sqrt(Skk/Q - mk*mk) (0 if not > 0),
+ *             sigma_time likewise (in pads and time bins). */
+typedef struct {
+  double pad_pitch;     /* cm (default 0.4) */
+  double time_bin_w;    /* cm of drift coordinate per time bin (default (250/90) * 0.2: 0.2 us) */
+  int32_t q_peak_min;   /* default 3 */
+  int32_t q_total_min;  /* default 10 */
+} tpc_cf_params;
+
+/* Digits of one time frame, structure of arrays in the caller's order (n entries each): at most one
+ * digit per (sector, row, pad, time) cell, sector < 36, row < 152, pad < n_pads(row),
+ * time < n_time, adc >= 1; anything else makes tpc_find_clusters return TPC_E_INVAL. */
+typedef struct {
+  const uint8_t* sector;
+  const uint8_t* row;
+  const uint16_t* pad;
+  const uint16_t* time;
+  const uint16_t* adc;
+  int64_t n;            /* < 2^31 */
+  int32_t n_time;       /* time bins of the frame, <= 65535 */
+  int32_t on_device;    /* 1: device pointers (read during the call), 0: host memory */
+} tpc_digits;
+
+/* Clusters found in a frame's digits, in the input order of their peak digits. The arrays belong
+ * to the context and stay valid until its next tpc_find_clusters() call or tpc_destroy(). With
+ * on_device = 1 they are device arrays: (sector, row, y, w) can be passed as a tpc_clusters with
+ * on_device = 1 to tpc_load_clusters(), which borrows them until the frame's tracking completes,
+ * so track it before the next tpc_find_clusters() call. */
+typedef struct {
+  int64_t n_clusters;
+  int32_t on_device;
+  const uint8_t* sector;
+  const uint8_t* row;
+  const float* y;
+  const float* w;
+  const uint32_t* q_tot;
+  const uint16_t* q_max;      /* the peak digit's charge */
+  const float* sigma_pad;
+  const float* sigma_time;
+  const uint32_t* digit;      /* input index of the peak digit */
+} tpc_cluster_list;
+
+void tpc_cf_default_params(tpc_cf_params* p);
+
+/* Find the clusters of one frame's digits (the kernels run on cuda_stream, NULL = the context's
+ * stream; the call waits, bounded, for them). to_host = 1 returns page-locked host copies, 0 the
+ * device arrays. The context keeps a charge map of 36 * 152 * (n_time + 4) * stride 16-bit cells
+ * (stride = n_pads of the widest row + 4, rounded up to 16) in device memory between calls;
+ * TPC_E_BUDGET if it would exceed half of the context's hbm_budget. Returns TPC_OK, TPC_E_INVAL
+ * (bad parameters or digits, nothing written), TPC_E_BUDGET, TPC_E_NOMEM, TPC_E_TIMEOUT or TPC_E_CUDA. */
+int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digits* digits, int32_t to_host,
+                      tpc_cluster_list* out, void* cuda_stream);
+
+/* Per-kernel device time of the last tpc_find_clusters() call (with tpc_set_timing(ctx, 1)). */
+int tpc_get_cf_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
+
 /* Diagnostic of the kernels' bounded waits (no counterpart in the paper). Every device-side wait of
  * the library (the neighbour search waits on shared-memory barriers for its staging copies) gives
  * up after a time limit, records a timeout in a device status word and returns, so a lost copy

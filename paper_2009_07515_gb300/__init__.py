@@ -12,9 +12,9 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import TpcError, default_params, load, tracks_to_numpy
+from ._lib import TpcError, cf_default_params, default_params, load, tracks_to_numpy
 
-__all__ = ["Tracker", "TpcError", "default_params", "load", "build"]
+__all__ = ["Tracker", "TpcError", "default_params", "cf_default_params", "load", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -149,6 +149,45 @@ class Tracker:
             return self.tracks(f)
         finally:
             self.release(f)
+
+    # --------------------------------------------------------------- cluster finding
+    def find_clusters(self, sector, row, pad, time, adc, n_time: int, *, to_host: bool = True,
+                      cf_params: _lib.tpc_cf_params | None = None, stream=None):
+        """Clusters of one frame's digits (tpc_find_clusters). Digit arrays: numpy (host) or torch
+        CUDA tensors (device). to_host=True returns numpy copies; to_host=False returns the raw
+        tpc_cluster_list of device arrays, valid until the next call (see load_cluster_list)."""
+        keep = []
+        arrs = []
+        for a, dt in ((sector, np.uint8), (row, np.uint8), (pad, np.uint16), (time, np.uint16), (adc, np.uint16)):
+            if isinstance(a, np.ndarray):
+                a = np.ascontiguousarray(a, dtype=dt)
+            arrs.append(a)
+        keep.extend(arrs)
+        ptrs = [_ptr(a) for a in arrs]
+        on_dev = {p[1] for p in ptrs}
+        if len(on_dev) != 1:
+            raise ValueError("digit arrays must all be on the host or all on the device")
+        d = _lib.tpc_digits(*(p[0] for p in ptrs), int(arrs[4].shape[0]), int(n_time), on_dev.pop())
+        out = _lib.tpc_cluster_list()
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream)
+        cp = ctypes.byref(cf_params) if cf_params is not None else None
+        self._check(self.lib.tpc_find_clusters(self.ctx, cp, ctypes.byref(d), 1 if to_host else 0, ctypes.byref(out), s))
+        return _lib.clusters_to_numpy(out) if to_host else out
+
+    def load_cluster_list(self, cl: _lib.tpc_cluster_list) -> int:
+        """Load the device clusters of find_clusters(to_host=False) as a frame (borrowed: track it
+        before the next find_clusters call)."""
+        if not cl.on_device:
+            raise ValueError("expected a device cluster list")
+        c = _lib.tpc_clusters(cl.sector, cl.row, cl.y, cl.w, int(cl.n_clusters), 1)
+        h = ctypes.c_uint64()
+        self._check(self.lib.tpc_load_clusters(self.ctx, ctypes.byref(c), ctypes.byref(h)))
+        return h.value
+
+    def cf_kernel_times(self) -> dict:
+        kt = _lib.tpc_kernel_times()
+        self._check(self.lib.tpc_get_cf_kernel_times(self.ctx, ctypes.byref(kt)))
+        return {kt.names[i].decode(): float(kt.ms[i]) for i in range(kt.n_kernels)}
 
     # --------------------------------------------------------------- serving
     def submit(self, sector, row, y, w) -> int:

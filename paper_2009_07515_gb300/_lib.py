@@ -126,6 +126,73 @@ class tpc_tune_report(ctypes.Structure):
     ]
 
 
+class tpc_cf_params(ctypes.Structure):
+    _fields_ = [
+        ("pad_pitch", ctypes.c_double),
+        ("time_bin_w", ctypes.c_double),
+        ("q_peak_min", ctypes.c_int32),
+        ("q_total_min", ctypes.c_int32),
+    ]
+
+
+class tpc_digits(ctypes.Structure):
+    _fields_ = [
+        ("sector", ctypes.c_void_p),
+        ("row", ctypes.c_void_p),
+        ("pad", ctypes.c_void_p),
+        ("time", ctypes.c_void_p),
+        ("adc", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("n_time", ctypes.c_int32),
+        ("on_device", ctypes.c_int32),
+    ]
+
+
+class tpc_cluster_list(ctypes.Structure):
+    _fields_ = [
+        ("n_clusters", ctypes.c_int64),
+        ("on_device", ctypes.c_int32),
+        ("sector", ctypes.c_void_p),
+        ("row", ctypes.c_void_p),
+        ("y", ctypes.c_void_p),
+        ("w", ctypes.c_void_p),
+        ("q_tot", ctypes.c_void_p),
+        ("q_max", ctypes.c_void_p),
+        ("sigma_pad", ctypes.c_void_p),
+        ("sigma_time", ctypes.c_void_p),
+        ("digit", ctypes.c_void_p),
+    ]
+
+
+CLUSTER_FIELDS = (("sector", np.uint8), ("row", np.uint8), ("y", np.float32), ("w", np.float32),
+                  ("q_tot", np.uint32), ("q_max", np.uint16), ("sigma_pad", np.float32),
+                  ("sigma_time", np.float32), ("digit", np.uint32))
+
+
+def clusters_to_numpy(c: tpc_cluster_list) -> dict:
+    """Copies of a host cluster list (to_host = 1) as numpy arrays."""
+    if c.on_device:
+        raise ValueError("the cluster list holds device pointers")
+    n = int(c.n_clusters)
+    out = {"n_clusters": n}
+    for name, dt in CLUSTER_FIELDS:
+        ptr = getattr(c, name)
+        if n == 0 or not ptr:
+            out[name] = np.zeros(0, dt)
+        else:
+            buf = (ctypes.c_char * (n * np.dtype(dt).itemsize)).from_address(ptr)
+            out[name] = np.frombuffer(buf, dtype=dt).copy()
+    return out
+
+
+def cf_default_params(**overrides) -> tpc_cf_params:
+    p = tpc_cf_params()
+    load().tpc_cf_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
 _ctx_p = ctypes.c_void_p
 _frame = ctypes.c_uint64
 
@@ -152,6 +219,10 @@ SIGNATURES = [
     ("tpc_check_wait_timeout", ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p]),
     ("tpc_set_timing", ctypes.c_int, [_ctx_p, ctypes.c_int32]),
     ("tpc_get_kernel_times", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_kernel_times)]),
+    ("tpc_cf_default_params", None, [ctypes.POINTER(tpc_cf_params)]),
+    ("tpc_find_clusters", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_cf_params), ctypes.POINTER(tpc_digits),
+                                         ctypes.c_int32, ctypes.POINTER(tpc_cluster_list), ctypes.c_void_p]),
+    ("tpc_get_cf_kernel_times", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_kernel_times)]),
     ("tpc_links_static", ctypes.c_int, [ctypes.POINTER(tpc_params), ctypes.POINTER(tpc_clusters), ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]),
 ]

@@ -63,6 +63,37 @@ __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_set_ntracklets(Work);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
+__global__ void k_cf_fill(CfArgs);
+__global__ void k_cf_peaks(CfArgs);
+__global__ void k_cf_build(CfArgs);
+__global__ void k_cf_clear(CfArgs);
+
+// Cluster finding: device buffers sized by a digit capacity, the charge map (kept zero between
+// calls), page-locked host copies of the last call's clusters, timing events.
+constexpr int kCfKernels = 5;
+struct CfState {
+  void* dev = nullptr;
+  long long cap = 0;
+  uint8_t *in_sector = nullptr, *in_row = nullptr;
+  uint16_t *in_pad = nullptr, *in_time = nullptr, *in_adc = nullptr;
+  uint32_t *mask = nullptr, *tcount = nullptr, *toff = nullptr, *scan_tmp = nullptr, *small = nullptr;
+  uint16_t* npads = nullptr;
+  uint8_t *o_sector = nullptr, *o_row = nullptr;
+  float *o_y = nullptr, *o_w = nullptr, *o_sp = nullptr, *o_st = nullptr;
+  uint32_t *o_qtot = nullptr, *o_digit = nullptr;
+  uint16_t* o_qmax = nullptr;
+  uint16_t* map = nullptr;
+  size_t map_bytes = 0;
+  int lines = 0, stride = 0;
+  bool map_clean = false;
+  uint32_t* h_small = nullptr;      // page-locked: total, error bits
+  void* host = nullptr;
+  size_t host_bytes = 0;
+  cudaEvent_t ev[kCfKernels + 1] = {nullptr};
+  cudaEvent_t done = nullptr;
+  float ms[kCfKernels] = {0};
+  int64_t launches[kCfKernels] = {0};
+};
 }  // namespace tpc
 
 namespace tpc {
@@ -277,6 +308,7 @@ struct tpc_ctx {
   };
   std::deque<Fetching> fetching;
   std::vector<cudaEvent_t> spare_events;
+  CfState cf;
 };
 
 namespace {
@@ -875,6 +907,93 @@ void drop_frame(tpc_ctx* ctx, Frame* f) {
 }
 
 
+// ------------------------------------------------------------------------- cluster finding
+
+// pads of a row: 2 ceil(x_r tan(10 deg) / pitch), in double
+int cf_npads(double pitch, int r) {
+  const double x = 85.0 + (double)r * (160.0 / 151.0);
+  return 2 * (int)std::ceil(x * std::tan(10.0 * 3.14159265358979323846 / 180.0) / pitch);
+}
+
+// device buffers for n digits (one allocation; grown by 1/8 beyond the request)
+int cf_reserve(tpc_ctx* ctx, long long n) {
+  CfState& cf = ctx->cf;
+  if (cf.dev && cf.cap >= n) return TPC_OK;
+  const long long cap = std::max<long long>(n + n / 8, 1 << 16);
+  const long long tiles = (cap + kCfTile - 1) / kCfTile;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_is = take(cap), o_ir = take(cap), o_ip = take(2 * cap), o_it = take(2 * cap), o_ia = take(2 * cap);
+  const size_t o_mask = take(4 * ((cap + 31) / 32)), o_tc = take(4 * tiles), o_to = take(4 * (tiles + 1));
+  const size_t o_tmp = take(4 * (tiles / 2048 + 2)), o_small = take(16), o_np = take(2 * kNRow);
+  const size_t o_os = take(cap), o_or = take(cap), o_y = take(4 * cap), o_w = take(4 * cap), o_sp = take(4 * cap);
+  const size_t o_st = take(4 * cap), o_q = take(4 * cap), o_d = take(4 * cap), o_qm = take(2 * cap);
+  if (cf.dev) {
+    cudaFree(cf.dev);
+    cf.dev = nullptr;
+    cf.cap = 0;
+  }
+  if (cudaMalloc(&cf.dev, off) != cudaSuccess) {
+    cudaGetLastError();
+    cf.dev = nullptr;
+    return fail(ctx, TPC_E_NOMEM, "cluster-finder buffers of " + std::to_string(off) + " bytes");
+  }
+  char* b = static_cast<char*>(cf.dev);
+  cf.in_sector = (uint8_t*)(b + o_is);
+  cf.in_row = (uint8_t*)(b + o_ir);
+  cf.in_pad = (uint16_t*)(b + o_ip);
+  cf.in_time = (uint16_t*)(b + o_it);
+  cf.in_adc = (uint16_t*)(b + o_ia);
+  cf.mask = (uint32_t*)(b + o_mask);
+  cf.tcount = (uint32_t*)(b + o_tc);
+  cf.toff = (uint32_t*)(b + o_to);
+  cf.scan_tmp = (uint32_t*)(b + o_tmp);
+  cf.small = (uint32_t*)(b + o_small);
+  cf.npads = (uint16_t*)(b + o_np);
+  cf.o_sector = (uint8_t*)(b + o_os);
+  cf.o_row = (uint8_t*)(b + o_or);
+  cf.o_y = (float*)(b + o_y);
+  cf.o_w = (float*)(b + o_w);
+  cf.o_sp = (float*)(b + o_sp);
+  cf.o_st = (float*)(b + o_st);
+  cf.o_qtot = (uint32_t*)(b + o_q);
+  cf.o_digit = (uint32_t*)(b + o_d);
+  cf.o_qmax = (uint16_t*)(b + o_qm);
+  cf.cap = cap;
+  return TPC_OK;
+}
+
+// the charge map for a geometry (zero everywhere): reused while it is clean and large enough
+int cf_map(tpc_ctx* ctx, int lines, int stride, cudaStream_t s) {
+  CfState& cf = ctx->cf;
+  const size_t need = (size_t)kSegPerFrame * (size_t)lines * (size_t)stride * 2;
+  if (need > (size_t)std::max<int64_t>(ctx->p.hbm_budget, 0) / 2)
+    return fail(ctx, TPC_E_BUDGET, "charge map of " + std::to_string(need) + " bytes exceeds half of the HBM budget");
+  if (!cf.map || cf.map_bytes < need) {
+    if (cf.map) cudaFree(cf.map);
+    cf.map = nullptr;
+    cf.map_bytes = 0;
+    cf.map_clean = false;
+    if (cudaMalloc(&cf.map, need) != cudaSuccess) {
+      cudaGetLastError();
+      cf.map = nullptr;
+      return fail(ctx, TPC_E_NOMEM, "charge map of " + std::to_string(need) + " bytes");
+    }
+    cf.map_bytes = need;
+  }
+  if (!cf.map_clean) {
+    CK(cudaMemsetAsync(cf.map, 0, cf.map_bytes, s));
+    cf.map_clean = true;
+  }
+  cf.lines = lines;
+  cf.stride = stride;
+  return TPC_OK;
+}
+
 }  // namespace
 
 // ============================================================================== C-ABI
@@ -1014,6 +1133,14 @@ void tpc_destroy(tpc_ctx* ctx) {
   for (int k = 0; k <= kNumKernels; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   if (ctx->ev_sync) cudaEventDestroy(ctx->ev_sync);
+  CfState& cf = ctx->cf;
+  if (cf.dev) cudaFree(cf.dev);
+  if (cf.map) cudaFree(cf.map);
+  if (cf.h_small) cudaFreeHost(cf.h_small);
+  if (cf.host) cudaFreeHost(cf.host);
+  for (auto& e : cf.ev)
+    if (e) cudaEventDestroy(e);
+  if (cf.done) cudaEventDestroy(cf.done);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
 }
@@ -1548,6 +1675,168 @@ int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out) {
   out->names = kKernelNames;
   out->ms = ctx->ms;
   out->launches = ctx->launches;
+  return TPC_OK;
+}
+
+void tpc_cf_default_params(tpc_cf_params* p) {
+  if (!p) return;
+  p->pad_pitch = 0.4;
+  p->time_bin_w = (250.0 / 90.0) * 0.2;
+  p->q_peak_min = 3;
+  p->q_total_min = 10;
+}
+
+int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digits* d, int32_t to_host,
+                      tpc_cluster_list* out, void* cuda_stream) {
+  if (!ctx) return TPC_E_INVAL;
+  if (!d || !out) return fail(ctx, TPC_E_INVAL, "null digits or output");
+  tpc_cf_params P;
+  if (params) P = *params;
+  else tpc_cf_default_params(&P);
+  if (!(P.pad_pitch >= 0.01 && P.pad_pitch <= 100.0) || !(P.time_bin_w > 0.0 && P.time_bin_w <= 1e4) ||
+      P.q_peak_min < 1 || P.q_total_min < 0)
+    return fail(ctx, TPC_E_INVAL, "bad cluster-finder parameters");
+  if (d->n < 0 || d->n >= (1LL << 31) || d->n_time < 0 || d->n_time > 65535)
+    return fail(ctx, TPC_E_INVAL, "bad digit descriptor");
+  if (d->n > 0 && (!d->sector || !d->row || !d->pad || !d->time || !d->adc))
+    return fail(ctx, TPC_E_INVAL, "null digit array");
+  CfState& cf = ctx->cf;
+  memset(out, 0, sizeof(*out));
+  out->on_device = to_host ? 0 : 1;
+  if (d->n == 0) return TPC_OK;
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  uint16_t np[kNRow];
+  int npmax = 0;
+  for (int r = 0; r < kNRow; ++r) {
+    const int v = cf_npads(P.pad_pitch, r);
+    np[r] = (uint16_t)v;
+    npmax = std::max(npmax, v);
+  }
+  const int stride = (int)align_up((size_t)npmax + 2 * kCfGuard, 16);
+  const int lines = d->n_time + 2 * kCfGuard;
+  int rc = cf_reserve(ctx, d->n);
+  if (rc) return rc;
+  if (!cf.done) {
+    for (auto& e : cf.ev) CK(cudaEventCreate(&e));
+    CK(cudaEventCreateWithFlags(&cf.done, cudaEventDisableTiming));
+    CK(cudaMallocHost((void**)&cf.h_small, 16));
+  }
+  rc = cf_map(ctx, lines, stride, s);
+  if (rc) return rc;
+  const long long n = d->n;
+  CK(cudaMemcpyAsync(cf.npads, np, sizeof(np), cudaMemcpyHostToDevice, s));
+  CfArgs A{};
+  if (d->on_device) {
+    A.sector = d->sector; A.row = d->row; A.pad = d->pad; A.time = d->time; A.adc = d->adc;
+  } else {
+    CK(cudaMemcpyAsync(cf.in_sector, d->sector, n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cf.in_row, d->row, n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cf.in_pad, d->pad, 2 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cf.in_time, d->time, 2 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(cf.in_adc, d->adc, 2 * n, cudaMemcpyHostToDevice, s));
+    A.sector = cf.in_sector; A.row = cf.in_row; A.pad = cf.in_pad; A.time = cf.in_time; A.adc = cf.in_adc;
+  }
+  A.n = n;
+  A.n_time = d->n_time;
+  A.lines = lines;
+  A.stride = stride;
+  A.q_peak_min = P.q_peak_min;
+  A.q_total_min = P.q_total_min;
+  A.pitch = (float)P.pad_pitch;
+  A.dw = (float)P.time_bin_w;
+  A.map = cf.map;
+  A.mask = cf.mask;
+  A.tcount = cf.tcount;
+  A.toff = cf.toff;
+  A.err = cf.small + 1;
+  A.o_sector = cf.o_sector; A.o_row = cf.o_row; A.o_y = cf.o_y; A.o_w = cf.o_w; A.o_qtot = cf.o_qtot;
+  A.o_qmax = cf.o_qmax; A.o_sig_pad = cf.o_sp; A.o_sig_time = cf.o_st; A.o_digit = cf.o_digit;
+  A.npads = cf.npads;
+  CK(cudaMemsetAsync(cf.small, 0, 16, s));
+  const long long tiles = (n + kCfTile - 1) / kCfTile;
+  const int grid = (int)std::min<long long>(tiles, (long long)ctx->sms * (2048 / kCfTile));
+  const int G = ctx->sms;
+  const bool timing = ctx->timing;
+  cf.map_clean = false;
+  if (timing) cudaEventRecord(cf.ev[0], s);
+  k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
+  if (timing) cudaEventRecord(cf.ev[1], s);
+  k_cf_peaks<<<grid, kCfTile, 0, s>>>(A);
+  if (timing) cudaEventRecord(cf.ev[2], s);
+  k_scan_reduce<<<2 * G, 256, 0, s>>>(cf.tcount, nullptr, tiles, 0, cf.scan_tmp);
+  k_scan_tiles<<<1, 1024, 0, s>>>(cf.scan_tmp, nullptr, tiles, 0, cf.small);
+  k_scan_apply<<<2 * G, 256, 0, s>>>(cf.tcount, nullptr, tiles, 0, cf.scan_tmp, cf.small, cf.toff);
+  if (timing) cudaEventRecord(cf.ev[3], s);
+  k_cf_build<<<grid, kCfTile, 0, s>>>(A);
+  if (timing) cudaEventRecord(cf.ev[4], s);
+  k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
+  if (timing) cudaEventRecord(cf.ev[5], s);
+  const int64_t nl[kCfKernels] = {1, 1, 3, 1, 1};
+  for (int k = 0; k < kCfKernels; ++k) cf.launches[k] = nl[k];
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("cluster-finder launch: ") + cudaGetErrorString(e));
+  CK(cudaMemcpyAsync(cf.h_small, cf.small, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(cf.done, s));
+  rc = wait_event(ctx, cf.done, 120.0);
+  if (rc) return rc;
+  cf.map_clean = true;
+  if (timing)
+    for (int k = 0; k < kCfKernels; ++k) {
+      float m = 0;
+      if (cudaEventElapsedTime(&m, cf.ev[k], cf.ev[k + 1]) == cudaSuccess) cf.ms[k] = m;
+    }
+  const uint32_t total = cf.h_small[0], err = cf.h_small[1];
+  if (err & kCfErrDigit) return fail(ctx, TPC_E_INVAL, "malformed digit (cell outside the pad row or frame, or zero charge)");
+  if (err & kCfErrTwice) return fail(ctx, TPC_E_INVAL, "two digits in one cell");
+  const long long m = total;
+  out->n_clusters = m;
+  if (!to_host) {
+    out->sector = cf.o_sector; out->row = cf.o_row; out->y = cf.o_y; out->w = cf.o_w; out->q_tot = cf.o_qtot;
+    out->q_max = cf.o_qmax; out->sigma_pad = cf.o_sp; out->sigma_time = cf.o_st; out->digit = cf.o_digit;
+    return TPC_OK;
+  }
+  const size_t need = (size_t)std::max<long long>(m, 1) * 28 + 64;
+  if (cf.host_bytes < need) {
+    if (cf.host) cudaFreeHost(cf.host);
+    cf.host = nullptr;
+    cf.host_bytes = 0;
+    if (cudaMallocHost(&cf.host, need + need / 4) != cudaSuccess) {
+      cudaGetLastError();
+      cf.host = nullptr;
+      return fail(ctx, TPC_E_NOMEM, "page-locked cluster copies");
+    }
+    cf.host_bytes = need + need / 4;
+  }
+  char* h = static_cast<char*>(cf.host);
+  size_t o = 0;
+  auto put = [&](const void* src, size_t bytes) -> void* {
+    void* dst = h + o;
+    if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    o = align_up(o + bytes, 4);
+    return dst;
+  };
+  out->y = (const float*)put(cf.o_y, 4 * m);
+  out->w = (const float*)put(cf.o_w, 4 * m);
+  out->sigma_pad = (const float*)put(cf.o_sp, 4 * m);
+  out->sigma_time = (const float*)put(cf.o_st, 4 * m);
+  out->q_tot = (const uint32_t*)put(cf.o_qtot, 4 * m);
+  out->digit = (const uint32_t*)put(cf.o_digit, 4 * m);
+  out->q_max = (const uint16_t*)put(cf.o_qmax, 2 * m);
+  out->sector = (const uint8_t*)put(cf.o_sector, m);
+  out->row = (const uint8_t*)put(cf.o_row, m);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("cluster copies: ") + cudaGetErrorString(e));
+  CK(cudaEventRecord(cf.done, s));
+  return wait_event(ctx, cf.done, 120.0);
+}
+
+int tpc_get_cf_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out) {
+  static const char* names[kCfKernels] = {"cf_fill", "cf_peaks", "cf_scan", "cf_build", "cf_clear"};
+  if (!ctx || !out) return TPC_E_INVAL;
+  out->n_kernels = kCfKernels;
+  out->names = names;
+  out->ms = ctx->cf.ms;
+  out->launches = ctx->cf.launches;
   return TPC_OK;
 }
 

@@ -1,0 +1,145 @@
+"""GPU parity of the cluster finder (tpc_find_clusters) with the FP32 oracle (cf_oracle.c).
+
+Every decision is an integer one (peaks, included cells, sums) and every value a fixed sequence of
+IEEE FP32 operations on both sides, so the clusters must agree bit for bit: same count, same order
+(input order of the peak digits), same bits in every field. Cases: the small pp frame in readout and
+in shuffled order, the Pb-Pb frame of the tracking benchmark, another pad pitch and thresholds,
+edge cells, empty input, malformed input (refused, and the next call still correct), a sequence of
+frames of different lengths on one context, device-resident digits, and digits -> clusters -> tracks
+against the oracle's tracker on the oracle's clusters.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.test_gpu_parity import compare_tracks
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("sector", "row", "y", "w", "q_tot", "q_max", "sigma_pad", "sigma_time", "digit")
+
+
+@pytest.fixture(scope="module")
+def tpc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2009_07515_gb300 as t
+    t.build()
+    return t
+
+
+@pytest.fixture(scope="module")
+def tracker(tpc):
+    tr = tpc.Tracker()
+    yield tr
+    tr.close()
+
+
+def oracle_cf(d, n_time=None, **kw):
+    p = oracle.cf_default_params("f32", **kw)
+    return oracle.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time if n_time is None else n_time,
+                                precision="f32", params=p, n_threads=8)
+
+
+def assert_same(gpu, orc):
+    assert gpu["n_clusters"] == orc["n_clusters"]
+    for k in FIELDS:
+        g = gpu[k]
+        o = orc[k]
+        if g.dtype == np.float32:
+            assert np.array_equal(g.view(np.uint32), o.astype(np.float32).view(np.uint32)), k
+        else:
+            assert np.array_equal(g.astype(np.int64), o.astype(np.int64)), k
+
+
+@pytest.mark.parametrize("shuffle", [0, 1])
+def test_pp_frame_bit_exact(tracker, shuffle):
+    f = synth.generate("pp_500")
+    d = synth.digitize(f, shuffle=shuffle)
+    gpu = tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
+    orc = oracle_cf(d)
+    assert orc["n_clusters"] > 70000
+    assert_same(gpu, orc)
+
+
+def test_pbpb_frame_bit_exact(tracker):
+    f, d = synth.generate_digits("pbpb_2x10000")
+    gpu = tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
+    orc = oracle_cf(d)
+    assert orc["n_clusters"] > 2_500_000
+    assert_same(gpu, orc)
+
+
+def test_other_pitch_and_thresholds(tpc, tracker):
+    f = synth.generate("pp_500", mult_fixed=200, seed=9)
+    d = synth.digitize(f, pad_pitch=0.6, time_bin_w=0.5, sigma_pad=0.4)
+    cp = tpc.cf_default_params(pad_pitch=0.6, time_bin_w=0.5, q_peak_min=6, q_total_min=25)
+    gpu = tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time, cf_params=cp)
+    orc = oracle_cf(d, pad_pitch=0.6, time_bin_w=0.5, q_peak_min=6, q_total_min=25)
+    assert orc["n_clusters"] > 1000
+    assert_same(gpu, orc)
+
+
+def _cells(cells):
+    a = np.array(cells, dtype=np.int64).reshape(-1, 5)
+    return [a[:, i] for i in range(5)]
+
+
+def test_edge_cells_and_small_inputs(tracker):
+    n151 = oracle.n_pads(151)
+    cells = [(35, 151, 0, 0, 20), (35, 151, 1, 0, 10), (35, 151, n151 - 1, 99, 20), (0, 0, 75, 50, 7),
+             (0, 0, 74, 50, 7), (17, 3, 10, 10, 5), (17, 3, 12, 10, 9), (17, 3, 11, 10, 2), (18, 1, 5, 5, 3)]
+    cols = _cells(cells)
+    gpu = tracker.find_clusters(*cols, 100)
+    orc = oracle.find_clusters(*cols, 100, precision="f32")
+    assert orc["n_clusters"] >= 3
+    assert_same(gpu, orc)
+    empty = [np.zeros(0, t) for t in (np.uint8, np.uint8, np.uint16, np.uint16, np.uint16)]
+    assert tracker.find_clusters(*empty, 100)["n_clusters"] == 0
+    one = _cells([(4, 4, 4, 4, 44)])
+    g = tracker.find_clusters(*one, 5)
+    assert_same(g, oracle.find_clusters(*one, 5, precision="f32"))
+
+
+@pytest.mark.parametrize("bad", [(36, 0, 0, 0, 5), (0, 152, 0, 0, 5), (0, 0, 76, 0, 5), (0, 0, 0, 64, 5),
+                                 (0, 0, 0, 0, 0), (0, 0, 3, 3, 4)])
+def test_malformed_digits_are_refused_and_leave_the_map_clean(tpc, tracker, bad):
+    cols = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30), bad])
+    with pytest.raises(tpc.TpcError) as e:
+        tracker.find_clusters(*cols, 64)
+    assert e.value.code == -1
+    ok = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30)])
+    assert_same(tracker.find_clusters(*ok, 64), oracle.find_clusters(*ok, 64, precision="f32"))
+
+
+def test_frames_of_different_lengths_on_one_context(tracker):
+    for seed, frame_us in ((21, 20.0), (22, 90.0), (23, 5.0)):
+        f = synth.generate("serve", n_collisions=2, mult_fixed=300, frame_us=frame_us, seed=seed)
+        d = synth.digitize(f, shuffle=1, seed=seed)
+        assert_same(tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time + 3), oracle_cf(d, d.n_time + 3))
+
+
+def test_device_digits_and_tracking_of_found_clusters(tpc, tracker):
+    import torch
+    f, d = synth.generate_digits("pp_500", seed=12)
+    dev = torch.device("cuda", 0)
+    t = [torch.from_numpy(a.astype(np.int32)).to(dev) for a in (d.sector, d.row, d.pad, d.time, d.adc)]
+    t = [t[0].to(torch.uint8), t[1].to(torch.uint8)] + [x.to(torch.uint16) for x in t[2:]]
+    gpu = tracker.find_clusters(*t, d.n_time)
+    orc = oracle_cf(d)
+    assert_same(gpu, orc)
+    cl = tracker.find_clusters(*t, d.n_time, to_host=False)
+    assert cl.on_device == 1 and cl.n_clusters == orc["n_clusters"]
+    h = tracker.load_cluster_list(cl)
+    try:
+        tracker.track(h)
+        res = tracker.tracks(h)
+    finally:
+        tracker.release(h)
+    trk = oracle.track(orc["sector"], orc["row"], orc["y"].astype(np.float32), orc["w"].astype(np.float32),
+                       precision="f32")
+    assert trk.n_tracks > 300
+    gi, oi = compare_tracks(res, trk)
+    assert len(gi) == trk.n_tracks == res["n_tracks"]
