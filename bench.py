@@ -14,6 +14,9 @@ Keys beyond the base contract:
                 the measured HBM copy bandwidth
   cpu_baseline  the CPU oracle (FP32) on the machine's host cores, on a bounded sample
   kernels_ms    per-kernel device time of one step (CUDA events between launches)
+  cluster_finding  the upstream step on the same frame: its clusters digitized by the generator, the
+                clusters found again from the digits on the GPU (digits/s, kernels, roofline, end to
+                end, digits -> tracks, and the FP32 oracle on a sample)
   --impl reference   times the CPU oracle as the reference arm (this method has no other code)
 Multi-GPU (torchrun): frames are independent, so every rank tracks its own replica of the
 workload on its own GPU with no collective in the data path ("scaling": "weak").
@@ -324,6 +327,107 @@ def compression_benchmark(tpc, torch, d_in, tuned_params: dict, storage: dict, n
                              "absolute_y": bits(np.rint(y * 512)), "absolute_w": bits(np.rint(w * 512))}}
 
 
+# Algorithmic bytes of the cluster-finder kernels: (per digit, per cluster). A digit is 8 bytes
+# (sector, row, pad, time, adc); its map cell 2; a cluster 28 (sector, row, y, w, q_tot, q_max,
+# sigma_pad, sigma_time, digit index), written compacted per warp by the peak kernel and copied to
+# its slot; a count (and its offset) per 32 digits.
+CF_BYTES = {"cf_fill": (8 + 2, 0), "cf_peaks": (8 + 2 + 4.0 / 32, 28), "cf_copy": (8.0 / 32, 28 + 28),
+            "cf_clear": (6 + 2, 0), "cf_scan": (8.0 / 32, 0)}
+
+
+def cluster_finding_benchmark(tpc, synth, torch, workload: str, steps: int = 10, warmup: int = 3,
+                              cpu: bool = True) -> dict:
+    """Cluster finding from the digits of the workload frame (its clusters digitized by the generator):
+    device time of the kernel sequence with digits resident and L2 flushed before each call (CUDA
+    events on the call's stream), the roofline of its dominant kernel, end to end from page-locked
+    host digits to host clusters, digits -> tracks through the device cluster list, and the FP32
+    oracle on a bounded sample of sectors."""
+    import oracle
+    if workload == "full_570":
+        return {"skipped": "digitizing the full-size frame (about 1.5e9 digits) is beyond the host generator"}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f, d = synth.generate_digits(workload)
+    nd = d.n
+    host = [torch.from_numpy(a.astype(np.int32)) for a in (d.sector, d.row, d.pad, d.time, d.adc)]
+    host = [host[0].to(torch.uint8), host[1].to(torch.uint8)] + [x.to(torch.uint16) for x in host[2:]]
+    pinned = [x.pin_memory() for x in host]
+    dv = [x.to(dev) for x in host]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    tr = tpc.Tracker()
+    try:
+        for _ in range(warmup):
+            cl = tr.find_clusters(*dv, d.n_time, to_host=False, stream=stream)
+        nc = int(cl.n_clusters)
+        tr.set_timing(True)
+        per = []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            tr.find_clusters(*dv, d.n_time, to_host=False, stream=stream)
+            per.append(tr.cf_kernel_times())
+        tr.set_timing(False)
+        kern = {k: float(np.median([p[k] for p in per])) for k in per[0]}
+        dev_ms = float(np.median([sum(p.values()) for p in per]))
+        top = max(kern, key=kern.get)
+        bpd, bpc = CF_BYTES[top]
+        alg = bpd * nd + bpc * nc
+        peak, src = _peaks()
+        achieved = alg / (kern[top] * 1e-3) / 1e9
+        # end to end: page-locked host digits in, host cluster copies out
+        for _ in range(2):
+            tr.find_clusters(*pinned, d.n_time, stream=stream)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            out = tr.find_clusters(*pinned, d.n_time, stream=stream, copy=False)
+        e2e_s = (time.perf_counter() - t0) / steps
+        assert out["n_clusters"] == nc
+        # digits -> tracks: device clusters loaded as a frame and tracked
+        def chain():
+            c = tr.find_clusters(*pinned, d.n_time, to_host=False, stream=stream)
+            h = tr.load_cluster_list(c)
+            tr.track(h)
+            r = tr.tracks(h)
+            tr.release(h)
+            return r
+        chain()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            r = chain()
+        chain_s = (time.perf_counter() - t0) / 3
+    finally:
+        tr.close()
+    line = {"metric": "TPC digits clustered per second", "unit": "digits/s", "value": nd / (dev_ms * 1e-3),
+            "ms": dev_ms, "digits": nd, "clusters": nc, "time_bins": d.n_time,
+            "data": f"synthetic: the {workload} clusters digitized (0.4 cm pads, 0.2 us bins, 0.3 cm spread), "
+                    "in readout order (grouped by sector and row, time-major)",
+            "l2": "flushed (512 MB write) before each call", "kernels_ms": kern,
+            "roofline": {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src, "algorithmic_bytes": alg,
+                         "bytes_per_digit": bpd, "bytes_per_cluster": bpc, "traffic": None},
+            "e2e": {"value": nd / e2e_s, "unit": "digits/s", "ms": e2e_s * 1e3, "h2d_bytes_per_step": 8 * nd,
+                    "d2h_bytes_per_step": 28 * nc},
+            "digits_to_tracks": {"ms": chain_s * 1e3, "tracks": int(r["n_tracks"]),
+                                 "value": nd / chain_s, "unit": "digits/s"},
+            "gpu_launches": 7 * steps}
+    if not cpu:
+        return line
+    # FP32 oracle on whole sectors (about 10 s on one core)
+    m0 = d.sector == 0
+    t0 = time.perf_counter()
+    oracle.find_clusters(d.sector[m0], d.row[m0], d.pad[m0], d.time[m0], d.adc[m0], d.n_time, precision="f32",
+                         n_threads=1)
+    per_sector = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(36, max(1, 10.0 / per_sector)))
+    m = d.sector < k
+    t0 = time.perf_counter()
+    oracle.find_clusters(d.sector[m], d.row[m], d.pad[m], d.time[m], d.adc[m], d.n_time, precision="f32", n_threads=1)
+    cpu_s = time.perf_counter() - t0
+    line["cpu_baseline"] = {"value": int(m.sum()) / cpu_s, "unit": "digits/s", "cores": 1, "kind": "oracle",
+                            "sample": f"sectors 0-{k - 1} ({int(m.sum())} digits), FP32 oracle, {cpu_s:.2f} s"}
+    return line
+
+
 def batched_benchmark(tpc, synth, torch, *, n_frames: int = 16, steps: int = 5, packed: bool = True) -> dict:
     """The batched path: n_frames frames of uneven occupancy (Poisson(5) collisions, exponential
     multiplicity) tracked by one batched graph launch (tpc_track_batch) with launch shapes autotuned
@@ -414,6 +518,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-frame batched-path measurement")
     ap.add_argument("--no-compression", action="store_true", help="skip the compression-inputs measurement")
+    ap.add_argument("--no-cluster-finding", action="store_true", help="skip the cluster-finding measurement")
+    ap.add_argument("--cf-only", action="store_true", help="run only the cluster-finding measurement")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "packed"],
                     help="cluster storage of the main workload: FP32 or 16-bit fixed point")
     ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
@@ -442,6 +548,12 @@ def main():
     __graft_entry__.build()
     import synth
     import paper_2009_07515_gb300 as tpc
+
+    if args.cf_only:
+        # the cluster-finding measurement alone (for profiling its kernels)
+        print(json.dumps(cluster_finding_benchmark(tpc, synth, torch, args.workload, steps=args.steps,
+                                                   warmup=args.warmup, cpu=not args.no_cpu_baseline)), flush=True)
+        return
 
     frame = synth.generate(args.workload)
     n = frame.n
@@ -590,6 +702,8 @@ def main():
     tr.release(h)
     if not args.no_compression:
         line["compression"] = compression_benchmark(tpc, torch, d_in, tuned_params, storage, n)
+    if not args.no_cluster_finding:
+        line["cluster_finding"] = cluster_finding_benchmark(tpc, synth, torch, args.workload)
     if not args.no_batched:
         line["batched"] = batched_benchmark(tpc, synth, torch)
     if not args.no_serving:

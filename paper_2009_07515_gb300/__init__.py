@@ -152,10 +152,11 @@ class Tracker:
 
     # --------------------------------------------------------------- cluster finding
     def find_clusters(self, sector, row, pad, time, adc, n_time: int, *, to_host: bool = True,
-                      cf_params: _lib.tpc_cf_params | None = None, stream=None):
+                      cf_params: _lib.tpc_cf_params | None = None, stream=None, copy: bool = True):
         """Clusters of one frame's digits (tpc_find_clusters). Digit arrays: numpy (host) or torch
-        CUDA tensors (device). to_host=True returns numpy copies; to_host=False returns the raw
-        tpc_cluster_list of device arrays, valid until the next call (see load_cluster_list)."""
+        CUDA tensors (device). to_host=True returns numpy arrays (copies, or with copy=False views
+        valid until the next call); to_host=False returns the raw tpc_cluster_list of device arrays,
+        valid until the next call (see load_cluster_list)."""
         keep = []
         arrs = []
         for a, dt in ((sector, np.uint8), (row, np.uint8), (pad, np.uint16), (time, np.uint16), (adc, np.uint16)):
@@ -172,7 +173,7 @@ class Tracker:
         s = ctypes.c_void_p(stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream)
         cp = ctypes.byref(cf_params) if cf_params is not None else None
         self._check(self.lib.tpc_find_clusters(self.ctx, cp, ctypes.byref(d), 1 if to_host else 0, ctypes.byref(out), s))
-        return _lib.clusters_to_numpy(out) if to_host else out
+        return _lib.clusters_to_numpy(out, copy=copy) if to_host else out
 
     def load_cluster_list(self, cl: _lib.tpc_cluster_list) -> int:
         """Load the device clusters of find_clusters(to_host=False) as a frame (borrowed: track it

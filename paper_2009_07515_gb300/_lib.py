@@ -169,8 +169,9 @@ CLUSTER_FIELDS = (("sector", np.uint8), ("row", np.uint8), ("y", np.float32), ("
                   ("sigma_time", np.float32), ("digit", np.uint32))
 
 
-def clusters_to_numpy(c: tpc_cluster_list) -> dict:
-    """Copies of a host cluster list (to_host = 1) as numpy arrays."""
+def clusters_to_numpy(c: tpc_cluster_list, copy: bool = True) -> dict:
+    """numpy arrays of a host cluster list (to_host = 1): copies, or (copy=False) views of the
+    context's page-locked block, valid until its next tpc_find_clusters call."""
     if c.on_device:
         raise ValueError("the cluster list holds device pointers")
     n = int(c.n_clusters)
@@ -181,7 +182,8 @@ def clusters_to_numpy(c: tpc_cluster_list) -> dict:
             out[name] = np.zeros(0, dt)
         else:
             buf = (ctypes.c_char * (n * np.dtype(dt).itemsize)).from_address(ptr)
-            out[name] = np.frombuffer(buf, dtype=dt).copy()
+            a = np.frombuffer(buf, dtype=dt)
+            out[name] = a.copy() if copy else a
     return out
 
 

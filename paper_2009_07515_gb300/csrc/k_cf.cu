@@ -13,11 +13,14 @@
 // The charge map is dense per (sector, row) and lives in HBM across calls, zero between them:
 // only the cells of the frame's digits are written, read and cleared, so a frame costs traffic in
 // proportion to its digits, not to the map. Kernels (persistent, tiles of 256 digits):
-//   k_cf_fill   validate each digit and OR its charge into its cell (a 32-bit atomic on the cell's
-//               word; a nonzero old half is a second digit in the same cell)
-//   k_cf_peaks  peak test and cluster charge; one bit per digit, kept clusters per tile
-//   (exclusive scan of the tile counts: each tile's first output slot)
-//   k_cf_build  each kept peak recomputes its sums and writes its cluster at its ordered slot
+//   k_cf_fill   validate each digit and add its charge into its cell (a 32-bit reduction on the
+//               cell's word, nothing waits for it)
+//   k_cf_peaks  each digit checks that its cell holds its own charge (else a second digit shares
+//               the cell), the peak test, the cluster of a kept peak; each warp writes its kept
+//               clusters compacted in digit order into its block's region of a temporary array
+//               (slots taken from a shared-memory counter), their first slot and their count
+//   (exclusive scan of the per-warp counts: each warp's first output slot)
+//   k_cf_copy   the clusters of each 32 digits move to their output slots (coalesced stores)
 //   k_cf_clear  zero the cells of the valid digits, leaving the map clean for the next call
 #include "tpc_dev.cuh"
 
@@ -92,76 +95,105 @@ __global__ void __launch_bounds__(kCfTile) k_cf_fill(CfArgs A) {
       continue;
     }
     const size_t c = cf_cell(A, s, r, k, j);
-    const uint32_t sh = (uint32_t)(c & 1) * 16u;
-    const uint32_t old = atomicOr(reinterpret_cast<uint32_t*>(A.map) + (c >> 1), (uint32_t)q << sh);
-    if ((old >> sh) & 0xFFFFu) bad |= kCfErrTwice;
+    atomicAdd(reinterpret_cast<uint32_t*>(A.map) + (c >> 1), (uint32_t)q << ((uint32_t)(c & 1) * 16u));
   }
   if (bad) atomicOr(A.err, bad);
 }
 
 __global__ void __launch_bounds__(kCfTile) k_cf_peaks(CfArgs A) {
-  __shared__ uint32_t wc[kCfTile / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ uint32_t used;  // temporary slots taken in this block's region
+  const int lane = threadIdx.x & 31;
   const long long ntiles = (A.n + kCfTile - 1) / kCfTile;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long i = t * kCfTile + threadIdx.x;
+  // the block's region: as many slots as the digits of its tiles (blockIdx.x + k * gridDim.x)
+  const uint32_t region = (uint32_t)(blockIdx.x * ((ntiles + gridDim.x - 1) / gridDim.x) * kCfTile);
+  if (threadIdx.x == 0) used = 0;
+  __syncthreads();
+  uint32_t bad = 0;
+  // warp-uniform trip count (block-aligned bases): every lane takes part in the warp's compaction
+  for (long long base = (long long)blockIdx.x * kCfTile; base < A.n; base += (long long)gridDim.x * kCfTile) {
+    const long long i = base + threadIdx.x;
     bool keep = false;
-    int s, r, k, j, q;
-    if (i < A.n && cf_digit(A, i, s, r, k, j, q) && q >= A.q_peak_min) {
+    int s = 0, r = 0, k = 0, j = 0, q = 0;
+    CfSums S{0, 0, 0, 0, 0};
+    if (i < A.n && cf_digit(A, i, s, r, k, j, q)) {
       const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
-      if (cf_is_peak(m, A.stride, q)) keep = cf_sums(m, A.stride).Q >= A.q_total_min;
+      if ((int)__ldg(m) != q) bad |= kCfErrTwice;
+      if (q >= A.q_peak_min && cf_is_peak(m, A.stride, q)) {
+        S = cf_sums(m, A.stride);
+        keep = S.Q >= A.q_total_min;
+      }
     }
     const uint32_t b = __ballot_sync(0xffffffffu, keep);
-    const long long wbase = t * kCfTile + warp * 32;
-    if (lane == 0) {
-      if (wbase < A.n) A.mask[wbase >> 5] = b;
-      wc[warp] = (uint32_t)__popc(b);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t c = 0;
-#pragma unroll
-      for (int w = 0; w < kCfTile / 32; ++w) c += wc[w];
-      A.tcount[t] = c;
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(kCfTile) k_cf_build(CfArgs A) {
-  __shared__ uint32_t wc[kCfTile / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long ntiles = (A.n + kCfTile - 1) / kCfTile;
-  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long long wbase = t * kCfTile + warp * 32;
-    const uint32_t b = wbase < A.n ? A.mask[wbase >> 5] : 0u;
-    if (lane == 0) wc[warp] = (uint32_t)__popc(b);
-    __syncthreads();
-    uint32_t off = A.toff[t];
-    for (int w = 0; w < warp; ++w) off += wc[w];
-    __syncthreads();
-    if ((b >> lane) & 1u) {
-      const long long i = wbase + lane;
-      const int s = A.sector[i], r = A.row[i], k = A.pad[i], j = A.time[i];
-      const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
-      const CfSums S = cf_sums(m, A.stride);
-      const uint32_t o = off + (uint32_t)__popc(b & ((1u << lane) - 1u));
+    const long long wbase = i - lane;
+    uint32_t first = 0;
+    if (lane == 0 && b) first = region + atomicAdd(&used, (uint32_t)__popc(b));
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (keep) {
+      const uint32_t o = first + (uint32_t)__popc(b & ((1u << lane) - 1u));
       const float Qf = (float)S.Q;
       const float mk = __fdiv_rn((float)S.Sk, Qf), mj = __fdiv_rn((float)S.Sj, Qf);
       const float pc = __fadd_rn((float)k, mk), tc = __fadd_rn((float)j, mj);
       const float centre = __fsub_rn((float)((int)__ldg(A.npads + r) / 2), 0.5f);
       const float vk = __fsub_rn(__fdiv_rn((float)S.Skk, Qf), __fmul_rn(mk, mk));
       const float vj = __fsub_rn(__fdiv_rn((float)S.Sjj, Qf), __fmul_rn(mj, mj));
-      A.o_sector[o] = (uint8_t)s;
-      A.o_row[o] = (uint8_t)r;
-      A.o_y[o] = __fmul_rn(__fsub_rn(pc, centre), A.pitch);
-      A.o_w[o] = __fmul_rn(__fadd_rn(tc, 0.5f), A.dw);
-      A.o_qtot[o] = (uint32_t)S.Q;
-      A.o_qmax[o] = A.adc[i];
-      A.o_sig_pad[o] = vk > 0.f ? __fsqrt_rn(vk) : 0.f;
-      A.o_sig_time[o] = vj > 0.f ? __fsqrt_rn(vj) : 0.f;
-      A.o_digit[o] = (uint32_t)i;
+      A.t_sector[o] = (uint8_t)s;
+      A.t_row[o] = (uint8_t)r;
+      A.t_y[o] = __fmul_rn(__fsub_rn(pc, centre), A.pitch);
+      A.t_w[o] = __fmul_rn(__fadd_rn(tc, 0.5f), A.dw);
+      A.t_qtot[o] = (uint32_t)S.Q;
+      A.t_qmax[o] = (uint16_t)q;
+      A.t_sig_pad[o] = vk > 0.f ? __fsqrt_rn(vk) : 0.f;
+      A.t_sig_time[o] = vj > 0.f ? __fsqrt_rn(vj) : 0.f;
+      A.t_digit[o] = (uint32_t)i;
     }
+    if (lane == 0 && wbase < A.n) {
+      A.wcount[wbase >> 5] = (uint32_t)__popc(b);
+      A.wsrc[wbase >> 5] = first;
+    }
+  }
+  if (bad) atomicOr(A.err, bad);
+}
+
+// The kept clusters of each 32 digits (a group), compacted from their temporary slot on, move to
+// their output slots. A warp takes 32 consecutive groups, whose output slots are consecutive: each lane
+// lists the source slots of its group's clusters in shared memory at their output positions, then
+// the warp copies in output order, so the stores of each field are coalesced.
+__global__ void __launch_bounds__(kCfTile) k_cf_copy(CfArgs A) {
+  __shared__ uint32_t srcs[kCfTile / 32][32 * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* sl = srcs[warp];
+  const long long ng = (A.n + 31) / 32;
+  const long long step = (long long)gridDim.x * kCfTile;
+  // block-aligned bases: the trip count is warp-uniform
+  for (long long base = (long long)blockIdx.x * kCfTile; base < ng; base += step) {
+    const long long g = base + threadIdx.x;
+    const long long g0 = g - lane;
+    if (g0 >= ng) continue;  // warp-uniform
+    const uint32_t cnt = g < ng ? A.wcount[g] : 0u, off = g < ng ? A.woff[g] : 0u;
+    const uint32_t first = __shfl_sync(0xffffffffu, off, 0);
+    uint32_t x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, x, 31);
+    const uint32_t src0 = g < ng ? A.wsrc[g] : 0u;
+    for (uint32_t r = 0; r < cnt; ++r) sl[off - first + r] = src0 + r;
+    __syncwarp();
+    for (uint32_t q = lane; q < total; q += 32) {
+      const uint32_t src = sl[q], dst = first + q;
+      A.o_sector[dst] = A.t_sector[src];
+      A.o_row[dst] = A.t_row[src];
+      A.o_y[dst] = A.t_y[src];
+      A.o_w[dst] = A.t_w[src];
+      A.o_qtot[dst] = A.t_qtot[src];
+      A.o_qmax[dst] = A.t_qmax[src];
+      A.o_sig_pad[dst] = A.t_sig_pad[src];
+      A.o_sig_time[dst] = A.t_sig_time[src];
+      A.o_digit[dst] = A.t_digit[src];
+    }
+    __syncwarp();
   }
 }
 

@@ -65,7 +65,7 @@ __global__ void k_set_ntracklets(Work);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
 __global__ void k_cf_fill(CfArgs);
 __global__ void k_cf_peaks(CfArgs);
-__global__ void k_cf_build(CfArgs);
+__global__ void k_cf_copy(CfArgs);
 __global__ void k_cf_clear(CfArgs);
 
 // Cluster finding: device buffers sized by a digit capacity, the charge map (kept zero between
@@ -76,7 +76,11 @@ struct CfState {
   long long cap = 0;
   uint8_t *in_sector = nullptr, *in_row = nullptr;
   uint16_t *in_pad = nullptr, *in_time = nullptr, *in_adc = nullptr;
-  uint32_t *mask = nullptr, *tcount = nullptr, *toff = nullptr, *scan_tmp = nullptr, *small = nullptr;
+  uint32_t *wcount = nullptr, *woff = nullptr, *wsrc = nullptr, *scan_tmp = nullptr, *small = nullptr;
+  uint8_t *t_sector = nullptr, *t_row = nullptr;
+  float *t_y = nullptr, *t_w = nullptr, *t_sp = nullptr, *t_st = nullptr;
+  uint32_t *t_qtot = nullptr, *t_digit = nullptr;
+  uint16_t* t_qmax = nullptr;
   uint16_t* npads = nullptr;
   uint8_t *o_sector = nullptr, *o_row = nullptr;
   float *o_y = nullptr, *o_w = nullptr, *o_sp = nullptr, *o_st = nullptr;
@@ -920,7 +924,8 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
   CfState& cf = ctx->cf;
   if (cf.dev && cf.cap >= n) return TPC_OK;
   const long long cap = std::max<long long>(n + n / 8, 1 << 16);
-  const long long tiles = (cap + kCfTile - 1) / kCfTile;
+  // temporary slots: the peak kernel's blocks (at most 8 per SM) each own a region of whole tiles
+  const long long nw = (cap + 31) / 32, cap32 = nw * 32 + (long long)ctx->sms * 8 * kCfTile;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -928,8 +933,11 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
     return o;
   };
   const size_t o_is = take(cap), o_ir = take(cap), o_ip = take(2 * cap), o_it = take(2 * cap), o_ia = take(2 * cap);
-  const size_t o_mask = take(4 * ((cap + 31) / 32)), o_tc = take(4 * tiles), o_to = take(4 * (tiles + 1));
-  const size_t o_tmp = take(4 * (tiles / 2048 + 2)), o_small = take(16), o_np = take(2 * kNRow);
+  const size_t o_wc = take(4 * nw), o_wo = take(4 * (nw + 1)), o_ws = take(4 * nw);
+  const size_t o_tmp = take(4 * (nw / 2048 + 2)), o_small = take(16), o_np = take(2 * kNRow);
+  const size_t t_s = take(cap32), t_r = take(cap32), t_y = take(4 * cap32), t_w = take(4 * cap32);
+  const size_t t_sp = take(4 * cap32), t_st = take(4 * cap32), t_q = take(4 * cap32), t_d = take(4 * cap32);
+  const size_t t_qm = take(2 * cap32);
   const size_t o_os = take(cap), o_or = take(cap), o_y = take(4 * cap), o_w = take(4 * cap), o_sp = take(4 * cap);
   const size_t o_st = take(4 * cap), o_q = take(4 * cap), o_d = take(4 * cap), o_qm = take(2 * cap);
   if (cf.dev) {
@@ -948,9 +956,18 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
   cf.in_pad = (uint16_t*)(b + o_ip);
   cf.in_time = (uint16_t*)(b + o_it);
   cf.in_adc = (uint16_t*)(b + o_ia);
-  cf.mask = (uint32_t*)(b + o_mask);
-  cf.tcount = (uint32_t*)(b + o_tc);
-  cf.toff = (uint32_t*)(b + o_to);
+  cf.wcount = (uint32_t*)(b + o_wc);
+  cf.woff = (uint32_t*)(b + o_wo);
+  cf.wsrc = (uint32_t*)(b + o_ws);
+  cf.t_sector = (uint8_t*)(b + t_s);
+  cf.t_row = (uint8_t*)(b + t_r);
+  cf.t_y = (float*)(b + t_y);
+  cf.t_w = (float*)(b + t_w);
+  cf.t_sp = (float*)(b + t_sp);
+  cf.t_st = (float*)(b + t_st);
+  cf.t_qtot = (uint32_t*)(b + t_q);
+  cf.t_digit = (uint32_t*)(b + t_d);
+  cf.t_qmax = (uint16_t*)(b + t_qm);
   cf.scan_tmp = (uint32_t*)(b + o_tmp);
   cf.small = (uint32_t*)(b + o_small);
   cf.npads = (uint16_t*)(b + o_np);
@@ -1745,9 +1762,11 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
   A.pitch = (float)P.pad_pitch;
   A.dw = (float)P.time_bin_w;
   A.map = cf.map;
-  A.mask = cf.mask;
-  A.tcount = cf.tcount;
-  A.toff = cf.toff;
+  A.wcount = cf.wcount;
+  A.woff = cf.woff;
+  A.wsrc = cf.wsrc;
+  A.t_sector = cf.t_sector; A.t_row = cf.t_row; A.t_y = cf.t_y; A.t_w = cf.t_w; A.t_qtot = cf.t_qtot;
+  A.t_qmax = cf.t_qmax; A.t_sig_pad = cf.t_sp; A.t_sig_time = cf.t_st; A.t_digit = cf.t_digit;
   A.err = cf.small + 1;
   A.o_sector = cf.o_sector; A.o_row = cf.o_row; A.o_y = cf.o_y; A.o_w = cf.o_w; A.o_qtot = cf.o_qtot;
   A.o_qmax = cf.o_qmax; A.o_sig_pad = cf.o_sp; A.o_sig_time = cf.o_st; A.o_digit = cf.o_digit;
@@ -1763,11 +1782,13 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
   if (timing) cudaEventRecord(cf.ev[1], s);
   k_cf_peaks<<<grid, kCfTile, 0, s>>>(A);
   if (timing) cudaEventRecord(cf.ev[2], s);
-  k_scan_reduce<<<2 * G, 256, 0, s>>>(cf.tcount, nullptr, tiles, 0, cf.scan_tmp);
-  k_scan_tiles<<<1, 1024, 0, s>>>(cf.scan_tmp, nullptr, tiles, 0, cf.small);
-  k_scan_apply<<<2 * G, 256, 0, s>>>(cf.tcount, nullptr, tiles, 0, cf.scan_tmp, cf.small, cf.toff);
+  const long long nwarps = (n + 31) / 32;
+  k_scan_reduce<<<2 * G, 256, 0, s>>>(cf.wcount, nullptr, nwarps, 0, cf.scan_tmp);
+  k_scan_tiles<<<1, 1024, 0, s>>>(cf.scan_tmp, nullptr, nwarps, 0, cf.small);
+  k_scan_apply<<<2 * G, 256, 0, s>>>(cf.wcount, nullptr, nwarps, 0, cf.scan_tmp, cf.small, cf.woff);
   if (timing) cudaEventRecord(cf.ev[3], s);
-  k_cf_build<<<grid, kCfTile, 0, s>>>(A);
+  k_cf_copy<<<(int)std::min<long long>((nwarps + kCfTile - 1) / kCfTile, (long long)G * (2048 / kCfTile)), kCfTile, 0,
+              s>>>(A);
   if (timing) cudaEventRecord(cf.ev[4], s);
   k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
   if (timing) cudaEventRecord(cf.ev[5], s);
@@ -1787,7 +1808,10 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
     }
   const uint32_t total = cf.h_small[0], err = cf.h_small[1];
   if (err & kCfErrDigit) return fail(ctx, TPC_E_INVAL, "malformed digit (cell outside the pad row or frame, or zero charge)");
-  if (err & kCfErrTwice) return fail(ctx, TPC_E_INVAL, "two digits in one cell");
+  if (err & kCfErrTwice) {
+    cf.map_clean = false;  // charges of one cell added up and may have carried into the next cell
+    return fail(ctx, TPC_E_INVAL, "two digits in one cell");
+  }
   const long long m = total;
   out->n_clusters = m;
   if (!to_host) {
@@ -1831,7 +1855,7 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
 }
 
 int tpc_get_cf_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out) {
-  static const char* names[kCfKernels] = {"cf_fill", "cf_peaks", "cf_scan", "cf_build", "cf_clear"};
+  static const char* names[kCfKernels] = {"cf_fill", "cf_peaks", "cf_scan", "cf_copy", "cf_clear"};
   if (!ctx || !out) return TPC_E_INVAL;
   out->n_kernels = kCfKernels;
   out->names = names;

@@ -536,10 +536,21 @@ struct CfArgs {
   int q_peak_min, q_total_min;
   float pitch, dw;
   uint16_t* map;
-  uint32_t* mask;     // [ceil(n / 32)] bit per digit: a kept cluster's peak
-  uint32_t* tcount;   // [tiles] kept clusters per tile
-  uint32_t* toff;     // [tiles] exclusive scan of tcount
+  uint32_t* wcount;   // [ceil(n / 32)] kept clusters per 32 digits (one warp's digits)
+  uint32_t* woff;     // [ceil(n / 32) + 1] exclusive scan of wcount: their first output slot
+  uint32_t* wsrc;     // [ceil(n / 32)] first temporary slot of their clusters
   uint32_t* err;
+  // the kept clusters of each 32 digits, in digit order from slot wsrc on (each block of the peak
+  // kernel fills its own region of the temporary arrays)
+  uint8_t* t_sector;
+  uint8_t* t_row;
+  float* t_y;
+  float* t_w;
+  uint32_t* t_qtot;
+  uint16_t* t_qmax;
+  float* t_sig_pad;
+  float* t_sig_time;
+  uint32_t* t_digit;
   // clusters, in the input order of their peak digits
   uint8_t* o_sector;
   uint8_t* o_row;
