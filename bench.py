@@ -91,6 +91,11 @@ def _method_defaults(tpc) -> dict:
     return {k: (list(getattr(p, k)) if k == "cov0" else getattr(p, k)) for k in keys}
 
 
+def _cf_defaults(tpc) -> dict:
+    p = tpc.cf_default_params()
+    return {k: getattr(p, k) for k in ("pad_pitch", "time_bin_w", "q_peak_min", "q_total_min")}
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -404,7 +409,8 @@ def cluster_finding_benchmark(tpc, synth, torch, workload: str, steps: int = 10,
             "l2": "flushed (512 MB write) before each call", "kernels_ms": kern,
             "roofline": {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src, "algorithmic_bytes": alg,
-                         "bytes_per_digit": bpd, "bytes_per_cluster": bpc, "traffic": None},
+                         "bytes_per_digit": bpd, "bytes_per_cluster": bpc,
+                         **_traffic_fields(top, workload, {}, _cf_defaults(tpc))},
             "e2e": {"value": nd / e2e_s, "unit": "digits/s", "ms": e2e_s * 1e3, "h2d_bytes_per_step": 8 * nd,
                     "d2h_bytes_per_step": 28 * nc},
             "digits_to_tracks": {"ms": chain_s * 1e3, "tracks": int(r["n_tracks"]),

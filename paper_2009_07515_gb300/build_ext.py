@@ -39,7 +39,8 @@ def _stale(out: str, deps: list[str]) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "tpc_dev.cuh"), os.path.join(ROOT, "include", "tpctrack.h"), __file__]
+    headers = [os.path.join(CSRC, "tpc_dev.cuh"), os.path.join(CSRC, "cf_dev.cuh"), os.path.join(ROOT, "include", "tpctrack.h"),
+               __file__]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

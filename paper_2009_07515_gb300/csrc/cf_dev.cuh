@@ -1,0 +1,54 @@
+// cf_dev.cuh — device-side definitions of the cluster finder (k_cf.cu, sm_103a).
+#pragma once
+#include "tpc_dev.cuh"
+
+namespace tpc {
+
+// Arguments of the cluster-finder kernels (k_cf.cu). The charge map holds one plane per
+// (sector, row): lines = n_time + 4 time lines of `stride` u16 cells, cell (k, j) at
+// (j + 2) * stride + (k + 2); the two guard lines and guard pads on each side are never written,
+// so every 5x5 window read stays inside the plane and sees 0 outside the row.
+constexpr int kCfTile = 256;          // digits per block iteration (8 warps)
+constexpr int kCfGuard = 2;
+constexpr uint32_t kCfErrDigit = 1u;  // a digit outside the pad row / frame, or with zero charge
+constexpr uint32_t kCfErrTwice = 2u;  // two digits in one cell
+struct CfArgs {
+  const uint8_t* sector;
+  const uint8_t* row;
+  const uint16_t* pad;
+  const uint16_t* time;
+  const uint16_t* adc;
+  long long n;
+  int n_time, lines, stride;
+  int q_peak_min, q_total_min;
+  float pitch, dw;
+  uint16_t* map;
+  uint32_t* wcount;   // [ceil(n / 32)] kept clusters per 32 digits (one warp's digits)
+  uint32_t* woff;     // [ceil(n / 32) + 1] exclusive scan of wcount: their first output slot
+  uint32_t* wsrc;     // [ceil(n / 32)] first temporary slot of their clusters
+  uint32_t* err;
+  // the kept clusters of each 32 digits, in digit order from slot wsrc on (each block of the peak
+  // kernel fills its own region of the temporary arrays)
+  uint8_t* t_sector;
+  uint8_t* t_row;
+  float* t_y;
+  float* t_w;
+  uint32_t* t_qtot;
+  uint16_t* t_qmax;
+  float* t_sig_pad;
+  float* t_sig_time;
+  uint32_t* t_digit;
+  // clusters, in the input order of their peak digits
+  uint8_t* o_sector;
+  uint8_t* o_row;
+  float* o_y;
+  float* o_w;
+  uint32_t* o_qtot;
+  uint16_t* o_qmax;
+  float* o_sig_pad;
+  float* o_sig_time;
+  uint32_t* o_digit;
+  const uint16_t* npads;  // [kNRow] pads of each row
+};
+
+}  // namespace tpc

@@ -22,7 +22,7 @@
 //   (exclusive scan of the per-warp counts: each warp's first output slot)
 //   k_cf_copy   the clusters of each 32 digits move to their output slots (coalesced stores)
 //   k_cf_clear  zero the cells of the valid digits, leaving the map clean for the next call
-#include "tpc_dev.cuh"
+#include "cf_dev.cuh"
 
 namespace tpc {
 
@@ -86,7 +86,7 @@ __device__ __forceinline__ CfSums cf_sums(const uint16_t* m, int stride) {
   return S;
 }
 
-__global__ void __launch_bounds__(kCfTile) k_cf_fill(CfArgs A) {
+__global__ void __launch_bounds__(kCfTile, 8) k_cf_fill(CfArgs A) {
   uint32_t bad = 0;
   for (long long i = (long long)blockIdx.x * kCfTile + threadIdx.x; i < A.n; i += (long long)gridDim.x * kCfTile) {
     int s, r, k, j, q;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kCfTile) k_cf_peaks(CfArgs A) {
 // their output slots. A warp takes 32 consecutive groups, whose output slots are consecutive: each lane
 // lists the source slots of its group's clusters in shared memory at their output positions, then
 // the warp copies in output order, so the stores of each field are coalesced.
-__global__ void __launch_bounds__(kCfTile) k_cf_copy(CfArgs A) {
+__global__ void __launch_bounds__(kCfTile, 8) k_cf_copy(CfArgs A) {
   __shared__ uint32_t srcs[kCfTile / 32][32 * 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* sl = srcs[warp];

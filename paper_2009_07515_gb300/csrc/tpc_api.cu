@@ -19,7 +19,7 @@
 #include <thread>
 #include <vector>
 
-#include "tpc_dev.cuh"
+#include "cf_dev.cuh"
 #include "tpctrack.h"
 
 namespace tpc {
