@@ -57,6 +57,17 @@ def test_params_struct_layout_and_defaults(lib):
     assert list(p.cov0) == list(o.cov0)
 
 
+def test_cluster_finder_defaults_equal_the_oracle(lib):
+    """The cluster finder's default parameters are the oracle's (the same reading of the step)."""
+    import oracle
+    from paper_2009_07515_gb300 import _lib
+    p = _lib.cf_default_params()
+    o = oracle.cf_default_params("f32")
+    for k in ("pad_pitch", "time_bin_w", "q_peak_min", "q_total_min"):
+        assert getattr(p, k) == getattr(o, k), k
+    assert lib.tpc_find_clusters(None, None, None, 0, None, None) == -1
+
+
 def test_host_calls_without_gpu(lib):
     """Calls that need no device: version string, error paths on null arguments."""
     assert b"tpctrack" in lib.tpc_version()

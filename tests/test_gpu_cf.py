@@ -143,3 +143,44 @@ def test_device_digits_and_tracking_of_found_clusters(tpc, tracker):
     assert trk.n_tracks > 300
     gi, oi = compare_tracks(res, trk)
     assert len(gi) == trk.n_tracks == res["n_tracks"]
+
+
+def test_long_frame(tracker):
+    """A frame of several thousand time bins (a long drift window at low occupancy)."""
+    f = synth.generate("serve", n_collisions=3, mult_fixed=200, frame_us=900.0, seed=31)
+    d = synth.digitize(f, shuffle=1, seed=31)
+    assert d.n_time > 4000
+    assert_same(tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time), oracle_cf(d))
+
+
+def test_charge_map_beyond_the_budget_is_refused(tpc):
+    """The map of 36 x 152 x (n_time + 4) x stride cells must fit half of the HBM budget."""
+    f = synth.generate("pp_500", mult_fixed=20, seed=32)
+    d = synth.digitize(f)
+    tr = tpc.Tracker(hbm_budget=4 << 30)
+    try:
+        with pytest.raises(tpc.TpcError) as e:
+            tr.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, 60000)
+        assert e.value.code == -3
+        assert_same(tr.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time), oracle_cf(d))
+    finally:
+        tr.close()
+
+
+def test_tracks_from_found_clusters_match_tracks_from_generated_clusters(tracker):
+    """Physics check of the whole chain on the Pb-Pb frame: the tracks of the found clusters are as
+    many as the tracks of the generator's clusters (within 3%), and nearly every track found from
+    the digits has its peaks from one generated track."""
+    f, d = synth.generate_digits("pbpb_2x10000", truth=True)
+    c = tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
+    t_dig = tracker.run(c["sector"], c["row"], c["y"], c["w"])
+    t_gen = tracker.run(f.sector, f.row, f.y, f.w)
+    assert abs(t_dig["n_tracks"] - t_gen["n_tracks"]) < 0.03 * t_gen["n_tracks"]
+    src = f.truth_track[d.truth_cluster[c["digit"]]]
+    off, hits = t_dig["hit_offset"], t_dig["hit_index"]
+    pure = 0
+    for i in range(t_dig["n_tracks"]):
+        tt = src[hits[off[i]:off[i + 1]]]
+        vals, cnt = np.unique(tt, return_counts=True)
+        pure += cnt.max() >= 0.9 * len(tt) and vals[cnt.argmax()] >= 0
+    assert pure >= 0.95 * t_dig["n_tracks"]
