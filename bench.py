@@ -709,7 +709,8 @@ def main():
     if not args.no_compression:
         line["compression"] = compression_benchmark(tpc, torch, d_in, tuned_params, storage, n)
     if not args.no_cluster_finding:
-        line["cluster_finding"] = cluster_finding_benchmark(tpc, synth, torch, args.workload)
+        line["cluster_finding"] = cluster_finding_benchmark(
+            tpc, synth, torch, args.workload, cpu=rank == 0 and ws == 1 and not args.no_cpu_baseline)
     if not args.no_batched:
         line["batched"] = batched_benchmark(tpc, synth, torch)
     if not args.no_serving:
