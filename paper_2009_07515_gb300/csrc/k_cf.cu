@@ -40,42 +40,50 @@ __device__ __forceinline__ size_t cf_cell(const CfArgs& A, int s, int r, int k, 
          (size_t)(k + kCfGuard);
 }
 
-// c beats its 3x3 neighbours: earlier ones (in (time, pad) order) strictly, later ones or ties
-__device__ __forceinline__ bool cf_is_peak(const uint16_t* m, int stride, int q) {
+// the 3x3 window around a cell, w[dj + 1][dk + 1]
+__device__ __forceinline__ void cf_window3(const uint16_t* m, int stride, int w[3][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) w[a][b] = __ldg(m + (a - 1) * stride + (b - 1));
+}
+
+// the centre beats its 3x3 neighbours: earlier ones (in (time, pad) order) strictly, later ones or ties
+__device__ __forceinline__ bool cf_is_peak3(const int w[3][3]) {
+  const int q = w[1][1];
+  bool peak = true;
 #pragma unroll
   for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
     for (int dk = -1; dk <= 1; ++dk) {
       if (dk == 0 && dj == 0) continue;
-      const int qn = __ldg(m + dj * stride + dk);
+      const int qn = w[dj + 1][dk + 1];
       const bool later = dj > 0 || (dj == 0 && dk > 0);
-      if (later ? qn > q : qn >= q) return false;
+      peak &= later ? qn <= q : qn < q;
     }
-  return true;
+  return peak;
 }
 
 struct CfSums {
   int Q, Sk, Sj, Skk, Sjj;
 };
 
-// moment sums over the 3x3 window and the 5x5 ring cells that do not rise away from the peak
-__device__ __forceinline__ CfSums cf_sums(const uint16_t* m, int stride) {
-  int v[5][5];  // v[dj + 2][dk + 2]
-#pragma unroll
-  for (int a = 0; a < 5; ++a)
-#pragma unroll
-    for (int b = 0; b < 5; ++b) v[a][b] = __ldg(m + (a - 2) * stride + (b - 2));
+// moment sums over the 3x3 window (given) and the 5x5 ring cells that do not rise away from the peak
+__device__ __forceinline__ CfSums cf_sums3(const uint16_t* m, int stride, const int w[3][3]) {
   CfSums S{0, 0, 0, 0, 0};
 #pragma unroll
   for (int dj = -2; dj <= 2; ++dj)
 #pragma unroll
     for (int dk = -2; dk <= 2; ++dk) {
-      int q = v[dj + 2][dk + 2];
       const bool ring = dk == 2 || dk == -2 || dj == 2 || dj == -2;
+      int q;
       if (ring) {
         const int ik = dk == 2 ? 1 : dk == -2 ? -1 : dk;
         const int ij = dj == 2 ? 1 : dj == -2 ? -1 : dj;
-        if (q > v[ij + 2][ik + 2]) q = 0;
+        q = __ldg(m + dj * stride + dk);
+        if (q > w[ij + 1][ik + 1]) q = 0;
+      } else {
+        q = w[dj + 1][dk + 1];
       }
       S.Q += q;
       S.Sk += q * dk;
@@ -117,9 +125,11 @@ __global__ void __launch_bounds__(kCfTile) k_cf_peaks(CfArgs A) {
     CfSums S{0, 0, 0, 0, 0};
     if (i < A.n && cf_digit(A, i, s, r, k, j, q)) {
       const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
-      if ((int)__ldg(m) != q) bad |= kCfErrTwice;
-      if (q >= A.q_peak_min && cf_is_peak(m, A.stride, q)) {
-        S = cf_sums(m, A.stride);
+      int w[3][3];
+      cf_window3(m, A.stride, w);
+      if (w[1][1] != q) bad |= kCfErrTwice;
+      if (q >= A.q_peak_min && cf_is_peak3(w)) {
+        S = cf_sums3(m, A.stride, w);
         keep = S.Q >= A.q_total_min;
       }
     }
