@@ -208,9 +208,13 @@ __global__ void __launch_bounds__(kCfTile, 8) k_cf_copy(CfArgs A) {
 }
 
 __global__ void __launch_bounds__(kCfTile) k_cf_clear(CfArgs A) {
-  for (long long i = (long long)blockIdx.x * kCfTile + threadIdx.x; i < A.n; i += (long long)gridDim.x * kCfTile) {
-    int s, r, k, j, q;
-    if (cf_digit(A, i, s, r, k, j, q)) A.map[cf_cell(A, s, r, k, j)] = 0;
+  const long long step = (long long)gridDim.x * kCfTile;
+  for (long long i = (long long)blockIdx.x * kCfTile + threadIdx.x; i < A.n; i += 2 * step) {
+    int s0, r0, k0, j0, q0, s1 = 0, r1 = 0, k1 = 0, j1 = 0, q1 = 0;
+    const bool v0 = cf_digit(A, i, s0, r0, k0, j0, q0);
+    const bool v1 = i + step < A.n && cf_digit(A, i + step, s1, r1, k1, j1, q1);
+    if (v0) A.map[cf_cell(A, s0, r0, k0, j0)] = 0;
+    if (v1) A.map[cf_cell(A, s1, r1, k1, j1)] = 0;
   }
 }
 
