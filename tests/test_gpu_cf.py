@@ -184,3 +184,14 @@ def test_tracks_from_found_clusters_match_tracks_from_generated_clusters(tracker
         vals, cnt = np.unique(tt, return_counts=True)
         pure += cnt.max() >= 0.9 * len(tt) and vals[cnt.argmax()] >= 0
     assert pure >= 0.95 * t_dig["n_tracks"]
+
+
+def test_two_large_digits_in_one_cell_carry_and_the_next_call_is_exact(tpc, tracker):
+    """Two digits of 40000 in one cell add up past 16 bits and carry into the next pad's cell; the
+    call is refused, and the next call (which re-clears the whole map) sees only its own digits."""
+    bad = _cells([(0, 0, 2, 3, 40000), (0, 0, 2, 3, 40000), (0, 0, 6, 3, 20)])
+    with pytest.raises(tpc.TpcError) as e:
+        tracker.find_clusters(*bad, 64)
+    assert e.value.code == -1
+    ok = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30), (0, 0, 2, 4, 7)])
+    assert_same(tracker.find_clusters(*ok, 64), oracle.find_clusters(*ok, 64, precision="f32"))
