@@ -10,6 +10,7 @@ and names the workloads of this project:
                       exponential multiplicity (mean 2500, capped at 12000);
 * ``full_570``      — full-size synchronous frame: 570 collisions over 128 orbits (11.44 ms),
                       exponential multiplicity, about 1.7e8 clusters;
+* ``slice_80``      — an 18-orbit slice of the synchronous frame (80 collisions, about 2.5e7 clusters);
 * ``serve``         — a serving-stream frame with ``n_collisions`` given by the caller.
 
 ``digitize`` turns a frame's clusters into the zero-suppressed pad x time-bin digits a cluster finder
@@ -158,6 +159,9 @@ CONFIGS = {
     # full-size synchronous frame: 570 collisions over 128 orbits; the frame ends with the last orbit,
     # so tracks of collisions in its last 90 us are cut (Sec. 2); clusters in generation order
     "full_570": dict(seed=4, n_collisions=570, mult_fixed=0, t_zero=0, frame_us=128 * ORBIT_US,
+                     tail_us=0.0, x0_total=0.03, shuffle=0),
+    # an 18-orbit slice of the synchronous frame: 80 collisions over 18 orbits (1.6 ms), cut like it
+    "slice_80": dict(seed=4, n_collisions=80, mult_fixed=0, t_zero=0, frame_us=18 * ORBIT_US,
                      tail_us=0.0, x0_total=0.03, shuffle=0),
     # serving stream frame: n_collisions set by the caller, 20 us per collision at 50 kHz
     "serve": dict(seed=5, n_collisions=1, mult_fixed=0, t_zero=0, frame_us=20.0, x0_total=0.03),
