@@ -8,7 +8,8 @@
 //   cluster  the 3x3 window plus each cell of the 5x5 ring whose charge does not exceed that of
 //            the window cell next to it on the way to the peak; kept if its charge Q >= q_total_min;
 //   values   integer moment sums, then FP32 IEEE operations in a fixed order (mean pad and time,
-//            y and w of the centroid, widths in pads and time bins).
+//            y and w of the centroid, widths in pads and time bins);
+//   order    the input order of the peak digits.
 //
 // The charge map is dense per (sector, row) and lives in HBM across calls, zero between them:
 // only the cells of the frame's digits are written, read and cleared, so a frame costs traffic in
