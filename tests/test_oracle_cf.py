@@ -236,3 +236,15 @@ def test_digitized_pbpb_row_occupancy_merges_but_keeps_most_clusters():
     c64 = oracle.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time, precision="f64", n_threads=4)
     assert np.array_equal(c["digit"], c64["digit"]) and np.array_equal(c["q_tot"], c64["q_tot"])
     assert np.max(np.abs(c["y"] - c64["y"])) < 1e-4 and np.max(np.abs(c["w"] - c64["w"])) < 1e-3
+
+
+def test_total_charge_threshold_selects_a_subset():
+    """Raising q_total_min keeps exactly the clusters whose charge reaches it, unchanged."""
+    f, d = synth.generate_digits("pp_500", mult_fixed=200, seed=8)
+    lo = oracle.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time, precision="f32")
+    p = oracle.cf_default_params("f32", q_total_min=60)
+    hi = oracle.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time, precision="f32", params=p)
+    keep = lo["q_tot"] >= 60
+    assert 0 < hi["n_clusters"] == keep.sum() < lo["n_clusters"]
+    for k in ("digit", "y", "w", "q_tot", "sigma_pad", "sigma_time"):
+        assert np.array_equal(hi[k], lo[k][keep])

@@ -61,3 +61,38 @@ def test_workload_sizes():
     assert 6e4 < g.n < 9e4
     b = [synth.generate("batch16", frame_id=i).n for i in range(4)]
     assert len(set(b)) == 4           # uneven frame sizes
+
+
+def test_digits_readout_order_cells_and_charge():
+    """Digits: deterministic, every cell inside its row and frame and unique, grouped by (sector, row)
+    in (time, pad) order unless shuffled, and an isolated cluster's digits hold its charge (the
+    Gaussian integrated over the cells, less what rounds away under the threshold)."""
+    f = synth.generate("pp_500", mult_fixed=30, noise_frac=0.0, seed=5)
+    d = synth.digitize(f)
+    d2 = synth.digitize(f, n_threads=1)
+    for k in ("sector", "row", "pad", "time", "adc", "truth_cluster"):
+        assert np.array_equal(getattr(d, k), getattr(d2, k))
+    npads = np.array([synth.n_pads(r) for r in range(152)])
+    assert np.all(d.pad < npads[d.row]) and np.all(d.time < d.n_time) and np.all(d.adc >= 2)
+    key = ((d.sector.astype(np.int64) * 152 + d.row) * 65536 + d.time) * 65536 + d.pad
+    assert np.all(np.diff(key) > 0)
+    s = synth.digitize(f, shuffle=1)
+    ks = ((s.sector.astype(np.int64) * 152 + s.row) * 65536 + s.time) * 65536 + s.pad
+    assert np.array_equal(np.sort(ks), key) and not np.array_equal(ks, key)
+    # charge per cluster: the digits it dominates, against a direct numeric integration of its
+    # Gaussian over the same cells (independent of the generator's erf-based cell fractions)
+    q = np.bincount(d.truth_cluster, weights=d.adc, minlength=f.n)
+    i = int(np.argmax(q))
+    cells = d.truth_cluster == i
+    pitch, dw, sig = 0.4, synth.DIGIT_DEFAULTS["time_bin_w"], 0.3
+    n = npads[f.row[i]]
+    tot = 0.0
+    for k, j in zip(d.pad[cells], d.time[cells]):
+        ys = np.linspace((k - n / 2) * pitch, (k + 1 - n / 2) * pitch, 201)
+        ws = np.linspace(j * dw, (j + 1) * dw, 201)
+        gy = np.trapezoid(np.exp(-0.5 * ((ys - f.y[i]) / sig) ** 2), ys) / (sig * math.sqrt(2 * math.pi))
+        gw = np.trapezoid(np.exp(-0.5 * ((ws - f.w[i]) / sig) ** 2), ws) / (sig * math.sqrt(2 * math.pi))
+        tot += gy * gw
+    assert 0.8 < tot <= 1.0
+    qmed = synth.DIGIT_DEFAULTS["q_median"]
+    assert q[i] / tot > 0.5 * qmed
