@@ -295,7 +295,7 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
 
 
 def compression_benchmark(tpc, torch, d_in, tuned_params: dict, storage: dict, n: int, reps: int = 5) -> dict:
-    """The compression inputs of the bench frame (Sec. 3), measured apart from the tracking step:
+    """The compression inputs of the bench frame (Sec. 4), measured apart from the tracking step:
     the device time of the residual / keep-mask stage, the fraction of clusters strategy B keeps,
     and the empirical entropy (bits per hit) of the stored residuals against the absolute
     positions of the same hits, both in 2^-9 cm steps."""

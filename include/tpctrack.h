@@ -5,7 +5,7 @@
  * described in "Overview of online and offline reconstruction in ALICE for LHC Run 3"
  * (arXiv:2009.07515): clusters of a continuous-readout time frame in (Sec. 2: native row/time
  * coordinates, z unknown until a vertex time is known), sector tracks with helix parameters,
- * covariances and cluster indices out (Sec. 5: TPC tracking runs standalone, without space-charge,
+ * covariances and cluster indices out (Sec. 6: TPC tracking runs standalone, without space-charge,
  * field or hit-error corrections; the algorithm derives from the Run-2 HLT tracker). Every stage
  * runs as a CUDA kernel on one GPU: per-row search grid, cellular-automaton neighbour finding and
  * cleaning, start-hit selection, Kalman-filter tracklet construction in the solenoid field, and
@@ -71,7 +71,7 @@ typedef struct {
   double drift_length;    /* drift length L, cm: a cluster of a collision at time t_c has
                              w = v_d t_c + L - |z| (250) */
   double drift_velocity;  /* v_d, cm per microsecond (250/90) */
-  double keep_vy, keep_vw;/* compression, strategy B (Sec. 3): clusters within +-keep_vy in y and
+  double keep_vy, keep_vw;/* compression, strategy B (Sec. 4): clusters within +-keep_vy in y and
                              +-keep_vw in w of a good track's predicted position are kept (1, 1 cm) */
   double keep_qpt_max;    /* a good track has |q/pT| <= keep_qpt_max, i.e. pT >= 50 MeV/c (20) */
   /* storage / runtime */
@@ -130,11 +130,11 @@ typedef struct {
   const int64_t* hit_offset;  /* [n+1] */
   const uint32_t* hit_index;  /* [hit_offset[n]] */
   const float* beam;          /* [n][5] the fit transported to the beam line x = 0 without material
-                                 (Sec. 5): y0, w0, var(w0), then for a primary from z = 0 its
+                                 (Sec. 6): y0, w0, var(w0), then for a primary from z = 0 its
                                  collision time t0 = (w0 - L)/v_d (us) and its z at x_ref,
                                  +-(w0 - w_ref) (+ on side A); all NaN where the transport fails
                                  (|sin(phi)| reaches max_sin before x = 0) */
-  /* compression inputs (Sec. 3), NULL unless tpc_params.compress: each track's fit is transported
+  /* compression inputs (Sec. 4), NULL unless tpc_params.compress: each track's fit is transported
    * (state only, no scattering) from x_ref directly to each row it spans; hit i of the track is stored as
    * q(hit) - q(prediction) at its row, q(v) = rint(512 v) in units of 2^-9 cm, for i < n_pred, and
    * as q(hit) beyond (the transport failed there). A decoder with the same arithmetic restores q(hit). */
@@ -151,38 +151,52 @@ typedef struct {
   const int64_t* launches;    /* [n_kernels] kernel launches of each stage */
 } tpc_kernel_times;
 
+/* Defaults of every parameter: the method's readings of Sec. 6 (the paper gives no values) and the
+ * runtime's sizes. */
 void tpc_default_params(tpc_params* p);
 
-/* Create a context on the current CUDA device. */
+/* Create a context on the current CUDA device. It owns the device memory and streams of the
+ * tracking steps of Sec. 6 (the paper's one GPU per time frame, Sec. 7.1). */
 int tpc_create(const tpc_params* p, tpc_ctx** out);
+/* Free the context and all its device and host memory (no counterpart in the paper). */
 void tpc_destroy(tpc_ctx* ctx);
+/* One-line description of the context's last failure (no counterpart in the paper). */
 const char* tpc_last_error(const tpc_ctx* ctx);
+/* Library name and version (no counterpart in the paper). */
 const char* tpc_version(void);
 
-/* Load one frame's clusters (validated on the device during tracking: sector < 36, row < 152,
- * finite y and w). Returns a frame handle in *out. */
+/* Load one frame's clusters (Sec. 2: a time frame of continuous readout in native row and time
+ * coordinates; frames are reconstructed independently). Validated on the device during tracking:
+ * sector < 36, row < 152, finite y and w. Returns a frame handle in *out. */
 int tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* out);
 
-/* Enqueue tracking of one loaded frame on `cuda_stream` (a cudaStream_t; NULL = the context's
+/* Enqueue the standalone sector tracking of one loaded frame (Sec. 6: tracking without corrections,
+ * derived from the Run-2 HLT tracker) on `cuda_stream` (a cudaStream_t; NULL = the context's
  * stream). Asynchronous: results are available from tpc_get_tracks(). */
 int tpc_track_sectors(tpc_ctx* ctx, tpc_frame_t frame, void* cuda_stream);
 
 /* Enqueue tracking of several loaded frames in one batched launch sequence (all their sectors
- * together). Each frame's tracks are identical to tracking it alone. */
+ * together; Sec. 7.1: enough parallelism comes from processing many collisions in one go). Each
+ * frame's tracks are identical to tracking it alone. */
 int tpc_track_batch(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, void* cuda_stream);
 
-/* Wait (bounded) for the frame's tracking and return host views of its tracks. */
+/* Wait (bounded) for the frame's tracking and return host views of its sector tracks (Sec. 6:
+ * tracks with parameters, covariances and their clusters). */
 int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out);
 
-/* Free the frame's device and host memory. */
+/* Free the frame's device and host memory (Sec. 7.1: memory is reused for consecutive steps and
+ * frames rather than held per collision). */
 int tpc_release_frame(tpc_ctx* ctx, tpc_frame_t frame);
 
-/* Serving: admit a frame (copied/borrowed as for tpc_load_clusters) into the request queue.
+/* Serving: admit a frame (copied/borrowed as for tpc_load_clusters) into the request queue. The
+ * paper has no serving loop; this follows the continuous-batching pattern of this library (frames of
+ * uneven size admitted by HBM budget, their work overlapped on the device).
  * Never blocks on the HBM budget: frames wait host-side until memory frees up. A frame larger
  * than the whole budget is refused with TPC_E_BUDGET. */
 int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ticket);
 
-/* Serving: advance the scheduler (retire finished batches, queueing their results' copies; admit
+/* Serving (no counterpart in the paper; the continuous-batching pattern of tpc_submit_frame):
+ * advance the scheduler (retire finished batches, queueing their results' copies; admit
  * queued frames into free slots, a batch growing only while it holds at most 2^21 clusters, and
  * launch it) and return up to max_done finished tickets in done[] (frames whose results are on the
  * host); waits at most timeout_us for at least one.
@@ -190,30 +204,33 @@ int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ti
  * with tpc_get_tracks() and freed with tpc_release_frame(). */
 int tpc_poll(tpc_ctx* ctx, tpc_frame_t* done, int32_t max_done, int32_t timeout_us);
 
-/* Diagnostics for parity tests: copy a per-cluster array of a tracked frame into host memory
+/* Diagnostics for parity tests (the cellular-automaton links of the HLT-derived tracker, Sec. 6):
+ * copy a per-cluster array of a tracked frame into host memory
  * (caller-owned, n = number of clusters), indexed by the caller's cluster order.
  * what: 0 = raw up link, 1 = raw down link, 2 = cleaned up link, 3 = cleaned down link
  * (each the input index of the linked cluster or -1). */
 int tpc_get_links(tpc_ctx* ctx, tpc_frame_t frame, int32_t what, int32_t* host_out, int64_t n);
 
-/* Compression, strategy B (Sec. 3: every hit not in the vicinity of a good track is removed): copy
+/* Compression, strategy B (Sec. 4: every hit not in the vicinity of a good track is removed): copy
  * the keep mask of a tracked frame into host memory (caller-owned, n = number of clusters), indexed
  * by the caller's cluster order: 1 = kept (a hit of a good track, or within +-(keep_vy, keep_vw) of a
  * good track's predicted position at its row), 0 = removed. Needs tpc_params.compress = 1 (else
  * TPC_E_STATE). */
 int tpc_get_keep_mask(tpc_ctx* ctx, tpc_frame_t frame, uint8_t* host_out, int64_t n);
 
-/* Number of start hits and of tracks of a tracked frame. */
+/* Number of start hits and of tracks of a tracked frame (diagnostic; Sec. 6 steps). */
 int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n_tracks);
 
-/* Device counters of the batch a frame was tracked in, for diagnostics and roofline accounting:
+/* Device counters of the batch a frame was tracked in, for diagnostics and roofline accounting
+ * (no counterpart in the paper):
  * out[0..n) = clusters, clusters in the grid, grid bins, start hits, tracklets, tracklet row steps,
  * hits fitted by tracklets, tracks, track hits, device error bits. Returns the number of counters
  * available (>= 0) or a negative error. */
 int tpc_get_stats(tpc_ctx* ctx, tpc_frame_t frame, int64_t* out, int32_t n);
 
 /* ---- autotuning of the launch shapes (the batched persistent path's rows-per-block and
- * tracklets-per-warp choices). One timed configuration: */
+ * tracklets-per-warp choices; the paper has no tuner: its one common source runs on CUDA,
+ * OpenCL, HIP and the CPU, abstract). One timed configuration: */
 typedef struct {
   float bin_occupancy;
   int32_t k2_warps, k2_tma, k5_block, k5_regs, k5_blocks_per_sm, k5_order, sel_lanes;
@@ -238,11 +255,12 @@ typedef struct {
  * returns. */
 int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int32_t reps, tpc_tune_report* out);
 
-/* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times. */
+/* Enable (1) or disable (0) per-kernel CUDA-event timing; read the last call's times (Sec. 7.2 times
+ * the steps per GPU; these are the per-kernel times of this library's steps). */
 int tpc_set_timing(tpc_ctx* ctx, int32_t enable);
 int tpc_get_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 
-/* ---- cluster finding from digits (Table 1 of Sec. 6.2 times it as the first GPU step of the
+/* ---- cluster finding from digits (Table 1 of Sec. 7.2 times it as the first GPU step of the
  * synchronous reconstruction; Sec. 2: the TPC records, per pad, the charge of every time bin, and a
  * pad row's clusters are reconstructed from these zero-suppressed digits). The paper names the step
  * but not its rules; the library computes:
@@ -345,7 +363,9 @@ int tpc_check_wait_timeout(int32_t limit_us, void* cuda_stream);
  *   cuda_stream  stream to run on (NULL: the legacy default stream)
  * Returns TPC_OK once the links are written (the call waits, at most two minutes, for its kernels),
  * TPC_E_CAPACITY if clusters->n > TPC_STATIC_MAX_CLUSTERS, TPC_E_INVAL for bad arguments or
- * malformed clusters, TPC_E_TIMEOUT, or TPC_E_CUDA. All calls share the one scratch array, which
+ * malformed clusters, TPC_E_TIMEOUT, or TPC_E_CUDA. After TPC_E_TIMEOUT the call's kernels may still
+ * be running and writing the scratch array and up/down: synchronise cuda_stream before freeing up or
+ * down or making the next call. All calls share the one scratch array, which
  * keeps the previous call's contents (each call clears what must start at zero); calls that overlap
  * on the GPU, from two host threads or on two streams, race on it and must be serialised by the
  * caller. The first call on a device looks up the array's device address (cudaGetSymbolAddress) and

@@ -4,7 +4,7 @@
  * TEST INFRASTRUCTURE ONLY, under the same rules as tpc_oracle.c: only the tests, the package smoke
  * check and the CPU-baseline leg of the benchmark may load it; the product path shares no code with it.
  *
- * What it computes: the cluster finding of the synchronous reconstruction (Table 1 of Sec. 6.2 times
+ * What it computes: the cluster finding of the synchronous reconstruction (Table 1 of Sec. 7.2 times
  * it as the first GPU step; Sec. 2: the TPC records, per pad, the charge of each time bin, and the
  * clusters of a pad row are reconstructed from these digits). The paper names the step but not its
  * rules, so this file states the reading the project takes:

@@ -5,7 +5,7 @@
  * benchmark may load this. The product path never calls it and shares no code with it.
  *
  * What it computes: the standalone TPC sector tracking of the paper's synchronous reconstruction
- * (Sec. 5: the TPC tracking runs first standalone, without space-charge, field or hit-error
+ * (Sec. 6: the TPC tracking runs first standalone, without space-charge, field or hit-error
  * corrections, on clusters whose z is unknown in continuous readout, Sec. 2; the algorithm is
  * derived from the Run-2 HLT tracker). The paper names the method but defers its steps to the HLT
  * papers it cites, so each step below states the reading this project takes:
@@ -22,13 +22,13 @@
  *      through the found hits and inward extension;
  *   6. tracklet selection: each hit goes to the tracklet with the largest (nhits, -start index) key;
  *      a tracklet becomes a track if it keeps >= nmin hits and at least half of its hits;
- *   7. beam line (Sec. 5: track seeds are extrapolated to the beam line, and the most likely z is
+ *   7. beam line (Sec. 6: track seeds are extrapolated to the beam line, and the most likely z is
  *      computed assuming a primary from a vertex at the origin): each track's fit is transported
  *      by the same exact helix step, without scattering, from x_ref to the plane x = 0 through the
  *      beam axis; there y0 and the drift coordinate w0 (with its variance) are read. A primary from
  *      z = 0 has w0 = v_d t_c + L (continuous readout, Sec. 2: w = v_d t_c + L - |z|), so its
  *      collision time is t0 = (w0 - L) / v_d and its z at x_ref is +-(w0 - w_ref) by drift side;
- *   8. compression inputs (Sec. 3: hits of good tracks are stored as residuals to the extrapolated
+ *   8. compression inputs (Sec. 4: hits of good tracks are stored as residuals to the extrapolated
  *      track position; strategy B removes every hit not in the vicinity of a good track): each
  *      track's fit is transported (state only, no scattering) from x_ref directly to every row up
  *      to its last hit's row, one exact helix step per row (rows independent; once a transport
@@ -177,7 +177,7 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
 
 static inline real absr(real v) { return v < 0 ? -v : v; }
 
-/* 16-bit fixed-point cluster storage (Sec. 3 of the paper: custom formats that keep only the bits
+/* 16-bit fixed-point cluster storage (Sec. 4 of the paper: custom formats that keep only the bits
  * the intrinsic resolution needs). y is stored as qy = rint((y + 64) * 512) clamped to [0, 65535],
  * read back as qy / 512 - 64; w is stored as a 16-bit offset, in steps of 2^-9 cm, from the lower
  * edge of its search-grid bin (bins are aligned power-of-two widths of at most 128 cm), which reads

@@ -1,4 +1,4 @@
-"""GB300-native TPC sector tracking (standalone TPC tracking of arXiv:2009.07515, Sec. 5).
+"""GB300-native TPC sector tracking (standalone TPC tracking of arXiv:2009.07515, Sec. 6).
 
 The tracking runs entirely in ``libtpctrack.so`` (hand-written sm_103a CUDA kernels behind the
 C-ABI of ``include/tpctrack.h``). This package is its thin Python binding: ``_lib`` mirrors the

@@ -1,5 +1,5 @@
 // k_cf.cu — cluster finding from digits: the first GPU step of the synchronous reconstruction
-// (Table 1 of Sec. 6.2; Sec. 2: the TPC records, per pad, the charge of every time bin, and a pad
+// (Table 1 of Sec. 7.2; Sec. 2: the TPC records, per pad, the charge of every time bin, and a pad
 // row's clusters are reconstructed from these zero-suppressed digits).
 //
 // Rules (the full statement is at tpc_find_clusters in tpctrack.h):
@@ -14,8 +14,8 @@
 // The charge map is dense per (sector, row) and lives in HBM across calls, zero between them:
 // only the cells of the frame's digits are written, read and cleared, so a frame costs traffic in
 // proportion to its digits, not to the map. Kernels (persistent, tiles of 256 digits):
-//   k_cf_fill   validate each digit and add its charge into its cell (a 32-bit reduction on the
-//               cell's word, nothing waits for it)
+//   k_cf_fill   validate each digit and add its charge into its cell (a 32-bit atomic add on the
+//               cell's word; a cell that was not zero before the add holds a second digit)
 //   k_cf_peaks  each digit checks that its cell holds its own charge (else a second digit shares
 //               the cell), the peak test, the cluster of a kept peak; each warp writes its kept
 //               clusters compacted in digit order into its block's region of a temporary array
@@ -104,7 +104,11 @@ __global__ void __launch_bounds__(kCfTile, 8) k_cf_fill(CfArgs A) {
       continue;
     }
     const size_t c = cf_cell(A, s, r, k, j);
-    atomicAdd(reinterpret_cast<uint32_t*>(A.map) + (c >> 1), (uint32_t)q << ((uint32_t)(c & 1) * 16u));
+    const uint32_t sh = (uint32_t)(c & 1) * 16u;
+    const uint32_t old = atomicAdd(reinterpret_cast<uint32_t*>(A.map) + (c >> 1), (uint32_t)q << sh);
+    // the map is zero at the start of a call, so a non-zero cell before the add means a second
+    // digit in the cell, whatever the charges add up to
+    if ((old >> sh) & 0xffffu) bad |= kCfErrTwice;
   }
   if (bad) atomicOr(A.err, bad);
 }

@@ -223,7 +223,7 @@ void launch_write_tracks(int lanes, int grid, cudaStream_t s, const Work& W, con
   else k_write_tracks_warp<<<grid, 256, 0, s>>>(W, Q);
 }
 
-// K10 compression inputs (Sec. 3: hits of good tracks are stored as residuals to the extrapolated
+// K10 compression inputs (Sec. 4: hits of good tracks are stored as residuals to the extrapolated
 // track position; strategy B removes every hit not in the vicinity of a good track). One warp per
 // track, its lanes on 32 rows at a time: the fit is transported (state only, no scattering) from
 // x_ref directly to each row up to the last hit's row. At every row a good track (|q/pT| <=
@@ -316,7 +316,7 @@ void launch_compress(int packed, int grid, cudaStream_t s, const Work& W, const 
   else k_compress<false><<<grid, 256, 0, s>>>(W, Q);
 }
 
-// K9 beam line (Sec. 5: track seeds are extrapolated to the beam line, and the most likely z is
+// K9 beam line (Sec. 6: track seeds are extrapolated to the beam line, and the most likely z is
 // computed assuming a primary from a vertex at the origin). One thread per track: its fit at
 // x_ref is transported by the exact helix step, without scattering noise, to the plane x = 0
 // through the beam axis. Out: y0, w0, var(w0) there; for a primary from z = 0 (continuous

@@ -1807,11 +1807,12 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
       if (cudaEventElapsedTime(&m, cf.ev[k], cf.ev[k + 1]) == cudaSuccess) cf.ms[k] = m;
     }
   const uint32_t total = cf.h_small[0], err = cf.h_small[1];
+  // After any refused frame the next call re-zeros the whole map: two digits in one cell may have
+  // carried charge into a neighbouring cell (also one the clear kernel does not visit), whatever
+  // other error was found beside it.
+  if (err) cf.map_clean = false;
   if (err & kCfErrDigit) return fail(ctx, TPC_E_INVAL, "malformed digit (cell outside the pad row or frame, or zero charge)");
-  if (err & kCfErrTwice) {
-    cf.map_clean = false;  // charges of one cell added up and may have carried into the next cell
-    return fail(ctx, TPC_E_INVAL, "two digits in one cell");
-  }
+  if (err & kCfErrTwice) return fail(ctx, TPC_E_INVAL, "two digits in one cell");
   const long long m = total;
   out->n_clusters = m;
   if (!to_host) {

@@ -235,8 +235,13 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
     if (e != cudaErrorNotReady) { cudaGetLastError(); return TPC_E_CUDA; }
     if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(120)) return TPC_E_TIMEOUT;
   }
+  // the error word, read on the caller's stream only (a device-to-pageable copy returns once it has
+  // landed; the legacy default stream would also wait for unrelated work of other streams)
   uint32_t err = 0;
-  if (cudaMemcpy(&err, &C->err, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) { cudaGetLastError(); return TPC_E_CUDA; }
+  if (cudaMemcpyAsync(&err, &C->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+    cudaGetLastError();
+    return TPC_E_CUDA;
+  }
   if (err & kErrInput) return TPC_E_INVAL;
   if (err & kErrTimeout) return TPC_E_TIMEOUT;
   if (err & kErrBins) return TPC_E_CAPACITY;

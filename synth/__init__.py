@@ -17,7 +17,7 @@ and names the workloads of this project:
 starts from (``DIGIT_DEFAULTS``: 0.4 cm pads, 0.2 us time bins, 0.3 cm charge spread, log-normal
 cluster charge, 2-ADC threshold, 10-bit saturation).
 
-Common laws (Sec. 2 and 6.1 of the paper describe the continuous-readout frames these stand in for):
+Common laws (Sec. 2 and 7.1 of the paper describe the continuous-readout frames these stand in for):
 pT log-uniform in [0.1, 10] GeV, |eta| < 0.9, phi uniform, q = +-1, Bz = 0.5 T, sigma_y = sigma_w =
 0.1 cm, 2% row-crossing inefficiency, 5% uniform noise clusters per (sector, row).
 """

@@ -3,7 +3,7 @@
  *
  * This module produces inputs only. It holds none of the tracker's arithmetic and is shared by the
  * CPU oracle tests and the CUDA path alike. It models the workloads of the paper's synchronous
- * reconstruction (Sec. 2: continuous readout, clusters in native row/time coordinates; Sec. 6.1:
+ * reconstruction (Sec. 2: continuous readout, clusters in native row/time coordinates; Sec. 7.1:
  * time frames of many overlapping collisions) with the detector layout of the Pb-Pb/pp configurations
  * used throughout this project: 36 sectors of 20 degrees (18 in phi x 2 drift sides), 152 pad rows
  * at radii 85-245 cm, 250 cm drift length, solenoid field Bz along +z.

@@ -266,7 +266,7 @@ def test_device_resident_input(tracker, torch_cuda):
 @pytest.mark.parametrize("packed", [0, 1], ids=["fp32", "16bit"])
 @pytest.mark.parametrize("cfg", ["pp_500", "pbpb_2x10000"])
 def test_compression_inputs_match_oracle(torch_cuda, cfg, packed, n_threads):
-    """Track-model residuals, predicted-hit counts and the strategy-B keep mask (Sec. 3) of the
+    """Track-model residuals, predicted-hit counts and the strategy-B keep mask (Sec. 4) of the
     GPU path equal the FP32 oracle's exactly: the same transport of the same fits, integer outputs."""
     import paper_2009_07515_gb300 as tpc
     tr = tpc.Tracker(compress=1, packed=packed)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's beam-line step (Sec. 5: track seeds are extrapolated to the beam line and the
+"""Pins of the oracle's beam-line step (Sec. 6: track seeds are extrapolated to the beam line and the
 most likely z is computed for a primary from a vertex at the origin).
 
 The step transports each track's fit from x_ref to the plane x = 0 without material and reads

@@ -1,4 +1,4 @@
-"""Pins of the oracle's cluster finder (cluster finding from digits, Sec. 2 and Table 1 of Sec. 6.2).
+"""Pins of the oracle's cluster finder (cluster finding from digits, Sec. 2 and Table 1 of Sec. 7.2).
 
 The finder takes each digit that wins against its 3x3 neighbours (ties go to the earlier cell in
 (time, pad) order), sums the charges of the 3x3 window plus the 5x5 ring cells whose charge does not

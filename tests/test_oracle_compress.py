@@ -1,4 +1,4 @@
-"""Pins of the oracle's compression inputs (Sec. 3: hits of good tracks are stored as residuals to
+"""Pins of the oracle's compression inputs (Sec. 4: hits of good tracks are stored as residuals to
 the extrapolated track position; strategy B removes every hit not in the vicinity of a good track).
 
 Each track's fit is transported (state only, no scattering) from x_ref directly to every row it

@@ -65,8 +65,8 @@ def test_workload_sizes():
 
 def test_digits_readout_order_cells_and_charge():
     """Digits: deterministic, every cell inside its row and frame and unique, grouped by (sector, row)
-    in (time, pad) order unless shuffled, and an isolated cluster's digits hold its charge (the
-    Gaussian integrated over the cells, less what rounds away under the threshold)."""
+    in (time, pad) order unless shuffled, and the cells of isolated clusters hold their charge (the
+    Gaussian integrated over each cell and rounded, kept from the threshold up)."""
     f = synth.generate("pp_500", mult_fixed=30, noise_frac=0.0, seed=5)
     d = synth.digitize(f)
     d2 = synth.digitize(f, n_threads=1)
@@ -79,20 +79,39 @@ def test_digits_readout_order_cells_and_charge():
     s = synth.digitize(f, shuffle=1)
     ks = ((s.sector.astype(np.int64) * 152 + s.row) * 65536 + s.time) * 65536 + s.pad
     assert np.array_equal(np.sort(ks), key) and not np.array_equal(ks, key)
-    # charge per cluster: the digits it dominates, against a direct numeric integration of its
-    # Gaussian over the same cells (independent of the generator's erf-based cell fractions)
-    q = np.bincount(d.truth_cluster, weights=d.adc, minlength=f.n)
-    i = int(np.argmax(q))
-    cells = d.truth_cluster == i
-    pitch, dw, sig = 0.4, synth.DIGIT_DEFAULTS["time_bin_w"], 0.3
-    n = npads[f.row[i]]
-    tot = 0.0
-    for k, j in zip(d.pad[cells], d.time[cells]):
-        ys = np.linspace((k - n / 2) * pitch, (k + 1 - n / 2) * pitch, 201)
-        ws = np.linspace(j * dw, (j + 1) * dw, 201)
-        gy = np.trapezoid(np.exp(-0.5 * ((ys - f.y[i]) / sig) ** 2), ys) / (sig * math.sqrt(2 * math.pi))
-        gw = np.trapezoid(np.exp(-0.5 * ((ws - f.w[i]) / sig) ** 2), ws) / (sig * math.sqrt(2 * math.pi))
-        tot += gy * gw
-    assert 0.8 < tot <= 1.0
+    # charge of isolated clusters: with a fixed cluster charge (q_log_sigma = 0), every cell of the
+    # footprint (+-3 cells) of a cluster with no other cluster within 7 cells of its row holds the
+    # rounded charge of its Gaussian integrated numerically over the cell (independent of the
+    # generator's erf-based cell fractions), and exactly the cells that round to >= 2 ADC are digits
     qmed = synth.DIGIT_DEFAULTS["q_median"]
-    assert q[i] / tot > 0.5 * qmed
+    dq = synth.digitize(f, q_log_sigma=0.0)
+    pitch, dw, sig = 0.4, synth.DIGIT_DEFAULTS["time_bin_w"], 0.3
+    kc = np.floor(f.y / pitch + npads[f.row] / 2).astype(np.int64)
+    jc = np.floor(f.w / dw).astype(np.int64)
+    grp = f.sector.astype(np.int64) * 152 + f.row
+    checked = 0
+    cell_adc = {(int(a), int(b), int(c), int(e)): int(q) for a, b, c, e, q in
+                zip(dq.sector, dq.row, dq.pad, dq.time, dq.adc)}
+    for i in np.random.default_rng(3).permutation(f.n):
+        same = np.flatnonzero(grp == grp[i])
+        near = same[(np.abs(kc[same] - kc[i]) <= 7) & (np.abs(jc[same] - jc[i]) <= 7)]
+        if len(near) != 1 or not (4 <= kc[i] < npads[f.row[i]] - 4) or jc[i] < 4:
+            continue
+        for dk in range(-3, 4):
+            for dj in range(-3, 4):
+                k, j = kc[i] + dk, jc[i] + dj
+                n = npads[f.row[i]]
+                ys = np.linspace((k - n / 2) * pitch, (k + 1 - n / 2) * pitch, 401)
+                ws = np.linspace(j * dw, (j + 1) * dw, 401)
+                gy = np.trapezoid(np.exp(-0.5 * ((ys - f.y[i]) / sig) ** 2), ys) / (sig * math.sqrt(2 * math.pi))
+                gw = np.trapezoid(np.exp(-0.5 * ((ws - f.w[i]) / sig) ** 2), ws) / (sig * math.sqrt(2 * math.pi))
+                e = qmed * gy * gw
+                if abs(e - math.floor(e) - 0.5) < 1e-3:
+                    continue   # on a rounding edge: the integration error decides, not the charge
+                want = int(math.floor(e + 0.5))
+                got = cell_adc.get((int(f.sector[i]), int(f.row[i]), int(k), int(j)), 0)
+                assert got == (want if want >= 2 else 0), (i, dk, dj, e, got)
+        checked += 1
+        if checked == 20:
+            break
+    assert checked == 20
