@@ -1,22 +1,29 @@
 """Throughput benchmark of GB300 TPC sector tracking (clusters tracked per second).
 
 One step = one pass of the whole tracking path (grid, neighbours, cleaning, start hits, tracklet
-construction, selection, canonical output) over one synthetic time frame already resident in HBM.
-Default workload: the overlapping Pb-Pb-like frame of two central-like collisions of 10000
-primaries each (about 3 M clusters, FP32 storage). The L2 cache (129 MB) is flushed before each
-timed step by writing a 512 MB buffer; each step is timed with CUDA events on the stream the
-tracking runs on, and the flush lies outside the timed interval.
+construction, selection, canonical output, beam line) over one synthetic time frame already resident
+in HBM. Default workload: the full-size synchronous frame (570 collisions over 128 LHC orbits,
+exponential multiplicity, about 2.0e8 clusters), FP32 cluster storage; the same frame with 16-bit
+fixed-point storage is measured beside it. The frame (1.8 GB of clusters, 10 GB and more of working
+arrays) is larger than the L2 cache (129 MB), and the L2 is also flushed before each timed step by
+writing a 512 MB buffer; each step is timed with CUDA events on the stream the tracking runs on.
 
 Keys beyond the base contract:
-  e2e           the same metric through the C-ABI with host buffers: every step copies the frame's
-                clusters from pinned host memory, tracks, and reads the tracks back
-  roofline      the dominant kernel, algorithmic bytes per launch / its event-timed duration against
-                the measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle (FP32) on the machine's host cores, on a bounded sample
+  e2e           the same metric through the C-ABI with host buffers: every step submits the frame's
+                clusters from pinned host memory and reads its tracks back (pipelined submit/poll;
+                the synchronous load/track/read loop is e2e.sync_value)
+  roofline      the dominant kernel: algorithmic HBM bytes per launch (bytes per unit of the scope
+                table x units of the launch) / its event-timed duration, against the measured HBM
+                copy bandwidth; its ALU issue figure beside it (alu), and the whole path's bytes
+  storage_16bit the same frame in 16-bit fixed-point storage, same measurements
+  extra_workloads  the Pb-Pb-like frame of two 10000-primary collisions, FP32 storage
+  serving       frames of U{1..570} collisions arriving as a Poisson stream at several rates: p50/p99
+                latency and clusters/s, served (tpc_submit_frame/tpc_poll) against plain
+  cpu_baseline  the CPU oracle (FP32) on the machine's host cores, on a bounded sample of the frame
   kernels_ms    per-kernel device time of one step (CUDA events between launches)
-  cluster_finding  the upstream step on the same frame: its clusters digitized by the generator, the
-                clusters found again from the digits on the GPU (digits/s, kernels, roofline, end to
-                end, digits -> tracks, and the FP32 oracle on a sample)
+  cluster_finding  the upstream step on the Pb-Pb-like frame's digits (digits/s, kernels, roofline,
+                end to end, digits -> tracks, FP32 oracle on a sample)
+  batched       16 frames of uneven occupancy in one batched graph launch against one at a time
   --impl reference   times the CPU oracle as the reference arm (this method has no other code)
 Multi-GPU (torchrun): frames are independent, so every rank tracks its own replica of the
 workload on its own GPU with no collective in the data path ("scaling": "weak").
@@ -39,33 +46,50 @@ sys.path.insert(0, ROOT)
 METRIC = "TPC clusters tracked/s"
 UNIT = "clusters/s"
 
-# Roofline accounting:
-#  - memory-bound kernels: algorithmic bytes per cluster counted from the data layout, e.g. the
-#    neighbour search reads its row's (y, w) and the two adjacent rows once (3 x 8 B) and writes
-#    the links (8 B);
-#  - the tracklet kernel is bound by FP32 issue: algorithmic flops = row steps (device counter) x
-#    FLOPS_PER_STEP, the add/sub/mul/div/sqrt operations of one helix propagation with scattering
-#    noise, one chi2 and one Joseph-form update, counted from their definition; peak = 152 SMs x
-#    128 FP32 lanes x 2 flops (FMA) x the maximum SM clock.
-ALG_BYTES_PER_CLUSTER = {"neighbours": 32.0, "clean": 24.0, "seg_hist": 10.0, "bin_rank": 10.0,
-                         "scatter": 30.0, "starts": 12.0}
+# Roofline accounting. Algorithmic (compulsory) HBM bytes per unit of each step of the path, FP32-
+# stored / 16-bit stored, counted from the data layout: the grid build reads the input (10 B) and
+# writes the sorted coordinates (8 / 4 B) and input index (4 B) per cluster; the neighbour search
+# reads the coordinates once with perfect row reuse (8 / 4 B) and writes two links (8 B); cleaning
+# reads the links, gathers the partners' and writes them (24 B); start hits read the links (8 B);
+# tracklet construction reads, per hit it fits, the coordinates (8 / 4 B) and a link (4 B) and
+# writes a hit index (4 B); selection reads each tracklet hit twice (8 B), updates its weight (8 B)
+# and writes an output index (4 B); the beam line reads a fit (88 B) and writes 5 values (20 B) per
+# track. The unit counts come from the library's device counters (tpc_get_stats).
+STEPS = [  # (step, kernels, unit, FP32 bytes per unit, 16-bit bytes per unit)
+    ("K1 grid", ("seg_hist", "seg_layout", "scan_seg", "zero_bins", "bin_rank", "scan_bins", "scatter"),
+     "clusters", 22.0, 18.0),
+    ("K2 neighbours", ("neighbours",), "clusters", 16.0, 12.0),
+    ("K3 cleaning", ("clean",), "clusters", 24.0, 24.0),
+    ("K4 start hits", ("scan_start", "starts", "start_order"), "clusters", 8.0, 8.0),
+    ("K5 tracklets", ("chains", "tracklets"), "tracklet_hits", 16.0, 12.0),
+    ("K6/K7 selection", ("zero_w", "votes", "kept", "scan_kept", "write_tracks"), "tracklet_hits", 20.0, 20.0),
+    ("K9 beam line", ("beamline",), "tracks", 108.0, 108.0),
+]
+# The tracklet kernel is also reported against its FP32 issue rate: algorithmic flops = row steps
+# (device counter) x FLOPS_PER_STEP, the operations of one helix propagation with scattering noise,
+# one chi2 and one Joseph-form update counted from their definition (FMA = 2); peak = SMs x 128 FP32
+# lanes x 2 x the maximum SM clock, both read from the device.
 FLOPS_PER_STEP = 480.0
 E2E_WINDOW = 3  # frames in flight in the end-to-end measurement
 
 
-def _recorded_traffic(kernel: str, workload: str, shape: dict, method_defaults: dict):
-    """(DRAM bytes per launch of `kernel`, launch shape of the capture) from the committed ncu record
-    (profiles/traffic.json), or (None, None) when there is none for this workload, the method
-    defaults differ, or a source the kernel is built from has changed since the capture. The launch
-    shape changes no source: the caller reports the capture's shape beside the figure when it
-    differs from the timed one."""
+def _recorded_traffic(kernel: str, workload: str, method_defaults: dict, units: dict | None = None):
+    """DRAM bytes per launch of `kernel` from the committed ncu record (profiles/traffic.json), as
+    (bytes, note): None when there is no record, the method defaults differ, or a source the kernel
+    is built from has changed since the capture. A record taken on a smaller workload of the same
+    kind (`scales_to` names this one) is scaled to this launch by its unit count (`units`: the device
+    counter the kernel's traffic grows with), and the note says so."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None, None
     with open(p) as fh:
-        rec = json.load(fh).get(kernel)
-    if not rec or rec.get("workload") != workload or rec.get("method_defaults") != method_defaults:
+        recs = json.load(fh)
+    rec = recs.get(f"{kernel}@{workload}") or recs.get(kernel)
+    if not rec or rec.get("method_defaults") != method_defaults:
+        return None, None
+    scaled = rec.get("workload") != workload
+    if scaled and (workload not in rec.get("scales_to", []) or not units):
         return None, None
     h = hashlib.sha256()
     for src in rec["sources"]:
@@ -73,14 +97,20 @@ def _recorded_traffic(kernel: str, workload: str, shape: dict, method_defaults: 
             h.update(fh.read())
     if h.hexdigest() != rec["sources_sha256"]:
         return None, None
-    return float(rec["dram_bytes_per_launch"]), rec.get("launch_shape")
+    b = float(rec["dram_bytes_per_launch"])
+    note = {"capture_workload": rec["workload"], "capture_launch_shape": rec.get("launch_shape")}
+    if scaled:
+        u = rec["unit"]
+        b = b * float(units[u]) / float(rec["units_per_launch"])
+        note["scaled_by"] = f"{u}: {units[u]} / {rec['units_per_launch']} of the capture"
+    return b, note
 
 
-def _traffic_fields(kernel: str, workload: str, shape: dict, method_defaults: dict) -> dict:
-    traffic, cap_shape = _recorded_traffic(kernel, workload, shape, method_defaults)
+def _traffic_fields(kernel: str, workload: str, method_defaults: dict, units: dict | None = None) -> dict:
+    traffic, note = _recorded_traffic(kernel, workload, method_defaults, units)
     out = {"traffic": traffic}
-    if traffic is not None and cap_shape != shape:
-        out["traffic_launch_shape"] = cap_shape  # the capture's shape; the timed one is config.launch_shape
+    if traffic is not None:
+        out["traffic_source"] = note
     return out
 
 
@@ -190,79 +220,136 @@ def _barrier(ws: int):
         dist.barrier()
 
 
-def cpu_baseline(frame, n_threads: int, budget_s: float = 20.0) -> dict:
-    """The FP32 oracle on the host cores over whole sectors of the frame (sectors are independent),
-    as many sectors as fit about `budget_s` seconds on `n_threads` threads."""
+def cpu_sample(frame, n_sectors: int, window_clusters: int):
+    """A bounded sample of a frame for the CPU oracle: in each of the first `n_sectors` sectors, the
+    clusters whose drift coordinate lies in a window around the sector's median w holding about
+    `window_clusters` of them (the frame's occupancy and track mix, tracks crossing the window
+    edges cut there). Returns the boolean mask."""
+    m = np.zeros(frame.n, bool)
+    for s in range(n_sectors):
+        idx = np.flatnonzero(frame.sector == s)
+        if len(idx) <= window_clusters:
+            m[idx] = True
+            continue
+        w = np.sort(frame.w[idx])
+        mid = len(w) // 2
+        lo, hi = w[mid - window_clusters // 2], w[mid + window_clusters // 2]
+        m[idx[(frame.w[idx] >= lo) & (frame.w[idx] < hi)]] = True
+    return m
+
+
+def cpu_baseline(frame, n_threads: int, budget_s: float = 12.0, window: int = 0) -> dict:
+    """The FP32 oracle on the host cores over a bounded sample of the frame: whole sectors when a
+    sector fits the budget, else one window of each of `n_threads` sectors (sectors are independent and
+    run in parallel), sized to about `budget_s` seconds of wall time."""
     import oracle
-    sec = frame.sector
-    m1 = sec == 0
+    per_sector_n = frame.n / 36.0
+    if not window:
+        # calibrate on a small window of sector 0
+        m = cpu_sample(frame, 1, 20000)
+        t0 = time.perf_counter()
+        oracle.track(frame.sector[m], frame.row[m], frame.y[m], frame.w[m], precision="f32", n_threads=1)
+        per_cluster = max(time.perf_counter() - t0, 1e-4) / max(int(m.sum()), 1)
+        window = int(min(per_sector_n, max(20000, budget_s / per_cluster)))
+    k = int(min(36, max(1, n_threads)))
+    m = cpu_sample(frame, k, window)
     t0 = time.perf_counter()
-    oracle.track(sec[m1], frame.row[m1], frame.y[m1], frame.w[m1], precision="f32", n_threads=1)
-    per_sector = max(time.perf_counter() - t0, 1e-3)
-    k = int(min(36, max(1, budget_s * n_threads / per_sector)))
-    m = sec < k
-    t0 = time.perf_counter()
-    oracle.track(sec[m], frame.row[m], frame.y[m], frame.w[m], precision="f32", n_threads=n_threads)
+    oracle.track(frame.sector[m], frame.row[m], frame.y[m], frame.w[m], precision="f32", n_threads=n_threads)
     dt = time.perf_counter() - t0
     n = int(m.sum())
-    return {"value": n / dt, "unit": UNIT, "cores": int(n_threads), "kind": "oracle",
-            "sample": f"sectors 0-{k - 1} of the workload frame ({n} clusters), FP32 oracle, {dt:.2f} s"}
+    what = (f"sectors 0-{k - 1} whole" if window >= per_sector_n else
+            f"sectors 0-{k - 1}, in each the {window} clusters of a drift-coordinate window around its median")
+    return {"value": n / dt, "unit": UNIT, "cores": int(n_threads), "kind": "oracle", "window": window,
+            "sample": f"{what} ({n} clusters of the workload frame), FP32 oracle, {dt:.2f} s"}
 
 
-def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_frames: int, loads, seed: int = 5,
+def time_ordered_frames(frame):
+    """The frame's clusters reordered by the time of the collision they belong to (noise clusters by
+    their drift coordinate), and the start of each collision's run: the clusters of collisions
+    [a, a + n) in time order are then one contiguous slice, a frame of n collisions with the
+    occupancy of the full frame. Returns (sector, row, y, w, offsets[n_collisions + 1])."""
+    tc = frame.coll_tc
+    order_c = np.argsort(tc, kind="stable")
+    rank_c = np.empty_like(order_c)
+    rank_c[order_c] = np.arange(len(tc))
+    tt = frame.truth_track
+    coll = frame.tracks["coll"]
+    key = np.empty(frame.n, np.int32)
+    sig = tt >= 0
+    key[sig] = rank_c[coll[tt[sig]]]
+    # a noise cluster belongs to the last collision before the time its w stands for (mid drift)
+    t_nom = (frame.w[~sig].astype(np.float64) - 125.0) / (250.0 / 90.0)
+    key[~sig] = np.clip(np.searchsorted(np.sort(tc), t_nom, side="right") - 1, 0, len(tc) - 1)
+    order = np.argsort(key, kind="stable")
+    off = np.zeros(len(tc) + 1, np.int64)
+    off[1:] = np.cumsum(np.bincount(key, minlength=len(tc)))
+    return (frame.sector[order], frame.row[order], frame.y[order], frame.w[order], off)
+
+
+def serving_benchmark(tpc, torch, frame, *, max_collisions: int, n_frames: int, loads, seed: int = 5,
                       budget_gb: float = 80.0, params: dict | None = None):
     """Frame p50/p99 latency and throughput, served (continuous batching, tpc_submit_frame/tpc_poll)
     against plain one-frame-at-a-time tracking (load, track, read back), for a Poisson stream of
-    frames with collision counts uniform in 1..max_collisions (drawn from a pool of generated frames).
-    Loads are arrival rates relative to the plain path's mean service rate. Latency = time from a
-    frame's arrival to its tracks being readable on the host."""
-    import torch
+    frames with collision counts uniform in 1..max_collisions. Each request is n consecutive
+    collisions (in time) of the full-size frame, so requests have its occupancy and multiplicity law
+    and need no generation: they are views of one page-locked copy of its clusters. Loads are
+    arrival rates relative to the plain path's mean service rate, measured on the first frames of
+    the stream. Latency = time from a frame's arrival to its tracks being readable on the host."""
     rng = np.random.default_rng(seed)
-    colls = rng.integers(1, max_collisions + 1, pool_size)
-    pool = [synth.generate("serve", n_collisions=int(c), frame_id=i) for i, c in enumerate(colls)]
-    # requests arrive in pinned host memory (both arms read the same buffers)
-    for f in pool:
-        for k in ("sector", "row", "y", "w"):
-            setattr(f, k, torch.from_numpy(np.ascontiguousarray(getattr(f, k))).pin_memory().numpy())
+    sec, row, y, w, off = time_ordered_frames(frame)
+    nc = len(off) - 1
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (sec, row, y, w)]
+    arrs = [p.numpy() for p in pin]
+    n_req = rng.integers(1, min(max_collisions, nc) + 1, size=n_frames * len(loads) + 20)
+    a_req = np.array([rng.integers(0, nc - k + 1) for k in n_req])
+    reqs = [(int(off[a]), int(off[a + k])) for a, k in zip(a_req, n_req)]
     params = params or {}
     plain = tpc.Tracker(**params)
 
-    def plain_run(f):
+    def view(r):
+        return [x[r[0]:r[1]] for x in arrs]
+
+    def plain_run(r):
         # one frame at a time: upload, track, read the tracks back (views of the read-back block)
-        h = plain.load(f.sector, f.row, f.y, f.w)
+        h = plain.load(*view(r))
         plain.track(h)
         plain.tracks(h, copy=False)
         plain.release(h)
 
-    for f in pool[:2]:
-        plain_run(f)
+    for r in reqs[:3]:
+        plain_run(r)
     t0 = time.perf_counter()
-    for f in pool:
-        plain_run(f)
-    service = (time.perf_counter() - t0) / pool_size
-    out = {"workload": f"Poisson stream, frames of U{{1..{max_collisions}}} collisions (pool of {pool_size})",
-           "mean_plain_service_ms": service * 1e3, "budget_gb": budget_gb, "points": []}
+    for r in reqs[3:20]:
+        plain_run(r)
+    service = (time.perf_counter() - t0) / 17
+    mean_clusters = float(np.mean([b - a for a, b in reqs]))
+    out = {"workload": f"Poisson stream of frames of U{{1..{max_collisions}}} consecutive collisions of the "
+                       f"full-size frame (mean {mean_clusters:.3g} clusters)",
+           "mean_plain_service_ms": service * 1e3, "budget_gb": budget_gb, "frames_per_rate": n_frames,
+           "points": []}
     srv = tpc.Tracker(hbm_budget=int(budget_gb * (1 << 30)), **params)
-    # warm-up: slot workspaces allocated and their graphs captured before timing
-    warm = [srv.submit(f.sector, f.row, f.y, f.w) for f in pool[:6]]
+    # warm-up: slot workspaces allocated and their graphs captured before timing (the largest
+    # request first, so no workspace grows inside the timed stream)
+    warm = sorted(reqs[:20], key=lambda r: r[0] - r[1])[:4]
+    tks = [srv.submit(*view(r)) for r in warm]
     got = []
-    while len(got) < len(warm):
-        got += srv.poll(64, 100000)
+    while len(got) < len(tks):
+        got += srv.poll(64, 200000)
     for t in got:
         srv.release(t)
-    for load in loads:
+    for li, load in enumerate(loads):
         lam = load / service
         arrivals = np.cumsum(rng.exponential(1.0 / lam, n_frames))
-        pick = rng.integers(0, pool_size, n_frames)
-        clusters = float(sum(pool[k].n for k in pick))
+        batch = reqs[20 + li * n_frames: 20 + (li + 1) * n_frames]
+        clusters = float(sum(b - a for a, b in batch))
         # plain: one frame at a time in arrival order
         lat = []
         t0 = time.perf_counter()
-        for a, k in zip(arrivals, pick):
+        for a, r in zip(arrivals, batch):
             now = time.perf_counter() - t0
             if now < a:
                 time.sleep(a - now)
-            plain_run(pool[k])
+            plain_run(r)
             lat.append(time.perf_counter() - t0 - a)
         plain_span = (time.perf_counter() - t0) - arrivals[0]
         # served: submit on arrival, poll continuously
@@ -272,8 +359,7 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
         while len(done) < n_frames:
             now = time.perf_counter() - t0
             while i < n_frames and arrivals[i] <= now:
-                f = pool[pick[i]]
-                tk = srv.submit(f.sector, f.row, f.y, f.w)
+                tk = srv.submit(*view(batch[i]))
                 sub[tk] = arrivals[i]
                 i += 1
             wait_us = int(max(0.0, (arrivals[i] - now) * 1e6)) if i < n_frames else 200000
@@ -283,7 +369,7 @@ def serving_benchmark(tpc, synth, *, max_collisions: int, pool_size: int, n_fram
                 srv.release(tk)
         srv_lat = [done[t] - sub[t] for t in done]
         served_span = max(done.values()) - arrivals[0]
-        pt = {"load": load, "rate_per_s": lam, "frames": n_frames,
+        pt = {"load": load, "rate_per_s": lam, "frames": n_frames, "clusters": clusters,
               "plain": {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
                         "clusters_per_s": clusters / plain_span},
               "served": {"p50_ms": float(np.percentile(srv_lat, 50) * 1e3),
@@ -410,7 +496,7 @@ def cluster_finding_benchmark(tpc, synth, torch, workload: str, steps: int = 10,
             "roofline": {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src, "algorithmic_bytes": alg,
                          "bytes_per_digit": bpd, "bytes_per_cluster": bpc,
-                         **_traffic_fields(top, workload, {}, _cf_defaults(tpc))},
+                         **_traffic_fields(top, workload, _cf_defaults(tpc))},
             "e2e": {"value": nd / e2e_s, "unit": "digits/s", "ms": e2e_s * 1e3, "h2d_bytes_per_step": 8 * nd,
                     "d2h_bytes_per_step": 28 * nc},
             "digits_to_tracks": {"ms": chain_s * 1e3, "tracks": int(r["n_tracks"]),
@@ -492,13 +578,11 @@ def run_reference(args, ws, rank):
     frame = synth.generate(args.workload)
     cores = os.cpu_count() or 1
     budget = max(1.0, 60.0 / max(1, args.steps))
-    for _ in range(args.warmup):
-        cpu_baseline(frame, cores, budget_s=budget / 4)
-    times = []
-    for _ in range(args.steps):
-        times.append(cpu_baseline(frame, cores, budget_s=budget))
-    vals = [t["value"] for t in times]
-    value = float(np.mean(vals))
+    first = cpu_baseline(frame, cores, budget_s=budget)
+    for _ in range(max(0, args.warmup - 1)):
+        cpu_baseline(frame, cores, window=first["window"])
+    times = [cpu_baseline(frame, cores, window=first["window"]) for _ in range(args.steps)]
+    value = float(np.mean([t["value"] for t in times]))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -509,25 +593,189 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def _alu_peak_tflops(torch, sm_max_mhz) -> tuple[float, str]:
+    """FP32 issue peak of the device: SMs x 128 lanes x 2 (FMA) x the maximum SM clock."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    src = "sampled clocks.max.sm" if sm_max_mhz else "nominal maximum SM clock (no clock sample)"
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz ({src})"
+
+
+def step_rooflines(kernels: dict, stats: dict, packed: bool, hbm_peak: float) -> dict:
+    """Per step of the path: algorithmic bytes (bytes per unit x device unit count), device time and
+    the fraction of the HBM copy bandwidth."""
+    out = {}
+    for name, ks, unit, b32, b16 in STEPS:
+        ms = sum(kernels.get(k, 0.0) for k in ks)
+        units = stats.get(unit, 0)
+        alg = (b16 if packed else b32) * units
+        gbs = alg / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+        out[name] = {"kernels": list(ks), "ms": ms, "unit": unit, "units": units,
+                     "bytes_per_unit": b16 if packed else b32, "alg_bytes": alg, "achieved_gbs": gbs,
+                     "frac": gbs / hbm_peak}
+    return out
+
+
+def measure_tracking(tpc, torch, frame, *, workload: str, storage: dict, shape: dict, steps: int, warmup: int,
+                     ws: int, autotune: bool, stream, flush, e2e_window: int, tune_reps: int = 2) -> dict:
+    """Device throughput of the tracking step on one resident frame (autotuned launch shape, L2 flushed
+    before each step, CUDA events on the tracking stream), per-kernel times, the roofline of the
+    dominant kernel and of every step, and the end-to-end rate through the C-ABI from pinned host
+    memory (pipelined submit/poll, and the synchronous load/track/read loop)."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = frame.n
+    packed = bool(storage.get("packed"))
+    tr = tpc.Tracker(**shape, **storage)
+    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
+    h = tr.load(*d_in)
+    tuned = None
+    tuned_params = dict(shape)
+    if autotune and not shape:
+        # the library's autotuner picks the launch shapes on this frame (results do not depend on them)
+        rep = tr.autotune([h], reps=tune_reps)
+        tuned = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
+        tuned_params = dict(tuned)
+        tuned["configs_timed"] = len(rep["entries"])
+        for e in rep["entries"]:  # the tuner's log goes to stderr; stdout keeps the one result line
+            print("tune", workload, json.dumps(e), file=sys.stderr)
+    for _ in range(warmup):
+        tr.track(h, stream)
+    res = tr.tracks(h)
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident, L2 flushed before each step)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            tr.track(h, stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    _barrier(ws)
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    value = whole_job_value(n, steps, dev_ms / 1e3, ws)
+    dev_ms = _max_over_ranks(dev_ms, ws)
+    ms_per_step = dev_ms / steps
+    res = tr.tracks(h)
+    clocks = clk.summary()
+
+    # ---- per-kernel times (eager launches with events between kernels)
+    tr.set_timing(True)
+    kt_runs = []
+    for _ in range(5):
+        flush.zero_()
+        tr.track(h, stream)
+        tr.tracks(h)
+        kt_runs.append(tr.kernel_times())
+    tr.set_timing(False)
+    kernels = {k: float(np.median([r[k] for r in kt_runs])) for k in kt_runs[0]}
+    launches_per_step = int(sum(tr.kernel_times(launches=True).values()))
+    stats = tr.stats(h)
+    stats["tracks"] = int(res["n_tracks"])
+    dominant = max(kernels, key=kernels.get)
+    hbm_peak, peak_src = _peaks()
+    steps_rl = step_rooflines(kernels, stats, packed, hbm_peak)
+    step_of = {k: st for st, ks, *_ in STEPS for k in ks}
+    st = steps_rl[step_of[dominant]]
+    alg = st["bytes_per_unit"] * st["units"]
+    achieved = alg / (kernels[dominant] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else peak_src,
+                "alg_bytes_per_launch": alg, "bytes_per_unit": st["bytes_per_unit"], "unit_counted": st["unit"],
+                "units_per_launch": st["units"], "kernel_ms": kernels[dominant],
+                **_traffic_fields(dominant, workload, {**_method_defaults(tpc), "packed": int(packed)}, stats)}
+    whole_alg = sum(v["alg_bytes"] for v in steps_rl.values())
+    roofline["whole_path"] = {"alg_bytes": whole_alg, "ms": ms_per_step,
+                              "achieved_gbs": whole_alg / (ms_per_step * 1e-3) / 1e9,
+                              "frac": whole_alg / (ms_per_step * 1e-3) / 1e9 / hbm_peak}
+    if dominant == "tracklets":
+        peak_t, psrc = _alu_peak_tflops(torch, clocks.get("sm_max_mhz"))
+        flops = stats["steps"] * FLOPS_PER_STEP
+        roofline["alu"] = {"achieved": flops / (kernels[dominant] * 1e-3) / 1e12, "peak": peak_t,
+                           "unit": "TFLOP/s", "frac": flops / (kernels[dominant] * 1e-3) / 1e12 / peak_t,
+                           "peak_source": psrc, "alg_flops_per_launch": flops, "row_steps": stats["steps"],
+                           "flops_per_row_step": FLOPS_PER_STEP}
+
+    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region.
+    # Pipelined, as a production loop drives the serving calls: every step submits the frame from
+    # pinned host memory and every finished frame's tracks are read back to the host and released;
+    # up to e2e_window frames are in flight, so the upload and read-back of one frame overlap the
+    # tracking of another. The synchronous loop (load, track, read back) is e2e.sync_value.
+    tr.release(h)
+    del d_in
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
+    pin_np = [p.numpy() for p in pin]
+    h2d = int(sum(p.numel() * p.element_size() for p in pin))
+    e2e_tr = tpc.Tracker(**tuned_params, **storage)
+
+    def pipelined(k: int) -> int:
+        done = sub = inflight = d2h = 0
+        while done < k:
+            while sub < k and inflight < e2e_window:
+                e2e_tr.submit(*pin_np)
+                sub += 1
+                inflight += 1
+            for t in e2e_tr.poll(64, 200000):
+                out = e2e_tr.tracks(t, copy=False)  # views of the read-back tracks, until release
+                d2h = int(sum(np.asarray(v).nbytes for kk, v in out.items() if kk != "n_tracks"))
+                e2e_tr.release(t)
+                done += 1
+                inflight -= 1
+        return d2h
+
+    e2e_steps = max(3, min(steps, 10))
+    pipelined(2 * e2e_window)  # warm-up: slot workspaces and their graphs
+    torch.cuda.synchronize()
+    _barrier(ws)
+    t0 = time.perf_counter()
+    d2h = pipelined(e2e_steps)
+    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    e2e_tr.close()
+    for _ in range(2):
+        tr.run(*pin_np)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tr.run(*pin_np)
+    sync_s = _max_over_ranks(time.perf_counter() - t0, ws)
+    tr.close()
+    e2e = {"value": n * ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+           "mode": f"pipelined submit/poll, {e2e_window} frames in flight",
+           "sync_value": n * ws * e2e_steps / sync_s}
+    return {"value": value, "ms_per_step": ms_per_step, "clusters_per_frame": n,
+            "tracks_per_frame": int(res["n_tracks"]), "stats": stats, "kernels_ms": kernels, "roofline": roofline,
+            "steps_roofline": steps_rl, "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * steps,
+            "launch_shape": tuned if tuned is not None else (shape or "default"), "autotuned": tuned is not None,
+            "tuned_params": tuned_params}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="pbpb_2x10000")
+    ap.add_argument("--workload", default="full_570")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-collisions", type=int, default=40,
+    ap.add_argument("--serve-collisions", type=int, default=570,
                     help="serving stream: collisions per frame uniform in 1..N (570 = full-size frames)")
-    ap.add_argument("--serve-loads", default="0.9", help="comma-separated arrival rates / plain service rate")
-    ap.add_argument("--serve-frames", type=int, default=80)
+    ap.add_argument("--serve-loads", default="0.7,0.9,1.1",
+                    help="comma-separated arrival rates / plain service rate")
+    ap.add_argument("--serve-frames", type=int, default=300, help="frames per arrival rate")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-16bit", action="store_true", help="skip the 16-bit storage measurement of the workload")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Pb-Pb-like frame measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-frame batched-path measurement")
     ap.add_argument("--no-compression", action="store_true", help="skip the compression-inputs measurement")
     ap.add_argument("--no-cluster-finding", action="store_true", help="skip the cluster-finding measurement")
     ap.add_argument("--cf-only", action="store_true", help="run only the cluster-finding measurement")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "packed"],
-                    help="cluster storage of the main workload: FP32 or 16-bit fixed point")
+                    help="cluster storage of the headline: FP32 or 16-bit fixed point")
     ap.add_argument("--no-autotune", action="store_true", help="run the default launch shape, untuned")
     ap.add_argument("--e2e-window", type=int, default=E2E_WINDOW, help="frames in flight in the end-to-end measurement")
     ap.add_argument("--shape", default="",
@@ -565,10 +813,6 @@ def main():
     n = frame.n
     shape = json.loads(args.shape) if args.shape else {}
     storage = {"packed": 1} if args.storage == "packed" else {}
-    tr = tpc.Tracker(**shape, **storage)
-    # inputs resident in HBM
-    d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
-    h = tr.load(*d_in)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     # a dedicated (non-default) stream: the tracking kernels are launched on it, and the step
     # events are recorded on it
@@ -576,152 +820,65 @@ def main():
     torch.cuda.set_stream(stream)
 
     if args.profile_only:
+        tr = tpc.Tracker(**shape, **storage)
+        d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
+        h = tr.load(*d_in)
         tr.set_timing(True)  # eager launches, one kernel per launch for the profiler
         for _ in range(args.warmup + args.steps):
             tr.track(h, stream)
             tr.tracks(h)
+        st = tr.stats(h)
         print(json.dumps({"profile_only": True, "workload": args.workload, "clusters": n,
-                          "runs": args.warmup + args.steps}), flush=True)
+                          "runs": args.warmup + args.steps, "stats": st}), flush=True)
         tr.close()
         return
-    tuned = None
-    tuned_params = dict(shape)
-    if not shape and not args.no_autotune:
-        # the library's autotuner picks the launch shapes on this workload (results do not depend
-        # on them); the chosen shape is reported in config.launch_shape
-        rep = tr.autotune([h], reps=3)
-        tuned = {k: v for k, v in rep["best"].items() if k not in ("ms", "total_ms", "stage")}
-        tuned_params = dict(tuned)
-        tuned["configs_timed"] = len(rep["entries"])
-        for e in rep["entries"]:  # the tuner's log goes to stderr; stdout keeps the one result line
-            print("tune", json.dumps(e), file=sys.stderr)
-    for _ in range(args.warmup):
-        tr.track(h, stream)
-    res = tr.tracks(h)
-    torch.cuda.synchronize()
 
-    # ---- device-timed steps (inputs resident, L2 flushed before each step)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    _barrier(ws)
-    torch.cuda.synchronize()
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            tr.track(h, stream)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-    _barrier(ws)
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    value = whole_job_value(n, args.steps, dev_ms / 1e3, ws)
-    dev_ms = _max_over_ranks(dev_ms, ws)
-    ms_per_step = dev_ms / args.steps
-    res = tr.tracks(h)
-
-    # ---- per-kernel times (eager launches with events between kernels)
-    tr.set_timing(True)
-    kt_runs = []
-    for _ in range(5):
-        flush.zero_()
-        tr.track(h, stream)
-        tr.tracks(h)
-        kt_runs.append(tr.kernel_times())
-    tr.set_timing(False)
-    kernels = {k: float(np.median([r[k] for r in kt_runs])) for k in kt_runs[0]}
-    launches_per_step = int(sum(tr.kernel_times(launches=True).values()))
-    stats = tr.stats(h)
-    dominant = max(kernels, key=kernels.get)
-    hbm_peak, peak_src = _peaks()
-    if dominant == "tracklets":
-        flops = stats["steps"] * FLOPS_PER_STEP
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        achieved = flops / (kernels[dominant] / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, **_traffic_fields(dominant, args.workload, tuned_params,
-                                                               _method_defaults(tpc)),
-                    "peak_source": "derived (FP32 lanes x 2 x max SM clock)",
-                    "alg_flops_per_launch": flops, "row_steps": stats["steps"]}
-    else:
-        alg = ALG_BYTES_PER_CLUSTER.get(dominant, 32.0) * n
-        achieved = alg / (kernels[dominant] / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, **_traffic_fields(dominant, args.workload, tuned_params,
-                                                                   _method_defaults(tpc)),
-                    "peak_source": peak_src,
-                    "alg_bytes_per_launch": alg}
-
-    # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region.
-    # Pipelined, as a production loop drives the serving calls: every step submits the frame from
-    # pinned host memory (uploaded at submit) and every finished frame's tracks are read back to
-    # the host and released; up to E2E_WINDOW frames are in flight, so the upload and read-back of
-    # one frame overlap the tracking of another. The synchronous path (load, track, read back, one
-    # frame at a time) is reported beside it as e2e.sync_value.
-    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
-    pin_np = [p.numpy() for p in pin]
-    h2d = int(sum(p.numel() * p.element_size() for p in pin))
-    e2e_tr = tpc.Tracker(**tuned_params, **storage)
-
-    def pipelined(k: int) -> int:
-        done = sub = inflight = d2h = 0
-        while done < k:
-            while sub < k and inflight < args.e2e_window:
-                e2e_tr.submit(*pin_np)
-                sub += 1
-                inflight += 1
-            for t in e2e_tr.poll(64, 200000):
-                out = e2e_tr.tracks(t, copy=False)  # views of the read-back tracks, until release
-                d2h = int(sum(np.asarray(v).nbytes for kk, v in out.items() if kk != "n_tracks"))
-                e2e_tr.release(t)
-                done += 1
-                inflight -= 1
-        return d2h
-
-    pipelined(2 * args.e2e_window)  # warm-up: slot workspaces and their graphs
-    torch.cuda.synchronize()
-    _barrier(ws)
-    t0 = time.perf_counter()
-    d2h = pipelined(args.steps)
-    e2e_s = _max_over_ranks(time.perf_counter() - t0, ws)
-    e2e_tr.close()
-    for _ in range(2):
-        tr.run(*pin_np)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        tr.run(*pin_np)
-    sync_s = _max_over_ranks(time.perf_counter() - t0, ws)
-    e2e = {"value": n * ws * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "mode": f"pipelined submit/poll, {args.e2e_window} frames in flight",
-           "sync_value": n * ws * args.steps / sync_s}
-
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+    common = dict(steps=args.steps, warmup=args.warmup, ws=ws, autotune=not args.no_autotune, stream=stream,
+                  flush=flush, e2e_window=args.e2e_window)
+    head = measure_tracking(tpc, torch, frame, workload=args.workload, storage=storage, shape=shape, **common)
+    line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "clusters_per_frame": n, "tracks_per_frame": int(res["n_tracks"]),
-                       "tracklets_per_frame": int(stats.get("tracklets", 0)),
-                       "storage": "16-bit fixed point" if storage else "fp32", "l2": "flushed (512 MB write) before each step",
-                       "parallelism": f"replicas x{ws}",
-                       "launch_shape": tuned if tuned is not None else (shape or "default"),
-                       "autotuned": tuned is not None},
-            "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches_per_step * args.steps,
-            "kernels_ms": kernels}
-    tr.release(h)
-    if not args.no_compression:
-        line["compression"] = compression_benchmark(tpc, torch, d_in, tuned_params, storage, n)
-    if not args.no_cluster_finding:
-        line["cluster_finding"] = cluster_finding_benchmark(
-            tpc, synth, torch, args.workload, cpu=rank == 0 and ws == 1 and not args.no_cpu_baseline)
-    if not args.no_batched:
-        line["batched"] = batched_benchmark(tpc, synth, torch)
-    if not args.no_serving:
-        line["serving"] = serving_benchmark(
-            tpc, synth, max_collisions=args.serve_collisions, pool_size=12, n_frames=args.serve_frames,
-            loads=[float(x) for x in args.serve_loads.split(",")], seed=5 + rank, params=tuned_params)
+            "config": {"workload": args.workload, "clusters_per_frame": n, "tracks_per_frame": head["tracks_per_frame"],
+                       "tracklets_per_frame": int(head["stats"].get("tracklets", 0)),
+                       "storage": "16-bit fixed point" if storage else "fp32",
+                       "l2": "inputs larger than L2 (1.8 GB of clusters), and flushed (512 MB write) before each step",
+                       "parallelism": f"replicas x{ws}", "launch_shape": head["launch_shape"],
+                       "autotuned": head["autotuned"]},
+            "e2e": head["e2e"], "roofline": head["roofline"], "clocks": head["clocks"],
+            "gpu_launches": head["gpu_launches"], "kernels_ms": head["kernels_ms"],
+            "steps_roofline": head["steps_roofline"], "counters": head["stats"]}
+    if not args.no_16bit and not storage:
+        o = measure_tracking(tpc, torch, frame, workload=args.workload, storage={"packed": 1}, shape=shape, **common)
+        line["storage_16bit"] = {k: o[k] for k in ("value", "ms_per_step", "tracks_per_frame", "kernels_ms", "roofline",
+                                                    "steps_roofline", "e2e", "clocks", "launch_shape")}
+        line["storage_16bit"]["vs_fp32"] = o["value"] / head["value"]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(frame, os.cpu_count() or 1)
+    if not args.no_serving:
+        line["serving"] = serving_benchmark(
+            tpc, torch, frame, max_collisions=args.serve_collisions, n_frames=args.serve_frames,
+            loads=[float(x) for x in args.serve_loads.split(",")], seed=5 + rank, params=head["tuned_params"])
+    del frame
+    extra_name = "pbpb_2x10000"
+    if not args.no_extra or not args.no_compression:
+        ef = synth.generate(extra_name)
+        o = measure_tracking(tpc, torch, ef, workload=extra_name, storage={}, shape=shape, **common)
+        if not args.no_extra:
+            line["extra_workloads"] = {extra_name: {k: o[k] for k in ("value", "ms_per_step", "clusters_per_frame",
+                                                                      "tracks_per_frame", "kernels_ms", "roofline",
+                                                                      "e2e", "launch_shape")}}
+        if not args.no_compression:
+            d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (ef.sector, ef.row, ef.y, ef.w)]
+            line["compression"] = compression_benchmark(tpc, torch, d_in, o["tuned_params"], {}, ef.n)
+            line["compression"]["workload"] = extra_name
+    if not args.no_cluster_finding:
+        line["cluster_finding"] = cluster_finding_benchmark(
+            tpc, synth, torch, extra_name, cpu=rank == 0 and ws == 1 and not args.no_cpu_baseline)
+    if not args.no_batched:
+        line["batched"] = batched_benchmark(tpc, synth, torch)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    tr.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -4,8 +4,10 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench
 package. The product path (``paper_2009_07515_gb300``) never imports it and shares no code with it.
 
 ``tpc_oracle.c`` (sector tracking) and ``cf_oracle.c`` (cluster finding from digits) are compiled
-twice with gcc (``-ffp-contract=off``, no fast-math): REAL = double (``precision="f64"``) and REAL =
-float (``precision="f32"``). The step-by-step definition of what each computes is in its header.
+three times with gcc (``-ffp-contract=off``, no fast-math): REAL = double (``precision="f64"``), REAL =
+float with the kernels' arithmetic form (``precision="f32"``: explicit fused multiply-adds,
+reciprocals formed once) and REAL = float in plain form (``precision="f32plain"``: no fused
+multiply-add, true divisions). The step-by-step definition of what each computes is in its header.
 """
 from __future__ import annotations
 
@@ -27,14 +29,19 @@ BRUTE_FORCE = 1
 PACKED = 2
 
 
+PRECISIONS = ("f32", "f64", "f32plain")
+
+
 def _lib_path(precision: str) -> str:
     return os.path.join(_HERE, f"libtpcoracle_{precision}.so")
 
 
 def build(force: bool = False) -> None:
-    """Compile both precisions beside the source (a checker build; nothing on the product path)."""
+    """Compile every precision beside the source (a checker build; nothing on the product path):
+    ``f64``, ``f32`` (the kernels' arithmetic form: fused multiply-adds, reciprocals formed once) and
+    ``f32plain`` (plain FP32: every product and sum rounded, true divisions)."""
     with _lock:
-        for prec in ("f32", "f64"):
+        for prec in PRECISIONS:
             out = _lib_path(prec)
             if (not force and os.path.exists(out)
                     and all(os.path.getmtime(out) >= os.path.getmtime(s) for s in _SRCS)):
@@ -42,8 +49,10 @@ def build(force: bool = False) -> None:
             tmp = out + f".tmp{os.getpid()}"
             cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                    "-fPIC", "-shared"] + _SRCS + ["-o", tmp, "-lm"]
-            if prec == "f32":
+            if prec in ("f32", "f32plain"):
                 cmd.insert(1, "-DORACLE_F32")
+            if prec == "f32plain":
+                cmd.insert(1, "-DORACLE_PLAIN")
             subprocess.run(cmd, check=True)
             os.replace(tmp, out)
 
@@ -118,8 +127,8 @@ class _CFResult(ctypes.Structure):
 
 
 def _load(precision: str):
-    if precision not in ("f32", "f64"):
-        raise ValueError("precision must be 'f32' or 'f64'")
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {PRECISIONS}")
     if precision in _libs:
         return _libs[precision]
     build()
@@ -143,6 +152,10 @@ def _load(precision: str):
     f = getattr(lib, pre + "beamline")
     f.argtypes = [_P(Params), _f64p, _f64p, ctypes.c_double, ctypes.c_int, _f64p]
     f.restype = None
+    f = getattr(lib, pre + "select")
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p, _i32p,
+                  _P(ctypes.c_uint64)]
+    f.restype = ctypes.c_int
     f = getattr(lib, pre + "cf_default_params"); f.argtypes = [_P(CFParams)]; f.restype = None
     f = getattr(lib, pre + "n_pads"); f.argtypes = [ctypes.c_double, ctypes.c_int]; f.restype = ctypes.c_int
     f = getattr(lib, pre + "find_clusters")
@@ -336,6 +349,26 @@ def beamline(P, C, x_ref: float, sector: int, *, precision="f64", params: Params
                                                  C.ctypes.data_as(_f64p), float(x_ref), int(sector),
                                                  out.ctypes.data_as(_f64p))
     return out
+
+
+def select(rank, slots, n_hits: int, *, nmin: int = 10, precision: str = "f32"):
+    """Step 6 (tracklet selection) alone on caller-given tracklets of one sector: rank[t] the unique
+    start-hit rank of tracklet t, slots[t, r] its hit in row r (an index < n_hits) or -1. Returns
+    (accepted bool[nt], kept int[nt], weight uint64[n_hits])."""
+    lib = _load(precision)
+    rank = np.ascontiguousarray(rank, dtype=np.int32)
+    slots = np.ascontiguousarray(slots, dtype=np.int32).reshape(-1, 152)
+    nt = int(rank.shape[0])
+    assert slots.shape[0] == nt
+    acc = np.zeros(max(nt, 1), np.int32)
+    kept = np.zeros(max(nt, 1), np.int32)
+    weight = np.zeros(max(n_hits, 1), np.uint64)
+    rc = getattr(lib, f"oracle_{precision}_select")(
+        int(nmin), int(n_hits), nt, rank.ctypes.data_as(_i32p), slots.ctypes.data_as(_i32p),
+        acc.ctypes.data_as(_i32p), kept.ctypes.data_as(_i32p), weight.ctypes.data_as(_P(ctypes.c_uint64)))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the tracklets (code {rc})")
+    return acc[:nt].astype(bool), kept[:nt], weight[:n_hits]
 
 
 def row_x(r: int, *, precision="f64") -> float:

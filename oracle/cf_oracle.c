@@ -38,7 +38,13 @@
 #include <omp.h>
 #endif
 
-#ifdef ORACLE_F32
+#if defined(ORACLE_F32) && defined(ORACLE_PLAIN)
+/* the plain-FP32 build of the tracker oracle links this file too; the cluster finder has no fused
+ * multiply-add or reciprocal to undo, so it is the FP32 cluster finder under that build's prefix */
+typedef float real;
+#define CF_SQRT sqrtf
+#define CF_SYM(name) oracle_f32plain_##name
+#elif defined(ORACLE_F32)
 typedef float real;
 #define CF_SQRT sqrtf
 #define CF_SYM(name) oracle_f32_##name

@@ -58,7 +58,15 @@
 #include <omp.h>
 #endif
 
-#ifdef ORACLE_F32
+#if defined(ORACLE_F32) && defined(ORACLE_PLAIN)
+/* plain FP32: every sum of products rounds each product and each sum (no fused multiply-add), and
+ * every quotient is a true division (no reciprocal formed once and multiplied) */
+typedef float real;
+#define SQRT sqrtf
+#define RINT rintf
+#define FMA(a, b, c) ((a) * (b) + (c))
+#define ORACLE_SYM(name) oracle_f32plain_##name
+#elif defined(ORACLE_F32)
 typedef float real;
 #define SQRT sqrtf
 #define RINT rintf
@@ -70,6 +78,13 @@ typedef double real;
 #define RINT rint
 #define FMA fma
 #define ORACLE_SYM(name) oracle_f64_##name
+#endif
+
+/* x / v, written with the reciprocal iv = 1 / v formed once (default) or as a true division (plain) */
+#ifdef ORACLE_PLAIN
+#define QUO(x, v, iv) ((x) / (v))
+#else
+#define QUO(x, v, iv) ((x) * (iv))
 #endif
 
 #define NSEC 36
@@ -295,7 +310,7 @@ static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real 
   const real c1 = SQRT((real)1 - s1 * s1);
   const real N = s0 + s1, D = c0 + c1;
   const real iD = (real)1 / D;
-  const real dy = dx * (N * iD);                /* chord relation of a circle */
+  const real dy = dx * QUO(N, D, iD);           /* chord relation of a circle */
   const real l = SQRT(dx * dx + dy * dy);       /* chord length in the xy plane */
   const real t = l * k * (real)0.5;             /* sin of half the turning angle */
   real a = l * arc_ratio(t);                    /* arc length */
@@ -304,13 +319,13 @@ static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real 
   const real ic0 = (real)1 / c0, ic1 = (real)1 / c1, il = (real)1 / l;
   /* Jacobian d(y1, w1, s1, t, q/pT) / d(y0, w0, s0, t, q/pT) */
   const real iDD = iD * iD;
-  const real dy_ds0 = dx * ((real)2 * iD + N * (s0 * ic0 + s1 * ic1) * iDD);
-  const real dy_dk = dx * dx * (iD + N * s1 * ic1 * iDD);
+  const real dy_ds0 = dx * (QUO((real)2, D, iD) + QUO(N * (QUO(s0, c0, ic0) + QUO(s1, c1, ic1)), D * D, iDD));
+  const real dy_dk = dx * dx * (QUO((real)1, D, iD) + QUO(QUO(N * s1, c1, ic1), D * D, iDD));
   real da_dl = (real)1 / SQRT((real)1 - t * t);
   real da_dk = l * l * (real)0.5 * arc_ratio_deriv(t); /* at fixed chord */
   if (dx < 0) { da_dl = -da_dl; da_dk = -da_dk; }
-  const real dl_ds0 = dy * dy_ds0 * il;
-  const real dl_dk = dy * dy_dk * il;
+  const real dl_ds0 = QUO(dy * dy_ds0, l, il);
+  const real dl_dk = QUO(dy * dy_dk, l, il);
   real J[5][5];
   memset(J, 0, sizeof(J));
   for (int i = 0; i < 5; ++i) J[i][i] = 1;
@@ -334,7 +349,7 @@ static int kf_propagate(const ctx_t* cx, real P[5], real C[5][5], real x0, real 
    * var(t) = (1+t^2)^2 th^2; with q2 = 1/p^2 = (q/pT)^2/(1+t^2), 1/(beta p)^2 = q2 (1 + m^2 q2) */
   if (cx->ms_on && P[4] != 0) {
     const real one_tw2 = (real)1 + tw * tw;
-    const real pathf = SQRT(one_tw2) * ic1;
+    const real pathf = QUO(SQRT(one_tw2), c1, ic1);
     const real xx0 = cx->x0_row * pathf;
     const real q2 = P[4] * P[4] / one_tw2;
     const real th2 = cx->ms_c * xx0 * q2 * ((real)1 + cx->mass2 * q2);
@@ -356,7 +371,7 @@ static int propagate_state(const ctx_t* cx, real P[5], real x0, real x1) {
   const real c1 = SQRT((real)1 - s1 * s1);
   const real N = s0 + s1, D = c0 + c1;
   const real iD = (real)1 / D;
-  const real dy = dx * (N * iD);
+  const real dy = dx * QUO(N, D, iD);
   const real l = SQRT(dx * dx + dy * dy);
   const real t = l * k * (real)0.5;
   real a = l * arc_ratio(t);
@@ -373,7 +388,8 @@ static real kf_chi2(const ctx_t* cx, const real P[5], real C[5][5], real ym, rea
   const real det = S00 * S11 - S01 * S10;
   if (!(det > 0)) return (real)INFINITY;
   const real idet = (real)1 / det;
-  const real i00 = S11 * idet, i01 = -S01 * idet, i10 = -S10 * idet, i11 = S00 * idet;
+  const real i00 = QUO(S11, det, idet), i01 = QUO(-S01, det, idet), i10 = QUO(-S10, det, idet),
+             i11 = QUO(S00, det, idet);
   const real r0 = ym - P[0], r1 = wm - P[1];
   const real u0 = FMA(i01, r1, i00 * r0), u1 = FMA(i11, r1, i10 * r0); /* S^-1 r */
   return FMA(r1, u1, r0 * u0);
@@ -387,8 +403,8 @@ static void kf_update(const ctx_t* cx, real P[5], real C[5][5], real ym, real wm
   S[1][0] = C[1][0] + 0;       S[1][1] = C[1][1] + cx->r11;
   const real det = S[0][0] * S[1][1] - S[0][1] * S[1][0];
   const real idet = (real)1 / det;
-  Si[0][0] = S[1][1] * idet; Si[0][1] = -S[0][1] * idet;
-  Si[1][0] = -S[1][0] * idet; Si[1][1] = S[0][0] * idet;
+  Si[0][0] = QUO(S[1][1], det, idet); Si[0][1] = QUO(-S[0][1], det, idet);
+  Si[1][0] = QUO(-S[1][0], det, idet); Si[1][1] = QUO(S[0][0], det, idet);
   real K[5][2];
   for (int i = 0; i < 5; ++i)
     for (int l = 0; l < 2; ++l) {
@@ -928,6 +944,53 @@ static void select_tracks(const ctx_t* cx, sector_t* S) {
       S->ntr++;
     }
   }
+}
+
+static void free_sector(sector_t* S);
+
+/* Step 6 alone, on tracklets given by the caller (for the pins of the selection rule): nt tracklets
+ * of one sector, tracklet t with start-hit rank rank[t] (unique) and hit slots[t * NROW + r] (a hit
+ * index in [0, n_hits) or -1) in row r. Out: accepted[t] (0/1), kept[t] (hits it keeps, 0 if not
+ * accepted) and weight[h] (the largest key of a voting tracklet holding hit h, 0 if none). Returns 0,
+ * or -1 for a malformed input. */
+int ORACLE_SYM(select)(int32_t nmin, int64_t n_hits, int64_t nt, const int32_t* rank, const int32_t* slots,
+                       int32_t* accepted, int32_t* kept, uint64_t* weight) {
+  if (n_hits < 0 || nt < 0 || n_hits >= INT32_MAX) return -1;
+  for (int64_t i = 0; i < nt * NROW; ++i)
+    if (slots[i] < -1 || slots[i] >= n_hits) return -1;
+  ctx_t cx;
+  memset(&cx, 0, sizeof(cx));
+  cx.nmin = nmin;
+  sector_t S;
+  memset(&S, 0, sizeof(S));
+  S.n = n_hits;
+  S.nt = nt;
+  const int64_t ta = nt > 0 ? nt : 1;
+  S.t_rank = (int32_t*)malloc(ta * sizeof(int32_t));
+  S.t_nhits = (int32_t*)malloc(ta * sizeof(int32_t));
+  S.t_ok = (int32_t*)malloc(ta * sizeof(int32_t));
+  S.t_slots = (int32_t*)malloc(ta * NROW * sizeof(int32_t));
+  S.orig = (int32_t*)malloc((n_hits > 0 ? n_hits : 1) * sizeof(int32_t));
+  for (int64_t h = 0; h < n_hits; ++h) S.orig[h] = (int32_t)h;
+  for (int64_t t = 0; t < nt; ++t) {
+    int c = 0;
+    for (int r = 0; r < NROW; ++r) {
+      S.t_slots[t * NROW + r] = slots[t * NROW + r];
+      c += slots[t * NROW + r] >= 0;
+    }
+    S.t_rank[t] = rank[t];
+    S.t_nhits[t] = c;
+    S.t_ok[t] = 1;
+  }
+  select_tracks(&cx, &S);
+  for (int64_t t = 0; t < nt; ++t) { accepted[t] = 0; kept[t] = 0; }
+  for (int64_t k = 0; k < S.ntr; ++k) {
+    accepted[S.tr_t[k]] = 1;
+    kept[S.tr_t[k]] = S.tr_nk[k];
+  }
+  for (int64_t h = 0; h < n_hits; ++h) weight[h] = S.weight[h];
+  free_sector(&S);
+  return 0;
 }
 
 static void track_sector(const ctx_t* cx, sector_t* S, int brute) {

@@ -195,3 +195,26 @@ def test_two_large_digits_in_one_cell_carry_and_the_next_call_is_exact(tpc, trac
     assert e.value.code == -1
     ok = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30), (0, 0, 2, 4, 7)])
     assert_same(tracker.find_clusters(*ok, 64), oracle.find_clusters(*ok, 64, precision="f32"))
+
+
+def test_malformed_digit_beside_a_carrying_pair_leaves_the_map_clean(tpc, tracker):
+    """A frame with a malformed digit and, beside it, two digits of 40000 in one cell (their sum
+    carries into the next pad's cell) is refused; the next call sees only its own digits."""
+    bad = _cells([(0, 0, 2, 3, 40000), (0, 0, 2, 3, 40000), (0, 0, 6, 3, 20), (0, 152, 0, 0, 5)])
+    with pytest.raises(tpc.TpcError) as e:
+        tracker.find_clusters(*bad, 64)
+    assert e.value.code == -1
+    ok = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30), (0, 0, 2, 4, 7)])
+    assert_same(tracker.find_clusters(*ok, 64), oracle.find_clusters(*ok, 64, precision="f32"))
+
+
+def test_digits_whose_sum_wraps_to_their_own_charge_are_refused(tpc, tracker):
+    """Three digits of 32768 in one cell leave 32768 in the cell (the sum wraps) and carry 1 into the
+    next pad's cell: the cell still holds each digit's charge, yet the call is refused and the next
+    call is exact."""
+    bad = _cells([(0, 0, 2, 3, 32768)] * 3 + [(0, 0, 6, 3, 20)])
+    with pytest.raises(tpc.TpcError) as e:
+        tracker.find_clusters(*bad, 64)
+    assert e.value.code == -1
+    ok = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30), (0, 0, 2, 4, 7)])
+    assert_same(tracker.find_clusters(*ok, 64), oracle.find_clusters(*ok, 64, precision="f32"))

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 import synth
+from tests.helpers import compare_tracks, track_sets  # noqa: F401 (compare_tracks is imported from here too)
 
 pytestmark = pytest.mark.gpu
 
@@ -31,45 +32,6 @@ def tracker(torch_cuda):
     t = tpc.Tracker()
     yield t
     t.close()
-
-
-def track_sets(gpu, orc):
-    g = {}
-    for i in range(gpu["n_tracks"]):
-        h = gpu["hit_index"][gpu["hit_offset"][i]:gpu["hit_offset"][i + 1]]
-        g[(int(gpu["sector"][i]), tuple(h.tolist()))] = i
-    o = {}
-    for i in range(orc.n_tracks):
-        o[(int(orc.tr_sector[i]), tuple(orc.track_hits(i).tolist()))] = i
-    return g, o
-
-
-def compare_tracks(gpu, orc, *, frac=0.999, margin=1e-5):
-    """Returns the matched (gpu, oracle) index pairs after checking the parity bar."""
-    g, o = track_sets(gpu, orc)
-    common = sorted(set(g) & set(o), key=lambda k: o[k])
-    n = max(len(g), len(o), 1)
-    assert len(common) >= frac * n, f"{len(common)} identical of {len(g)} GPU / {len(o)} oracle tracks"
-    # every disagreement must sit on a near-cut decision of the oracle
-    for k in set(o) - set(g):
-        tl = orc.tr_tracklet[o[k]]
-        hits = np.array(k[1])
-        near = orc.tl_margin[tl] < margin or np.any(orc.nb_margin[hits] < margin)
-        assert near, f"untraced disagreement: oracle track {o[k]} margin {orc.tl_margin[tl]:.3g}"
-    gi = np.array([g[k] for k in common], dtype=np.int64)
-    oi = np.array([o[k] for k in common], dtype=np.int64)
-    if len(common):
-        assert np.array_equal(gpu["ndf"][gi], orc.tr_ndf[oi])
-        np.testing.assert_allclose(gpu["x_ref"][gi], orc.tr_xref[oi], rtol=1e-6)
-        np.testing.assert_allclose(gpu["param"][gi], orc.tr_param[oi], rtol=1e-4, atol=1e-6)
-        np.testing.assert_allclose(gpu["cov"][gi], orc.tr_cov[oi], rtol=1e-3, atol=1e-9)
-        np.testing.assert_allclose(gpu["chi2"][gi], orc.tr_chi2[oi], rtol=1e-3, atol=1e-5)
-        # beam line (y0, w0, var(w0), t0, z_ref): same transport of the same fit, NaN where it fails
-        gb, ob = gpu["beam"][gi].astype(np.float64), orc.tr_beam[oi]
-        assert np.array_equal(np.isnan(gb), np.isnan(ob))
-        for c, (rtol, atol) in enumerate(((1e-4, 1e-4), (1e-4, 1e-4), (1e-3, 1e-9), (1e-4, 1e-4), (1e-4, 1e-4))):
-            np.testing.assert_allclose(gb[:, c], ob[:, c], rtol=rtol, atol=atol, equal_nan=True)
-    return gi, oi
 
 
 def run_gpu(tracker, f):

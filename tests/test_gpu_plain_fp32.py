@@ -1,0 +1,80 @@
+"""The GPU path against the plain-FP32 oracle build: a real test of the disagreement bar.
+
+The default FP32 oracle evaluates the kernels' sequence of IEEE operations (fused multiply-adds,
+reciprocals formed once), so the GPU matches it bit for bit and the disagreement machinery of the
+parity bar never runs. The plain build (every product and sum rounded, true divisions) is the same
+method in another FP32 arithmetic form; against it the unchanged GPU path must still give identical
+integer results (neighbour links, cluster-to-track assignments) on at least 99.9% of the tracks, the
+tracks both find in the same order, and every disagreeing track traced to a decision near its cut.
+
+Trace margin. A decision variable here is computed from the drift coordinate w, hundreds to tens of
+thousands of cm, against a resolution of 0.1 cm: a relative difference e of the fitted state moves a
+prediction by e |w| and a chi2 near its cut of 16 (a residual of about 0.4 cm) by 2 e |w| / 0.4 of
+itself. The two forms differ by e of about 1e-6 (median state difference) on the Pb-Pb-like frame
+(|w| < 600 cm) and by the rounding of w itself (2^-9 cm at |w| > 16384 cm) on the full-size frame,
+so the two forms may decide differently up to about 1e-2 relative from a cut: the trace margin
+here is 2e-2. Fits are compared in units of the oracle fit's sigma (median < 0.01, 99th percentile
+< 0.2), as against the FP64 oracle.
+"""
+import json
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.helpers import compare_tracks
+
+pytestmark = pytest.mark.gpu
+
+MARGIN = 2e-2
+
+
+@pytest.fixture(scope="module")
+def tracker():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2009_07515_gb300 as tpc
+    tpc.build()
+    t = tpc.Tracker()
+    yield t
+    t.close()
+
+
+def _links(tracker, f):
+    h = tracker.load(f.sector, f.row, f.y, f.w)
+    tracker.track(h)
+    res = tracker.tracks(h)
+    links = [tracker.links(h, k, f.n) for k in range(4)]
+    tracker.release(h)
+    return res, links
+
+
+def test_pbpb_frame_against_plain_fp32_oracle(tracker, n_threads):
+    f = synth.generate("pbpb_2x10000")
+    gpu, links = _links(tracker, f)
+    orc = oracle.track(f.sector, f.row, f.y, f.w, precision="f32plain", n_threads=n_threads)
+    for k, name in enumerate(("up", "down", "up_c", "down_c")):
+        diff = np.flatnonzero(links[k] != getattr(orc, name))
+        assert np.all(orc.nb_margin[diff] < MARGIN), f"{name}: untraced link differences"
+    rep = {}
+    compare_tracks(gpu, orc, margin=MARGIN, fit="sigma", report=rep)
+    print("pbpb_2x10000 GPU vs plain-FP32 oracle:", json.dumps(rep))
+    assert rep["n_common"] > 30000
+
+
+def test_full_size_sector_against_plain_fp32_oracle(tracker):
+    """Sector 7 of the full-size frame (2.0e8 clusters, 570 collisions): the whole frame on the GPU,
+    the sector's clusters alone in the plain-FP32 oracle (sectors are independent)."""
+    from tests.test_gpu_fullsize import sector_view
+    f = synth.generate("full_570")
+    res = tracker.run(f.sector, f.row, f.y, f.w)
+    s = 7
+    idx = np.flatnonzero(f.sector == s)
+    orc = oracle.track(f.sector[idx], f.row[idx], f.y[idx], f.w[idx], precision="f32plain", n_threads=1)
+    gpu = sector_view(res, s, idx)
+    rep = {}
+    compare_tracks(gpu, orc, margin=MARGIN, fit="sigma", report=rep)
+    print("full_570 sector 7 GPU vs plain-FP32 oracle:", json.dumps(rep))
+    assert rep["n_common"] > 20000

@@ -256,9 +256,13 @@ def test_links_invariants():
     assert np.array_equal(res.up_c >= 0, recip)
     okc = res.up_c >= 0
     assert np.all(res.down_c[res.up_c[okc]] == i[okc])
-    # start hits: up link, no down link, chain of >= 3
+    # start hits: up link, no down link, a cleaned chain of at least 6 hits (lmin)
     for s in res.start:
-        assert res.up_c[s] >= 0 and res.down_c[s] < 0 and res.up_c[res.up_c[s]] >= 0
+        assert res.up_c[s] >= 0 and res.down_c[s] < 0
+        n, h = 0, s
+        while h >= 0:
+            n, h = n + 1, res.up_c[h]
+        assert n >= 6
 
 
 # ------------------------------------------------------------------ whole-tracker pins (T1, T2, T4)
