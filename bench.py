@@ -190,6 +190,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _progress(msg: str) -> None:
+    """One progress line on stderr with the process's resident and the host's available memory."""
+    rss = avail = -1.0
+    try:
+        with open("/proc/self/status") as fh:
+            for ln in fh:
+                if ln.startswith("VmRSS:"):
+                    rss = int(ln.split()[1]) / 2**20
+        with open("/proc/meminfo") as fh:
+            for ln in fh:
+                if ln.startswith("MemAvailable:"):
+                    avail = int(ln.split()[1]) / 2**20
+    except OSError:
+        pass
+    print(f"[bench] {msg} (rss {rss:.1f} GB, host available {avail:.1f} GB)", file=sys.stderr, flush=True)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -338,6 +355,7 @@ def serving_benchmark(tpc, torch, frame, *, max_collisions: int, n_frames: int, 
     for t in got:
         srv.release(t)
     for li, load in enumerate(loads):
+        _progress(f"serving load {load}")
         lam = load / service
         arrivals = np.cumsum(rng.exponential(1.0 / lam, n_frames))
         batch = reqs[20 + li * n_frames: 20 + (li + 1) * n_frames]
@@ -628,6 +646,7 @@ def measure_tracking(tpc, torch, frame, *, workload: str, storage: dict, shape: 
     tr = tpc.Tracker(**shape, **storage)
     d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
     h = tr.load(*d_in)
+    _progress(f"{workload} {'16-bit' if packed else 'fp32'}: loaded")
     tuned = None
     tuned_params = dict(shape)
     if autotune and not shape:
@@ -707,6 +726,7 @@ def measure_tracking(tpc, torch, frame, *, workload: str, storage: dict, shape: 
     # tracking of another. The synchronous loop (load, track, read back) is e2e.sync_value.
     tr.release(h)
     del d_in
+    _progress(f"{workload} {'16-bit' if packed else 'fp32'}: device steps done, end to end next")
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (frame.sector, frame.row, frame.y, frame.w)]
     pin_np = [p.numpy() for p in pin]
     h2d = int(sum(p.numel() * p.element_size() for p in pin))
@@ -743,6 +763,8 @@ def measure_tracking(tpc, torch, frame, *, workload: str, storage: dict, shape: 
         tr.run(*pin_np)
     sync_s = _max_over_ranks(time.perf_counter() - t0, ws)
     tr.close()
+    del pin, pin_np
+    _progress(f"{workload} {'16-bit' if packed else 'fp32'}: end to end done")
     e2e = {"value": n * ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "steps": e2e_steps,
            "mode": f"pipelined submit/poll, {e2e_window} frames in flight",
@@ -811,6 +833,7 @@ def main():
 
     frame = synth.generate(args.workload)
     n = frame.n
+    _progress(f"{args.workload} generated ({n} clusters)")
     shape = json.loads(args.shape) if args.shape else {}
     storage = {"packed": 1} if args.storage == "packed" else {}
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
@@ -854,12 +877,15 @@ def main():
                                                     "steps_roofline", "e2e", "clocks", "launch_shape")}
         line["storage_16bit"]["vs_fp32"] = o["value"] / head["value"]
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        _progress("cpu baseline")
         line["cpu_baseline"] = cpu_baseline(frame, os.cpu_count() or 1)
     if not args.no_serving:
+        _progress("serving")
         line["serving"] = serving_benchmark(
             tpc, torch, frame, max_collisions=args.serve_collisions, n_frames=args.serve_frames,
             loads=[float(x) for x in args.serve_loads.split(",")], seed=5 + rank, params=head["tuned_params"])
     del frame
+    _progress("extra workloads")
     extra_name = "pbpb_2x10000"
     if not args.no_extra or not args.no_compression:
         ef = synth.generate(extra_name)
@@ -873,10 +899,13 @@ def main():
             line["compression"] = compression_benchmark(tpc, torch, d_in, o["tuned_params"], {}, ef.n)
             line["compression"]["workload"] = extra_name
     if not args.no_cluster_finding:
+        _progress("cluster finding")
         line["cluster_finding"] = cluster_finding_benchmark(
             tpc, synth, torch, extra_name, cpu=rank == 0 and ws == 1 and not args.no_cpu_baseline)
     if not args.no_batched:
+        _progress("batched")
         line["batched"] = batched_benchmark(tpc, synth, torch)
+    _progress("done")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -27,6 +27,7 @@ _libs: dict = {}
 
 BRUTE_FORCE = 1
 PACKED = 2
+MERGE = 4
 
 
 PRECISIONS = ("f32", "f64", "f32plain")
@@ -77,6 +78,11 @@ class Params(ctypes.Structure):
         ("drift_velocity", ctypes.c_double),
         ("keep_vy", ctypes.c_double), ("keep_vw", ctypes.c_double),
         ("keep_qpt_max", ctypes.c_double),
+        ("merge_gap_rows", ctypes.c_int32),
+        ("merge_dw", ctypes.c_double),
+        ("merge_chi2_max", ctypes.c_double),
+        ("refit_passes", ctypes.c_int32),
+        ("refit_scale", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -87,6 +93,16 @@ class Params(ctypes.Structure):
 
 _P = ctypes.POINTER
 _i32p, _i64p, _f64p = _P(ctypes.c_int32), _P(ctypes.c_int64), _P(ctypes.c_double)
+
+
+class _Merge(ctypes.Structure):
+    _fields_ = [
+        ("n_tracks", ctypes.c_int64), ("n_merged", ctypes.c_int64),
+        ("mt_head", _i32p), ("mt_nseg", _i32p), ("mt_sector", _i32p), ("mt_ndf", _i32p), ("mt_nfit", _i32p),
+        ("mt_xref", _f64p), ("mt_param", _f64p), ("mt_cov", _f64p), ("mt_chi2", _f64p),
+        ("mt_hit_off", _i64p), ("mt_hits", _i32p),
+        ("tr_next", _i32p), ("tr_merge_chi2", _f64p), ("tr_outer", _f64p),
+    ]
 
 
 class _Result(ctypes.Structure):
@@ -107,6 +123,7 @@ class _Result(ctypes.Structure):
         ("tr_beam", _f64p),
         ("tr_res", _i32p), ("tr_npred", _i32p), ("keep", _P(ctypes.c_uint8)),
         ("tr_hit_off", _i64p), ("tr_hits", _i32p),
+        ("merged", _P(_Merge)),
     ]
 
 
@@ -152,6 +169,14 @@ def _load(precision: str):
     f = getattr(lib, pre + "beamline")
     f.argtypes = [_P(Params), _f64p, _f64p, ctypes.c_double, ctypes.c_int, _f64p]
     f.restype = None
+    f = getattr(lib, pre + "merge")
+    f.argtypes = [_P(Params), ctypes.c_int64, _P(ctypes.c_uint8), _f64p, _f64p, ctypes.c_int64, _i32p, _i32p,
+                  _f64p, _f64p, _i64p, _i32p, ctypes.c_int, _P(_P(_Merge))]
+    f.restype = ctypes.c_int
+    f = getattr(lib, pre + "free_merge"); f.argtypes = [_P(_Merge)]; f.restype = None
+    f = getattr(lib, pre + "rotate")
+    f.argtypes = [_P(Params), _f64p, _f64p, _f64p, ctypes.c_int, ctypes.c_int]
+    f.restype = ctypes.c_int
     f = getattr(lib, pre + "select")
     f.argtypes = [ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _i32p, _i32p, _i32p, _i32p,
                   _P(ctypes.c_uint64)]
@@ -217,6 +242,7 @@ class Result:
     keep: np.ndarray        # [n_clusters] uint8: 1 = kept by strategy B
     tr_hit_off: np.ndarray
     tr_hits: np.ndarray
+    merged: "Merged | None" = None   # step 9 (track(..., merge=True))
 
     @property
     def n_tracks(self) -> int:
@@ -229,6 +255,46 @@ class Result:
         return self.tl_hits[self.tl_hit_off[i]:self.tl_hit_off[i + 1]]
 
 
+@dataclass
+class Merged:
+    """Step 9: merged tracks in canonical order (their innermost sector track's index), each a chain
+    of sector tracks refit over all its hits; per sector track its outer partner, the merge chi2 and
+    the outer state used for matching."""
+    head: np.ndarray        # [m] sector-track index of the innermost segment
+    nseg: np.ndarray        # [m] segments
+    sector: np.ndarray      # [m] frame of the refit result (the innermost segment reached)
+    ndf: np.ndarray         # [m] 2 * fitted hits - 5
+    nfit: np.ndarray        # [m] hits the refit used
+    xref: np.ndarray        # [m] x of the innermost fitted hit
+    param: np.ndarray       # [m, 5]
+    cov: np.ndarray         # [m, 15]
+    chi2: np.ndarray        # [m]
+    hit_off: np.ndarray     # [m + 1]
+    hits: np.ndarray        # cluster indices: the segments' hits, inner segment first
+    tr_next: np.ndarray     # [n_tracks] outer partner or -1
+    tr_merge_chi2: np.ndarray
+    tr_outer: np.ndarray    # [n_tracks, 5]
+
+    @property
+    def n(self) -> int:
+        return int(self.head.shape[0])
+
+    def track_hits(self, i: int) -> np.ndarray:
+        return self.hits[self.hit_off[i]:self.hit_off[i + 1]]
+
+
+def _merged(M) -> Merged:
+    nt, m = int(M.n_tracks), int(M.n_merged)
+    off = _copy(M.mt_hit_off, m + 1, np.int64)
+    return Merged(head=_copy(M.mt_head, m, np.int32), nseg=_copy(M.mt_nseg, m, np.int32),
+                  sector=_copy(M.mt_sector, m, np.int32), ndf=_copy(M.mt_ndf, m, np.int32),
+                  nfit=_copy(M.mt_nfit, m, np.int32), xref=_copy(M.mt_xref, m, np.float64),
+                  param=_copy(M.mt_param, 5 * m, np.float64, (m, 5)), cov=_copy(M.mt_cov, 15 * m, np.float64, (m, 15)),
+                  chi2=_copy(M.mt_chi2, m, np.float64), hit_off=off, hits=_copy(M.mt_hits, int(off[-1]), np.int32),
+                  tr_next=_copy(M.tr_next, nt, np.int32), tr_merge_chi2=_copy(M.tr_merge_chi2, nt, np.float64),
+                  tr_outer=_copy(M.tr_outer, 5 * nt, np.float64, (nt, 5)))
+
+
 def _copy(ptr, n, dtype, shape=None):
     if n == 0:
         return np.zeros(shape if shape else (0,), dtype=dtype)
@@ -237,8 +303,8 @@ def _copy(ptr, n, dtype, shape=None):
 
 
 def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = None,
-          brute_force: bool = False, packed: bool = False, n_threads: int = 0) -> Result:
-    """Run the oracle tracker on one frame (clusters in caller order)."""
+          brute_force: bool = False, packed: bool = False, merge: bool = False, n_threads: int = 0) -> Result:
+    """Run the oracle tracker on one frame (clusters in caller order); merge=True adds step 9."""
     lib = _load(precision)
     pre = f"oracle_{precision}_"
     if params is None:
@@ -254,7 +320,8 @@ def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = 
     rc = getattr(lib, pre + "track")(
         ctypes.byref(params), n, sector.ctypes.data_as(_P(ctypes.c_uint8)),
         row.ctypes.data_as(_P(ctypes.c_uint8)), y.ctypes.data_as(_f64p), w.ctypes.data_as(_f64p),
-        (BRUTE_FORCE if brute_force else 0) | (PACKED if packed else 0), int(n_threads), ctypes.byref(rp))
+        (BRUTE_FORCE if brute_force else 0) | (PACKED if packed else 0) | (MERGE if merge else 0), int(n_threads),
+        ctypes.byref(rp))
     if rc != 0:
         raise ValueError(f"oracle rejected the input (code {rc})")
     try:
@@ -285,7 +352,8 @@ def track(sector, row, y, w, *, precision: str = "f32", params: Params | None = 
             tr_res=_copy(R.tr_res, 2 * int(tr_off[-1]), np.int32, (int(tr_off[-1]), 2)),
             tr_npred=_copy(R.tr_npred, ntr, np.int32),
             keep=_copy(R.keep, n, np.uint8),
-            tr_hit_off=tr_off, tr_hits=_copy(R.tr_hits, int(tr_off[-1]), np.int32))
+            tr_hit_off=tr_off, tr_hits=_copy(R.tr_hits, int(tr_off[-1]), np.int32),
+            merged=_merged(R.merged.contents) if R.merged else None)
     finally:
         getattr(lib, pre + "free_result")(rp)
     return res
@@ -349,6 +417,49 @@ def beamline(P, C, x_ref: float, sector: int, *, precision="f64", params: Params
                                                  C.ctypes.data_as(_f64p), float(x_ref), int(sector),
                                                  out.ctypes.data_as(_f64p))
     return out
+
+
+def merge(row, y, w, sector, row_ref, param, cov, hit_off, hits, *, precision: str = "f32",
+          params: Params | None = None, brute_force: bool = False) -> Merged:
+    """Step 9 alone on given sector tracks: sector, row of x_ref, fit (param [n, 5], cov [n, 15]) and
+    kept hits (hit_off, hits: cluster indices in ascending row) of each; row, y, w of the clusters."""
+    lib = _load(precision)
+    params = params or default_params(precision)
+    row = np.ascontiguousarray(row, dtype=np.uint8)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    sector = np.ascontiguousarray(sector, dtype=np.int32)
+    row_ref = np.ascontiguousarray(row_ref, dtype=np.int32)
+    param = np.ascontiguousarray(param, dtype=np.float64).reshape(-1)
+    cov = np.ascontiguousarray(cov, dtype=np.float64).reshape(-1)
+    hit_off = np.ascontiguousarray(hit_off, dtype=np.int64)
+    hits = np.ascontiguousarray(hits, dtype=np.int32)
+    mp = _P(_Merge)()
+    rc = getattr(lib, f"oracle_{precision}_merge")(
+        ctypes.byref(params), int(y.shape[0]), row.ctypes.data_as(_P(ctypes.c_uint8)), y.ctypes.data_as(_f64p),
+        w.ctypes.data_as(_f64p), int(sector.shape[0]), sector.ctypes.data_as(_i32p), row_ref.ctypes.data_as(_i32p),
+        param.ctypes.data_as(_f64p), cov.ctypes.data_as(_f64p), hit_off.ctypes.data_as(_i64p),
+        hits.ctypes.data_as(_i32p), 1 if brute_force else 0, ctypes.byref(mp))
+    if rc != 0:
+        raise ValueError(f"oracle rejected the tracks (code {rc})")
+    try:
+        return _merged(mp.contents)
+    finally:
+        getattr(lib, f"oracle_{precision}_free_merge")(mp)
+
+
+def rotate(P, C, x: float, sector_from: int, sector_to: int, *, precision="f64", params: Params | None = None):
+    """One rotation of a state (P, full 5x5 C at x) from a sector's frame into its phi neighbour's:
+    (rc, P', C', x')."""
+    lib = _load(precision)
+    params = params or default_params(precision)
+    P = np.array(P, dtype=np.float64).copy()
+    C = np.array(C, dtype=np.float64).reshape(5, 5).copy()
+    xx = ctypes.c_double(x)
+    rc = getattr(lib, f"oracle_{precision}_rotate")(ctypes.byref(params), P.ctypes.data_as(_f64p),
+                                                    C.ctypes.data_as(_f64p), ctypes.byref(xx), int(sector_from),
+                                                    int(sector_to))
+    return rc, P, C, xx.value
 
 
 def select(rank, slots, n_hits: int, *, nmin: int = 10, precision: str = "f32"):

@@ -112,6 +112,11 @@ typedef struct {
   double drift_velocity; /* cm per microsecond */
   double keep_vy, keep_vw; /* strategy-B vicinity of a good track's prediction (cm) */
   double keep_qpt_max;     /* good track: |q/pT| <= this (c/GeV) */
+  int32_t merge_gap_rows;  /* step 9: the outer segment starts 1 .. this many rows above the inner one */
+  double merge_dw;         /* step 9: |w difference| of a candidate pair at the outer segment's start (cm) */
+  double merge_chi2_max;   /* step 9: 5-parameter chi2 cut of a merge */
+  int32_t refit_passes;    /* step 9: refit passes, alternately inward and outward (odd, >= 1) */
+  double refit_scale;      /* step 9: a refit pass starts from the previous covariance times this */
 } oracle_params;
 
 void ORACLE_SYM(default_params)(oracle_params* p) {
@@ -134,6 +139,11 @@ void ORACLE_SYM(default_params)(oracle_params* p) {
   p->keep_vy = 1.0;
   p->keep_vw = 1.0;
   p->keep_qpt_max = 20.0;
+  p->merge_gap_rows = 10;
+  p->merge_dw = 5.0;
+  p->merge_chi2_max = 50.0;
+  p->refit_passes = 3;
+  p->refit_scale = 100.0;
 }
 
 typedef struct {
@@ -154,6 +164,11 @@ typedef struct {
   int ext_stop;
   real drift_len, vdrift;
   real keep_vy, keep_vw, keep_qpt_max;
+  int merge_gap_rows;
+  real merge_dw, merge_chi2_max;
+  real rot_c, rot_s;       /* cos and sin of the 20-degree angle between neighbouring sectors */
+  real refit_scale;        /* step 9: a refit pass starts from the previous covariance times this */
+  int refit_passes;        /* step 9: passes of the refit, alternately inward and outward (odd) */
 } ctx_t;
 
 static void make_ctx(const oracle_params* p, ctx_t* c) {
@@ -186,6 +201,13 @@ static void make_ctx(const oracle_params* p, ctx_t* c) {
   c->keep_vy = (real)p->keep_vy;
   c->keep_vw = (real)p->keep_vw;
   c->keep_qpt_max = (real)p->keep_qpt_max;
+  c->merge_gap_rows = p->merge_gap_rows;
+  c->merge_dw = (real)p->merge_dw;
+  c->merge_chi2_max = (real)p->merge_chi2_max;
+  c->rot_c = (real)0.93969262078590838;  /* cos(20 deg) */
+  c->rot_s = (real)0.34202014332566873;  /* sin(20 deg) */
+  c->refit_scale = (real)p->refit_scale;
+  c->refit_passes = p->refit_passes;
   for (int r = 0; r < NROW; ++r) c->x[r] = (real)85 + (real)r * ((real)160 / (real)151);
   c->want_margins = 1;
 }
@@ -578,10 +600,26 @@ typedef struct {
   uint8_t* keep;                   /* [n_clusters] step 8: strategy-B protection */
   int64_t* tr_hit_off;
   int32_t* tr_hits;                /* original indices, ascending row */
+  struct merge_out* merged;        /* step 9 (ORACLE_MERGE), else NULL */
 } oracle_result;
+
+/* Step 9 output: merged tracks in canonical order (the canonical index of their innermost sector
+ * track), each a chain of sector tracks (segments) inner to outer, refit over all their hits. */
+typedef struct merge_out {
+  int64_t n_tracks;                /* sector tracks the step read */
+  int64_t n_merged;
+  int32_t *mt_head, *mt_nseg, *mt_sector, *mt_ndf, *mt_nfit;
+  double *mt_xref, *mt_param, *mt_cov, *mt_chi2;
+  int64_t* mt_hit_off;             /* [n_merged + 1] */
+  int32_t* mt_hits;                /* original indices: the segments' hits, inner segment first */
+  int32_t* tr_next;                /* [n_tracks] the outer partner of each sector track, -1 if none */
+  double* tr_merge_chi2;           /* [n_tracks] chi2 of that merge, NaN if none */
+  double* tr_outer;                /* [n_tracks][5] the fit transported to the last hit's row, NaN if it fails */
+} merge_out;
 
 #define ORACLE_BRUTE_FORCE 1
 #define ORACLE_PACKED 2
+#define ORACLE_MERGE 4
 
 
 typedef struct {
@@ -1012,6 +1050,373 @@ static void track_sector(const ctx_t* cx, sector_t* S, int brute) {
   select_tracks(cx, S);
 }
 
+/* ------------------------------------------------------------------------------------------------
+ * Step 9: merging of sector tracks across sector boundaries and a global refit without corrections
+ * (Sec. 6: after the standalone sector tracking the tracks are refit; Table 1 of Sec. 7.2 times the
+ * refit with its sorts as "Track Fit").
+ *
+ *   outer state  each sector track's fit (at x_ref) transported row by row, with the scattering
+ *                noise of each row, to the row of its last hit;
+ *   candidates   a track B in a phi-neighbouring sector of the same drift side whose reference row
+ *                lies 1 .. merge_gap_rows rows above the last hit row of A, with
+ *                |w_B(x_ref) - w_A(outer)| <= merge_dw;
+ *   chi2         A's outer state rotated into B's frame (rotate_state) and carried by one helix step
+ *                (one row of scattering noise) to B's x_ref; chi2 = d^T (C_A + C_B)^-1 d over the 5
+ *                parameters (Cholesky); a candidate needs chi2 <= merge_chi2_max;
+ *   matching     A's best candidate and B's best candidate (smallest chi2, tie: smaller index); A and
+ *                B merge when each is the other's best; merged pairs chain inner to outer;
+ *   refit        each chain (a single sector track is a chain of one) is refit over all its hits by
+ *                the Kalman filter of step 5 in refit_passes passes (3), inward, outward, inward, each
+ *                starting at the end hit of the previous one (the first at the outermost segment's
+ *                outer state) from the previous state, its covariance multiplied by refit_scale (100:
+ *                the previous pass's information counts 1%, while the state keeps the linearisation
+ *                point; a reset to cov0 would let the first updates move the slope far from it), and
+ *                updating with every hit in turn: row by row within a segment, rotated into the next
+ *                hit's frame at a segment change and carried by one step to its row; no hit is
+ *                rejected; a failed step ends the refit at the last updated hit. The result is the
+ *                last pass's fit at the innermost hit, in its segment's frame, with that pass's chi2
+ *                and hits.
+ * Tracks never cross the central membrane in the workloads here (primaries from z = 0), so no A/C
+ * pair is formed.
+ * ---------------------------------------------------------------------------------------------- */
+
+/* The state at x in the frame of angle alpha, expressed in the frame of angle alpha + d (cd = cos d,
+ * sd = sin d): the point keeps its place, x' = x cd + y sd, y' = y cd - x sd, and the direction
+ * angle drops by d. The covariance is carried at fixed x' to first order: a change dy at fixed x
+ * moves the point off the line x' = const by sd dy, and the state is moved back along the track to
+ * it, so dy' = (cos phi / cos phi') dy, dw' = -t sd / cos phi' dy, d sin phi' = -k sd dy +
+ * (cos phi' / cos phi) d sin phi. Returns 1 if cos phi' <= 0 or |sin phi'| >= max_sin. */
+static int rotate_state(const ctx_t* cx, real P[5], real C[5][5], real* x, real cd, real sd) {
+  const real s = P[2];
+  const real c = SQRT((real)1 - s * s);
+  const real s1 = s * cd - c * sd;
+  const real c1 = c * cd + s * sd;
+  if (!(c1 > 0) || !(absr(s1) < cx->max_sin)) return 1;
+  const real x1 = *x * cd + P[0] * sd;
+  const real y1 = P[0] * cd - *x * sd;
+  const real k = cx->kq * P[4];
+  const real ic = (real)1 / c, ic1 = (real)1 / c1;
+  real J[5][5];
+  memset(J, 0, sizeof(J));
+  for (int i = 0; i < 5; ++i) J[i][i] = 1;
+  J[0][0] = QUO(c, c1, ic1);
+  J[1][0] = -QUO(P[3] * sd, c1, ic1);
+  J[2][0] = -(k * sd);
+  J[2][2] = QUO(c1, c, ic);
+  real T[5][5], O[5][5];
+  mat_mul5(J, C, T);
+  mat_mul5_bt(T, J, O);
+  mirror_lower(O);
+  memcpy(C, O, sizeof(O));
+  P[0] = y1;
+  P[2] = s1;
+  *x = x1;
+  return 0;
+}
+
+/* chi2 = d^T S^-1 d for a symmetric positive definite S (lower triangle used), by Cholesky
+ * S = L L^T and forward substitution; +inf if S is not positive definite. */
+static real chi2_5(real S[5][5], const real d[5]) {
+  real L[5][5], z[5];
+  memset(L, 0, sizeof(L));
+  for (int j = 0; j < 5; ++j) {
+    real acc = S[j][j];
+    for (int k = 0; k < j; ++k) acc = FMA(-L[j][k], L[j][k], acc);
+    if (!(acc > 0)) return (real)INFINITY;
+    L[j][j] = SQRT(acc);
+    const real il = (real)1 / L[j][j];
+    for (int i = j + 1; i < 5; ++i) {
+      real a = S[i][j];
+      for (int k = 0; k < j; ++k) a = FMA(-L[i][k], L[j][k], a);
+      L[i][j] = QUO(a, L[j][j], il);
+    }
+  }
+  for (int i = 0; i < 5; ++i) {
+    real acc = d[i];
+    for (int k = 0; k < i; ++k) acc = FMA(-L[i][k], z[k], acc);
+    z[i] = QUO(acc, L[i][i], (real)1 / L[i][i]);
+  }
+  real q = 0;
+  for (int i = 0; i < 5; ++i) q = FMA(z[i], z[i], q);
+  return q;
+}
+
+static void unpack_cov(const real* c15, real C[5][5]) {
+  for (int i = 0, o = 0; i < 5; ++i)
+    for (int k = 0; k <= i; ++k, ++o) C[i][k] = C[k][i] = c15[o];
+}
+
+/* the rotation from sector a's frame to the frame of its phi neighbour b: +20 degrees if b follows a
+ * in phi, else -20 degrees */
+static real rot_sign(int sa, int sb) { return ((sa % 18) + 1) % 18 == sb % 18 ? (real)1 : (real)-1; }
+
+typedef struct { real w; int32_t t; } wkey;
+static int cmp_wkey(const void* a, const void* b) {
+  const wkey* x = (const wkey*)a;
+  const wkey* y = (const wkey*)b;
+  if (x->w < y->w) return -1;
+  if (x->w > y->w) return 1;
+  return (x->t > y->t) - (x->t < y->t);
+}
+
+static merge_out* merge_tracks(const ctx_t* cx, int64_t nt, const int32_t* sec, const int32_t* row_ref,
+                               const real* P0, const real* C0, const int64_t* hoff, const int32_t* hits,
+                               const uint8_t* crow, const real* cy, const real* cw, int brute) {
+  merge_out* M = (merge_out*)calloc(1, sizeof(merge_out));
+  const int64_t na = nt > 0 ? nt : 1;
+  M->n_tracks = nt;
+  real* PO = (real*)malloc(na * 5 * sizeof(real));
+  real* CO = (real*)malloc(na * 25 * sizeof(real));
+  int* has_out = (int*)calloc(na, sizeof(int));
+  int* last_row = (int*)malloc(na * sizeof(int));
+  M->tr_outer = (double*)malloc(na * 5 * sizeof(double));
+  /* outer states */
+  for (int64_t t = 0; t < nt; ++t) {
+    last_row[t] = hoff[t + 1] > hoff[t] ? crow[hits[hoff[t + 1] - 1]] : row_ref[t];
+    real P[5], C[5][5];
+    memcpy(P, P0 + 5 * t, sizeof(P));
+    unpack_cov(C0 + 15 * t, C);
+    int ok = 1;
+    for (int r = row_ref[t] + 1; r <= last_row[t] && ok; ++r)
+      if (kf_propagate(cx, P, C, cx->x[r - 1], cx->x[r], NULL, NULL)) ok = 0;
+    has_out[t] = ok;
+    memcpy(PO + 5 * t, P, sizeof(P));
+    memcpy(CO + 25 * t, C, sizeof(C));
+    for (int i = 0; i < 5; ++i) M->tr_outer[5 * t + i] = ok ? (double)P[i] : NAN;
+  }
+  /* each sector's tracks ordered by w at x_ref, for the candidates' w window */
+  int64_t cnt[NSEC + 1];
+  memset(cnt, 0, sizeof(cnt));
+  for (int64_t t = 0; t < nt; ++t) cnt[sec[t] + 1]++;
+  for (int q = 0; q < NSEC; ++q) cnt[q + 1] += cnt[q];
+  wkey* keys = (wkey*)malloc(na * sizeof(wkey));
+  {
+    int64_t fill[NSEC];
+    for (int q = 0; q < NSEC; ++q) fill[q] = cnt[q];
+    for (int64_t t = 0; t < nt; ++t) {
+      keys[fill[sec[t]]].w = P0[5 * t + 1];
+      keys[fill[sec[t]]++].t = (int32_t)t;
+    }
+    for (int q = 0; q < NSEC; ++q) qsort(keys + cnt[q], cnt[q + 1] - cnt[q], sizeof(wkey), cmp_wkey);
+  }
+  int32_t* bestB = (int32_t*)malloc(na * sizeof(int32_t));
+  int32_t* bestA = (int32_t*)malloc(na * sizeof(int32_t));
+  real* chiB = (real*)malloc(na * sizeof(real));
+  real* chiA = (real*)malloc(na * sizeof(real));
+  for (int64_t t = 0; t < nt; ++t) { bestB[t] = bestA[t] = -1; chiB[t] = chiA[t] = (real)INFINITY; }
+  for (int64_t a = 0; a < nt; ++a) {
+    if (!has_out[a]) continue;
+    const int side = sec[a] / 18, ka = sec[a] % 18;
+    const real wa = PO[5 * a + 1];
+    for (int dir = -1; dir <= 1; dir += 2) {
+      const int sb = side * 18 + (ka + dir + 18) % 18;
+      /* the sector's tracks with w inside the window (widened by a hair; the exact test decides) */
+      const real pad = absr(wa) * (real)1e-6 + (real)1e-6;
+      const real lo = (wa - cx->merge_dw) - pad;
+      int64_t i0 = cnt[sb], i1 = cnt[sb + 1];
+      while (!brute && i0 < i1) {
+        const int64_t mid = i0 + (i1 - i0) / 2;
+        if (keys[mid].w < lo) i0 = mid + 1; else i1 = mid;
+      }
+      if (brute) i0 = cnt[sb];
+      for (int64_t i = i0; i < cnt[sb + 1] && (brute || keys[i].w <= (wa + cx->merge_dw) + pad); ++i) {
+        const int64_t b = keys[i].t;
+        const int g = row_ref[b] - last_row[a];
+        if (g < 1 || g > cx->merge_gap_rows) continue;
+        if (!(absr(P0[5 * b + 1] - wa) <= cx->merge_dw)) continue;
+        real P[5], C[5][5], Cb[5][5], x = cx->x[last_row[a]];
+        memcpy(P, PO + 5 * a, sizeof(P));
+        memcpy(C, CO + 25 * a, sizeof(C));
+        if (rotate_state(cx, P, C, &x, cx->rot_c, rot_sign(sec[a], sb) * cx->rot_s)) continue;
+        if (kf_propagate(cx, P, C, x, cx->x[row_ref[b]], NULL, NULL)) continue;
+        unpack_cov(C0 + 15 * b, Cb);
+        real S[5][5], d[5];
+        for (int r = 0; r < 5; ++r) {
+          d[r] = P[r] - P0[5 * b + r];
+          for (int q = 0; q < 5; ++q) S[r][q] = C[r][q] + Cb[r][q];
+        }
+        const real chi = chi2_5(S, d);
+        if (!(chi <= cx->merge_chi2_max)) continue;
+        if (chi < chiB[a] || (chi == chiB[a] && b < bestB[a])) { chiB[a] = chi; bestB[a] = (int32_t)b; }
+        if (chi < chiA[b] || (chi == chiA[b] && a < bestA[b])) { chiA[b] = chi; bestA[b] = (int32_t)a; }
+      }
+    }
+  }
+  M->tr_next = (int32_t*)malloc(na * sizeof(int32_t));
+  M->tr_merge_chi2 = (double*)malloc(na * sizeof(double));
+  int32_t* prev = (int32_t*)malloc(na * sizeof(int32_t));
+  for (int64_t t = 0; t < nt; ++t) { M->tr_next[t] = -1; prev[t] = -1; M->tr_merge_chi2[t] = NAN; }
+  for (int64_t a = 0; a < nt; ++a) {
+    const int32_t b = bestB[a];
+    if (b >= 0 && bestA[b] == a) {
+      M->tr_next[a] = b;
+      prev[b] = (int32_t)a;
+      M->tr_merge_chi2[a] = (double)chiB[a];
+    }
+  }
+  /* chains and their refit */
+  int64_t nm = 0, nh = 0;
+  for (int64_t t = 0; t < nt; ++t)
+    if (prev[t] < 0) ++nm;
+  nh = nt > 0 ? hoff[nt] : 0;
+  const int64_t ma = nm > 0 ? nm : 1;
+  M->n_merged = nm;
+  M->mt_head = (int32_t*)malloc(ma * sizeof(int32_t));
+  M->mt_nseg = (int32_t*)malloc(ma * sizeof(int32_t));
+  M->mt_sector = (int32_t*)malloc(ma * sizeof(int32_t));
+  M->mt_ndf = (int32_t*)malloc(ma * sizeof(int32_t));
+  M->mt_nfit = (int32_t*)malloc(ma * sizeof(int32_t));
+  M->mt_xref = (double*)malloc(ma * sizeof(double));
+  M->mt_param = (double*)malloc(ma * 5 * sizeof(double));
+  M->mt_cov = (double*)malloc(ma * 15 * sizeof(double));
+  M->mt_chi2 = (double*)malloc(ma * sizeof(double));
+  M->mt_hit_off = (int64_t*)malloc((nm + 1) * sizeof(int64_t));
+  M->mt_hits = (int32_t*)malloc((nh > 0 ? nh : 1) * sizeof(int32_t));
+  M->mt_hit_off[0] = 0;
+  int32_t* segs = (int32_t*)malloc(na * sizeof(int32_t));
+  int64_t m = 0, oh = 0;
+  for (int64_t h0 = 0; h0 < nt; ++h0) {
+    if (prev[h0] >= 0) continue;
+    int ns = 0;
+    for (int32_t t = (int32_t)h0; t >= 0; t = M->tr_next[t]) {
+      segs[ns++] = t;
+      for (int64_t i = hoff[t]; i < hoff[t + 1]; ++i) M->mt_hits[oh++] = hits[i];
+    }
+    M->mt_head[m] = (int32_t)h0;
+    M->mt_nseg[m] = ns;
+    M->mt_hit_off[m + 1] = oh;
+    /* refit: three passes over the chain's hits (inward, outward, inward), each from the previous
+     * pass's end state with the covariance reset, starting from the outermost segment's outer state */
+    const int32_t tm = segs[ns - 1];
+    int nfit = 0;
+    real chi2sum = 0, Pr[5], Cr[5][5], xr = 0;
+    int sr = sec[h0];
+    if (has_out[tm]) {
+      int64_t nh_chain = 0;
+      for (int j = 0; j < ns; ++j) nh_chain += hoff[segs[j] + 1] - hoff[segs[j]];
+      int32_t* H = (int32_t*)malloc((nh_chain > 0 ? nh_chain : 1) * sizeof(int32_t));
+      int32_t* Hs = (int32_t*)malloc((nh_chain > 0 ? nh_chain : 1) * sizeof(int32_t));
+      int64_t q = 0;
+      for (int j = 0; j < ns; ++j)
+        for (int64_t i = hoff[segs[j]]; i < hoff[segs[j] + 1]; ++i) { H[q] = hits[i]; Hs[q++] = sec[segs[j]]; }
+      real P[5], Cs[5][5];
+      memcpy(P, PO + 5 * tm, sizeof(P));
+      memcpy(Cs, CO + 25 * tm, sizeof(Cs));
+      int ok = 1;
+      for (int pass = 0; pass < cx->refit_passes && ok; ++pass) {
+        const int inward = pass != 1;
+        real C[5][5];
+        for (int i = 0; i < 5; ++i)
+          for (int k = 0; k < 5; ++k) C[i][k] = Cs[i][k] * cx->refit_scale;
+        int cur_sec = inward ? Hs[nh_chain - 1] : Hs[0], cur_row = -2;
+        real cur_x = 0;
+        int n_pass = 0;
+        real chi_pass = 0;
+        for (int64_t k2 = 0; k2 < nh_chain; ++k2) {
+          const int64_t i = inward ? nh_chain - 1 - k2 : k2;
+          const int32_t hc = H[i];
+          const int r = crow[hc];
+          if (Hs[i] != cur_sec) {
+            if (rotate_state(cx, P, C, &cur_x, cx->rot_c, rot_sign(cur_sec, Hs[i]) * cx->rot_s)) { ok = 0; break; }
+            cur_sec = Hs[i];
+            cur_row = -1;
+          }
+          if (cur_row == -1) {
+            if (kf_propagate(cx, P, C, cur_x, cx->x[r], NULL, NULL)) { ok = 0; break; }
+          } else if (cur_row >= 0) {
+            int bad = 0;
+            if (inward)
+              for (int rr = cur_row - 1; rr >= r && !bad; --rr) bad = kf_propagate(cx, P, C, cx->x[rr + 1], cx->x[rr], NULL, NULL);
+            else
+              for (int rr = cur_row + 1; rr <= r && !bad; ++rr) bad = kf_propagate(cx, P, C, cx->x[rr - 1], cx->x[rr], NULL, NULL);
+            if (bad) { ok = 0; break; }
+          }
+          cur_row = r;
+          cur_x = cx->x[r];
+          const real chi = kf_chi2(cx, P, C, cy[hc], cw[hc]);
+          kf_update(cx, P, C, cy[hc], cw[hc]);
+          chi_pass = chi_pass + chi;
+          ++n_pass;
+          memcpy(Pr, P, sizeof(Pr));
+          memcpy(Cr, C, sizeof(Cr));
+          xr = cur_x;
+          sr = cur_sec;
+        }
+        nfit = n_pass;
+        chi2sum = chi_pass;
+        memcpy(Cs, Cr, sizeof(Cs));
+      }
+      free(H);
+      free(Hs);
+    }
+    M->mt_nfit[m] = nfit;
+    M->mt_ndf[m] = 2 * nfit - 5;
+    M->mt_sector[m] = sr;
+    M->mt_chi2[m] = nfit ? (double)chi2sum : NAN;
+    M->mt_xref[m] = nfit ? (double)xr : NAN;
+    for (int i = 0; i < 5; ++i) M->mt_param[5 * m + i] = nfit ? (double)Pr[i] : NAN;
+    for (int i = 0, o = 0; i < 5; ++i)
+      for (int k = 0; k <= i; ++k, ++o) M->mt_cov[15 * m + o] = nfit ? (double)Cr[i][k] : NAN;
+    ++m;
+  }
+  free(PO); free(CO); free(has_out); free(last_row); free(keys); free(bestB); free(bestA); free(chiB);
+  free(chiA); free(prev); free(segs);
+  return M;
+}
+
+void ORACLE_SYM(free_merge)(merge_out* M) {
+  if (!M) return;
+  free(M->mt_head); free(M->mt_nseg); free(M->mt_sector); free(M->mt_ndf); free(M->mt_nfit); free(M->mt_xref);
+  free(M->mt_param); free(M->mt_cov); free(M->mt_chi2); free(M->mt_hit_off); free(M->mt_hits); free(M->tr_next);
+  free(M->tr_merge_chi2); free(M->tr_outer);
+  free(M);
+}
+
+/* Step 9 alone on caller-given sector tracks (for the pins): nt tracks with sector, the row of
+ * x_ref, the fit (param [nt][5], cov [nt][15]) and kept hits (hit_off, hits: cluster indices,
+ * ascending row); the clusters' rows and (y, w), rounded to REAL on entry. brute = 1 tests every track of
+ * a neighbouring sector instead of the w-ordered window. Returns 0 or -1. */
+int ORACLE_SYM(merge)(const oracle_params* p, int64_t n, const uint8_t* row, const double* y, const double* w,
+                      int64_t nt, const int32_t* sector, const int32_t* row_ref, const double* param,
+                      const double* cov, const int64_t* hit_off, const int32_t* hits, int brute, merge_out** out) {
+  *out = NULL;
+  if (n < 0 || nt < 0) return -1;
+  for (int64_t t = 0; t < nt; ++t) {
+    if (sector[t] < 0 || sector[t] >= NSEC || row_ref[t] < 0 || row_ref[t] >= NROW || hit_off[t + 1] < hit_off[t])
+      return -1;
+    for (int64_t i = hit_off[t]; i < hit_off[t + 1]; ++i)
+      if (hits[i] < 0 || hits[i] >= n) return -1;
+  }
+  ctx_t cx;
+  make_ctx(p, &cx);
+  const int64_t na = n > 0 ? n : 1, ta = nt > 0 ? nt : 1;
+  real* cy = (real*)malloc(na * sizeof(real));
+  real* cw = (real*)malloc(na * sizeof(real));
+  real* P = (real*)malloc(ta * 5 * sizeof(real));
+  real* C = (real*)malloc(ta * 15 * sizeof(real));
+  for (int64_t i = 0; i < n; ++i) { cy[i] = (real)y[i]; cw[i] = (real)w[i]; }
+  for (int64_t i = 0; i < nt * 5; ++i) P[i] = (real)param[i];
+  for (int64_t i = 0; i < nt * 15; ++i) C[i] = (real)cov[i];
+  *out = merge_tracks(&cx, nt, sector, row_ref, P, C, hit_off, hits, row, cy, cw, brute);
+  free(cy); free(cw); free(P); free(C);
+  return 0;
+}
+
+/* one rotation (for the pins): the state P, C (full 5x5) at x in sector sa's frame into the frame of
+ * its phi neighbour sb; returns 0 and the new x, or 1 */
+int ORACLE_SYM(rotate)(const oracle_params* p, double* P, double* C, double* x, int sa, int sb) {
+  ctx_t cx;
+  make_ctx(p, &cx);
+  real Pr[5], Cr[5][5], xr = (real)*x;
+  for (int i = 0; i < 5; ++i) Pr[i] = (real)P[i];
+  for (int i = 0; i < 25; ++i) Cr[i / 5][i % 5] = (real)C[i];
+  const int rc = rotate_state(&cx, Pr, Cr, &xr, cx.rot_c, rot_sign(sa, sb) * cx.rot_s);
+  for (int i = 0; i < 5; ++i) P[i] = Pr[i];
+  for (int i = 0; i < 25; ++i) C[i] = Cr[i / 5][i % 5];
+  *x = xr;
+  return rc;
+}
+
 void ORACLE_SYM(free_result)(oracle_result* R) {
   if (!R) return;
   free(R->up); free(R->down); free(R->up_c); free(R->down_c); free(R->nb_margin); free(R->start);
@@ -1021,6 +1426,7 @@ void ORACLE_SYM(free_result)(oracle_result* R) {
   free(R->tr_sector); free(R->tr_ndf); free(R->tr_nhits); free(R->tr_tracklet); free(R->tr_xref);
   free(R->tr_param); free(R->tr_cov); free(R->tr_chi2); free(R->tr_hit_off); free(R->tr_hits);
   free(R->tr_beam); free(R->tr_res); free(R->tr_npred); free(R->keep);
+  ORACLE_SYM(free_merge)(R->merged);
   free(R);
 }
 
@@ -1071,6 +1477,17 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
       int64_t o = fill[sector[i]][row[i]]++;
       S->orig[o] = (int32_t)i; S->y[o] = (real)y[i]; S->w[o] = (real)w[i];
       if (flags & ORACLE_PACKED) pack_roundtrip(&S->y[o], &S->w[o]);
+    }
+  }
+  /* the tracker's view of every cluster, kept for step 9's refit */
+  real *cy = NULL, *cw = NULL;
+  if (flags & ORACLE_MERGE) {
+    cy = (real*)malloc((n > 0 ? n : 1) * sizeof(real));
+    cw = (real*)malloc((n > 0 ? n : 1) * sizeof(real));
+    for (int64_t i = 0; i < n; ++i) {
+      cy[i] = (real)y[i];
+      cw[i] = (real)w[i];
+      if (flags & ORACLE_PACKED) pack_roundtrip(&cy[i], &cw[i]);
     }
   }
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads > 0 ? n_threads : 1)
@@ -1195,6 +1612,18 @@ int ORACLE_SYM(track)(const oracle_params* p, int64_t n, const uint8_t* sector, 
     free_sector(S);
   }
   free(secs);
+  if (flags & ORACLE_MERGE) {
+    const int64_t nt = R->n_tracks, ta = nt > 0 ? nt : 1;
+    int32_t* rref = (int32_t*)malloc(ta * sizeof(int32_t));
+    real* P = (real*)malloc(ta * 5 * sizeof(real));
+    real* C = (real*)malloc(ta * 15 * sizeof(real));
+    for (int64_t t = 0; t < nt; ++t) rref[t] = R->tl_row_ref[R->tr_tracklet[t]];
+    for (int64_t i = 0; i < nt * 5; ++i) P[i] = (real)R->tr_param[i];
+    for (int64_t i = 0; i < nt * 15; ++i) C[i] = (real)R->tr_cov[i];
+    R->merged = merge_tracks(&cx, nt, R->tr_sector, rref, P, C, R->tr_hit_off, R->tr_hits, row, cy, cw,
+                             flags & ORACLE_BRUTE_FORCE);
+    free(rref); free(P); free(C); free(cy); free(cw);
+  }
   *out = R;
   return 0;
 }
