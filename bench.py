@@ -24,6 +24,8 @@ Keys beyond the base contract:
   cluster_finding  the upstream step on the Pb-Pb-like frame's digits (digits/s, kernels, roofline,
                 end to end, digits -> tracks, FP32 oracle on a sample)
   batched       16 frames of uneven occupancy in one batched graph launch against one at a time
+  merging       the step after the sector tracking on the same frame: tracks merged across sector
+                boundaries and refit (merge stage device time, merged tracks, segments)
   --impl reference   times the CPU oracle as the reference arm (this method has no other code)
 Multi-GPU (torchrun): frames are independent, so every rank tracks its own replica of the
 workload on its own GPU with no collective in the data path ("scaling": "weak").
@@ -311,7 +313,9 @@ def serving_benchmark(tpc, torch, frame, *, max_collisions: int, n_frames: int, 
     collisions (in time) of the full-size frame, so requests have its occupancy and multiplicity law
     and need no generation: they are views of one page-locked copy of its clusters. Loads are
     arrival rates relative to the plain path's mean service rate, measured on the first frames of
-    the stream. Latency = time from a frame's arrival to its tracks being readable on the host."""
+    the stream. Latency = time from a frame's arrival to its tracks being readable on the host.
+    Served frames are submitted as borrowed page-locked host input (uploaded at admission); the
+    plain path uploads each frame from the same page-locked memory before tracking it."""
     rng = np.random.default_rng(seed)
     sec, row, y, w, off = time_ordered_frames(frame)
     nc = len(off) - 1
@@ -348,7 +352,7 @@ def serving_benchmark(tpc, torch, frame, *, max_collisions: int, n_frames: int, 
     # warm-up: slot workspaces allocated and their graphs captured before timing (the largest
     # request first, so no workspace grows inside the timed stream)
     warm = sorted(reqs[:20], key=lambda r: r[0] - r[1])[:4]
-    tks = [srv.submit(*view(r)) for r in warm]
+    tks = [srv.submit(*view(r), borrow=True) for r in warm]
     got = []
     while len(got) < len(tks):
         got += srv.poll(64, 200000)
@@ -377,7 +381,7 @@ def serving_benchmark(tpc, torch, frame, *, max_collisions: int, n_frames: int, 
         while len(done) < n_frames:
             now = time.perf_counter() - t0
             while i < n_frames and arrivals[i] <= now:
-                tk = srv.submit(*view(batch[i]))
+                tk = srv.submit(*view(batch[i]), borrow=True)
                 sub[tk] = arrivals[i]
                 i += 1
             wait_us = int(max(0.0, (arrivals[i] - now) * 1e6)) if i < n_frames else 200000
@@ -395,6 +399,42 @@ def serving_benchmark(tpc, torch, frame, *, max_collisions: int, n_frames: int, 
         out["points"].append(pt)
     plain.close()
     srv.close()
+    return out
+
+
+def merging_benchmark(tpc, torch, frame, tuned_params: dict, flush, stream, reps: int = 3) -> dict:
+    """K12 on a frame: its sector tracks merged across sector boundaries and refit (Sec. 6; Table 1
+    of Sec. 7.2 "Track Fit"), measured apart from the tracking step: the device time of the merge
+    stage (CUDA events between stages, L2 flushed before each run), the merged tracks and their
+    segments."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    tr = tpc.Tracker(merge=1, **tuned_params)
+    try:
+        d_in = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (frame.sector, frame.row, frame.y, frame.w)]
+        h = tr.load(*d_in)
+        tr.track(h, stream)
+        tr.tracks(h, copy=False)
+        tr.set_timing(True)
+        times, total = [], []
+        for _ in range(reps):
+            flush.zero_()
+            tr.track(h, stream)
+            tr.tracks(h, copy=False)
+            kt = tr.kernel_times()
+            times.append(kt["merge"])
+            total.append(sum(kt.values()))
+        tr.set_timing(False)
+        res = tr.tracks(h, copy=False)
+        mg = tr.merged(h)
+        nseg = mg["n_seg"]
+        out = {"merge_ms": float(np.median(times)), "tracking_plus_merge_ms": float(np.median(total)),
+               "sector_tracks": int(res["n_tracks"]), "merged_tracks": int(mg["n_merged"]),
+               "chains_by_segments": {int(k): int(v) for k, v in zip(*np.unique(nseg, return_counts=True))},
+               "refit_failed": int(np.sum(mg["n_fit"] < np.diff(mg["hit_offset"]))),
+               "tracks_per_s": float(res["n_tracks"] / (np.median(times) * 1e-3))}
+        tr.release(h)
+    finally:
+        tr.close()
     return out
 
 
@@ -721,7 +761,8 @@ def measure_tracking(tpc, torch, frame, *, workload: str, storage: dict, shape: 
 
     # ---- end to end through the C-ABI with host buffers (pinned), copies inside the timed region.
     # Pipelined, as a production loop drives the serving calls: every step submits the frame from
-    # pinned host memory and every finished frame's tracks are read back to the host and released;
+    # pinned host memory (borrowed: uploaded on the slot's stream when the frame is admitted) and
+    # every finished frame's tracks are read back to the host and released;
     # up to e2e_window frames are in flight, so the upload and read-back of one frame overlap the
     # tracking of another. The synchronous loop (load, track, read back) is e2e.sync_value.
     tr.release(h)
@@ -736,7 +777,7 @@ def measure_tracking(tpc, torch, frame, *, workload: str, storage: dict, shape: 
         done = sub = inflight = d2h = 0
         while done < k:
             while sub < k and inflight < e2e_window:
-                e2e_tr.submit(*pin_np)
+                e2e_tr.submit(*pin_np, borrow=True)  # page-locked input, uploaded at admission
                 sub += 1
                 inflight += 1
             for t in e2e_tr.poll(64, 200000):
@@ -794,6 +835,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the Pb-Pb-like frame measurement")
     ap.add_argument("--no-batched", action="store_true", help="skip the 16-frame batched-path measurement")
     ap.add_argument("--no-compression", action="store_true", help="skip the compression-inputs measurement")
+    ap.add_argument("--no-merging", action="store_true", help="skip the merging and refit measurement")
     ap.add_argument("--no-cluster-finding", action="store_true", help="skip the cluster-finding measurement")
     ap.add_argument("--cf-only", action="store_true", help="run only the cluster-finding measurement")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "packed"],
@@ -876,6 +918,10 @@ def main():
         line["storage_16bit"] = {k: o[k] for k in ("value", "ms_per_step", "tracks_per_frame", "kernels_ms", "roofline",
                                                     "steps_roofline", "e2e", "clocks", "launch_shape")}
         line["storage_16bit"]["vs_fp32"] = o["value"] / head["value"]
+    if not args.no_merging:
+        _progress("merging")
+        line["merging"] = merging_benchmark(tpc, torch, frame, head["tuned_params"], flush, stream)
+        line["merging"]["workload"] = args.workload
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         _progress("cpu baseline")
         line["cpu_baseline"] = cpu_baseline(frame, os.cpu_count() or 1)

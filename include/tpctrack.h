@@ -101,11 +101,26 @@ typedef struct {
                              at a time) or 1 (a warp takes a tile of 32 tracklets row by row) */
   int32_t autotune;       /* 1: the first tpc_track_batch / tpc_track_sectors call runs
                              tpc_autotune() on its batch first (0) */
+  /* merging across sector boundaries and the global refit (Sec. 6: the tracks are refit after the
+   * sector tracking; Table 1 of Sec. 7.2: "Track Fit"); results from tpc_get_merged_tracks() */
+  int32_t merge;          /* 1: also merge and refit the frame's sector tracks (0) */
+  int32_t merge_gap_rows; /* the outer segment's reference row lies 1 .. this many rows above the
+                             inner segment's last hit row (10) */
+  double merge_dw;        /* |w(outer segment at x_ref) - w(inner segment at its last row)| <= this,
+                             cm (5) */
+  double merge_chi2_max;  /* 5-parameter chi2 cut of a merge (50) */
+  int32_t refit_passes;   /* Kalman passes of the refit, alternately inward and outward, odd (3) */
+  double refit_scale;     /* a refit pass starts from the previous pass's covariance times this (100) */
 } tpc_params;
 
 /* Clusters of one time frame, structure of arrays in the caller's order (n entries each).
  * on_device = 0: host pointers, copied before tpc_load_clusters/tpc_submit_frame returns.
- * on_device = 1: device pointers borrowed until the frame's tracking has completed. */
+ * on_device = 1: device pointers borrowed until the frame's tracking has completed.
+ * on_device = 2: host pointers (page-locked for an asynchronous copy) borrowed by tpc_submit_frame
+ *                until the frame's tracks are read: the frame is uploaded when it is admitted, on
+ *                the stream of the slot that tracks it, and waits in the queue without a host copy
+ *                or device memory; the caller keeps the arrays unchanged until tpc_get_tracks() of
+ *                the frame. tpc_load_clusters() copies such input before return, as for 0. */
 typedef struct {
   const uint8_t* sector;
   const uint8_t* row;
@@ -141,6 +156,28 @@ typedef struct {
   const int32_t* residual;    /* [hit_offset[n]][2] (y, w) */
   const int32_t* n_pred;      /* [n] */
 } tpc_tracks;
+
+/* Merged tracks of a frame (tpc_params.merge = 1), owned by the context until tpc_release_frame().
+ * Each is a chain of sector tracks (segments) in phi-neighbouring sectors of one drift side, inner to
+ * outer, refit over all its hits; a sector track without partners is a chain of one. Order: the
+ * canonical index of the innermost segment. */
+typedef struct {
+  int64_t n_merged;
+  const int32_t* sector;      /* [n] sector whose frame holds the refit result (the innermost segment's) */
+  const int32_t* n_seg;       /* [n] segments */
+  const int32_t* head;        /* [n] index of the innermost segment among the frame's sector tracks */
+  const float* x_ref;         /* [n] x of the innermost refit hit */
+  const float* param;         /* [n][5] y, w, sin(phi), dw/ds, q/pT at x_ref */
+  const float* cov;           /* [n][15] lower triangle */
+  const float* chi2;          /* [n] chi2 of the last refit pass */
+  const int32_t* ndf;         /* [n] 2 * n_fit - 5 */
+  const int32_t* n_fit;       /* [n] hits of the last refit pass (all of them unless a step failed) */
+  const int64_t* hit_offset;  /* [n+1] */
+  const uint32_t* hit_index;  /* the segments' hits, inner segment first, each in ascending row */
+  int64_t n_tracks;           /* the frame's sector tracks */
+  const int32_t* track_next;  /* [n_tracks] each sector track's outer partner, -1 if none */
+  const float* track_merge_chi2; /* [n_tracks] chi2 of that merge, NaN if none */
+} tpc_merged_tracks;
 
 /* Per-kernel device time of the last tpc_track_* call on a frame or batch (CUDA events on the
  * launching stream; filled when timing is enabled with tpc_set_timing). */
@@ -183,6 +220,31 @@ int tpc_track_batch(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, v
 /* Wait (bounded) for the frame's tracking and return host views of its sector tracks (Sec. 6:
  * tracks with parameters, covariances and their clusters). */
 int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out);
+
+/* Merged and refit tracks of a tracked frame (tpc_params.merge = 1; else TPC_E_STATE): the step
+ * after the sector tracking (Sec. 6: the tracks are refit; Table 1 of Sec. 7.2 times it as "Track
+ * Fit", with its sorts). The paper gives no rule; the library computes:
+ *   outer state  each sector track's fit transported row by row, with the scattering noise of each
+ *                row, from its reference row to the row of its last hit;
+ *   candidates   a sector track B of a phi-neighbouring sector of the same frame and drift side whose
+ *                reference row lies 1 .. merge_gap_rows above A's last hit row, with
+ *                |w_B(x_ref) - w_A(outer)| <= merge_dw;
+ *   chi2         A's outer state rotated into B's frame (the point kept, the direction angle less
+ *                20 degrees, the covariance carried at fixed x to first order) and carried by one
+ *                helix step with one row of scattering noise to B's x_ref; chi2 = d^T (C_A + C_B)^-1 d
+ *                over the 5 parameters (Cholesky), at most merge_chi2_max;
+ *   matching     A's best candidate and B's best candidate (smallest chi2, tie: smaller index); the
+ *                two merge when each is the other's best; merged pairs chain inner to outer;
+ *   refit        every chain refit over all its hits by the Kalman filter of the tracklets (no hit
+ *                rejected) in refit_passes passes, inward, outward, inward, each from the previous
+ *                pass's end state with its covariance times refit_scale (the first from the
+ *                outermost segment's outer state), row by row within a segment, rotated into the next
+ *                hit's frame at a segment change and carried by one step to its row; a failed step
+ *                ends the refit at the last updated hit (NaN fit if no hit was updated).
+ * No pair across the central membrane (opposite drift sides) is formed: there the drift coordinate
+ * of the outer segment mirrors about the unknown collision time (primaries from z = 0 never cross it).
+ * Host views, valid until tpc_release_frame(). */
+int tpc_get_merged_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_merged_tracks* out);
 
 /* Free the frame's device and host memory (Sec. 7.1: memory is reused for consecutive steps and
  * frames rather than held per collision). */

@@ -113,6 +113,12 @@ class Tracker:
         self._check(self.lib.tpc_get_tracks(self.ctx, ctypes.c_uint64(frame), ctypes.byref(t)))
         return tracks_to_numpy(t, copy=copy)
 
+    def merged(self, frame: int, copy: bool = True) -> dict:
+        """The frame's merged and refit tracks (tpc_get_merged_tracks; needs merge=1)."""
+        t = _lib.tpc_merged_tracks()
+        self._check(self.lib.tpc_get_merged_tracks(self.ctx, ctypes.c_uint64(frame), ctypes.byref(t)))
+        return _lib.merged_to_numpy(t, copy=copy)
+
     def links(self, frame: int, what: int, n: int) -> np.ndarray:
         out = np.empty(n, np.int32)
         self._check(self.lib.tpc_get_links(self.ctx, ctypes.c_uint64(frame), what, out.ctypes.data, n))
@@ -191,9 +197,15 @@ class Tracker:
         return {kt.names[i].decode(): float(kt.ms[i]) for i in range(kt.n_kernels)}
 
     # --------------------------------------------------------------- serving
-    def submit(self, sector, row, y, w) -> int:
+    def submit(self, sector, row, y, w, borrow: bool = False) -> int:
+        """Serving: admit a frame (tpc_submit_frame). borrow=True lends page-locked host arrays
+        (on_device = 2): no copy is made; they must stay unchanged until the frame's tracks are read."""
         keep: list = []
         cl = make_clusters(sector, row, y, w, keep)
+        if borrow:
+            if cl.on_device:
+                raise ValueError("borrow=True takes host arrays")
+            cl.on_device = 2
         h = ctypes.c_uint64()
         self._check(self.lib.tpc_submit_frame(self.ctx, ctypes.byref(cl), ctypes.byref(h)))
         if cl.on_device:

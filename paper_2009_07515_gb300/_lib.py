@@ -66,6 +66,12 @@ class tpc_params(ctypes.Structure):
         ("k5_order", ctypes.c_int32),
         ("sel_lanes", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("merge", ctypes.c_int32),
+        ("merge_gap_rows", ctypes.c_int32),
+        ("merge_dw", ctypes.c_double),
+        ("merge_chi2_max", ctypes.c_double),
+        ("refit_passes", ctypes.c_int32),
+        ("refit_scale", ctypes.c_double),
     ]
 
 
@@ -77,6 +83,26 @@ class tpc_clusters(ctypes.Structure):
         ("w", ctypes.c_void_p),
         ("n", ctypes.c_int64),
         ("on_device", ctypes.c_int32),
+    ]
+
+
+class tpc_merged_tracks(ctypes.Structure):
+    _fields_ = [
+        ("n_merged", ctypes.c_int64),
+        ("sector", ctypes.POINTER(ctypes.c_int32)),
+        ("n_seg", ctypes.POINTER(ctypes.c_int32)),
+        ("head", ctypes.POINTER(ctypes.c_int32)),
+        ("x_ref", ctypes.POINTER(ctypes.c_float)),
+        ("param", ctypes.POINTER(ctypes.c_float)),
+        ("cov", ctypes.POINTER(ctypes.c_float)),
+        ("chi2", ctypes.POINTER(ctypes.c_float)),
+        ("ndf", ctypes.POINTER(ctypes.c_int32)),
+        ("n_fit", ctypes.POINTER(ctypes.c_int32)),
+        ("hit_offset", ctypes.POINTER(ctypes.c_int64)),
+        ("hit_index", ctypes.POINTER(ctypes.c_uint32)),
+        ("n_tracks", ctypes.c_int64),
+        ("track_next", ctypes.POINTER(ctypes.c_int32)),
+        ("track_merge_chi2", ctypes.POINTER(ctypes.c_float)),
     ]
 
 
@@ -209,6 +235,7 @@ SIGNATURES = [
     ("tpc_track_sectors", ctypes.c_int, [_ctx_p, _frame, ctypes.c_void_p]),
     ("tpc_track_batch", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_void_p]),
     ("tpc_get_tracks", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(tpc_tracks)]),
+    ("tpc_get_merged_tracks", ctypes.c_int, [_ctx_p, _frame, ctypes.POINTER(tpc_merged_tracks)]),
     ("tpc_release_frame", ctypes.c_int, [_ctx_p, _frame]),
     ("tpc_submit_frame", ctypes.c_int, [_ctx_p, ctypes.POINTER(tpc_clusters), ctypes.POINTER(_frame)]),
     ("tpc_poll", ctypes.c_int, [_ctx_p, ctypes.POINTER(_frame), ctypes.c_int32, ctypes.c_int32]),
@@ -297,3 +324,24 @@ def tracks_to_numpy(t: tpc_tracks, copy: bool = True) -> dict:
                 **({} if not t.residual else
                    dict(residual=arr(t.residual, 2 * int(off[-1]), np.int32, (int(off[-1]), 2)),
                         n_pred=arr(t.n_pred, n, np.int32))))
+
+
+def merged_to_numpy(t: tpc_merged_tracks, copy: bool = True) -> dict:
+    """numpy arrays of a tpc_merged_tracks view (copies, or views valid until the frame is released)."""
+    n, nt = int(t.n_merged), int(t.n_tracks)
+
+    def arr(ptr, count, dtype, shape=None):
+        if count == 0:
+            return np.zeros(shape if shape else (0,), dtype)
+        a = np.ctypeslib.as_array(ptr, shape=(count,))
+        if copy:
+            a = a.copy()
+        return a.reshape(shape) if shape else a
+
+    off = arr(t.hit_offset, n + 1, np.int64) if n else np.zeros(1, np.int64)
+    return dict(n_merged=n, sector=arr(t.sector, n, np.int32), n_seg=arr(t.n_seg, n, np.int32),
+                head=arr(t.head, n, np.int32), x_ref=arr(t.x_ref, n, np.float32),
+                param=arr(t.param, 5 * n, np.float32, (n, 5)), cov=arr(t.cov, 15 * n, np.float32, (n, 15)),
+                chi2=arr(t.chi2, n, np.float32), ndf=arr(t.ndf, n, np.int32), n_fit=arr(t.n_fit, n, np.int32),
+                hit_offset=off, hit_index=arr(t.hit_index, int(off[-1]), np.uint32),
+                track_next=arr(t.track_next, nt, np.int32), track_merge_chi2=arr(t.track_merge_chi2, nt, np.float32))

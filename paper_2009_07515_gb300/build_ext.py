@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtpctrack.so")
-SOURCES = ["k_grid.cu", "k_links.cu", "k_tracklet.cu", "k_select.cu", "k_cf.cu", "tpc_api.cu", "tpc_static.cu"]
+SOURCES = ["k_grid.cu", "k_links.cu", "k_tracklet.cu", "k_select.cu", "k_merge.cu", "k_cf.cu", "tpc_api.cu", "tpc_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -fmad=false: the Kalman filter and window arithmetic are kept as separately rounded IEEE
 # operations (no contraction into FMA), with IEEE division and square root (nvcc defaults).

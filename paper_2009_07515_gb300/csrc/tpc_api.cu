@@ -63,6 +63,13 @@ __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
 __global__ void k_set_ntracklets(Work);
 __global__ void k_links_to_input(Work, int, int, int32_t*);
+__global__ void k_merge_outer(Work, DevParams);
+__global__ void k_merge_fill(Work);
+__global__ void k_merge_match(Work, DevParams);
+__global__ void k_merge_link(Work);
+__global__ void k_merge_heads(Work);
+__global__ void k_merge_refit(Work, DevParams);
+__global__ void k_merge_frames(Work);
 __global__ void k_cf_fill(CfArgs);
 __global__ void k_cf_peaks(CfArgs);
 __global__ void k_cf_copy(CfArgs);
@@ -130,6 +137,13 @@ void make_dev_params(const tpc_params& p, DevParams& d) {
   d.keep_vy = (float)p.keep_vy;
   d.keep_vw = (float)p.keep_vw;
   d.keep_qpt_max = (float)p.keep_qpt_max;
+  d.merge_gap_rows = p.merge_gap_rows;
+  d.merge_dw = (float)p.merge_dw;
+  d.merge_chi2_max = (float)p.merge_chi2_max;
+  d.rot_c = (float)0.93969262078590838;  // cos(20 deg)
+  d.rot_s = (float)0.34202014332566873;  // sin(20 deg)
+  d.refit_scale = (float)p.refit_scale;
+  d.refit_passes = p.refit_passes;
   d.occ = p.bin_occupancy > 0 ? p.bin_occupancy : 2.0f;
   volatile float pitch = (float)160 / (float)151;
   d.pitch = pitch;
@@ -161,7 +175,7 @@ namespace {
 const char* kKernelNames[] = {"reset",  "seg_hist", "seg_layout", "scan_seg",  "zero_bins", "bin_rank", "scan_bins",
                               "scatter", "neighbours", "clean",   "scan_start", "starts",   "start_order",
                               "chains", "tracklets", "zero_w", "votes",    "kept",      "scan_kept", "write_tracks", "compress", "beamline",
-                              "frame_off"};
+                              "frame_off", "merge"};
 constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 
 // Launch shape: the knobs that change the speed of the sequence, never its results.
@@ -211,6 +225,8 @@ struct Frame {
   std::shared_ptr<Workspace> ws;
   int fidx = 0;
   std::vector<char> host_copy;      // serving: clusters submitted from host memory, until admitted
+  const void* borrowed[4] = {};     // serving: borrowed page-locked host input (on_device = 2)
+  bool is_borrowed = false;
   bool served = false;
   size_t input_bytes = 0;           // serving: device input counted against the waiting-input reserve
   double t_submit = 0, t_done = 0;
@@ -226,6 +242,17 @@ struct Frame {
   uint32_t* hits = nullptr;
   size_t fetch_nt = 0, fetch_nh = 0;  // tracks and hits copied into res (split by fetch_finish)
   uint32_t fetch_h0 = 0;              // the frame's first hit in the batch's hit list
+  // merged tracks (K12), views into the same block
+  bool fetch_merge = false;
+  size_t fetch_nm = 0, fetch_nmh = 0;
+  uint32_t fetch_mh0 = 0;
+  int64_t n_merged = 0;
+  int32_t *m_sector = nullptr, *m_nseg = nullptr, *m_head = nullptr, *m_ndf = nullptr, *m_nfit = nullptr;
+  float *m_xref = nullptr, *m_param = nullptr, *m_cov = nullptr, *m_chi2 = nullptr;
+  int64_t* m_hoff = nullptr;
+  uint32_t* m_hits = nullptr;
+  int32_t* tr_next = nullptr;
+  float* tr_mchi2 = nullptr;
 };
 
 // Page-locked host blocks for results, cached by capacity (powers of two from 1 MiB), so a frame's
@@ -365,7 +392,9 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   const double occ = ws->dp.occ;
   // a segment grid has at most 4 ceil(n / occ) + 260 bins, 513 in the 16-bit storage (k_seg_layout)
   ws->bcap = 4 * ((long long)std::ceil((double)ws->ncap / occ) + ws->scap) + (ctx->p.packed ? 520 : 264) * ws->scap + 16;
-  long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1});
+  const bool merge = ctx->p.merge != 0;        // merging and refit (K12)
+  const long long mbcap = merge ? (long long)nf_cap * kNSec * kMergeBins : 0;
+  long long maxscan = std::max({ws->bcap + 1, ws->scap + 1, ws->tcap + 1, mbcap + 1});
   const bool compress = ctx->p.compress != 0;  // compression inputs (K10)
   ws->scan_cap = (maxscan + 2047) / 2048 + 16;
   struct Item { void** ptr; size_t bytes; };
@@ -415,6 +444,30 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.keep, compress ? (size_t)(ws->ncap + 3) / 4 * 4 : 0},
       {(void**)&W.tr_hits, 4 * (size_t)ws->ncap},
       {(void**)&W.scan_tmp, 4 * (size_t)ws->scan_cap},
+      {(void**)&W.m_state, merge ? 80 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_info, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_bin, merge ? 4 * (size_t)(mbcap + 1) : 0},
+      {(void**)&W.m_list, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_bestA, merge ? 8 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_bestB, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_chi, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_next, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_prev, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_hidx, merge ? 4 * (size_t)(ws->tcap + 1) : 0},
+      {(void**)&W.m_hoff, merge ? 4 * (size_t)(ws->tcap + 1) : 0},
+      {(void**)&W.mt_param, merge ? 20 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_cov, merge ? 60 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_chi2, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_xref, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_sector, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_ndf, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_nfit, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_nseg, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_head, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_hoff, merge ? 8 * (size_t)ws->tcap : 0},
+      {(void**)&W.mt_hits, merge ? 4 * (size_t)ws->ncap : 0},
+      {(void**)&W.tr_next, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.tr_mchi2, merge ? 4 * (size_t)ws->tcap : 0},
   };
   size_t total = 0;
   std::vector<size_t> offs;
@@ -435,6 +488,14 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
     W.tr_npred = nullptr;
     W.keep = nullptr;
   }
+  if (!merge) {
+    W.m_state = nullptr; W.m_info = nullptr; W.m_bin = nullptr; W.m_list = nullptr; W.m_bestA = nullptr;
+    W.m_bestB = nullptr; W.m_chi = nullptr; W.m_next = nullptr; W.m_prev = nullptr; W.m_hidx = nullptr;
+    W.m_hoff = nullptr; W.mt_param = nullptr; W.mt_cov = nullptr; W.mt_chi2 = nullptr; W.mt_xref = nullptr;
+    W.mt_sector = nullptr; W.mt_ndf = nullptr; W.mt_nfit = nullptr; W.mt_nseg = nullptr; W.mt_head = nullptr;
+    W.mt_hoff = nullptr; W.mt_hits = nullptr; W.tr_next = nullptr; W.tr_mchi2 = nullptr;
+  }
+  W.mbcap = mbcap;
   W.cnt = (DevCounters*)p_cnt;
   ws->d_desc = (BatchDesc*)p_desc;
   W.batch = ws->d_desc;
@@ -607,6 +668,25 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   ++nl; k_beamline<<<2 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // frame_off
   ++nl; k_frame_offsets<<<1, 128, 0, s>>>(W);
+  mark(ki++);  // merge
+  if (W.m_state) {
+    ++nl; k_zero_u32<<<2 * G, 256, 0, s>>>(W.m_bin, nullptr, W.mbcap + 1, 0, 1);
+    ++nl; k_merge_outer<<<2 * G, 256, 0, s>>>(W, Q);
+    scan(W.m_bin, W.m_bin, nullptr, W.mbcap, &C->n_merge_bins);
+    ++nl; k_merge_fill<<<2 * G, 256, 0, s>>>(W);
+    ++nl; k_merge_match<<<4 * G, 256, 0, s>>>(W, Q);
+    ++nl; k_merge_link<<<2 * G, 256, 0, s>>>(W);
+    ++nl; k_merge_heads<<<2 * G, 256, 0, s>>>(W);
+    if (W.tcap <= kSmallScanCap) {
+      scan2(W.m_hidx, W.m_hidx, &C->n_tracks, W.tcap, &C->n_merged, W.m_hoff, W.m_hoff, &C->n_tracks, W.tcap,
+            &C->n_merged_hits);
+    } else {
+      scan(W.m_hidx, W.m_hidx, &C->n_tracks, W.tcap, &C->n_merged);
+      scan(W.m_hoff, W.m_hoff, &C->n_tracks, W.tcap, &C->n_merged_hits);
+    }
+    ++nl; k_merge_refit<<<4 * G, 128, 0, s>>>(W, Q);
+    ++nl; k_merge_frames<<<1, 128, 0, s>>>(W);
+  }
   ctx->stage_launches[kNumKernels - 1] = nl;
   if (timing) cudaEventRecord(ctx->ev[kNumKernels], s);
   cudaMemcpyAsync(ws.h_cnt, W.cnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
@@ -756,9 +836,10 @@ void release_results(tpc_ctx* ctx, Frame* f) {
 // Layout of a frame's results in its page-locked block: the output arrays, each copied from the
 // workspace's track arrays as one block.
 struct ResLayout {
-  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, beam, res, npred, bytes;
+  size_t hits, sec, ndf, xref, chi2, par, cov, hoff, beam, res, npred;
+  size_t mhits, msec, mnseg, mhead, mndf, mnfit, mxref, mpar, mcov, mchi2, mhoff, tnext, tmchi2, bytes;
 };
-ResLayout res_layout(size_t nt, size_t nh, bool compress) {
+ResLayout res_layout(size_t nt, size_t nh, bool compress, size_t nm = 0, size_t nmh = 0, bool merge = false) {
   ResLayout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align_up(off + bytes, 256); return o; };
@@ -767,6 +848,11 @@ ResLayout res_layout(size_t nt, size_t nh, bool compress) {
   L.beam = take(nt * 20);
   L.res = take(compress ? nh * 8 : 0);
   L.npred = take(compress ? nt * 4 : 0);
+  if (!merge) nm = nmh = 0;
+  L.mhits = take(nmh * 4); L.msec = take(nm * 4); L.mnseg = take(nm * 4); L.mhead = take(nm * 4);
+  L.mndf = take(nm * 4); L.mnfit = take(nm * 4); L.mxref = take(nm * 4); L.mpar = take(nm * 20);
+  L.mcov = take(nm * 60); L.mchi2 = take(nm * 4); L.mhoff = take(merge ? (nm + 1) * 8 : 0);
+  L.tnext = take(merge ? nt * 4 : 0); L.tmchi2 = take(merge ? nt * 4 : 0);
   L.bytes = off;
   return L;
 }
@@ -781,7 +867,10 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   const uint32_t h0 = c.frame_hit0[k], h1 = c.frame_hit0[k + 1];
   const size_t nt = t1 - t0, nh = h1 - h0;
   const bool compress = ws.W.tr_res != nullptr;
-  const ResLayout L = res_layout(nt, nh, compress);
+  const bool merge = ws.W.m_state != nullptr;
+  const uint32_t m0 = merge ? c.frame_merged0[k] : 0, mh0 = merge ? c.frame_mhit0[k] : 0;
+  const size_t nm = merge ? c.frame_merged0[k + 1] - m0 : 0, nmh = merge ? c.frame_mhit0[k + 1] - mh0 : 0;
+  const ResLayout L = res_layout(nt, nh, compress, nm, nmh, merge);
   release_results(ctx, f);
   size_t cap = 0;
   char* b = (char*)ctx->pinned.get(L.bytes, cap);
@@ -792,6 +881,10 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   f->fetch_nh = nh;
   f->fetch_h0 = h0;
   f->fetch_compress = compress;
+  f->fetch_merge = merge;
+  f->fetch_nm = nm;
+  f->fetch_nmh = nmh;
+  f->fetch_mh0 = mh0;
   const Work& W = ws.W;
   const auto d2h = [&](size_t o, const void* src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(b + o, src, bytes, cudaMemcpyDeviceToHost, s) : cudaSuccess;
@@ -809,13 +902,28 @@ int fetch_enqueue(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
     CK(d2h(L.res, W.tr_res + 2 * (size_t)h0, nh * 8));
     CK(d2h(L.npred, W.tr_npred + t0, nt * 4));
   }
+  if (merge) {
+    CK(d2h(L.mhits, W.mt_hits + mh0, nmh * 4));
+    CK(d2h(L.msec, W.mt_sector + m0, nm * 4));
+    CK(d2h(L.mnseg, W.mt_nseg + m0, nm * 4));
+    CK(d2h(L.mhead, W.mt_head + m0, nm * 4));
+    CK(d2h(L.mndf, W.mt_ndf + m0, nm * 4));
+    CK(d2h(L.mnfit, W.mt_nfit + m0, nm * 4));
+    CK(d2h(L.mxref, W.mt_xref + m0, nm * 4));
+    CK(d2h(L.mpar, W.mt_param + (size_t)m0 * 5, nm * 20));
+    CK(d2h(L.mcov, W.mt_cov + (size_t)m0 * 15, nm * 60));
+    CK(d2h(L.mchi2, W.mt_chi2 + m0, nm * 4));
+    CK(d2h(L.mhoff, W.mt_hoff + m0, nm * 8));
+    CK(d2h(L.tnext, W.tr_next + t0, nt * 4));
+    CK(d2h(L.tmchi2, W.tr_mchi2 + t0, nt * 4));
+  }
   return TPC_OK;
 }
 
 // Step 2, once the copies have completed: the arrays' views, hit offsets made frame-relative.
 void fetch_finish(Frame* f) {
   const size_t nt = f->fetch_nt, nh = f->fetch_nh;
-  const ResLayout L = res_layout(nt, nh, f->fetch_compress);
+  const ResLayout L = res_layout(nt, nh, f->fetch_compress, f->fetch_nm, f->fetch_nmh, f->fetch_merge);
   char* b = (char*)f->res;
   f->hits = (uint32_t*)(b + L.hits);
   f->sector = (int32_t*)(b + L.sec);
@@ -832,6 +940,25 @@ void fetch_finish(Frame* f) {
     for (size_t i = 0; i < nt; ++i) f->hoff[i] -= (int64_t)f->fetch_h0;
   f->hoff[nt] = (int64_t)nh;
   f->n_tracks = (int64_t)nt;
+  if (f->fetch_merge) {
+    const size_t nm = f->fetch_nm;
+    f->m_hits = (uint32_t*)(b + L.mhits);
+    f->m_sector = (int32_t*)(b + L.msec);
+    f->m_nseg = (int32_t*)(b + L.mnseg);
+    f->m_head = (int32_t*)(b + L.mhead);
+    f->m_ndf = (int32_t*)(b + L.mndf);
+    f->m_nfit = (int32_t*)(b + L.mnfit);
+    f->m_xref = (float*)(b + L.mxref);
+    f->m_param = (float*)(b + L.mpar);
+    f->m_cov = (float*)(b + L.mcov);
+    f->m_chi2 = (float*)(b + L.mchi2);
+    f->m_hoff = (int64_t*)(b + L.mhoff);
+    f->tr_next = (int32_t*)(b + L.tnext);
+    f->tr_mchi2 = (float*)(b + L.tmchi2);
+    for (size_t i = 0; i < nm; ++i) f->m_hoff[i] -= (int64_t)f->fetch_mh0;
+    f->m_hoff[nm] = (int64_t)f->fetch_nmh;
+    f->n_merged = (int64_t)nm;
+  }
   f->state = 5;
 }
 
@@ -875,9 +1002,10 @@ void release_ws_user(tpc_ctx* ctx, Frame* f) {
 int load_frame(tpc_ctx* ctx, const tpc_clusters* cl, Frame*& out) {
   if (!cl || cl->n < 0 || cl->n >= (1LL << 31)) return fail(ctx, TPC_E_INVAL, "bad cluster descriptor");
   if (cl->n > 0 && (!cl->sector || !cl->row || !cl->y || !cl->w)) return fail(ctx, TPC_E_INVAL, "null cluster array");
+  if (cl->on_device < 0 || cl->on_device > 2) return fail(ctx, TPC_E_INVAL, "bad on_device value");
   auto f = std::make_unique<Frame>();
   f->n = cl->n;
-  if (cl->on_device) {
+  if (cl->on_device == 1) {
     f->d_sector = (uint8_t*)cl->sector; f->d_row = (uint8_t*)cl->row;
     f->d_y = (float*)cl->y; f->d_w = (float*)cl->w;
   } else {
@@ -1053,6 +1181,12 @@ void tpc_default_params(tpc_params* p) {
   p->k5_order = 1;
   p->sel_lanes = 32;
   p->autotune = 0;
+  p->merge = 0;
+  p->merge_gap_rows = 10;
+  p->merge_dw = 5.0;
+  p->merge_chi2_max = 50.0;
+  p->refit_passes = 3;
+  p->refit_scale = 100.0;
 }
 
 const char* tpc_version(void) { return "tpctrack 0.1 (sm_103a)"; }
@@ -1072,7 +1206,9 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
       q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
       (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 72 && q.k5_regs != 80) ||
       q.k2_tma < 0 || q.k2_tma > 2 || (q.sel_lanes != 1 && q.sel_lanes != 32) ||
-      q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f) {
+      q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f ||
+      q.merge_gap_rows < 1 || q.merge_gap_rows > 150 || !(q.merge_dw >= 0) || !(q.merge_chi2_max >= 0) ||
+      q.refit_passes < 1 || q.refit_passes % 2 == 0 || q.refit_passes > 15 || !(q.refit_scale > 0)) {
     delete ctx;
     return TPC_E_INVAL;
   }
@@ -1253,6 +1389,33 @@ int tpc_get_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_tracks* out) {
   return TPC_OK;
 }
 
+int tpc_get_merged_tracks(tpc_ctx* ctx, tpc_frame_t frame, tpc_merged_tracks* out) {
+  if (!ctx || !out) return TPC_E_INVAL;
+  if (!ctx->p.merge) return fail(ctx, TPC_E_STATE, "merging is off (tpc_params.merge = 0)");
+  tpc_tracks t;
+  int rc = tpc_get_tracks(ctx, frame, &t);
+  if (rc) return rc;
+  Frame* f = find_frame(ctx, frame);
+  if (!f->fetch_merge) return fail(ctx, TPC_E_STATE, "frame was tracked without merging");
+  static const int64_t zero_offset = 0;
+  out->n_merged = f->n_merged;
+  out->sector = f->m_sector;
+  out->n_seg = f->m_nseg;
+  out->head = f->m_head;
+  out->x_ref = f->m_xref;
+  out->param = f->m_param;
+  out->cov = f->m_cov;
+  out->chi2 = f->m_chi2;
+  out->ndf = f->m_ndf;
+  out->n_fit = f->m_nfit;
+  out->hit_offset = f->m_hoff ? f->m_hoff : &zero_offset;
+  out->hit_index = f->m_hits;
+  out->n_tracks = f->n_tracks;
+  out->track_next = f->tr_next;
+  out->track_merge_chi2 = f->tr_mchi2;
+  return TPC_OK;
+}
+
 int tpc_get_counts(tpc_ctx* ctx, tpc_frame_t frame, int64_t* n_start, int64_t* n_tracks) {
   if (!ctx) return TPC_E_INVAL;
   Frame* f = find_frame(ctx, frame);
@@ -1342,15 +1505,22 @@ int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ti
   if (clusters->n < 0 || clusters->n >= (1LL << 31)) return fail(ctx, TPC_E_INVAL, "bad cluster descriptor");
   if (clusters->n > 0 && (!clusters->sector || !clusters->row || !clusters->y || !clusters->w))
     return fail(ctx, TPC_E_INVAL, "null cluster array");
+  if (clusters->on_device < 0 || clusters->on_device > 2) return fail(ctx, TPC_E_INVAL, "bad on_device value");
   if (clusters->n > ctx->slot_clusters) return fail(ctx, TPC_E_BUDGET, "frame larger than a serving slot of the HBM budget");
   auto fr = std::make_unique<Frame>();
   Frame* f = fr.get();
   f->n = clusters->n;
   f->served = true;
   const size_t in_bytes = (size_t)f->n * 10;
-  if (clusters->on_device) {
+  if (clusters->on_device == 1) {
     f->d_sector = (uint8_t*)clusters->sector; f->d_row = (uint8_t*)clusters->row;
     f->d_y = (float*)clusters->y; f->d_w = (float*)clusters->w;
+  } else if (clusters->on_device == 2) {
+    // borrowed host memory: read by an asynchronous copy on the slot's stream at admission, so
+    // neither a host copy nor device memory is held while the frame waits
+    f->borrowed[0] = clusters->sector; f->borrowed[1] = clusters->row;
+    f->borrowed[2] = clusters->y; f->borrowed[3] = clusters->w;
+    f->is_borrowed = true;
   } else if (ctx->queued_input_bytes + in_bytes <= (size_t)(ctx->p.hbm_budget / 8)) {
     // uploaded now (inputs of waiting frames may use an eighth of the budget); the copy ends
     // before return, so the caller's buffers are free again
@@ -1390,7 +1560,7 @@ int tpc_submit_frame(tpc_ctx* ctx, const tpc_clusters* clusters, tpc_frame_t* ti
 namespace {
 // upload a queued host frame on the slot's stream
 int upload_frame(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
-  if (f->host_copy.empty() || f->d_block) return TPC_OK;
+  if ((f->host_copy.empty() && !f->is_borrowed) || f->d_block) return TPC_OK;
   const size_t n = (size_t)f->n;
   const size_t o1 = align_up(n, 256), o2 = o1 + align_up(n, 256), o3 = o2 + align_up(4 * n, 256);
   const size_t bytes = o3 + align_up(4 * n, 256) + 256;
@@ -1398,7 +1568,12 @@ int upload_frame(tpc_ctx* ctx, Frame* f, cudaStream_t s) {
   if (e != cudaSuccess) { cudaGetLastError(); return fail(ctx, TPC_E_NOMEM, "input allocation failed"); }
   char* b = (char*)f->d_block;
   f->d_sector = (uint8_t*)b; f->d_row = (uint8_t*)(b + o1); f->d_y = (float*)(b + o2); f->d_w = (float*)(b + o3);
-  if (n) {
+  if (n && f->is_borrowed) {
+    CK(cudaMemcpyAsync(f->d_sector, f->borrowed[0], n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f->d_row, f->borrowed[1], n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f->d_y, f->borrowed[2], 4 * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(f->d_w, f->borrowed[3], 4 * n, cudaMemcpyHostToDevice, s));
+  } else if (n) {
     const char* h = f->host_copy.data();
     CK(cudaMemcpyAsync(f->d_sector, h, n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(f->d_row, h + n, n, cudaMemcpyHostToDevice, s));

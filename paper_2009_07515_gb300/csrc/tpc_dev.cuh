@@ -40,6 +40,7 @@ constexpr int kSegPerFrame = kNSec * kNRow;  // 5472
 constexpr int kMaxFrames = 64;               // frames per batched launch
 constexpr int kHistThreads = 1024;           // threads per block of the segment histogram
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
+constexpr int kMergeBins = 2048;             // w bins per (frame, sector) of the merge step's search
 
 // error bits (device error word)
 constexpr uint32_t kErrInput = 1u;      // malformed cluster (sector/row range, non-finite)
@@ -65,6 +66,13 @@ struct DevParams {
   float keep_vy, keep_vw;        // strategy-B vicinity of a good track's prediction (cm)
   float keep_qpt_max;            // good track: |q/pT| <= this
   float cov0[5];
+  // K12 merging and refit
+  int merge_gap_rows;            // the outer segment starts 1 .. this many rows above the inner one
+  float merge_dw;                // |w difference| of a candidate pair (cm)
+  float merge_chi2_max;          // 5-parameter chi2 cut of a merge
+  float rot_c, rot_s;            // cos and sin of the 20-degree angle between neighbouring sectors
+  float refit_scale;             // a refit pass starts from the previous covariance times this
+  int refit_passes;              // refit passes, alternately inward and outward
   float occ;                     // target clusters per grid bin
   float aspect;                  // w/y extent of a grid bin (the neighbour window's aspect)
   float x[kNRow];                // row radii
@@ -111,6 +119,11 @@ struct DevCounters {
   uint32_t frame_start0[kMaxFrames + 1];  // first start index of each frame
   uint32_t frame_track0[kMaxFrames + 1];  // first track index of each frame
   uint32_t frame_hit0[kMaxFrames + 1];    // first output hit of each frame
+  uint32_t n_merged;                      // K12: merged tracks (chains) of the batch
+  uint32_t n_merged_hits;
+  uint32_t n_merge_bins;                  // K12: tracks placed in the search bins
+  uint32_t frame_merged0[kMaxFrames + 1]; // first merged track of each frame
+  uint32_t frame_mhit0[kMaxFrames + 1];   // first merged hit of each frame
 };
 
 // Workspace pointers (device arrays), sized by capacities.
@@ -161,6 +174,32 @@ struct Work {
   int32_t* tr_npred;     // [tcap] output hits stored as residuals (K10)
   uint8_t* keep;         // [ncap] strategy-B protection per batch input index (K10)
   uint32_t* tr_hits;     // [ncap] output hits (frame-local input indices)
+  // K12 merging and refit (null when off)
+  float* m_state;        // [tcap][20] outer state: P[5], C[15] at the last hit's row
+  uint32_t* m_info;      // [tcap] last_row | ref_row << 8 | outer state ok << 16 | frame << 17
+  uint32_t* m_bin;       // [mbcap + 1] tracks per (frame, sector, w bin) -> scanned -> bin ends
+  uint32_t* m_list;      // [tcap] tracks in bin order
+  unsigned long long* m_bestA;  // [tcap] best inner partner of each track: chi2 bits << 32 | index
+  int32_t* m_bestB;      // [tcap] best outer partner, -1 if none
+  float* m_chi;          // [tcap] its chi2
+  int32_t* m_next;       // [tcap] linked outer partner, -1 if none
+  uint32_t* m_prev;      // [tcap] 1 if linked from an inner partner
+  uint32_t* m_hidx;      // [tcap + 1] chain head flags -> scanned -> merged index
+  uint32_t* m_hoff;      // [tcap + 1] chain hit counts -> scanned -> first merged hit
+  float* mt_param;       // [tcap][5] refit state at x_ref
+  float* mt_cov;         // [tcap][15]
+  float* mt_chi2;        // [tcap]
+  float* mt_xref;        // [tcap]
+  int32_t* mt_sector;    // [tcap] frame of the refit result
+  int32_t* mt_ndf;       // [tcap]
+  int32_t* mt_nfit;      // [tcap]
+  int32_t* mt_nseg;      // [tcap]
+  int32_t* mt_head;      // [tcap] frame-local sector-track index of the innermost segment
+  long long* mt_hoff;    // [tcap] first merged hit
+  uint32_t* mt_hits;     // [ncap] frame-local input indices, inner segment first
+  int32_t* tr_next;      // [tcap] frame-local outer partner of each sector track, -1 if none
+  float* tr_mchi2;       // [tcap] chi2 of that merge, NaN if none
+  long long mbcap;       // search bins (frames x sectors x kMergeBins)
   // scan scratch
   uint32_t* scan_tmp;    // [scan_tmp_cap]
   long long ncap, scap, bcap, tcap, scan_tmp_cap, k2cap;

@@ -157,16 +157,23 @@ def test_batch_alone_vs_in_the_mix(tracker):
         tracker.release(h)
 
 
-def test_serving_results_equal_plain(tracker, torch_cuda):
-    """Continuous batching: each frame's tracks are identical alone and in the mix."""
+@pytest.mark.parametrize("borrow", [False, True], ids=["copied", "borrowed"])
+def test_serving_results_equal_plain(tracker, torch_cuda, borrow):
+    """Continuous batching: each frame's tracks are identical alone and in the mix, with the input
+    copied at submit or borrowed (page-locked host arrays uploaded at admission)."""
     import paper_2009_07515_gb300 as tpc
+    torch = torch_cuda
     frames = [synth.generate("serve", n_collisions=int(c), frame_id=i) for i, c in enumerate([3, 1, 7, 2, 5, 1, 4, 6])]
     plain = [tracker.run(f.sector, f.row, f.y, f.w) for f in frames]
+    if borrow:
+        for f in frames:
+            for k in ("sector", "row", "y", "w"):
+                setattr(f, k, torch.from_numpy(np.ascontiguousarray(getattr(f, k))).pin_memory().numpy())
     srv = tpc.Tracker(hbm_budget=3 << 30, max_batch_frames=3)
     tickets = []
     done = []
     for f in frames:  # arrivals interleaved with polls: later frames join while earlier ones run
-        tickets.append(srv.submit(f.sector, f.row, f.y, f.w))
+        tickets.append(srv.submit(f.sector, f.row, f.y, f.w, borrow=borrow))
         done += srv.poll(64, 0)
     for _ in range(10000):
         done += srv.poll(64, 100000)
