@@ -12,6 +12,8 @@
 //   k_seg_layout  bins per segment (occupancy target), bin origins and densities in w and y
 //   k_bin_rank    bin histogram; each cluster keeps its arrival rank inside its bin
 //   k_scatter     sorted (y, w) and input index at bin_start[bin] + rank
+//   (the main path does these two steps per segment: k_seg_bucket, k_bin_rank_seg, k_scatter_seg;
+//   the allocation-free entry keeps the one-pass form)
 //   scans         exclusive prefix sums with device-side lengths
 #include "tpc_dev.cuh"
 
@@ -389,6 +391,82 @@ __global__ void __launch_bounds__(256) k_scatter(Work W) {
       W.hyw[p] = make_float2(h.y, h.w);
     }
     W.horig[p] = (uint32_t)j;
+  }
+}
+
+// ---- Two-pass placement into grid order (the main path). Pass A appends each cluster, as a
+// 16-byte record (y, w, batch index, segment), to its segment's contiguous range: the ranges are
+// the exclusive scan of the per-segment counts, and each segment's cursor grows by warp-aggregated
+// atomics, so the writes of all warps form one append stream per segment whose open 32-byte
+// sectors stay in L2. Pass B takes one segment per block: its records are read in order, ranked in
+// their bins (atomics on the segment's own bin counters), and after the bin scan written to their
+// sorted positions, which are the same range [seg_start, seg_start + n) of the segment; the random
+// accesses of a block stay inside one segment's few hundred kilobytes.
+__global__ void __launch_bounds__(256) k_seg_bucket(Work W) {
+  const BatchDesc* B = W.batch;
+  const long long ntot = B->ntot;
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane takes part in the aggregation
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < ntot; base += stride) {
+    const long long i = base + lane;
+    InHit h{0, 0.f, 0.f, false};
+    if (i < ntot) {
+      int fi;
+      long long j;
+      h = read_input(B, W.packed, i, fi, j);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, h.ok ? h.g : -1 - lane);
+    const int leader = __ffs(peers) - 1;
+    uint32_t off = 0;
+    if (h.ok && lane == leader) off = atomicAdd(&W.seg_cur[h.g], (uint32_t)__popc(peers));
+    off = __shfl_sync(0xffffffffu, off, leader);
+    if (h.ok) {
+      const uint32_t p = W.seg_start[h.g] + off + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+      W.rec[p] = make_uint4(__float_as_uint(h.y), __float_as_uint(h.w), (uint32_t)i, (uint32_t)h.g);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
+  if (W.cnt->n_bins > (uint32_t)W.bcap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&W.cnt->err, kErrBins);
+    return;
+  }
+  const int nseg = (int)W.cnt->nseg;
+  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const uint32_t p1 = W.seg_start[g + 1];
+    for (uint32_t p = W.seg_start[g] + threadIdx.x; p < p1; p += blockDim.x) {
+      const uint4 r = W.rec[p];
+      int iw;
+      W.rank[p] = atomicAdd(&W.bin_start[seg_bin(W, g, __uint_as_float(r.x), __uint_as_float(r.y), iw)], 1u);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scatter_seg(Work W) {
+  if (W.cnt->n_bins > (uint32_t)W.bcap) return;
+  const BatchDesc* B = W.batch;
+  const int nseg = (int)W.cnt->nseg;
+  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const uint32_t p1 = W.seg_start[g + 1];
+    const long long foff = B->f[g / kSegPerFrame].off;
+    for (uint32_t p = W.seg_start[g] + threadIdx.x; p < p1; p += blockDim.x) {
+      const uint4 r = W.rec[p];
+      const float y = __uint_as_float(r.x), w = __uint_as_float(r.y);
+      int iw;
+      const uint32_t q = W.bin_start[seg_bin(W, g, y, w, iw)] + W.rank[p];
+      if (W.packed) {
+        const int4 dim = W.seg_dim[g];
+        const uint32_t qy = (uint32_t)rintf((y + 64.0f) * 512.0f);
+        const int qw = (int)rintf(w * 512.0f) - col_base(dim.z, dim.w, iw);
+        W.hq[q] = qy | ((uint32_t)qw << 16);
+        W.hcol[q] = (uint16_t)iw;
+      } else {
+        W.hyw[q] = make_float2(y, w);
+      }
+      W.horig[q] = (uint32_t)((long long)r.z - foff);
+    }
   }
 }
 

@@ -38,6 +38,9 @@ __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
 __global__ void k_bin_rank(Work);
 __global__ void k_scatter(Work);
+__global__ void k_seg_bucket(Work);
+__global__ void k_bin_rank_seg(Work);
+__global__ void k_scatter_seg(Work);
 __global__ void k_chunk_count(Work);
 __global__ void k_chunk_fill(Work);
 __global__ void k_clean(Work, DevParams);
@@ -410,6 +413,9 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.seg_geo, 16 * (size_t)ws->scap},
       {(void**)&W.bin_start, 4 * (size_t)(ws->bcap + 1)},
       {(void**)&W.rank, 4 * (size_t)ws->ncap},
+      {(void**)&W.seg_start, 4 * (size_t)(ws->scap + 1)},
+      {(void**)&W.seg_cur, 4 * (size_t)ws->scap},
+      {(void**)&W.rec, 16 * (size_t)ws->ncap},
       {(void**)&W.hyw, ctx->p.packed ? 0 : 8 * (size_t)(ws->ncap + 2)},
       {(void**)&W.hq, ctx->p.packed ? 4 * (size_t)(ws->ncap + 4) : 0},
       {(void**)&W.hcol, ctx->p.packed ? 2 * (size_t)ws->ncap : 0},
@@ -605,15 +611,22 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // seg_layout
   ++nl; k_seg_layout<<<G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_seg
-  scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
+  if (W.scap <= kSmallScanCap) {
+    scan2(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins, W.seg_cnt, W.seg_start, &C->nseg, W.scap, &C->n_sorted);
+  } else {
+    scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
+    scan(W.seg_cnt, W.seg_start, &C->nseg, W.scap, &C->n_sorted);
+  }
   mark(ki++);  // zero_bins
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
-  mark(ki++);  // bin_rank
-  ++nl; k_bin_rank<<<8 * G, 256, 0, s>>>(W);
+  ++nl; k_zero_u32<<<G, 256, 0, s>>>(W.seg_cur, &C->nseg, W.scap, 0, 1);
+  mark(ki++);  // bin_rank: clusters appended to their segments, then ranked in their bins per segment
+  ++nl; k_seg_bucket<<<8 * G, 256, 0, s>>>(W);
+  ++nl; k_bin_rank_seg<<<G, 1024, 0, s>>>(W);
   mark(ki++);  // scan_bins
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
-  mark(ki++);  // scatter
-  ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W);
+  mark(ki++);  // scatter: per segment, into the segment's range of sorted positions
+  ++nl; k_scatter_seg<<<G, 1024, 0, s>>>(W);
   mark(ki++);  // neighbours
   ++nl; k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);

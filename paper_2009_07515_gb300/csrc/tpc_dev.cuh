@@ -137,7 +137,10 @@ struct Work {
   int4* seg_dim;         // [scap] (nw, ny, iw0, k + 9)
   float4* seg_geo;       // [scap] (w_lo, w-bins per cm, y_lo, y-bins per cm)
   uint32_t* bin_start;   // [bcap + 1]
-  uint32_t* rank;        // [ncap]
+  uint32_t* rank;        // [ncap] rank of each record in its bin (two-pass placement)
+  uint32_t* seg_start;   // [scap + 1] exclusive scan of seg_cnt: first record of each segment
+  uint32_t* seg_cur;     // [scap] append cursor of each segment
+  uint4* rec;            // [ncap] (y, w, batch index, segment) in segment order
   float2* hyw;           // [ncap + 2] FP32 storage
   uint32_t* hq;          // [ncap + 4] 16-bit storage
   uint16_t* hcol;        // [ncap]     16-bit storage: grid column of each position
