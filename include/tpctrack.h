@@ -385,14 +385,20 @@ void tpc_cf_default_params(tpc_cf_params* p);
 
 /* Find the clusters of one frame's digits (the kernels run on cuda_stream, NULL = the context's
  * stream; the call waits, bounded, for them). to_host = 1 returns page-locked host copies, 0 the
- * device arrays. The context keeps a charge map of 36 * 152 * (n_time + 4) * stride 16-bit cells
- * (stride = n_pads of the widest row + 4, rounded up to 16) in device memory between calls;
- * TPC_E_BUDGET if it would exceed half of the context's hbm_budget. Returns TPC_OK, TPC_E_INVAL
- * (bad parameters or digits, nothing written), TPC_E_BUDGET, TPC_E_NOMEM, TPC_E_TIMEOUT or TPC_E_CUDA. */
+ * device arrays. The context keeps a charge map of 36 * 152 * (lines) * stride 16-bit cells
+ * (stride = n_pads of the widest row + 4, rounded up to 16) in device memory between calls, within
+ * half of the context's hbm_budget: lines = n_time + 4 when the whole frame fits, else the frame is
+ * processed in time windows of as many bins as fit (lines = window + 4, two passes over the windows,
+ * each window's map also holding the 2 time bins beyond each of its edges); the clusters are the
+ * same, in the same order. TPC_E_BUDGET if not even a window of 16 time bins fits. Returns TPC_OK,
+ * TPC_E_INVAL (bad parameters or digits, nothing written), TPC_E_BUDGET, TPC_E_NOMEM, TPC_E_TIMEOUT
+ * or TPC_E_CUDA. */
 int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digits* digits, int32_t to_host,
                       tpc_cluster_list* out, void* cuda_stream);
 
-/* Per-kernel device time of the last tpc_find_clusters() call (with tpc_set_timing(ctx, 1)). */
+/* Per-kernel device time of the last tpc_find_clusters() call (with tpc_set_timing(ctx, 1)); in
+ * time windows cf_fill holds the first pass (fill, peak flags, clear) and cf_copy the second (fill,
+ * clusters written to their slots, clear). */
 int tpc_get_cf_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 
 /* Diagnostic of the kernels' bounded waits (no counterpart in the paper). Every device-side wait of

@@ -5,9 +5,10 @@
 namespace tpc {
 
 // Arguments of the cluster-finder kernels (k_cf.cu). The charge map holds one plane per
-// (sector, row): lines = n_time + 4 time lines of `stride` u16 cells, cell (k, j) at
-// (j + 2) * stride + (k + 2); the two guard lines and guard pads on each side are never written,
-// so every 5x5 window read stays inside the plane and sees 0 outside the row.
+// (sector, row): lines = (t_hi - t_lo) + 4 time lines of `stride` u16 cells, cell (k, j) at
+// (j - t_lo + 2) * stride + (k + 2); the two guard lines and guard pads on each side hold no digit
+// of the window's peaks, so every 5x5 window read stays inside the plane and sees 0 outside the
+// row. A frame whose map does not fit the budget is processed in time windows.
 constexpr int kCfTile = 256;          // digits per block iteration (8 warps)
 constexpr int kCfGuard = 2;
 constexpr uint32_t kCfErrDigit = 1u;  // a digit outside the pad row / frame, or with zero charge
@@ -20,6 +21,11 @@ struct CfArgs {
   const uint16_t* adc;
   long long n;
   int n_time, lines, stride;
+  // time window of this pass (the whole frame when the map holds it): peaks of digits with time in
+  // [t_lo, t_hi) are evaluated; digits with time in [t_lo - 2, t_hi + 2) are filled and cleared;
+  // map line = time - t_lo + 2
+  int t_lo, t_hi;
+  uint32_t* wflag;    // [ceil(n / 32)] windowed mode: bit l set when digit 32 g + l is a kept peak
   int q_peak_min, q_total_min;
   float pitch, dw;
   uint16_t* map;

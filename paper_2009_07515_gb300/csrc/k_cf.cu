@@ -37,9 +37,12 @@ __device__ __forceinline__ bool cf_digit(const CfArgs& A, long long i, int& s, i
 }
 
 __device__ __forceinline__ size_t cf_cell(const CfArgs& A, int s, int r, int k, int j) {
-  return ((size_t)(s * kNRow + r) * (size_t)A.lines + (size_t)(j + kCfGuard)) * (size_t)A.stride +
+  return ((size_t)(s * kNRow + r) * (size_t)A.lines + (size_t)(j - A.t_lo + kCfGuard)) * (size_t)A.stride +
          (size_t)(k + kCfGuard);
 }
+// the digit's cell is in this pass's map: its window or the two halo lines on each side
+__device__ __forceinline__ bool cf_in_map(const CfArgs& A, int j) { return j >= A.t_lo - kCfGuard && j < A.t_hi + kCfGuard; }
+__device__ __forceinline__ bool cf_in_window(const CfArgs& A, int j) { return j >= A.t_lo && j < A.t_hi; }
 
 // the 3x3 window around a cell, w[dj + 1][dk + 1]
 __device__ __forceinline__ void cf_window3(const uint16_t* m, int stride, int w[3][3]) {
@@ -103,6 +106,7 @@ __global__ void __launch_bounds__(kCfTile, 8) k_cf_fill(CfArgs A) {
       bad |= kCfErrDigit;
       continue;
     }
+    if (!cf_in_map(A, j)) continue;
     const size_t c = cf_cell(A, s, r, k, j);
     const uint32_t sh = (uint32_t)(c & 1) * 16u;
     const uint32_t old = atomicAdd(reinterpret_cast<uint32_t*>(A.map) + (c >> 1), (uint32_t)q << sh);
@@ -216,10 +220,72 @@ __global__ void __launch_bounds__(kCfTile) k_cf_clear(CfArgs A) {
   const long long step = (long long)gridDim.x * kCfTile;
   for (long long i = (long long)blockIdx.x * kCfTile + threadIdx.x; i < A.n; i += 2 * step) {
     int s0, r0, k0, j0, q0, s1 = 0, r1 = 0, k1 = 0, j1 = 0, q1 = 0;
-    const bool v0 = cf_digit(A, i, s0, r0, k0, j0, q0);
-    const bool v1 = i + step < A.n && cf_digit(A, i + step, s1, r1, k1, j1, q1);
+    const bool v0 = cf_digit(A, i, s0, r0, k0, j0, q0) && cf_in_map(A, j0);
+    const bool v1 = i + step < A.n && cf_digit(A, i + step, s1, r1, k1, j1, q1) && cf_in_map(A, j1);
     if (v0) A.map[cf_cell(A, s0, r0, k0, j0)] = 0;
     if (v1) A.map[cf_cell(A, s1, r1, k1, j1)] = 0;
+  }
+}
+
+// ---- time windows (a frame whose map exceeds the budget). Pass 1, per window: fill, flag, clear;
+// the flags of each 32 digits accumulate over the windows (each digit lies in one window), and so do
+// their counts. After the scan of the counts, pass 2, per window: fill, emit, clear; each kept peak
+// computes its cluster again and writes it to its output slot (the group's first slot plus its
+// rank among the group's flagged digits), so the output is in the input order of the peaks, as in
+// one pass over the whole frame.
+__global__ void __launch_bounds__(kCfTile) k_cf_flag(CfArgs A) {
+  const int lane = threadIdx.x & 31;
+  uint32_t bad = 0;
+  for (long long base = (long long)blockIdx.x * kCfTile; base < A.n; base += (long long)gridDim.x * kCfTile) {
+    const long long i = base + threadIdx.x;
+    bool keep = false;
+    int s = 0, r = 0, k = 0, j = 0, q = 0;
+    if (i < A.n && cf_digit(A, i, s, r, k, j, q) && cf_in_window(A, j)) {
+      const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
+      int w[3][3];
+      cf_window3(m, A.stride, w);
+      if (w[1][1] != q) bad |= kCfErrTwice;
+      if (q >= A.q_peak_min && cf_is_peak3(w)) keep = cf_sums3(m, A.stride, w).Q >= A.q_total_min;
+    }
+    const uint32_t b = __ballot_sync(0xffffffffu, keep);
+    const long long wbase = i - lane;
+    if (lane == 0 && wbase < A.n && b) {
+      A.wflag[wbase >> 5] |= b;
+      A.wcount[wbase >> 5] += (uint32_t)__popc(b);
+    }
+  }
+  if (bad) atomicOr(A.err, bad);
+}
+
+__global__ void __launch_bounds__(kCfTile) k_cf_emit(CfArgs A) {
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * kCfTile; base < A.n; base += (long long)gridDim.x * kCfTile) {
+    const long long i = base + threadIdx.x;
+    const long long wbase = i - lane;
+    if (wbase >= A.n) continue;  // warp-uniform
+    const uint32_t fl = A.wflag[wbase >> 5];
+    int s = 0, r = 0, k = 0, j = 0, q = 0;
+    if (!((fl >> lane) & 1u) || !cf_digit(A, i, s, r, k, j, q) || !cf_in_window(A, j)) continue;
+    const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
+    int w[3][3];
+    cf_window3(m, A.stride, w);
+    const CfSums S = cf_sums3(m, A.stride, w);
+    const uint32_t o = A.woff[wbase >> 5] + (uint32_t)__popc(fl & ((1u << lane) - 1u));
+    const float Qf = (float)S.Q;
+    const float mk = __fdiv_rn((float)S.Sk, Qf), mj = __fdiv_rn((float)S.Sj, Qf);
+    const float pc = __fadd_rn((float)k, mk), tc = __fadd_rn((float)j, mj);
+    const float centre = __fsub_rn((float)((int)__ldg(A.npads + r) / 2), 0.5f);
+    const float vk = __fsub_rn(__fdiv_rn((float)S.Skk, Qf), __fmul_rn(mk, mk));
+    const float vj = __fsub_rn(__fdiv_rn((float)S.Sjj, Qf), __fmul_rn(mj, mj));
+    A.o_sector[o] = (uint8_t)s;
+    A.o_row[o] = (uint8_t)r;
+    A.o_y[o] = __fmul_rn(__fsub_rn(pc, centre), A.pitch);
+    A.o_w[o] = __fmul_rn(__fadd_rn(tc, 0.5f), A.dw);
+    A.o_qtot[o] = (uint32_t)S.Q;
+    A.o_qmax[o] = (uint16_t)q;
+    A.o_sig_pad[o] = vk > 0.f ? __fsqrt_rn(vk) : 0.f;
+    A.o_sig_time[o] = vj > 0.f ? __fsqrt_rn(vj) : 0.f;
+    A.o_digit[o] = (uint32_t)i;
   }
 }
 

@@ -12,8 +12,8 @@
 //   k_seg_layout  bins per segment (occupancy target), bin origins and densities in w and y
 //   k_bin_rank    bin histogram; each cluster keeps its arrival rank inside its bin
 //   k_scatter     sorted (y, w) and input index at bin_start[bin] + rank
-//   (the main path does these two steps per segment: k_seg_bucket, k_bin_rank_seg, k_scatter_seg;
-//   the allocation-free entry keeps the one-pass form)
+//   (batches of more than kTwoPassMin clusters do these two steps per segment instead:
+//   k_seg_bucket, k_bin_rank_seg, k_scatter_seg; the allocation-free entry keeps the one-pass form)
 //   scans         exclusive prefix sums with device-side lengths
 #include "tpc_dev.cuh"
 
@@ -354,9 +354,11 @@ __device__ __forceinline__ uint32_t seg_bin(const Work& W, int g, float y, float
   return W.seg_bb[g] + (uint32_t)(iw * dim.y + iy);
 }
 
-__global__ void __launch_bounds__(256) k_bin_rank(Work W) {
+// one_pass_only: skip batches that the two-pass kernels place (the main path launches both forms)
+__global__ void __launch_bounds__(256) k_bin_rank(Work W, int one_pass_only) {
   const BatchDesc* B = W.batch;
   const long long ntot = B->ntot;
+  if (one_pass_only && ntot > kTwoPassMin) return;
   const uint32_t bcap = (uint32_t)W.bcap;
   if (W.cnt->n_bins > bcap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&W.cnt->err, kErrBins);
@@ -371,9 +373,10 @@ __global__ void __launch_bounds__(256) k_bin_rank(Work W) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_scatter(Work W) {
+__global__ void __launch_bounds__(256) k_scatter(Work W, int one_pass_only) {
   const BatchDesc* B = W.batch;
   const long long ntot = B->ntot;
+  if (one_pass_only && ntot > kTwoPassMin) return;
   if (W.cnt->n_bins > (uint32_t)W.bcap) return;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < ntot; i += (long long)gridDim.x * blockDim.x) {
     int fi, iw;
@@ -405,6 +408,7 @@ __global__ void __launch_bounds__(256) k_scatter(Work W) {
 __global__ void __launch_bounds__(256) k_seg_bucket(Work W) {
   const BatchDesc* B = W.batch;
   const long long ntot = B->ntot;
+  if (ntot <= kTwoPassMin) return;
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
   // warp-uniform trip count: every lane takes part in the aggregation
@@ -429,6 +433,7 @@ __global__ void __launch_bounds__(256) k_seg_bucket(Work W) {
 }
 
 __global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
+  if (W.batch->ntot <= kTwoPassMin) return;
   if (W.cnt->n_bins > (uint32_t)W.bcap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&W.cnt->err, kErrBins);
     return;
@@ -445,7 +450,7 @@ __global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
 }
 
 __global__ void __launch_bounds__(1024) k_scatter_seg(Work W) {
-  if (W.cnt->n_bins > (uint32_t)W.bcap) return;
+  if (W.batch->ntot <= kTwoPassMin || W.cnt->n_bins > (uint32_t)W.bcap) return;
   const BatchDesc* B = W.batch;
   const int nseg = (int)W.cnt->nseg;
   for (int g = blockIdx.x; g < nseg; g += gridDim.x) {

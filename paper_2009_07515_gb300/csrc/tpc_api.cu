@@ -36,8 +36,8 @@ struct SmallScan {
 __global__ void k_scan_small(SmallScan);
 __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
-__global__ void k_bin_rank(Work);
-__global__ void k_scatter(Work);
+__global__ void k_bin_rank(Work, int);
+__global__ void k_scatter(Work, int);
 __global__ void k_seg_bucket(Work);
 __global__ void k_bin_rank_seg(Work);
 __global__ void k_scatter_seg(Work);
@@ -77,6 +77,8 @@ __global__ void k_cf_fill(CfArgs);
 __global__ void k_cf_peaks(CfArgs);
 __global__ void k_cf_copy(CfArgs);
 __global__ void k_cf_clear(CfArgs);
+__global__ void k_cf_flag(CfArgs);
+__global__ void k_cf_emit(CfArgs);
 
 // Cluster finding: device buffers sized by a digit capacity, the charge map (kept zero between
 // calls), page-locked host copies of the last call's clusters, timing events.
@@ -87,6 +89,8 @@ struct CfState {
   uint8_t *in_sector = nullptr, *in_row = nullptr;
   uint16_t *in_pad = nullptr, *in_time = nullptr, *in_adc = nullptr;
   uint32_t *wcount = nullptr, *woff = nullptr, *wsrc = nullptr, *scan_tmp = nullptr, *small = nullptr;
+  uint32_t* wflag = nullptr;
+  int windows = 1;                  // time windows of the last call (1: the whole frame in one map)
   uint8_t *t_sector = nullptr, *t_row = nullptr;
   float *t_y = nullptr, *t_w = nullptr, *t_sp = nullptr, *t_st = nullptr;
   uint32_t *t_qtot = nullptr, *t_digit = nullptr;
@@ -620,12 +624,16 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // zero_bins
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
   ++nl; k_zero_u32<<<G, 256, 0, s>>>(W.seg_cur, &C->nseg, W.scap, 0, 1);
-  mark(ki++);  // bin_rank: clusters appended to their segments, then ranked in their bins per segment
+  mark(ki++);  // bin_rank: one pass for small batches; for large ones the clusters are appended to
+  // their segments, then ranked in their bins per segment (each kernel returns at once on the
+  // other side of kTwoPassMin, so one captured graph serves every batch size)
+  ++nl; k_bin_rank<<<8 * G, 256, 0, s>>>(W, 1);
   ++nl; k_seg_bucket<<<8 * G, 256, 0, s>>>(W);
   ++nl; k_bin_rank_seg<<<G, 1024, 0, s>>>(W);
   mark(ki++);  // scan_bins
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
-  mark(ki++);  // scatter: per segment, into the segment's range of sorted positions
+  mark(ki++);  // scatter: one pass, or per segment into the segment's range of sorted positions
+  ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W, 1);
   ++nl; k_scatter_seg<<<G, 1024, 0, s>>>(W);
   mark(ki++);  // neighbours
   ++nl; k_chunk_count<<<G, 256, 0, s>>>(W);
@@ -1074,7 +1082,7 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
     return o;
   };
   const size_t o_is = take(cap), o_ir = take(cap), o_ip = take(2 * cap), o_it = take(2 * cap), o_ia = take(2 * cap);
-  const size_t o_wc = take(4 * nw), o_wo = take(4 * (nw + 1)), o_ws = take(4 * nw);
+  const size_t o_wc = take(4 * nw), o_wo = take(4 * (nw + 1)), o_ws = take(4 * nw), o_wf = take(4 * nw);
   const size_t o_tmp = take(4 * (nw / 2048 + 2)), o_small = take(16), o_np = take(2 * kNRow);
   const size_t t_s = take(cap32), t_r = take(cap32), t_y = take(4 * cap32), t_w = take(4 * cap32);
   const size_t t_sp = take(4 * cap32), t_st = take(4 * cap32), t_q = take(4 * cap32), t_d = take(4 * cap32);
@@ -1100,6 +1108,7 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
   cf.wcount = (uint32_t*)(b + o_wc);
   cf.woff = (uint32_t*)(b + o_wo);
   cf.wsrc = (uint32_t*)(b + o_ws);
+  cf.wflag = (uint32_t*)(b + o_wf);
   cf.t_sector = (uint8_t*)(b + t_s);
   cf.t_row = (uint8_t*)(b + t_r);
   cf.t_y = (float*)(b + t_y);
@@ -1918,7 +1927,21 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
     npmax = std::max(npmax, v);
   }
   const int stride = (int)align_up((size_t)npmax + 2 * kCfGuard, 16);
-  const int lines = d->n_time + 2 * kCfGuard;
+  // the charge map holds the whole frame when it fits half of the budget, else a time window of as
+  // many bins as fit (the frame then runs in two passes over its windows)
+  int lines = d->n_time + 2 * kCfGuard, tw = d->n_time;
+  {
+    const size_t line_bytes = (size_t)kSegPerFrame * (size_t)stride * 2;
+    const size_t half = (size_t)std::max<int64_t>(ctx->p.hbm_budget, 0) / 2;
+    if ((size_t)lines * line_bytes > half) {
+      const long long max_lines = (long long)(half / line_bytes);
+      if (max_lines < 2 * kCfGuard + 16)
+        return fail(ctx, TPC_E_BUDGET, "a charge map of 16 time bins exceeds half of the HBM budget");
+      tw = (int)(max_lines - 2 * kCfGuard);
+      lines = tw + 2 * kCfGuard;
+    }
+  }
+  const bool windowed = tw < d->n_time;
   int rc = cf_reserve(ctx, d->n);
   if (rc) return rc;
   if (!cf.done) {
@@ -1945,6 +1968,9 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
   A.n_time = d->n_time;
   A.lines = lines;
   A.stride = stride;
+  A.t_lo = 0;
+  A.t_hi = d->n_time;
+  A.wflag = cf.wflag;
   A.q_peak_min = P.q_peak_min;
   A.q_total_min = P.q_total_min;
   A.pitch = (float)P.pad_pitch;
@@ -1965,23 +1991,58 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
   const int G = ctx->sms;
   const bool timing = ctx->timing;
   cf.map_clean = false;
-  if (timing) cudaEventRecord(cf.ev[0], s);
-  k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
-  if (timing) cudaEventRecord(cf.ev[1], s);
-  k_cf_peaks<<<grid, kCfTile, 0, s>>>(A);
-  if (timing) cudaEventRecord(cf.ev[2], s);
   const long long nwarps = (n + 31) / 32;
-  k_scan_reduce<<<2 * G, 256, 0, s>>>(cf.wcount, nullptr, nwarps, 0, cf.scan_tmp);
-  k_scan_tiles<<<1, 1024, 0, s>>>(cf.scan_tmp, nullptr, nwarps, 0, cf.small);
-  k_scan_apply<<<2 * G, 256, 0, s>>>(cf.wcount, nullptr, nwarps, 0, cf.scan_tmp, cf.small, cf.woff);
-  if (timing) cudaEventRecord(cf.ev[3], s);
-  k_cf_copy<<<(int)std::min<long long>((nwarps + kCfTile - 1) / kCfTile, (long long)G * (2048 / kCfTile)), kCfTile, 0,
-              s>>>(A);
-  if (timing) cudaEventRecord(cf.ev[4], s);
-  k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
-  if (timing) cudaEventRecord(cf.ev[5], s);
-  const int64_t nl[kCfKernels] = {1, 1, 3, 1, 1};
-  for (int k = 0; k < kCfKernels; ++k) cf.launches[k] = nl[k];
+  auto scan_counts = [&]() {
+    k_scan_reduce<<<2 * G, 256, 0, s>>>(cf.wcount, nullptr, nwarps, 0, cf.scan_tmp);
+    k_scan_tiles<<<1, 1024, 0, s>>>(cf.scan_tmp, nullptr, nwarps, 0, cf.small);
+    k_scan_apply<<<2 * G, 256, 0, s>>>(cf.wcount, nullptr, nwarps, 0, cf.scan_tmp, cf.small, cf.woff);
+  };
+  if (!windowed) {
+    cf.windows = 1;
+    if (timing) cudaEventRecord(cf.ev[0], s);
+    k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
+    if (timing) cudaEventRecord(cf.ev[1], s);
+    k_cf_peaks<<<grid, kCfTile, 0, s>>>(A);
+    if (timing) cudaEventRecord(cf.ev[2], s);
+    scan_counts();
+    if (timing) cudaEventRecord(cf.ev[3], s);
+    k_cf_copy<<<(int)std::min<long long>((nwarps + kCfTile - 1) / kCfTile, (long long)G * (2048 / kCfTile)), kCfTile,
+                0, s>>>(A);
+    if (timing) cudaEventRecord(cf.ev[4], s);
+    k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
+    if (timing) cudaEventRecord(cf.ev[5], s);
+    const int64_t nl[kCfKernels] = {1, 1, 3, 1, 1};
+    for (int k = 0; k < kCfKernels; ++k) cf.launches[k] = nl[k];
+  } else {
+    // pass 1 over the windows: fill, flag the kept peaks, clear; then the scan of their counts;
+    // pass 2: fill, write each kept peak's cluster to its slot, clear (stage times: cf_fill holds
+    // pass 1, cf_copy pass 2)
+    CK(cudaMemsetAsync(cf.wcount, 0, 4 * (size_t)nwarps, s));
+    CK(cudaMemsetAsync(cf.wflag, 0, 4 * (size_t)nwarps, s));
+    int nwin = 0;
+    if (timing) cudaEventRecord(cf.ev[0], s);
+    for (int t0 = 0; t0 < d->n_time; t0 += tw, ++nwin) {
+      A.t_lo = t0;
+      A.t_hi = std::min(t0 + tw, d->n_time);
+      k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
+      k_cf_flag<<<grid, kCfTile, 0, s>>>(A);
+      k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
+    }
+    if (timing) { cudaEventRecord(cf.ev[1], s); cudaEventRecord(cf.ev[2], s); }
+    scan_counts();
+    if (timing) cudaEventRecord(cf.ev[3], s);
+    for (int t0 = 0; t0 < d->n_time; t0 += tw) {
+      A.t_lo = t0;
+      A.t_hi = std::min(t0 + tw, d->n_time);
+      k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
+      k_cf_emit<<<grid, kCfTile, 0, s>>>(A);
+      k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
+    }
+    if (timing) { cudaEventRecord(cf.ev[4], s); cudaEventRecord(cf.ev[5], s); }
+    cf.windows = nwin;
+    const int64_t nl[kCfKernels] = {3 * nwin, 0, 3, 3 * nwin, 0};
+    for (int k = 0; k < kCfKernels; ++k) cf.launches[k] = nl[k];
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(ctx, TPC_E_CUDA, std::string("cluster-finder launch: ") + cudaGetErrorString(e));
   CK(cudaMemcpyAsync(cf.h_small, cf.small, 8, cudaMemcpyDeviceToHost, s));

@@ -41,6 +41,9 @@ constexpr int kMaxFrames = 64;               // frames per batched launch
 constexpr int kHistThreads = 1024;           // threads per block of the segment histogram
 constexpr uint32_t kNoHit = 0xFFFFFFFFu;
 constexpr int kMergeBins = 2048;             // w bins per (frame, sector) of the merge step's search
+// batches of more clusters than this are placed into grid order in two passes per segment (their
+// grid and cluster arrays outgrow the L2); smaller ones in one pass
+constexpr long long kTwoPassMin = 1LL << 23;
 
 // error bits (device error word)
 constexpr uint32_t kErrInput = 1u;      // malformed cluster (sector/row range, non-finite)

@@ -31,8 +31,8 @@ __global__ void k_scan_tiles(uint32_t*, const uint32_t*, long long, int, uint32_
 __global__ void k_scan_apply(const uint32_t*, const uint32_t*, long long, int, const uint32_t*, const uint32_t*, uint32_t*);
 __global__ void k_seg_hist(Work);
 __global__ void k_seg_layout(Work, DevParams);
-__global__ void k_bin_rank(Work);
-__global__ void k_scatter(Work);
+__global__ void k_bin_rank(Work, int);
+__global__ void k_scatter(Work, int);
 __global__ void k_clean(Work, DevParams);
 __global__ void k_reset_counters(Work);
 __global__ void k_zero_u32(uint32_t*, const uint32_t*, long long, int, int);
@@ -210,9 +210,9 @@ extern "C" int tpc_links_static(const tpc_params* params, const tpc_clusters* cl
   k_seg_layout<<<G, 256, 0, s>>>(W, Q);
   scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
   k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
-  k_bin_rank<<<8 * G, 256, 0, s>>>(W);
+  k_bin_rank<<<8 * G, 256, 0, s>>>(W, 0);
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
-  k_scatter<<<8 * G, 256, 0, s>>>(W);
+  k_scatter<<<8 * G, 256, 0, s>>>(W, 0);
   prepare_neighbours();
   k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);

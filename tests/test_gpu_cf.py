@@ -153,18 +153,68 @@ def test_long_frame(tracker):
     assert_same(tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time), oracle_cf(d))
 
 
+LINE_BYTES = 36 * 152 * 224 * 2   # one time line of the charge map (widest row 218 pads + guards)
+
+
 def test_charge_map_beyond_the_budget_is_refused(tpc):
-    """The map of 36 x 152 x (n_time + 4) x stride cells must fit half of the HBM budget."""
+    """Half of the HBM budget must hold the map of a window of at least 16 time bins."""
     f = synth.generate("pp_500", mult_fixed=20, seed=32)
     d = synth.digitize(f)
-    tr = tpc.Tracker(hbm_budget=4 << 30)
+    tr = tpc.Tracker(hbm_budget=2 * 19 * LINE_BYTES)
     try:
         with pytest.raises(tpc.TpcError) as e:
-            tr.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, 60000)
+            tr.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
         assert e.value.code == -3
-        assert_same(tr.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time), oracle_cf(d))
     finally:
         tr.close()
+
+
+def _windowed(tpc, window_bins):
+    """A context whose budget holds the map of a window of window_bins time bins."""
+    return tpc.Tracker(hbm_budget=2 * (window_bins + 4) * LINE_BYTES + LINE_BYTES // 2)
+
+
+def test_long_frame_in_time_windows_equals_one_pass_and_oracle(tpc, tracker):
+    """A frame of 4400 time bins processed in five windows of about 1000 bins (the map of the whole
+    frame exceeds the budget): the same clusters, in the same order, bit for bit, as one pass over
+    the whole frame and as the oracle."""
+    f = synth.generate("serve", n_collisions=3, mult_fixed=200, frame_us=900.0, seed=31)
+    d = synth.digitize(f, shuffle=1, seed=31)
+    assert d.n_time > 4000
+    one = tracker.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
+    tw = _windowed(tpc, 1000)
+    try:
+        win = tw.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
+        assert_same(win, oracle_cf(d))
+        for k in FIELDS:
+            assert np.array_equal(np.asarray(win[k]), np.asarray(one[k])), k
+    finally:
+        tw.close()
+
+
+def test_pbpb_digits_in_small_windows_match_oracle(tpc):
+    """The Pb-Pb-like frame's 2.3e7 digits in windows of 40 time bins (19 windows, halos crossing
+    every window edge)."""
+    f, d = synth.generate_digits("pbpb_2x10000")
+    tw = _windowed(tpc, 40)
+    try:
+        assert_same(tw.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time), oracle_cf(d))
+    finally:
+        tw.close()
+
+
+def test_windowed_mode_refuses_malformed_input_and_stays_exact(tpc):
+    tw = _windowed(tpc, 20)
+    try:
+        ok = _cells([(0, 0, 3, 3, 9), (0, 0, 4, 3, 30), (0, 0, 2, 4, 7), (5, 9, 10, 50, 12), (5, 9, 10, 51, 20)])
+        for bad in ([(0, 0, 2, 3, 40000), (0, 0, 2, 3, 40000)], [(0, 152, 0, 0, 5)], [(0, 0, 3, 80, 5)]):
+            cols = _cells([(0, 0, 6, 3, 20), (4, 4, 4, 40, 30)] + bad)
+            with pytest.raises(tpc.TpcError) as e:
+                tw.find_clusters(*cols, 64)
+            assert e.value.code == -1
+            assert_same(tw.find_clusters(*ok, 64), oracle.find_clusters(*ok, 64, precision="f32"))
+    finally:
+        tw.close()
 
 
 def test_tracks_from_found_clusters_match_tracks_from_generated_clusters(tracker):
