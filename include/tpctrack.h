@@ -92,7 +92,8 @@ typedef struct {
                              whole warp with per-lane candidate lists */
   int32_t k5_block;       /* tracklet construction: threads per block, one tracklet per thread at
                              a time (64, 128 or 256) */
-  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64, 72, 80) */
+  int32_t k5_regs;        /* registers per tracklet thread the kernel is compiled for (64, 72, 80;
+                             see k5_ilp for 2 tracklets per thread) */
   int32_t k5_blocks_per_sm; /* tracklet blocks launched per SM (0 = all that fit); with k5_block
                              it sets how many tracklets each warp builds */
   int32_t k5_order;       /* tracklet processing order: 0 canonical, 1 longest chain first,
@@ -111,6 +112,9 @@ typedef struct {
   double merge_chi2_max;  /* 5-parameter chi2 cut of a merge (50) */
   int32_t refit_passes;   /* Kalman passes of the refit, alternately inward and outward, odd (3) */
   double refit_scale;     /* a refit pass starts from the previous pass's covariance times this (100) */
+  int32_t k5_ilp;         /* launch shape: tracklets each tracklet thread keeps in flight, 1 or 2; with
+                             2 a thread advances both by one row step per iteration, phase by
+                             phase, with k5_block 64 or 128 and k5_regs 128 (1) */
 } tpc_params;
 
 /* Clusters of one time frame, structure of arrays in the caller's order (n entries each).
@@ -300,6 +304,7 @@ typedef struct {
   float total_ms;  /* median device time of the whole sequence */
   int32_t stage;   /* what ms measures: 0 all stages, 1 neighbour search, 2 chains + tracklets,
                       3 votes + kept + write_tracks */
+  int32_t k5_ilp;
 } tpc_tune_entry;
 typedef struct {
   int32_t n_entries;               /* configurations timed, in the order they were timed */
@@ -310,8 +315,8 @@ typedef struct {
  * fastest for the context's later runs. Coordinate descent, each candidate run reps + 1 times (the
  * first discarded, median of the rest) with events between stages on the context's stream:
  * bin_occupancy in {0.35, 0.5, 0.7, 1, 2} on the whole sequence; then k2_warps in {4, 8} x k2_tma in {0, 1, 2}
- * on the neighbour search; then (k5_block, k5_regs), k5_order and k5_blocks_per_sm on chains +
- * tracklets; then sel_lanes in {1, 32} on the selection. Results of the frames are those of any
+ * on the neighbour search; then (k5_block, k5_regs, k5_ilp), k5_order and k5_blocks_per_sm on
+ * chains + tracklets; then sel_lanes in {1, 32} on the selection. Results of the frames are those of any
  * shape. Blocks until done. Errors: TPC_E_INVAL
  * (bad list, reps < 1), TPC_E_STATE (a frame queued for serving), or any error tpc_track_batch
  * returns. */

@@ -94,7 +94,7 @@ class Tracker:
         self._check(self.lib.tpc_track_batch(self.ctx, arr, len(frames), s))
 
     TUNE_KEYS = ("bin_occupancy", "k2_warps", "k2_tma", "k5_block", "k5_regs", "k5_blocks_per_sm", "k5_order",
-                 "sel_lanes", "ms", "total_ms", "stage")
+                 "k5_ilp", "sel_lanes", "ms", "total_ms", "stage")
 
     def autotune(self, frames, reps: int = 3) -> dict:
         """Time launch shapes on a batch (tpc_autotune) and keep the fastest. Returns the timed

@@ -72,6 +72,7 @@ class tpc_params(ctypes.Structure):
         ("merge_chi2_max", ctypes.c_double),
         ("refit_passes", ctypes.c_int32),
         ("refit_scale", ctypes.c_double),
+        ("k5_ilp", ctypes.c_int32),
     ]
 
 
@@ -141,6 +142,7 @@ class tpc_tune_entry(ctypes.Structure):
         ("ms", ctypes.c_float),
         ("total_ms", ctypes.c_float),
         ("stage", ctypes.c_int32),
+        ("k5_ilp", ctypes.c_int32),
     ]
 
 

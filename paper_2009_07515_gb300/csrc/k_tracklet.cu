@@ -5,7 +5,7 @@
 // without pointer chasing (the outward chain steps read slab rows at known addresses, like the
 // inward refit).
 //
-// k_tracklets: one lane builds one tracklet at a time; a lane that finishes takes the next start
+// k_tracklets: one lane builds one tracklet at a time (or two, interleaved); a lane that finishes one takes the next start
 // hit from a device work counter (persistent kernel, grid = SMs x resident blocks). The loop body
 // has one propagation and one update shared by both directions, so lanes of a warp that are in
 // different phases still execute the same Kalman instructions together. Steps of one tracklet:
@@ -325,42 +325,279 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
   }
 }
 
-// host-side launchers (the kernel templates stay in this translation unit). Shapes: threads per
-// block 64, 128 or 256, each compiled for 64, 72 or 80 registers per thread.
-template <int kT, int kR>
-static void launch_shape(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
-  if (packed) k_tracklets<kT, kR, true><<<grid, kT, 0, s>>>(W, Q, ordered);
-  else k_tracklets<kT, kR, false><<<grid, kT, 0, s>>>(W, Q, ordered);
+// One tracklet in flight in a lane: its state between row steps.
+struct Tl {
+  float P[5], C[15];
+  float chi2sum;
+  int t, r, r0, top, ref, nmiss, nh, mlen, gb;
+  uint32_t steps;
+  bool inward, active, done;
+};
+// The loads of one row step whose addresses are known before the propagation: a known candidate
+// (chain hit outward, outward result inward), or the grid geometry of the row to search.
+struct TlLoads {
+  bool known;
+  int khit;
+  float2 kc;
+  int4 sdim;
+  float4 sgeo;
+  uint32_t sbb;
+};
+
+// Takes start hits from the work counter until one seeds (T.active) or the counter is exhausted
+// (T.done).
+template <bool kPacked>
+__device__ __forceinline__ void tl_take(const Work& W, const DevParams& Q, Tl& T, uint32_t ntl, int ordered) {
+  while (!T.active) {
+    const uint32_t tn = atomicAdd(&W.cnt->k5_next, 1u);
+    if (tn >= ntl) {
+      T.done = true;
+      return;
+    }
+    const int t = ordered ? (int)W.order[tn] : (int)tn;
+    const uint4 st = W.starts[t];
+    const int4 ch = W.chains[t];
+    const int g = (int)st.y;
+    const int r0 = (g % kSegPerFrame) % kNRow;
+    const int gb = g - r0;
+    T.t = t;
+    T.r0 = r0;
+    T.gb = gb;
+    // seed from the precomputed chain
+    const float2 a = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, (int)st.x);
+    const float2 b = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r0 + ch.z / 2, ch.x);
+    const float2 c = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, gb + r0 + ch.z - 1, ch.y);
+    float hh[3][3];
+    hh[0][0] = Q.x[r0];                hh[0][1] = a.x; hh[0][2] = a.y;
+    hh[1][0] = Q.x[r0 + ch.z / 2];     hh[1][1] = b.x; hh[1][2] = b.y;
+    hh[2][0] = Q.x[r0 + ch.z - 1];     hh[2][1] = c.x; hh[2][2] = c.y;
+    if (!kf_seed(Q, hh, T.P)) {
+      W.tl_info[t] = 0u;
+      continue;
+    }
+    reset_cov(Q, T.C);
+    T.r = r0;
+    T.top = -1;
+    T.nmiss = 0;
+    T.mlen = ch.z;
+    T.inward = false;
+    T.active = true;
+  }
 }
-template <int kT, int kR>
+
+template <bool kPacked>
+__device__ __forceinline__ TlLoads tl_loads(const Work& W, const Tl& T) {
+  TlLoads L;
+  L.known = T.inward ? T.r >= T.r0 : T.r < T.r0 + T.mlen;
+  L.khit = -1;
+  L.kc = make_float2(0.f, 0.f);
+  L.sdim = make_int4(0, 0, 0, 0);
+  L.sgeo = make_float4(0.f, 0.f, 0.f, 0.f);
+  L.sbb = 0;
+  if (L.known) {
+    const uint32_t s = W.slab[slab_at((uint32_t)T.t, T.r)];
+    if (s != kNoHit) {
+      L.khit = (int)s;
+      L.kc = hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, T.gb + T.r, L.khit);
+    }
+  } else {
+    L.sdim = W.seg_dim[T.gb + T.r];
+    L.sgeo = W.seg_geo[T.gb + T.r];
+    L.sbb = W.seg_bb[T.gb + T.r];
+  }
+  return L;
+}
+
+// The propagation to the step's row (none on the first row of a direction); true: stop.
+__device__ __forceinline__ bool tl_propagate(const DevParams& Q, Tl& T) {
+  const bool prop = T.inward ? (T.r < T.top) : (T.r > T.r0);
+  if (!prop) return false;
+  const float xf = row_x(Q, T.inward ? T.r + 1 : T.r - 1);
+  if (!kf_propagate(Q, T.P, T.C, xf, row_x(Q, T.r))) return true;
+  return fabsf(T.P[0]) > row_x(Q, T.r) * Q.tan10 + Q.y_margin;
+}
+
+// The measurement of the step's row: the known hit or the window search, the update, the slab
+// entry; sv = the lane's column of the saved state (stride kStride). True: stop.
+template <bool kPacked, int kStride>
+__device__ __forceinline__ bool tl_measure(const Work& W, const DevParams& Q, Tl& T, const TlLoads& L, float* sv) {
+  bool stop = false;
+  int hit = -1;
+  float chi = __int_as_float(0x7f800000);
+  float2 c = make_float2(0.f, 0.f);
+  bool searched = false;
+  const SInv V = kf_sinv(Q, T.C);
+  if (L.known) {
+    hit = L.khit;
+    c = L.kc;
+    if (hit >= 0) chi = kf_chi2(V, T.P, c.x, c.y);
+  } else {
+    searched = true;
+    hit = search_row<kPacked>(W, Q, L.sdim, L.sgeo, L.sbb, T.P, T.C, V, chi, c);
+  }
+  const bool acc = hit >= 0 && chi <= Q.chi2_max;
+  if (acc) {
+    kf_update(Q, V, T.P, T.C, c.x, c.y);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) sv[i * kStride] = T.P[i];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) sv[(5 + i) * kStride] = T.C[i];
+    T.nmiss = 0;
+    if (T.inward) {
+      T.nh += 1;
+      T.chi2sum = T.chi2sum + chi;
+      T.ref = T.r;
+    } else {
+      T.top = T.r;
+      // the extension reached another tracklet's start hit: that tracklet covers the rows beyond
+      if (searched && Q.ext_stop && W.is_start[hit]) stop = true;
+    }
+  } else {
+    T.nmiss += 1;
+    if (searched && T.nmiss >= Q.n_miss_max) stop = true;
+  }
+  W.slab[slab_at((uint32_t)T.t, T.r)] = acc ? (uint32_t)hit : kNoHit;
+  T.r += T.inward ? -1 : 1;
+  if (T.r < 0 || T.r >= kNRow) stop = true;
+  return stop;
+}
+
+// The end of a direction: the outward pass turns inward from the outermost hit with the covariance
+// reset; the inward pass writes the tracklet's fit and frees the lane's slot.
+template <int kStride>
+__device__ __forceinline__ void tl_stop(const Work& W, const DevParams& Q, Tl& T, const float* sv,
+                                        unsigned long long& all_steps, unsigned long long& all_hits) {
+  if (!T.inward) {
+    if (T.top < 0) {
+      W.tl_info[T.t] = 0u;
+      all_steps += T.steps;
+      T.steps = 0;
+      T.active = false;
+      return;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) T.P[i] = sv[i * kStride];
+    reset_cov(Q, T.C);
+    T.inward = true;
+    T.r = T.top;
+    T.nmiss = 0;
+    T.nh = 0;
+    T.ref = -1;
+    T.chi2sum = 0.f;
+    return;
+  }
+  if (T.ref >= 0) {
+    float* o = W.tl_state + (long long)T.t * 24;
+#pragma unroll
+    for (int i = 0; i < 20; ++i) o[i] = sv[i * kStride];
+    o[20] = T.chi2sum;
+    o[21] = Q.x[T.ref];
+    W.tl_info[T.t] = (uint32_t)T.nh | ((uint32_t)T.ref << 8) | ((uint32_t)T.top << 16) | (1u << 24);
+    all_hits += (unsigned long long)T.nh;
+  } else {
+    W.tl_info[T.t] = 0u;
+  }
+  all_steps += T.steps;
+  T.steps = 0;
+  T.active = false;
+}
+
+// The same construction with kIlp tracklets in flight per lane: each loop iteration advances every
+// one of them by one row step, phase by phase (loads, propagations, measurements, ends), so their
+// independent chains of dependent arithmetic and loads can overlap within one thread.
+template <int kThreads, int kRegs, bool kPacked, int kIlp>
+__global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs))
+    k_tracklets_ilp(Work W, DevParams Q, int ordered) {
+  const uint32_t ntl = W.cnt->n_tracklets;
+  // state at the last accepted hit, kept in shared memory (one column per thread) to save registers
+  __shared__ float sv[kIlp][20][kThreads];
+  const int tid = threadIdx.x;
+  Tl T[kIlp];
+#pragma unroll
+  for (int k = 0; k < kIlp; ++k) {
+    T[k].chi2sum = 0.f;
+    T[k].t = -1; T[k].r = 0; T[k].r0 = 0; T[k].top = -1; T[k].ref = -1;
+    T[k].nmiss = 0; T[k].nh = 0; T[k].mlen = 0; T[k].gb = 0;
+    T[k].steps = 0;
+    T[k].inward = false; T[k].active = false; T[k].done = false;
+  }
+  unsigned long long all_steps = 0, all_hits = 0;
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) {
+      if (!T[k].active && !T[k].done) tl_take<kPacked>(W, Q, T[k], ntl, ordered);
+      any = any || T[k].active;
+    }
+    if (!any) break;
+    // ---- one row step of every tracklet in flight (both directions)
+    TlLoads L[kIlp];
+    bool stop[kIlp];
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k)
+      if (T[k].active) {
+        ++T[k].steps;
+        L[k] = tl_loads<kPacked>(W, T[k]);
+      }
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k) stop[k] = T[k].active && tl_propagate(Q, T[k]);
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k)
+      if (T[k].active && !stop[k]) stop[k] = tl_measure<kPacked, kThreads>(W, Q, T[k], L[k], &sv[k][0][tid]);
+#pragma unroll
+    for (int k = 0; k < kIlp; ++k)
+      if (T[k].active && stop[k]) tl_stop<kThreads>(W, Q, T[k], &sv[k][0][tid], all_steps, all_hits);
+  }
+  if (all_steps) {
+    atomicAdd(&W.cnt->n_steps, all_steps);
+    atomicAdd(&W.cnt->n_tracklet_hits, all_hits);
+  }
+}
+
+// host-side launchers (the kernel templates stay in this translation unit). Shapes: one tracklet
+// per lane at 64, 128 or 256 threads per block, each compiled for 64, 72 or 80 registers per
+// thread; two tracklets per lane at 64 or 128 threads, compiled for 128 registers (fewer spill).
+template <int kT, int kR, bool kP, int kI>
+static auto k5_kernel() {
+  if constexpr (kI == 1) return k_tracklets<kT, kR, kP>;
+  else return k_tracklets_ilp<kT, kR, kP, kI>;
+}
+template <int kT, int kR, int kI>
+static void launch_shape(int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int ordered) {
+  if (packed) k5_kernel<kT, kR, true, kI>()<<<grid, kT, 0, s>>>(W, Q, ordered);
+  else k5_kernel<kT, kR, false, kI>()<<<grid, kT, 0, s>>>(W, Q, ordered);
+}
+template <int kT, int kR, int kI>
 static int shape_blocks(int packed) {
   int nb = 0;
-  if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<kT, kR, true>, kT, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tracklets<kT, kR, false>, kT, 0);
+  if (packed) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k5_kernel<kT, kR, true, kI>(), kT, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k5_kernel<kT, kR, false, kI>(), kT, 0);
   return nb;
 }
+#define TPC_K5_SHAPES                                                                              \
+  TPC_K5_SHAPE(64, 64, 1) TPC_K5_SHAPE(64, 72, 1) TPC_K5_SHAPE(64, 80, 1)                          \
+  TPC_K5_SHAPE(128, 64, 1) TPC_K5_SHAPE(128, 72, 1) TPC_K5_SHAPE(128, 80, 1)                       \
+  TPC_K5_SHAPE(256, 64, 1) TPC_K5_SHAPE(256, 72, 1) TPC_K5_SHAPE(256, 80, 1)                       \
+  TPC_K5_SHAPE(64, 128, 2) TPC_K5_SHAPE(128, 128, 2)
 // false for a shape that is not compiled
-bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
-                      int ordered) {
-#define TPC_K5_SHAPE(T, R)                                      \
-  if (threads == T && regs == R) {                              \
-    launch_shape<T, R>(packed, grid, s, W, Q, ordered);         \
-    return true;                                                \
+bool launch_tracklets(int threads, int regs, int ilp, int packed, int grid, cudaStream_t s, const Work& W,
+                      const DevParams& Q, int ordered) {
+#define TPC_K5_SHAPE(T, R, I)                                  \
+  if (threads == T && regs == R && ilp == I) {                 \
+    launch_shape<T, R, I>(packed, grid, s, W, Q, ordered);     \
+    return true;                                               \
   }
-  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 72) TPC_K5_SHAPE(64, 80)
-  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 72) TPC_K5_SHAPE(128, 80)
-  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 72) TPC_K5_SHAPE(256, 80)
+  TPC_K5_SHAPES
 #undef TPC_K5_SHAPE
   return false;
 }
-int tracklets_blocks_per_sm(int threads, int regs, int packed) {
-#define TPC_K5_SHAPE(T, R) \
-  if (threads == T && regs == R) return shape_blocks<T, R>(packed);
-  TPC_K5_SHAPE(64, 64) TPC_K5_SHAPE(64, 72) TPC_K5_SHAPE(64, 80)
-  TPC_K5_SHAPE(128, 64) TPC_K5_SHAPE(128, 72) TPC_K5_SHAPE(128, 80)
-  TPC_K5_SHAPE(256, 64) TPC_K5_SHAPE(256, 72) TPC_K5_SHAPE(256, 80)
+int tracklets_blocks_per_sm(int threads, int regs, int ilp, int packed) {
+#define TPC_K5_SHAPE(T, R, I) \
+  if (threads == T && regs == R && ilp == I) return shape_blocks<T, R, I>(packed);
+  TPC_K5_SHAPES
 #undef TPC_K5_SHAPE
   return 0;
 }
+#undef TPC_K5_SHAPES
 
 }  // namespace tpc

@@ -49,9 +49,9 @@ __global__ void k_start_order(Work);
 __global__ void k_chains(Work, int);
 __global__ void k_length_offsets(Work);
 __global__ void k_length_scatter(Work, int);
-bool launch_tracklets(int threads, int regs, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
+bool launch_tracklets(int threads, int regs, int ilp, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
                       int ordered);
-int tracklets_blocks_per_sm(int threads, int regs, int packed);
+int tracklets_blocks_per_sm(int threads, int regs, int ilp, int packed);
 bool launch_neighbours(int packed, int warps, int grid, cudaStream_t s, const Work& W, const DevParams& Q, int use_tma);
 int neighbours_blocks_per_sm(int packed, int warps, int mode);
 void prepare_neighbours();
@@ -189,11 +189,12 @@ constexpr int kNumKernels = sizeof(kKernelNames) / sizeof(kKernelNames[0]);
 struct Shape {
   float occ = 2.0f;      // grid bin occupancy
   int k2_warps = 8, k2_tma = 1;
-  int k5_block = 128, k5_regs = 64, k5_bps = 0, k5_order = 0;
+  int k5_block = 128, k5_regs = 64, k5_bps = 0, k5_order = 0, k5_ilp = 1;
   int sel_lanes = 32;
   bool operator==(const Shape& o) const {
     return occ == o.occ && k2_warps == o.k2_warps && k2_tma == o.k2_tma && k5_block == o.k5_block &&
-           k5_regs == o.k5_regs && k5_bps == o.k5_bps && k5_order == o.k5_order && sel_lanes == o.sel_lanes;
+           k5_regs == o.k5_regs && k5_bps == o.k5_bps && k5_order == o.k5_order && k5_ilp == o.k5_ilp &&
+           sel_lanes == o.sel_lanes;
   }
 };
 
@@ -565,12 +566,15 @@ int get_workspace(tpc_ctx* ctx, long long ntot, int nf, std::shared_ptr<Workspac
 
 
 // Enqueue the whole kernel sequence for the batch described in ws->h_desc (already uploaded).
-// resident blocks per SM of a kernel shape (cached: the occupancy query is not free)
-int blocks_per_sm(tpc_ctx* ctx, int kernel, int a, int b) {
-  const long long key = ((long long)kernel << 40) | ((long long)a << 20) | ((long long)b << 1) | (ctx->p.packed ? 1 : 0);
+// resident blocks per SM of a kernel shape (cached: the occupancy query is not free); kernel 0 the
+// neighbour search (a warps, b staging mode), kernel 1 the tracklets (a threads, b registers, c
+// tracklets per lane)
+int blocks_per_sm(tpc_ctx* ctx, int kernel, int a, int b, int c = 1) {
+  const long long key = ((long long)kernel << 40) | ((long long)c << 36) | ((long long)a << 20) | ((long long)b << 1) |
+                        (ctx->p.packed ? 1 : 0);
   auto it = ctx->blocks_cache.find(key);
   if (it != ctx->blocks_cache.end()) return it->second;
-  const int nb = kernel == 0 ? neighbours_blocks_per_sm(ctx->p.packed, a, b) : tracklets_blocks_per_sm(a, b, ctx->p.packed);
+  const int nb = kernel == 0 ? neighbours_blocks_per_sm(ctx->p.packed, a, b) : tracklets_blocks_per_sm(a, b, c, ctx->p.packed);
   ctx->blocks_cache[key] = nb;
   return nb;
 }
@@ -660,9 +664,9 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   }
   mark(ki++);  // tracklets
   {
-    const int nb = std::max(blocks_per_sm(ctx, 1, sh.k5_block, sh.k5_regs), 1);
+    const int nb = std::max(blocks_per_sm(ctx, 1, sh.k5_block, sh.k5_regs, sh.k5_ilp), 1);
     const int bps = sh.k5_bps > 0 ? std::min(sh.k5_bps, nb) : nb;
-    ++nl; launch_tracklets(sh.k5_block, sh.k5_regs, ctx->p.packed, G * bps, s, W, Q, order ? 1 : 0);
+    ++nl; launch_tracklets(sh.k5_block, sh.k5_regs, sh.k5_ilp, ctx->p.packed, G * bps, s, W, Q, order ? 1 : 0);
   }
   mark(ki++);  // zero_w
   ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>((uint32_t*)W.hit_w, &C->ntot, 2 * W.ncap, 0, 2);
@@ -1209,9 +1213,17 @@ void tpc_default_params(tpc_params* p) {
   p->merge_chi2_max = 50.0;
   p->refit_passes = 3;
   p->refit_scale = 100.0;
+  p->k5_ilp = 1;
 }
 
 const char* tpc_version(void) { return "tpctrack 0.1 (sm_103a)"; }
+
+// the tracklet kernel shapes that are compiled (k_tracklet.cu)
+static bool k5_shape_compiled(int block, int regs, int ilp) {
+  if (ilp == 1) return (block == 64 || block == 128 || block == 256) && (regs == 64 || regs == 72 || regs == 80);
+  if (ilp == 2) return (block == 64 || block == 128) && regs == 128;
+  return false;
+}
 
 int tpc_create(const tpc_params* p, tpc_ctx** out) {
   if (!out) return TPC_E_INVAL;
@@ -1226,7 +1238,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   const tpc_params& q = ctx->p;
   if (q.nmin < 1 || q.lmin < 3 || q.n_miss_max < 1 || !(q.tracklet_capacity > 0) || q.max_batch_frames < 1 ||
       q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
-      (q.k5_block != 64 && q.k5_block != 128 && q.k5_block != 256) || (q.k5_regs != 64 && q.k5_regs != 72 && q.k5_regs != 80) ||
+      !k5_shape_compiled(q.k5_block, q.k5_regs, q.k5_ilp) ||
       q.k2_tma < 0 || q.k2_tma > 2 || (q.sel_lanes != 1 && q.sel_lanes != 32) ||
       q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f ||
       q.merge_gap_rows < 1 || q.merge_gap_rows > 150 || !(q.merge_dw >= 0) || !(q.merge_chi2_max >= 0) ||
@@ -1241,6 +1253,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   ctx->shape.k5_regs = q.k5_regs;
   ctx->shape.k5_bps = q.k5_blocks_per_sm;
   ctx->shape.k5_order = q.k5_order;
+  ctx->shape.k5_ilp = q.k5_ilp;
   ctx->shape.sel_lanes = q.sel_lanes;
   make_dev_params(ctx->p, ctx->dp);
   int rc = TPC_OK;
@@ -1760,6 +1773,7 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
       Shape o;
       o.occ = e.bin_occupancy; o.k2_warps = e.k2_warps; o.k2_tma = e.k2_tma; o.k5_block = e.k5_block;
       o.k5_regs = e.k5_regs; o.k5_bps = e.k5_blocks_per_sm; o.k5_order = e.k5_order; o.sel_lanes = e.sel_lanes;
+      o.k5_ilp = e.k5_ilp;
       if (o == sh && e.stage == stage) { obj = e.ms; return TPC_OK; }
     }
     ctx->shape = sh;
@@ -1784,6 +1798,7 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     tpc_tune_entry e{};
     e.bin_occupancy = sh.occ; e.k2_warps = sh.k2_warps; e.k2_tma = sh.k2_tma; e.k5_block = sh.k5_block;
     e.k5_regs = sh.k5_regs; e.k5_blocks_per_sm = sh.k5_bps; e.k5_order = sh.k5_order; e.sel_lanes = sh.sel_lanes;
+    e.k5_ilp = sh.k5_ilp;
     e.ms = vo[vo.size() / 2];
     e.total_ms = vt[vt.size() / 2];
     e.stage = stage;
@@ -1819,13 +1834,14 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     if ((rc = descend(c, 1))) break;
     c.clear();
     for (int b : {64, 128, 256})
-      for (int r : {64, 72, 80}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_bps = 0; c.push_back(t); }
+      for (int r : {64, 72, 80}) { Shape t = best; t.k5_block = b; t.k5_regs = r; t.k5_ilp = 1; t.k5_bps = 0; c.push_back(t); }
+    for (int b : {64, 128}) { Shape t = best; t.k5_block = b; t.k5_regs = 128; t.k5_ilp = 2; t.k5_bps = 0; c.push_back(t); }
     if ((rc = descend(c, 2))) break;
     c.clear();
     for (int o : {0, 1, 2, 3}) { Shape t = best; t.k5_order = o; c.push_back(t); }
     if ((rc = descend(c, 2))) break;
     c.clear();
-    const int nb = std::max(blocks_per_sm(ctx, 1, best.k5_block, best.k5_regs), 1);
+    const int nb = std::max(blocks_per_sm(ctx, 1, best.k5_block, best.k5_regs, best.k5_ilp), 1);
     for (int q : {4, 3, 2, 1}) {  // all resident blocks, then 3/4, 1/2, 1/4 of them
       Shape t = best;
       t.k5_bps = q == 4 ? 0 : std::max(nb * q / 4, 1);
@@ -1847,7 +1863,7 @@ int tpc_autotune(tpc_ctx* ctx, const tpc_frame_t* frames, int32_t n_frames, int3
     const auto& e = ctx->tune_entries[k];
     if (e.bin_occupancy == best.occ && e.k2_warps == best.k2_warps && e.k2_tma == best.k2_tma &&
         e.k5_block == best.k5_block && e.k5_regs == best.k5_regs && e.k5_blocks_per_sm == best.k5_bps &&
-        e.k5_order == best.k5_order && e.sel_lanes == best.sel_lanes)
+        e.k5_order == best.k5_order && e.sel_lanes == best.sel_lanes && e.k5_ilp == best.k5_ilp)
       best_idx = (int)k;
   }
   if (out) {
