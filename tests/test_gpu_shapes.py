@@ -58,6 +58,8 @@ def run(frame, **params):
         tr.track(h)
         res = tr.tracks(h)
         links = [tr.links(h, k, len(frame[2])) for k in range(4)]
+        st = tr.stats(h)
+        res["_steps"] = (st["steps"], st["tracklet_hits"], st["tracklets"])
         return res, links
     finally:
         tr.close()
@@ -74,6 +76,8 @@ def assert_same(a, b):
     for k in range(4):
         assert np.array_equal(la[k], lb[k]), f"links {k} differ"
     assert ra["n_tracks"] == rb["n_tracks"]
+    if "_steps" in ra and "_steps" in rb:
+        assert ra["_steps"] == rb["_steps"]  # the same row steps and fitted hits
     for key in ("sector", "ndf", "hit_offset", "hit_index"):
         assert np.array_equal(ra[key], rb[key]), key
     for key in ("x_ref", "param", "cov", "chi2", "beam"):
