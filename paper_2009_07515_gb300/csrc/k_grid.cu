@@ -449,14 +449,20 @@ __global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
   }
 }
 
+// kScatterParts consecutive blocks share a segment (each takes an interleaved share of its
+// records), so fewer segments are in flight at once and their random-access targets (grid positions
+// and bin starts) stay in L2 while the stores to a line accumulate. The grid is a multiple of it.
 __global__ void __launch_bounds__(1024) k_scatter_seg(Work W) {
   if (W.batch->ntot <= kTwoPassMin || W.cnt->n_bins > (uint32_t)W.bcap) return;
   const BatchDesc* B = W.batch;
   const int nseg = (int)W.cnt->nseg;
-  for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+  const int part = (int)(blockIdx.x % kScatterParts);
+  const int slots = (int)(gridDim.x / kScatterParts);
+  const uint32_t step = blockDim.x * kScatterParts;
+  for (int g = (int)(blockIdx.x / kScatterParts); g < nseg; g += slots) {
     const uint32_t p1 = W.seg_start[g + 1];
     const long long foff = B->f[g / kSegPerFrame].off;
-    for (uint32_t p = W.seg_start[g] + threadIdx.x; p < p1; p += blockDim.x) {
+    for (uint32_t p = W.seg_start[g] + part * blockDim.x + threadIdx.x; p < p1; p += step) {
       const uint4 r = W.rec[p];
       const float y = __uint_as_float(r.x), w = __uint_as_float(r.y);
       int iw;

@@ -638,7 +638,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
   mark(ki++);  // scatter: one pass, or per segment into the segment's range of sorted positions
   ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W, 1);
-  ++nl; k_scatter_seg<<<G, 1024, 0, s>>>(W);
+  ++nl; k_scatter_seg<<<(G / kScatterParts) * kScatterParts, 1024, 0, s>>>(W);
   mark(ki++);  // neighbours
   ++nl; k_chunk_count<<<G, 256, 0, s>>>(W);
   scan(W.k2_off, W.k2_off, &C->nseg, W.scap, &C->n_chunks);

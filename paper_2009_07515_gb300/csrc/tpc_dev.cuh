@@ -44,6 +44,7 @@ constexpr int kMergeBins = 2048;             // w bins per (frame, sector) of th
 // batches of more clusters than this are placed into grid order in two passes per segment (their
 // grid and cluster arrays outgrow the L2); smaller ones in one pass
 constexpr long long kTwoPassMin = 1LL << 23;
+constexpr int kScatterParts = 4;             // blocks that share one segment in the second pass
 
 // error bits (device error word)
 constexpr uint32_t kErrInput = 1u;      // malformed cluster (sector/row range, non-finite)
