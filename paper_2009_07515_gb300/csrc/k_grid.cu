@@ -57,7 +57,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
   }
 }
 
-// single block: exclusive scan of the tile sums in place; total written to *total (if given)
+// single block: exclusive scan of the tile sums in place; total written to *total (if given). Each
+// thread takes kTileItems consecutive sums per pass, so a pass covers 1024 * kTileItems tiles.
+constexpr int kTileItems = 8;
 __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* tile_sum, const uint32_t* n_dev, long long n_host,
                                                      int n_add, uint32_t* total) {
   const uint32_t n = scan_len(n_dev, n_host, n_add);
@@ -66,9 +68,15 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* tile_sum, const u
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  for (uint32_t base = 0; base < ntiles; base += blockDim.x) {
-    uint32_t i = base + threadIdx.x;
-    uint32_t v = i < ntiles ? tile_sum[i] : 0, x = v;
+  for (uint32_t base = 0; base < ntiles; base += blockDim.x * kTileItems) {
+    const uint32_t i0 = base + threadIdx.x * kTileItems;
+    uint32_t v[kTileItems], s = 0;
+#pragma unroll
+    for (int k = 0; k < kTileItems; ++k) {
+      v[k] = i0 + k < ntiles ? tile_sum[i0 + k] : 0u;
+      s += v[k];
+    }
+    uint32_t x = s;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -86,10 +94,14 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(uint32_t* tile_sum, const u
       warp_sums[threadIdx.x] = z - w;
     }
     __syncthreads();
-    uint32_t excl = carry + warp_sums[threadIdx.x >> 5] + x - v;
-    if (i < ntiles) tile_sum[i] = excl;
+    uint32_t run = carry + warp_sums[threadIdx.x >> 5] + x - s;
+#pragma unroll
+    for (int k = 0; k < kTileItems; ++k) {
+      if (i0 + k < ntiles) tile_sum[i0 + k] = run;
+      run += v[k];
+    }
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+    if (threadIdx.x == blockDim.x - 1) carry = run;
     __syncthreads();
   }
   if (threadIdx.x == 0 && total) *total = carry;

@@ -607,15 +607,15 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
       return;
     }
     nl += 3;
-    k_scan_reduce<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp);
+    k_scan_reduce<<<8 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp);
     k_scan_tiles<<<1, 1024, 0, s>>>(W.scan_tmp, n_dev, n_host, 0, total);
-    k_scan_apply<<<2 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp, total, out);
+    k_scan_apply<<<8 * G, 256, 0, s>>>(in, n_dev, n_host, 0, W.scan_tmp, total, out);
   };
   mark(ki++);  // reset
   ++nl; k_reset_counters<<<1, 128, 0, s>>>(W);
   ++nl; k_zero_u32<<<G, 256, 0, s>>>(W.seg_cnt, &C->nseg, W.scap, 0, 1);
   mark(ki++);  // seg_hist
-  ++nl; k_seg_hist<<<G, kHistThreads, 0, s>>>(W);
+  ++nl; k_seg_hist<<<2 * G, kHistThreads, 0, s>>>(W);
   mark(ki++);  // seg_layout
   ++nl; k_seg_layout<<<G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_seg
