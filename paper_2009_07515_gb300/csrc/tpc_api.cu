@@ -646,14 +646,14 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   ++nl; launch_neighbours(ctx->p.packed, sh.k2_warps, G * std::max(blocks_per_sm(ctx, 0, sh.k2_warps, sh.k2_tma), 1), s,
                           W, Q, sh.k2_tma);
   mark(ki++);  // clean
-  ++nl; k_clean<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_clean<<<8 * G, 256, 0, s>>>(W, Q);
   mark(ki++);  // scan_start
   scan(W.seg_nstart, W.seg_nstart, &C->nseg, W.scap, &C->n_starts);
   mark(ki++);  // starts
-  ++nl; k_starts<<<4 * G, 256, 0, s>>>(W, Q);
+  ++nl; k_starts<<<8 * G, 256, 0, s>>>(W, Q);
   ++nl; k_set_ntracklets<<<1, 32, 0, s>>>(W);
   mark(ki++);  // start_order
-  ++nl; k_start_order<<<2 * G, 256, 0, s>>>(W);
+  ++nl; k_start_order<<<8 * G, 256, 0, s>>>(W);
   mark(ki++);  // chains
   const int order = sh.k5_order;
   if (order) { ++nl; k_zero_u32<<<1, 256, 0, s>>>(W.len_cnt, nullptr, kNRow + 1, 0, 1); }
