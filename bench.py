@@ -492,8 +492,6 @@ def cluster_finding_benchmark(tpc, synth, torch, workload: str, steps: int = 10,
     host digits to host clusters, digits -> tracks through the device cluster list, and the FP32
     oracle on a bounded sample of sectors."""
     import oracle
-    if workload == "full_570":
-        return {"skipped": "digitizing the full-size frame (about 1.5e9 digits) is beyond the host generator"}
     dev = torch.device("cuda", torch.cuda.current_device())
     f, d = synth.generate_digits(workload)
     nd = d.n

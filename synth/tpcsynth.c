@@ -471,6 +471,7 @@ typedef struct {
 
 enum { SY_K_CHARGE = 5, SY_K_DSHUFFLE = 6 };
 #define SY_FOOT 3 /* cells deposited on each side of the cluster's own cell */
+#define SY_TCHUNK 512  /* time bins of the digitizer's charge map per pass */
 
 static sy_rng sy_dstream(uint64_t seed, uint64_t kind, uint64_t id) {
   sy_rng r;
@@ -545,60 +546,100 @@ int synth_digitize(const synth_digit_params* p, int64_t n, const uint8_t* sector
     if (jlo < 0) jlo = 0;
     if (jhi > 65534) jhi = 65534;
     if (jhi < jlo) continue;
-    const int64_t nt = jhi - jlo + 1;
-    double* q = (double*)calloc((size_t)(np * nt), sizeof(double));
-    double* qbest = (double*)calloc((size_t)(np * nt), sizeof(double));
-    int32_t* who = (int32_t*)malloc((size_t)(np * nt) * sizeof(int32_t));
-    if (!q || !qbest || !who) { free(q); free(qbest); free(who); failed = 1; continue; }
+    /* the row's charge map in chunks of SY_TCHUNK time bins (a long frame's rows span tens of
+     * thousands of bins at low occupancy): each chunk takes the deposits of the clusters whose
+     * footprint reaches it, in the clusters' order, so every cell sums the same terms in the same
+     * order as a map of the whole range, and the chunks emit their digits in (time, pad) order */
+    const int64_t ncl = e - b;
+    double* cq = (double*)malloc((size_t)(ncl > 0 ? ncl : 1) * sizeof(double));
+    int64_t* cjc = (int64_t*)malloc((size_t)(ncl > 0 ? ncl : 1) * sizeof(int64_t));
+    double* q = (double*)malloc((size_t)np * SY_TCHUNK * sizeof(double));
+    double* qbest = (double*)malloc((size_t)np * SY_TCHUNK * sizeof(double));
+    int32_t* who = (int32_t*)malloc((size_t)np * SY_TCHUNK * sizeof(int32_t));
+    int64_t cap = 1024, cnt = 0;
+    sy_drec* buf = (sy_drec*)malloc((size_t)cap * sizeof(sy_drec));
+    if (!cq || !cjc || !q || !qbest || !who || !buf) {
+      free(cq); free(cjc); free(q); free(qbest); free(who); free(buf);
+      failed = 1;
+      continue;
+    }
     for (int64_t c = b; c < e; ++c) {
       const int64_t i = order[c];
       sy_rng rr = sy_dstream(p->seed, SY_K_CHARGE, (uint64_t)i);
-      const double Q = p->q_median * exp(p->q_log_sigma * sy_gauss(&rr));
-      const double yc = (double)y[i], wc = (double)w[i];
-      const int64_t kc = (int64_t)floor(yc / p->pad_pitch + half);
-      const int64_t jc = (int64_t)floor(wc / p->time_bin_w);
-      double fk[2 * SY_FOOT + 1], fj[2 * SY_FOOT + 1];
-      for (int d = -SY_FOOT; d <= SY_FOOT; ++d) {
-        const double k = (double)(kc + d), j = (double)(jc + d);
-        fk[d + SY_FOOT] = sy_frac((k - half) * p->pad_pitch, (k + 1.0 - half) * p->pad_pitch, yc, p->sigma_pad);
-        fj[d + SY_FOOT] = sy_frac(j * p->time_bin_w, (j + 1.0) * p->time_bin_w, wc, p->sigma_time);
-      }
-      for (int dj = -SY_FOOT; dj <= SY_FOOT; ++dj) {
-        const int64_t j = jc + dj;
-        if (j < jlo || j > jhi) continue;
-        for (int dk = -SY_FOOT; dk <= SY_FOOT; ++dk) {
-          const int64_t k = kc + dk;
-          if (k < 0 || k >= np) continue;
-          const double dq = Q * fk[dk + SY_FOOT] * fj[dj + SY_FOOT];
-          const int64_t cell = (j - jlo) * np + k;
-          q[cell] += dq;
-          if (dq > qbest[cell]) { qbest[cell] = dq; who[cell] = (int32_t)i; }
+      cq[c - b] = p->q_median * exp(p->q_log_sigma * sy_gauss(&rr));
+      cjc[c - b] = (int64_t)floor((double)w[i] / p->time_bin_w);
+    }
+    /* chunks no cluster footprint reaches hold no digit */
+    const int64_t nchunk = (jhi - jlo) / SY_TCHUNK + 1;
+    unsigned char* used = (unsigned char*)calloc((size_t)nchunk, 1);
+    if (!used) {
+      free(cq); free(cjc); free(q); free(qbest); free(who); free(buf);
+      failed = 1;
+      continue;
+    }
+    for (int64_t c = 0; c < ncl; ++c) {
+      int64_t lo = cjc[c] - SY_FOOT - jlo, hi = cjc[c] + SY_FOOT - jlo;
+      if (lo < 0) lo = 0;
+      if (hi > jhi - jlo) hi = jhi - jlo;
+      for (int64_t u = lo / SY_TCHUNK; u <= hi / SY_TCHUNK && lo <= hi; ++u) used[u] = 1;
+    }
+    int32_t tmax = 0;
+    for (int64_t t0 = jlo; t0 <= jhi && !failed; t0 += SY_TCHUNK) {
+      if (!used[(t0 - jlo) / SY_TCHUNK]) continue;
+      const int64_t t1 = t0 + SY_TCHUNK - 1 < jhi ? t0 + SY_TCHUNK - 1 : jhi;
+      const int64_t nt = t1 - t0 + 1;
+      memset(q, 0, (size_t)(np * nt) * sizeof(double));
+      memset(qbest, 0, (size_t)(np * nt) * sizeof(double));
+      for (int64_t c = b; c < e; ++c) {
+        const int64_t jc = cjc[c - b];
+        if (jc + SY_FOOT < t0 || jc - SY_FOOT > t1) continue;
+        const int64_t i = order[c];
+        const double Q = cq[c - b];
+        const double yc = (double)y[i], wc = (double)w[i];
+        const int64_t kc = (int64_t)floor(yc / p->pad_pitch + half);
+        double fk[2 * SY_FOOT + 1], fj[2 * SY_FOOT + 1];
+        for (int d = -SY_FOOT; d <= SY_FOOT; ++d) {
+          const double k = (double)(kc + d), j = (double)(jc + d);
+          fk[d + SY_FOOT] = sy_frac((k - half) * p->pad_pitch, (k + 1.0 - half) * p->pad_pitch, yc, p->sigma_pad);
+          fj[d + SY_FOOT] = sy_frac(j * p->time_bin_w, (j + 1.0) * p->time_bin_w, wc, p->sigma_time);
+        }
+        for (int dj = -SY_FOOT; dj <= SY_FOOT; ++dj) {
+          const int64_t j = jc + dj;
+          if (j < t0 || j > t1) continue;
+          for (int dk = -SY_FOOT; dk <= SY_FOOT; ++dk) {
+            const int64_t k = kc + dk;
+            if (k < 0 || k >= np) continue;
+            const double dq = Q * fk[dk + SY_FOOT] * fj[dj + SY_FOOT];
+            const int64_t cell = (j - t0) * np + k;
+            q[cell] += dq;
+            if (dq > qbest[cell]) { qbest[cell] = dq; who[cell] = (int32_t)i; }
+          }
         }
       }
+      for (int64_t cell = 0; cell < np * nt; ++cell) {
+        int64_t a = (int64_t)floor(q[cell] + 0.5);
+        if (a < p->adc_threshold) continue;
+        if (a > p->adc_max) a = p->adc_max;
+        if (cnt == cap) {
+          sy_drec* nb = (sy_drec*)realloc(buf, (size_t)(2 * cap) * sizeof(sy_drec));
+          if (!nb) { failed = 1; break; }
+          buf = nb;
+          cap *= 2;
+        }
+        const int64_t j = t0 + cell / np;
+        buf[cnt].pad = (uint16_t)(cell % np);
+        buf[cnt].time = (uint16_t)j;
+        buf[cnt].adc = (uint16_t)a;
+        buf[cnt].truth = who[cell];
+        if ((int32_t)j > tmax) tmax = (int32_t)j;
+        ++cnt;
+      }
     }
-    int64_t cnt = 0;
-    for (int64_t cell = 0; cell < np * nt; ++cell)
-      if ((int64_t)floor(q[cell] + 0.5) >= p->adc_threshold) ++cnt;
-    sy_drec* buf = (sy_drec*)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(sy_drec));
-    if (!buf) { free(q); free(qbest); free(who); failed = 1; continue; }
-    int64_t o = 0;
-    int32_t tmax = 0;
-    for (int64_t cell = 0; cell < np * nt; ++cell) {
-      int64_t a = (int64_t)floor(q[cell] + 0.5);
-      if (a < p->adc_threshold) continue;
-      if (a > p->adc_max) a = p->adc_max;
-      const int64_t j = jlo + cell / np;
-      buf[o].pad = (uint16_t)(cell % np);
-      buf[o].time = (uint16_t)j;
-      buf[o].adc = (uint16_t)a;
-      buf[o].truth = who[cell];
-      if ((int32_t)j > tmax) tmax = (int32_t)j;
-      ++o;
-    }
+    free(cq); free(cjc); free(q); free(qbest); free(who); free(used);
+    if (failed) { free(buf); continue; }
     gbuf[g] = buf;
     gcnt[g] = cnt;
     gtmax[g] = cnt > 0 ? tmax + 1 : 0;
-    free(q); free(qbest); free(who);
   }
   int64_t total = 0;
   int32_t ntime = 0;

@@ -203,6 +203,37 @@ def test_pbpb_digits_in_small_windows_match_oracle(tpc):
         tw.close()
 
 
+def test_full_length_frame_in_windows_at_the_default_budget(tpc):
+    """A frame as long as the full-size synchronous frame (128 orbits, about 55,000 time bins) at low
+    occupancy (16 collisions, 4.4e7 digits). Its charge map, about 135 GB, exceeds half of the default
+    80 GB budget, so the default context clusters it in time windows; the clusters of sectors 0-2
+    equal the oracle's on those sectors' digits, bit for bit and in order."""
+    f = synth.generate("full_570", n_collisions=16, seed=41)
+    d = synth.digitize(f)
+    assert d.n_time > 50000 and (d.n_time + 4) * LINE_BYTES > 40 * (1 << 30)
+    tr = tpc.Tracker()
+    try:
+        tr.set_timing(True)
+        g = tr.find_clusters(d.sector, d.row, d.pad, d.time, d.adc, d.n_time)
+        kt = tr.cf_kernel_times()
+        assert kt["cf_peaks"] == 0.0 and kt["cf_fill"] > 0.0 and kt["cf_copy"] > 0.0  # the windowed passes ran
+    finally:
+        tr.close()
+    m = d.sector < 3
+    idx = np.flatnonzero(m)
+    o = oracle.find_clusters(d.sector[m], d.row[m], d.pad[m], d.time[m], d.adc[m], d.n_time, precision="f32",
+                             n_threads=8)
+    sel = np.asarray(g["sector"]) < 3
+    assert int(sel.sum()) == o["n_clusters"] > 0
+    for k in FIELDS:
+        gk = np.asarray(g[k])[sel]
+        ok = idx[o[k].astype(np.int64)] if k == "digit" else o[k]
+        if gk.dtype == np.float32:
+            assert np.array_equal(gk.view(np.uint32), ok.astype(np.float32).view(np.uint32)), k
+        else:
+            assert np.array_equal(gk.astype(np.int64), ok.astype(np.int64)), k
+
+
 def test_windowed_mode_refuses_malformed_input_and_stays_exact(tpc):
     tw = _windowed(tpc, 20)
     try:
