@@ -403,7 +403,8 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
 
 /* Per-kernel device time of the last tpc_find_clusters() call (with tpc_set_timing(ctx, 1)); in
  * time windows cf_fill holds the first pass (fill, peak flags, clear) and cf_copy the second (fill,
- * clusters written to their slots, clear). */
+ * clusters written to their slots, clear), and the launch counts are 3 per window for each of them
+ * and 0 for cf_peaks and cf_clear. */
 int tpc_get_cf_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 
 /* Diagnostic of the kernels' bounded waits (no counterpart in the paper). Every device-side wait of

@@ -191,9 +191,11 @@ class Tracker:
         self._check(self.lib.tpc_load_clusters(self.ctx, ctypes.byref(c), ctypes.byref(h)))
         return h.value
 
-    def cf_kernel_times(self) -> dict:
+    def cf_kernel_times(self, launches: bool = False) -> dict:
         kt = _lib.tpc_kernel_times()
         self._check(self.lib.tpc_get_cf_kernel_times(self.ctx, ctypes.byref(kt)))
+        if launches:
+            return {kt.names[i].decode(): int(kt.launches[i]) for i in range(kt.n_kernels)}
         return {kt.names[i].decode(): float(kt.ms[i]) for i in range(kt.n_kernels)}
 
     # --------------------------------------------------------------- serving

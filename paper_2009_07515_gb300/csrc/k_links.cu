@@ -270,51 +270,55 @@ __global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q,
     const int i = c0 + lane;
     const bool valid = i < b;
     const float2 hi = valid ? hit_by_index<kPacked>(W.hyw, W.hq, W.hcol, W.seg_dim, g, i) : make_float2(0.f, 0.f);
-    float lo_w = valid ? hi.y : 3.0e38f, hi_w = valid ? hi.y : -3.0e38f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      lo_w = fminf(lo_w, __shfl_xor_sync(0xffffffffu, lo_w, o));
-      hi_w = fmaxf(hi_w, __shfl_xor_sync(0xffffffffu, hi_w, o));
-    }
-    // lane 0: ranges of the adjacent rows, then the copies
-    int rng[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per side: p0, p1, iw0, staged base
+    // per side: p0, p1, iw0, staged base (staging modes only: without staging each lane reads its
+    // own window through L1, and the chunk needs neither the ranges nor the barrier)
+    int rng[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int cnt0 = 0, cnt1 = 0, conv = 0;
-    if (lane == 0) {
-      const float amax = fmaxf(fabsf(lo_w), fabsf(hi_w));
-      uint32_t bytes = 0;
-      column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), rng[0], rng[1],
-                   rng[2]);
-      int q0 = rng[0] & ~(kAlign - 1), q1 = (rng[1] + kAlign - 1) & ~(kAlign - 1);
-      const bool st0 = use_tma && q1 > q0 && q1 - q0 <= kSlot;
-      if (st0) { rng[3] = q0; cnt0 = q1 - q0; bytes += (uint32_t)(cnt0 * kRec); }
-      column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), rng[4], rng[5],
-                   rng[6]);
-      q0 = rng[4] & ~(kAlign - 1);
-      q1 = (rng[5] + kAlign - 1) & ~(kAlign - 1);
-      const bool st1 = use_tma && q1 > q0 && q1 - q0 <= kSlot;
-      if (st1) { rng[7] = q0; cnt1 = q1 - q0; bytes += (uint32_t)(cnt1 * kRec); }
-      conv = use_tma == 2 && (st0 || rng[1] <= rng[0]) && (st1 || rng[5] <= rng[4]);
-      // the slots were read by this warp's previous chunk (generic proxy): order before the copies
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive_expect_tx(S.bar, bytes);
-      const char* src = kPacked ? (const char*)W.hq : (const char*)W.hyw;
-      if (cnt0) tma_load_1d(S.stage[0], src + (size_t)rng[3] * kRec, (uint32_t)(cnt0 * kRec), S.bar);
-      if (cnt1) tma_load_1d(S.stage[1], src + (size_t)rng[7] * kRec, (uint32_t)(cnt1 * kRec), S.bar);
-    }
+    if (use_tma) {
+      float lo_w = valid ? hi.y : 3.0e38f, hi_w = valid ? hi.y : -3.0e38f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) rng[j] = __shfl_sync(0xffffffffu, rng[j], 0);
-    cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
-    cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
-    conv = __shfl_sync(0xffffffffu, conv, 0);
-    const bool ok = mbar_wait_bounded(S.bar, parity);
-    if (!__all_sync(0xffffffffu, ok)) {
-      // give the copies in flight a second bounded wait, then this warp stops (its stage is not
-      // used again; the other warps go on)
-      if (!ok) (void)mbar_wait_bounded(S.bar, parity);
-      if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
-      break;
+      for (int o = 16; o > 0; o >>= 1) {
+        lo_w = fminf(lo_w, __shfl_xor_sync(0xffffffffu, lo_w, o));
+        hi_w = fmaxf(hi_w, __shfl_xor_sync(0xffffffffu, hi_w, o));
+      }
+      // lane 0: ranges of the adjacent rows, then the copies
+      if (lane == 0) {
+        const float amax = fmaxf(fabsf(lo_w), fabsf(hi_w));
+        uint32_t bytes = 0;
+        column_range(W, g - 1, (lo_w - ww_dn) - win_pad(amax, ww_dn), (hi_w + ww_dn) + win_pad(amax, ww_dn), rng[0], rng[1],
+                     rng[2]);
+        int q0 = rng[0] & ~(kAlign - 1), q1 = (rng[1] + kAlign - 1) & ~(kAlign - 1);
+        const bool st0 = use_tma && q1 > q0 && q1 - q0 <= kSlot;
+        if (st0) { rng[3] = q0; cnt0 = q1 - q0; bytes += (uint32_t)(cnt0 * kRec); }
+        column_range(W, g + 1, (lo_w - ww_up) - win_pad(amax, ww_up), (hi_w + ww_up) + win_pad(amax, ww_up), rng[4], rng[5],
+                     rng[6]);
+        q0 = rng[4] & ~(kAlign - 1);
+        q1 = (rng[5] + kAlign - 1) & ~(kAlign - 1);
+        const bool st1 = use_tma && q1 > q0 && q1 - q0 <= kSlot;
+        if (st1) { rng[7] = q0; cnt1 = q1 - q0; bytes += (uint32_t)(cnt1 * kRec); }
+        conv = use_tma == 2 && (st0 || rng[1] <= rng[0]) && (st1 || rng[5] <= rng[4]);
+        // the slots were read by this warp's previous chunk (generic proxy): order before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(S.bar, bytes);
+        const char* src = kPacked ? (const char*)W.hq : (const char*)W.hyw;
+        if (cnt0) tma_load_1d(S.stage[0], src + (size_t)rng[3] * kRec, (uint32_t)(cnt0 * kRec), S.bar);
+        if (cnt1) tma_load_1d(S.stage[1], src + (size_t)rng[7] * kRec, (uint32_t)(cnt1 * kRec), S.bar);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) rng[j] = __shfl_sync(0xffffffffu, rng[j], 0);
+      cnt0 = __shfl_sync(0xffffffffu, cnt0, 0);
+      cnt1 = __shfl_sync(0xffffffffu, cnt1, 0);
+      conv = __shfl_sync(0xffffffffu, conv, 0);
+      const bool ok = mbar_wait_bounded(S.bar, parity);
+      if (!__all_sync(0xffffffffu, ok)) {
+        // give the copies in flight a second bounded wait, then this warp stops (its stage is not
+        // used again; the other warps go on)
+        if (!ok) (void)mbar_wait_bounded(S.bar, parity);
+        if (lane == 0) atomicOr(&W.cnt->err, kErrTimeout);
+        break;
+      }
+      parity ^= 1u;
     }
-    parity ^= 1u;
     const float yi = hi.x, wi = hi.y;
     float best = __int_as_float(0x7f800000);
     int bd = -1, bu = -1;
