@@ -115,6 +115,9 @@ typedef struct {
   int32_t k5_ilp;         /* launch shape: tracklets each tracklet thread keeps in flight, 1 or 2; with
                              2 a thread advances both by one row step per iteration, phase by
                              phase, with k5_block 64 or 128 and k5_regs 128 (1) */
+  int32_t wide_votes;     /* tracklet selection: 0 votes with 32-bit keys (hit count, start-hit
+                             rank) while every rank of the batch is below 2^24, else 64-bit keys;
+                             1 always 64-bit keys. The selection is the same either way (0) */
 } tpc_params;
 
 /* Clusters of one time frame, structure of arrays in the caller's order (n entries each).
@@ -402,9 +405,10 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
                       tpc_cluster_list* out, void* cuda_stream);
 
 /* Per-kernel device time of the last tpc_find_clusters() call (with tpc_set_timing(ctx, 1)); in
- * time windows cf_fill holds the first pass (fill, peak flags, clear) and cf_copy the second (fill,
- * clusters written to their slots, clear), and the launch counts are 3 per window for each of them
- * and 0 for cf_peaks and cf_clear. */
+ * time windows cf_fill holds the lists of each window's digit groups and the first pass (fill, peak
+ * flags, clear), cf_copy the second (fill, clusters written to their slots, clear), and the launch
+ * counts are 3 per window for each of them, 6 for cf_scan (the count scan and the three list
+ * kernels) and 0 for cf_peaks and cf_clear. */
 int tpc_get_cf_kernel_times(tpc_ctx* ctx, tpc_kernel_times* out);
 
 /* Diagnostic of the kernels' bounded waits (no counterpart in the paper). Every device-side wait of

@@ -73,6 +73,7 @@ class tpc_params(ctypes.Structure):
         ("refit_passes", ctypes.c_int32),
         ("refit_scale", ctypes.c_double),
         ("k5_ilp", ctypes.c_int32),
+        ("wide_votes", ctypes.c_int32),
     ]
 
 

@@ -13,6 +13,7 @@ constexpr int kCfTile = 256;          // digits per block iteration (8 warps)
 constexpr int kCfGuard = 2;
 constexpr uint32_t kCfErrDigit = 1u;  // a digit outside the pad row / frame, or with zero charge
 constexpr uint32_t kCfErrTwice = 2u;  // two digits in one cell
+constexpr int kCfMaxWindows = 4096;   // a window holds at least 16 of at most 65536 time bins
 struct CfArgs {
   const uint8_t* sector;
   const uint8_t* row;
@@ -55,6 +56,15 @@ struct CfArgs {
   float* o_sig_time;
   uint32_t* o_digit;
   const uint16_t* npads;  // [kNRow] pads of each row
+  // windowed mode: the groups of 32 digits (digits 32 g .. 32 g + 31) a window's passes visit
+  int win, tw, nwin;      // this pass's window, bins per window, windows
+  uint32_t* glist;        // [2 * groups] by window: the groups whose valid digits reach one or two
+                          // windows' maps (window + 2 halo bins on each side)
+  uint32_t* gwide;        // [groups] the groups that reach more windows (visited in every window)
+  uint32_t* gwin;         // [groups] each group's first and last window
+  uint32_t* gcnt;         // [kCfMaxWindows + 1] groups listed per window; [kCfMaxWindows]: wide groups
+  uint32_t* gbeg;         // [kCfMaxWindows + 1] first entry of each window's list (exclusive scan)
+  uint32_t* gcur;         // [kCfMaxWindows + 1] placement cursors; [kCfMaxWindows]: the wide list's
 };
 
 }  // namespace tpc

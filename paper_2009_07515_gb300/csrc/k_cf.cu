@@ -227,17 +227,203 @@ __global__ void __launch_bounds__(kCfTile) k_cf_clear(CfArgs A) {
   }
 }
 
-// ---- time windows (a frame whose map exceeds the budget). Pass 1, per window: fill, flag, clear;
-// the flags of each 32 digits accumulate over the windows (each digit lies in one window), and so do
-// their counts. After the scan of the counts, pass 2, per window: fill, emit, clear; each kept peak
-// computes its cluster again and writes it to its output slot (the group's first slot plus its
-// rank among the group's flagged digits), so the output is in the input order of the peaks, as in
-// one pass over the whole frame.
+// ---- time windows (a frame whose map exceeds the budget). First the group lists: each group of 32
+// consecutive digits is listed under the windows whose maps its valid digits reach (window w's map
+// holds bins [w tw - 2, (w + 1) tw + 2)); a group reaching more than two windows (digits far apart in
+// time, e.g. a shuffled frame) goes to a wide list that every window visits. Then pass 1, per window:
+// fill, flag, clear over the window's groups; the flags of each 32 digits accumulate over the
+// windows (each digit lies in one window), and so do their counts. After the scan of the counts,
+// pass 2, per window: fill, emit, clear; each kept peak computes its cluster again and writes it to
+// its output slot (the group's first slot plus its rank among the group's flagged digits), so the
+// output is in the input order of the peaks, as in one pass over the whole frame. A window's passes
+// read only its groups' digits, not the whole frame's.
+
+// windows [wlo, whi] whose maps the group's digits reach; false when it has none (all lanes take
+// part). Only the sector, row and time are read: a digit with a bad sector, row or time sets
+// kCfErrDigit in bad here, one with a bad pad or charge is found by k_cf_wfill (its group is
+// listed).
+__device__ __forceinline__ bool cf_group_windows(const CfArgs& A, long long g, int lane, int& wlo, int& whi,
+                                                 uint32_t& bad) {
+  const long long i = g * 32 + lane;
+  int tmin = 0x7fffffff, tmax = -1;
+  if (i < A.n) {
+    const int j = A.time[i];
+    if (A.sector[i] < kNSec && A.row[i] < kNRow && j < A.n_time) {
+      tmin = j;
+      tmax = j;
+    } else {
+      bad |= kCfErrDigit;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+  }
+  if (tmax < 0) return false;
+  wlo = max(0, tmin - kCfGuard) / A.tw;
+  whi = min(A.nwin - 1, (tmax + kCfGuard) / A.tw);
+  return true;
+}
+
+// a group's windows as one word: wlo | whi << 16, kCfNoWindow for a group without valid digits
+constexpr uint32_t kCfNoWindow = 0xFFFFFFFFu;
+
+// per group, one warp: its windows into gwin; per block: the groups of each window (shared
+// counters, then one global add per window)
+__global__ void __launch_bounds__(kCfTile) k_cf_gcount(CfArgs A) {
+  extern __shared__ uint32_t sc[];  // [nwin + 1]
+  for (int w = threadIdx.x; w <= A.nwin; w += blockDim.x) sc[w] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long ng = (A.n + 31) / 32, nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  uint32_t bad = 0;
+  for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nwarp) {
+    int wlo = 0, whi = 0;
+    const bool any = cf_group_windows(A, g, lane, wlo, whi, bad);
+    if (lane != 0) continue;
+    A.gwin[g] = any ? (uint32_t)wlo | ((uint32_t)whi << 16) : kCfNoWindow;
+    if (!any) continue;
+    if (whi - wlo <= 1) {
+      atomicAdd(&sc[wlo], 1u);
+      if (whi != wlo) atomicAdd(&sc[whi], 1u);
+    } else {
+      atomicAdd(&sc[A.nwin], 1u);
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < A.nwin; w += blockDim.x)
+    if (sc[w]) atomicAdd(&A.gcnt[w], sc[w]);
+  if (threadIdx.x == 0 && sc[A.nwin]) atomicAdd(&A.gcnt[kCfMaxWindows], sc[A.nwin]);
+  if (bad) atomicOr(A.err, bad);
+}
+
+// one block: exclusive scan of the windows' group counts into the list starts and cursors
+__global__ void __launch_bounds__(1024) k_cf_gscan(CfArgs A) {
+  constexpr int kPer = (kCfMaxWindows + 1 + 1023) / 1024;
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t v[kPer], s = 0;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int w = t * kPer + k;
+    v[k] = w < A.nwin ? A.gcnt[w] : 0u;
+    s += v[k];
+  }
+  uint32_t x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w0 = wsum[lane];
+    uint32_t z = w0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+      if (lane >= o) z += y;
+    }
+    wsum[lane] = z - w0;
+  }
+  __syncthreads();
+  uint32_t run = wsum[warp] + x - s;
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int w = t * kPer + k;
+    if (w <= A.nwin) {
+      A.gbeg[w] = run;
+      A.gcur[w] = run;
+    }
+    run += v[k];
+  }
+  if (t == 0) A.gcur[kCfMaxWindows] = 0u;
+}
+
+// per block, one thread per group (from gwin): the groups counted again, a base per window taken
+// from the cursors, then each group written to its windows' lists (or the wide list)
+__global__ void __launch_bounds__(kCfTile) k_cf_gplace(CfArgs A) {
+  extern __shared__ uint32_t sc[];  // [2 (nwin + 1)]: counts, then local cursors; block bases
+  uint32_t* sb = sc + A.nwin + 1;
+  for (int w = threadIdx.x; w <= A.nwin; w += blockDim.x) sc[w] = 0u;
+  __syncthreads();
+  const long long ng = (A.n + 31) / 32, nthr = (long long)gridDim.x * blockDim.x;
+  const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long g = g0; g < ng; g += nthr) {
+    const uint32_t e = A.gwin[g];
+    if (e == kCfNoWindow) continue;
+    const int wlo = (int)(e & 0xFFFFu), whi = (int)(e >> 16);
+    if (whi - wlo <= 1) {
+      atomicAdd(&sc[wlo], 1u);
+      if (whi != wlo) atomicAdd(&sc[whi], 1u);
+    } else {
+      atomicAdd(&sc[A.nwin], 1u);
+    }
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w <= A.nwin; w += blockDim.x) {
+    sb[w] = sc[w] ? atomicAdd(w < A.nwin ? &A.gcur[w] : &A.gcur[kCfMaxWindows], sc[w]) : 0u;
+    sc[w] = 0u;
+  }
+  __syncthreads();
+  for (long long g = g0; g < ng; g += nthr) {
+    const uint32_t e = A.gwin[g];
+    if (e == kCfNoWindow) continue;
+    const int wlo = (int)(e & 0xFFFFu), whi = (int)(e >> 16);
+    if (whi - wlo <= 1) {
+      A.glist[sb[wlo] + atomicAdd(&sc[wlo], 1u)] = (uint32_t)g;
+      if (whi != wlo) A.glist[sb[whi] + atomicAdd(&sc[whi], 1u)] = (uint32_t)g;
+    } else {
+      A.gwide[sb[A.nwin] + atomicAdd(&sc[A.nwin], 1u)] = (uint32_t)g;
+    }
+  }
+}
+
+// the groups of window A.win, one warp per group: its list, then the wide list
+template <typename F>
+__device__ __forceinline__ void cf_visit_groups(const CfArgs& A, F&& f) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long b = A.gbeg[A.win], nl = (long long)A.gbeg[A.win + 1] - b, nw = A.gcnt[kCfMaxWindows];
+  for (long long x = wid; x < nl + nw; x += nwarp) f(x < nl ? (long long)A.glist[b + x] : (long long)A.gwide[x - nl]);
+}
+
+__global__ void __launch_bounds__(kCfTile) k_cf_wfill(CfArgs A) {
+  const int lane = threadIdx.x & 31;
+  uint32_t bad = 0;
+  cf_visit_groups(A, [&](long long g) {
+    const long long i = g * 32 + lane;
+    int s, r, k, j, q;
+    if (i >= A.n) return;
+    if (!cf_digit(A, i, s, r, k, j, q)) {
+      bad |= kCfErrDigit;
+      return;
+    }
+    if (!cf_in_map(A, j)) return;
+    const size_t c = cf_cell(A, s, r, k, j);
+    const uint32_t sh = (uint32_t)(c & 1) * 16u;
+    const uint32_t old = atomicAdd(reinterpret_cast<uint32_t*>(A.map) + (c >> 1), (uint32_t)q << sh);
+    if ((old >> sh) & 0xffffu) bad |= kCfErrTwice;
+  });
+  if (bad) atomicOr(A.err, bad);
+}
+
+__global__ void __launch_bounds__(kCfTile) k_cf_wclear(CfArgs A) {
+  const int lane = threadIdx.x & 31;
+  cf_visit_groups(A, [&](long long g) {
+    const long long i = g * 32 + lane;
+    int s, r, k, j, q;
+    if (i < A.n && cf_digit(A, i, s, r, k, j, q) && cf_in_map(A, j)) A.map[cf_cell(A, s, r, k, j)] = 0;
+  });
+}
+
 __global__ void __launch_bounds__(kCfTile) k_cf_flag(CfArgs A) {
   const int lane = threadIdx.x & 31;
   uint32_t bad = 0;
-  for (long long base = (long long)blockIdx.x * kCfTile; base < A.n; base += (long long)gridDim.x * kCfTile) {
-    const long long i = base + threadIdx.x;
+  cf_visit_groups(A, [&](long long g) {
+    const long long i = g * 32 + lane;
     bool keep = false;
     int s = 0, r = 0, k = 0, j = 0, q = 0;
     if (i < A.n && cf_digit(A, i, s, r, k, j, q) && cf_in_window(A, j)) {
@@ -248,45 +434,57 @@ __global__ void __launch_bounds__(kCfTile) k_cf_flag(CfArgs A) {
       if (q >= A.q_peak_min && cf_is_peak3(w)) keep = cf_sums3(m, A.stride, w).Q >= A.q_total_min;
     }
     const uint32_t b = __ballot_sync(0xffffffffu, keep);
-    const long long wbase = i - lane;
-    if (lane == 0 && wbase < A.n && b) {
-      A.wflag[wbase >> 5] |= b;
-      A.wcount[wbase >> 5] += (uint32_t)__popc(b);
+    if (lane == 0 && b) {
+      A.wflag[g] |= b;
+      A.wcount[g] += (uint32_t)__popc(b);
     }
-  }
+  });
   if (bad) atomicOr(A.err, bad);
 }
 
+// the groups of window A.win, one lane per group (for kernels whose work per group is sparse)
+template <typename F>
+__device__ __forceinline__ void cf_visit_groups_lane(const CfArgs& A, F&& f) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const long long b = A.gbeg[A.win], nl = (long long)A.gbeg[A.win + 1] - b, nw = A.gcnt[kCfMaxWindows];
+  for (long long x = tid; x < nl + nw; x += nthr) f(x < nl ? (long long)A.glist[b + x] : (long long)A.gwide[x - nl]);
+}
+
+// one lane per group: the group's flagged digits of this window, each cluster computed again and
+// written to its slot (the peaks are about one digit in eight, so a warp per group would leave
+// most lanes idle)
 __global__ void __launch_bounds__(kCfTile) k_cf_emit(CfArgs A) {
-  const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * kCfTile; base < A.n; base += (long long)gridDim.x * kCfTile) {
-    const long long i = base + threadIdx.x;
-    const long long wbase = i - lane;
-    if (wbase >= A.n) continue;  // warp-uniform
-    const uint32_t fl = A.wflag[wbase >> 5];
-    int s = 0, r = 0, k = 0, j = 0, q = 0;
-    if (!((fl >> lane) & 1u) || !cf_digit(A, i, s, r, k, j, q) || !cf_in_window(A, j)) continue;
-    const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
-    int w[3][3];
-    cf_window3(m, A.stride, w);
-    const CfSums S = cf_sums3(m, A.stride, w);
-    const uint32_t o = A.woff[wbase >> 5] + (uint32_t)__popc(fl & ((1u << lane) - 1u));
-    const float Qf = (float)S.Q;
-    const float mk = __fdiv_rn((float)S.Sk, Qf), mj = __fdiv_rn((float)S.Sj, Qf);
-    const float pc = __fadd_rn((float)k, mk), tc = __fadd_rn((float)j, mj);
-    const float centre = __fsub_rn((float)((int)__ldg(A.npads + r) / 2), 0.5f);
-    const float vk = __fsub_rn(__fdiv_rn((float)S.Skk, Qf), __fmul_rn(mk, mk));
-    const float vj = __fsub_rn(__fdiv_rn((float)S.Sjj, Qf), __fmul_rn(mj, mj));
-    A.o_sector[o] = (uint8_t)s;
-    A.o_row[o] = (uint8_t)r;
-    A.o_y[o] = __fmul_rn(__fsub_rn(pc, centre), A.pitch);
-    A.o_w[o] = __fmul_rn(__fadd_rn(tc, 0.5f), A.dw);
-    A.o_qtot[o] = (uint32_t)S.Q;
-    A.o_qmax[o] = (uint16_t)q;
-    A.o_sig_pad[o] = vk > 0.f ? __fsqrt_rn(vk) : 0.f;
-    A.o_sig_time[o] = vj > 0.f ? __fsqrt_rn(vj) : 0.f;
-    A.o_digit[o] = (uint32_t)i;
-  }
+  cf_visit_groups_lane(A, [&](long long g) {
+    uint32_t fl = A.wflag[g];
+    const uint32_t o0 = A.woff[g];
+    for (uint32_t rest = fl; rest; rest &= rest - 1u) {
+      const int l = __ffs(rest) - 1;
+      const long long i = g * 32 + l;
+      int s = 0, r = 0, k = 0, j = 0, q = 0;
+      if (i >= A.n || !cf_digit(A, i, s, r, k, j, q) || !cf_in_window(A, j)) continue;
+      const uint16_t* m = A.map + cf_cell(A, s, r, k, j);
+      int w[3][3];
+      cf_window3(m, A.stride, w);
+      const CfSums S = cf_sums3(m, A.stride, w);
+      const uint32_t o = o0 + (uint32_t)__popc(fl & ((1u << l) - 1u));
+      const float Qf = (float)S.Q;
+      const float mk = __fdiv_rn((float)S.Sk, Qf), mj = __fdiv_rn((float)S.Sj, Qf);
+      const float pc = __fadd_rn((float)k, mk), tc = __fadd_rn((float)j, mj);
+      const float centre = __fsub_rn((float)((int)__ldg(A.npads + r) / 2), 0.5f);
+      const float vk = __fsub_rn(__fdiv_rn((float)S.Skk, Qf), __fmul_rn(mk, mk));
+      const float vj = __fsub_rn(__fdiv_rn((float)S.Sjj, Qf), __fmul_rn(mj, mj));
+      A.o_sector[o] = (uint8_t)s;
+      A.o_row[o] = (uint8_t)r;
+      A.o_y[o] = __fmul_rn(__fsub_rn(pc, centre), A.pitch);
+      A.o_w[o] = __fmul_rn(__fadd_rn(tc, 0.5f), A.dw);
+      A.o_qtot[o] = (uint32_t)S.Q;
+      A.o_qmax[o] = (uint16_t)q;
+      A.o_sig_pad[o] = vk > 0.f ? __fsqrt_rn(vk) : 0.f;
+      A.o_sig_time[o] = vj > 0.f ? __fsqrt_rn(vj) : 0.f;
+      A.o_digit[o] = (uint32_t)i;
+    }
+  });
 }
 
 }  // namespace tpc

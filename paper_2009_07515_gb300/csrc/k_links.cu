@@ -562,7 +562,9 @@ __global__ void __launch_bounds__(256) k_start_order(Work W) {
     }
     const int r = (g % kSegPerFrame) % kNRow;
     const uint32_t sec_first = W.bin_start[W.seg_bb[g - r]];
-    W.starts[lo + before] = make_uint4((uint32_t)i, (uint32_t)g, (c0 - sec_first) + incol, 0u);
+    const uint32_t rank = (c0 - sec_first) + incol;
+    if (rank >= (1u << 24)) atomicOr(&W.cnt->wide_keys, 1u);  // the selection's 32-bit vote keys do not fit
+    W.starts[lo + before] = make_uint4((uint32_t)i, (uint32_t)g, rank, 0u);
   }
 }
 

@@ -1,8 +1,8 @@
 // k_select.cu — K6/K7 tracklet selection and K8 canonical output.
 //
-// Every hit goes to the tracklet with the largest key (nhits << 32 | (2^32 - 1 - rank of the
-// start hit)) among the tracklets with >= nmin hits that contain it (atomicMax on a 64-bit word
-// per hit; keys are unique within a sector, so the outcome does not depend on atomic order). A
+// Every hit goes to the tracklet with the largest key (nhits, then the smaller rank of the start
+// hit) among the tracklets with >= nmin hits that contain it (atomicMax on a 32- or 64-bit word per
+// hit, see Votes; keys are unique within a sector, so the outcome does not depend on atomic order). A
 // tracklet becomes a track if it keeps >= nmin hits and at least half of its hits. Tracks are
 // compacted by prefix sums in tracklet order, which is already canonical (frame, sector, rank of
 // the start hit); each track's kept hits are written in ascending row order as input indices.
@@ -14,6 +14,27 @@ __device__ __forceinline__ unsigned long long tl_key(uint32_t nh, uint32_t rank)
   return ((unsigned long long)nh << 32) | (unsigned long long)(0xFFFFFFFFu - rank);
 }
 
+// The vote words of the hits: 32-bit keys nhits << 24 | (2^24 - 1 - rank) when every start-hit rank
+// of the batch is below 2^24 (k_start_order sets cnt->wide_keys otherwise; nhits <= kNRow < 2^8),
+// else the 64-bit keys of tl_key. Both order a sector's tracklets the same way (nhits, then the
+// smaller rank), so they give the same selection; the 32-bit words halve the array the selection
+// kernels gather from.
+struct Votes {
+  unsigned long long* w64;
+  uint32_t* w32;
+  bool narrow;
+  __device__ explicit Votes(const Work& W)
+      : w64(W.hit_w), w32(reinterpret_cast<uint32_t*>(W.hit_w)), narrow(W.cnt->wide_keys == 0u) {}
+  __device__ __forceinline__ unsigned long long key(uint32_t nh, uint32_t rank) const {
+    return narrow ? (unsigned long long)((nh << 24) | (0xFFFFFFu - rank)) : tl_key(nh, rank);
+  }
+  __device__ __forceinline__ void cast(uint32_t h, unsigned long long k) const {
+    if (narrow) atomicMax(w32 + h, (uint32_t)k);
+    else atomicMax(w64 + h, k);
+  }
+  __device__ __forceinline__ unsigned long long of(uint32_t h) const { return narrow ? (unsigned long long)w32[h] : w64[h]; }
+};
+
 // One warp per tracklet (grid-stride over tracklets): the lanes take the tracklet's rows 32 at a
 // time, so the row loop's dependent loads (slab entry, then the hit's word) overlap across lanes;
 // a tracklet's rows are consecutive slab words, so each pass reads one or two 128-byte lines.
@@ -24,23 +45,25 @@ __device__ __forceinline__ uint32_t warp_global(int& lane) {
 
 __global__ void __launch_bounds__(256) k_votes_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
+  const Votes votes(W);
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
     const uint32_t info = W.tl_info[t];
     const uint32_t nh = info & 255u;
     if (!(info >> 24) || (int)nh < Q.nmin) continue;
-    const unsigned long long key = tl_key(nh, W.starts[t].z);
+    const unsigned long long key = votes.key(nh, W.starts[t].z);
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     for (int r = ref + lane; r <= top; r += 32) {
       const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit) atomicMax(&W.hit_w[h], key);
+      if (h != kNoHit) votes.cast(h, key);
     }
   }
 }
 
 __global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
+  const Votes votes(W);
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
@@ -48,14 +71,14 @@ __global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
     const uint32_t nh = info & 255u;
     uint32_t acc = 0, kept = 0;
     if ((info >> 24) && (int)nh >= Q.nmin) {
-      const unsigned long long key = tl_key(nh, W.starts[t].z);
+      const unsigned long long key = votes.key(nh, W.starts[t].z);
       const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
       for (int r0 = ref; r0 <= top; r0 += 32) {
         const int r = r0 + lane;
         bool mine = false;
         if (r <= top) {
           const uint32_t h = W.slab[slab_at(t, r)];
-          mine = h != kNoHit && W.hit_w[h] == key;
+          mine = h != kNoHit && votes.of(h) == key;
         }
         kept += (uint32_t)__popc(__ballot_sync(0xffffffffu, mine));
       }
@@ -70,6 +93,7 @@ __global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
 
 __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
+  const Votes votes(W);
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
@@ -78,7 +102,7 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
     const uint32_t info = W.tl_info[t];
     const uint32_t nh = info & 255u;
     const uint4 st = W.starts[t];
-    const unsigned long long key = tl_key(nh, st.z);
+    const unsigned long long key = votes.key(nh, st.z);
     if (lane < 22) {
       const float v = W.tl_state[(long long)t * 24 + lane];
       if (lane < 5) W.tr_param[(long long)k * 5 + lane] = v;
@@ -100,7 +124,7 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
       bool mine = false;
       if (r <= top) {
         h = W.slab[slab_at(t, r)];
-        mine = h != kNoHit && W.hit_w[h] == key;
+        mine = h != kNoHit && votes.of(h) == key;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (mine) W.tr_hits[off + (uint32_t)__popc(m & ((1u << lane) - 1u))] = W.horig[h];
@@ -127,39 +151,41 @@ __device__ __forceinline__ RowRange warp_rows(bool on, int ref, int top) {
 
 __global__ void __launch_bounds__(256) k_votes_thread(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
+  const Votes votes(W);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
     const uint32_t t = t0 + (threadIdx.x & 31u);
     const uint32_t info = t < ntl ? W.tl_info[t] : 0u;
     const uint32_t nh = info & 255u;
     const bool on = (info >> 24) && (int)nh >= Q.nmin;
-    const unsigned long long key = on ? tl_key(nh, W.starts[t].z) : 0ull;
+    const unsigned long long key = on ? votes.key(nh, W.starts[t].z) : 0ull;
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     const RowRange rr = warp_rows(on, ref, top);
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
       const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit) atomicMax(&W.hit_w[h], key);
+      if (h != kNoHit) votes.cast(h, key);
     }
   }
 }
 
 __global__ void __launch_bounds__(256) k_kept_thread(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
+  const Votes votes(W);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
     const uint32_t t = t0 + (threadIdx.x & 31u);
     const uint32_t info = t < ntl ? W.tl_info[t] : 0u;
     const uint32_t nh = info & 255u;
     const bool on = (info >> 24) && (int)nh >= Q.nmin;
-    const unsigned long long key = on ? tl_key(nh, W.starts[t].z) : 0ull;
+    const unsigned long long key = on ? votes.key(nh, W.starts[t].z) : 0ull;
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     const RowRange rr = warp_rows(on, ref, top);
     uint32_t kept = 0;
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
       const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit && W.hit_w[h] == key) ++kept;
+      if (h != kNoHit && votes.of(h) == key) ++kept;
     }
     const uint32_t acc = (on && (int)kept >= Q.nmin && 2u * kept >= nh) ? 1u : 0u;
     if (t < ntl) {
@@ -171,6 +197,7 @@ __global__ void __launch_bounds__(256) k_kept_thread(Work W, DevParams Q) {
 
 __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
+  const Votes votes(W);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
     const uint32_t t = t0 + (threadIdx.x & 31u);
@@ -186,7 +213,7 @@ __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q
       info = W.tl_info[t];
       const uint32_t nh = info & 255u;
       const uint4 st = W.starts[t];
-      key = tl_key(nh, st.z);
+      key = votes.key(nh, st.z);
       const float* src = W.tl_state + (long long)t * 24;
 #pragma unroll
       for (int i = 0; i < 5; ++i) W.tr_param[(long long)k * 5 + i] = src[i];
@@ -204,7 +231,7 @@ __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
       const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit && W.hit_w[h] == key) W.tr_hits[off++] = W.horig[h];
+      if (h != kNoHit && votes.of(h) == key) W.tr_hits[off++] = W.horig[h];
     }
   }
 }
@@ -247,6 +274,7 @@ __device__ __forceinline__ void mark_vicinity(const Work& W, const DevParams& Q,
 }
 template <bool kPacked>
 __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
+  const Votes votes(W);
   const uint32_t ntl = W.cnt->n_tracklets;
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -255,7 +283,7 @@ __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
     if (W.tl_kept[t + 1] == k) continue;
     const uint32_t info = W.tl_info[t];
     const uint4 st = W.starts[t];
-    const unsigned long long key = tl_key(info & 255u, st.z);
+    const unsigned long long key = votes.key(info & 255u, st.z);
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     const int g0 = (int)st.y, gb = g0 - (g0 % kSegPerFrame) % kNRow;
     const long long off = W.batch->f[g0 / kSegPerFrame].off;
@@ -271,7 +299,7 @@ __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
       bool mine = false;
       if (r <= top) {
         const uint32_t h = W.slab[slab_at(t, r)];
-        mine = h != kNoHit && W.hit_w[h] == key;
+        mine = h != kNoHit && votes.of(h) == key;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (m) last = c0 + 31 - __clz((int)m);
@@ -294,7 +322,7 @@ __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
       uint32_t h = kNoHit;
       if (in) {
         h = W.slab[slab_at(t, r)];
-        mine = h != kNoHit && W.hit_w[h] == key;
+        mine = h != kNoHit && votes.of(h) == key;
       }
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (mine) {
@@ -376,6 +404,7 @@ __global__ void k_reset_counters(Work W) {
     c->err = 0; c->n_starts = 0; c->n_tracklets = 0; c->k5_next = 0; c->n_bins = 0;
     c->seg_next[0] = 0; c->seg_next[1] = 0; c->seg_next[2] = 0; c->n_chunks = 0; c->k2_next = 0;
     c->n_sorted = 0; c->n_tracks = 0; c->n_track_hits = 0; c->n_steps = 0; c->n_tracklet_hits = 0;
+    c->wide_keys = W.wide_votes ? 1u : 0u;
   }
 }
 

@@ -79,6 +79,11 @@ __global__ void k_cf_copy(CfArgs);
 __global__ void k_cf_clear(CfArgs);
 __global__ void k_cf_flag(CfArgs);
 __global__ void k_cf_emit(CfArgs);
+__global__ void k_cf_gcount(CfArgs);
+__global__ void k_cf_gscan(CfArgs);
+__global__ void k_cf_gplace(CfArgs);
+__global__ void k_cf_wfill(CfArgs);
+__global__ void k_cf_wclear(CfArgs);
 
 // Cluster finding: device buffers sized by a digit capacity, the charge map (kept zero between
 // calls), page-locked host copies of the last call's clusters, timing events.
@@ -90,6 +95,7 @@ struct CfState {
   uint16_t *in_pad = nullptr, *in_time = nullptr, *in_adc = nullptr;
   uint32_t *wcount = nullptr, *woff = nullptr, *wsrc = nullptr, *scan_tmp = nullptr, *small = nullptr;
   uint32_t* wflag = nullptr;
+  uint32_t *glist = nullptr, *gwide = nullptr, *gwin = nullptr, *gcnt = nullptr, *gbeg = nullptr, *gcur = nullptr;
   int windows = 1;                  // time windows of the last call (1: the whole frame in one map)
   uint8_t *t_sector = nullptr, *t_row = nullptr;
   float *t_y = nullptr, *t_w = nullptr, *t_sp = nullptr, *t_st = nullptr;
@@ -513,6 +519,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
   W.ncap = ws->ncap; W.scap = ws->scap; W.bcap = ws->bcap; W.tcap = ws->tcap; W.scan_tmp_cap = ws->scan_cap;
   W.k2cap = ws->ncap / 32 + ws->scap + 1;
   W.packed = ctx->p.packed ? 1 : 0;
+  W.wide_votes = ctx->p.wide_votes ? 1 : 0;
   CK(cudaMallocHost(&ws->h_desc, sizeof(BatchDesc)));
   CK(cudaMallocHost(&ws->h_cnt, sizeof(DevCounters)));
   memset(ws->h_desc, 0, sizeof(BatchDesc));
@@ -1087,6 +1094,8 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
   };
   const size_t o_is = take(cap), o_ir = take(cap), o_ip = take(2 * cap), o_it = take(2 * cap), o_ia = take(2 * cap);
   const size_t o_wc = take(4 * nw), o_wo = take(4 * (nw + 1)), o_ws = take(4 * nw), o_wf = take(4 * nw);
+  const size_t o_gl = take(4 * 2 * nw), o_gw = take(4 * nw), o_gn = take(4 * nw);
+  const size_t o_gc = take(4 * 3 * (size_t)(kCfMaxWindows + 1));
   const size_t o_tmp = take(4 * (nw / 2048 + 2)), o_small = take(16), o_np = take(2 * kNRow);
   const size_t t_s = take(cap32), t_r = take(cap32), t_y = take(4 * cap32), t_w = take(4 * cap32);
   const size_t t_sp = take(4 * cap32), t_st = take(4 * cap32), t_q = take(4 * cap32), t_d = take(4 * cap32);
@@ -1113,6 +1122,12 @@ int cf_reserve(tpc_ctx* ctx, long long n) {
   cf.woff = (uint32_t*)(b + o_wo);
   cf.wsrc = (uint32_t*)(b + o_ws);
   cf.wflag = (uint32_t*)(b + o_wf);
+  cf.glist = (uint32_t*)(b + o_gl);
+  cf.gwide = (uint32_t*)(b + o_gw);
+  cf.gwin = (uint32_t*)(b + o_gn);
+  cf.gcnt = (uint32_t*)(b + o_gc);
+  cf.gbeg = cf.gcnt + (kCfMaxWindows + 1);
+  cf.gcur = cf.gbeg + (kCfMaxWindows + 1);
   cf.t_sector = (uint8_t*)(b + t_s);
   cf.t_row = (uint8_t*)(b + t_r);
   cf.t_y = (float*)(b + t_y);
@@ -1214,6 +1229,7 @@ void tpc_default_params(tpc_params* p) {
   p->refit_passes = 3;
   p->refit_scale = 100.0;
   p->k5_ilp = 1;
+  p->wide_votes = 0;
 }
 
 const char* tpc_version(void) { return "tpctrack 0.1 (sm_103a)"; }
@@ -1238,7 +1254,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
   const tpc_params& q = ctx->p;
   if (q.nmin < 1 || q.lmin < 3 || q.n_miss_max < 1 || !(q.tracklet_capacity > 0) || q.max_batch_frames < 1 ||
       q.max_batch_frames > kMaxFrames || (q.k2_warps != 4 && q.k2_warps != 8) ||
-      !k5_shape_compiled(q.k5_block, q.k5_regs, q.k5_ilp) ||
+      !k5_shape_compiled(q.k5_block, q.k5_regs, q.k5_ilp) || q.wide_votes < 0 || q.wide_votes > 1 ||
       q.k2_tma < 0 || q.k2_tma > 2 || (q.sel_lanes != 1 && q.sel_lanes != 32) ||
       q.k5_blocks_per_sm < 0 || q.k5_order < 0 || q.k5_order > 3 || q.bin_occupancy > 64.0f ||
       q.merge_gap_rows < 1 || q.merge_gap_rows > 150 || !(q.merge_dw >= 0) || !(q.merge_chi2_max >= 0) ||
@@ -2030,33 +2046,43 @@ int tpc_find_clusters(tpc_ctx* ctx, const tpc_cf_params* params, const tpc_digit
     const int64_t nl[kCfKernels] = {1, 1, 3, 1, 1};
     for (int k = 0; k < kCfKernels; ++k) cf.launches[k] = nl[k];
   } else {
-    // pass 1 over the windows: fill, flag the kept peaks, clear; then the scan of their counts;
-    // pass 2: fill, write each kept peak's cluster to its slot, clear (stage times: cf_fill holds
-    // pass 1, cf_copy pass 2)
+    // the group lists of the windows; pass 1 over the windows: fill, flag the kept peaks, clear;
+    // then the scan of their counts; pass 2: fill, write each kept peak's cluster to its slot, clear
+    // (stage times: cf_fill holds the lists and pass 1, cf_copy pass 2)
+    const int nwin = (d->n_time + tw - 1) / tw;  // <= kCfMaxWindows: tw >= 16, n_time <= 65535
+    A.tw = tw;
+    A.nwin = nwin;
+    A.glist = cf.glist; A.gwide = cf.gwide; A.gwin = cf.gwin; A.gcnt = cf.gcnt; A.gbeg = cf.gbeg; A.gcur = cf.gcur;
     CK(cudaMemsetAsync(cf.wcount, 0, 4 * (size_t)nwarps, s));
     CK(cudaMemsetAsync(cf.wflag, 0, 4 * (size_t)nwarps, s));
-    int nwin = 0;
+    CK(cudaMemsetAsync(cf.gcnt, 0, 4 * (size_t)(kCfMaxWindows + 1), s));
     if (timing) cudaEventRecord(cf.ev[0], s);
-    for (int t0 = 0; t0 < d->n_time; t0 += tw, ++nwin) {
-      A.t_lo = t0;
-      A.t_hi = std::min(t0 + tw, d->n_time);
-      k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
+    const size_t list_smem = 4 * (size_t)(nwin + 1);
+    k_cf_gcount<<<grid, kCfTile, list_smem, s>>>(A);
+    k_cf_gscan<<<1, 1024, 0, s>>>(A);
+    k_cf_gplace<<<grid, kCfTile, 2 * list_smem, s>>>(A);
+    for (int w = 0; w < nwin; ++w) {
+      A.win = w;
+      A.t_lo = w * tw;
+      A.t_hi = std::min(A.t_lo + tw, d->n_time);
+      k_cf_wfill<<<grid, kCfTile, 0, s>>>(A);
       k_cf_flag<<<grid, kCfTile, 0, s>>>(A);
-      k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
+      k_cf_wclear<<<grid, kCfTile, 0, s>>>(A);
     }
     if (timing) { cudaEventRecord(cf.ev[1], s); cudaEventRecord(cf.ev[2], s); }
     scan_counts();
     if (timing) cudaEventRecord(cf.ev[3], s);
-    for (int t0 = 0; t0 < d->n_time; t0 += tw) {
-      A.t_lo = t0;
-      A.t_hi = std::min(t0 + tw, d->n_time);
-      k_cf_fill<<<grid, kCfTile, 0, s>>>(A);
+    for (int w = 0; w < nwin; ++w) {
+      A.win = w;
+      A.t_lo = w * tw;
+      A.t_hi = std::min(A.t_lo + tw, d->n_time);
+      k_cf_wfill<<<grid, kCfTile, 0, s>>>(A);
       k_cf_emit<<<grid, kCfTile, 0, s>>>(A);
-      k_cf_clear<<<grid, kCfTile, 0, s>>>(A);
+      k_cf_wclear<<<grid, kCfTile, 0, s>>>(A);
     }
     if (timing) { cudaEventRecord(cf.ev[4], s); cudaEventRecord(cf.ev[5], s); }
     cf.windows = nwin;
-    const int64_t nl[kCfKernels] = {3 * nwin, 0, 3, 3 * nwin, 0};
+    const int64_t nl[kCfKernels] = {3 * nwin, 0, 6, 3 * nwin, 0};  // cf_scan: the count scan and the three list kernels
     for (int k = 0; k < kCfKernels; ++k) cf.launches[k] = nl[k];
   }
   cudaError_t e = cudaGetLastError();

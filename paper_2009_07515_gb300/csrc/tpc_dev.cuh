@@ -110,6 +110,7 @@ struct DevCounters {
   uint32_t n_starts;      // start hits found (may exceed tcap: overflow)
   uint32_t n_tracklets;   // min(n_starts, tcap)
   uint32_t k5_next;       // work counter of the tracklet kernel
+  uint32_t wide_keys;     // non-zero: a start-hit rank of the batch is >= 2^24 (64-bit vote keys)
   uint32_t seg_next[3];   // segment work counters of the neighbour, cleaning and start kernels
   uint32_t n_chunks;      // 32-hit chunks of the neighbour kernel
   uint32_t k2_next;       // chunk work counter of the neighbour kernel
@@ -211,6 +212,7 @@ struct Work {
   uint32_t* scan_tmp;    // [scan_tmp_cap]
   long long ncap, scap, bcap, tcap, scan_tmp_cap, k2cap;
   int packed;            // 1: 16-bit cluster storage (hq, hcol), 0: FP32 (hyw)
+  int wide_votes;        // 1: 64-bit vote keys whatever the ranks (tpc_params.wide_votes)
 };
 
 // ------------------------------------------------------------------------------------ helpers

@@ -84,13 +84,13 @@ def test_launch_shape_parameters_are_validated(lib):
     from paper_2009_07515_gb300 import _lib
     for bad in (dict(k2_warps=5), dict(k2_tma=3), dict(k5_block=96), dict(k5_regs=32), dict(k5_order=4), dict(sel_lanes=8), dict(k5_blocks_per_sm=-1), dict(k5_ilp=0), dict(k5_ilp=3),
                 dict(k5_ilp=2), dict(k5_ilp=2, k5_regs=128, k5_block=256), dict(k5_ilp=2, k5_regs=96, k5_block=128),
-                dict(k5_ilp=1, k5_regs=128)):
+                dict(k5_ilp=1, k5_regs=128), dict(wide_votes=2), dict(wide_votes=-1)):
         p = _lib.default_params(**bad)
         ctx = ctypes.c_void_p()
         assert lib.tpc_create(ctypes.byref(p), ctypes.byref(ctx)) == _lib.TPC_E_INVAL, bad
     p = _lib.default_params()
     assert (p.k2_warps, p.k2_tma, p.k5_block, p.k5_regs, p.k5_blocks_per_sm, p.k5_order, p.sel_lanes, p.autotune,
-            p.k5_ilp) == (8, 1, 128, 80, 0, 1, 32, 0, 1)
+            p.k5_ilp, p.wide_votes) == (8, 1, 128, 80, 0, 1, 32, 0, 1, 0)
     assert lib.tpc_autotune(None, None, 0, 1, None) == _lib.TPC_E_INVAL
 
 

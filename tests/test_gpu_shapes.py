@@ -1,8 +1,8 @@
 """Launch shapes and the autotuner: no result depends on the shape the kernels run with.
 
 Every shape the autotuner can pick (grid occupancy, neighbour-search warps per block and staging,
-tracklet block size, registers, tracklets in flight per thread, blocks per SM and processing order)
-must give bit-identical links
+tracklet block size, registers, tracklets in flight per thread, blocks per SM, processing order and
+the width of the selection's vote keys) must give bit-identical links
 and tracks; the autotuner must report what it timed and leave the results unchanged.
 """
 import numpy as np
@@ -34,6 +34,8 @@ SHAPES = [
     dict(k5_ilp=2, k5_block=128, k5_regs=128),
     dict(k5_ilp=2, k5_block=64, k5_regs=128, k5_order=1),
     dict(k5_ilp=2, k5_block=128, k5_regs=128, k5_blocks_per_sm=1),
+    dict(wide_votes=1),
+    dict(wide_votes=1, sel_lanes=1),
     dict(sel_lanes=1),
 ]
 
