@@ -5,7 +5,8 @@
 // hit, see Votes; keys are unique within a sector, so the outcome does not depend on atomic order). A
 // tracklet becomes a track if it keeps >= nmin hits and at least half of its hits. Tracks are
 // compacted by prefix sums in tracklet order, which is already canonical (frame, sector, rank of
-// the start hit); each track's kept hits are written in ascending row order as input indices.
+// the start hit); each track's kept hits are written in ascending row order as input indices
+// (k_kept clears the slab entries of the hits a tracklet lost, so the writer reads no vote words).
 #include "tpc_dev.cuh"
 
 namespace tpc {
@@ -79,6 +80,7 @@ __global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
         if (r <= top) {
           const uint32_t h = W.slab[slab_at(t, r)];
           mine = h != kNoHit && votes.of(h) == key;
+          if (h != kNoHit && !mine) W.slab[slab_at(t, r)] = kNoHit;  // a hit the tracklet lost
         }
         kept += (uint32_t)__popc(__ballot_sync(0xffffffffu, mine));
       }
@@ -93,7 +95,6 @@ __global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
 
 __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  const Votes votes(W);
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = warp_global(lane); t < ntl; t += nw) {
@@ -102,7 +103,6 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
     const uint32_t info = W.tl_info[t];
     const uint32_t nh = info & 255u;
     const uint4 st = W.starts[t];
-    const unsigned long long key = votes.key(nh, st.z);
     if (lane < 22) {
       const float v = W.tl_state[(long long)t * 24 + lane];
       if (lane < 5) W.tr_param[(long long)k * 5 + lane] = v;
@@ -116,16 +116,14 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
       W.tr_ndf[k] = 2 * (int)nh - 5;
       W.tr_hoff[k] = (long long)off;
     }
-    // kept hits in ascending row order: ballot over each group of 32 rows
+    // kept hits in ascending row order (k_kept left only them in the slab): ballot over each group
+    // of 32 rows
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     for (int r0 = ref; r0 <= top; r0 += 32) {
       const int r = r0 + lane;
       uint32_t h = kNoHit;
-      bool mine = false;
-      if (r <= top) {
-        h = W.slab[slab_at(t, r)];
-        mine = h != kNoHit && votes.of(h) == key;
-      }
+      if (r <= top) h = W.slab[slab_at(t, r)];
+      const bool mine = h != kNoHit;
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (mine) W.tr_hits[off + (uint32_t)__popc(m & ((1u << lane) - 1u))] = W.horig[h];
       off += (uint32_t)__popc(m);
@@ -185,7 +183,9 @@ __global__ void __launch_bounds__(256) k_kept_thread(Work W, DevParams Q) {
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
       const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit && votes.of(h) == key) ++kept;
+      if (h == kNoHit) continue;
+      if (votes.of(h) == key) ++kept;
+      else W.slab[slab_at(t, r)] = kNoHit;  // a hit the tracklet lost
     }
     const uint32_t acc = (on && (int)kept >= Q.nmin && 2u * kept >= nh) ? 1u : 0u;
     if (t < ntl) {
@@ -197,7 +197,6 @@ __global__ void __launch_bounds__(256) k_kept_thread(Work W, DevParams Q) {
 
 __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q) {
   const uint32_t ntl = W.cnt->n_tracklets;
-  const Votes votes(W);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t t0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); t0 < ntl; t0 += stride) {
     const uint32_t t = t0 + (threadIdx.x & 31u);
@@ -208,12 +207,10 @@ __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q
       on = W.tl_kept[t + 1] != k;
     }
     uint32_t info = 0, off = 0;
-    unsigned long long key = 0;
     if (on) {
       info = W.tl_info[t];
       const uint32_t nh = info & 255u;
       const uint4 st = W.starts[t];
-      key = votes.key(nh, st.z);
       const float* src = W.tl_state + (long long)t * 24;
 #pragma unroll
       for (int i = 0; i < 5; ++i) W.tr_param[(long long)k * 5 + i] = src[i];
@@ -230,8 +227,8 @@ __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q
     const RowRange rr = warp_rows(on, ref, top);
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
-      const uint32_t h = W.slab[slab_at(t, r)];
-      if (h != kNoHit && votes.of(h) == key) W.tr_hits[off++] = W.horig[h];
+      const uint32_t h = W.slab[slab_at(t, r)];  // k_kept left only the track's own hits
+      if (h != kNoHit) W.tr_hits[off++] = W.horig[h];
     }
   }
 }
