@@ -453,10 +453,24 @@ __global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
   const int nseg = (int)W.cnt->nseg;
   for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
     const uint32_t p1 = W.seg_start[g + 1];
-    for (uint32_t p = W.seg_start[g] + threadIdx.x; p < p1; p += blockDim.x) {
-      const uint4 r = W.rec[p];
-      int iw;
-      W.rank[p] = atomicAdd(&W.bin_start[seg_bin(W, g, __uint_as_float(r.x), __uint_as_float(r.y), iw)], 1u);
+    // kSegUnroll records per thread in flight: their loads, then their atomics, then the ranks
+    for (uint32_t b = W.seg_start[g] + threadIdx.x; b < p1; b += blockDim.x * kSegUnroll) {
+      uint4 r[kSegUnroll];
+      uint32_t rk[kSegUnroll];
+#pragma unroll
+      for (int u = 0; u < kSegUnroll; ++u) {
+        const uint32_t p = b + u * blockDim.x;
+        r[u] = p < p1 ? W.rec[p] : make_uint4(0u, 0u, 0u, 0u);
+      }
+#pragma unroll
+      for (int u = 0; u < kSegUnroll; ++u) {
+        int iw;
+        if (b + u * blockDim.x < p1)
+          rk[u] = atomicAdd(&W.bin_start[seg_bin(W, g, __uint_as_float(r[u].x), __uint_as_float(r[u].y), iw)], 1u);
+      }
+#pragma unroll
+      for (int u = 0; u < kSegUnroll; ++u)
+        if (b + u * blockDim.x < p1) W.rank[b + u * blockDim.x] = rk[u];
     }
   }
 }
@@ -474,21 +488,36 @@ __global__ void __launch_bounds__(1024) k_scatter_seg(Work W) {
   for (int g = (int)(blockIdx.x / kScatterParts); g < nseg; g += slots) {
     const uint32_t p1 = W.seg_start[g + 1];
     const long long foff = B->f[g / kSegPerFrame].off;
-    for (uint32_t p = W.seg_start[g] + part * blockDim.x + threadIdx.x; p < p1; p += step) {
-      const uint4 r = W.rec[p];
-      const float y = __uint_as_float(r.x), w = __uint_as_float(r.y);
-      int iw;
-      const uint32_t q = W.bin_start[seg_bin(W, g, y, w, iw)] + W.rank[p];
-      if (W.packed) {
-        const int4 dim = W.seg_dim[g];
-        const uint32_t qy = (uint32_t)rintf((y + 64.0f) * 512.0f);
-        const int qw = (int)rintf(w * 512.0f) - col_base(dim.z, dim.w, iw);
-        W.hq[q] = qy | ((uint32_t)qw << 16);
-        W.hcol[q] = (uint16_t)iw;
-      } else {
-        W.hyw[q] = make_float2(y, w);
+    // kSegUnroll records per thread in flight: their loads, then their bins' starts, then the stores
+    for (uint32_t b = W.seg_start[g] + part * blockDim.x + threadIdx.x; b < p1; b += step * kSegUnroll) {
+      uint4 r[kSegUnroll];
+      uint32_t rk[kSegUnroll], q[kSegUnroll];
+      int iw[kSegUnroll];
+#pragma unroll
+      for (int u = 0; u < kSegUnroll; ++u) {
+        const uint32_t p = b + u * step;
+        r[u] = p < p1 ? W.rec[p] : make_uint4(0u, 0u, 0u, 0u);
+        rk[u] = p < p1 ? W.rank[p] : 0u;
       }
-      W.horig[q] = (uint32_t)((long long)r.z - foff);
+#pragma unroll
+      for (int u = 0; u < kSegUnroll; ++u)
+        if (b + u * step < p1)
+          q[u] = W.bin_start[seg_bin(W, g, __uint_as_float(r[u].x), __uint_as_float(r[u].y), iw[u])] + rk[u];
+#pragma unroll
+      for (int u = 0; u < kSegUnroll; ++u) {
+        if (b + u * step >= p1) continue;
+        const float y = __uint_as_float(r[u].x), w = __uint_as_float(r[u].y);
+        if (W.packed) {
+          const int4 dim = W.seg_dim[g];
+          const uint32_t qy = (uint32_t)rintf((y + 64.0f) * 512.0f);
+          const int qw = (int)rintf(w * 512.0f) - col_base(dim.z, dim.w, iw[u]);
+          W.hq[q[u]] = qy | ((uint32_t)qw << 16);
+          W.hcol[q[u]] = (uint16_t)iw[u];
+        } else {
+          W.hyw[q[u]] = make_float2(y, w);
+        }
+        W.horig[q[u]] = (uint32_t)((long long)r[u].z - foff);
+      }
     }
   }
 }

@@ -45,6 +45,7 @@ constexpr int kMergeBins = 2048;             // w bins per (frame, sector) of th
 // grid and cluster arrays outgrow the L2); smaller ones in one pass
 constexpr long long kTwoPassMin = 1LL << 23;
 constexpr int kScatterParts = 4;             // blocks that share one segment in the second pass
+constexpr int kSegUnroll = 4;                // records a thread has in flight in the per-segment passes
 
 // error bits (device error word)
 constexpr uint32_t kErrInput = 1u;      // malformed cluster (sector/row range, non-finite)
