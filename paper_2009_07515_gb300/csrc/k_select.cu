@@ -271,7 +271,6 @@ __device__ __forceinline__ void mark_vicinity(const Work& W, const DevParams& Q,
 }
 template <bool kPacked>
 __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
-  const Votes votes(W);
   const uint32_t ntl = W.cnt->n_tracklets;
   int lane;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -280,7 +279,6 @@ __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
     if (W.tl_kept[t + 1] == k) continue;
     const uint32_t info = W.tl_info[t];
     const uint4 st = W.starts[t];
-    const unsigned long long key = votes.key(info & 255u, st.z);
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     const int g0 = (int)st.y, gb = g0 - (g0 % kSegPerFrame) % kNRow;
     const long long off = W.batch->f[g0 / kSegPerFrame].off;
@@ -296,7 +294,7 @@ __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
       bool mine = false;
       if (r <= top) {
         const uint32_t h = W.slab[slab_at(t, r)];
-        mine = h != kNoHit && votes.of(h) == key;
+        mine = h != kNoHit;  // k_kept left only the track's own hits
       }
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (m) last = c0 + 31 - __clz((int)m);
@@ -319,7 +317,7 @@ __global__ void __launch_bounds__(256) k_compress(Work W, DevParams Q) {
       uint32_t h = kNoHit;
       if (in) {
         h = W.slab[slab_at(t, r)];
-        mine = h != kNoHit && votes.of(h) == key;
+        mine = h != kNoHit;  // k_kept left only the track's own hits
       }
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (mine) {
