@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256) k_merge_heads(Work W) {
 
 constexpr int kMaxSeg = 18;  // segments of a chain: at most the sectors of one drift side
 
-__global__ void __launch_bounds__(128) k_merge_refit(Work W, DevParams Q) {
+__global__ void __launch_bounds__(128, 5) k_merge_refit(Work W, DevParams Q) {
   const uint32_t ntr = W.cnt->n_tracks;
   const int packed = W.packed;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntr; t += gridDim.x * blockDim.x) {
@@ -291,24 +291,22 @@ __global__ void __launch_bounds__(128) k_merge_refit(Work W, DevParams Q) {
     if (W.m_prev[t] != 0u) continue;
     const uint32_t m = W.m_hidx[t];
     const FrameIn F = W.batch->f[fr];
-    // the chain's segments (track, first hit, hits) and its hits copied in order, inner segment first
-    int seg_t[kMaxSeg];
-    long long seg_h0[kMaxSeg];
-    uint32_t seg_n[kMaxSeg];
+    // the chain's hits copied in order, inner segment first; per segment its end in that order and
+    // its sector, packed as end | sector << 16 (a chain holds at most kMaxSeg * kNRow hits), read
+    // only where a pass crosses from one segment into the next
+    uint32_t seg_es[kMaxSeg];
     const uint32_t h_out = W.m_hoff[t];
     uint32_t nh = 0;
-    int nseg = 0;
+    int nseg = 0, tm = (int)t;
     for (int s = (int)t; s >= 0 && nseg < kMaxSeg; s = W.m_next[s]) {
       const uint32_t n = track_nhits(W, (uint32_t)s, ntr);
       const long long h0 = W.tr_hoff[s];
       for (uint32_t i = 0; i < n; ++i) W.mt_hits[h_out + nh + i] = W.tr_hits[h0 + i];
-      seg_t[nseg] = s;
-      seg_h0[nseg] = h0;
-      seg_n[nseg] = n;
       nh += n;
+      seg_es[nseg] = nh | (uint32_t)W.tr_sector[s] << 16;
+      tm = s;
       ++nseg;
     }
-    const int tm = seg_t[nseg - 1];
     float Pr[5], Cr[15], xr = 0.f, chi_last = 0.f;
     int sr = W.tr_sector[t], nfit = 0;
     if (W.m_info[tm] >> 16 & 1u) {
@@ -318,34 +316,39 @@ __global__ void __launch_bounds__(128) k_merge_refit(Work W, DevParams Q) {
       for (int i = 0; i < 5; ++i) P[i] = om[i];
 #pragma unroll
       for (int i = 0; i < 15; ++i) Cs[i] = om[5 + i];
+      const uint32_t* mh = W.mt_hits + h_out;
       bool ok = true;
       for (int pass = 0; pass < Q.refit_passes && ok; ++pass) {
         const bool inward = pass != 1;
         float C[15];
 #pragma unroll
         for (int i = 0; i < 15; ++i) C[i] = Cs[i] * Q.refit_scale;
-        // hit cursor: segment j, hit i of the segment; the next hit's row and (y, w) are loaded one
-        // hit ahead, so their latency is not on the chain of dependent Kalman operations
+        // the current segment j spans hits [lo, hi) of the chain; the next hit's row and (y, w)
+        // are loaded one hit ahead, so their latency is not on the chain of dependent Kalman
+        // operations
         int j = inward ? nseg - 1 : 0;
-        int i = inward ? (int)seg_n[j] - 1 : 0;
-        int cur_sec = W.tr_sector[seg_t[j]], cur_row = -2;
+        uint32_t hi = seg_es[j] & 0xffffu, lo = j > 0 ? seg_es[j - 1] & 0xffffu : 0u;
+        int hsec = (int)(seg_es[j] >> 16);
+        int cur_sec = hsec, cur_row = -2;
         float cur_x = 0.f, chi_pass = 0.f;
         int n_pass = 0;
-        uint32_t hc = W.tr_hits[seg_h0[j] + i];
+        uint32_t k = inward ? nh - 1 : 0;
+        uint32_t hc = mh[k];
         int nrow = F.row[hc];
         float2 nc = cluster_yw(F, hc, packed);
         for (uint32_t k2 = 0; k2 < nh; ++k2) {
-          const int hsec = W.tr_sector[seg_t[j]];
+          if (k < lo || k >= hi) {
+            j += inward ? -1 : 1;
+            hi = seg_es[j] & 0xffffu;
+            lo = j > 0 ? seg_es[j - 1] & 0xffffu : 0u;
+            hsec = (int)(seg_es[j] >> 16);
+          }
           const int r = nrow;
           const float2 c = nc;
           // advance the cursor and prefetch the next hit
           if (k2 + 1 < nh) {
-            if (inward) {
-              if (--i < 0) { --j; i = (int)seg_n[j] - 1; }
-            } else {
-              if (++i >= (int)seg_n[j]) { ++j; i = 0; }
-            }
-            const uint32_t hn = W.tr_hits[seg_h0[j] + i];
+            k = inward ? k - 1 : k + 1;
+            const uint32_t hn = mh[k];
             nrow = F.row[hn];
             nc = cluster_yw(F, hn, packed);
           }

@@ -716,7 +716,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
       scan(W.m_hidx, W.m_hidx, &C->n_tracks, W.tcap, &C->n_merged);
       scan(W.m_hoff, W.m_hoff, &C->n_tracks, W.tcap, &C->n_merged_hits);
     }
-    ++nl; k_merge_refit<<<4 * G, 128, 0, s>>>(W, Q);
+    ++nl; k_merge_refit<<<5 * G, 128, 0, s>>>(W, Q);
     ++nl; k_merge_frames<<<1, 128, 0, s>>>(W);
   }
   ctx->stage_launches[kNumKernels - 1] = nl;
