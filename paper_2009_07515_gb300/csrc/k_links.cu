@@ -134,26 +134,34 @@ __device__ __forceinline__ void column_range(const Work& W, int g, float lo, flo
 //                 two lists. A lane whose list overflows walks its own bins instead.
 // All modes give the same result: the grid only bounds the candidates, the exact window test decides.
 constexpr int kK2Slot = 256;  // staged FP32 records per adjacent row per warp (twice as many 16-bit)
-constexpr int kK2Cap = 6;     // listed candidates per lane and adjacent row
+constexpr int kK2Cap = 6;     // candidates per lane and adjacent row listed by the converged scan (mode 2)
+constexpr int kK2Own = 16;    // candidate positions per lane and adjacent row listed by the own walk
 
 // Shared memory of one warp, by staging mode: the mbarrier (16 B), the two staging slots (modes 1
-// and 2; 16-byte aligned, bulk-copy destinations), the per-lane row r+1 candidate list, and the
-// row r-1 list (mode 2).
+// and 2; 16-byte aligned, bulk-copy destinations), then one list region: the converged scan's
+// per-lane candidate lists of both adjacent rows (mode 2), or the own walk's per-lane position
+// lists of both rows (every mode; a chunk uses one or the other: the own walk runs after a
+// converged scan only when the scan's lists overflowed, and then replaces them).
 constexpr int kK2ListBytes = kK2Cap * 32 * (8 + 4);
+constexpr int kK2OwnBytes = 2 * kK2Own * 32 * 4;
 __host__ __device__ constexpr int k2_warp_bytes(int mode) {
-  return 16 + (mode >= 1 ? 2 * (kK2Slot + 2) * 8 : 0) + (mode == 2 ? 2 : 1) * kK2ListBytes;
+  return 16 + (mode >= 1 ? 2 * (kK2Slot + 2) * 8 : 0) +
+         (mode == 2 && 2 * kK2ListBytes > kK2OwnBytes ? 2 * kK2ListBytes : kK2OwnBytes);
 }
 struct K2Warp {
   uint64_t* bar;
   float2* stage[2];  // [0] row r-1, [1] row r+1
-  float2* cand[2];   // [side][n * 32 + lane]
+  float2* cand[2];   // converged scan: [side][n * 32 + lane]
   int* pos[2];
+  int* own[2];       // own walk: [side][n * 32 + lane] candidate positions
   __device__ K2Warp(unsigned char* base, int mode) {
     bar = reinterpret_cast<uint64_t*>(base);
     unsigned char* p = base + 16;
     stage[0] = reinterpret_cast<float2*>(p);
     stage[1] = stage[0] + (kK2Slot + 2);
     if (mode >= 1) p += 2 * (kK2Slot + 2) * 8;
+    own[0] = reinterpret_cast<int*>(p);
+    own[1] = own[0] + kK2Own * 32;
     cand[1] = reinterpret_cast<float2*>(p);
     pos[1] = reinterpret_cast<int*>(p + kK2Cap * 32 * 8);
     p += kK2ListBytes;
@@ -161,6 +169,44 @@ struct K2Warp {
     pos[0] = reinterpret_cast<int*>(p + kK2Cap * 32 * 8);
   }
 };
+
+// Positions inside a lane's window of one adjacent row, listed in own[n * 32 + lane] for n < kK2Own:
+// one flat loop over the window's positions, a w-column's bin range after the other, so a warp
+// iterates as often as its lane with the most positions (nested column / position loops would
+// iterate, column by column, as often as the lane with the most positions in that column). Returns
+// the lane's count of positions inside the window (beyond kK2Own counted, not listed).
+template <bool kPacked>
+__device__ __forceinline__ int list_window(const Work& W, const GridWin& q, const RowView& v, bool staged, float yi,
+                                           float wi, float wy, float ww, int* own, int lane) {
+  int n = 0;
+  int cw = q.iw0;
+  uint32_t col = q.bb + (uint32_t)(cw * q.ny);
+  int p = (int)W.bin_start[col + q.iy0], pe = (int)W.bin_start[col + q.iy1 + 1];
+  int cb = col_base(q.cw0, q.cshift, cw);
+  for (;;) {
+    if (p >= pe) {
+      if (++cw > q.iw1) break;
+      col += (uint32_t)q.ny;
+      p = (int)W.bin_start[col + q.iy0];
+      pe = (int)W.bin_start[col + q.iy1 + 1];
+      cb = col_base(q.cw0, q.cshift, cw);
+      continue;
+    }
+    const float2 h = cand_at<kPacked>(W, v, staged, p, cb);
+    if (fabsf(h.x - yi) <= wy && fabsf(h.y - wi) <= ww) {
+      if (n < kK2Own) own[n * 32 + lane] = p;
+      ++n;
+    }
+    ++p;
+  }
+  return n;
+}
+
+// (y, w) of a listed candidate position of the window q (16-bit storage: its column from hcol)
+template <bool kPacked>
+__device__ __forceinline__ float2 cand_of(const Work& W, const GridWin& q, const RowView& v, bool staged, int p) {
+  return cand_at<kPacked>(W, v, staged, p, kPacked ? col_base(q.cw0, q.cshift, (int)W.hcol[p]) : 0);
+}
 
 template <bool kPacked>
 __device__ __forceinline__ void pair_step(const Work& W, int gd, int gu, float yi, float wi, float fm,
@@ -345,20 +391,26 @@ __global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q,
       const bool sd = cnt0 > 0, su = cnt1 > 0;
       const GridWin qd = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g - 1, yi, wi, wy_dn, ww_dn);
       const GridWin qu = grid_window(W.seg_bb, W.seg_dim, W.seg_geo, g + 1, yi, wi, wy_up, ww_up);
-      // row r+1 candidates inside the window
-      int nu = 0;
-      for (int cw = qu.iw0; cw <= qu.iw1; ++cw) {
-        const uint32_t col = qu.bb + (uint32_t)(cw * qu.ny);
-        const int pe = (int)W.bin_start[col + qu.iy1 + 1];
-        const int cb = col_base(qu.cw0, qu.cshift, cw);
-        for (int u = (int)W.bin_start[col + qu.iy0]; u < pe; ++u) {
-          const float2 hu = cand_at<kPacked>(W, vu, su, u, cb);
-          if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-          if (nu < kK2Cap) { S.cand[1][nu * 32 + lane] = hu; S.pos[1][nu * 32 + lane] = u; }
-          ++nu;
+      // both windows listed (flat walks), then every (d, u) pair in one flat loop: a warp iterates
+      // as often as its lane with the most pairs. A lane whose window holds more than kK2Own
+      // positions walks its windows nested instead, each row r-1 candidate against a fresh walk of
+      // the row r+1 window (same pairs, same result: the pair order is a total order).
+      const int nu = list_window<kPacked>(W, qu, vu, su, yi, wi, wy_up, ww_up, S.own[1], lane);
+      const int nd = nu > 0 && nu <= kK2Own ? list_window<kPacked>(W, qd, vd, sd, yi, wi, wy_dn, ww_dn, S.own[0], lane) : 0;
+      if (nu > 0 && nu <= kK2Own && nd <= kK2Own) {
+        const int np = nd * nu;
+        float2 hd = make_float2(0.f, 0.f);
+        int d = -1;
+        for (int k = 0, a = 0, c = 0; k < np; ++k) {
+          if (c == 0) {
+            d = S.own[0][a * 32 + lane];
+            hd = cand_of<kPacked>(W, qd, vd, sd, d);
+          }
+          const int u = S.own[1][c * 32 + lane];
+          pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, cand_of<kPacked>(W, qu, vu, su, u), u, best, bd, bu);
+          if (++c == nu) { c = 0; ++a; }
         }
-      }
-      if (nu > 0) {
+      } else if (nu > 0) {
         for (int cwd = qd.iw0; cwd <= qd.iw1; ++cwd) {
           const uint32_t cold = qd.bb + (uint32_t)(cwd * qd.ny);
           const int ped = (int)W.bin_start[cold + qd.iy1 + 1];
@@ -366,20 +418,14 @@ __global__ void __launch_bounds__(32 * kWarps) k_neighbours(Work W, DevParams Q,
           for (int d = (int)W.bin_start[cold + qd.iy0]; d < ped; ++d) {
             const float2 hd = cand_at<kPacked>(W, vd, sd, d, cbd);
             if (!(fabsf(hd.x - yi) <= wy_dn && fabsf(hd.y - wi) <= ww_dn)) continue;
-            if (nu <= kK2Cap) {
-              for (int c = 0; c < nu; ++c)
-                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, S.cand[1][c * 32 + lane],
-                                   S.pos[1][c * 32 + lane], best, bd, bu);
-            } else {
-              for (int cw = qu.iw0; cw <= qu.iw1; ++cw) {
-                const uint32_t col = qu.bb + (uint32_t)(cw * qu.ny);
-                const int pe = (int)W.bin_start[col + qu.iy1 + 1];
-                const int cb = col_base(qu.cw0, qu.cshift, cw);
-                for (int u = (int)W.bin_start[col + qu.iy0]; u < pe; ++u) {
-                  const float2 hu = cand_at<kPacked>(W, vu, su, u, cb);
-                  if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
-                  pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
-                }
+            for (int cw = qu.iw0; cw <= qu.iw1; ++cw) {
+              const uint32_t col = qu.bb + (uint32_t)(cw * qu.ny);
+              const int pe = (int)W.bin_start[col + qu.iy1 + 1];
+              const int cb = col_base(qu.cw0, qu.cshift, cw);
+              for (int u = (int)W.bin_start[col + qu.iy0]; u < pe; ++u) {
+                const float2 hu = cand_at<kPacked>(W, vu, su, u, cb);
+                if (!(fabsf(hu.x - yi) <= wy_up && fabsf(hu.y - wi) <= ww_up)) continue;
+                pair_step<kPacked>(W, g - 1, g + 1, yi, wi, fm, hd, d, hu, u, best, bd, bu);
               }
             }
           }
