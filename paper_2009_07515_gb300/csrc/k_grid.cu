@@ -13,7 +13,8 @@
 //   k_bin_rank    bin histogram; each cluster keeps its arrival rank inside its bin
 //   k_scatter     sorted (y, w) and input index at bin_start[bin] + rank
 //   (batches of more than kTwoPassMin clusters do these two steps per segment instead:
-//   k_seg_bucket, k_bin_rank_seg, k_scatter_seg; the allocation-free entry keeps the one-pass form)
+//   k_seg_bucket, k_bin_rank_seg, k_scatter_seg, with each segment's bins zeroed and scanned by the
+//   block that ranks it; the allocation-free entry keeps the one-pass form)
 //   scans         exclusive prefix sums with device-side lengths
 #include "tpc_dev.cuh"
 
@@ -444,14 +445,32 @@ __global__ void __launch_bounds__(256) k_seg_bucket(Work W) {
   }
 }
 
+// The bins the one-pass placement zeroes and scans (the per-segment passes do both per segment).
+__global__ void k_one_pass_bins(Work W) {
+  W.cnt->n_bins_1p = W.batch->ntot <= kTwoPassMin ? W.cnt->n_bins : 0u;
+}
+
+// One block per segment: its bin counters zeroed, its records ranked in their bins (atomics on the
+// counters), then the counters turned in place into the bins' first sorted positions: their
+// exclusive scan plus the segment's first position (a segment's bins and its positions follow the
+// same segment order, so this equals the scan over all bins). Block 0 also writes the end of the
+// last bin, bin_start[n_bins] = the batch's placed clusters.
+constexpr int kBinItems = 4;
 __global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
   if (W.batch->ntot <= kTwoPassMin) return;
   if (W.cnt->n_bins > (uint32_t)W.bcap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&W.cnt->err, kErrBins);
     return;
   }
+  __shared__ uint32_t warp_sums[32];
+  __shared__ uint32_t block_total;
   const int nseg = (int)W.cnt->nseg;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) W.bin_start[W.cnt->n_bins] = W.seg_start[nseg];
   for (int g = blockIdx.x; g < nseg; g += gridDim.x) {
+    const uint32_t bb = W.seg_bb[g], nb = W.seg_nb[g];
+    for (uint32_t j = threadIdx.x; j < nb; j += blockDim.x) W.bin_start[bb + j] = 0u;
+    __syncthreads();
     const uint32_t p1 = W.seg_start[g + 1];
     // kSegUnroll records per thread in flight: their loads, then their atomics, then the ranks
     for (uint32_t b = W.seg_start[g] + threadIdx.x; b < p1; b += blockDim.x * kSegUnroll) {
@@ -471,6 +490,46 @@ __global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
 #pragma unroll
       for (int u = 0; u < kSegUnroll; ++u)
         if (b + u * blockDim.x < p1) W.rank[b + u * blockDim.x] = rk[u];
+    }
+    __syncthreads();
+    // exclusive scan of the segment's counters in place, kBinItems consecutive bins per thread
+    uint32_t carry = W.seg_start[g];
+    for (uint32_t base = 0; base < nb; base += blockDim.x * kBinItems) {
+      const uint32_t i0 = base + threadIdx.x * kBinItems;
+      uint32_t v[kBinItems], sum = 0;
+#pragma unroll
+      for (int k = 0; k < kBinItems; ++k) {
+        v[k] = i0 + k < nb ? __ldcg(&W.bin_start[bb + i0 + k]) : 0u;
+        sum += v[k];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) warp_sums[wid] = x;
+      __syncthreads();
+      if (wid == 0) {
+        const uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+        uint32_t z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, z, o);
+          if (lane >= o) z += y;
+        }
+        warp_sums[lane] = z - w;
+        if (lane == 31) block_total = z;
+      }
+      __syncthreads();
+      uint32_t run = carry + warp_sums[wid] + (x - sum);
+#pragma unroll
+      for (int k = 0; k < kBinItems; ++k) {
+        if (i0 + k < nb) W.bin_start[bb + i0 + k] = run;
+        run += v[k];
+      }
+      carry += block_total;
+      __syncthreads();
     }
   }
 }

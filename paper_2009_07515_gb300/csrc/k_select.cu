@@ -38,7 +38,10 @@ struct Votes {
 
 // One warp per tracklet (grid-stride over tracklets): the lanes take the tracklet's rows 32 at a
 // time, so the row loop's dependent loads (slab entry, then the hit's word) overlap across lanes;
-// a tracklet's rows are consecutive slab words, so each pass reads one or two 128-byte lines.
+// a tracklet's rows are consecutive slab words, so each pass reads one or two 128-byte lines. The
+// selection kernels read (and k_kept clears) the slab with streaming cache hints: each slab line is
+// used once per kernel, and evicting it first keeps the L2 for the vote and cluster words that the
+// tracklets in flight share.
 __device__ __forceinline__ uint32_t warp_global(int& lane) {
   lane = threadIdx.x & 31;
   return (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(256) k_votes_warp(Work W, DevParams Q) {
     const unsigned long long key = votes.key(nh, W.starts[t].z);
     const int ref = (info >> 8) & 255, top = (info >> 16) & 255;
     for (int r = ref + lane; r <= top; r += 32) {
-      const uint32_t h = W.slab[slab_at(t, r)];
+      const uint32_t h = __ldcs(&W.slab[slab_at(t, r)]);
       if (h != kNoHit) votes.cast(h, key);
     }
   }
@@ -78,9 +81,9 @@ __global__ void __launch_bounds__(256) k_kept_warp(Work W, DevParams Q) {
         const int r = r0 + lane;
         bool mine = false;
         if (r <= top) {
-          const uint32_t h = W.slab[slab_at(t, r)];
+          const uint32_t h = __ldcs(&W.slab[slab_at(t, r)]);
           mine = h != kNoHit && votes.of(h) == key;
-          if (h != kNoHit && !mine) W.slab[slab_at(t, r)] = kNoHit;  // a hit the tracklet lost
+          if (h != kNoHit && !mine) __stcs(&W.slab[slab_at(t, r)], kNoHit);  // a hit the tracklet lost
         }
         kept += (uint32_t)__popc(__ballot_sync(0xffffffffu, mine));
       }
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(256) k_write_tracks_warp(Work W, DevParams Q) 
     for (int r0 = ref; r0 <= top; r0 += 32) {
       const int r = r0 + lane;
       uint32_t h = kNoHit;
-      if (r <= top) h = W.slab[slab_at(t, r)];
+      if (r <= top) h = __ldcs(&W.slab[slab_at(t, r)]);
       const bool mine = h != kNoHit;
       const uint32_t m = __ballot_sync(0xffffffffu, mine);
       if (mine) W.tr_hits[off + (uint32_t)__popc(m & ((1u << lane) - 1u))] = W.horig[h];
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256) k_votes_thread(Work W, DevParams Q) {
     const RowRange rr = warp_rows(on, ref, top);
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
-      const uint32_t h = W.slab[slab_at(t, r)];
+      const uint32_t h = __ldcs(&W.slab[slab_at(t, r)]);
       if (h != kNoHit) votes.cast(h, key);
     }
   }
@@ -182,10 +185,10 @@ __global__ void __launch_bounds__(256) k_kept_thread(Work W, DevParams Q) {
     uint32_t kept = 0;
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
-      const uint32_t h = W.slab[slab_at(t, r)];
+      const uint32_t h = __ldcs(&W.slab[slab_at(t, r)]);
       if (h == kNoHit) continue;
       if (votes.of(h) == key) ++kept;
-      else W.slab[slab_at(t, r)] = kNoHit;  // a hit the tracklet lost
+      else __stcs(&W.slab[slab_at(t, r)], kNoHit);  // a hit the tracklet lost
     }
     const uint32_t acc = (on && (int)kept >= Q.nmin && 2u * kept >= nh) ? 1u : 0u;
     if (t < ntl) {
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(256) k_write_tracks_thread(Work W, DevParams Q
     const RowRange rr = warp_rows(on, ref, top);
     for (int r = rr.lo; r <= rr.hi; ++r) {
       if (!on || r < ref || r > top) continue;
-      const uint32_t h = W.slab[slab_at(t, r)];  // k_kept left only the track's own hits
+      const uint32_t h = __ldcs(&W.slab[slab_at(t, r)]);  // k_kept left only the track's own hits
       if (h != kNoHit) W.tr_hits[off++] = W.horig[h];
     }
   }

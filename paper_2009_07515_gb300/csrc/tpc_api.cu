@@ -47,6 +47,7 @@ __global__ void k_clean(Work, DevParams);
 __global__ void k_starts(Work, DevParams);
 __global__ void k_start_order(Work);
 __global__ void k_chains(Work, int);
+__global__ void k_one_pass_bins(Work);
 __global__ void k_length_offsets(Work);
 __global__ void k_length_scatter(Work, int);
 bool launch_tracklets(int threads, int regs, int ilp, int packed, int grid, cudaStream_t s, const Work& W, const DevParams& Q,
@@ -632,8 +633,9 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
     scan(W.seg_nb, W.seg_bb, &C->nseg, W.scap, &C->n_bins);
     scan(W.seg_cnt, W.seg_start, &C->nseg, W.scap, &C->n_sorted);
   }
-  mark(ki++);  // zero_bins
-  ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins, W.bcap + 1, 1, 1);
+  ++nl; k_one_pass_bins<<<1, 1, 0, s>>>(W);
+  mark(ki++);  // zero_bins (the one-pass placement's; the per-segment passes zero their own)
+  ++nl; k_zero_u32<<<4 * G, 256, 0, s>>>(W.bin_start, &C->n_bins_1p, W.bcap + 1, 1, 1);
   ++nl; k_zero_u32<<<G, 256, 0, s>>>(W.seg_cur, &C->nseg, W.scap, 0, 1);
   mark(ki++);  // bin_rank: one pass for small batches; for large ones the clusters are appended to
   // their segments, then ranked in their bins per segment (each kernel returns at once on the
@@ -641,8 +643,8 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   ++nl; k_bin_rank<<<8 * G, 256, 0, s>>>(W, 1);
   ++nl; k_seg_bucket<<<8 * G, 256, 0, s>>>(W);
   ++nl; k_bin_rank_seg<<<G, 1024, 0, s>>>(W);
-  mark(ki++);  // scan_bins
-  scan(W.bin_start, W.bin_start, &C->n_bins, W.bcap, &C->n_sorted);
+  mark(ki++);  // scan_bins (the one-pass placement's; the per-segment passes scan in k_bin_rank_seg)
+  scan(W.bin_start, W.bin_start, &C->n_bins_1p, W.bcap, &C->scan_sink);
   mark(ki++);  // scatter: one pass, or per segment into the segment's range of sorted positions
   ++nl; k_scatter<<<8 * G, 256, 0, s>>>(W, 1);
   ++nl; k_scatter_seg<<<(G / kScatterParts) * kScatterParts, 1024, 0, s>>>(W);

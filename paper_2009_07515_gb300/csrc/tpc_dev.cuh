@@ -116,6 +116,9 @@ struct DevCounters {
   uint32_t n_chunks;      // 32-hit chunks of the neighbour kernel
   uint32_t k2_next;       // chunk work counter of the neighbour kernel
   uint32_t n_bins;        // total bins of the batch
+  uint32_t n_bins_1p;     // bins the one-pass placement zeroes and scans: n_bins, or 0 when the
+                          // per-segment passes place the batch (they zero and scan each segment's bins)
+  uint32_t scan_sink;     // total of a scan whose total is already known
   uint32_t n_sorted;      // clusters placed in the grid
   uint32_t n_tracks;
   uint32_t n_track_hits;
