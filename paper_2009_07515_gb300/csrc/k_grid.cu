@@ -456,7 +456,7 @@ __global__ void k_one_pass_bins(Work W) {
 // same segment order, so this equals the scan over all bins). Block 0 also writes the end of the
 // last bin, bin_start[n_bins] = the batch's placed clusters.
 constexpr int kBinItems = 4;
-__global__ void __launch_bounds__(1024) k_bin_rank_seg(Work W) {
+__global__ void __launch_bounds__(1024, 2) k_bin_rank_seg(Work W) {
   if (W.batch->ntot <= kTwoPassMin) return;
   if (W.cnt->n_bins > (uint32_t)W.bcap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&W.cnt->err, kErrBins);

@@ -642,7 +642,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   // other side of kTwoPassMin, so one captured graph serves every batch size)
   ++nl; k_bin_rank<<<8 * G, 256, 0, s>>>(W, 1);
   ++nl; k_seg_bucket<<<8 * G, 256, 0, s>>>(W);
-  ++nl; k_bin_rank_seg<<<G, 1024, 0, s>>>(W);
+  ++nl; k_bin_rank_seg<<<2 * G, 1024, 0, s>>>(W);
   mark(ki++);  // scan_bins (the one-pass placement's; the per-segment passes scan in k_bin_rank_seg)
   scan(W.bin_start, W.bin_start, &C->n_bins_1p, W.bcap, &C->scan_sink);
   mark(ki++);  // scatter: one pass, or per segment into the segment's range of sorted positions
