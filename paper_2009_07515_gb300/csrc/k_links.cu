@@ -182,13 +182,23 @@ __device__ __forceinline__ int list_window(const Work& W, const GridWin& q, cons
   int cw = q.iw0;
   uint32_t col = q.bb + (uint32_t)(cw * q.ny);
   int p = (int)W.bin_start[col + q.iy0], pe = (int)W.bin_start[col + q.iy1 + 1];
+  // the next column's range is loaded one column ahead, so its latency overlaps this column's tests
+  int np = 0, npe = 0;
+  if (cw < q.iw1) {
+    np = (int)W.bin_start[col + (uint32_t)q.ny + q.iy0];
+    npe = (int)W.bin_start[col + (uint32_t)q.ny + q.iy1 + 1];
+  }
   int cb = col_base(q.cw0, q.cshift, cw);
   for (;;) {
     if (p >= pe) {
       if (++cw > q.iw1) break;
       col += (uint32_t)q.ny;
-      p = (int)W.bin_start[col + q.iy0];
-      pe = (int)W.bin_start[col + q.iy1 + 1];
+      p = np;
+      pe = npe;
+      if (cw < q.iw1) {
+        np = (int)W.bin_start[col + (uint32_t)q.ny + q.iy0];
+        npe = (int)W.bin_start[col + (uint32_t)q.ny + q.iy1 + 1];
+      }
       cb = col_base(q.cw0, q.cshift, cw);
       continue;
     }
