@@ -264,8 +264,12 @@ __global__ void __launch_bounds__(kThreads, 65536 / (kThreads * kRegs)) k_trackl
         kf_update(Q, V, P, C, c.x, c.y);
 #pragma unroll
         for (int i = 0; i < 5; ++i) sv[i][tid] = P[i];
+        // the saved covariance is read only at the end of the inward pass (the tracklet's fit); the
+        // inward restart after the outward pass takes the parameters alone
+        if (inward) {
 #pragma unroll
-        for (int i = 0; i < 15; ++i) sv[5 + i][tid] = C[i];
+          for (int i = 0; i < 15; ++i) sv[5 + i][tid] = C[i];
+        }
         nmiss = 0;
         if (inward) {
           nh += 1;
