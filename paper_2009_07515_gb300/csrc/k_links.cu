@@ -124,10 +124,10 @@ __device__ __forceinline__ void column_range(const Work& W, int g, float lo, flo
 // One warp takes 32 consecutive hits of a row (a chunk); with use_tma >= 1 lane 0 stages the
 // w-columns of rows r-1 and r+1 that the 32 windows touch into the warp's own shared-memory slots
 // (two bulk copies, one mbarrier per warp), so warps never wait for one another.
-//   use_tma 0, 1: each lane walks its own window, column by column and position by position
-//                 (from the stage when its side is staged: the union of the 32 windows lies inside
-//                 it; through L1 otherwise), listing its row r+1 candidates, then pairs each row r-1
-//                 candidate with the list;
+//   use_tma 0, 1: each lane walks its own windows, one flat loop over each window's positions
+//                 across its w-columns (from the stage when its side is staged: the union of the 32
+//                 windows lies inside it; through L1 otherwise), listing the positions inside its
+//                 row r+1 and row r-1 windows, then tests every pair of the two lists in one loop;
 //   use_tma 2:    when both ranges are staged, the warp scans each staged range once, all lanes
 //                 together (one candidate per iteration, broadcast from shared memory): a lane whose
 //                 window holds the candidate appends it to its own list; each lane then pairs its
