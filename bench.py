@@ -279,6 +279,7 @@ def cpu_baseline(frame, n_threads: int, budget_s: float = 12.0, window: int = 0)
     what = (f"sectors 0-{k - 1} whole" if window >= per_sector_n else
             f"sectors 0-{k - 1}, in each the {window} clusters of a drift-coordinate window around its median")
     return {"value": n / dt, "unit": UNIT, "cores": int(n_threads), "kind": "oracle", "window": window,
+            "clusters": n, "seconds": dt,
             "sample": f"{what} ({n} clusters of the workload frame), FP32 oracle, {dt:.2f} s"}
 
 
@@ -639,12 +640,15 @@ def run_reference(args, ws, rank):
         cpu_baseline(frame, cores, window=first["window"])
     times = [cpu_baseline(frame, cores, window=first["window"]) for _ in range(args.steps)]
     value = float(np.mean([t["value"] for t in times]))
+    # a step is one bounded sample of the workload (its clusters and wall time are in the line)
+    ms_per_step = float(np.mean([t["seconds"] for t in times]) * 1e3)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "parallelism": "host threads over sectors"},
             "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": times[0]["sample"], "value": value},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": times[0]["sample"], "value": value,
+                             "clusters_per_step": times[0]["clusters"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
