@@ -19,8 +19,9 @@
 //   k_merge_outer   frame, reference and last row of each track, its outer state, bin counts
 //   (exclusive scan of the bin counts)
 //   k_merge_fill    each track into its bin's list
-//   k_merge_match   candidates of each track in the neighbouring sectors' bins around its outer w:
-//                   its best partner, and an atomic minimum of (chi2, index) on each partner
+//   k_merge_match   candidates of each track in the neighbouring sectors' bins around its outer w,
+//                   queued per warp and evaluated 32 at a time: an atomic minimum of (chi2, index)
+//                   on each track's best inner and best outer partner
 //   k_merge_link    mutual best partners linked; chain heads and their hit counts
 //   (exclusive scans: merged index and first hit of each chain head)
 //   k_merge_refit   each chain's hits copied in order, the refit, the merged track written
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(256) k_merge_outer(Work W, DevParams Q) {
     for (int i = 0; i < 15; ++i) o[5 + i] = C[i];
     W.m_info[k] = (uint32_t)last | (uint32_t)ref << 8 | (ok ? 1u : 0u) << 16 | (uint32_t)fr << 17;
     W.m_bestA[k] = ~0ull;
+    W.m_bestB[k] = ~0ull;
     W.m_prev[k] = 0u;
     const int sec = W.tr_sector[k];
     atomicAdd(W.m_bin + merge_bin(fr, sec, merge_bins(W.cnt, fr), W.tr_param[(long long)k * 5 + 1]), 1u);
@@ -197,57 +199,101 @@ __global__ void __launch_bounds__(256) k_merge_fill(Work W) {
   }
 }
 
+// The chi2 of a candidate pair (A, B): A's outer state rotated into B's frame and carried to B's
+// reference row, against B's fit; an atomic minimum of (chi2 bits, index) on both tracks' best
+// partner words when it passes the cut (chi2 >= 0, so its bits order like its value).
+__device__ __forceinline__ void merge_pair(const Work& W, const DevParams& Q, uint32_t a, uint32_t b) {
+  const int last = (int)(W.m_info[a] & 255u);
+  const int ref_b = (int)((W.m_info[b] >> 8) & 255u);
+  const float* oa = W.m_state + (long long)a * 20;
+  const float* pb = W.tr_param + (long long)b * 5;
+  const float* cb = W.tr_cov + (long long)b * 15;
+  float P[5], C[15], x = row_x(Q, last);
+#pragma unroll
+  for (int q = 0; q < 5; ++q) P[q] = oa[q];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) C[q] = oa[5 + q];
+  if (!rotate_state(Q, P, C, x, Q.rot_c, rot_sign(W.tr_sector[a], W.tr_sector[b]) * Q.rot_s)) return;
+  if (!kf_propagate(Q, P, C, x, row_x(Q, ref_b))) return;
+  float S[15], d[5];
+#pragma unroll
+  for (int q = 0; q < 15; ++q) S[q] = C[q] + cb[q];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) d[q] = P[q] - pb[q];
+  const float chi = chi2_5(S, d);
+  if (!(chi <= Q.merge_chi2_max)) return;
+  const unsigned long long cbits = (unsigned long long)__float_as_uint(chi) << 32;
+  atomicMin(W.m_bestA + b, cbits | a);
+  atomicMin(W.m_bestB + a, cbits | b);
+}
+
+// One lane per track A walks A's candidate range in each phi-neighbouring sector's w bins, one
+// candidate per iteration, and applies the cheap cuts (B's reference row 1 .. merge_gap_rows rows
+// above A's last row, |w_B(x_ref) - w_A(outer)| <= merge_dw). The pairs that pass go to the warp's
+// queue in shared memory; whenever it holds 32 pairs, the 32 lanes compute their chi2 together
+// (rotation, one helix step, Cholesky), so the expensive arithmetic runs on full warps although
+// only a few tracks of a warp have candidates at a time.
+constexpr int kMatchQ = 64;
 __global__ void __launch_bounds__(256) k_merge_match(Work W, DevParams Q) {
+  __shared__ uint2 queue[256 / 32][kMatchQ];
+  const int lane = threadIdx.x & 31;
+  uint2* q = queue[threadIdx.x >> 5];
+  const unsigned below = (1u << lane) - 1u;
   const uint32_t ntr = W.cnt->n_tracks;
-  for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < ntr; a += gridDim.x * blockDim.x) {
-    const uint32_t ia = W.m_info[a];
-    int best = -1;
-    float best_chi = __int_as_float(0x7f800000);
-    if (ia >> 16 & 1u) {
-      const int fr = (int)(ia >> 17), last = (int)(ia & 255u);
-      const int sa = W.tr_sector[a], side = sa / 18, ka = sa % 18;
-      const float* oa = W.m_state + (long long)a * 20;
-      const float wa = oa[1];
-      const MergeBins mb = merge_bins(W.cnt, fr);
-      const float pad = fabsf(wa) * 1.0e-6f + 1.0e-6f;
-      const float xa = row_x(Q, last);
-      for (int dir = -1; dir <= 1; dir += 2) {
-        const int sb = side * 18 + (ka + dir + 18) % 18;
-        const long long b0 = merge_bin(fr, sb, mb, (wa - Q.merge_dw) - pad);
-        const long long b1 = merge_bin(fr, sb, mb, (wa + Q.merge_dw) + pad);
-        const uint32_t e1 = W.m_bin[b1];
-        for (uint32_t i = b0 > 0 ? W.m_bin[b0 - 1] : 0u; i < e1; ++i) {
-          const uint32_t b = W.m_list[i];
-          const int ref_b = (int)((W.m_info[b] >> 8) & 255u);
-          const int g = ref_b - last;
-          if (g < 1 || g > Q.merge_gap_rows) continue;
-          const float* pb = W.tr_param + (long long)b * 5;
-          if (!(fabsf(pb[1] - wa) <= Q.merge_dw)) continue;
-          float P[5], C[15], x = xa;
-#pragma unroll
-          for (int q = 0; q < 5; ++q) P[q] = oa[q];
-#pragma unroll
-          for (int q = 0; q < 15; ++q) C[q] = oa[5 + q];
-          if (!rotate_state(Q, P, C, x, Q.rot_c, rot_sign(sa, sb) * Q.rot_s)) continue;
-          if (!kf_propagate(Q, P, C, x, row_x(Q, ref_b))) continue;
-          float S[15], d[5];
-          const float* cb = W.tr_cov + (long long)b * 15;
-#pragma unroll
-          for (int q = 0; q < 15; ++q) S[q] = C[q] + cb[q];
-#pragma unroll
-          for (int q = 0; q < 5; ++q) d[q] = P[q] - pb[q];
-          const float chi = chi2_5(S, d);
-          if (!(chi <= Q.merge_chi2_max)) continue;
-          if (chi < best_chi || (chi == best_chi && (int)b < best)) {
-            best_chi = chi;
-            best = (int)b;
-          }
-          atomicMin(W.m_bestA + b, (unsigned long long)__float_as_uint(chi) << 32 | a);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  int qn = 0;  // pairs in the warp's queue (warp-uniform)
+  for (uint32_t a0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); a0 < ntr; a0 += stride) {
+    const uint32_t a = a0 + (uint32_t)lane;
+    // the lane's two candidate ranges [i, e) and [i2, e2) of the list of bin members
+    uint32_t i = 0, e = 0, i2 = 0, e2 = 0;
+    int last = 0;
+    float wa = 0.f;
+    if (a < ntr) {
+      const uint32_t ia = W.m_info[a];
+      if (ia >> 16 & 1u) {
+        const int fr = (int)(ia >> 17);
+        last = (int)(ia & 255u);
+        const int sa = W.tr_sector[a], side = sa / 18, ka = sa % 18;
+        wa = W.m_state[(long long)a * 20 + 1];
+        const MergeBins mb = merge_bins(W.cnt, fr);
+        const float pad = fabsf(wa) * 1.0e-6f + 1.0e-6f;
+        for (int dir = -1; dir <= 1; dir += 2) {
+          const int sb = side * 18 + (ka + dir + 18) % 18;
+          const long long b0 = merge_bin(fr, sb, mb, (wa - Q.merge_dw) - pad);
+          const long long b1 = merge_bin(fr, sb, mb, (wa + Q.merge_dw) + pad);
+          const uint32_t lo = b0 > 0 ? W.m_bin[b0 - 1] : 0u, hi = W.m_bin[b1];
+          if (dir < 0) { i = lo; e = hi; } else { i2 = lo; e2 = hi; }
         }
       }
     }
-    W.m_bestB[a] = best;
-    W.m_chi[a] = best_chi;
+    for (;;) {
+      if (i >= e && i2 < e2) { i = i2; e = e2; i2 = e2; }
+      const bool more = i < e;
+      if (!__any_sync(0xffffffffu, more)) break;
+      bool pass = false;
+      uint32_t b = 0;
+      if (more) {
+        b = W.m_list[i++];
+        const int g = (int)((W.m_info[b] >> 8) & 255u) - last;
+        pass = g >= 1 && g <= Q.merge_gap_rows && fabsf(W.tr_param[(long long)b * 5 + 1] - wa) <= Q.merge_dw;
+      }
+      const unsigned pm = __ballot_sync(0xffffffffu, pass);
+      if (pass) q[qn + __popc(pm & below)] = make_uint2(a, b);
+      qn += __popc(pm);
+      __syncwarp();
+      if (qn >= 32) {
+        const uint2 pr = q[lane];
+        merge_pair(W, Q, pr.x, pr.y);
+        __syncwarp();
+        if (lane < qn - 32) q[lane] = q[32 + lane];
+        qn -= 32;
+        __syncwarp();
+      }
+    }
+  }
+  if (lane < qn) {
+    const uint2 pr = q[lane];
+    merge_pair(W, Q, pr.x, pr.y);
   }
 }
 
@@ -255,7 +301,10 @@ __global__ void __launch_bounds__(256) k_merge_match(Work W, DevParams Q) {
 __global__ void __launch_bounds__(256) k_merge_link(Work W) {
   const uint32_t ntr = W.cnt->n_tracks;
   for (uint32_t a = blockIdx.x * blockDim.x + threadIdx.x; a < ntr; a += gridDim.x * blockDim.x) {
-    const int b = W.m_bestB[a];
+    // A's best outer partner and its chi2 (+inf and -1 when A has none)
+    const unsigned long long kb = W.m_bestB[a];
+    const int b = kb == ~0ull ? -1 : (int)(uint32_t)(kb & 0xFFFFFFFFull);
+    W.m_chi[a] = kb == ~0ull ? __int_as_float(0x7f800000) : __uint_as_float((uint32_t)(kb >> 32));
     const bool link = b >= 0 && (uint32_t)(W.m_bestA[b] & 0xFFFFFFFFull) == a;
     W.m_next[a] = link ? b : -1;
     if (link) W.m_prev[b] = 1u;

@@ -467,7 +467,7 @@ int alloc_workspace(tpc_ctx* ctx, long long ncap, long long tcap, int nf_cap, st
       {(void**)&W.m_bin, merge ? 4 * (size_t)(mbcap + 1) : 0},
       {(void**)&W.m_list, merge ? 4 * (size_t)ws->tcap : 0},
       {(void**)&W.m_bestA, merge ? 8 * (size_t)ws->tcap : 0},
-      {(void**)&W.m_bestB, merge ? 4 * (size_t)ws->tcap : 0},
+      {(void**)&W.m_bestB, merge ? 8 * (size_t)ws->tcap : 0},
       {(void**)&W.m_chi, merge ? 4 * (size_t)ws->tcap : 0},
       {(void**)&W.m_next, merge ? 4 * (size_t)ws->tcap : 0},
       {(void**)&W.m_prev, merge ? 4 * (size_t)ws->tcap : 0},

@@ -192,7 +192,7 @@ struct Work {
   uint32_t* m_bin;       // [mbcap + 1] tracks per (frame, sector, w bin) -> scanned -> bin ends
   uint32_t* m_list;      // [tcap] tracks in bin order
   unsigned long long* m_bestA;  // [tcap] best inner partner of each track: chi2 bits << 32 | index
-  int32_t* m_bestB;      // [tcap] best outer partner, -1 if none
+  unsigned long long* m_bestB;  // [tcap] best outer partner of each track: chi2 bits << 32 | index
   float* m_chi;          // [tcap] its chi2
   int32_t* m_next;       // [tcap] linked outer partner, -1 if none
   uint32_t* m_prev;      // [tcap] 1 if linked from an inner partner
