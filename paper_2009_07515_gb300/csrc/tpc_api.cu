@@ -705,7 +705,7 @@ int enqueue_sequence(tpc_ctx* ctx, Workspace& ws, cudaStream_t s, bool timing) {
   mark(ki++);  // merge
   if (W.m_state) {
     ++nl; k_zero_u32<<<2 * G, 256, 0, s>>>(W.m_bin, nullptr, W.mbcap + 1, 0, 1);
-    ++nl; k_merge_outer<<<2 * G, 256, 0, s>>>(W, Q);
+    ++nl; k_merge_outer<<<4 * G, 256, 0, s>>>(W, Q);
     scan(W.m_bin, W.m_bin, nullptr, W.mbcap, &C->n_merge_bins);
     ++nl; k_merge_fill<<<2 * G, 256, 0, s>>>(W);
     ++nl; k_merge_match<<<4 * G, 256, 0, s>>>(W, Q);
