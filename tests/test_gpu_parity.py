@@ -67,6 +67,24 @@ def test_links_and_tracks_match_fp32_oracle(tracker, cfg, n_threads):
     assert gpu["n_tracks"] > 500
 
 
+@pytest.mark.parametrize("packed", [0, 1], ids=["fp32", "16bit"])
+def test_dense_windows_match_oracle(tracker, tracker16, packed, n_threads):
+    """Six central-like collisions at one drift time (8.9e6 clusters, so the grid is placed by the
+    per-segment passes): the neighbour windows of the inner rows hold 16-19 candidates on average and
+    up to about 37, so the neighbour search runs both its listed pairs (up to 16 positions per window)
+    and its nested walk beyond them; links and tracks against the FP32 oracle as above."""
+    f = synth.generate("pbpb_2x10000", n_collisions=6, t_zero=1)
+    assert f.n > (1 << 23)
+    gpu, links = run_gpu(tracker16 if packed else tracker, f)
+    orc = oracle.track(f.sector, f.row, f.y, f.w, precision="f32", packed=bool(packed), n_threads=n_threads)
+    for k, name in enumerate(("up", "down", "up_c", "down_c")):
+        diff = np.flatnonzero(links[k] != getattr(orc, name))
+        assert np.all(orc.nb_margin[diff] < 1e-5), f"{name}: {len(diff)} untraced link differences"
+        assert len(diff) <= 1e-4 * f.n
+    compare_tracks(gpu, orc)
+    assert gpu["n_tracks"] > 10000
+
+
 @pytest.mark.parametrize("cfg", ["pp_500", "pbpb_2x10000", "batch16"])
 def test_16bit_storage_matches_oracle_on_read_back_clusters(tracker16, cfg, n_threads):
     """16-bit cluster storage: the GPU equals the FP32 oracle run on the read-back coordinates."""
