@@ -329,6 +329,10 @@ struct tpc_ctx {
   bool timing = false;
   cudaEvent_t ev[kNumKernels + 1] = {nullptr};
   cudaEvent_t ev_sync = nullptr;
+  // serving: end of the last launched tracking of a large batch (kServeSerialClusters), which the
+  // next large batch's tracking waits for on its own slot
+  cudaEvent_t ev_track = nullptr;
+  bool large_launched = false;
   float ms[kNumKernels] = {0};
   int64_t launches[kNumKernels] = {0};
   int64_t stage_launches[kNumKernels] = {0};
@@ -365,6 +369,12 @@ constexpr long long kSmallScanCap = 1LL << 16;
 
 // serving: queued frames join one batch only up to this many clusters (a larger frame goes alone)
 constexpr long long kServeBatchClusters = 1LL << 21;
+// Batches above this many clusters track one at a time across the slots: each fills the GPU for
+// tens of milliseconds, so two of them side by side only share the SMs and the L2 and end together,
+// and the slots then copy their inputs and results at the same time while the GPU idles. One after
+// the other, a slot's uploads and result copies run during the other slot's tracking. Smaller
+// batches still run side by side, where the overlap of their latency-bound tails pays.
+constexpr long long kServeSerialClusters = 1LL << 24;
 
 // grid occupancies the autotuner times, finest first
 constexpr float kTunerOccupancies[] = {0.35f, 0.5f, 0.7f, 1.0f, 2.0f};
@@ -1291,6 +1301,7 @@ int tpc_create(const tpc_params* p, tpc_ctx** out) {
     cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     for (int k = 0; k <= kNumKernels; ++k) cudaEventCreate(&ctx->ev[k]);
     cudaEventCreateWithFlags(&ctx->ev_sync, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&ctx->ev_track, cudaEventDisableTiming);
     ctx->slots.resize(2);
     for (auto& sl : ctx->slots) cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     // slot capacity: the largest batch whose workspace and inputs fit half of the HBM budget at
@@ -1339,6 +1350,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   for (int k = 0; k <= kNumKernels; ++k)
     if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
   if (ctx->ev_sync) cudaEventDestroy(ctx->ev_sync);
+  if (ctx->ev_track) cudaEventDestroy(ctx->ev_track);
   CfState& cf = ctx->cf;
   if (cf.dev) cudaFree(cf.dev);
   if (cf.map) cudaFree(cf.map);
@@ -1737,9 +1749,15 @@ int serve_step(tpc_ctx* ctx) {
       if (rc) return rc;
       f->state = 2;
     }
+    const bool large = n > kServeSerialClusters;
+    if (large && ctx->large_launched) CK(cudaStreamWaitEvent(sl.stream, ctx->ev_track, 0));
     std::shared_ptr<Workspace> ws;
     int rc = run_batch(ctx, batch, sl.stream, ws, sl.ws);
     if (rc) return rc;
+    if (large) {
+      CK(cudaEventRecord(ctx->ev_track, sl.stream));
+      ctx->large_launched = true;
+    }
     sl.frames.clear();
     for (Frame* f : batch) sl.frames.push_back(f->id);
     sl.busy = true;
