@@ -370,10 +370,10 @@ constexpr long long kSmallScanCap = 1LL << 16;
 // serving: queued frames join one batch only up to this many clusters (a larger frame goes alone)
 constexpr long long kServeBatchClusters = 1LL << 21;
 // Batches above this many clusters track one at a time across the slots: each fills the GPU for
-// tens of milliseconds, so two of them side by side only share the SMs and the L2 and end together,
-// and the slots then copy their inputs and results at the same time while the GPU idles. One after
-// the other, a slot's uploads and result copies run during the other slot's tracking. Smaller
-// batches still run side by side, where the overlap of their latency-bound tails pays.
+// tens of milliseconds, and two of them side by side left their uploads and result copies exposed
+// (the end-to-end time of a full-size frame was about its tracking plus its copies). One after the
+// other, a slot's uploads and result copies run during the other slot's tracking. Smaller batches
+// still run side by side, where the overlap of their latency-bound tails pays.
 constexpr long long kServeSerialClusters = 1LL << 24;
 
 // grid occupancies the autotuner times, finest first
